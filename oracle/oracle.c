@@ -1,0 +1,428 @@
+/*
+ * CPU oracle for the GAPA critical-node-detection hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline arm may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; both follow the same written
+ * definitions independently.
+ *
+ * What it computes (paper: Yu et al., "Efficient Parallel Genetic Algorithm for
+ * Perturbed Substructure Optimization in Complex Network", arXiv 2412.20980):
+ *
+ *  - Fitness of a deletion set D (Section III-C, Eq. 13 with node deletion =
+ *    removal of every incident edge; the CND quality metric PC(G) of
+ *    Table "Whole"): the pairwise connectivity of G[V \ D],
+ *        PC(D) = sum over connected components C of G[V \ D] of |C|(|C|-1)/2,
+ *    in int64.  Two independent computations: breadth-first search from every
+ *    unvisited live node in ascending id order (oracle_pc_bfs), and a
+ *    union-find with union by size and full path compression over the edges
+ *    in CSR order (oracle_pc_uf).
+ *  - The genetic operators of Section III-B in the paper's order: population
+ *    initialisation (Eq. 2), selection + crossover with a Bernoulli(pc) mask
+ *    per gene (Eqs. 3-6), mutation with a Bernoulli(pm) mask and replacement
+ *    genes (Eqs. 7-9), fitness, and elitism.  Where the paper is silent the
+ *    readings are fixed as follows (and the CUDA path follows the same ones):
+ *      * selection: tournament of size t drawn with replacement, lower PC
+ *        wins, ties to the lower index (the paper's Eq. 5 uses roulette);
+ *      * elitism: the single best member (lowest PC, lowest index) is copied
+ *        unchanged to row 0 with its fitness carried over;
+ *      * a child's gene j comes from parent B when the crossover mask is set,
+ *        else from parent A (Eq. 6 with both parents chosen by selection);
+ *      * duplicate genes are repaired by a deterministic rule (see repair()).
+ *  - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel
+ *    Random Numbers: As Easy as 1, 2, 3", SC 2011), counter
+ *    (j, i, g, tag << 24 | round), key (seed low word, seed high word); word 0
+ *    of the output is used.  Bernoulli(p) is x < floor(p * 2^32) with the
+ *    threshold passed in as an integer; uniform in [0, n) is (x * n) >> 32.
+ *
+ * Parity: PC is pinned by closed forms, brute force, scipy and the dense
+ * reachability identity of Eqs. 14-17; Philox by an independent
+ * implementation; the genetic operators by statistical laws and special
+ * cases (see the tests).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10                                                        */
+/* ------------------------------------------------------------------ */
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; round++) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+enum { TAG_INIT = 1, TAG_SEL = 2, TAG_XOVER = 3, TAG_MUT = 4, TAG_MUTVAL = 5, TAG_REPAIR = 6 };
+#define REPAIR_ROUNDS 32
+
+static uint32_t draw(uint64_t seed, uint32_t j, uint32_t i, uint32_t g, uint32_t tag, uint32_t round)
+{
+    uint32_t ctr[4] = { j, i, g, (tag << 24) | round };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+static int32_t uniform_below(uint32_t x, int32_t n)
+{
+    return (int32_t)(((uint64_t)x * (uint64_t)(uint32_t)n) >> 32);
+}
+
+/* ------------------------------------------------------------------ */
+/* Fitness: pairwise connectivity of the residual graph                 */
+/* ------------------------------------------------------------------ */
+
+/* Error codes shared only within this file and its Python loader. */
+#define ORACLE_OK 0
+#define ORACLE_EINVAL -1
+#define ORACLE_ENOMEM -3
+
+/* Marks the deletion set in `dead` (n bytes, zeroed here).  Genes outside
+ * [0, n) make the set invalid. */
+static int mark_deleted(int32_t n, const int32_t* genes, int32_t k, uint8_t* dead)
+{
+    memset(dead, 0, (size_t)n);
+    for (int32_t j = 0; j < k; j++) {
+        if (genes[j] < 0 || genes[j] >= n) return ORACLE_EINVAL;
+        dead[genes[j]] = 1;
+    }
+    return ORACLE_OK;
+}
+
+/* BFS over G[V \ D]; writes the component sizes in discovery order to
+ * sizes_out (may be NULL) and returns the number of components, or < 0. */
+int64_t oracle_components_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                              const int32_t* genes, int32_t k, int32_t* sizes_out)
+{
+    uint8_t* dead = (uint8_t*)malloc((size_t)n + 1);
+    uint8_t* seen = (uint8_t*)calloc((size_t)n + 1, 1);
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (!dead || !seen || !queue) { free(dead); free(seen); free(queue); return ORACLE_ENOMEM; }
+    if (mark_deleted(n, genes, k, dead) != ORACLE_OK) { free(dead); free(seen); free(queue); return ORACLE_EINVAL; }
+    int64_t ncomp = 0;
+    for (int32_t start = 0; start < n; start++) {
+        if (dead[start] || seen[start]) continue;
+        int32_t head = 0, tail = 0;
+        queue[tail++] = start;
+        seen[start] = 1;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+                int32_t v = col[e];
+                if (!dead[v] && !seen[v]) { seen[v] = 1; queue[tail++] = v; }
+            }
+        }
+        if (sizes_out) sizes_out[ncomp] = tail;
+        ncomp++;
+    }
+    free(dead); free(seen); free(queue);
+    return ncomp;
+}
+
+int64_t oracle_pc_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                      const int32_t* genes, int32_t k)
+{
+    int32_t* sizes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (!sizes) return ORACLE_ENOMEM;
+    int64_t ncomp = oracle_components_bfs(n, row_ptr, col, genes, k, sizes);
+    if (ncomp < 0) { free(sizes); return ncomp; }
+    int64_t pc = 0;
+    for (int64_t c = 0; c < ncomp; c++) pc += (int64_t)sizes[c] * (int64_t)(sizes[c] - 1) / 2;
+    free(sizes);
+    return pc;
+}
+
+static int32_t uf_find(int32_t* parent, int32_t x)
+{
+    int32_t root = x;
+    while (parent[root] != root) root = parent[root];
+    while (parent[x] != root) { int32_t next = parent[x]; parent[x] = root; x = next; }
+    return root;
+}
+
+int64_t oracle_pc_uf(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                     const int32_t* genes, int32_t k)
+{
+    uint8_t* dead = (uint8_t*)malloc((size_t)n + 1);
+    int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int64_t* size = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    if (!dead || !parent || !size) { free(dead); free(parent); free(size); return ORACLE_ENOMEM; }
+    if (mark_deleted(n, genes, k, dead) != ORACLE_OK) { free(dead); free(parent); free(size); return ORACLE_EINVAL; }
+    for (int32_t v = 0; v < n; v++) { parent[v] = v; size[v] = 1; }
+    for (int32_t u = 0; u < n; u++) {
+        if (dead[u]) continue;
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+            int32_t v = col[e];
+            if (v <= u || dead[v]) continue;
+            int32_t ru = uf_find(parent, u), rv = uf_find(parent, v);
+            if (ru == rv) continue;
+            if (size[ru] < size[rv]) { int32_t t = ru; ru = rv; rv = t; }
+            parent[rv] = ru;
+            size[ru] += size[rv];
+        }
+    }
+    int64_t pc = 0;
+    for (int32_t v = 0; v < n; v++)
+        if (!dead[v] && parent[v] == v) pc += size[v] * (size[v] - 1) / 2;
+    free(dead); free(parent); free(size);
+    return pc;
+}
+
+/* Fitness of s members (rows of k genes) with the chosen method
+ * (0 = BFS, 1 = union-find), in parallel over members when nthreads > 1.
+ * Returns ORACLE_OK or the first error. */
+int oracle_fitness(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                   const int32_t* pop, int32_t s, int32_t k, int64_t* fit,
+                   int32_t method, int32_t nthreads)
+{
+    int err = ORACLE_OK;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int32_t i = 0; i < s; i++) {
+        const int32_t* genes = pop + (size_t)i * (size_t)k;
+        int64_t v = method == 0 ? oracle_pc_bfs(n, row_ptr, col, genes, k)
+                                : oracle_pc_uf(n, row_ptr, col, genes, k);
+        fit[i] = v;
+        if (v < 0) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            { if (err == ORACLE_OK) err = (int)v; }
+        }
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------ */
+/* Genetic operators                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Kept-set as one byte per node (plain and slow on purpose). */
+typedef struct {
+    int32_t n;
+    uint8_t* in;
+} keptset;
+
+/* Duplicate repair (the paper is silent on duplicates).  `holes` lists the
+ * positions without a gene in ascending order, `cand0` their first
+ * candidates.  Round r = 0 .. 31: every remaining hole, in ascending position
+ * order, takes its round-r candidate if that node is not in the kept set, and
+ * the node joins the kept set at once.  The round-0 candidate is cand0; a
+ * later round's candidate is uniform over [0, n) from draw(j, i, g, REPAIR, r).
+ * Holes still open after round 31 take, in ascending position order, the
+ * smallest node id not in the kept set. */
+static void repair(uint64_t seed, int32_t i, int32_t g, int32_t n, keptset* kept,
+                   int32_t* row, int32_t* holes, int32_t nholes, const int32_t* cand0)
+{
+    for (int32_t r = 0; r < REPAIR_ROUNDS && nholes > 0; r++) {
+        int32_t still = 0;
+        for (int32_t h = 0; h < nholes; h++) {
+            int32_t j = holes[h];
+            int32_t c = r == 0 ? cand0[h] : uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_REPAIR, (uint32_t)r), n);
+            if (!kept->in[c]) {
+                kept->in[c] = 1;
+                row[j] = c;
+            } else {
+                holes[still++] = j;
+            }
+        }
+        nholes = still;
+    }
+    int32_t next = 0;
+    for (int32_t h = 0; h < nholes; h++) {
+        while (kept->in[next]) next++;
+        kept->in[next] = 1;
+        row[holes[h]] = next;
+    }
+}
+
+/* Population initialisation (Eq. 2): member i is a uniformly drawn k-subset:
+ * every position is a hole whose round-0 candidate is uniform over [0, n) from
+ * draw(j, i, 0, INIT, 0), then the repair rule runs with generation 0. */
+int oracle_pop_init(int32_t n, int32_t k, int32_t s, uint64_t seed, int32_t* pop)
+{
+    if (n < 1 || k < 0 || k >= n || s < 1) return ORACLE_EINVAL;
+    keptset kept = { n, (uint8_t*)malloc((size_t)n) };
+    int32_t* holes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    int32_t* cand0 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    if (!kept.in || !holes || !cand0) { free(kept.in); free(holes); free(cand0); return ORACLE_ENOMEM; }
+    for (int32_t i = 0; i < s; i++) {
+        int32_t* row = pop + (size_t)i * (size_t)k;
+        memset(kept.in, 0, (size_t)n);
+        for (int32_t j = 0; j < k; j++) {
+            holes[j] = j;
+            cand0[j] = uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, 0, TAG_INIT, 0), n);
+        }
+        repair(seed, i, 0, n, &kept, row, holes, k, cand0);
+    }
+    free(kept.in); free(holes); free(cand0);
+    return ORACLE_OK;
+}
+
+/* Tournament of size t for parent slot `slot` of child i (selection; the
+ * paper's Eq. 5 uses roulette, this reading uses tournaments): draw t indices
+ * with replacement, uniform over [0, s) from draw(slot*t + r, i, g, SEL, 0);
+ * the lowest fitness wins, ties to the lower index. */
+static int32_t tournament(uint64_t seed, int32_t i, int32_t g, int32_t slot, int32_t t,
+                          int32_t s, const int64_t* fit)
+{
+    int32_t best = -1;
+    for (int32_t r = 0; r < t; r++) {
+        int32_t x = uniform_below(draw(seed, (uint32_t)(slot * t + r), (uint32_t)i, (uint32_t)g, TAG_SEL, 0), s);
+        if (best < 0 || fit[x] < fit[best] || (fit[x] == fit[best] && x < best)) best = x;
+    }
+    return best;
+}
+
+#define ORACLE_FLAG_ROWWISE 1u
+
+/* One generation g >= 1 (Fig. 1's loop body), producing (pop_out, fit_out)
+ * from (pop_in, fit_in):
+ *   elitism  - row 0 = the member with the lowest fitness (lowest index on
+ *              ties), fitness carried over;
+ *   for each child i = 1 .. s-1:
+ *   selection - parents A and B by two tournaments (slot 0 and slot 1); with
+ *              the row-wise flag, A = member i itself (Eq. 6 read literally);
+ *   crossover - gene j is B[j] where draw(j,i,g,XOVER,0) < pc_thr, else A[j];
+ *   mutation  - gene j becomes a hole where draw(j,i,g,MUT,0) < pm_thr, with
+ *              round-0 candidate uniform over [0,n) from draw(j,i,g,MUTVAL,0);
+ *   duplicates - a gene taken from B that equals a kept gene taken from A
+ *              becomes a hole whose round-0 candidate is A[j];
+ *   repair    - as in repair();
+ *   fitness   - PC of every child (BFS).
+ */
+int oracle_generation(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                      int32_t k, int32_t s, int32_t t, uint32_t pc_thr, uint32_t pm_thr,
+                      uint64_t seed, uint32_t flags, int32_t g,
+                      const int32_t* pop_in, const int64_t* fit_in,
+                      int32_t* pop_out, int64_t* fit_out, int32_t nthreads)
+{
+    if (n < 1 || k < 0 || k >= n || s < 2 || t < 1 || g < 1) return ORACLE_EINVAL;
+    int32_t elite = 0;
+    for (int32_t x = 1; x < s; x++)
+        if (fit_in[x] < fit_in[elite]) elite = x;
+    memcpy(pop_out, pop_in + (size_t)elite * (size_t)k, sizeof(int32_t) * (size_t)k);
+    fit_out[0] = fit_in[elite];
+
+    int err = ORACLE_OK;
+    keptset kept = { n, (uint8_t*)malloc((size_t)n) };
+    int32_t* holes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    int32_t* cand0 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    uint8_t* from_b = (uint8_t*)malloc((size_t)k + 1);
+    uint8_t* mutated = (uint8_t*)malloc((size_t)k + 1);
+    if (!kept.in || !holes || !cand0 || !from_b || !mutated) err = ORACLE_ENOMEM;
+    for (int32_t i = 1; i < s && err == ORACLE_OK; i++) {
+        int32_t pa = (flags & ORACLE_FLAG_ROWWISE) ? i : tournament(seed, i, g, 0, t, s, fit_in);
+        int32_t pb = tournament(seed, i, g, 1, t, s, fit_in);
+        const int32_t* A = pop_in + (size_t)pa * (size_t)k;
+        const int32_t* B = pop_in + (size_t)pb * (size_t)k;
+        int32_t* row = pop_out + (size_t)i * (size_t)k;
+        memset(kept.in, 0, (size_t)n);
+        for (int32_t j = 0; j < k; j++) {
+            from_b[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_XOVER, 0) < pc_thr;
+            mutated[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUT, 0) < pm_thr;
+            row[j] = -1;
+        }
+        /* genes kept from A first, then genes from B that do not repeat one */
+        for (int32_t j = 0; j < k; j++)
+            if (!mutated[j] && !from_b[j]) { row[j] = A[j]; kept.in[A[j]] = 1; }
+        for (int32_t j = 0; j < k; j++)
+            if (!mutated[j] && from_b[j] && !kept.in[B[j]]) { row[j] = B[j]; kept.in[B[j]] = 1; }
+        int32_t nh = 0;
+        for (int32_t j = 0; j < k; j++) {
+            if (row[j] >= 0) continue;
+            holes[nh] = j;
+            cand0[nh] = mutated[j] ? uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)
+                                   : A[j];
+            nh++;
+        }
+        repair(seed, i, g, n, &kept, row, holes, nh, cand0);
+    }
+    free(kept.in); free(holes); free(cand0); free(from_b); free(mutated);
+    if (err != ORACLE_OK) return err;
+    return oracle_fitness(n, row_ptr, col, pop_out + k, s - 1, k, fit_out + 1, 0, nthreads);
+}
+
+/* A whole run: initialisation, fitness, then `gens` generations.
+ * traj_best (gens+1 entries, may be NULL) receives the lowest fitness after
+ * initialisation and after every generation; best_set (k entries) the genes
+ * of the final best member (lowest fitness, lowest index) in ascending order;
+ * pop_final / fit_final (may be NULL) the final population. */
+static int cmp_i32(const void* a, const void* b)
+{
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+int oracle_run(int32_t n, const int32_t* row_ptr, const int32_t* col,
+               int32_t k, int32_t s, int32_t gens, int32_t t, uint32_t pc_thr, uint32_t pm_thr,
+               uint64_t seed, uint32_t flags, int32_t* best_set, int64_t* best_fit,
+               int64_t* traj_best, int32_t* pop_final, int64_t* fit_final, int32_t nthreads)
+{
+    if (n < 1 || k < 0 || k >= n || s < 2 || t < 1 || gens < 0) return ORACLE_EINVAL;
+    size_t cells = (size_t)s * (size_t)k;
+    int32_t* pa = (int32_t*)malloc(sizeof(int32_t) * (cells + 1));
+    int32_t* pb = (int32_t*)malloc(sizeof(int32_t) * (cells + 1));
+    int64_t* fa = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
+    int64_t* fb = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
+    int err = (!pa || !pb || !fa || !fb) ? ORACLE_ENOMEM : ORACLE_OK;
+    if (err == ORACLE_OK) err = oracle_pop_init(n, k, s, seed, pa);
+    if (err == ORACLE_OK) err = oracle_fitness(n, row_ptr, col, pa, s, k, fa, 0, nthreads);
+    for (int32_t g = 0; g <= gens && err == ORACLE_OK; g++) {
+        if (g > 0) {
+            err = oracle_generation(n, row_ptr, col, k, s, t, pc_thr, pm_thr, seed, flags, g,
+                                    pa, fa, pb, fb, nthreads);
+            int32_t* tp = pa; pa = pb; pb = tp;
+            int64_t* tf = fa; fa = fb; fb = tf;
+        }
+        if (traj_best && err == ORACLE_OK) {
+            int64_t m = fa[0];
+            for (int32_t x = 1; x < s; x++) if (fa[x] < m) m = fa[x];
+            traj_best[g] = m;
+        }
+    }
+    if (err == ORACLE_OK) {
+        int32_t e = 0;
+        for (int32_t x = 1; x < s; x++) if (fa[x] < fa[e]) e = x;
+        if (best_fit) *best_fit = fa[e];
+        if (best_set) {
+            memcpy(best_set, pa + (size_t)e * (size_t)k, sizeof(int32_t) * (size_t)k);
+            qsort(best_set, (size_t)k, sizeof(int32_t), cmp_i32);
+        }
+        if (pop_final) memcpy(pop_final, pa, sizeof(int32_t) * cells);
+        if (fit_final) memcpy(fit_final, fa, sizeof(int64_t) * (size_t)s);
+    }
+    free(pa); free(pb); free(fa); free(fb);
+    return err;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

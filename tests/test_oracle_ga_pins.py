@@ -1,0 +1,271 @@
+"""Pins of the oracle's random stream and genetic operators.
+
+Philox4x32-10 (Salmon et al., SC 2011) is checked against an independent
+implementation (Triton's, run by its CPU interpreter).  The operators of
+Section III-B have no reference values, so they are pinned by their laws:
+the selection law of a size-2 tournament with replacement, binomial bounds on
+the crossover (Eq. 4) and mutation (Eq. 8) mask rates, the special cases
+pc = 0 / pc = 1 / pm = 0 of Eqs. 6 and 9, elitism (Eqs. 10-11 with one elite),
+distinctness of every deletion set, and brute-force optimality on tiny graphs.
+"""
+import json
+import os
+import subprocess
+import sys
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+SEED = 0x1234_5678_9ABC
+
+
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+
+@triton.jit
+def k(out_ptr, c_ptr, key_ptr, N, BLOCK: tl.constexpr):
+    off = tl.arange(0, BLOCK)
+    m = off < N
+    c0 = tl.load(c_ptr + off * 4 + 0, mask=m).to(tl.uint32)
+    c1 = tl.load(c_ptr + off * 4 + 1, mask=m).to(tl.uint32)
+    c2 = tl.load(c_ptr + off * 4 + 2, mask=m).to(tl.uint32)
+    c3 = tl.load(c_ptr + off * 4 + 3, mask=m).to(tl.uint32)
+    k0 = tl.load(key_ptr + off * 2 + 0, mask=m).to(tl.uint32)
+    k1 = tl.load(key_ptr + off * 2 + 1, mask=m).to(tl.uint32)
+    a, b, c, d = tl.random.philox_impl(c0, c1, c2, c3, k0, k1, 10)
+    tl.store(out_ptr + off * 4 + 0, a.to(tl.int64) & 0xffffffff, mask=m)
+    tl.store(out_ptr + off * 4 + 1, b.to(tl.int64) & 0xffffffff, mask=m)
+    tl.store(out_ptr + off * 4 + 2, c.to(tl.int64) & 0xffffffff, mask=m)
+    tl.store(out_ptr + off * 4 + 3, d.to(tl.int64) & 0xffffffff, mask=m)
+
+data = json.load(sys.stdin)
+ctr = torch.tensor(data["ctr"], dtype=torch.int64).to(torch.int32)
+key = torch.tensor(data["key"], dtype=torch.int64).to(torch.int32)
+N = ctr.shape[0]
+out = torch.zeros(N * 4, dtype=torch.int64)
+k[(1,)](out, ctr.reshape(-1), key.reshape(-1), N, BLOCK=triton.next_power_of_2(N))
+print(json.dumps(out.tolist()))
+"""
+
+
+def test_philox_against_independent_implementation():
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2**32, size=(200, 4), dtype=np.uint64)
+    key = rng.integers(0, 2**32, size=(200, 2), dtype=np.uint64)
+    ctr[0] = 0
+    key[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key[1] = 0xFFFFFFFF
+    ctr[2] = [5, 17, 3, (6 << 24) | 31]  # a counter of the layout used by the operators
+    # signed int32 view for torch transport
+    to_i32 = lambda a: ((a.astype(np.int64) + 2**31) % 2**32 - 2**31).tolist()
+    payload = json.dumps({"ctr": to_i32(ctr), "key": to_i32(key)})
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=payload, capture_output=True,
+                          text=True, timeout=300, env=dict(os.environ, TRITON_INTERPRET="1"))
+    if proc.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {proc.stderr[-300:]}")
+    want = np.array(json.loads(proc.stdout.strip().splitlines()[-1]), dtype=np.uint64).reshape(-1, 4)
+    for r in range(ctr.shape[0]):
+        got = oracle.philox4x32_10(ctr[r], key[r])
+        assert np.array_equal(got.astype(np.uint64), want[r]), r
+
+
+def test_philox_uniformity_chi2():
+    # 2^14 draws of word 0 along the gene axis, 64 bins
+    vals = np.array([oracle.draw(SEED, j, 3, 9, oracle.TAG_XOVER) for j in range(1 << 14)], dtype=np.uint64)
+    bins = np.bincount((vals >> np.uint64(26)).astype(np.int64), minlength=64)
+    e = vals.size / 64
+    chi2 = ((bins - e) ** 2 / e).sum()
+    assert chi2 < 130  # 63 dof; p ~ 1e-6
+
+
+def _graph():
+    return synth.ba_graph(400, 2, 3)
+
+
+def test_pop_init_distinct_in_range_and_uniform():
+    n, k, s = 97, 12, 3000
+    pop = oracle.pop_init(n, k, s, SEED)
+    assert pop.min() >= 0 and pop.max() < n
+    assert all(len(set(r.tolist())) == k for r in pop)
+    counts = np.bincount(pop.ravel(), minlength=n)
+    e = s * k / n
+    chi2 = ((counts - e) ** 2 / e).sum()
+    assert chi2 < 96 + 5 * np.sqrt(2 * 96)
+
+
+@pytest.mark.parametrize("n,k", [(5, 4), (8, 7), (40, 39), (3, 0), (2, 1)])
+def test_pop_init_dense_sets_use_fill_path(n, k):
+    pop = oracle.pop_init(n, k, 50, SEED)
+    for r in pop:
+        assert len(set(r.tolist())) == k and (k == 0 or (r.min() >= 0 and r.max() < n))
+
+
+def _distinct_population(n, k, s, seed=0):
+    """Rows on disjoint gene ranges (needs n >= s*k): no duplicate can arise from crossover."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n)[: s * k]
+    return perm.reshape(s, k).astype(np.int32)
+
+
+def test_tournament_law_with_pc0_pm0():
+    """pc = 0, pm = 0: child = parent A (Eq. 6 with RC = 0, Eq. 9 with RM = 0);
+    A's rank follows the size-2 tournament-with-replacement law (2(s-r)-1)/s^2."""
+    g = synth.named_graph("empty", 4000)
+    s, k = 20, 3
+    pop = _distinct_population(g.n, k, s)
+    fit = np.arange(s, dtype=np.int64)[::-1].copy()  # rank 0 = row s-1 (lowest PC)
+    rank_of_row = {tuple(pop[i].tolist()): int(s - 1 - i) for i in range(s)}
+    counts = np.zeros(s, dtype=np.int64)
+    total = 0
+    for gen in range(1, 301):
+        out, _ = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=0, pm_thr=0, seed=SEED)
+        assert tuple(out[0].tolist()) == tuple(pop[s - 1].tolist())  # elite
+        for i in range(1, s):
+            counts[rank_of_row[tuple(out[i].tolist())]] += 1
+            total += 1
+    p = np.array([(2 * (s - r) - 1) / s**2 for r in range(s)])
+    e = total * p
+    chi2 = ((counts - e) ** 2 / e).sum()
+    assert chi2 < 19 + 6 * np.sqrt(38), (counts, e)
+
+
+def test_pc1_takes_parent_b_and_tournament_ties_to_lower_index():
+    g = synth.named_graph("empty", 3000)
+    s, k = 16, 4
+    pop = _distinct_population(g.n, k, s, 1)
+    fit = np.zeros(s, dtype=np.int64)  # all tied: winner = smaller drawn index
+    rows = {tuple(pop[i].tolist()): i for i in range(s)}
+    counts = np.zeros(s, dtype=np.int64)
+    for gen in range(1, 201):
+        out, _ = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=0xFFFFFFFF, pm_thr=0,
+                                   seed=SEED)
+        assert tuple(out[0].tolist()) == tuple(pop[0].tolist())  # tie -> lowest index elite
+        for i in range(1, s):
+            counts[rows[tuple(out[i].tolist())]] += 1
+    # with all fitness tied, the winner is min of two uniform draws: P(idx=r) = (2(s-r)-1)/s^2
+    total = counts.sum()
+    e = total * np.array([(2 * (s - r) - 1) / s**2 for r in range(s)])
+    assert ((counts - e) ** 2 / e).sum() < 15 + 6 * np.sqrt(30)
+
+
+def test_crossover_rate_binomial():
+    g = synth.named_graph("empty", 5000)
+    s, k = 40, 50
+    pop = _distinct_population(g.n, k, s, 2)
+    fit = np.arange(s, dtype=np.int64)
+    owner = np.full(g.n, -1)
+    for i in range(s):
+        owner[pop[i]] = i
+    pc_thr, _ = oracle.thresholds(0.8, 0.0)
+    from_b = 0
+    total = 0
+    for gen in range(1, 21):
+        out, _ = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=pc_thr, pm_thr=0, seed=SEED)
+        for i in range(1, s):
+            owners = owner[out[i]]
+            ids, cnt = np.unique(owners, return_counts=True)
+            assert len(ids) <= 2
+            if len(ids) == 2:
+                # the parent contributing the larger share is B under pc = 0.8
+                from_b += cnt.max()
+                total += k
+    p = 0.8
+    assert abs(from_b / total - p) < 5 * np.sqrt(p * (1 - p) / total) + 1e-3
+
+
+def test_mutation_rate_binomial_and_distinct():
+    g = synth.named_graph("empty", 200000)
+    s, k = 30, 100
+    pop = _distinct_population(g.n, k, s, 3)
+    fit = np.arange(s, dtype=np.int64)
+    _, pm_thr = oracle.thresholds(0.0, 0.05)
+    changed = 0
+    total = 0
+    parents = {tuple(sorted(r.tolist())) for r in pop}
+    pool = set(pop.ravel().tolist())
+    for gen in range(1, 31):
+        out, _ = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=0, pm_thr=pm_thr, seed=SEED)
+        for i in range(1, s):
+            assert len(set(out[i].tolist())) == k
+            changed += sum(1 for x in out[i].tolist() if x not in pool)
+            total += k
+    p = 0.05
+    assert abs(changed / total - p) < 5 * np.sqrt(p * (1 - p) / total)
+
+
+def test_rowwise_flag_with_pc0_pm0_is_identity_on_children():
+    g = _graph()
+    s, k = 12, 10
+    pop = oracle.pop_init(g.n, k, s, SEED)
+    fit = oracle.fitness(g.row_ptr, g.col, pop)
+    out, fout = oracle.generation(g.row_ptr, g.col, pop, fit, 1, tourn=2, pc_thr=0, pm_thr=0, seed=SEED,
+                                  flags=oracle.FLAG_ROWWISE)
+    e = int(np.argmin(fit))
+    assert np.array_equal(out[0], pop[e]) and fout[0] == fit[e]
+    assert np.array_equal(out[1:], pop[1:])
+    assert np.array_equal(fout[1:], fit[1:])
+
+
+def test_generation_invariants_and_child_fitness():
+    g = _graph()
+    s, k = 30, 40
+    pc_thr, pm_thr = oracle.thresholds(0.8, 0.1)
+    pop = oracle.pop_init(g.n, k, s, SEED)
+    fit = oracle.fitness(g.row_ptr, g.col, pop)
+    for gen in range(1, 6):
+        out, fout = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr,
+                                      seed=SEED)
+        assert out.min() >= 0 and out.max() < g.n
+        assert all(len(set(r.tolist())) == k for r in out)
+        e = int(np.argmin(fit))
+        assert np.array_equal(out[0], pop[e]) and fout[0] == fit[e]
+        assert np.array_equal(fout, oracle.fitness(g.row_ptr, g.col, out, "uf"))
+        assert fout.min() <= fit.min()
+        pop, fit = out, fout
+
+
+def test_heavy_duplicates_small_n():
+    """k close to n forces crossover duplicates and the final fill path."""
+    g = synth.named_graph("cycle", 12)
+    s, k = 10, 10
+    pc_thr, pm_thr = oracle.thresholds(0.5, 0.5)
+    pop = oracle.pop_init(g.n, k, s, SEED)
+    fit = oracle.fitness(g.row_ptr, g.col, pop)
+    for gen in range(1, 30):
+        pop, fit = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=3, pc_thr=pc_thr, pm_thr=pm_thr,
+                                     seed=SEED)
+        assert all(len(set(r.tolist())) == k for r in pop)
+
+
+def test_run_reaches_brute_force_optimum_on_tiny_graph():
+    g = synth.er_graph(14, 22, 5)
+    k = 3
+    best = min(oracle.pc(g.row_ptr, g.col, np.array(c, dtype=np.int32))
+               for c in __import__("itertools").combinations(range(14), k))
+    pc_thr, pm_thr = oracle.thresholds(0.8, 0.1)
+    r = oracle.run(g.row_ptr, g.col, k=k, pop=30, gens=60, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr, seed=SEED)
+    assert r["best_fit"] == best
+    assert np.all(np.diff(r["traj"]) <= 0)  # elitism: best never gets worse
+    assert oracle.pc(g.row_ptr, g.col, r["best_set"]) == r["best_fit"]
+    assert np.all(np.diff(r["best_set"]) > 0)
+
+
+def test_run_is_generation_composition():
+    g = _graph()
+    pc_thr, pm_thr = oracle.thresholds(0.8, 0.02)
+    r = oracle.run(g.row_ptr, g.col, k=20, pop=16, gens=7, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr, seed=SEED)
+    pop = oracle.pop_init(g.n, 20, 16, SEED)
+    fit = oracle.fitness(g.row_ptr, g.col, pop)
+    for gen in range(1, 8):
+        pop, fit = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr,
+                                     seed=SEED)
+    assert np.array_equal(pop, r["pop"]) and np.array_equal(fit, r["fit"])
