@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the batched critical-node-detection hot path on GB300.
+
+Default workload (one step = one GA generation on each of two graphs):
+  Barabasi-Albert n=20000, m=4 (79,984 edges) and Holme-Kim n=20000, m=4,
+  p=0.3 (79,984 edges); k = 1000 deleted nodes (5% of n); population s = 1024;
+  tournament 2, uniform crossover pc = 0.8, per-gene mutation pm = 0.02,
+  elitism 1, Philox seed = rank.  Each generation runs elitism, selection,
+  crossover, mutation, duplicate repair and the exact fitness (pairwise
+  connectivity) of the s-1 children, all in libgapa.so's kernels.
+Metric: exact CND fitness evaluations per second (whole job), with the
+generations per second beside it.
+
+``--impl reference`` times the CPU oracle (plain C, OpenMP over members) on a
+bounded sample of the same workload.  Under torchrun every rank runs its own
+populations (weak scaling, no collective on the data path); rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact CND fitness evals/s"
+K_DEL, POP = 1000, 1024
+PC, PM, TOURN = 0.8, 0.02, 2
+L2_FLUSH_BYTES = 512 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def graphs():
+    import synth
+
+    return [synth.ba_graph(20000, 4, 1), synth.hk_graph(20000, 4, 0.3, 1)]
+
+
+def bytes_per_eval(n: int, num_edges: int, k: int) -> int:
+    """Algorithmic bytes of one exact evaluation: row pointers, each undirected
+    edge once, the deletion bitmap, the genes and the int64 result."""
+    return 4 * (n + 1) + 4 * num_edges + (n + 7) // 8 + 4 * k + 8
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("fitness.cu", "gapa_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2412_20980_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """dram read+write bytes per launch of the fitness kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "fitness_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(workload)
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.4)
+        except Exception as e:  # no nvidia-smi: report clocks as unknown
+            log("clock sampler unavailable:", e)
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 9]
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].strip() == "Active"})
+        loaded = [x for x in sm if mx and x > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(seconds: float = 12.0) -> dict:
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    workload: oracle generations of the BA graph's population until `seconds`."""
+    import oracle
+
+    g = graphs()[0]
+    pc_thr, pm_thr = oracle.thresholds(PC, PM)
+    nt = oracle.max_threads()
+    pop = oracle.pop_init(g.n, K_DEL, POP, 0)
+    fit = oracle.fitness(g.row_ptr, g.col, pop, nthreads=nt)
+    t0 = time.perf_counter()
+    gens = 0
+    while True:
+        pop, fit = oracle.generation(g.row_ptr, g.col, pop, fit, gens + 1, tourn=TOURN, pc_thr=pc_thr,
+                                     pm_thr=pm_thr, seed=0, nthreads=nt)
+        gens += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    evals = gens * (POP - 1)
+    return {"value": evals / el, "unit": "evals/s", "cores": nt, "kind": "oracle",
+            "sample": f"{gens} oracle generations on BA n=20000 (k=1000, s=1024): {evals} evals in {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+
+    gs = graphs()
+    pc_thr, pm_thr = oracle.thresholds(PC, PM)
+    nt = oracle.max_threads()
+    # bounded sample: a sub-population whose step fits the time budget
+    s_ref = POP
+    pops = [oracle.pop_init(g.n, K_DEL, s_ref, 0) for g in gs]
+    fits = [oracle.fitness(g.row_ptr, g.col, p, nthreads=nt) for g, p in zip(gs, pops)]
+
+    def step(t, s):
+        for j, g in enumerate(gs):
+            pops[j], fits[j] = oracle.generation(g.row_ptr, g.col, pops[j][:s], fits[j][:s], t + 1, tourn=TOURN,
+                                                 pc_thr=pc_thr, pm_thr=pm_thr, seed=0, nthreads=nt)
+
+    t0 = time.perf_counter()
+    step(0, s_ref)
+    one = time.perf_counter() - t0
+    budget = 150.0
+    total_steps = args.steps + args.warmup
+    if one * total_steps > budget:
+        s_ref = max(16, int(s_ref * budget / (one * total_steps)))
+    for t in range(1, args.warmup):
+        step(t, s_ref)
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        step(args.warmup + t, s_ref)
+    el = time.perf_counter() - t0
+    evals = args.steps * len(gs) * (s_ref - 1)
+    v = evals / el
+    sample = (f"oracle generations on BA and HK n=20000, k=1000, population {s_ref} (of 1024): "
+              f"{args.steps} steps = {evals} evals in {el:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": workload_config(s_ref),
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": nt, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(pop=POP):
+    return {"workload": "GA generation step on BA(n=20000,m=4) + HK(n=20000,m=4,p=0.3), k=1000, "
+                        f"s={pop}, tournament 2, pc=0.8, pm=0.02, elitism 1",
+            "graphs": ["ba_n20000_m4_seed1 (E=79984)", "hk_n20000_m4_p0.3_seed1 (E=79984)"],
+            "k": K_DEL, "pop": pop, "evals_per_step": 2 * (pop - 1),
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)", "parallelism": "dp (independent populations per rank)"}
+
+
+def run_gapa(args):
+    import torch
+
+    from paper_2412_20980_gb300 import Context, make_config
+    from paper_2412_20980_gb300 import build as b
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        b.build()
+    if dist is not None:
+        dist.barrier()
+    gs = graphs()
+    cfg = make_config(k=K_DEL, pop=POP, tourn=TOURN, pc=PC, pm=PM, seed=rank)
+    ctxs, state = [], []
+    for g in gs:
+        c = Context(local)
+        c.graph_upload(g.row_ptr, g.col)
+        pa = c.pop_init(cfg)
+        fa = c.fitness(pa)
+        state.append([pa, fa, torch.empty_like(pa), torch.empty_like(fa)])
+        ctxs.append(c)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(t):
+        for c, st in zip(ctxs, state):
+            c.generation(cfg, t + 1, st[0], st[1], st[2], st[3])
+            st[0], st[2] = st[2], st[0]
+            st[1], st[3] = st[3], st[1]
+
+    for t in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+    evals_per_step = len(gs) * (POP - 1)
+    # --- timed region: device time per step, L2 flushed between steps ---
+    sampler = ClockSampler(local)
+    sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.profile_begin()
+    for t in range(args.steps):
+        flush.fill_(t & 0xFF)
+        starts[t].record()
+        step(args.warmup + t)
+        ends[t].record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    profs = [c.profile_end() for c in ctxs]
+    clocks = sampler.stop()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    for c, st in zip(ctxs, state):
+        c.sync()
+    value = evals_per_step * args.steps * ws / (total_ms / 1000.0)
+    gens_per_s = len(gs) * args.steps * ws / (total_ms / 1000.0)
+
+    # --- dominant kernel: the fitness launches inside the timed region ---
+    fit_ms = sum(p["fitness_ms"] for p in profs)
+    fit_launches = sum(p["fitness_launches"] for p in profs)
+    fit_evals = sum(p["evals"] for p in profs)
+    op_launches = sum(p["operator_launches"] for p in profs)
+    beval = bytes_per_eval(gs[0].n, gs[0].num_edges, K_DEL)
+    peak, peak_src = measured_peaks()
+    avg_launch_s = fit_ms / 1000.0 / max(1, fit_launches)
+    achieved = beval * (fit_evals / max(1, fit_launches)) / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic("c1"), "kernel": "cc_smem_kernel",
+                "bytes_per_eval": beval, "evals_per_launch": fit_evals / max(1, fit_launches),
+                "avg_launch_ms": avg_launch_s * 1000, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "fitness_share_of_step": fit_ms / max(1e-9, total_ms)}
+
+    # --- end to end through the C ABI with pinned host buffers ---
+    e2e = None
+    if rank == 0 or ws > 1:
+        hp, pinned = [], []
+        for c, st in zip(ctxs, state):
+            ts = [st[0].cpu().pin_memory(), st[1].cpu().pin_memory(),
+                  torch.empty(st[0].shape, dtype=torch.int32).pin_memory(),
+                  torch.empty(st[1].shape, dtype=torch.int64).pin_memory()]
+            pinned.append(ts)  # keeps the page-locked buffers alive
+            hp.append([t.numpy() for t in ts])
+        e2e_steps = max(3, min(args.steps, 50))
+        torch.cuda.synchronize()
+        el = 0.0
+        for t in range(e2e_steps):
+            flush.fill_(t & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for c, h in zip(ctxs, hp):
+                c.generation_host(cfg, 10_000 + t, h[0], h[1], h[2], h[3])
+                h[0], h[2] = h[2], h[0]
+                h[1], h[3] = h[3], h[1]
+            el += time.perf_counter() - t0
+        per = len(gs) * (POP * K_DEL * 4 + POP * 8)
+        e2e = {"value": evals_per_step * e2e_steps * ws / el, "unit": "evals/s", "h2d_bytes_per_step": per,
+               "d2h_bytes_per_step": per, "steps": e2e_steps,
+               "api": "gapa_generation_host (pinned host population and fitness in and out)"}
+
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": workload_config(),
+            "gens_per_s": gens_per_s, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(p["fitness_launches"] + p["operator_launches"] for p in profs)),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gapa", "reference"], default="gapa")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gapa":
+        log("warm-up raised to 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gapa(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * gapa.h - C ABI of libgapa.so: batched critical-node-detection fitness and
+ * the genetic-algorithm step on one sm_103a GPU.
+ *
+ * Method: Yu et al., "Efficient Parallel Genetic Algorithm for Perturbed
+ * Substructure Optimization in Complex Network" (GAPA, arXiv 2412.20980).
+ *  - Problem (Section III-A, Eq. 1): an undirected, unweighted graph
+ *    G = (V, E) and a perturbation p of cost |p| = k; for critical node
+ *    detection p is a set of k deleted nodes.
+ *  - Population (Section III-B, Eq. 2): s individuals of k genes, an
+ *    int32 matrix POP[s][k] in row-major order; a gene is a node id.
+ *  - Fitness (Section III-C, Eq. 13; PC(G) of Table "Whole"): deleting a
+ *    node removes all of its edges; the fitness of a member is the pairwise
+ *    connectivity of what remains, sum over components C of |C|(|C|-1)/2,
+ *    an int64 to be minimised.
+ *  - Generation (Section III-B, Eqs. 3-11, Fig. 1): elitism, selection,
+ *    crossover with a per-gene Bernoulli(pc) mask, mutation with a per-gene
+ *    Bernoulli(pm) mask, duplicate repair, fitness of the children.
+ *
+ * Conventions for every call:
+ *  - Return value: GAPA_OK (0) or a negative GAPA_ERR_* code; the message of
+ *    the last failure on the calling thread is returned by gapa_last_error().
+ *  - Ownership: the caller owns every pointer it passes; the library copies
+ *    the graph at upload and owns that copy and its scratch buffers, freed by
+ *    gapa_destroy().  "_dev" pointers are device memory of the context's
+ *    device; "_host" pointers are host memory (pinned memory is fastest).
+ *  - Asynchrony: calls that take only device pointers enqueue work on the
+ *    context's stream and return at once; errors found by kernels (a gene
+ *    outside [0, n), an exhausted wait) are reported by the next
+ *    gapa_sync().  Calls that take host pointers return after the result is
+ *    in host memory.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC 2011), key = seed,
+ *    counter = (gene j, member i, generation g, tag << 24 | round); runs are
+ *    bit-reproducible for a given seed and configuration.
+ */
+#ifndef GAPA_H
+#define GAPA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GAPA_OK 0
+#define GAPA_ERR_INVALID_ARG -1   /* a size, pointer or configuration value is out of range */
+#define GAPA_ERR_INVALID_GRAPH -2 /* CSR not simple/symmetric/in range (self-loop, duplicate, asymmetric arc) */
+#define GAPA_ERR_OOM -3           /* device or host allocation failed */
+#define GAPA_ERR_CUDA -4          /* a CUDA runtime call failed */
+#define GAPA_ERR_TIMEOUT -5       /* a bounded device-side wait ran out */
+#define GAPA_ERR_STATE -6         /* call out of order, e.g. fitness before a graph was uploaded */
+#define GAPA_ERR_DEVICE -7        /* a kernel rejected its input, e.g. a gene outside [0, n) */
+
+#define GAPA_WHERE_HOST 0
+#define GAPA_WHERE_DEVICE 1
+
+/* gapa_config.flags */
+#define GAPA_FLAG_ROWWISE 1u  /* parent A of child i is member i itself (Eq. 6 read literally) */
+
+typedef struct gapa_ctx gapa_ctx; /* opaque, library-owned */
+
+/* GA configuration (Table "Params" of the paper gives pc, pm, iterations,
+ * population size and perturbation rate k/n per algorithm). */
+typedef struct gapa_config {
+    int32_t k;       /* genes per member = deleted nodes, 0 <= k < n */
+    int32_t pop;     /* population size s >= 2 */
+    int32_t gens;    /* generations run by gapa_run, >= 0 */
+    int32_t tourn;   /* tournament size t >= 1 (selection, Eq. 5) */
+    int32_t elite;   /* elite count; must be 1 */
+    uint32_t pc_thr; /* crossover mask threshold floor(pc * 2^32) (Eq. 4): mask = draw < pc_thr */
+    uint32_t pm_thr; /* mutation mask threshold floor(pm * 2^32) (Eq. 8): mask = draw < pm_thr */
+    uint64_t seed;   /* Philox key */
+    uint32_t flags;  /* GAPA_FLAG_* */
+} gapa_config;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream) that the context borrows for all work;
+ * it must outlive the context or be replaced with gapa_set_stream(). */
+int gapa_create(gapa_ctx** out, int device, void* cuda_stream);
+
+/* Free the context and everything it owns; NULL is ignored. */
+void gapa_destroy(gapa_ctx* ctx);
+
+/* Replace the borrowed stream. */
+int gapa_set_stream(gapa_ctx* ctx, void* cuda_stream);
+
+/* Upload the graph G (Section III-A: undirected, unweighted) as symmetric
+ * CSR: row_ptr[n+1] (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz) and
+ * col[nnz], every undirected edge {u,v} stored as both u->v and v->u.
+ * `where` says whether the two arrays are host or device memory.  The arrays
+ * are validated on the host (rows may be unsorted; no self-loops, no
+ * repeated arcs, every arc has its reverse, ids in [0, n)) and copied; the
+ * caller keeps ownership.  A new upload replaces the previous graph.
+ * Limits: 1 <= n < 2^31, nnz < 2^31.  Synchronous. */
+int gapa_graph_upload(gapa_ctx* ctx, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                      const int32_t* col, int where);
+
+/* Population initialisation (Eq. 2): fills pop_dev[s][k] (s = cfg->pop,
+ * k = cfg->k) with s uniformly drawn deletion sets of k distinct node ids
+ * (generation 0 of the Philox stream).  Asynchronous. */
+int gapa_pop_init(gapa_ctx* ctx, const gapa_config* cfg, int32_t* pop_dev);
+
+/* Fitness of a whole population in one batch (Section III-C, Eq. 13):
+ * fit_dev[i] = pairwise connectivity of G with the genes of row i of
+ * pop_dev[s][k] deleted.  Repeated genes in a row count once.  A gene
+ * outside [0, n) is reported by gapa_sync() as GAPA_ERR_DEVICE.
+ * s >= 0, k >= 0.  Asynchronous. */
+int gapa_fitness(gapa_ctx* ctx, const int32_t* pop_dev, int32_t s, int32_t k, int64_t* fit_dev);
+
+/* Same as gapa_fitness with host arrays: copies pop_host in, runs, copies
+ * fit_host out and synchronises (kernel errors are returned here). */
+int gapa_fitness_host(gapa_ctx* ctx, const int32_t* pop_host, int32_t s, int32_t k, int64_t* fit_host);
+
+/* One generation g >= 1 (Fig. 1 loop body; Eqs. 3-11) from
+ * (pop_in[s][k], fit_in[s]) to (pop_out[s][k], fit_out[s]):
+ *  - elitism: row 0 = the member with the lowest fitness (lowest index on
+ *    ties), fitness carried over;
+ *  - each child i in [1, s): parents A and B by two tournaments of size t
+ *    (draws with replacement, lower fitness wins, ties to the lower index);
+ *    gene j is B[j] when draw(j,i,g,XOVER) < pc_thr, else A[j]; it mutates
+ *    when draw(j,i,g,MUT) < pm_thr into a node uniform over [0, n);
+ *    repeated genes are repaired so that the k genes stay distinct;
+ *  - fitness of rows 1 .. s-1.
+ * pop_out/fit_out must not alias pop_in/fit_in.  Asynchronous. */
+int gapa_generation(gapa_ctx* ctx, const gapa_config* cfg, int32_t g, const int32_t* pop_in,
+                    const int64_t* fit_in, int32_t* pop_out, int64_t* fit_out);
+
+/* Same as gapa_generation with host arrays (copies in, runs, copies out,
+ * synchronises). */
+int gapa_generation_host(gapa_ctx* ctx, const gapa_config* cfg, int32_t g, const int32_t* pop_in_host,
+                         const int64_t* fit_in_host, int32_t* pop_out_host, int64_t* fit_out_host);
+
+/* A whole run: initialisation, fitness, then cfg->gens generations, each one
+ * replayed from a captured CUDA graph with the generation counter kept on
+ * the device.  Outputs: best_set_host[k] = genes of the final best member
+ * (lowest fitness, lowest index) in ascending order; *best_fit its fitness;
+ * traj_best_fit[gens+1] (may be NULL) the lowest fitness after
+ * initialisation and after every generation; final_pop_dev[s][k] (may be
+ * NULL) the final population.  Synchronous. */
+int gapa_run(gapa_ctx* ctx, const gapa_config* cfg, int32_t* best_set_host, int64_t* best_fit,
+             int64_t* traj_best_fit, int32_t* final_pop_dev);
+
+/* Per-kernel timing of the calls made between gapa_profile_begin() and
+ * gapa_profile_end(): CUDA events are recorded on the launching stream around
+ * every fitness launch and every genetic-operator launch (not inside the
+ * graph replays of gapa_run).  gapa_profile_end() synchronises and returns
+ * the totals. */
+typedef struct gapa_profile {
+    double fitness_ms;          /* summed duration of fitness launches */
+    double operators_ms;        /* summed duration of init/offspring launches */
+    int64_t fitness_launches;   /* fitness kernel launches */
+    int64_t operator_launches;  /* init/offspring kernel launches */
+    int64_t evals;              /* population members evaluated by those fitness launches */
+} gapa_profile;
+
+int gapa_profile_begin(gapa_ctx* ctx);
+int gapa_profile_end(gapa_ctx* ctx, gapa_profile* out);
+
+/* Wait for the context's stream and report device-side errors (then clear
+ * them). */
+int gapa_sync(gapa_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gapa_last_error(void);
+
+/* Library version string. */
+const char* gapa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAPA_H */

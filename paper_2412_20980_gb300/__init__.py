@@ -1,0 +1,17 @@
+"""GB300-native batched critical-node-detection fitness and GA step (GAPA, arXiv 2412.20980).
+
+The compute path is libgapa.so (hand-written sm_103a CUDA kernels behind a C
+ABI, declared in include/gapa.h); ``gapa`` is its ctypes binding.
+"""
+from .gapa import (
+    Config,
+    Context,
+    GapaError,
+    EXPORTS,
+    FLAG_ROWWISE,
+    load,
+    make_config,
+    threshold,
+)
+
+__all__ = ["Config", "Context", "GapaError", "EXPORTS", "FLAG_ROWWISE", "load", "make_config", "threshold"]

@@ -1,0 +1,541 @@
+// C ABI of libgapa.so: contexts, graph upload and validation, and the
+// drivers of fitness, generation and whole runs.  Every compute step runs in
+// the kernels of fitness.cu and ga.cu; this file moves data and orders work.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "gapa_internal.cuh"
+
+int gapa_fitness_kernels_init(gapa_ctx* c);
+int gapa_ga_kernels_init(gapa_ctx* c);
+
+namespace {
+thread_local std::string g_last_error;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void free_graph(DeviceGraph& g) {
+    cudaFree(g.row_ptr);
+    cudaFree(g.col);
+    cudaFree(g.edges);
+    cudaFree(g.probe);
+    g = DeviceGraph();
+}
+
+// Host-side validation of a symmetric simple CSR; returns the rows sorted.
+int validate_csr(int32_t n, int64_t nnz, const int32_t* rp, const int32_t* col_in, std::vector<int32_t>& col) {
+    if (rp[0] != 0) return gapa_fail(GAPA_ERR_INVALID_GRAPH, "row_ptr[0] = %d, expected 0", rp[0]);
+    for (int32_t v = 0; v < n; ++v)
+        if (rp[v + 1] < rp[v]) return gapa_fail(GAPA_ERR_INVALID_GRAPH, "row_ptr decreases at row %d", v);
+    if ((int64_t)rp[n] != nnz)
+        return gapa_fail(GAPA_ERR_INVALID_GRAPH, "row_ptr[n] = %d but nnz = %lld", rp[n], (long long)nnz);
+    col.assign(col_in, col_in + nnz);
+    const unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<int> bad(nth, 0);
+    std::vector<int32_t> bad_row(nth, -1);
+    auto work = [&](unsigned t, int pass) {
+        const int32_t lo = (int32_t)((int64_t)n * t / nth), hi = (int32_t)((int64_t)n * (t + 1) / nth);
+        for (int32_t u = lo; u < hi && !bad[t]; ++u) {
+            int32_t* b = col.data() + rp[u];
+            int32_t* e = col.data() + rp[u + 1];
+            if (pass == 0) {
+                for (int32_t* p = b; p < e; ++p) {
+                    if (*p < 0 || *p >= n) { bad[t] = 1; bad_row[t] = u; break; }
+                    if (*p == u) { bad[t] = 2; bad_row[t] = u; break; }
+                }
+                if (bad[t]) break;
+                std::sort(b, e);
+                for (int32_t* p = b + 1; p < e; ++p)
+                    if (*p == *(p - 1)) { bad[t] = 3; bad_row[t] = u; break; }
+            } else {
+                for (int32_t* p = b; p < e; ++p) {
+                    const int32_t v = *p;
+                    const int32_t* vb = col.data() + rp[v];
+                    const int32_t* ve = col.data() + rp[v + 1];
+                    if (!std::binary_search(vb, ve, u)) { bad[t] = 4; bad_row[t] = u; break; }
+                }
+            }
+        }
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nth; ++t) th.emplace_back(work, t, pass);
+        for (auto& x : th) x.join();
+        for (unsigned t = 0; t < nth; ++t) {
+            static const char* what[] = {"", "column id out of range", "self-loop", "repeated arc",
+                                         "arc without its reverse"};
+            if (bad[t]) return gapa_fail(GAPA_ERR_INVALID_GRAPH, "%s in row %d", what[bad[t]], bad_row[t]);
+        }
+    }
+    return GAPA_OK;
+}
+
+int check_cfg(gapa_ctx* c, const gapa_config* cfg) {
+    if (!cfg) return gapa_fail(GAPA_ERR_INVALID_ARG, "config is NULL");
+    if (c->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "no graph uploaded");
+    if (cfg->k < 0 || cfg->k >= c->g.n) return gapa_fail(GAPA_ERR_INVALID_ARG, "need 0 <= k < n (k=%d, n=%d)", cfg->k, c->g.n);
+    if (cfg->pop < 2) return gapa_fail(GAPA_ERR_INVALID_ARG, "population must be >= 2 (got %d)", cfg->pop);
+    if (cfg->tourn < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "tournament size must be >= 1");
+    if (cfg->elite != 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "elite count must be 1 (got %d)", cfg->elite);
+    if (cfg->gens < 0) return gapa_fail(GAPA_ERR_INVALID_ARG, "gens must be >= 0");
+    if (cfg->flags & ~GAPA_FLAG_ROWWISE) return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
+    return gapa_ga_check_limits(c, c->g.n, cfg->k, cfg->pop);
+}
+
+GaParams make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_ptr) {
+    GaParams p;
+    p.n = c->g.n;
+    p.k = cfg->k;
+    p.s = cfg->pop;
+    p.t = cfg->tourn;
+    p.pc_thr = cfg->pc_thr;
+    p.pm_thr = cfg->pm_thr;
+    p.key = RngKey{(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
+    p.flags = cfg->flags;
+    p.g = g;
+    p.g_ptr = g_ptr;
+    return p;
+}
+
+// One generation on stream st: offspring rows, then fitness of rows 1..s-1.
+int enqueue_generation(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,
+                       int32_t* pop_out, int64_t* fit_out, cudaStream_t st) {
+    int rc = gapa_launch_offspring(c, p, pop_in, fit_in, pop_out, fit_out, st);
+    if (rc != GAPA_OK) return rc;
+    return gapa_launch_fitness(c, pop_out + p.k, p.s - 1, p.k, fit_out + 1, st);
+}
+
+int read_status(gapa_ctx* c, cudaStream_t st) {
+    int h = 0;
+    GAPA_CUDA(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GAPA_CUDA(cudaStreamSynchronize(st));
+    if (h == 0) return GAPA_OK;
+    GAPA_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), st));
+    GAPA_CUDA(cudaStreamSynchronize(st));
+    if (h & GAPA_DEV_TIMEOUT) return gapa_fail(GAPA_ERR_TIMEOUT, "a device-side wait ran out (status 0x%x)", h);
+    if (h & GAPA_DEV_BAD_GENE) return gapa_fail(GAPA_ERR_DEVICE, "a gene outside [0, n) was passed (status 0x%x)", h);
+    return gapa_fail(GAPA_ERR_DEVICE, "device status 0x%x", h);
+}
+
+int ensure_stage(gapa_ctx* c, size_t pop_elems, size_t fit_elems) {
+    if (pop_elems > c->stage_pop_cap) {
+        for (auto& p : c->stage_pop) { cudaFree(p); p = nullptr; }
+        c->stage_pop_cap = 0;
+        for (auto& p : c->stage_pop)
+            if (cudaMalloc(&p, std::max<size_t>(pop_elems, 1) * sizeof(int32_t)) != cudaSuccess)
+                return gapa_fail(GAPA_ERR_OOM, "staging population of %zu genes", pop_elems);
+        c->stage_pop_cap = pop_elems;
+    }
+    if (fit_elems > c->stage_fit_cap) {
+        for (auto& p : c->stage_fit) { cudaFree(p); p = nullptr; }
+        c->stage_fit_cap = 0;
+        for (auto& p : c->stage_fit)
+            if (cudaMalloc(&p, std::max<size_t>(fit_elems, 1) * sizeof(int64_t)) != cudaSuccess)
+                return gapa_fail(GAPA_ERR_OOM, "staging fitness of %zu members", fit_elems);
+        c->stage_fit_cap = fit_elems;
+    }
+    return GAPA_OK;
+}
+
+}  // namespace
+
+int gapa_fail(int code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int gapa_cuda_fail(cudaError_t e, const char* what) {
+    const int code = e == cudaErrorMemoryAllocation ? GAPA_ERR_OOM : GAPA_ERR_CUDA;
+    return gapa_fail(code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int gapa_set_smem_limit(const void* kernel, size_t optin, size_t* max_dyn) {
+    cudaFuncAttributes a;
+    GAPA_CUDA(cudaFuncGetAttributes(&a, kernel));
+    const size_t dyn = optin > a.sharedSizeBytes ? optin - a.sharedSizeBytes : 0;
+    GAPA_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    if (*max_dyn == 0 || dyn < *max_dyn) *max_dyn = dyn;
+    return GAPA_OK;
+}
+
+int gapa_reserve(void** ptr, size_t* cap, size_t count, size_t elem) {
+    if (count <= *cap) return GAPA_OK;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc(ptr, std::max<size_t>(count, 1) * elem) != cudaSuccess) {
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "device scratch of %zu bytes", count * elem);
+    }
+    *cap = count;
+    return GAPA_OK;
+}
+
+ProfileScope::ProfileScope(gapa_ctx* c_, cudaStream_t st_, int kind_, int evals_)
+    : c(c_), st(st_), kind(kind_), evals(evals_) {
+    if (!c->profiling || c->capturing) return;
+    for (cudaEvent_t* e : {&a, &b}) {
+        if (!c->event_pool.empty()) {
+            *e = c->event_pool.back();
+            c->event_pool.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+            *e = nullptr;
+        }
+    }
+    if (a && b) cudaEventRecord(a, st);
+}
+
+ProfileScope::~ProfileScope() {
+    if (!a || !b) {
+        if (a) c->event_pool.push_back(a);
+        if (b) c->event_pool.push_back(b);
+        return;
+    }
+    cudaEventRecord(b, st);
+    c->timed.push_back(gapa_ctx::Timed{a, b, kind, evals});
+}
+
+extern "C" {
+
+const char* gapa_last_error(void) { return g_last_error.c_str(); }
+
+const char* gapa_version(void) { return "gapa-gb300 0.1 (sm_103a)"; }
+
+int gapa_create(gapa_ctx** out, int device, void* cuda_stream) {
+    if (!out) return gapa_fail(GAPA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    GAPA_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return gapa_fail(GAPA_ERR_INVALID_ARG, "device %d of %d", device, ndev);
+    DeviceGuard guard(device);
+    gapa_ctx* c = new gapa_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    int v = 0;
+    auto bail = [&](int rc) {
+        gapa_destroy(c);
+        return rc;
+    };
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_CUDA, "device attribute query failed"));
+    c->num_sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_CUDA, "device attribute query failed"));
+    c->smem_optin = (size_t)v;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_CUDA, "stream/event creation failed"));
+    if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess || cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_OOM, "status word"));
+    if (cudaMalloc(&c->run_gen, sizeof(int)) != cudaSuccess || cudaMalloc(&c->run_best, sizeof(int)) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_OOM, "run counters"));
+    int rc = gapa_fitness_kernels_init(c);
+    if (rc == GAPA_OK) rc = gapa_ga_kernels_init(c);
+    if (rc != GAPA_OK) return bail(rc);
+    *out = c;
+    return GAPA_OK;
+}
+
+void gapa_destroy(gapa_ctx* c) {
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    free_graph(c->g);
+    cudaFree(c->status);
+    cudaFree(c->labels);
+    for (auto p : c->stage_pop) cudaFree(p);
+    for (auto p : c->stage_fit) cudaFree(p);
+    cudaFree(c->run_gen);
+    cudaFree(c->run_best);
+    cudaFree(c->run_traj);
+    for (auto& t : c->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->ev_a) cudaEventDestroy(c->ev_a);
+    if (c->ev_b) cudaEventDestroy(c->ev_b);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+int gapa_set_stream(gapa_ctx* c, void* s) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    c->stream = (cudaStream_t)s;
+    return GAPA_OK;
+}
+
+int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, int where) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "n must be >= 1 (got %d)", n);
+    if (nnz < 0 || nnz >= (1LL << 31)) return gapa_fail(GAPA_ERR_INVALID_ARG, "nnz out of range (%lld)", (long long)nnz);
+    if (nnz & 1) return gapa_fail(GAPA_ERR_INVALID_GRAPH, "odd arc count %lld cannot be symmetric", (long long)nnz);
+    if (!row_ptr || (nnz > 0 && !col)) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL CSR array");
+    if (where != GAPA_WHERE_HOST && where != GAPA_WHERE_DEVICE) return gapa_fail(GAPA_ERR_INVALID_ARG, "bad 'where'");
+    DeviceGuard guard(c->device);
+    std::vector<int32_t> rp((size_t)n + 1), cin;
+    const int32_t* src_col = col;
+    if (where == GAPA_WHERE_DEVICE) {
+        GAPA_CUDA(cudaMemcpy(rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
+        cin.resize((size_t)nnz);
+        if (nnz) GAPA_CUDA(cudaMemcpy(cin.data(), col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost));
+        src_col = cin.data();
+    } else {
+        std::memcpy(rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+    }
+    std::vector<int32_t> sorted;
+    int rc = validate_csr(n, nnz, rp.data(), src_col, sorted);
+    if (rc != GAPA_OK) return rc;
+    // undirected edge list (u < v) in CSR order, and the highest-degree nodes
+    const int E = (int)(nnz / 2);
+    std::vector<int2> edges;
+    edges.reserve((size_t)E);
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t e = rp[u]; e < rp[u + 1]; ++e)
+            if (sorted[e] > u) edges.push_back(make_int2(u, sorted[e]));
+    std::vector<int32_t> order((size_t)n);
+    for (int32_t v = 0; v < n; ++v) order[v] = v;
+    const int np = std::min(n, kProbe);
+    std::partial_sort(order.begin(), order.begin() + np, order.end(), [&](int32_t a, int32_t b) {
+        const int32_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
+        return da != db ? da > db : a < b;
+    });
+    std::vector<int32_t> probe(kProbe, order[0]);
+    for (int i = 0; i < np; ++i) probe[i] = order[i];
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    free_graph(c->g);
+    DeviceGraph g;
+    g.n = n;
+    g.nnz = nnz;
+    g.num_edges = E;
+    g.max_degree = rp[order[0] + 1] - rp[order[0]];
+    if (cudaMalloc(&g.row_ptr, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+        cudaMalloc(&g.col, sizeof(int32_t) * std::max<size_t>((size_t)nnz, 1)) != cudaSuccess ||
+        cudaMalloc(&g.edges, sizeof(int2) * std::max<size_t>((size_t)E, 2)) != cudaSuccess ||
+        cudaMalloc(&g.probe, sizeof(int32_t) * kProbe) != cudaSuccess) {
+        free_graph(g);
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "graph of %d nodes, %lld arcs", n, (long long)nnz);
+    }
+    GAPA_CUDA(cudaMemcpy(g.row_ptr, rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice));
+    if (nnz) GAPA_CUDA(cudaMemcpy(g.col, sorted.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice));
+    if (E) GAPA_CUDA(cudaMemcpy(g.edges, edges.data(), sizeof(int2) * (size_t)E, cudaMemcpyHostToDevice));
+    GAPA_CUDA(cudaMemcpy(g.probe, probe.data(), sizeof(int32_t) * kProbe, cudaMemcpyHostToDevice));
+    c->g = g;
+    return GAPA_OK;
+}
+
+int gapa_pop_init(gapa_ctx* c, const gapa_config* cfg, int32_t* pop_dev) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_cfg(c, cfg);
+    if (rc != GAPA_OK) return rc;
+    if (!pop_dev && cfg->k > 0) return gapa_fail(GAPA_ERR_INVALID_ARG, "pop_dev is NULL");
+    DeviceGuard guard(c->device);
+    return gapa_launch_init(c, make_params(c, cfg, 0, nullptr), pop_dev, c->stream);
+}
+
+int gapa_fitness(gapa_ctx* c, const int32_t* pop_dev, int32_t s, int32_t k, int64_t* fit_dev) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "no graph uploaded");
+    if (s < 0 || k < 0) return gapa_fail(GAPA_ERR_INVALID_ARG, "negative size (s=%d, k=%d)", s, k);
+    if ((long long)s * k >= (1LL << 31)) return gapa_fail(GAPA_ERR_INVALID_ARG, "s*k must be below 2^31");
+    if (s > 0 && (!fit_dev || (!pop_dev && k > 0))) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard guard(c->device);
+    return gapa_launch_fitness(c, pop_dev, s, k, fit_dev, c->stream);
+}
+
+int gapa_fitness_host(gapa_ctx* c, const int32_t* pop_host, int32_t s, int32_t k, int64_t* fit_host) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "no graph uploaded");
+    if (s < 0 || k < 0) return gapa_fail(GAPA_ERR_INVALID_ARG, "negative size (s=%d, k=%d)", s, k);
+    if ((long long)s * k >= (1LL << 31)) return gapa_fail(GAPA_ERR_INVALID_ARG, "s*k must be below 2^31");
+    if (s == 0) return GAPA_OK;
+    if (!fit_host || (!pop_host && k > 0)) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard guard(c->device);
+    int rc = ensure_stage(c, (size_t)s * k, (size_t)s);
+    if (rc != GAPA_OK) return rc;
+    cudaStream_t st = c->stream;
+    if (k) GAPA_CUDA(cudaMemcpyAsync(c->stage_pop[0], pop_host, sizeof(int32_t) * (size_t)s * k, cudaMemcpyHostToDevice, st));
+    rc = gapa_launch_fitness(c, c->stage_pop[0], s, k, c->stage_fit[0], st);
+    if (rc != GAPA_OK) return rc;
+    GAPA_CUDA(cudaMemcpyAsync(fit_host, c->stage_fit[0], sizeof(int64_t) * (size_t)s, cudaMemcpyDeviceToHost, st));
+    return read_status(c, st);
+}
+
+int gapa_generation(gapa_ctx* c, const gapa_config* cfg, int32_t g, const int32_t* pop_in, const int64_t* fit_in,
+                    int32_t* pop_out, int64_t* fit_out) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_cfg(c, cfg);
+    if (rc != GAPA_OK) return rc;
+    if (g < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "generation index must be >= 1 (got %d)", g);
+    if (!fit_in || !fit_out || (cfg->k > 0 && (!pop_in || !pop_out)))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL pointer");
+    if (pop_in == pop_out || fit_in == fit_out) return gapa_fail(GAPA_ERR_INVALID_ARG, "outputs alias inputs");
+    DeviceGuard guard(c->device);
+    return enqueue_generation(c, make_params(c, cfg, g, nullptr), pop_in, fit_in, pop_out, fit_out, c->stream);
+}
+
+int gapa_generation_host(gapa_ctx* c, const gapa_config* cfg, int32_t g, const int32_t* pop_in_host,
+                         const int64_t* fit_in_host, int32_t* pop_out_host, int64_t* fit_out_host) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_cfg(c, cfg);
+    if (rc != GAPA_OK) return rc;
+    if (g < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "generation index must be >= 1 (got %d)", g);
+    if (!fit_in_host || !fit_out_host || (cfg->k > 0 && (!pop_in_host || !pop_out_host)))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard guard(c->device);
+    const size_t cells = (size_t)cfg->pop * cfg->k;
+    rc = ensure_stage(c, cells, (size_t)cfg->pop);
+    if (rc != GAPA_OK) return rc;
+    cudaStream_t st = c->stream;
+    if (cells) GAPA_CUDA(cudaMemcpyAsync(c->stage_pop[0], pop_in_host, sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
+    GAPA_CUDA(cudaMemcpyAsync(c->stage_fit[0], fit_in_host, sizeof(int64_t) * cfg->pop, cudaMemcpyHostToDevice, st));
+    rc = enqueue_generation(c, make_params(c, cfg, g, nullptr), c->stage_pop[0], c->stage_fit[0], c->stage_pop[1],
+                            c->stage_fit[1], st);
+    if (rc != GAPA_OK) return rc;
+    if (cells) GAPA_CUDA(cudaMemcpyAsync(pop_out_host, c->stage_pop[1], sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st));
+    GAPA_CUDA(cudaMemcpyAsync(fit_out_host, c->stage_fit[1], sizeof(int64_t) * cfg->pop, cudaMemcpyDeviceToHost, st));
+    return read_status(c, st);
+}
+
+int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_t* best_fit, int64_t* traj_best_fit,
+             int32_t* final_pop_dev) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_cfg(c, cfg);
+    if (rc != GAPA_OK) return rc;
+    if (!best_fit || (cfg->k > 0 && !best_set_host)) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL output pointer");
+    DeviceGuard guard(c->device);
+    const int s = cfg->pop, k = cfg->k, G = cfg->gens;
+    const size_t cells = (size_t)s * k;
+    rc = ensure_stage(c, cells, (size_t)s);
+    if (rc == GAPA_OK) rc = gapa_reserve((void**)&c->run_traj, &c->run_traj_cap, (size_t)G + 1, sizeof(int64_t));
+    if (rc == GAPA_OK) rc = gapa_fitness_prepare(c, s);
+    if (rc != GAPA_OK) return rc;
+    cudaStream_t st = c->own_stream;
+    // order after the caller's pending work
+    GAPA_CUDA(cudaEventRecord(c->ev_a, c->stream));
+    GAPA_CUDA(cudaStreamWaitEvent(st, c->ev_a, 0));
+    int32_t* P[2] = {c->stage_pop[0], c->stage_pop[1]};
+    int64_t* F[2] = {c->stage_fit[0], c->stage_fit[1]};
+    GAPA_CUDA(cudaMemsetAsync(c->run_gen, 0, sizeof(int), st));
+    const GaParams p0 = make_params(c, cfg, 0, nullptr);
+    rc = gapa_launch_init(c, p0, P[0], st);
+    if (rc == GAPA_OK) rc = gapa_launch_fitness(c, P[0], s, k, F[0], st);
+    if (rc == GAPA_OK) rc = gapa_launch_record(c, F[0], s, c->run_gen, c->run_traj, c->run_best, st);
+    if (rc != GAPA_OK) return rc;
+    const GaParams pg = make_params(c, cfg, 0, c->run_gen);  // generation read from the device counter
+    if (G >= 2) {
+        // capture two generations (P0 -> P1 -> P0) and replay them G/2 times
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        GAPA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        c->capturing = true;
+        int crc = GAPA_OK;
+        for (int h = 0; h < 2 && crc == GAPA_OK; ++h) {
+            crc = enqueue_generation(c, pg, P[h], F[h], P[h ^ 1], F[h ^ 1], st);
+            if (crc == GAPA_OK) crc = gapa_launch_record(c, F[h ^ 1], s, c->run_gen, c->run_traj, c->run_best, st);
+        }
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        c->capturing = false;
+        if (crc != GAPA_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return crc;
+        }
+        GAPA_CUDA(ce);
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        GAPA_CUDA(ce);
+        for (int r = 0; r < G / 2; ++r) {
+            ce = cudaGraphLaunch(exec, st);
+            if (ce != cudaSuccess) break;
+        }
+        cudaGraphExecDestroy(exec);
+        GAPA_CUDA(ce);
+    }
+    if (G % 2 == 1) {
+        // the last (odd) generation, launched directly: P0 -> P1
+        rc = enqueue_generation(c, pg, P[0], F[0], P[1], F[1], st);
+        if (rc == GAPA_OK) rc = gapa_launch_record(c, F[1], s, c->run_gen, c->run_traj, c->run_best, st);
+        if (rc != GAPA_OK) return rc;
+    }
+    const int fin = G % 2;
+    int best = 0;
+    GAPA_CUDA(cudaMemcpyAsync(&best, c->run_best, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GAPA_CUDA(cudaStreamSynchronize(st));
+    rc = read_status(c, st);
+    if (rc != GAPA_OK) return rc;
+    GAPA_CUDA(cudaMemcpyAsync(best_fit, F[fin] + best, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (k) GAPA_CUDA(cudaMemcpyAsync(best_set_host, P[fin] + (size_t)best * k, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, st));
+    if (traj_best_fit)
+        GAPA_CUDA(cudaMemcpyAsync(traj_best_fit, c->run_traj, sizeof(int64_t) * ((size_t)G + 1), cudaMemcpyDeviceToHost, st));
+    if (final_pop_dev && cells)
+        GAPA_CUDA(cudaMemcpyAsync(final_pop_dev, P[fin], sizeof(int32_t) * cells, cudaMemcpyDeviceToDevice, st));
+    GAPA_CUDA(cudaStreamSynchronize(st));
+    std::sort(best_set_host, best_set_host + k);
+    // later work on the caller's stream sees the final population
+    GAPA_CUDA(cudaEventRecord(c->ev_b, st));
+    GAPA_CUDA(cudaStreamWaitEvent(c->stream, c->ev_b, 0));
+    return GAPA_OK;
+}
+
+int gapa_profile_begin(gapa_ctx* c) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    c->profiling = true;
+    return GAPA_OK;
+}
+
+int gapa_profile_end(gapa_ctx* c, gapa_profile* out) {
+    if (!c || !out) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(c->device);
+    c->profiling = false;
+    *out = gapa_profile{0.0, 0.0, 0, 0, 0};
+    int rc = GAPA_OK;
+    for (auto& t : c->timed) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.a, t.b);
+        if (e != cudaSuccess && rc == GAPA_OK) rc = gapa_cuda_fail(e, "profile event");
+        if (t.kind == 0) {
+            out->fitness_ms += ms;
+            out->fitness_launches += 1;
+            out->evals += t.evals;
+        } else {
+            out->operators_ms += ms;
+            out->operator_launches += 1;
+        }
+        c->event_pool.push_back(t.a);
+        c->event_pool.push_back(t.b);
+    }
+    c->timed.clear();
+    return rc;
+}
+
+int gapa_sync(gapa_ctx* c) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    GAPA_CUDA(cudaStreamSynchronize(c->stream));
+    return read_status(c, c->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,355 @@
+// Genetic operators on the GPU (Section III-B, Eqs. 2-11, Fig. 1).
+//
+// One CTA builds one population row.  The kept-gene set of the row is a
+// bitmap of n bits in shared memory; the per-position crossover/mutation
+// flags (k bytes) and the list of open positions (k ints) sit beside it.
+// Random numbers: Philox4x32-10 at counter (j, i, g, tag << 24 | round).
+//
+// Readings where the paper is silent (the same ones the CPU oracle follows):
+//  - selection: tournament of size t with replacement, lower fitness wins,
+//    ties to the lower index (Eq. 5 uses roulette);
+//  - elitism: one elite, the lowest fitness (lowest index on ties), copied to
+//    row 0 with its fitness;
+//  - a gene from B that repeats a kept gene from A becomes an open position
+//    whose first candidate is A[j]; a mutated position is open with first
+//    candidate uniform over [0, n);
+//  - repair: rounds r = 0..31; in ascending position order each open
+//    position takes its round-r candidate if that node is not kept yet (and
+//    keeps it at once); round r >= 1 candidates are uniform over [0, n) from
+//    tag REPAIR, round r; positions still open after round 31 take the
+//    smallest free ids in ascending position order.
+#include <climits>
+
+#include "gapa_internal.cuh"
+
+namespace {
+
+constexpr int kGaBlock = 256;
+
+__device__ __forceinline__ bool bit_test(const unsigned* bm, int v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
+__device__ __forceinline__ void bit_set(unsigned* bm, int v) { atomicOr(&bm[v >> 5], 1u << (v & 31)); }
+
+// Row layout in dynamic shared memory: kept bitmap | flags (k bytes) | holes (k ints)
+struct RowSmem {
+    unsigned* kept;
+    unsigned char* flags;
+    int* holes;
+};
+
+__device__ __forceinline__ RowSmem carve(unsigned char* base, int n, int k) {
+    RowSmem r;
+    const int words = (n + 31) >> 5;
+    r.kept = reinterpret_cast<unsigned*>(base);
+    r.flags = base + (size_t)words * 4;
+    const size_t off = ((size_t)words * 4 + (size_t)k + 15) & ~(size_t)15;
+    r.holes = reinterpret_cast<int*>(base + off);
+    return r;
+}
+
+size_t row_smem_bytes(int n, int k) {
+    const size_t words = ((size_t)n + 31) >> 5;
+    return ((words * 4 + (size_t)k + 15) & ~(size_t)15) + (size_t)k * 4;
+}
+
+enum FlagBits : unsigned char { F_XOVER = 1, F_MUT = 2, F_HOLE = 4 };
+
+// Round-0 candidate of an open position.
+struct InitCand {
+    RngKey key;
+    int i, n;
+    __device__ int operator()(int j) const { return uniform_below(gapa_draw(key, j, i, 0, TAG_INIT, 0), n); }
+};
+
+struct ChildCand {
+    RngKey key;
+    int i, g, n;
+    const unsigned char* flags;
+    const int* A;
+    int* status;
+    __device__ int operator()(int j) const {
+        if (flags[j] & F_MUT) return uniform_below(gapa_draw(key, j, i, g, TAG_MUTVAL, 0), n);
+        const int a = A[j];
+        if ((unsigned)a >= (unsigned)n) {
+            atomicOr(status, GAPA_DEV_BAD_GENE);
+            return -1;
+        }
+        return a;
+    }
+};
+
+// Repair by warp 0 of the CTA: holes[0..nholes) ascending positions of `row`.
+template <class Cand>
+__device__ void repair_warp(unsigned* kept, int* holes, int nholes, int* row, const Cand& cand0, RngKey key,
+                            int i, int g, int n) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < kRepairRounds && nholes > 0; ++r) {
+        int out = 0;
+        for (int base = 0; base < nholes; base += 32) {
+            const int idx = base + lane;
+            const bool active = idx < nholes;
+            const int j = active ? holes[idx] : -1;
+            int c = -1;
+            if (active) c = r == 0 ? cand0(j) : uniform_below(gapa_draw(key, j, i, g, TAG_REPAIR, r), n);
+            const bool valid = active && c >= 0;
+            const bool taken = valid && bit_test(kept, c);
+            const unsigned peers = __match_any_sync(0xffffffffu, c);
+            const bool first = lane == __ffs(peers) - 1;
+            const bool accept = valid && !taken && first;
+            if (accept) {
+                bit_set(kept, c);
+                row[j] = c;
+            }
+            const bool reject = active && !accept;
+            const unsigned rej = __ballot_sync(0xffffffffu, reject);
+            if (reject) holes[out + __popc(rej & lt_mask)] = j;
+            out += __popc(rej);
+            __syncwarp();
+        }
+        nholes = out;
+    }
+    if (nholes > 0 && lane == 0) {
+        int next = 0;
+        for (int h = 0; h < nholes; ++h) {
+            while (bit_test(kept, next)) ++next;
+            bit_set(kept, next);
+            row[holes[h]] = next;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void clear_bitmap(unsigned* kept, int n) {
+    const int words = (n + 31) >> 5;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) kept[w] = 0u;
+}
+
+// Population initialisation (Eq. 2): every position open, candidates from tag INIT.
+__global__ void __launch_bounds__(kGaBlock) init_kernel(GaParams p, int* __restrict__ pop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int i = blockIdx.x;
+    RowSmem sm = carve(smem, p.n, p.k);
+    clear_bitmap(sm.kept, p.n);
+    for (int j = threadIdx.x; j < p.k; j += blockDim.x) sm.holes[j] = j;
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    InitCand cand{p.key, i, p.n};
+    repair_warp(sm.kept, sm.holes, p.k, pop + (size_t)i * p.k, cand, p.key, i, 0, p.n);
+}
+
+// Tournament of size t for parent slot `slot` of child i.
+__device__ int tournament(const GaParams& p, int i, int g, int slot, const long long* fit) {
+    int best = -1;
+    long long bf = 0;
+    for (int r = 0; r < p.t; ++r) {
+        const int x = uniform_below(gapa_draw(p.key, slot * p.t + r, i, g, TAG_SEL, 0), p.s);
+        const long long fx = fit[x];
+        if (best < 0 || fx < bf || (fx == bf && x < best)) {
+            best = x;
+            bf = fx;
+        }
+    }
+    return best;
+}
+
+// Block argmin of fit[0..s) (lowest value, lowest index); result valid in all threads.
+__device__ void block_argmin(const long long* __restrict__ fit, int s, long long* out_val, int* out_idx) {
+    __shared__ long long sv[32];
+    __shared__ int si[32];
+    long long bv = LLONG_MAX;
+    int bi = INT_MAX;
+    for (int x = threadIdx.x; x < s; x += blockDim.x) {
+        const long long v = fit[x];
+        if (v < bv || (v == bv && x < bi)) {
+            bv = v;
+            bi = x;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov < bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        bv = lane < nw ? sv[lane] : LLONG_MAX;
+        bi = lane < nw ? si[lane] : INT_MAX;
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            sv[0] = bv;
+            si[0] = bi;
+        }
+    }
+    __syncthreads();
+    *out_val = sv[0];
+    *out_idx = si[0];
+}
+
+// One generation's rows: CTA 0 = elite copy, CTA i >= 1 = child i.
+__global__ void __launch_bounds__(kGaBlock) offspring_kernel(GaParams p, const int* __restrict__ pop_in,
+                                                             const long long* __restrict__ fit_in,
+                                                             int* __restrict__ pop_out,
+                                                             long long* __restrict__ fit_out, int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int sh_parent[2];
+    __shared__ int sh_warp_cnt[kGaBlock / 32];
+    const int i = blockIdx.x;
+    const int g = p.g_ptr ? *p.g_ptr : p.g;
+    const int n = p.n, k = p.k;
+    if (i == 0) {
+        long long v;
+        int e;
+        block_argmin(fit_in, p.s, &v, &e);
+        const int* src = pop_in + (size_t)e * k;
+        for (int j = threadIdx.x; j < k; j += blockDim.x) pop_out[j] = src[j];
+        if (threadIdx.x == 0) fit_out[0] = v;
+        return;
+    }
+    RowSmem sm = carve(smem, n, k);
+    if (threadIdx.x == 0) {
+        sh_parent[0] = (p.flags & GAPA_FLAG_ROWWISE) ? i : tournament(p, i, g, 0, fit_in);
+        sh_parent[1] = tournament(p, i, g, 1, fit_in);
+    }
+    clear_bitmap(sm.kept, n);
+    __syncthreads();
+    const int* A = pop_in + (size_t)sh_parent[0] * k;
+    const int* B = pop_in + (size_t)sh_parent[1] * k;
+    int* C = pop_out + (size_t)i * k;
+    // crossover and mutation masks (Eqs. 3-4, 7-8); genes kept from A
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const bool xo = gapa_draw(p.key, j, i, g, TAG_XOVER, 0) < p.pc_thr;
+        const bool mu = gapa_draw(p.key, j, i, g, TAG_MUT, 0) < p.pm_thr;
+        unsigned char f = (xo ? F_XOVER : 0) | (mu ? F_MUT : 0);
+        if (!mu && !xo) {
+            const int a = A[j];
+            if ((unsigned)a < (unsigned)n) {
+                C[j] = a;
+                bit_set(sm.kept, a);
+            } else {
+                atomicOr(status, GAPA_DEV_BAD_GENE);
+                f |= F_HOLE;
+            }
+        }
+        if (mu) f |= F_HOLE;
+        sm.flags[j] = f;
+    }
+    __syncthreads();
+    // genes from B (Eq. 6); a repeat of a kept A gene opens the position
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const unsigned char f = sm.flags[j];
+        if (f == F_XOVER) {
+            const int b = B[j];
+            if ((unsigned)b >= (unsigned)n) {
+                atomicOr(status, GAPA_DEV_BAD_GENE);
+                sm.flags[j] = f | F_HOLE;
+            } else if (bit_test(sm.kept, b)) {
+                sm.flags[j] = f | F_HOLE;
+            } else {
+                C[j] = b;
+                bit_set(sm.kept, b);
+            }
+        }
+    }
+    __syncthreads();
+    // open positions in ascending order: contiguous ranges per thread + block scan
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int per = (k + T - 1) / T;
+    const int j0 = min(k, tid * per), j1 = min(k, j0 + per);
+    int cnt = 0;
+    for (int j = j0; j < j1; ++j) cnt += (sm.flags[j] & F_HOLE) ? 1 : 0;
+    const int lane = tid & 31, warp = tid >> 5;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh_warp_cnt[warp] = incl;
+    __syncthreads();
+    int warp_off = 0, total = 0;
+    for (int w = 0; w < (T >> 5); ++w) {
+        if (w < warp) warp_off += sh_warp_cnt[w];
+        total += sh_warp_cnt[w];
+    }
+    int pos = warp_off + incl - cnt;
+    for (int j = j0; j < j1; ++j)
+        if (sm.flags[j] & F_HOLE) sm.holes[pos++] = j;
+    __syncthreads();
+    if (warp != 0) return;
+    ChildCand cand{p.key, i, g, n, sm.flags, A, status};
+    repair_warp(sm.kept, sm.holes, total, C, cand, p.key, i, g, n);
+}
+
+// Lowest fitness of a population: traj[*gen] = min, *best = argmin, then ++*gen.
+__global__ void __launch_bounds__(1024) record_kernel(const long long* __restrict__ fit, int s, int* gen,
+                                                      long long* traj, int* best) {
+    long long v;
+    int e;
+    block_argmin(fit, s, &v, &e);
+    if (threadIdx.x == 0) {
+        const int gg = *gen;
+        if (traj) traj[gg] = v;
+        *best = e;
+        *gen = gg + 1;
+    }
+}
+
+}  // namespace
+
+int gapa_ga_check_limits(gapa_ctx* c, int n, int k, int s) {
+    const size_t need = row_smem_bytes(n, k);
+    if (need > c->ga_smem_max)
+        return gapa_fail(GAPA_ERR_INVALID_ARG,
+                         "genetic operators need n/8 + 5k bytes of shared memory per row (n=%d, k=%d: %zu > %zu)",
+                         n, k, need, c->ga_smem_max);
+    if ((long long)s * (long long)k >= (1LL << 31))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "s*k must be below 2^31");
+    return GAPA_OK;
+}
+
+int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st) {
+    if (p.s <= 0) return GAPA_OK;
+    ProfileScope prof(c, st, 1, 0);
+    init_kernel<<<p.s, kGaBlock, row_smem_bytes(p.n, p.k), st>>>(p, pop);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,
+                          int32_t* pop_out, int64_t* fit_out, cudaStream_t st) {
+    ProfileScope prof(c, st, 1, 0);
+    offspring_kernel<<<p.s, kGaBlock, row_smem_bytes(p.n, p.k), st>>>(
+        p, pop_in, reinterpret_cast<const long long*>(fit_in), pop_out, reinterpret_cast<long long*>(fit_out),
+        c->status);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_launch_record(gapa_ctx* c, const int64_t* fit, int s, int* gen, int64_t* traj, int* best,
+                       cudaStream_t st) {
+    record_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const long long*>(fit), s, gen,
+                                      reinterpret_cast<long long*>(traj), best);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_ga_kernels_init(gapa_ctx* c) {
+    int rc = gapa_set_smem_limit((const void*)init_kernel, c->smem_optin, &c->ga_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)offspring_kernel, c->smem_optin, &c->ga_smem_max);
+    return rc;
+}

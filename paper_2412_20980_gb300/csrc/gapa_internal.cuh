@@ -1,0 +1,163 @@
+// Internal declarations of libgapa.so (CUDA path).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gapa.h"
+
+// ---------------------------------------------------------------------------
+// Device status word: kernels OR these bits in; gapa_sync() reports them.
+// ---------------------------------------------------------------------------
+enum : int {
+    GAPA_DEV_BAD_GENE = 1,   // a gene outside [0, n)
+    GAPA_DEV_TIMEOUT = 2,    // a bounded wait ran out
+    GAPA_DEV_CAPACITY = 4,   // a work list overflowed its bound
+};
+
+// Philox tags of the counter's last word (tag << 24 | round).
+enum : uint32_t {
+    TAG_INIT = 1,
+    TAG_SEL = 2,
+    TAG_XOVER = 3,
+    TAG_MUT = 4,
+    TAG_MUTVAL = 5,
+    TAG_REPAIR = 6,
+};
+
+constexpr int kRepairRounds = 32;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of the
+// two-multiplier bijection with a Weyl-sequence key schedule; returns output
+// word 0 only.
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        const uint32_t hi0 = __umulhi(m0, c0), lo0 = m0 * c0;
+        const uint32_t hi1 = __umulhi(m1, c2), lo1 = m1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+struct RngKey {
+    uint32_t lo, hi;
+};
+
+__device__ __forceinline__ uint32_t gapa_draw(RngKey key, uint32_t j, uint32_t i, uint32_t g, uint32_t tag,
+                                              uint32_t round) {
+    return philox_word0(j, i, g, (tag << 24) | round, key.lo, key.hi);
+}
+
+// Uniform integer in [0, n): multiply-high of a 32-bit word by n.
+__device__ __forceinline__ int uniform_below(uint32_t x, int n) { return (int)__umulhi(x, (uint32_t)n); }
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct DeviceGraph {
+    int n = 0;
+    long long nnz = 0;        // arcs = 2E
+    int num_edges = 0;        // E (undirected)
+    int* row_ptr = nullptr;   // [n+1]
+    int* col = nullptr;       // [nnz], rows sorted
+    int2* edges = nullptr;    // [E] (u, v) with u < v, CSR order
+    int* probe = nullptr;     // [kProbe] node ids of highest degree, descending
+    int max_degree = 0;
+};
+
+constexpr int kProbe = 8;
+
+struct gapa_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;      // borrowed
+    cudaStream_t own_stream = nullptr;  // owned, used for capture in gapa_run
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    int num_sms = 0;
+    size_t smem_optin = 0;  // max shared memory per block (opt-in)
+    size_t fit_smem_max = 0;  // max dynamic shared memory of the shared-memory fitness kernel
+    size_t ga_smem_max = 0;   // max dynamic shared memory of the operator kernels
+    DeviceGraph g;
+    int* status = nullptr;  // device status word
+    // scratch owned by the context
+    int* labels = nullptr;  // global label scratch for graphs too large for shared memory
+    size_t labels_cap = 0;  // ints
+    int32_t* stage_pop[2] = {nullptr, nullptr};
+    int64_t* stage_fit[2] = {nullptr, nullptr};
+    size_t stage_pop_cap = 0, stage_fit_cap = 0;  // elements
+    int* run_gen = nullptr;
+    int* run_best = nullptr;
+    int64_t* run_traj = nullptr;
+    size_t run_traj_cap = 0;
+    int fitness_variant = 0;  // 0 = auto
+    // profiling (gapa_profile_begin/end): event pairs around launches
+    bool profiling = false;
+    bool capturing = false;
+    struct Timed {
+        cudaEvent_t a, b;
+        int kind;  // 0 = fitness, 1 = operators
+        int evals;
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+// Event pair around one launch when profiling is on (no-op otherwise).
+struct ProfileScope {
+    gapa_ctx* c;
+    cudaStream_t st;
+    int kind, evals;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfileScope(gapa_ctx* c_, cudaStream_t st_, int kind_, int evals_);
+    ~ProfileScope();
+};
+
+// Error reporting (thread-local message).
+int gapa_fail(int code, const char* fmt, ...);
+int gapa_cuda_fail(cudaError_t e, const char* what);
+#define GAPA_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t _e = (call);                          \
+        if (_e != cudaSuccess) return gapa_cuda_fail(_e, #call); \
+    } while (0)
+
+// Raise a kernel's dynamic shared memory limit to the opt-in maximum minus its
+// static shared memory; returns that limit through *max_dyn.
+int gapa_set_smem_limit(const void* kernel, size_t optin, size_t* max_dyn);
+
+// Ensure a device buffer holds at least `count` elements of size `elem`.
+int gapa_reserve(void** ptr, size_t* cap, size_t count, size_t elem);
+
+// ---------------------------------------------------------------------------
+// Launchers (fitness.cu, ga.cu)
+// ---------------------------------------------------------------------------
+struct GaParams {
+    int n, k, s, t;
+    uint32_t pc_thr, pm_thr;
+    RngKey key;
+    uint32_t flags;
+    int g;               // generation when g_ptr is null
+    const int* g_ptr;    // device-resident generation counter (CUDA-graph replay)
+};
+
+int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st);
+int gapa_fitness_prepare(gapa_ctx* c, int s);  // allocate scratch before capture
+int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);
+int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,
+                          int32_t* pop_out, int64_t* fit_out, cudaStream_t st);
+int gapa_launch_record(gapa_ctx* c, const int64_t* fit, int s, int* gen, int64_t* traj, int* best,
+                       cudaStream_t st);
+int gapa_ga_check_limits(gapa_ctx* c, int n, int k, int s);
+int gapa_kernels_init(gapa_ctx* c);

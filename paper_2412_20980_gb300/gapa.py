@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libgapa.so (argument marshalling only).
+
+Every step of the path runs in the library's CUDA kernels; this module checks
+dtypes/devices, passes raw pointers and the current torch stream, and turns
+status codes into exceptions.  There is no fallback: if libgapa.so is missing
+or cannot be loaded, importing the library functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgapa.so")
+
+GAPA_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG",
+    -2: "INVALID_GRAPH",
+    -3: "OOM",
+    -4: "CUDA",
+    -5: "TIMEOUT",
+    -6: "STATE",
+    -7: "DEVICE",
+}
+WHERE_HOST, WHERE_DEVICE = 0, 1
+FLAG_ROWWISE = 1
+
+# every entry point declared in include/gapa.h
+EXPORTS = [
+    "gapa_create", "gapa_destroy", "gapa_set_stream", "gapa_graph_upload", "gapa_pop_init",
+    "gapa_fitness", "gapa_fitness_host", "gapa_generation", "gapa_generation_host", "gapa_run",
+    "gapa_sync", "gapa_last_error", "gapa_version", "gapa_profile_begin", "gapa_profile_end",
+]
+
+
+class GapaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Profile(ctypes.Structure):
+    """Mirror of gapa_profile."""
+
+    _fields_ = [
+        ("fitness_ms", ctypes.c_double),
+        ("operators_ms", ctypes.c_double),
+        ("fitness_launches", ctypes.c_int64),
+        ("operator_launches", ctypes.c_int64),
+        ("evals", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Config(ctypes.Structure):
+    """Mirror of gapa_config."""
+
+    _fields_ = [
+        ("k", ctypes.c_int32),
+        ("pop", ctypes.c_int32),
+        ("gens", ctypes.c_int32),
+        ("tourn", ctypes.c_int32),
+        ("elite", ctypes.c_int32),
+        ("pc_thr", ctypes.c_uint32),
+        ("pm_thr", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+def threshold(p: float) -> int:
+    """floor(p * 2^32), clamped to 2^32 - 1 (a mask bit is set when the draw is below it)."""
+    return min(int(p * 4294967296.0), 0xFFFFFFFF)
+
+
+def make_config(k: int, pop: int, gens: int = 0, tourn: int = 2, pc: float = 0.8, pm: float = 0.02,
+                seed: int = 0, flags: int = 0, elite: int = 1) -> Config:
+    return Config(k, pop, gens, tourn, elite, threshold(pc), threshold(pm), seed & (2**64 - 1), flags)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libgapa.so (raises OSError when it is missing: build it first)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise OSError(f"libgapa.so not found at {p}; run paper_2412_20980_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        V, I32, I64, U = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+        cfgp = ctypes.POINTER(Config)
+        sig = {
+            "gapa_create": ([ctypes.POINTER(V), U, V], U),
+            "gapa_destroy": ([V], None),
+            "gapa_set_stream": ([V, V], U),
+            "gapa_graph_upload": ([V, I32, I64, V, V, U], U),
+            "gapa_pop_init": ([V, cfgp, V], U),
+            "gapa_fitness": ([V, V, I32, I32, V], U),
+            "gapa_fitness_host": ([V, V, I32, I32, V], U),
+            "gapa_generation": ([V, cfgp, I32, V, V, V, V], U),
+            "gapa_generation_host": ([V, cfgp, I32, V, V, V, V], U),
+            "gapa_run": ([V, cfgp, V, V, V, V], U),
+            "gapa_sync": ([V], U),
+            "gapa_profile_begin": ([V], U),
+            "gapa_profile_end": ([V, ctypes.POINTER(Profile)], U),
+            "gapa_last_error": ([], ctypes.c_char_p),
+            "gapa_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().gapa_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != GAPA_OK:
+        raise GapaError(rc, last_error())
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _dev_ptr(t, dtype, name: str, device_index: int):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda or t.device.index != device_index:
+        raise ValueError(f"{name} must live on cuda:{device_index}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """One GPU context holding one uploaded graph (wraps gapa_ctx)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(self.lib.gapa_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)))
+        self.handle = h
+        self.n = 0
+        self.num_edges = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gapa_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(self.lib.gapa_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
+
+    # -- graph -------------------------------------------------------------
+    def graph_upload(self, row_ptr, col):
+        """Upload a symmetric CSR from numpy (host) or torch (host or this device) int32 arrays."""
+        torch = _torch()
+        if isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda:
+            rp = _dev_ptr(row_ptr, torch.int32, "row_ptr", self.device)
+            cp = _dev_ptr(col, torch.int32, "col", self.device)
+            n, nnz, where = row_ptr.numel() - 1, col.numel(), WHERE_DEVICE
+            keep = (row_ptr, col)
+        else:
+            rpa = np.ascontiguousarray(row_ptr.numpy() if isinstance(row_ptr, torch.Tensor) else row_ptr, dtype=np.int32)
+            ca = np.ascontiguousarray(col.numpy() if isinstance(col, torch.Tensor) else col, dtype=np.int32)
+            rp, cp = _host_ptr(rpa), _host_ptr(ca)
+            n, nnz, where = rpa.shape[0] - 1, ca.shape[0], WHERE_HOST
+            keep = (rpa, ca)
+        _check(self.lib.gapa_graph_upload(self.handle, n, nnz, rp, cp, where))
+        del keep
+        self.n = n
+        self.num_edges = nnz // 2
+
+    # -- operators -----------------------------------------------------------
+    def pop_init(self, cfg: Config, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((cfg.pop, cfg.k), dtype=torch.int32, device=f"cuda:{self.device}")
+        _check(self.lib.gapa_pop_init(self.handle, ctypes.byref(cfg), _dev_ptr(out, torch.int32, "pop", self.device)))
+        return out
+
+    def fitness(self, pop, out=None):
+        torch = _torch()
+        if pop.dim() != 2:
+            raise ValueError("pop must be 2-D [s, k]")
+        s, k = pop.shape
+        if out is None:
+            out = torch.empty(s, dtype=torch.int64, device=f"cuda:{self.device}")
+        _check(self.lib.gapa_fitness(self.handle, _dev_ptr(pop, torch.int32, "pop", self.device), s, k,
+                                     _dev_ptr(out, torch.int64, "fit", self.device)))
+        return out
+
+    def fitness_host(self, pop: np.ndarray, out: np.ndarray | None = None) -> np.ndarray:
+        pop = np.ascontiguousarray(pop, dtype=np.int32)
+        s, k = pop.shape
+        if out is None:
+            out = np.empty(s, dtype=np.int64)
+        _check(self.lib.gapa_fitness_host(self.handle, _host_ptr(pop), s, k, _host_ptr(out)))
+        return out
+
+    def generation(self, cfg: Config, g: int, pop_in, fit_in, pop_out=None, fit_out=None):
+        torch = _torch()
+        if pop_out is None:
+            pop_out = torch.empty_like(pop_in)
+        if fit_out is None:
+            fit_out = torch.empty_like(fit_in)
+        _check(self.lib.gapa_generation(self.handle, ctypes.byref(cfg), g,
+                                        _dev_ptr(pop_in, torch.int32, "pop_in", self.device),
+                                        _dev_ptr(fit_in, torch.int64, "fit_in", self.device),
+                                        _dev_ptr(pop_out, torch.int32, "pop_out", self.device),
+                                        _dev_ptr(fit_out, torch.int64, "fit_out", self.device)))
+        return pop_out, fit_out
+
+    def generation_host(self, cfg: Config, g: int, pop_in: np.ndarray, fit_in: np.ndarray,
+                        pop_out: np.ndarray | None = None, fit_out: np.ndarray | None = None):
+        pop_in = np.ascontiguousarray(pop_in, dtype=np.int32)
+        fit_in = np.ascontiguousarray(fit_in, dtype=np.int64)
+        if pop_out is None:
+            pop_out = np.empty_like(pop_in)
+        if fit_out is None:
+            fit_out = np.empty_like(fit_in)
+        _check(self.lib.gapa_generation_host(self.handle, ctypes.byref(cfg), g, _host_ptr(pop_in), _host_ptr(fit_in),
+                                             _host_ptr(pop_out), _host_ptr(fit_out)))
+        return pop_out, fit_out
+
+    def run(self, cfg: Config, want_pop: bool = False) -> dict:
+        torch = _torch()
+        best = np.zeros(max(cfg.k, 1), dtype=np.int32)
+        best_fit = np.zeros(1, dtype=np.int64)
+        traj = np.zeros(cfg.gens + 1, dtype=np.int64)
+        pop = torch.empty((cfg.pop, cfg.k), dtype=torch.int32, device=f"cuda:{self.device}") if want_pop else None
+        _check(self.lib.gapa_run(self.handle, ctypes.byref(cfg), _host_ptr(best), _host_ptr(best_fit),
+                                 _host_ptr(traj),
+                                 _dev_ptr(pop, torch.int32, "pop", self.device) if want_pop else None))
+        return {"best_set": best[: cfg.k].copy(), "best_fit": int(best_fit[0]), "traj": traj, "pop": pop}
+
+    def sync(self):
+        _check(self.lib.gapa_sync(self.handle))
+
+    def profile_begin(self):
+        _check(self.lib.gapa_profile_begin(self.handle))
+
+    def profile_end(self) -> dict:
+        prof = Profile()
+        _check(self.lib.gapa_profile_end(self.handle, ctypes.byref(prof)))
+        return prof.as_dict()

@@ -1,0 +1,187 @@
+"""GPU fitness parity: libgapa.so's batched pairwise connectivity equals the oracle bit-exactly.
+
+Fitness is integer (int64), so the bar is exact equality, element by element.
+Covers hand-worked values, exhaustive subsets of tiny graphs, the benchmark
+graphs (BA/HK n = 20000, k = 1000, s = 1024), graphs too large for shared
+memory (global labels), and degenerate sets and graphs.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pc_worked_examples.json")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_2412_20980_gb300 import Context
+    from paper_2412_20980_gb300 import build as b
+
+    b.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def gpu_fit(ctx, g, pop):
+    import torch
+
+    ctx.graph_upload(g.row_ptr, g.col)
+    p = torch.from_numpy(np.ascontiguousarray(pop, dtype=np.int32)).cuda()
+    f = ctx.fitness(p)
+    ctx.sync()
+    return f.cpu().numpy()
+
+
+def test_worked_examples(ctx):
+    data = json.load(open(GOLDEN))
+    for case in data["cases"]:
+        e = np.array(case["edges"], dtype=np.int64).reshape(-1, 2)
+        g = synth.csr_from_edges(case["n"], e[:, 0], e[:, 1])
+        for s in case["sets"]:
+            got = gpu_fit(ctx, g, np.array([s["del"]], dtype=np.int32).reshape(1, -1))
+            assert got[0] == s["pc"], (case["name"], s)
+
+
+@pytest.mark.parametrize("seed,n,m", [(1, 12, 16), (3, 11, 25), (5, 10, 9)])
+def test_exhaustive_subsets(ctx, seed, n, m):
+    g = synth.er_graph(n, m, seed)
+    for k in range(n + 1):
+        pop = np.array(list(itertools.combinations(range(n), k)), dtype=np.int32).reshape(-1, k)
+        assert np.array_equal(gpu_fit(ctx, g, pop), oracle.fitness(g.row_ptr, g.col, pop)), k
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.ba_graph(20000, 4, 1),
+    lambda: synth.hk_graph(20000, 4, 0.3, 1),
+])
+def test_benchmark_graphs_full_population(ctx, make):
+    g = make()
+    pop = synth.random_deletion_sets(g.n, 1000, 1024, 0)
+    want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
+    assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
+@pytest.mark.parametrize("make,k,s", [
+    (lambda: synth.ba_graph(1000, 3, 1), 50, 100),
+    (lambda: synth.relabel(synth.ba_graph(5000, 2, 4), 9), 500, 64),
+    (lambda: synth.rmat_graph(12, 30000, seed=3, chunk=1 << 15), 200, 48),
+    (lambda: synth.named_graph("grid", 40000), 4000, 16),
+])
+def test_various_graphs(ctx, make, k, s):
+    g = make()
+    pop = synth.random_deletion_sets(g.n, k, s, 1)
+    assert np.array_equal(gpu_fit(ctx, g, pop), oracle.fitness(g.row_ptr, g.col, pop))
+
+
+def test_global_label_path_100k(ctx):
+    """n = 100000 needs 400 KB of labels: the global-memory variant."""
+    g = synth.ba_graph(100000, 3, 1)
+    pop = synth.random_deletion_sets(g.n, 2000, 40, 2)
+    want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
+    assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
+def test_global_label_path_rmat(ctx):
+    g = synth.rmat_graph(17, 1 << 20, seed=1, chunk=1 << 20)
+    pop = synth.random_deletion_sets(g.n, 1300, 24, 5)
+    want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
+    assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
+def test_adversarial_graphs(ctx):
+    path = synth.named_graph("path", 30000)  # deep union-find chains
+    pop = np.stack([np.array([], dtype=np.int32).reshape(0)] * 1).reshape(1, 0)
+    assert gpu_fit(ctx, path, pop)[0] == 30000 * 29999 // 2
+    pop = synth.random_deletion_sets(path.n, 100, 8, 3)
+    assert np.array_equal(gpu_fit(ctx, path, pop), oracle.fitness(path.row_ptr, path.col, pop))
+    star = synth.named_graph("star", 20001)  # one hot root
+    pop = np.array([[0], [1], [20000]], dtype=np.int32)
+    assert list(gpu_fit(ctx, star, pop)) == [0, 20000 * 19999 // 2, 20000 * 19999 // 2]
+    empty = synth.named_graph("empty", 5000)  # all isolated
+    assert gpu_fit(ctx, empty, np.zeros((3, 0), dtype=np.int32)).tolist() == [0, 0, 0]
+    # all neighbours of the hub deleted
+    ba = synth.ba_graph(3000, 2, 7)
+    hub = int(np.argmax(ba.degrees()))
+    nb = ba.col[ba.row_ptr[hub]:ba.row_ptr[hub + 1]]
+    pop = nb.reshape(1, -1).astype(np.int32)
+    assert np.array_equal(gpu_fit(ctx, ba, pop), oracle.fitness(ba.row_ptr, ba.col, pop))
+
+
+def test_degenerate_sets(ctx):
+    g = synth.ba_graph(2000, 3, 2)
+    n = g.n
+    # k = 0, k = n - 1, k = n, repeated genes
+    assert gpu_fit(ctx, g, np.zeros((2, 0), dtype=np.int32)).tolist() == [n * (n - 1) // 2] * 2
+    allbut = np.arange(1, n, dtype=np.int32).reshape(1, -1)
+    assert gpu_fit(ctx, g, allbut).tolist() == [0]
+    assert gpu_fit(ctx, g, np.arange(n, dtype=np.int32).reshape(1, -1)).tolist() == [0]
+    rep = np.array([[5, 5, 5, 9], [9, 5, 9, 5]], dtype=np.int32)
+    want = oracle.fitness(g.row_ptr, g.col, rep)
+    assert np.array_equal(gpu_fit(ctx, g, rep), want) and want[0] == want[1]
+
+
+def test_empty_population(ctx):
+    import torch
+
+    g = synth.ba_graph(500, 2, 1)
+    ctx.graph_upload(g.row_ptr, g.col)
+    f = ctx.fitness(torch.zeros((0, 10), dtype=torch.int32, device="cuda"))
+    ctx.sync()
+    assert f.numel() == 0
+
+
+def test_bad_gene_reported_at_sync(ctx):
+    import torch
+
+    from paper_2412_20980_gb300 import GapaError
+
+    g = synth.ba_graph(500, 2, 1)
+    ctx.graph_upload(g.row_ptr, g.col)
+    pop = torch.tensor([[1, 2, 500]], dtype=torch.int32, device="cuda")
+    ctx.fitness(pop)
+    with pytest.raises(GapaError) as ei:
+        ctx.sync()
+    assert ei.value.code == -7
+    # the context stays usable
+    ok = ctx.fitness(torch.tensor([[1, 2, 3]], dtype=torch.int32, device="cuda"))
+    ctx.sync()
+    assert ok.item() == oracle.fitness(g.row_ptr, g.col, np.array([[1, 2, 3]]))[0]
+
+
+def test_host_entry_point_matches_device(ctx):
+    g = synth.hk_graph(3000, 3, 0.3, 4)
+    pop = synth.random_deletion_sets(g.n, 150, 33, 8)
+    ctx.graph_upload(g.row_ptr, g.col)
+    host = ctx.fitness_host(pop)
+    assert np.array_equal(host, gpu_fit(ctx, g, pop))
+    assert np.array_equal(host, oracle.fitness(g.row_ptr, g.col, pop))
+
+
+def test_invalid_graphs_rejected(ctx):
+    from paper_2412_20980_gb300 import GapaError
+
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    for col, code in [(np.array([1, 1], dtype=np.int32), -2),  # fine shape but... 0->1, 1->1 self loop
+                      (np.array([0, 0], dtype=np.int32), -2),
+                      (np.array([1, 5], dtype=np.int32), -2)]:
+        with pytest.raises(GapaError) as ei:
+            ctx.graph_upload(rp, col)
+        assert ei.value.code == code
+    # asymmetric: 0->1, 1->2, 2->? (row 2 empty)
+    with pytest.raises(GapaError):
+        ctx.graph_upload(np.array([0, 1, 2, 2], dtype=np.int32), np.array([1, 2], dtype=np.int32))
+    # repeated arc
+    with pytest.raises(GapaError):
+        ctx.graph_upload(np.array([0, 2, 4], dtype=np.int32), np.array([1, 1, 0, 0], dtype=np.int32))
