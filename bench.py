@@ -298,7 +298,7 @@ def run_gapa(args):
 
     # --- end to end through the C ABI with pinned host buffers ---
     e2e = None
-    if rank == 0 or ws > 1:
+    if not args.no_e2e:
         hp, pinned = [], []
         for c, st in zip(ctxs, state):
             ts = [st[0].cpu().pin_memory(), st[1].cpu().pin_memory(),
@@ -352,6 +352,7 @@ def main():
     ap.add_argument("--impl", choices=["gapa", "reference"], default="gapa")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gapa":
         log("warm-up raised to 3 steps")

@@ -499,6 +499,14 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
     return GAPA_OK;
 }
 
+int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_SAMPLED)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown fitness kernel %d", variant);
+    c->fitness_variant = variant;
+    return GAPA_OK;
+}
+
 int gapa_profile_begin(gapa_ctx* c) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
     c->profiling = true;

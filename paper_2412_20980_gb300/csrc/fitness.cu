@@ -31,6 +31,18 @@ __device__ __forceinline__ int uf_find(volatile int* lab, int x) {
     }
 }
 
+// Root of x by a read-only walk.  Used once no hooking is left: every write
+// then is an owner storing its node's final root, so no walk can leave a
+// stale (non-root) ancestor behind, which path halving could.
+__device__ __forceinline__ int uf_root(volatile int* lab, int x) {
+    int p = lab[x];
+    while (p != x) {
+        x = p;
+        p = lab[x];
+    }
+    return x;
+}
+
 // Union of the trees of live nodes a and b: hook the larger root under the
 // smaller with a CAS on the root's slot; retry from the new parent on a race.
 __device__ __forceinline__ void uf_unite(volatile int* lab, int a, int b) {
@@ -67,16 +79,13 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long* red) {
     return tot;  // valid in thread 0
 }
 
-// The whole per-member pipeline on a label array `lab` of n ints that only
-// this CTA touches.
-__device__ __forceinline__ void member_pc(volatile int* lab, int n, int num_edges, const int2* __restrict__ edges,
-                                          const int* __restrict__ genes, int k, long long* out, int* status,
-                                          long long* red) {
+// Labels: every node its own root, then the perturbation P^(A, p) of Eq. 13
+// marks the deleted nodes.
+__device__ __forceinline__ void init_labels(volatile int* lab, int n, const int* __restrict__ genes, int k,
+                                            int* status) {
     const int tid = threadIdx.x, T = blockDim.x;
-    // labels: every node its own root
     for (int v = tid; v < n; v += T) lab[v] = v;
     __syncthreads();
-    // perturbation P^(A, p): mark the deleted nodes
     for (int j = tid; j < k; j += T) {
         const int d = __ldg(&genes[j]);
         if ((unsigned)d < (unsigned)n)
@@ -85,7 +94,11 @@ __device__ __forceinline__ void member_pc(volatile int* lab, int n, int num_edge
             atomicOr(status, GAPA_DEV_BAD_GENE);
     }
     __syncthreads();
-    // hooking over every undirected edge once, two edges per 16-byte load
+}
+
+// Hooking, plain: every undirected edge once, two edges per 16-byte load.
+__device__ __forceinline__ void hook_all_edges(volatile int* lab, int num_edges, const int2* __restrict__ edges) {
+    const int tid = threadIdx.x, T = blockDim.x;
     const int pairs = num_edges >> 1;
     const int4* e4 = reinterpret_cast<const int4*>(edges);
     int q = tid;
@@ -103,10 +116,63 @@ __device__ __forceinline__ void member_pc(volatile int* lab, int n, int num_edge
         edge_op(lab, last.x, last.y);
     }
     __syncthreads();
+}
+
+// Hooking, sampled: (1) every live node is joined to its first kSample live
+// neighbours in CSR order; (2) the tree of the first live probe node (the
+// highest-degree nodes) is taken as the giant tree G; (3) every live node not
+// in G joins all its live neighbours.  Exact: an edge {v,w} is either joined
+// in (3) from an endpoint outside G, or both endpoints were seen inside G.
+constexpr int kSample = 2;
+
+__device__ __forceinline__ void hook_sampled(volatile int* lab, int n, const int* __restrict__ row_ptr,
+                                             const int* __restrict__ col, const int* __restrict__ probe,
+                                             int* sh_root) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int v = tid; v < n; v += T) {
+        if (lab[v] == kDead) continue;
+        const int beg = __ldg(&row_ptr[v]), end = __ldg(&row_ptr[v + 1]);
+        int linked = 0;
+        for (int e = beg; e < end && linked < kSample; ++e) {
+            const int w = __ldg(&col[e]);
+            if (lab[w] == kDead) continue;
+            uf_unite(lab, v, w);
+            ++linked;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int r = -1;
+        for (int q = 0; q < kProbe && r < 0; ++q) {
+            const int p = __ldg(&probe[q]);
+            if (p < n && lab[p] != kDead) r = uf_root(lab, p);
+        }
+        *sh_root = r;
+    }
+    __syncthreads();
+    const int giant = *sh_root;
+    for (int v = tid; v < n; v += T) {
+        if (lab[v] == kDead) continue;
+        if (giant >= 0) {
+            const int r = uf_find(lab, v);
+            if (r == giant || r == uf_find(lab, giant)) continue;
+        }
+        const int beg = __ldg(&row_ptr[v]), end = __ldg(&row_ptr[v + 1]);
+        for (int e = beg; e < end; ++e) {
+            const int w = __ldg(&col[e]);
+            if (lab[w] != kDead) uf_unite(lab, v, w);
+        }
+    }
+    __syncthreads();
+}
+
+// Component sizes and the int64 sum of C(size, 2) (PC(G) of Table "Whole").
+__device__ __forceinline__ void count_pc(volatile int* lab, int n, long long* out, long long* red) {
+    const int tid = threadIdx.x, T = blockDim.x;
     // flatten: every live node points at its root
     for (int v = tid; v < n; v += T) {
         const int l = lab[v];
-        if (l != kDead && l != v) lab[v] = uf_find(lab, v);
+        if (l != kDead && l != v) lab[v] = uf_root(lab, l);
     }
     __syncthreads();
     // roots become counters: -1 for the root itself
@@ -139,22 +205,46 @@ __device__ __forceinline__ void member_pc(volatile int* lab, int n, int num_edge
     if (tid == 0) *out = tot;
 }
 
-__global__ void __launch_bounds__(1024) cc_smem_kernel(int n, int num_edges, const int2* __restrict__ edges,
-                                                       const int* __restrict__ pop, int k,
+struct GraphArgs {
+    int n, num_edges;
+    const int2* edges;
+    const int* row_ptr;
+    const int* col;
+    const int* probe;
+};
+
+template <bool kSampled>
+__device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k,
+                                          long long* out, int* status, long long* red, int* sh_root) {
+    init_labels(lab, g.n, genes, k, status);
+    if (kSampled)
+        hook_sampled(lab, g.n, g.row_ptr, g.col, g.probe, sh_root);
+    else
+        hook_all_edges(lab, g.num_edges, g.edges);
+    count_pc(lab, g.n, out, red);
+}
+
+// One CTA per member, labels in shared memory.
+template <bool kSampled>
+__global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* __restrict__ pop, int k,
                                                        long long* __restrict__ fit, int* status) {
     extern __shared__ int smem_lab[];
     __shared__ long long red[32];
+    __shared__ int sh_root;
     const int i = blockIdx.x;
-    member_pc(smem_lab, n, num_edges, edges, pop + (size_t)i * k, k, &fit[i], status, red);
+    member_pc<kSampled>(smem_lab, g, pop + (size_t)i * k, k, &fit[i], status, red, &sh_root);
 }
 
-__global__ void __launch_bounds__(1024) cc_global_kernel(int n, int num_edges, const int2* __restrict__ edges,
-                                                         const int* __restrict__ pop, int k,
-                                                         long long* __restrict__ fit, int* status,
-                                                         int* labels, int member_base) {
+// One CTA per member, labels in a global scratch slice per CTA.
+template <bool kSampled>
+__global__ void __launch_bounds__(1024) cc_global_kernel(GraphArgs g, const int* __restrict__ pop, int k,
+                                                         long long* __restrict__ fit, int* status, int* labels,
+                                                         int member_base) {
     __shared__ long long red[32];
+    __shared__ int sh_root;
     const int i = member_base + blockIdx.x;
-    member_pc(labels + (size_t)blockIdx.x * n, n, num_edges, edges, pop + (size_t)i * k, k, &fit[i], status, red);
+    member_pc<kSampled>(labels + (size_t)blockIdx.x * g.n, g, pop + (size_t)i * k, k, &fit[i], status, red,
+                        &sh_root);
 }
 
 
@@ -181,9 +271,14 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     const int n = c->g.n;
     const size_t lab_bytes = (size_t)n * 4;
     long long* f = reinterpret_cast<long long*>(fit);
+    const GraphArgs ga{n, c->g.num_edges, c->g.edges, c->g.row_ptr, c->g.col, c->g.probe};
+    const bool sampled = c->fitness_variant != GAPA_FITNESS_EDGES;
     if (lab_bytes <= c->fit_smem_max) {
         const int block = smem_block_for(n);
-        cc_smem_kernel<<<s, block, lab_bytes, st>>>(n, c->g.num_edges, c->g.edges, pop, k, f, c->status);
+        if (sampled)
+            cc_smem_kernel<true><<<s, block, lab_bytes, st>>>(ga, pop, k, f, c->status);
+        else
+            cc_smem_kernel<false><<<s, block, lab_bytes, st>>>(ga, pop, k, f, c->status);
         GAPA_CUDA(cudaGetLastError());
         return GAPA_OK;
     }
@@ -192,13 +287,17 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     const int wave = (int)(c->labels_cap / (size_t)n);
     for (int base = 0; base < s; base += wave) {
         const int cnt = s - base < wave ? s - base : wave;
-        cc_global_kernel<<<cnt, 1024, 0, st>>>(n, c->g.num_edges, c->g.edges, pop, k, f, c->status, c->labels,
-                                                base);
+        if (sampled)
+            cc_global_kernel<true><<<cnt, 1024, 0, st>>>(ga, pop, k, f, c->status, c->labels, base);
+        else
+            cc_global_kernel<false><<<cnt, 1024, 0, st>>>(ga, pop, k, f, c->status, c->labels, base);
         GAPA_CUDA(cudaGetLastError());
     }
     return GAPA_OK;
 }
 
 int gapa_fitness_kernels_init(gapa_ctx* c) {
-    return gapa_set_smem_limit((const void*)cc_smem_kernel, c->smem_optin, &c->fit_smem_max);
+    int rc = gapa_set_smem_limit((const void*)cc_smem_kernel<true>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<false>, c->smem_optin, &c->fit_smem_max);
+    return rc;
 }

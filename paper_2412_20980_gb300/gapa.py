@@ -34,7 +34,9 @@ EXPORTS = [
     "gapa_create", "gapa_destroy", "gapa_set_stream", "gapa_graph_upload", "gapa_pop_init",
     "gapa_fitness", "gapa_fitness_host", "gapa_generation", "gapa_generation_host", "gapa_run",
     "gapa_sync", "gapa_last_error", "gapa_version", "gapa_profile_begin", "gapa_profile_end",
+    "gapa_set_fitness_kernel",
 ]
+FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED = 0, 1, 2
 
 
 class GapaError(RuntimeError):
@@ -113,6 +115,7 @@ def load(path: str | None = None):
             "gapa_run": ([V, cfgp, V, V, V, V], U),
             "gapa_sync": ([V], U),
             "gapa_profile_begin": ([V], U),
+            "gapa_set_fitness_kernel": ([V, U], U),
             "gapa_profile_end": ([V, ctypes.POINTER(Profile)], U),
             "gapa_last_error": ([], ctypes.c_char_p),
             "gapa_version": ([], ctypes.c_char_p),
@@ -279,6 +282,9 @@ class Context:
 
     def sync(self):
         _check(self.lib.gapa_sync(self.handle))
+
+    def set_fitness_kernel(self, variant: int):
+        _check(self.lib.gapa_set_fitness_kernel(self.handle, variant))
 
     def profile_begin(self):
         _check(self.lib.gapa_profile_begin(self.handle))

@@ -20,15 +20,17 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pc_worked_examples.json")
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["sampled", "edges"])
+def ctx(request):
     import torch
 
     from paper_2412_20980_gb300 import Context
     from paper_2412_20980_gb300 import build as b
+    from paper_2412_20980_gb300.gapa import FITNESS_EDGES, FITNESS_SAMPLED
 
     b.build()
     c = Context(0)
+    c.set_fitness_kernel(FITNESS_SAMPLED if request.param == "sampled" else FITNESS_EDGES)
     yield c
     torch.cuda.synchronize()
     c.close()
@@ -58,7 +60,8 @@ def test_worked_examples(ctx):
 def test_exhaustive_subsets(ctx, seed, n, m):
     g = synth.er_graph(n, m, seed)
     for k in range(n + 1):
-        pop = np.array(list(itertools.combinations(range(n), k)), dtype=np.int32).reshape(-1, k)
+        combos = list(itertools.combinations(range(n), k))
+        pop = np.array(combos, dtype=np.int32).reshape(len(combos), k)
         assert np.array_equal(gpu_fit(ctx, g, pop), oracle.fitness(g.row_ptr, g.col, pop)), k
 
 
@@ -102,7 +105,7 @@ def test_global_label_path_rmat(ctx):
 
 def test_adversarial_graphs(ctx):
     path = synth.named_graph("path", 30000)  # deep union-find chains
-    pop = np.stack([np.array([], dtype=np.int32).reshape(0)] * 1).reshape(1, 0)
+    pop = np.zeros((1, 0), dtype=np.int32)
     assert gpu_fit(ctx, path, pop)[0] == 30000 * 29999 // 2
     pop = synth.random_deletion_sets(path.n, 100, 8, 3)
     assert np.array_equal(gpu_fit(ctx, path, pop), oracle.fitness(path.row_ptr, path.col, pop))
