@@ -140,14 +140,17 @@ int gapa_generation_host(gapa_ctx* ctx, const gapa_config* cfg, int32_t g, const
 int gapa_run(gapa_ctx* ctx, const gapa_config* cfg, int32_t* best_set_host, int64_t* best_fit,
              int64_t* traj_best_fit, int32_t* final_pop_dev);
 
-/* Fitness kernel selection (both are exact and give identical results):
- * SAMPLED joins every live node to its first two live neighbours, takes the
- * tree of the highest-degree live node as the giant tree and lets only nodes
- * outside it scan their whole adjacency; EDGES runs union-find over every
- * undirected edge.  AUTO (the default) is SAMPLED. */
+/* Fitness kernel selection (all are exact and give identical results):
+ * TREE starts every member from a BFS spanning forest of G (numbered so that
+ * parents precede children), cuts it at the deleted nodes and then joins the
+ * pieces along the non-tree edges; SAMPLED joins every live node to its first
+ * two live neighbours, takes the tree of the highest-degree live node as the
+ * giant tree and lets only nodes outside it scan their whole adjacency; EDGES
+ * runs union-find over every undirected edge.  AUTO (the default) is TREE. */
 #define GAPA_FITNESS_AUTO 0
 #define GAPA_FITNESS_EDGES 1
 #define GAPA_FITNESS_SAMPLED 2
+#define GAPA_FITNESS_TREE 3
 int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
 /* Per-kernel timing of the calls made between gapa_profile_begin() and

@@ -33,7 +33,62 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.col);
     cudaFree(g.edges);
     cudaFree(g.probe);
+    cudaFree(g.perm);
+    cudaFree(g.tparent);
+    cudaFree(g.nontree);
     g = DeviceGraph();
+}
+
+// BFS forest numbering: components are searched from their highest-degree
+// node (ties: lowest id), neighbours in CSR order.  Outputs the original ->
+// BFS-number map, each BFS number's tree parent, the non-tree edges in BFS
+// numbers (a < b, sorted) and the largest BFS level.
+struct BfsForest {
+    std::vector<int32_t> perm, tparent;
+    std::vector<std::pair<int32_t, int32_t>> nontree;
+    int depth = 0;
+};
+
+BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& col) {
+    BfsForest f;
+    f.perm.assign((size_t)n, -1);
+    f.tparent.assign((size_t)n, 0);
+    std::vector<int32_t> by_deg((size_t)n), parent_old((size_t)n, -1), level((size_t)n, 0), queue;
+    queue.reserve((size_t)n);
+    for (int32_t v = 0; v < n; ++v) by_deg[v] = v;
+    std::stable_sort(by_deg.begin(), by_deg.end(),
+                     [&](int32_t a, int32_t b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+    int32_t next = 0;
+    for (int32_t root : by_deg) {
+        if (f.perm[root] >= 0) continue;
+        size_t head = queue.size();
+        queue.push_back(root);
+        f.perm[root] = next++;
+        parent_old[root] = root;
+        while (head < queue.size()) {
+            const int32_t u = queue[head++];
+            for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
+                const int32_t w = col[e];
+                if (f.perm[w] >= 0) continue;
+                f.perm[w] = next++;
+                parent_old[w] = u;
+                level[w] = level[u] + 1;
+                f.depth = std::max(f.depth, level[w]);
+                queue.push_back(w);
+            }
+        }
+    }
+    for (int32_t v = 0; v < n; ++v) f.tparent[f.perm[v]] = f.perm[parent_old[v]];
+    f.nontree.reserve(col.size() / 2);
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
+            const int32_t w = col[e];
+            if (w <= u || parent_old[w] == u || parent_old[u] == w) continue;
+            const int32_t a = f.perm[u], b = f.perm[w];
+            f.nontree.emplace_back(std::min(a, b), std::max(a, b));
+        }
+    std::sort(f.nontree.begin(), f.nontree.end());
+    return f;
 }
 
 // Host-side validation of a symmetric simple CSR; returns the rows sorted.
@@ -342,6 +397,31 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     if (nnz) GAPA_CUDA(cudaMemcpy(g.col, sorted.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice));
     if (E) GAPA_CUDA(cudaMemcpy(g.edges, edges.data(), sizeof(int2) * (size_t)E, cudaMemcpyHostToDevice));
     GAPA_CUDA(cudaMemcpy(g.probe, probe.data(), sizeof(int32_t) * kProbe, cudaMemcpyHostToDevice));
+    // BFS forest numbering for the TREE kernel
+    BfsForest bf = bfs_forest(n, rp, sorted);
+    g.bfs_depth = bf.depth;
+    g.num_nontree = (int)bf.nontree.size();
+    g.packed16 = n <= 65536;
+    const size_t nt_bytes = (g.packed16 ? 4 : 8) * std::max<size_t>(bf.nontree.size(), 4);
+    if (cudaMalloc(&g.perm, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&g.tparent, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&g.nontree, nt_bytes) != cudaSuccess) {
+        free_graph(g);
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "BFS forest of %d nodes", n);
+    }
+    GAPA_CUDA(cudaMemcpy(g.perm, bf.perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+    GAPA_CUDA(cudaMemcpy(g.tparent, bf.tparent.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+    if (g.packed16) {
+        std::vector<uint32_t> w(bf.nontree.size());
+        for (size_t i = 0; i < w.size(); ++i)
+            w[i] = ((uint32_t)bf.nontree[i].first << 16) | (uint32_t)bf.nontree[i].second;
+        if (!w.empty()) GAPA_CUDA(cudaMemcpy(g.nontree, w.data(), 4 * w.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<int2> w(bf.nontree.size());
+        for (size_t i = 0; i < w.size(); ++i) w[i] = make_int2(bf.nontree[i].first, bf.nontree[i].second);
+        if (!w.empty()) GAPA_CUDA(cudaMemcpy(g.nontree, w.data(), 8 * w.size(), cudaMemcpyHostToDevice));
+    }
     c->g = g;
     return GAPA_OK;
 }
@@ -501,7 +581,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
 
 int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
-    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_SAMPLED)
+    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_TREE)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown fitness kernel %d", variant);
     c->fitness_variant = variant;
     return GAPA_OK;

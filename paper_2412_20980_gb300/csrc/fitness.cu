@@ -166,6 +166,88 @@ __device__ __forceinline__ void hook_sampled(volatile int* lab, int n, const int
     __syncthreads();
 }
 
+// Hooking, tree: labels start as the parents of a BFS spanning forest of G in
+// BFS numbering (parent < child), so the forest already joins every live node
+// to its live ancestors.  Cutting it at the deleted nodes leaves pieces; each
+// piece is flattened onto its top node, and the pieces are joined along the
+// non-tree edges.  An edge whose endpoints already share a label costs two
+// shared-memory reads.
+__device__ __forceinline__ void join_edge(volatile int* lab, int a, int b) {
+    const int la = lab[a], lb = lab[b];
+    if (la == lb || la == kDead || lb == kDead) return;
+    uf_unite(lab, la, lb);
+}
+
+template <bool kPacked16>
+__device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* __restrict__ tparent,
+                                          const int* __restrict__ perm, const void* __restrict__ nontree,
+                                          int num_nontree, const int* __restrict__ genes, int k, int* status) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int v = tid; v < n; v += T) lab[v] = __ldg(&tparent[v]);
+    __syncthreads();
+    // perturbation P^(A, p) of Eq. 13 in BFS numbering
+    for (int j = tid; j < k; j += T) {
+        const int d = __ldg(&genes[j]);
+        if ((unsigned)d < (unsigned)n)
+            lab[__ldg(&perm[d])] = kDead;
+        else
+            atomicOr(status, GAPA_DEV_BAD_GENE);
+    }
+    __syncthreads();
+    // cut: a live node whose parent is deleted becomes the top of its piece
+    for (int v = tid; v < n; v += T) {
+        const int p = lab[v];
+        if (p != kDead && p != v && lab[p] == kDead) lab[v] = v;
+    }
+    __syncthreads();
+    // flatten every piece onto its top node (owner writes only)
+    for (int v = tid; v < n; v += T) {
+        const int p = lab[v];
+        if (p != kDead && p != v) lab[v] = uf_root(lab, p);
+    }
+    __syncthreads();
+    // join the pieces along the non-tree edges
+    if (kPacked16) {
+        const uint4* e4 = reinterpret_cast<const uint4*>(nontree);
+        const int quads = num_nontree >> 2;
+        int q = tid;
+        uint4 w = q < quads ? __ldg(&e4[q]) : make_uint4(0, 0, 0, 0);
+        while (q < quads) {
+            const int qn = q + T;
+            const uint4 wn = qn < quads ? __ldg(&e4[qn]) : make_uint4(0, 0, 0, 0);
+            join_edge(lab, (int)(w.x >> 16), (int)(w.x & 0xFFFFu));
+            join_edge(lab, (int)(w.y >> 16), (int)(w.y & 0xFFFFu));
+            join_edge(lab, (int)(w.z >> 16), (int)(w.z & 0xFFFFu));
+            join_edge(lab, (int)(w.w >> 16), (int)(w.w & 0xFFFFu));
+            q = qn;
+            w = wn;
+        }
+        const unsigned* e1 = reinterpret_cast<const unsigned*>(nontree);
+        for (int e = quads * 4 + tid; e < num_nontree; e += T) {
+            const unsigned x = __ldg(&e1[e]);
+            join_edge(lab, (int)(x >> 16), (int)(x & 0xFFFFu));
+        }
+    } else {
+        const int4* e4 = reinterpret_cast<const int4*>(nontree);
+        const int pairs = num_nontree >> 1;
+        int q = tid;
+        int4 w = q < pairs ? __ldg(&e4[q]) : make_int4(0, 0, 0, 0);
+        while (q < pairs) {
+            const int qn = q + T;
+            const int4 wn = qn < pairs ? __ldg(&e4[qn]) : make_int4(0, 0, 0, 0);
+            join_edge(lab, w.x, w.y);
+            join_edge(lab, w.z, w.w);
+            q = qn;
+            w = wn;
+        }
+        if ((num_nontree & 1) && tid == 0) {
+            const int2 x = __ldg(reinterpret_cast<const int2*>(nontree) + (num_nontree - 1));
+            join_edge(lab, x.x, x.y);
+        }
+    }
+    __syncthreads();
+}
+
 // Component sizes and the int64 sum of C(size, 2) (PC(G) of Table "Whole").
 __device__ __forceinline__ void count_pc(volatile int* lab, int n, long long* out, long long* red) {
     const int tid = threadIdx.x, T = blockDim.x;
@@ -205,55 +287,85 @@ __device__ __forceinline__ void count_pc(volatile int* lab, int n, long long* ou
     if (tid == 0) *out = tot;
 }
 
-struct GraphArgs {
-    int n, num_edges;
-    const int2* edges;
-    const int* row_ptr;
-    const int* col;
-    const int* probe;
-};
-
-template <bool kSampled>
-__device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k,
-                                          long long* out, int* status, long long* red, int* sh_root) {
-    init_labels(lab, g.n, genes, k, status);
-    if (kSampled)
-        hook_sampled(lab, g.n, g.row_ptr, g.col, g.probe, sh_root);
-    else
-        hook_all_edges(lab, g.num_edges, g.edges);
-    count_pc(lab, g.n, out, red);
-}
-
-// One CTA per member, labels in shared memory.
-template <bool kSampled>
-__global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* __restrict__ pop, int k,
-                                                       long long* __restrict__ fit, int* status) {
-    extern __shared__ int smem_lab[];
-    __shared__ long long red[32];
-    __shared__ int sh_root;
-    const int i = blockIdx.x;
-    member_pc<kSampled>(smem_lab, g, pop + (size_t)i * k, k, &fit[i], status, red, &sh_root);
-}
-
-// One CTA per member, labels in a global scratch slice per CTA.
-template <bool kSampled>
-__global__ void __launch_bounds__(1024) cc_global_kernel(GraphArgs g, const int* __restrict__ pop, int k,
-                                                         long long* __restrict__ fit, int* status, int* labels,
-                                                         int member_base) {
-    __shared__ long long red[32];
-    __shared__ int sh_root;
-    const int i = member_base + blockIdx.x;
-    member_pc<kSampled>(labels + (size_t)blockIdx.x * g.n, g, pop + (size_t)i * k, k, &fit[i], status, red,
-                        &sh_root);
-}
-
-
 int smem_block_for(int n) {
     // enough threads to cover the graph, at most 1024; multiples of 32
     if (n <= 2048) return 256;
     if (n <= 8192) return 512;
     return 1024;
 }
+
+struct GraphArgs {
+    int n, num_edges;
+    const int2* edges;
+    const int* row_ptr;
+    const int* col;
+    const int* probe;
+    const int* perm;
+    const int* tparent;
+    const void* nontree;
+    int num_nontree;
+};
+
+enum Variant : int { V_EDGES = 0, V_SAMPLED = 1, V_TREE16 = 2, V_TREE32 = 3 };
+
+template <int kVar>
+__device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k,
+                                          long long* out, int* status, long long* red, int* sh_root) {
+    if (kVar == V_TREE16 || kVar == V_TREE32) {
+        hook_tree<kVar == V_TREE16>(lab, g.n, g.tparent, g.perm, g.nontree, g.num_nontree, genes, k, status);
+    } else {
+        init_labels(lab, g.n, genes, k, status);
+        if (kVar == V_SAMPLED)
+            hook_sampled(lab, g.n, g.row_ptr, g.col, g.probe, sh_root);
+        else
+            hook_all_edges(lab, g.num_edges, g.edges);
+    }
+    count_pc(lab, g.n, out, red);
+}
+
+// One CTA per member, labels in shared memory.
+template <int kVar>
+__global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* __restrict__ pop, int k,
+                                                       long long* __restrict__ fit, int* status) {
+    extern __shared__ int smem_lab[];
+    __shared__ long long red[32];
+    __shared__ int sh_root;
+    const int i = blockIdx.x;
+    member_pc<kVar>(smem_lab, g, pop + (size_t)i * k, k, &fit[i], status, red, &sh_root);
+}
+
+// One CTA per member, labels in a global scratch slice per CTA.
+template <int kVar>
+__global__ void __launch_bounds__(1024) cc_global_kernel(GraphArgs g, const int* __restrict__ pop, int k,
+                                                         long long* __restrict__ fit, int* status, int* labels,
+                                                         int member_base) {
+    __shared__ long long red[32];
+    __shared__ int sh_root;
+    const int i = member_base + blockIdx.x;
+    member_pc<kVar>(labels + (size_t)blockIdx.x * g.n, g, pop + (size_t)i * k, k, &fit[i], status, red, &sh_root);
+}
+
+template <int kVar>
+int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, int k, long long* f,
+                   cudaStream_t st) {
+    const int n = ga.n;
+    const size_t lab_bytes = (size_t)n * 4;
+    if (lab_bytes <= c->fit_smem_max) {
+        cc_smem_kernel<kVar><<<s, smem_block_for(n), lab_bytes, st>>>(ga, pop, k, f, c->status);
+        GAPA_CUDA(cudaGetLastError());
+        return GAPA_OK;
+    }
+    int rc = gapa_fitness_prepare(c, s);
+    if (rc != GAPA_OK) return rc;
+    const int wave = (int)(c->labels_cap / (size_t)n);
+    for (int base = 0; base < s; base += wave) {
+        const int cnt = s - base < wave ? s - base : wave;
+        cc_global_kernel<kVar><<<cnt, 1024, 0, st>>>(ga, pop, k, f, c->status, c->labels, base);
+        GAPA_CUDA(cudaGetLastError());
+    }
+    return GAPA_OK;
+}
+
 
 }  // namespace
 
@@ -269,35 +381,24 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     if (s <= 0) return GAPA_OK;
     ProfileScope prof(c, st, 0, s);
     const int n = c->g.n;
-    const size_t lab_bytes = (size_t)n * 4;
     long long* f = reinterpret_cast<long long*>(fit);
-    const GraphArgs ga{n, c->g.num_edges, c->g.edges, c->g.row_ptr, c->g.col, c->g.probe};
-    const bool sampled = c->fitness_variant != GAPA_FITNESS_EDGES;
-    if (lab_bytes <= c->fit_smem_max) {
-        const int block = smem_block_for(n);
-        if (sampled)
-            cc_smem_kernel<true><<<s, block, lab_bytes, st>>>(ga, pop, k, f, c->status);
-        else
-            cc_smem_kernel<false><<<s, block, lab_bytes, st>>>(ga, pop, k, f, c->status);
-        GAPA_CUDA(cudaGetLastError());
-        return GAPA_OK;
+    const GraphArgs ga{n,          c->g.num_edges, c->g.edges,   c->g.row_ptr,     c->g.col,
+                       c->g.probe, c->g.perm,      c->g.tparent, c->g.nontree,     c->g.num_nontree};
+    switch (c->fitness_variant) {
+        case GAPA_FITNESS_EDGES:
+            return launch_variant<V_EDGES>(c, ga, pop, s, k, f, st);
+        case GAPA_FITNESS_SAMPLED:
+            return launch_variant<V_SAMPLED>(c, ga, pop, s, k, f, st);
+        default:
+            return c->g.packed16 ? launch_variant<V_TREE16>(c, ga, pop, s, k, f, st)
+                                 : launch_variant<V_TREE32>(c, ga, pop, s, k, f, st);
     }
-    int rc = gapa_fitness_prepare(c, s);
-    if (rc != GAPA_OK) return rc;
-    const int wave = (int)(c->labels_cap / (size_t)n);
-    for (int base = 0; base < s; base += wave) {
-        const int cnt = s - base < wave ? s - base : wave;
-        if (sampled)
-            cc_global_kernel<true><<<cnt, 1024, 0, st>>>(ga, pop, k, f, c->status, c->labels, base);
-        else
-            cc_global_kernel<false><<<cnt, 1024, 0, st>>>(ga, pop, k, f, c->status, c->labels, base);
-        GAPA_CUDA(cudaGetLastError());
-    }
-    return GAPA_OK;
 }
 
 int gapa_fitness_kernels_init(gapa_ctx* c) {
-    int rc = gapa_set_smem_limit((const void*)cc_smem_kernel<true>, c->smem_optin, &c->fit_smem_max);
-    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<false>, c->smem_optin, &c->fit_smem_max);
+    int rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_EDGES>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_SAMPLED>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE16>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE32>, c->smem_optin, &c->fit_smem_max);
     return rc;
 }

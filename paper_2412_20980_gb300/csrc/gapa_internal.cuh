@@ -76,6 +76,15 @@ struct DeviceGraph {
     int2* edges = nullptr;    // [E] (u, v) with u < v, CSR order
     int* probe = nullptr;     // [kProbe] node ids of highest degree, descending
     int max_degree = 0;
+    // BFS forest numbering (TREE fitness kernel): nodes renumbered in BFS
+    // order from the highest-degree node of each component, so every tree
+    // parent has a smaller number than its child.
+    int* perm = nullptr;        // [n] original id -> BFS number
+    int* tparent = nullptr;     // [n] BFS number -> BFS number of its tree parent (roots: itself)
+    void* nontree = nullptr;    // non-tree edges (a < b, BFS numbers): uint32 a<<16|b if packed16, else int2
+    int num_nontree = 0;
+    bool packed16 = false;      // n <= 65536
+    int bfs_depth = 0;          // largest BFS level
 };
 
 constexpr int kProbe = 8;

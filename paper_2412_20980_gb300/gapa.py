@@ -36,7 +36,7 @@ EXPORTS = [
     "gapa_sync", "gapa_last_error", "gapa_version", "gapa_profile_begin", "gapa_profile_end",
     "gapa_set_fitness_kernel",
 ]
-FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED = 0, 1, 2
+FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE = 0, 1, 2, 3
 
 
 class GapaError(RuntimeError):

@@ -20,17 +20,17 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pc_worked_examples.json")
 
 
-@pytest.fixture(scope="module", params=["sampled", "edges"])
+@pytest.fixture(scope="module", params=["tree", "sampled", "edges"])
 def ctx(request):
     import torch
 
     from paper_2412_20980_gb300 import Context
     from paper_2412_20980_gb300 import build as b
-    from paper_2412_20980_gb300.gapa import FITNESS_EDGES, FITNESS_SAMPLED
+    from paper_2412_20980_gb300.gapa import FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE
 
     b.build()
     c = Context(0)
-    c.set_fitness_kernel(FITNESS_SAMPLED if request.param == "sampled" else FITNESS_EDGES)
+    c.set_fitness_kernel({"tree": FITNESS_TREE, "sampled": FITNESS_SAMPLED, "edges": FITNESS_EDGES}[request.param])
     yield c
     torch.cuda.synchronize()
     c.close()
