@@ -36,6 +36,8 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.perm);
     cudaFree(g.tparent);
     cudaFree(g.nontree);
+    cudaFree(g.lo_ptr);
+    cudaFree(g.lo_col);
     g = DeviceGraph();
 }
 
@@ -44,7 +46,7 @@ void free_graph(DeviceGraph& g) {
 // BFS-number map, each BFS number's tree parent, the non-tree edges in BFS
 // numbers (a < b, sorted) and the largest BFS level.
 struct BfsForest {
-    std::vector<int32_t> perm, tparent;
+    std::vector<int32_t> perm, tparent, lo_ptr, lo_col;
     std::vector<std::pair<int32_t, int32_t>> nontree;
     int depth = 0;
 };
@@ -88,6 +90,24 @@ BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vecto
             f.nontree.emplace_back(std::min(a, b), std::max(a, b));
         }
     std::sort(f.nontree.begin(), f.nontree.end());
+    // lower-numbered neighbours of every BFS number, ascending
+    std::vector<int32_t> inv((size_t)n);
+    for (int32_t v = 0; v < n; ++v) inv[f.perm[v]] = v;
+    f.lo_ptr.assign((size_t)n + 1, 0);
+    f.lo_col.clear();
+    f.lo_col.reserve(col.size() / 2);
+    std::vector<int32_t> tmp;
+    for (int32_t b = 0; b < n; ++b) {
+        const int32_t v = inv[b];
+        tmp.clear();
+        for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
+            const int32_t a = f.perm[col[e]];
+            if (a < b) tmp.push_back(a);
+        }
+        std::sort(tmp.begin(), tmp.end());
+        f.lo_col.insert(f.lo_col.end(), tmp.begin(), tmp.end());
+        f.lo_ptr[b + 1] = (int32_t)f.lo_col.size();
+    }
     return f;
 }
 
@@ -401,10 +421,12 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     BfsForest bf = bfs_forest(n, rp, sorted);
     g.bfs_depth = bf.depth;
     g.num_nontree = (int)bf.nontree.size();
-    g.packed16 = n <= 65536;
+    g.packed16 = n <= 65536 && (size_t)n * 4 <= c->fit_smem_max;  // 16-bit ids only on the shared-memory path
     const size_t nt_bytes = (g.packed16 ? 4 : 8) * std::max<size_t>(bf.nontree.size(), 4);
     if (cudaMalloc(&g.perm, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
         cudaMalloc(&g.tparent, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&g.lo_ptr, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+        cudaMalloc(&g.lo_col, sizeof(int32_t) * std::max<size_t>(bf.lo_col.size(), 1)) != cudaSuccess ||
         cudaMalloc(&g.nontree, nt_bytes) != cudaSuccess) {
         free_graph(g);
         cudaGetLastError();
@@ -412,6 +434,9 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     }
     GAPA_CUDA(cudaMemcpy(g.perm, bf.perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
     GAPA_CUDA(cudaMemcpy(g.tparent, bf.tparent.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+    GAPA_CUDA(cudaMemcpy(g.lo_ptr, bf.lo_ptr.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice));
+    if (!bf.lo_col.empty())
+        GAPA_CUDA(cudaMemcpy(g.lo_col, bf.lo_col.data(), sizeof(int32_t) * bf.lo_col.size(), cudaMemcpyHostToDevice));
     if (g.packed16) {
         std::vector<uint32_t> w(bf.nontree.size());
         for (size_t i = 0; i < w.size(); ++i)

@@ -168,18 +168,22 @@ __device__ __forceinline__ void hook_sampled(volatile int* lab, int n, const int
 
 // Hooking, tree: labels start as the parents of a BFS spanning forest of G in
 // BFS numbering (parent < child), so the forest already joins every live node
-// to its live ancestors.  Cutting it at the deleted nodes leaves pieces; each
-// piece is flattened onto its top node, and the pieces are joined along the
-// non-tree edges.  An edge whose endpoints already share a label costs two
-// shared-memory reads.
+// to its live ancestors.  A live node whose tree parent is deleted takes its
+// first live lower-numbered neighbour as parent instead (the top of a new
+// piece only if there is none).  Each piece is flattened onto its top node,
+// and the pieces are joined along the non-tree edges; an edge whose endpoints
+// already share a label costs two shared-memory reads.  kDeadV marks deleted
+// nodes (-1 for the 16-bit counting path, INT_MIN otherwise).
+template <int kDeadV>
 __device__ __forceinline__ void join_edge(volatile int* lab, int a, int b) {
     const int la = lab[a], lb = lab[b];
-    if (la == lb || la == kDead || lb == kDead) return;
+    if (la == lb || la == kDeadV || lb == kDeadV) return;
     uf_unite(lab, la, lb);
 }
 
-template <bool kPacked16>
+template <bool kPacked16, int kDeadV>
 __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* __restrict__ tparent,
+                                          const int* __restrict__ lo_ptr, const int* __restrict__ lo_col,
                                           const int* __restrict__ perm, const void* __restrict__ nontree,
                                           int num_nontree, const int* __restrict__ genes, int k, int* status) {
     const int tid = threadIdx.x, T = blockDim.x;
@@ -189,21 +193,33 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
     for (int j = tid; j < k; j += T) {
         const int d = __ldg(&genes[j]);
         if ((unsigned)d < (unsigned)n)
-            lab[__ldg(&perm[d])] = kDead;
+            lab[__ldg(&perm[d])] = kDeadV;
         else
             atomicOr(status, GAPA_DEV_BAD_GENE);
     }
     __syncthreads();
-    // cut: a live node whose parent is deleted becomes the top of its piece
+    // cut: a live node whose parent is deleted re-attaches to its first live
+    // lower-numbered neighbour, or tops its own piece.  Deadness is final here,
+    // so reading it while other slots change is safe.
     for (int v = tid; v < n; v += T) {
         const int p = lab[v];
-        if (p != kDead && p != v && lab[p] == kDead) lab[v] = v;
+        if (p == kDeadV || p == v || lab[p] != kDeadV) continue;
+        int q = v;
+        const int beg = __ldg(&lo_ptr[v]) + 1, end = __ldg(&lo_ptr[v + 1]);  // entry 0 is the tree parent
+        for (int e = beg; e < end; ++e) {
+            const int w = __ldg(&lo_col[e]);
+            if (lab[w] != kDeadV) {
+                q = w;
+                break;
+            }
+        }
+        lab[v] = q;
     }
     __syncthreads();
     // flatten every piece onto its top node (owner writes only)
     for (int v = tid; v < n; v += T) {
         const int p = lab[v];
-        if (p != kDead && p != v) lab[v] = uf_root(lab, p);
+        if (p != kDeadV && p != v) lab[v] = uf_root(lab, p);
     }
     __syncthreads();
     // join the pieces along the non-tree edges
@@ -215,17 +231,17 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
         while (q < quads) {
             const int qn = q + T;
             const uint4 wn = qn < quads ? __ldg(&e4[qn]) : make_uint4(0, 0, 0, 0);
-            join_edge(lab, (int)(w.x >> 16), (int)(w.x & 0xFFFFu));
-            join_edge(lab, (int)(w.y >> 16), (int)(w.y & 0xFFFFu));
-            join_edge(lab, (int)(w.z >> 16), (int)(w.z & 0xFFFFu));
-            join_edge(lab, (int)(w.w >> 16), (int)(w.w & 0xFFFFu));
+            join_edge<kDeadV>(lab, (int)(w.x >> 16), (int)(w.x & 0xFFFFu));
+            join_edge<kDeadV>(lab, (int)(w.y >> 16), (int)(w.y & 0xFFFFu));
+            join_edge<kDeadV>(lab, (int)(w.z >> 16), (int)(w.z & 0xFFFFu));
+            join_edge<kDeadV>(lab, (int)(w.w >> 16), (int)(w.w & 0xFFFFu));
             q = qn;
             w = wn;
         }
         const unsigned* e1 = reinterpret_cast<const unsigned*>(nontree);
         for (int e = quads * 4 + tid; e < num_nontree; e += T) {
             const unsigned x = __ldg(&e1[e]);
-            join_edge(lab, (int)(x >> 16), (int)(x & 0xFFFFu));
+            join_edge<kDeadV>(lab, (int)(x >> 16), (int)(x & 0xFFFFu));
         }
     } else {
         const int4* e4 = reinterpret_cast<const int4*>(nontree);
@@ -235,17 +251,55 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
         while (q < pairs) {
             const int qn = q + T;
             const int4 wn = qn < pairs ? __ldg(&e4[qn]) : make_int4(0, 0, 0, 0);
-            join_edge(lab, w.x, w.y);
-            join_edge(lab, w.z, w.w);
+            join_edge<kDeadV>(lab, w.x, w.y);
+            join_edge<kDeadV>(lab, w.z, w.w);
             q = qn;
             w = wn;
         }
         if ((num_nontree & 1) && tid == 0) {
             const int2 x = __ldg(reinterpret_cast<const int2*>(nontree) + (num_nontree - 1));
-            join_edge(lab, x.x, x.y);
+            join_edge<kDeadV>(lab, x.x, x.y);
         }
     }
     __syncthreads();
+}
+
+// Counting for n <= 65536 (ids fit 16 bits): a root's slot becomes
+// (members below it) << 16 | its id, built in one pass in which every live
+// non-root walks to its root (masking the count bits) and adds itself, warp-
+// aggregated; deleted nodes hold -1, which no root slot can equal because a
+// root id is below 65535.  Then the int64 sum of C(size, 2) over roots.
+__device__ __forceinline__ void count_pc16(volatile int* lab, int n, long long* out, long long* red) {
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+    for (int base = 0; base < n; base += T) {
+        const int v = base + tid;
+        int key = -1;
+        if (v < n) {
+            int p = lab[v];
+            if (p != -1 && p != v) {
+                int x = p;
+                while (true) {
+                    const int q = lab[x] & 0xFFFF;
+                    if (q == x) break;
+                    x = q;
+                }
+                key = x;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd((unsigned*)&lab[key], (unsigned)__popc(peers) << 16);
+    }
+    __syncthreads();
+    long long acc = 0;
+    for (int v = tid; v < n; v += T) {
+        const unsigned l = (unsigned)lab[v];
+        if (l != 0xFFFFFFFFu && (int)(l & 0xFFFFu) == v) {
+            const long long c = (long long)(l >> 16) + 1;
+            acc += c * (c - 1) / 2;
+        }
+    }
+    const long long tot = block_sum_ll(acc, red);
+    if (tid == 0) *out = tot;
 }
 
 // Component sizes and the int64 sum of C(size, 2) (PC(G) of Table "Whole").
@@ -302,6 +356,8 @@ struct GraphArgs {
     const int* probe;
     const int* perm;
     const int* tparent;
+    const int* lo_ptr;
+    const int* lo_col;
     const void* nontree;
     int num_nontree;
 };
@@ -311,8 +367,15 @@ enum Variant : int { V_EDGES = 0, V_SAMPLED = 1, V_TREE16 = 2, V_TREE32 = 3 };
 template <int kVar>
 __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k,
                                           long long* out, int* status, long long* red, int* sh_root) {
-    if (kVar == V_TREE16 || kVar == V_TREE32) {
-        hook_tree<kVar == V_TREE16>(lab, g.n, g.tparent, g.perm, g.nontree, g.num_nontree, genes, k, status);
+    if (kVar == V_TREE16) {
+        hook_tree<true, -1>(lab, g.n, g.tparent, g.lo_ptr, g.lo_col, g.perm, g.nontree, g.num_nontree, genes, k,
+                            status);
+        count_pc16(lab, g.n, out, red);
+        return;
+    }
+    if (kVar == V_TREE32) {
+        hook_tree<false, kDead>(lab, g.n, g.tparent, g.lo_ptr, g.lo_col, g.perm, g.nontree, g.num_nontree, genes, k,
+                                status);
     } else {
         init_labels(lab, g.n, genes, k, status);
         if (kVar == V_SAMPLED)
@@ -382,8 +445,8 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ProfileScope prof(c, st, 0, s);
     const int n = c->g.n;
     long long* f = reinterpret_cast<long long*>(fit);
-    const GraphArgs ga{n,          c->g.num_edges, c->g.edges,   c->g.row_ptr,     c->g.col,
-                       c->g.probe, c->g.perm,      c->g.tparent, c->g.nontree,     c->g.num_nontree};
+    const GraphArgs ga{n,         c->g.num_edges, c->g.edges,  c->g.row_ptr, c->g.col,         c->g.probe,
+                       c->g.perm, c->g.tparent,   c->g.lo_ptr, c->g.lo_col,  c->g.nontree,     c->g.num_nontree};
     switch (c->fitness_variant) {
         case GAPA_FITNESS_EDGES:
             return launch_variant<V_EDGES>(c, ga, pop, s, k, f, st);

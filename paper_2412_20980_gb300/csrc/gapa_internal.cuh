@@ -81,6 +81,8 @@ struct DeviceGraph {
     // parent has a smaller number than its child.
     int* perm = nullptr;        // [n] original id -> BFS number
     int* tparent = nullptr;     // [n] BFS number -> BFS number of its tree parent (roots: itself)
+    int* lo_ptr = nullptr;      // [n+1] CSR of lower-numbered neighbours (BFS numbers, ascending;
+    int* lo_col = nullptr;      //        the first one is the tree parent)
     void* nontree = nullptr;    // non-tree edges (a < b, BFS numbers): uint32 a<<16|b if packed16, else int2
     int num_nontree = 0;
     bool packed16 = false;      // n <= 65536

@@ -88,10 +88,12 @@ def test_various_graphs(ctx, make, k, s):
     assert np.array_equal(gpu_fit(ctx, g, pop), oracle.fitness(g.row_ptr, g.col, pop))
 
 
-def test_global_label_path_100k(ctx):
-    """n = 100000 needs 400 KB of labels: the global-memory variant."""
-    g = synth.ba_graph(100000, 3, 1)
-    pop = synth.random_deletion_sets(g.n, 2000, 40, 2)
+@pytest.mark.parametrize("n,k", [(100000, 2000), (60000, 3000)])
+def test_global_label_path(ctx, n, k):
+    """Too many labels for shared memory (n = 100000: 400 KB; n = 60000 sits between the
+    shared-memory limit and 2^16): the global-memory variant."""
+    g = synth.ba_graph(n, 3, 1)
+    pop = synth.random_deletion_sets(g.n, k, 40, 2)
     want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
     assert np.array_equal(gpu_fit(ctx, g, pop), want)
 
