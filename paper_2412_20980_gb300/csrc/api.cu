@@ -421,7 +421,8 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     BfsForest bf = bfs_forest(n, rp, sorted);
     g.bfs_depth = bf.depth;
     g.num_nontree = (int)bf.nontree.size();
-    g.packed16 = n <= 65536 && (size_t)n * 4 <= c->fit_smem_max;  // 16-bit ids only on the shared-memory path
+    // 16-bit ids only on the shared-memory path (labels + deleted-node bitmap)
+    g.packed16 = n <= 65536 && (size_t)n * 4 + (size_t)((n + 31) / 32) * 4 <= c->fit_smem_max;
     const size_t nt_bytes = (g.packed16 ? 4 : 8) * std::max<size_t>(bf.nontree.size(), 4);
     if (cudaMalloc(&g.perm, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
         cudaMalloc(&g.tparent, sizeof(int32_t) * (size_t)n) != cudaSuccess ||

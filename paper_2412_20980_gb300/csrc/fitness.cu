@@ -181,12 +181,62 @@ __device__ __forceinline__ void join_edge(volatile int* lab, int a, int b) {
     uf_unite(lab, la, lb);
 }
 
+// Initial labels with a deleted-node bitmap (shared memory, n bits) built
+// first: every live node takes its tree parent, or on a deleted tree parent
+// its first live lower-numbered neighbour, or itself.
+__device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsigned* dead, int n,
+                                                        const int* __restrict__ tparent,
+                                                        const int* __restrict__ lo_ptr,
+                                                        const int* __restrict__ lo_col,
+                                                        const int* __restrict__ perm,
+                                                        const int* __restrict__ genes, int k, int* status) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int words = (n + 31) >> 5;
+    for (int w = tid; w < words; w += T) dead[w] = 0u;
+    __syncthreads();
+    // perturbation P^(A, p) of Eq. 13 in BFS numbering
+    for (int j = tid; j < k; j += T) {
+        const int d = __ldg(&genes[j]);
+        if ((unsigned)d < (unsigned)n) {
+            const int b = __ldg(&perm[d]);
+            atomicOr(&dead[b >> 5], 1u << (b & 31));
+        } else {
+            atomicOr(status, GAPA_DEV_BAD_GENE);
+        }
+    }
+    __syncthreads();
+    for (int v = tid; v < n; v += T) {
+        if ((dead[v >> 5] >> (v & 31)) & 1u) {
+            lab[v] = -1;
+            continue;
+        }
+        int p = __ldg(&tparent[v]);
+        if (p != v && ((dead[p >> 5] >> (p & 31)) & 1u)) {
+            p = v;
+            const int beg = __ldg(&lo_ptr[v]) + 1, end = __ldg(&lo_ptr[v + 1]);  // entry 0 is the tree parent
+            for (int e = beg; e < end; ++e) {
+                const int w = __ldg(&lo_col[e]);
+                if (!((dead[w >> 5] >> (w & 31)) & 1u)) {
+                    p = w;
+                    break;
+                }
+            }
+        }
+        lab[v] = p;
+    }
+    __syncthreads();
+}
+
 template <bool kPacked16, int kDeadV>
 __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* __restrict__ tparent,
                                           const int* __restrict__ lo_ptr, const int* __restrict__ lo_col,
                                           const int* __restrict__ perm, const void* __restrict__ nontree,
-                                          int num_nontree, const int* __restrict__ genes, int k, int* status) {
+                                          int num_nontree, const int* __restrict__ genes, int k, int* status,
+                                          unsigned* dead_bitmap) {
     const int tid = threadIdx.x, T = blockDim.x;
+    if (dead_bitmap) {
+        init_tree_labels_bitmap(lab, dead_bitmap, n, tparent, lo_ptr, lo_col, perm, genes, k, status);
+    } else {
     for (int v = tid; v < n; v += T) lab[v] = __ldg(&tparent[v]);
     __syncthreads();
     // perturbation P^(A, p) of Eq. 13 in BFS numbering
@@ -216,6 +266,7 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
         lab[v] = q;
     }
     __syncthreads();
+    }
     // flatten every piece onto its top node (owner writes only)
     for (int v = tid; v < n; v += T) {
         const int p = lab[v];
@@ -275,9 +326,11 @@ __device__ __forceinline__ void count_pc16(volatile int* lab, int n, long long* 
         const int v = base + tid;
         int key = -1;
         if (v < n) {
-            int p = lab[v];
-            if (p != -1 && p != v) {
-                int x = p;
+            // a root's own slot may already carry count bits: classify by the
+            // masked id; a non-root's slot is never written in this pass
+            const int l = lab[v];
+            if (l != -1 && (l & 0xFFFF) != v) {
+                int x = l & 0xFFFF;
                 while (true) {
                     const int q = lab[x] & 0xFFFF;
                     if (q == x) break;
@@ -368,14 +421,15 @@ template <int kVar>
 __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k,
                                           long long* out, int* status, long long* red, int* sh_root) {
     if (kVar == V_TREE16) {
+        // shared-memory path: the deleted-node bitmap sits right after the labels
         hook_tree<true, -1>(lab, g.n, g.tparent, g.lo_ptr, g.lo_col, g.perm, g.nontree, g.num_nontree, genes, k,
-                            status);
+                            status, (unsigned*)(lab + g.n));
         count_pc16(lab, g.n, out, red);
         return;
     }
     if (kVar == V_TREE32) {
         hook_tree<false, kDead>(lab, g.n, g.tparent, g.lo_ptr, g.lo_col, g.perm, g.nontree, g.num_nontree, genes, k,
-                                status);
+                                status, nullptr);
     } else {
         init_labels(lab, g.n, genes, k, status);
         if (kVar == V_SAMPLED)
@@ -412,7 +466,7 @@ template <int kVar>
 int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, int k, long long* f,
                    cudaStream_t st) {
     const int n = ga.n;
-    const size_t lab_bytes = (size_t)n * 4;
+    const size_t lab_bytes = (size_t)n * 4 + (kVar == V_TREE16 ? (size_t)((n + 31) >> 5) * 4 : 0);
     if (lab_bytes <= c->fit_smem_max) {
         cc_smem_kernel<kVar><<<s, smem_block_for(n), lab_bytes, st>>>(ga, pop, k, f, c->status);
         GAPA_CUDA(cudaGetLastError());
