@@ -182,10 +182,17 @@ __device__ __forceinline__ void join_edge(volatile int* lab, int a, int b) {
 }
 
 // Initial labels with a deleted-node bitmap (shared memory, n bits) built
-// first: every live node takes its tree parent, or on a deleted tree parent
-// its first live lower-numbered neighbour, or itself.
+// first.  A live node v starts at its highest live tree ancestor u (the tree
+// path v..u is live; u's tree parent is deleted or u is a forest root), read
+// from the ancestor table with independent loads.  A node whose own tree
+// parent is deleted takes its first live lower-numbered neighbour (the pair
+// array holds the second one, the full list is read only beyond it), or
+// itself.  Every label is smaller than its node (or equal at a top).
+__device__ __forceinline__ bool bm_test(const unsigned* bm, int v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
+
 __device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsigned* dead, int n,
-                                                        const int* __restrict__ tparent,
+                                                        const int2* __restrict__ palt,
+                                                        const int* __restrict__ anc, int anc_depth,
                                                         const int* __restrict__ lo_ptr,
                                                         const int* __restrict__ lo_col,
                                                         const int* __restrict__ perm,
@@ -206,36 +213,63 @@ __device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsig
     }
     __syncthreads();
     for (int v = tid; v < n; v += T) {
-        if ((dead[v >> 5] >> (v & 31)) & 1u) {
+        if (bm_test(dead, v)) {
             lab[v] = -1;
             continue;
         }
-        int p = __ldg(&tparent[v]);
-        if (p != v && ((dead[p >> 5] >> (p & 31)) & 1u)) {
-            p = v;
-            const int beg = __ldg(&lo_ptr[v]) + 1, end = __ldg(&lo_ptr[v + 1]);  // entry 0 is the tree parent
-            for (int e = beg; e < end; ++e) {
-                const int w = __ldg(&lo_col[e]);
-                if (!((dead[w >> 5] >> (w & 31)) & 1u)) {
-                    p = w;
-                    break;
+        const int2 pa = __ldg(&palt[v]);
+        int p = pa.x;
+        if (p == v) {  // forest root
+            lab[v] = v;
+            continue;
+        }
+        if (!bm_test(dead, p)) {
+            // parent live: climb the live part of the tree path
+            // highest live ancestor below the first deleted one (ancestor 0 = p is live);
+            // the loads do not depend on the tests, so they are issued together
+            bool blocked = false;
+#pragma unroll
+            for (int j = 1; j < kAncMax; ++j) {
+                if (j < anc_depth) {
+                    const int a = __ldg(&anc[(size_t)j * n + v]);
+                    blocked = blocked || bm_test(dead, a);
+                    if (!blocked) p = a;
+                }
+            }
+            lab[v] = p;
+            continue;
+        }
+        // tree parent deleted: first live lower-numbered neighbour after it
+        int q = v;
+        if (pa.y >= 0) {
+            if (!bm_test(dead, pa.y)) {
+                q = pa.y;
+            } else {
+                const int beg = __ldg(&lo_ptr[v]) + 2, end = __ldg(&lo_ptr[v + 1]);
+                for (int e = beg; e < end; ++e) {
+                    const int w = __ldg(&lo_col[e]);
+                    if (!bm_test(dead, w)) {
+                        q = w;
+                        break;
+                    }
                 }
             }
         }
-        lab[v] = p;
+        lab[v] = q;
     }
     __syncthreads();
 }
 
 template <bool kPacked16, int kDeadV>
 __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* __restrict__ tparent,
+                                          const int2* __restrict__ palt, const int* __restrict__ anc, int anc_depth,
                                           const int* __restrict__ lo_ptr, const int* __restrict__ lo_col,
                                           const int* __restrict__ perm, const void* __restrict__ nontree,
                                           int num_nontree, const int* __restrict__ genes, int k, int* status,
                                           unsigned* dead_bitmap) {
     const int tid = threadIdx.x, T = blockDim.x;
     if (dead_bitmap) {
-        init_tree_labels_bitmap(lab, dead_bitmap, n, tparent, lo_ptr, lo_col, perm, genes, k, status);
+        init_tree_labels_bitmap(lab, dead_bitmap, n, palt, anc, anc_depth, lo_ptr, lo_col, perm, genes, k, status);
     } else {
     for (int v = tid; v < n; v += T) lab[v] = __ldg(&tparent[v]);
     __syncthreads();
@@ -282,10 +316,15 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
         while (q < quads) {
             const int qn = q + T;
             const uint4 wn = qn < quads ? __ldg(&e4[qn]) : make_uint4(0, 0, 0, 0);
-            join_edge<kDeadV>(lab, (int)(w.x >> 16), (int)(w.x & 0xFFFFu));
-            join_edge<kDeadV>(lab, (int)(w.y >> 16), (int)(w.y & 0xFFFFu));
-            join_edge<kDeadV>(lab, (int)(w.z >> 16), (int)(w.z & 0xFFFFu));
-            join_edge<kDeadV>(lab, (int)(w.w >> 16), (int)(w.w & 0xFFFFu));
+            // all eight labels first, then the (rarely failing) comparisons
+            const int a0 = (int)(w.x >> 16), b0 = (int)(w.x & 0xFFFFu), a1 = (int)(w.y >> 16), b1 = (int)(w.y & 0xFFFFu);
+            const int a2 = (int)(w.z >> 16), b2 = (int)(w.z & 0xFFFFu), a3 = (int)(w.w >> 16), b3 = (int)(w.w & 0xFFFFu);
+            const int la0 = lab[a0], lb0 = lab[b0], la1 = lab[a1], lb1 = lab[b1];
+            const int la2 = lab[a2], lb2 = lab[b2], la3 = lab[a3], lb3 = lab[b3];
+            if (la0 != lb0) join_edge<kDeadV>(lab, a0, b0);
+            if (la1 != lb1) join_edge<kDeadV>(lab, a1, b1);
+            if (la2 != lb2) join_edge<kDeadV>(lab, a2, b2);
+            if (la3 != lb3) join_edge<kDeadV>(lab, a3, b3);
             q = qn;
             w = wn;
         }
@@ -411,6 +450,9 @@ struct GraphArgs {
     const int* tparent;
     const int* lo_ptr;
     const int* lo_col;
+    const int2* palt;
+    const int* anc;
+    int anc_depth;
     const void* nontree;
     int num_nontree;
 };
@@ -422,14 +464,14 @@ __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g,
                                           long long* out, int* status, long long* red, int* sh_root) {
     if (kVar == V_TREE16) {
         // shared-memory path: the deleted-node bitmap sits right after the labels
-        hook_tree<true, -1>(lab, g.n, g.tparent, g.lo_ptr, g.lo_col, g.perm, g.nontree, g.num_nontree, genes, k,
-                            status, (unsigned*)(lab + g.n));
+        hook_tree<true, -1>(lab, g.n, g.tparent, g.palt, g.anc, g.anc_depth, g.lo_ptr, g.lo_col, g.perm, g.nontree,
+                            g.num_nontree, genes, k, status, (unsigned*)(lab + g.n));
         count_pc16(lab, g.n, out, red);
         return;
     }
     if (kVar == V_TREE32) {
-        hook_tree<false, kDead>(lab, g.n, g.tparent, g.lo_ptr, g.lo_col, g.perm, g.nontree, g.num_nontree, genes, k,
-                                status, nullptr);
+        hook_tree<false, kDead>(lab, g.n, g.tparent, g.palt, g.anc, g.anc_depth, g.lo_ptr, g.lo_col, g.perm,
+                                g.nontree, g.num_nontree, genes, k, status, nullptr);
     } else {
         init_labels(lab, g.n, genes, k, status);
         if (kVar == V_SAMPLED)
@@ -472,15 +514,20 @@ int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, 
         GAPA_CUDA(cudaGetLastError());
         return GAPA_OK;
     }
-    int rc = gapa_fitness_prepare(c, s);
-    if (rc != GAPA_OK) return rc;
-    const int wave = (int)(c->labels_cap / (size_t)n);
-    for (int base = 0; base < s; base += wave) {
-        const int cnt = s - base < wave ? s - base : wave;
-        cc_global_kernel<kVar><<<cnt, 1024, 0, st>>>(ga, pop, k, f, c->status, c->labels, base);
-        GAPA_CUDA(cudaGetLastError());
+    if constexpr (kVar == V_TREE16) {
+        // 16-bit ids are chosen at upload only when the labels fit in shared memory
+        return gapa_fail(GAPA_ERR_STATE, "16-bit tree labels need shared memory");
+    } else {
+        int rc = gapa_fitness_prepare(c, s);
+        if (rc != GAPA_OK) return rc;
+        const int wave = (int)(c->labels_cap / (size_t)n);
+        for (int base = 0; base < s; base += wave) {
+            const int cnt = s - base < wave ? s - base : wave;
+            cc_global_kernel<kVar><<<cnt, 1024, 0, st>>>(ga, pop, k, f, c->status, c->labels, base);
+            GAPA_CUDA(cudaGetLastError());
+        }
+        return GAPA_OK;
     }
-    return GAPA_OK;
 }
 
 
@@ -499,8 +546,22 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ProfileScope prof(c, st, 0, s);
     const int n = c->g.n;
     long long* f = reinterpret_cast<long long*>(fit);
-    const GraphArgs ga{n,         c->g.num_edges, c->g.edges,  c->g.row_ptr, c->g.col,         c->g.probe,
-                       c->g.perm, c->g.tparent,   c->g.lo_ptr, c->g.lo_col,  c->g.nontree,     c->g.num_nontree};
+    GraphArgs ga;
+    ga.n = n;
+    ga.num_edges = c->g.num_edges;
+    ga.edges = c->g.edges;
+    ga.row_ptr = c->g.row_ptr;
+    ga.col = c->g.col;
+    ga.probe = c->g.probe;
+    ga.perm = c->g.perm;
+    ga.tparent = c->g.tparent;
+    ga.lo_ptr = c->g.lo_ptr;
+    ga.lo_col = c->g.lo_col;
+    ga.palt = c->g.palt;
+    ga.anc = c->g.anc;
+    ga.anc_depth = c->g.anc_depth;
+    ga.nontree = c->g.nontree;
+    ga.num_nontree = c->g.num_nontree;
     switch (c->fitness_variant) {
         case GAPA_FITNESS_EDGES:
             return launch_variant<V_EDGES>(c, ga, pop, s, k, f, st);
