@@ -39,7 +39,6 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.lo_ptr);
     cudaFree(g.lo_col);
     cudaFree(g.palt);
-    cudaFree(g.anc);
     g = DeviceGraph();
 }
 
@@ -439,7 +438,7 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     GAPA_CUDA(cudaMemcpy(g.tparent, bf.tparent.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
     GAPA_CUDA(cudaMemcpy(g.lo_ptr, bf.lo_ptr.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice));
     {
-        // (tree parent, second lower neighbour) pairs and, for shallow forests, the ancestor table
+        // (tree parent, second lower neighbour) pairs
         std::vector<int2> palt((size_t)n);
         for (int32_t b = 0; b < n; ++b) {
             const int32_t cnt = bf.lo_ptr[b + 1] - bf.lo_ptr[b];
@@ -451,23 +450,6 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
             return gapa_fail(GAPA_ERR_OOM, "parent pairs of %d nodes", n);
         }
         GAPA_CUDA(cudaMemcpy(g.palt, palt.data(), sizeof(int2) * (size_t)n, cudaMemcpyHostToDevice));
-        if (bf.depth <= kAncMax) {
-            g.anc_depth = std::max(1, bf.depth);
-            std::vector<int32_t> anc((size_t)g.anc_depth * n);
-            for (int32_t b = 0; b < n; ++b) {
-                int32_t x = b;
-                for (int j = 0; j < g.anc_depth; ++j) {
-                    x = bf.tparent[x];
-                    anc[(size_t)j * n + b] = x;
-                }
-            }
-            if (cudaMalloc(&g.anc, sizeof(int32_t) * anc.size()) != cudaSuccess) {
-                free_graph(g);
-                cudaGetLastError();
-                return gapa_fail(GAPA_ERR_OOM, "ancestor table of %d nodes", n);
-            }
-            GAPA_CUDA(cudaMemcpy(g.anc, anc.data(), sizeof(int32_t) * anc.size(), cudaMemcpyHostToDevice));
-        }
     }
     if (!bf.lo_col.empty())
         GAPA_CUDA(cudaMemcpy(g.lo_col, bf.lo_col.data(), sizeof(int32_t) * bf.lo_col.size(), cudaMemcpyHostToDevice));

@@ -182,17 +182,14 @@ __device__ __forceinline__ void join_edge(volatile int* lab, int a, int b) {
 }
 
 // Initial labels with a deleted-node bitmap (shared memory, n bits) built
-// first.  A live node v starts at its highest live tree ancestor u (the tree
-// path v..u is live; u's tree parent is deleted or u is a forest root), read
-// from the ancestor table with independent loads.  A node whose own tree
-// parent is deleted takes its first live lower-numbered neighbour (the pair
-// array holds the second one, the full list is read only beyond it), or
-// itself.  Every label is smaller than its node (or equal at a top).
+// first.  A live node takes its tree parent; a node whose tree parent is
+// deleted takes its first live lower-numbered neighbour (the pair array holds
+// the second one, the full list is read only beyond it), or itself.  Every
+// label is smaller than its node (or equal at a top).
 __device__ __forceinline__ bool bm_test(const unsigned* bm, int v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
 
 __device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsigned* dead, int n,
                                                         const int2* __restrict__ palt,
-                                                        const int* __restrict__ anc, int anc_depth,
                                                         const int* __restrict__ lo_ptr,
                                                         const int* __restrict__ lo_col,
                                                         const int* __restrict__ perm,
@@ -224,18 +221,6 @@ __device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsig
             continue;
         }
         if (!bm_test(dead, p)) {
-            // parent live: climb the live part of the tree path
-            // highest live ancestor below the first deleted one (ancestor 0 = p is live);
-            // the loads do not depend on the tests, so they are issued together
-            bool blocked = false;
-#pragma unroll
-            for (int j = 1; j < kAncMax; ++j) {
-                if (j < anc_depth) {
-                    const int a = __ldg(&anc[(size_t)j * n + v]);
-                    blocked = blocked || bm_test(dead, a);
-                    if (!blocked) p = a;
-                }
-            }
             lab[v] = p;
             continue;
         }
@@ -262,14 +247,14 @@ __device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsig
 
 template <bool kPacked16, int kDeadV>
 __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* __restrict__ tparent,
-                                          const int2* __restrict__ palt, const int* __restrict__ anc, int anc_depth,
+                                          const int2* __restrict__ palt,
                                           const int* __restrict__ lo_ptr, const int* __restrict__ lo_col,
                                           const int* __restrict__ perm, const void* __restrict__ nontree,
                                           int num_nontree, const int* __restrict__ genes, int k, int* status,
                                           unsigned* dead_bitmap) {
     const int tid = threadIdx.x, T = blockDim.x;
     if (dead_bitmap) {
-        init_tree_labels_bitmap(lab, dead_bitmap, n, palt, anc, anc_depth, lo_ptr, lo_col, perm, genes, k, status);
+        init_tree_labels_bitmap(lab, dead_bitmap, n, palt, lo_ptr, lo_col, perm, genes, k, status);
     } else {
     for (int v = tid; v < n; v += T) lab[v] = __ldg(&tparent[v]);
     __syncthreads();
@@ -451,8 +436,6 @@ struct GraphArgs {
     const int* lo_ptr;
     const int* lo_col;
     const int2* palt;
-    const int* anc;
-    int anc_depth;
     const void* nontree;
     int num_nontree;
 };
@@ -464,13 +447,13 @@ __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g,
                                           long long* out, int* status, long long* red, int* sh_root) {
     if (kVar == V_TREE16) {
         // shared-memory path: the deleted-node bitmap sits right after the labels
-        hook_tree<true, -1>(lab, g.n, g.tparent, g.palt, g.anc, g.anc_depth, g.lo_ptr, g.lo_col, g.perm, g.nontree,
+        hook_tree<true, -1>(lab, g.n, g.tparent, g.palt, g.lo_ptr, g.lo_col, g.perm, g.nontree,
                             g.num_nontree, genes, k, status, (unsigned*)(lab + g.n));
         count_pc16(lab, g.n, out, red);
         return;
     }
     if (kVar == V_TREE32) {
-        hook_tree<false, kDead>(lab, g.n, g.tparent, g.palt, g.anc, g.anc_depth, g.lo_ptr, g.lo_col, g.perm,
+        hook_tree<false, kDead>(lab, g.n, g.tparent, g.palt, g.lo_ptr, g.lo_col, g.perm,
                                 g.nontree, g.num_nontree, genes, k, status, nullptr);
     } else {
         init_labels(lab, g.n, genes, k, status);
@@ -558,8 +541,6 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ga.lo_ptr = c->g.lo_ptr;
     ga.lo_col = c->g.lo_col;
     ga.palt = c->g.palt;
-    ga.anc = c->g.anc;
-    ga.anc_depth = c->g.anc_depth;
     ga.nontree = c->g.nontree;
     ga.num_nontree = c->g.num_nontree;
     switch (c->fitness_variant) {

@@ -84,8 +84,6 @@ struct DeviceGraph {
     int* lo_ptr = nullptr;      // [n+1] CSR of lower-numbered neighbours (BFS numbers, ascending;
     int* lo_col = nullptr;      //        the first one is the tree parent)
     int2* palt = nullptr;       // [n] (tree parent, second lower-numbered neighbour or -1)
-    int* anc = nullptr;         // [anc_depth][n] tree ancestors: anc[j*n+v] = (j+1)-th ancestor (roots repeat)
-    int anc_depth = 0;          // 0 when the forest is deeper than kAncMax
     void* nontree = nullptr;    // non-tree edges (a < b, BFS numbers): uint32 a<<16|b if packed16, else int2
     int num_nontree = 0;
     bool packed16 = false;      // n <= 65536
@@ -93,7 +91,6 @@ struct DeviceGraph {
 };
 
 constexpr int kProbe = 8;
-constexpr int kAncMax = 8;  // ancestor table kept when the BFS forest is at most this deep
 
 struct gapa_ctx {
     int device = 0;
