@@ -42,62 +42,56 @@ void free_graph(DeviceGraph& g) {
     g = DeviceGraph();
 }
 
-// BFS forest numbering: components are searched from their highest-degree
-// node (ties: lowest id), neighbours in CSR order.  Outputs the original ->
-// BFS-number map, each BFS number's tree parent, the non-tree edges in BFS
-// numbers (a < b, sorted) and the largest BFS level.
+// Forest numbering for the TREE fitness kernel.  Nodes are numbered by
+// descending degree (ties: lower id) - or, with bfs_order, in BFS order from
+// the highest-degree node of each component.  Every node's parent is its
+// lowest-numbered neighbour when that one is lower than the node itself (a
+// root otherwise), so parents always precede children; for BFS order this is
+// the BFS tree.  Outputs the original -> new map, the parents, each node's
+// lower-numbered neighbours (ascending; the first one is the parent), the
+// non-parent edges (a < b, sorted) and the deepest parent chain.
 struct BfsForest {
     std::vector<int32_t> perm, tparent, lo_ptr, lo_col;
     std::vector<std::pair<int32_t, int32_t>> nontree;
     int depth = 0;
 };
 
-BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& col) {
+BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                     bool bfs_order = false) {
     BfsForest f;
     f.perm.assign((size_t)n, -1);
-    f.tparent.assign((size_t)n, 0);
-    std::vector<int32_t> by_deg((size_t)n), parent_old((size_t)n, -1), level((size_t)n, 0), queue;
-    queue.reserve((size_t)n);
+    std::vector<int32_t> by_deg((size_t)n);
     for (int32_t v = 0; v < n; ++v) by_deg[v] = v;
     std::stable_sort(by_deg.begin(), by_deg.end(),
                      [&](int32_t a, int32_t b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
-    int32_t next = 0;
-    for (int32_t root : by_deg) {
-        if (f.perm[root] >= 0) continue;
-        size_t head = queue.size();
-        queue.push_back(root);
-        f.perm[root] = next++;
-        parent_old[root] = root;
-        while (head < queue.size()) {
-            const int32_t u = queue[head++];
-            for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
-                const int32_t w = col[e];
-                if (f.perm[w] >= 0) continue;
-                f.perm[w] = next++;
-                parent_old[w] = u;
-                level[w] = level[u] + 1;
-                f.depth = std::max(f.depth, level[w]);
-                queue.push_back(w);
+    if (bfs_order) {
+        std::vector<int32_t> queue;
+        queue.reserve((size_t)n);
+        int32_t next = 0;
+        for (int32_t root : by_deg) {
+            if (f.perm[root] >= 0) continue;
+            size_t head = queue.size();
+            queue.push_back(root);
+            f.perm[root] = next++;
+            while (head < queue.size()) {
+                const int32_t u = queue[head++];
+                for (int32_t e = rp[u]; e < rp[u + 1]; ++e)
+                    if (f.perm[col[e]] < 0) {
+                        f.perm[col[e]] = next++;
+                        queue.push_back(col[e]);
+                    }
             }
         }
+    } else {
+        for (int32_t r = 0; r < n; ++r) f.perm[by_deg[r]] = r;
     }
-    for (int32_t v = 0; v < n; ++v) f.tparent[f.perm[v]] = f.perm[parent_old[v]];
-    f.nontree.reserve(col.size() / 2);
-    for (int32_t u = 0; u < n; ++u)
-        for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
-            const int32_t w = col[e];
-            if (w <= u || parent_old[w] == u || parent_old[u] == w) continue;
-            const int32_t a = f.perm[u], b = f.perm[w];
-            f.nontree.emplace_back(std::min(a, b), std::max(a, b));
-        }
-    std::sort(f.nontree.begin(), f.nontree.end());
-    // lower-numbered neighbours of every BFS number, ascending
     std::vector<int32_t> inv((size_t)n);
     for (int32_t v = 0; v < n; ++v) inv[f.perm[v]] = v;
+    // lower-numbered neighbours, ascending; parent = the first of them
     f.lo_ptr.assign((size_t)n + 1, 0);
-    f.lo_col.clear();
     f.lo_col.reserve(col.size() / 2);
-    std::vector<int32_t> tmp;
+    f.tparent.assign((size_t)n, 0);
+    std::vector<int32_t> tmp, level((size_t)n, 0);
     for (int32_t b = 0; b < n; ++b) {
         const int32_t v = inv[b];
         tmp.clear();
@@ -106,9 +100,16 @@ BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vecto
             if (a < b) tmp.push_back(a);
         }
         std::sort(tmp.begin(), tmp.end());
+        f.tparent[b] = tmp.empty() ? b : tmp[0];
+        level[b] = tmp.empty() ? 0 : level[tmp[0]] + 1;
+        f.depth = std::max(f.depth, level[b]);
         f.lo_col.insert(f.lo_col.end(), tmp.begin(), tmp.end());
         f.lo_ptr[b + 1] = (int32_t)f.lo_col.size();
     }
+    f.nontree.reserve(col.size() / 2);
+    for (int32_t b = 0; b < n; ++b)
+        for (int32_t e = f.lo_ptr[b] + 1; e < f.lo_ptr[b + 1]; ++e) f.nontree.emplace_back(f.lo_col[e], b);
+    std::sort(f.nontree.begin(), f.nontree.end());
     return f;
 }
 

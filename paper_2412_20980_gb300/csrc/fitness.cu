@@ -209,38 +209,44 @@ __device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsig
         }
     }
     __syncthreads();
-    for (int v = tid; v < n; v += T) {
-        if (bm_test(dead, v)) {
-            lab[v] = -1;
-            continue;
+    // four nodes per thread per step, their pair loads issued together
+    constexpr int kU = 4;
+    for (int base = tid; base < n; base += kU * T) {
+        int2 pa[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int v = base + u * T;
+            pa[u] = v < n ? __ldg(&palt[v]) : make_int2(0, -1);
         }
-        const int2 pa = __ldg(&palt[v]);
-        int p = pa.x;
-        if (p == v) {  // forest root
-            lab[v] = v;
-            continue;
-        }
-        if (!bm_test(dead, p)) {
-            lab[v] = p;
-            continue;
-        }
-        // tree parent deleted: first live lower-numbered neighbour after it
-        int q = v;
-        if (pa.y >= 0) {
-            if (!bm_test(dead, pa.y)) {
-                q = pa.y;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int v = base + u * T;
+            if (v >= n) break;
+            int q;
+            if (bm_test(dead, v)) {
+                q = -1;
+            } else if (pa[u].x == v || !bm_test(dead, pa[u].x)) {
+                q = pa[u].x;  // forest root (itself) or live parent
             } else {
-                const int beg = __ldg(&lo_ptr[v]) + 2, end = __ldg(&lo_ptr[v + 1]);
-                for (int e = beg; e < end; ++e) {
-                    const int w = __ldg(&lo_col[e]);
-                    if (!bm_test(dead, w)) {
-                        q = w;
-                        break;
+                // parent deleted: first live lower-numbered neighbour after it
+                q = v;
+                if (pa[u].y >= 0) {
+                    if (!bm_test(dead, pa[u].y)) {
+                        q = pa[u].y;
+                    } else {
+                        const int beg = __ldg(&lo_ptr[v]) + 2, end = __ldg(&lo_ptr[v + 1]);
+                        for (int e = beg; e < end; ++e) {
+                            const int w = __ldg(&lo_col[e]);
+                            if (!bm_test(dead, w)) {
+                                q = w;
+                                break;
+                            }
+                        }
                     }
                 }
             }
+            lab[v] = q;
         }
-        lab[v] = q;
     }
     __syncthreads();
 }
