@@ -11,6 +11,7 @@
 // root slots with warp-aggregated atomics; the int64 sum is reduced with
 // warp shuffles.
 #include <climits>
+#include <mutex>
 
 #include "gapa_internal.cuh"
 
@@ -566,4 +567,121 @@ int gapa_fitness_kernels_init(gapa_ctx* c) {
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE16>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE32>, c->smem_optin, &c->fit_smem_max);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free fitness (gapa_fitness_noalloc).
+//
+// For callers that must not allocate device memory: code that runs while a
+// framework captures the stream into a CUDA graph (where cudaMalloc is not
+// allowed), latency-critical loops that cannot take cudaMalloc's implicit
+// synchronisation, and processes whose device memory is owned by another
+// allocator under a fixed budget.  The caller passes the graph as a device
+// edge list and the population and output as device arrays; the label
+// scratch is the file-scope array below, which every GPU that loads this
+// library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocLabels = (size_t)GAPA_NOALLOC_MAX_LABELS;  // 8 Mi int32 = 32 MiB
+__device__ __align__(256) int g_noalloc_labels[kNoAllocLabels];
+__device__ int g_noalloc_status;
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int* g_noalloc_labels_addr[kNoAllocMaxDevices];
+int* g_noalloc_status_addr[kNoAllocMaxDevices];
+
+// Union-find over a caller-supplied edge list (pairs of int32), every
+// endpoint checked against [0, n) because the list was not validated.
+__device__ __forceinline__ void hook_edge_list_checked(volatile int* lab, int n, int num_edges,
+                                                       const int* __restrict__ edges, int* status) {
+    for (int e = threadIdx.x; e < num_edges; e += blockDim.x) {
+        const int u = __ldg(&edges[2 * (size_t)e]), v = __ldg(&edges[2 * (size_t)e + 1]);
+        if ((unsigned)u >= (unsigned)n || (unsigned)v >= (unsigned)n) {
+            atomicOr(status, GAPA_DEV_BAD_EDGE);
+            continue;
+        }
+        if (u != v) edge_op(lab, u, v);
+    }
+    __syncthreads();
+}
+
+// One CTA per member; labels in the static scratch, slice blockIdx.x of the wave.
+__global__ void __launch_bounds__(1024) cc_noalloc_kernel(int n, int num_edges, const int* __restrict__ edges,
+                                                          const int* __restrict__ pop, int k,
+                                                          long long* __restrict__ fit, int* status, int* labels,
+                                                          int member_base) {
+    __shared__ long long red[32];
+    const int i = member_base + blockIdx.x;
+    volatile int* lab = labels + (size_t)blockIdx.x * n;
+    init_labels(lab, n, pop + (size_t)i * k, k, status);
+    hook_edge_list_checked(lab, n, num_edges, edges, status);
+    count_pc(lab, n, &fit[i], red);
+}
+
+// Device addresses of the static arrays on the current device, looked up once.
+int noalloc_setup(int dev, int** labels, int** status) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return gapa_fail(GAPA_ERR_INVALID_ARG, "device %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_labels_addr[dev]) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_labels);
+        if (e != cudaSuccess) return gapa_cuda_fail(e, "cudaGetSymbolAddress(label scratch)");
+        e = cudaGetSymbolAddress(&b, g_noalloc_status);
+        if (e != cudaSuccess) return gapa_cuda_fail(e, "cudaGetSymbolAddress(status word)");
+        g_noalloc_labels_addr[dev] = (int*)a;
+        g_noalloc_status_addr[dev] = (int*)b;
+    }
+    *labels = g_noalloc_labels_addr[dev];
+    *status = g_noalloc_status_addr[dev];
+    return GAPA_OK;
+}
+
+}  // namespace
+
+extern "C" int gapa_fitness_noalloc(int device, void* cuda_stream, int32_t n, int32_t num_edges,
+                                    const int32_t* edges_dev, const int32_t* pop_dev, int32_t s, int32_t k,
+                                    int64_t* fit_dev) {
+    if (n < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "n must be >= 1 (got %d)", n);
+    if ((size_t)n > kNoAllocLabels)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "n = %d exceeds the static scratch of %zu labels", n, kNoAllocLabels);
+    if (num_edges < 0 || s < 0 || k < 0) return gapa_fail(GAPA_ERR_INVALID_ARG, "negative size");
+    if ((long long)s * k >= (1LL << 31)) return gapa_fail(GAPA_ERR_INVALID_ARG, "s*k must be below 2^31");
+    if (s == 0) return GAPA_OK;
+    if (!fit_dev || (k > 0 && !pop_dev) || (num_edges > 0 && !edges_dev))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL pointer");
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return gapa_fail(GAPA_ERR_CUDA, "cudaGetDevice failed");
+    if (prev != device) {
+        const cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) return gapa_cuda_fail(e, "cudaSetDevice");
+    }
+    auto restore = [&](int rc) {
+        if (prev != device) cudaSetDevice(prev);
+        return rc;
+    };
+    int* labels = nullptr;
+    int* status = nullptr;
+    int rc = noalloc_setup(device, &labels, &status);
+    if (rc != GAPA_OK) return restore(rc);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return restore(gapa_cuda_fail(e, "clearing the status word"));
+    const int wave = (int)(kNoAllocLabels / (size_t)n);
+    for (int base = 0; base < s; base += wave) {
+        const int cnt = s - base < wave ? s - base : wave;
+        cc_noalloc_kernel<<<cnt, 1024, 0, st>>>(n, num_edges, edges_dev, pop_dev, k,
+                                                 reinterpret_cast<long long*>(fit_dev), status, labels, base);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return restore(gapa_cuda_fail(e, "cc_noalloc_kernel launch"));
+    }
+    int h = 0;
+    e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return restore(gapa_cuda_fail(e, "gapa_fitness_noalloc"));
+    if (h & GAPA_DEV_BAD_EDGE) return restore(gapa_fail(GAPA_ERR_DEVICE, "an edge endpoint outside [0, n)"));
+    if (h & GAPA_DEV_BAD_GENE) return restore(gapa_fail(GAPA_ERR_DEVICE, "a gene outside [0, n)"));
+    return restore(GAPA_OK);
 }

@@ -16,6 +16,7 @@ enum : int {
     GAPA_DEV_BAD_GENE = 1,   // a gene outside [0, n)
     GAPA_DEV_TIMEOUT = 2,    // a bounded wait ran out
     GAPA_DEV_CAPACITY = 4,   // a work list overflowed its bound
+    GAPA_DEV_BAD_EDGE = 8,   // an edge endpoint outside [0, n)
 };
 
 // Philox tags of the counter's last word (tag << 24 | round).

@@ -34,7 +34,7 @@ EXPORTS = [
     "gapa_create", "gapa_destroy", "gapa_set_stream", "gapa_graph_upload", "gapa_pop_init",
     "gapa_fitness", "gapa_fitness_host", "gapa_generation", "gapa_generation_host", "gapa_run",
     "gapa_sync", "gapa_last_error", "gapa_version", "gapa_profile_begin", "gapa_profile_end",
-    "gapa_set_fitness_kernel",
+    "gapa_set_fitness_kernel", "gapa_fitness_noalloc",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE = 0, 1, 2, 3
 
@@ -116,6 +116,7 @@ def load(path: str | None = None):
             "gapa_sync": ([V], U),
             "gapa_profile_begin": ([V], U),
             "gapa_set_fitness_kernel": ([V, U], U),
+            "gapa_fitness_noalloc": ([U, V, I32, I32, V, V, I32, I32, V], U),
             "gapa_profile_end": ([V, ctypes.POINTER(Profile)], U),
             "gapa_last_error": ([], ctypes.c_char_p),
             "gapa_version": ([], ctypes.c_char_p),
@@ -158,6 +159,24 @@ def _dev_ptr(t, dtype, name: str, device_index: int):
 
 def _host_ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def fitness_noalloc(edges, pop, n: int, out, stream=None):
+    """gapa_fitness_noalloc: fitness of pop[s][k] over the device edge list edges[E][2]
+    without any allocation by the library; `out` (int64[s] on the same device) is
+    caller-provided.  Synchronous."""
+    torch = _torch()
+    dev = pop.device.index
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    if edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError("edges must be [E, 2]")
+    s, k = pop.shape
+    _check(load().gapa_fitness_noalloc(dev, ctypes.c_void_p(stream.cuda_stream), n, edges.shape[0],
+                                       _dev_ptr(edges, torch.int32, "edges", dev),
+                                       _dev_ptr(pop, torch.int32, "pop", dev), s, k,
+                                       _dev_ptr(out, torch.int64, "fit", dev)))
+    return out
 
 
 class Context:
