@@ -71,14 +71,15 @@ def csr_from_edges(n: int, u, v, name: str = "", meta: dict | None = None) -> Gr
         raise ValueError("self-loop in edge list")
     lo = np.minimum(u, v)
     hi = np.maximum(u, v)
-    key = np.unique(lo * n + hi)
+    key = np.sort(lo * n + hi)
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     lo = key // n
     hi = key % n
-    src = np.concatenate([lo, hi])
-    dst = np.concatenate([hi, lo])
-    order = np.lexsort((dst, src))
-    src = src[order]
-    dst = dst[order]
+    arcs = np.concatenate([lo * n + hi, hi * n + lo])
+    arcs.sort()
+    src = arcs // n
+    dst = arcs % n
     counts = np.bincount(src, minlength=n)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])
@@ -173,8 +174,23 @@ def relabel(g: Graph, seed: int) -> Graph:
     return csr_from_edges(g.n, perm[u], perm[v], g.name + f"_perm{seed}", dict(g.meta, relabel=seed))
 
 
+def _rmat_keys(scale: int, count: int, ta, tb, tc, stream: int) -> np.ndarray:
+    """Samples 0..count-1: edge keys min*n+max, or -1 for self-loops."""
+    n = 1 << scale
+    u = np.zeros(count, dtype=np.int64)
+    v = np.zeros(count, dtype=np.int64)
+    for lvl in range(scale):
+        # one SplitMix64 stream per recursion level; sample j uses value j of each
+        w = splitmix64(stream ^ (lvl << 48), 0, count) >> np.uint64(32)
+        u = (u << 1) | (w >= tb).astype(np.int64)  # quadrants c, d set the row bit
+        v = (v << 1) | (((w >= ta) & (w < tb)) | (w >= tc)).astype(np.int64)  # quadrants b, d set the column bit
+    key = np.minimum(u, v) * n + np.maximum(u, v)
+    key[u == v] = -1
+    return key
+
+
 def rmat_graph(scale: int, edges: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
-               seed: int = 1, permute: bool = True, chunk: int = 1 << 22) -> Graph:
+               seed: int = 1, permute: bool = True, chunk: int | None = None) -> Graph:
     """R-MAT graph with exactly ``edges`` distinct undirected non-loop edges on 2^scale nodes."""
     n = 1 << scale
     if edges > n * (n - 1) // 2:
@@ -183,43 +199,24 @@ def rmat_graph(scale: int, edges: int, a: float = 0.57, b: float = 0.19, c: floa
     tb = np.uint64(int((a + b) * 4294967296.0))
     tc = np.uint64(int((a + b + c) * 4294967296.0))
     stream = seed ^ 0x524D415400000000
-    keys_all: list[np.ndarray] = []
-    have = 0
-    drawn = 0
-    seen = np.empty(0, dtype=np.int64)
-    while have < edges:
-        u = np.zeros(chunk, dtype=np.int64)
-        v = np.zeros(chunk, dtype=np.int64)
-        for lvl in range(scale):
-            # one SplitMix64 stream per recursion level; sample j uses value j of each
-            w = splitmix64(stream ^ (lvl << 48), drawn, chunk) >> np.uint64(32)
-            bu = (w >= tb).astype(np.int64)  # quadrants c, d set the row bit
-            bv = ((w >= ta) & (w < tb)) | (w >= tc)  # quadrants b, d set the column bit
-            u = (u << 1) | bu
-            v = (v << 1) | bv.astype(np.int64)
-        drawn += chunk
-        keep = u != v
-        lo = np.minimum(u[keep], v[keep])
-        hi = np.maximum(u[keep], v[keep])
-        key = lo * n + hi
-        # first appearance order within the chunk, then drop keys seen in earlier chunks
-        uk, first = np.unique(key, return_index=True)
-        fresh = ~np.isin(uk, seen, assume_unique=True)
-        uk = uk[fresh]
-        first = first[fresh]
-        order = np.argsort(first, kind="stable")
-        newkeys = uk[order]
-        keys_all.append(newkeys)
-        seen = np.union1d(seen, newkeys)
-        have += newkeys.size
-    keys = np.concatenate(keys_all)[:edges]
+    count = max(1024, int(edges * 1.3))
+    while True:
+        key = _rmat_keys(scale, count, ta, tb, tc, stream)
+        order = np.argsort(key, kind="stable")  # equal keys keep sample order
+        sk = key[order]
+        first = np.concatenate(([True], sk[1:] != sk[:-1])) & (sk >= 0)
+        first_idx = np.sort(order[first])  # first appearance of every distinct edge, in sample order
+        if first_idx.size >= edges:
+            break
+        count = int(count * 1.25) + 1024
+    keys = key[first_idx[:edges]]
     lo = keys // n
     hi = keys % n
     if permute:
         perm = random_permutation(n, seed)
         lo, hi = perm[lo], perm[hi]
     return csr_from_edges(n, lo, hi, f"rmat_s{scale}_e{edges}_s{seed}",
-                          {"kind": "rmat", "a": a, "b": b, "c": c, "seed": seed, "samples": drawn})
+                          {"kind": "rmat", "a": a, "b": b, "c": c, "seed": seed, "samples": int(first_idx[edges - 1]) + 1})
 
 
 def er_graph(n: int, m_edges: int, seed: int = 1) -> Graph:
