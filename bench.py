@@ -1,15 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the batched critical-node-detection hot path on GB300.
 
-Default workload (one step = one GA generation on each of two graphs):
+Default workload "throughput" (one step = one GA generation on each of two graphs):
   Barabasi-Albert n=20000, m=4 (79,984 edges) and Holme-Kim n=20000, m=4,
   p=0.3 (79,984 edges); k = 1000 deleted nodes (5% of n); population s = 1024;
   tournament 2, uniform crossover pc = 0.8, per-gene mutation pm = 0.02,
   elitism 1, Philox seed = rank.  Each generation runs elitism, selection,
   crossover, mutation, duplicate repair and the exact fitness (pairwise
   connectivity) of the s-1 children, all in libgapa.so's kernels.
-Metric: exact CND fitness evaluations per second (whole job), with the
-generations per second beside it.
+  Metric: exact CND fitness evaluations per second (whole job), with the
+  generations per second beside it.
+Other workloads (for the design notes, not the headline line):
+  "large": one GA generation on R-MAT scale 20 (2^24 edges), k = 10000, s = 256;
+  "small": one whole run (init + 100 generations, CUDA-graph replay) on
+           BA n=1000, m=3, k = 50, s = 100; metric GA generations per second.
 
 ``--impl reference`` times the CPU oracle (plain C, OpenMP over members) on a
 bounded sample of the same workload.  Under torchrun every rank runs its own
@@ -33,19 +37,36 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "exact CND fitness evals/s"
-K_DEL, POP = 1000, 1024
 PC, PM, TOURN = 0.8, 0.02, 2
 L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    "throughput": dict(k=1000, pop=1024, gens=1, metric="exact CND fitness evals/s", unit="evals/s",
+                       desc="GA generation step on BA(n=20000,m=4) + HK(n=20000,m=4,p=0.3), k=1000, s=1024, "
+                            "tournament 2, pc=0.8, pm=0.02, elitism 1",
+                       graphs=["ba_n20000_m4_seed1 (E=79984)", "hk_n20000_m4_p0.3_seed1 (E=79984)"]),
+    "large": dict(k=10000, pop=256, gens=1, metric="exact CND fitness evals/s", unit="evals/s",
+                  desc="GA generation step on R-MAT scale 20 (2^20 nodes, 2^24 edges, a=0.57 b=0.19 c=0.19), "
+                       "k=10000, s=256, tournament 2, pc=0.8, pm=0.02, elitism 1",
+                  graphs=["rmat_s20_e16777216_seed1"]),
+    "small": dict(k=50, pop=100, gens=100, metric="GA gens/s", unit="gens/s",
+                  desc="whole GA run: init + 100 generations on BA(n=1000,m=3), k=50, s=100, tournament 2, "
+                       "pc=0.8, pm=0.02, elitism 1, Philox seed 0",
+                  graphs=["ba_n1000_m3_seed1 (E=2991)"]),
+}
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def graphs():
+def graphs(workload: str):
     import synth
 
+    if workload == "large":
+        return [synth.rmat_graph(20, 1 << 24, seed=1)]
+    if workload == "small":
+        return [synth.ba_graph(1000, 3, 1)]
     return [synth.ba_graph(20000, 4, 1), synth.hk_graph(20000, 4, 0.3, 1)]
 
 
@@ -65,7 +86,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("fitness.cu", "gapa_internal.cuh"):
+    for f in ("fitness.cu", "fitness_ig.cu", "gapa_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2412_20980_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -133,90 +154,122 @@ def dist_info():
     return ws, rank, local
 
 
-def cpu_baseline(seconds: float = 12.0) -> dict:
-    """The oracle as it stands, on the host cores, on a bounded sample of the
-    workload: oracle generations of the BA graph's population until `seconds`."""
+def workload_config(wl: str, pop=None):
+    w = WORKLOADS[wl]
+    pop = pop or w["pop"]
+    cfg = {"workload": w["desc"], "graphs": w["graphs"], "k": w["k"], "pop": pop,
+           "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+           "parallelism": "dp (independent populations per rank)"}
+    if wl == "small":
+        cfg["gens_per_step"] = w["gens"]
+    else:
+        cfg["evals_per_step"] = len(w["graphs"]) * (pop - 1)
+    return cfg
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle: baseline and reference arm
+# ----------------------------------------------------------------------------
+def oracle_step_fn(wl: str, gs, s_ref: int):
+    """One step of the workload run by the oracle on a population of s_ref."""
     import oracle
 
-    g = graphs()[0]
+    w = WORKLOADS[wl]
     pc_thr, pm_thr = oracle.thresholds(PC, PM)
     nt = oracle.max_threads()
-    pop = oracle.pop_init(g.n, K_DEL, POP, 0)
-    fit = oracle.fitness(g.row_ptr, g.col, pop, nthreads=nt)
+    if wl == "small":
+        def step(t):
+            oracle.run(gs[0].row_ptr, gs[0].col, k=w["k"], pop=s_ref, gens=w["gens"], tourn=TOURN, pc_thr=pc_thr,
+                       pm_thr=pm_thr, seed=0, nthreads=nt)
+            return w["gens"]
+        return step, nt
+    pops = [oracle.pop_init(g.n, w["k"], s_ref, 0) for g in gs]
+    fits = [oracle.fitness(g.row_ptr, g.col, p, nthreads=nt) for g, p in zip(gs, pops)]
+
+    def step(t):
+        for j, g in enumerate(gs):
+            pops[j], fits[j] = oracle.generation(g.row_ptr, g.col, pops[j], fits[j], t + 1, tourn=TOURN,
+                                                 pc_thr=pc_thr, pm_thr=pm_thr, seed=0, nthreads=nt)
+        return len(gs) * (s_ref - 1)
+    return step, nt
+
+
+def sample_population(wl: str, gs, seconds: float) -> int:
+    """Largest population (<= the workload's) whose oracle step fits the time budget."""
+    import oracle
+
+    w = WORKLOADS[wl]
+    if wl == "small":
+        return w["pop"]
+    rows = min(4, w["pop"])
+    pop = oracle.pop_init(gs[0].n, w["k"], rows, 0)
     t0 = time.perf_counter()
-    gens = 0
+    for g in gs:
+        oracle.fitness(g.row_ptr, g.col, pop, nthreads=1)
+    per_member = (time.perf_counter() - t0) / rows / max(1, oracle.max_threads())
+    s = int(seconds / max(per_member, 1e-9))
+    return max(8, min(w["pop"], s))
+
+
+def cpu_baseline(wl: str, gs, seconds: float) -> dict:
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    s_ref = sample_population(wl, gs, seconds / 2)
+    step, nt = oracle_step_fn(wl, gs, s_ref)
+    t0 = time.perf_counter()
+    units, steps = 0, 0
     while True:
-        pop, fit = oracle.generation(g.row_ptr, g.col, pop, fit, gens + 1, tourn=TOURN, pc_thr=pc_thr,
-                                     pm_thr=pm_thr, seed=0, nthreads=nt)
-        gens += 1
+        units += step(steps)
+        steps += 1
         el = time.perf_counter() - t0
-        if el >= seconds:
+        if el >= seconds or (wl == "large" and steps >= 1):
             break
-    evals = gens * (POP - 1)
-    return {"value": evals / el, "unit": "evals/s", "cores": nt, "kind": "oracle",
-            "sample": f"{gens} oracle generations on BA n=20000 (k=1000, s=1024): {evals} evals in {el:.1f} s"}
+    w = WORKLOADS[wl]
+    return {"value": units / el, "unit": w["unit"], "cores": nt, "kind": "oracle",
+            "sample": f"{steps} oracle steps of the workload with population {s_ref} (of {w['pop']}): "
+                      f"{units} {'generations' if wl == 'small' else 'evals'} in {el:.1f} s"}
 
 
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
         return 0
-    import oracle
-
-    gs = graphs()
-    pc_thr, pm_thr = oracle.thresholds(PC, PM)
-    nt = oracle.max_threads()
-    # bounded sample: a sub-population whose step fits the time budget
-    s_ref = POP
-    pops = [oracle.pop_init(g.n, K_DEL, s_ref, 0) for g in gs]
-    fits = [oracle.fitness(g.row_ptr, g.col, p, nthreads=nt) for g, p in zip(gs, pops)]
-
-    def step(t, s):
-        for j, g in enumerate(gs):
-            pops[j], fits[j] = oracle.generation(g.row_ptr, g.col, pops[j][:s], fits[j][:s], t + 1, tourn=TOURN,
-                                                 pc_thr=pc_thr, pm_thr=pm_thr, seed=0, nthreads=nt)
-
-    t0 = time.perf_counter()
-    step(0, s_ref)
-    one = time.perf_counter() - t0
+    wl = args.workload
+    w = WORKLOADS[wl]
+    gs = graphs(wl)
     budget = 150.0
-    total_steps = args.steps + args.warmup
-    if one * total_steps > budget:
-        s_ref = max(16, int(s_ref * budget / (one * total_steps)))
-    for t in range(1, args.warmup):
-        step(t, s_ref)
+    s_ref = sample_population(wl, gs, budget / max(1, args.steps + args.warmup))
+    step, nt = oracle_step_fn(wl, gs, s_ref)
+    for t in range(args.warmup):
+        step(t)
     t0 = time.perf_counter()
+    units = 0
     for t in range(args.steps):
-        step(args.warmup + t, s_ref)
+        units += step(args.warmup + t)
     el = time.perf_counter() - t0
-    evals = args.steps * len(gs) * (s_ref - 1)
-    v = evals / el
-    sample = (f"oracle generations on BA and HK n=20000, k=1000, population {s_ref} (of 1024): "
-              f"{args.steps} steps = {evals} evals in {el:.1f} s")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": workload_config(s_ref),
-            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": nt, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    v = units / el
+    sample = (f"oracle, population {s_ref} (of {w['pop']}): {args.steps} steps = {units} "
+              f"{'generations' if wl == 'small' else 'evals'} in {el:.1f} s")
+    line = {"impl": "reference", "metric": w["metric"], "value": v, "unit": w["unit"], "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": workload_config(wl, s_ref),
+            "cpu_baseline": {"value": v, "unit": w["unit"], "cores": nt, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": w["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def workload_config(pop=POP):
-    return {"workload": "GA generation step on BA(n=20000,m=4) + HK(n=20000,m=4,p=0.3), k=1000, "
-                        f"s={pop}, tournament 2, pc=0.8, pm=0.02, elitism 1",
-            "graphs": ["ba_n20000_m4_seed1 (E=79984)", "hk_n20000_m4_p0.3_seed1 (E=79984)"],
-            "k": K_DEL, "pop": pop, "evals_per_step": 2 * (pop - 1),
-            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)", "parallelism": "dp (independent populations per rank)"}
-
-
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
 def run_gapa(args):
     import torch
 
     from paper_2412_20980_gb300 import Context, make_config
     from paper_2412_20980_gb300 import build as b
 
+    wl = args.workload
+    w = WORKLOADS[wl]
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -229,8 +282,9 @@ def run_gapa(args):
         b.build()
     if dist is not None:
         dist.barrier()
-    gs = graphs()
-    cfg = make_config(k=K_DEL, pop=POP, tourn=TOURN, pc=PC, pm=PM, seed=rank)
+    gs = graphs(wl)
+    k, pop = w["k"], w["pop"]
+    cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=PC, pm=PM, seed=rank)
     ctxs, state = [], []
     for g in gs:
         c = Context(local)
@@ -241,16 +295,22 @@ def run_gapa(args):
         ctxs.append(c)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step(t):
-        for c, st in zip(ctxs, state):
-            c.generation(cfg, t + 1, st[0], st[1], st[2], st[3])
-            st[0], st[2] = st[2], st[0]
-            st[1], st[3] = st[3], st[1]
+    if wl == "small":
+        def step(t):
+            for c in ctxs:
+                c.run(cfg)  # synchronous: init + gens generations, best set copied to the host
+            return len(ctxs) * w["gens"]
+    else:
+        def step(t):
+            for c, st in zip(ctxs, state):
+                c.generation(cfg, t + 1, st[0], st[1], st[2], st[3])
+                st[0], st[2] = st[2], st[0]
+                st[1], st[3] = st[3], st[1]
+            return len(ctxs) * (pop - 1)
 
     for t in range(args.warmup):
         step(t)
     torch.cuda.synchronize()
-    evals_per_step = len(gs) * (POP - 1)
     # --- timed region: device time per step, L2 flushed between steps ---
     sampler = ClockSampler(local)
     sampler.start()
@@ -261,10 +321,11 @@ def run_gapa(args):
     torch.cuda.synchronize()
     for c in ctxs:
         c.profile_begin()
+    units = 0
     for t in range(args.steps):
         flush.fill_(t & 0xFF)
         starts[t].record()
-        step(args.warmup + t)
+        units += step(args.warmup + t)
         ends[t].record()
     torch.cuda.synchronize()
     if dist is not None:
@@ -276,29 +337,30 @@ def run_gapa(args):
     if dist is not None:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
     total_ms = float(t_max.item())
-    for c, st in zip(ctxs, state):
+    for c in ctxs:
         c.sync()
-    value = evals_per_step * args.steps * ws / (total_ms / 1000.0)
-    gens_per_s = len(gs) * args.steps * ws / (total_ms / 1000.0)
+    value = units * ws / (total_ms / 1000.0)
 
     # --- dominant kernel: the fitness launches inside the timed region ---
     fit_ms = sum(p["fitness_ms"] for p in profs)
     fit_launches = sum(p["fitness_launches"] for p in profs)
     fit_evals = sum(p["evals"] for p in profs)
-    op_launches = sum(p["operator_launches"] for p in profs)
-    beval = bytes_per_eval(gs[0].n, gs[0].num_edges, K_DEL)
-    peak, peak_src = measured_peaks()
-    avg_launch_s = fit_ms / 1000.0 / max(1, fit_launches)
-    achieved = beval * (fit_evals / max(1, fit_launches)) / avg_launch_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic("c1"), "kernel": "cc_smem_kernel",
-                "bytes_per_eval": beval, "evals_per_launch": fit_evals / max(1, fit_launches),
-                "avg_launch_ms": avg_launch_s * 1000, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "fitness_share_of_step": fit_ms / max(1e-9, total_ms)}
+    roofline = None
+    if fit_launches:
+        beval = bytes_per_eval(gs[0].n, gs[0].num_edges, k)
+        peak, peak_src = measured_peaks()
+        avg_launch_s = fit_ms / 1000.0 / fit_launches
+        achieved = beval * (fit_evals / fit_launches) / avg_launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic(wl), "kernel": "fitness (cc_smem_kernel / ig_* phases)",
+                    "bytes_per_eval": beval, "evals_per_launch": fit_evals / fit_launches,
+                    "avg_launch_ms": avg_launch_s * 1000,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "fitness_share_of_step": fit_ms / max(1e-9, total_ms)}
 
     # --- end to end through the C ABI with pinned host buffers ---
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and wl != "small":
         hp, pinned = [], []
         for c, st in zip(ctxs, state):
             ts = [st[0].cpu().pin_memory(), st[1].cpu().pin_memory(),
@@ -318,8 +380,8 @@ def run_gapa(args):
                 h[0], h[2] = h[2], h[0]
                 h[1], h[3] = h[3], h[1]
             el += time.perf_counter() - t0
-        per = len(gs) * (POP * K_DEL * 4 + POP * 8)
-        e2e = {"value": evals_per_step * e2e_steps * ws / el, "unit": "evals/s", "h2d_bytes_per_step": per,
+        per = len(gs) * (pop * k * 4 + pop * 8)
+        e2e = {"value": len(gs) * (pop - 1) * e2e_steps * ws / el, "unit": "evals/s", "h2d_bytes_per_step": per,
                "d2h_bytes_per_step": per, "steps": e2e_steps,
                "api": "gapa_generation_host (pinned host population and fitness in and out)"}
 
@@ -329,13 +391,18 @@ def run_gapa(args):
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_seconds)
-    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": workload_config(),
-            "gens_per_s": gens_per_s, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(sum(p["fitness_launches"] + p["operator_launches"] for p in profs)),
-            "clocks": clocks}
+        cpu = cpu_baseline(wl, gs, args.cpu_seconds)
+    line = {"metric": w["metric"], "value": value, "unit": w["unit"], "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": workload_config(wl)}
+    if wl == "small":
+        line["evals_per_s"] = units / w["gens"] * (pop - 1) * ws / (total_ms / 1000.0)
+    else:
+        line["gens_per_s"] = args.steps * len(gs) * ws / (total_ms / 1000.0)
+    line.update({"roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                 "gpu_launches": int(sum(p["fitness_launches"] + p["operator_launches"] for p in profs)),
+                 "clocks": clocks})
     print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
@@ -350,6 +417,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gapa", "reference"], default="gapa")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="throughput")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")

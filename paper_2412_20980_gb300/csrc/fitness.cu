@@ -525,6 +525,8 @@ int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, 
 
 int gapa_fitness_prepare(gapa_ctx* c, int s) {
     const size_t lab_bytes = (size_t)c->g.n * 4;
+    const bool tree = c->fitness_variant != GAPA_FITNESS_EDGES && c->fitness_variant != GAPA_FITNESS_SAMPLED;
+    if (tree) return (c->g.packed16 || lab_bytes <= c->fit_smem_max) ? GAPA_OK : gapa_ig_prepare(c, s);
     if (lab_bytes <= c->fit_smem_max) return GAPA_OK;
     // global labels: process members in waves of at most `wave` CTAs
     const size_t wave = (size_t)(s < 4 * c->num_sms ? s : 4 * c->num_sms);
@@ -556,8 +558,10 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
         case GAPA_FITNESS_SAMPLED:
             return launch_variant<V_SAMPLED>(c, ga, pop, s, k, f, st);
         default:
-            return c->g.packed16 ? launch_variant<V_TREE16>(c, ga, pop, s, k, f, st)
-                                 : launch_variant<V_TREE32>(c, ga, pop, s, k, f, st);
+            if (c->g.packed16) return launch_variant<V_TREE16>(c, ga, pop, s, k, f, st);
+            if ((size_t)n * 4 <= c->fit_smem_max) return launch_variant<V_TREE32>(c, ga, pop, s, k, f, st);
+            // labels too large for shared memory: interleaved member groups in global memory
+            return gapa_launch_fitness_ig(c, pop, s, k, fit, st);
     }
 }
 

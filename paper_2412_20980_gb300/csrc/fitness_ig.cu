@@ -1,0 +1,288 @@
+// Batched fitness for graphs whose labels do not fit in shared memory
+// (Section III-C, Eq. 13; PC(G) of Table "Whole").
+//
+// Members are evaluated in groups of kM = 8 whose labels are interleaved,
+// L[v * 8 + m] for member m of the group, so one 32-byte sector holds a node's
+// labels for the whole group: every non-tree edge costs two sector reads for
+// eight members, and the edge list streams from HBM once per group.  Several
+// groups run per batch, as many as keep their labels within an L2-sized
+// budget.  The phases are those of the shared-memory TREE kernel (tree-parent
+// labels in BFS numbering, deleted nodes, cut with fallback parents, flatten,
+// join along non-tree edges), then sizes are counted into the roots and the
+// int64 sums of C(size, 2) are reduced per member.  Each phase is one
+// grid-wide kernel; thread t of a group handles (node t/8, member t%8) in a
+// grid-stride loop, so the eight lanes of a node share one sector.
+#include <climits>
+
+#include "gapa_internal.cuh"
+
+namespace {
+
+constexpr int kM = 8;
+constexpr int kDead = INT_MIN;
+constexpr int kIgBlock = 256;
+
+__device__ __forceinline__ volatile int* slot(int* L, int x, int m) { return (volatile int*)(L + (size_t)x * kM + m); }
+
+// Path halving on member m's view (parents have smaller BFS numbers).
+__device__ __forceinline__ int ig_find(int* L, int m, int x) {
+    while (true) {
+        const int p = *slot(L, x, m);
+        if (p == x) return x;
+        const int gp = *slot(L, p, m);
+        if (gp == p) return p;
+        *slot(L, x, m) = gp;
+        x = gp;
+    }
+}
+
+__device__ __forceinline__ int ig_root(int* L, int m, int x) {
+    int p = *slot(L, x, m);
+    while (p != x) {
+        x = p;
+        p = *slot(L, x, m);
+    }
+    return x;
+}
+
+__device__ __forceinline__ void ig_unite(int* L, int m, int a, int b) {
+    a = ig_find(L, m, a);
+    b = ig_find(L, m, b);
+    while (a != b) {
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS(L + (size_t)a * kM + m, a, b);
+        if (old == a) return;
+        a = ig_find(L, m, old);
+        b = ig_find(L, m, b);
+    }
+}
+
+struct IgArgs {
+    int n, k, s, member_base;  // members [member_base, member_base + 8 * groups) of the population
+    const int* pop;
+    const int* perm;
+    const int* tparent;
+    const int2* palt;
+    const int* lo_ptr;
+    const int* lo_col;
+    const int2* nontree;
+    int num_nontree;
+    int* L;  // [groups][n][8]
+    long long* fit;
+    int* status;
+};
+
+__device__ __forceinline__ int* group_labels(const IgArgs& a) { return a.L + (size_t)blockIdx.y * a.n * kM; }
+__device__ __forceinline__ size_t gthreads() { return (size_t)gridDim.x * blockDim.x; }
+__device__ __forceinline__ size_t gtid() { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
+
+// labels = tree parents for all eight members; fitness slots cleared
+__global__ void __launch_bounds__(kIgBlock) ig_init_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.n * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) L[t] = __ldg(&a.tparent[t / kM]);
+    if (blockIdx.x == 0 && threadIdx.x < kM) {
+        const int member = a.member_base + blockIdx.y * kM + threadIdx.x;
+        if (member < a.s) a.fit[member] = 0;
+    }
+}
+
+// perturbation P^(A, p) of Eq. 13: deleted nodes of each member
+__global__ void __launch_bounds__(kIgBlock) ig_dead_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.k * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int m = (int)(t / a.k), j = (int)(t % a.k);
+        const int member = a.member_base + blockIdx.y * kM + m;
+        if (member >= a.s) continue;
+        const int d = __ldg(&a.pop[(size_t)member * a.k + j]);
+        if ((unsigned)d < (unsigned)a.n)
+            L[(size_t)__ldg(&a.perm[d]) * kM + m] = kDead;
+        else
+            atomicOr(a.status, GAPA_DEV_BAD_GENE);
+    }
+}
+
+// cut: a live node whose tree parent is deleted takes its first live
+// lower-numbered neighbour, or tops its own piece (deadness is final here)
+__global__ void __launch_bounds__(kIgBlock) ig_cut_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.n * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int v = (int)(t / kM), m = (int)(t % kM);
+        const int p = *slot(L, v, m);
+        if (p == kDead || p == v || *slot(L, p, m) != kDead) continue;
+        int q = v;
+        const int2 pa = __ldg(&a.palt[v]);
+        if (pa.y >= 0) {
+            if (*slot(L, pa.y, m) != kDead) {
+                q = pa.y;
+            } else {
+                const int beg = __ldg(&a.lo_ptr[v]) + 2, end = __ldg(&a.lo_ptr[v + 1]);
+                for (int e = beg; e < end; ++e) {
+                    const int w = __ldg(&a.lo_col[e]);
+                    if (*slot(L, w, m) != kDead) {
+                        q = w;
+                        break;
+                    }
+                }
+            }
+        }
+        *slot(L, v, m) = q;
+    }
+}
+
+// every live node points at the top of its piece / its root (owner writes only)
+__global__ void __launch_bounds__(kIgBlock) ig_flatten_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.n * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int v = (int)(t / kM), m = (int)(t % kM);
+        const int p = *slot(L, v, m);
+        if (p != kDead && p != v) *slot(L, v, m) = ig_root(L, m, p);
+    }
+}
+
+// join the pieces along the non-tree edges: lane m of an edge handles member m
+__global__ void __launch_bounds__(kIgBlock) ig_join_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.num_nontree * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int m = (int)(t % kM);
+        const int2 e = __ldg(&a.nontree[t / kM]);
+        const int la = *slot(L, e.x, m), lb = *slot(L, e.y, m);
+        if (la == lb || la == kDead || lb == kDead) continue;
+        ig_unite(L, m, la, lb);
+    }
+}
+
+// roots become counters (-1 each)
+__global__ void __launch_bounds__(kIgBlock) ig_roots_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.n * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int v = (int)(t / kM), m = (int)(t % kM);
+        if (*slot(L, v, m) == v) *slot(L, v, m) = -1;
+    }
+}
+
+// every other live node adds itself to its root's counter; a thread keeps a
+// run of equal roots in a register and flushes it when the root changes
+__global__ void __launch_bounds__(kIgBlock) ig_count_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.n * kM;
+    const size_t stride = gthreads();  // a multiple of 8: a thread keeps its member
+    const int m = (int)(gtid() % kM);
+    int run_root = -1, run = 0;
+    for (size_t t = gtid(); t < total; t += stride) {
+        const int v = (int)(t / kM);
+        const int l = *slot(L, v, m);
+        if (l < 0) continue;  // deleted node or a root (counter)
+        if (l != run_root) {
+            if (run) atomicAdd(L + (size_t)run_root * kM + m, -run);
+            run_root = l;
+            run = 0;
+        }
+        ++run;
+    }
+    if (run) atomicAdd(L + (size_t)run_root * kM + m, -run);
+}
+
+// int64 sum of C(size, 2) over roots, per member: block reduce, then one atomic per member
+__global__ void __launch_bounds__(kIgBlock) ig_sum_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    __shared__ unsigned long long acc_m[kM];
+    if (threadIdx.x < kM) acc_m[threadIdx.x] = 0ull;
+    __syncthreads();
+    const size_t total = (size_t)a.n * kM;
+    const int m = (int)(gtid() % kM);
+    unsigned long long acc = 0;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int l = *slot(L, (int)(t / kM), m);
+        if (l < 0 && l != kDead) {
+            const unsigned long long c = (unsigned long long)(-(long long)l);
+            acc += c * (c - 1) / 2;
+        }
+    }
+    // lanes with equal (lane % 8) share a member: reduce over lanes 8 apart
+    acc += __shfl_down_sync(0xffffffffu, acc, 16);
+    acc += __shfl_down_sync(0xffffffffu, acc, 8);
+    if ((threadIdx.x & 31) < kM) atomicAdd(&acc_m[threadIdx.x & 31], acc);
+    __syncthreads();
+    if (threadIdx.x < kM) {
+        const int member = a.member_base + blockIdx.y * kM + threadIdx.x;
+        if (member < a.s) atomicAdd((unsigned long long*)&a.fit[member], acc_m[threadIdx.x]);
+    }
+}
+
+constexpr size_t kIgLabelBudget = 48ull << 20;  // labels of a batch of groups kept within this many bytes
+
+int ig_groups_per_batch(int n, int s) {
+    const size_t per_group = (size_t)n * kM * sizeof(int);
+    size_t g = kIgLabelBudget / per_group;
+    if (g < 1) g = 1;
+    const size_t need = ((size_t)s + kM - 1) / kM;
+    if (g > need) g = need;
+    if (g > 65535) g = 65535;
+    return (int)g;
+}
+
+}  // namespace
+
+int gapa_ig_prepare(gapa_ctx* c, int s) {
+    const int groups = ig_groups_per_batch(c->g.n, s < 1 ? 1 : s);
+    return gapa_reserve((void**)&c->labels, &c->labels_cap, (size_t)groups * c->g.n * kM, sizeof(int));
+}
+
+int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st) {
+    const int n = c->g.n;
+    int rc = gapa_ig_prepare(c, s);
+    if (rc != GAPA_OK) return rc;
+    const int gpb = ig_groups_per_batch(n, s);
+    IgArgs a;
+    a.n = n;
+    a.k = k;
+    a.s = s;
+    a.pop = pop;
+    a.perm = c->g.perm;
+    a.tparent = c->g.tparent;
+    a.palt = c->g.palt;
+    a.lo_ptr = c->g.lo_ptr;
+    a.lo_col = c->g.lo_col;
+    a.nontree = reinterpret_cast<const int2*>(c->g.nontree);
+    a.num_nontree = c->g.num_nontree;
+    a.L = c->labels;
+    a.fit = reinterpret_cast<long long*>(fit);
+    a.status = c->status;
+    // grid: enough CTAs to fill the GPU a few times over, a multiple of the SM count
+    const size_t work = (size_t)n * kM;
+    int bx = (int)((work + kIgBlock - 1) / kIgBlock);
+    const int cap = c->num_sms * 8;
+    const int per_batch_cap = gpb > 0 ? (cap + gpb - 1) / gpb : cap;
+    if (bx > per_batch_cap) bx = per_batch_cap < 1 ? 1 : per_batch_cap;
+    const size_t ework = (size_t)a.num_nontree * kM;
+    int bxe = (int)((ework + kIgBlock - 1) / kIgBlock);
+    if (bxe > per_batch_cap) bxe = per_batch_cap < 1 ? 1 : per_batch_cap;
+    if (bxe < 1) bxe = 1;
+    const int groups_total = (s + kM - 1) / kM;
+    for (int g0 = 0; g0 < groups_total; g0 += gpb) {
+        const int gcount = groups_total - g0 < gpb ? groups_total - g0 : gpb;
+        a.member_base = g0 * kM;
+        const dim3 grid(bx, gcount), egrid(bxe, gcount);
+        ig_init_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_dead_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_cut_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        if (a.num_nontree > 0) ig_join_kernel<<<egrid, kIgBlock, 0, st>>>(a);
+        ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_roots_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_count_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_sum_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        GAPA_CUDA(cudaGetLastError());
+    }
+    return GAPA_OK;
+}

@@ -167,6 +167,8 @@ struct GaParams {
 
 int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st);
 int gapa_fitness_prepare(gapa_ctx* c, int s);  // allocate scratch before capture
+int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st);
+int gapa_ig_prepare(gapa_ctx* c, int s);
 int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);
 int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,
                           int32_t* pop_out, int64_t* fit_out, cudaStream_t st);

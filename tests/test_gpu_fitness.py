@@ -31,6 +31,7 @@ def ctx(request):
     b.build()
     c = Context(0)
     c.set_fitness_kernel({"tree": FITNESS_TREE, "sampled": FITNESS_SAMPLED, "edges": FITNESS_EDGES}[request.param])
+    c.variant_name = request.param
     yield c
     torch.cuda.synchronize()
     c.close()
@@ -96,6 +97,30 @@ def test_global_label_path(ctx, n, k):
     pop = synth.random_deletion_sets(g.n, k, 40, 2)
     want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
     assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
+def test_global_label_partial_group(ctx):
+    """37 members: the last interleaved group of eight is partial."""
+    g = synth.relabel(synth.hk_graph(70000, 3, 0.3, 5), 3)
+    pop = synth.random_deletion_sets(g.n, 3500, 37, 9)
+    want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
+    assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
+def test_full_size_rmat_sampled_members(ctx):
+    """R-MAT scale 20 with 2^24 edges, k = 10000, s = 256 (the large configuration, evaluated as
+    one batch); eight members spread over the batch are checked against the oracle one by one."""
+    if ctx.variant_name != "tree":
+        pytest.skip("full-size check runs on the default kernel only")
+    g = synth.rmat_graph(20, 1 << 24, seed=1)
+    pop = synth.random_deletion_sets(g.n, 10000, 256, 0)
+    got = gpu_fit(ctx, g, pop)
+    rows = [0, 7, 8, 100, 127, 128, 200, 255]
+    want = oracle.fitness(g.row_ptr, g.col, pop[rows], nthreads=oracle.max_threads())
+    assert np.array_equal(got[rows], want)
+    # properties at any size: PC <= C(n-k, 2); and a hub-heavy member reduces PC
+    n, k = g.n, 10000
+    assert np.all(got <= (n - k) * (n - k - 1) // 2)
 
 
 def test_global_label_path_rmat(ctx):
