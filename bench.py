@@ -397,7 +397,7 @@ def run_gapa(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": workload_config(wl)}
     if wl == "small":
-        line["evals_per_s"] = units / w["gens"] * (pop - 1) * ws / (total_ms / 1000.0)
+        line["evals_per_s"] = units * (pop - 1) * ws / (total_ms / 1000.0)
     else:
         line["gens_per_s"] = args.steps * len(gs) * ws / (total_ms / 1000.0)
     line.update({"roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
