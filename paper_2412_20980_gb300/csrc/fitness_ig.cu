@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kIgBlock) ig_join_kernel(IgArgs a) {
     const size_t total = (size_t)a.num_nontree * kM;
     for (size_t t = gtid(); t < total; t += gthreads()) {
         const int m = (int)(t % kM);
-        const int2 e = __ldg(&a.nontree[t / kM]);
+        const int2 e = __ldcs(&a.nontree[t / kM]);  // streamed once per group: evict first, keep labels in L2
         const int la = *slot(L, e.x, m), lb = *slot(L, e.y, m);
         if (la == lb || la == kDead || lb == kDead) continue;
         ig_unite(L, m, la, lb);
