@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(kIgBlock) ig_join_kernel(IgArgs a) {
     for (size_t t = gtid(); t < total; t += gthreads()) {
         const int m = (int)(t % kM);
         const int2 e = __ldcs(&a.nontree[t / kM]);  // streamed once per group: evict first, keep labels in L2
-        const int la = *slot(L, e.x, m), lb = *slot(L, e.y, m);
+        // quick check through L1: a stale label is still an ancestor (or the node itself) at some
+        // earlier moment, so equal labels prove a common tree; unequal ones go to union-find
+        const int la = L[(size_t)e.x * kM + m], lb = L[(size_t)e.y * kM + m];
         if (la == lb || la == kDead || lb == kDead) continue;
         ig_unite(L, m, la, lb);
     }
