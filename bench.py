@@ -49,6 +49,11 @@ WORKLOADS = {
                   desc="GA generation step on R-MAT scale 20 (2^20 nodes, 2^24 edges, a=0.57 b=0.19 c=0.19), "
                        "k=10000, s=256, tournament 2, pc=0.8, pm=0.02, elitism 1",
                   graphs=["rmat_s20_e16777216_seed1"]),
+    "batched": dict(k=0, pop=0, gens=200, metric="exact CND fitness evals/s (aggregate)", unit="evals/s",
+                    desc="64 independent GA instances, BA graphs with n log-uniform in [500, 50000], m in 2..5, "
+                         "k = round(0.05 n), populations from {32,64,128,256,512}, 200 generations each, "
+                         "one batched run per step (CUDA-graph replay, persistent fitness kernel, autotuned teams)",
+                    graphs=["64 BA instances (synth.batched_instances, seed 0)"]),
     "small": dict(k=50, pop=100, gens=100, metric="GA gens/s", unit="gens/s",
                   desc="whole GA run: init + 100 generations on BA(n=1000,m=3), k=50, s=100, tournament 2, "
                        "pc=0.8, pm=0.02, elitism 1, Philox seed 0",
@@ -60,9 +65,17 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def batched_specs():
+    import synth
+
+    return synth.batched_instances(64, seed=0)
+
+
 def graphs(workload: str):
     import synth
 
+    if workload == "batched":
+        return [synth.ba_graph(d["n"], d["m"], d["graph_seed"]) for d in batched_specs()]
     if workload == "large":
         return [synth.rmat_graph(20, 1 << 24, seed=1)]
     if workload == "small":
@@ -283,6 +296,8 @@ def run_gapa(args):
     if dist is not None:
         dist.barrier()
     gs = graphs(wl)
+    if wl == "batched":
+        return run_batched(args, gs, dist, ws, rank, local, dev)
     k, pop = w["k"], w["pop"]
     cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=PC, pm=PM, seed=rank)
     ctxs, state = [], []
@@ -408,6 +423,84 @@ def run_gapa(args):
         c.close()
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_batched(args, gs, dist, ws, rank, local, dev):
+    """64 instances per step: one gapa_batch_run of 200 generations (all on the device)."""
+    import torch
+
+    from paper_2412_20980_gb300 import Batch, Context, make_config
+
+    w = WORKLOADS["batched"]
+    specs = batched_specs()
+    ctxs, cfgs = [], []
+    for d, g in zip(specs, gs):
+        c = Context(local)
+        c.graph_upload(g.row_ptr, g.col)
+        ctxs.append(c)
+        cfgs.append(make_config(k=d["k"], pop=d["pop"], tourn=TOURN, pc=PC, pm=PM, seed=1000 * rank + d["index"]))
+    bt = Batch(ctxs, cfgs)
+    t0 = time.perf_counter()
+    bt.autotune(os.path.join(ROOT, ".cache", "batch_teams.json") if os.path.isdir(os.path.join(ROOT, ".cache"))
+                else None)
+    tune_s = time.perf_counter() - t0
+    gens = w["gens"]
+    evals_per_run = sum(d["pop"] + (d["pop"] - 1) * gens for d in specs)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        bt.run(gens)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = 0.0
+    for t in range(args.steps):
+        flush.fill_(t & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = bt.run(gens)  # synchronous: results are on the host when it returns
+        wall += time.perf_counter() - t0
+    clocks = sampler.stop()
+    t_max = torch.tensor([wall], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    wall = float(t_max.item())
+    value = evals_per_run * args.steps * ws / wall
+    if rank != 0:
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        # bounded sample: the four smallest instances, 20 generations each
+        idx = sorted(range(len(specs)), key=lambda i: specs[i]["n"])[:4]
+        t0 = time.perf_counter()
+        units = 0
+        for i in idx:
+            d = specs[i]
+            pc_thr, pm_thr = oracle.thresholds(PC, PM)
+            oracle.run(gs[i].row_ptr, gs[i].col, k=d["k"], pop=d["pop"], gens=20, tourn=TOURN, pc_thr=pc_thr,
+                       pm_thr=pm_thr, seed=d["index"], nthreads=oracle.max_threads())
+            units += d["pop"] + (d["pop"] - 1) * 20
+        el = time.perf_counter() - t0
+        cpu = {"value": units / el, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"oracle runs of the 4 smallest instances, 20 generations each: {units} evals in {el:.1f} s"}
+    line = {"metric": w["metric"], "value": value, "unit": w["unit"], "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w["desc"], "instances": len(specs), "generations": gens,
+                       "evals_per_step": evals_per_run, "teams": bt.teams, "autotune_s": tune_s,
+                       "sum_n": sum(d["n"] for d in specs), "l2": "flushed between timed steps"},
+            "gens_per_s": len(specs) * gens * args.steps * ws / wall, "roofline": None, "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(8 * len(specs) * (gens + 2) + 4 * sum(d["k"] for d in specs)),
+                    "note": "gapa_batch_run is host-synchronous: the timed wall time includes the copies of best "
+                            "sets, fitness and trajectories"},
+            "clocks": clocks, "best_fit_first8": out["best_fit"][:8].tolist()}
+    print(json.dumps(line), flush=True)
+    bt.close()
     return 0
 
 

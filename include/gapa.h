@@ -140,6 +140,41 @@ int gapa_generation_host(gapa_ctx* ctx, const gapa_config* cfg, int32_t g, const
 int gapa_run(gapa_ctx* ctx, const gapa_config* cfg, int32_t* best_set_host, int64_t* best_fit,
              int64_t* traj_best_fit, int32_t* final_pop_dev);
 
+/* ---- Batched runs: many independent instances advanced together ----------
+ * The paper runs one GA per process (acceleration modes, Section III-D); a
+ * batch advances `num` independent GA instances - each with its own graph
+ * (an uploaded context) and configuration - with one operator launch, one
+ * persistent fitness launch over a work queue of (instance, members) packets
+ * and one record launch per generation, two generations captured as a CUDA
+ * graph and replayed.  Every instance's trajectory, final population and best
+ * set equal those of gapa_run() on its own context and configuration.
+ * Limits: every graph must fit the shared-memory fitness path (at most
+ * ~57,000 nodes; GAPA_ERR_INVALID_ARG otherwise); all contexts on one device;
+ * the batch borrows the contexts (they must outlive it) and runs on the first
+ * context's stream. */
+typedef struct gapa_batch gapa_batch;
+
+int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, const gapa_config* cfgs);
+void gapa_batch_destroy(gapa_batch* batch);
+
+/* Members per CTA of the persistent fitness kernel (1, 2, 4 or 8 teams of
+ * 1024/teams threads) per instance; results do not depend on it. */
+int gapa_batch_set_teams(gapa_batch* batch, const int32_t* teams /* [num] */);
+int gapa_batch_get_teams(gapa_batch* batch, int32_t* teams /* [num] */);
+
+/* Autotuner: for every graph-size bucket present (n <= 2048, 4096, 8192,
+ * 16384, 32768, 65536) time each feasible team count on the initial
+ * population and keep the fastest; choices are cached per device name in
+ * the JSON file `cache_path` (NULL: no cache). */
+int gapa_batch_autotune(gapa_batch* batch, const char* cache_path);
+
+/* Run every instance for `gens` generations from its initialisation.
+ * Outputs (host): best_fit[num]; best_sets = the k_i genes of each
+ * instance's best member, concatenated in instance order, each ascending
+ * (may be NULL); traj[num][gens+1] the lowest fitness after initialisation
+ * and after every generation (may be NULL).  Synchronous. */
+int gapa_batch_run(gapa_batch* batch, int32_t gens, int64_t* best_fit, int32_t* best_sets, int64_t* traj);
+
 /* Fitness kernel selection (all are exact and give identical results):
  * TREE starts every member from a BFS spanning forest of G (numbered so that
  * parents precede children), cuts it at the deleted nodes and then joins the

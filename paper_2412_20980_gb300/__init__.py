@@ -4,6 +4,7 @@ The compute path is libgapa.so (hand-written sm_103a CUDA kernels behind a C
 ABI, declared in include/gapa.h); ``gapa`` is its ctypes binding.
 """
 from .gapa import (
+    Batch,
     Config,
     Context,
     GapaError,
@@ -14,4 +15,4 @@ from .gapa import (
     threshold,
 )
 
-__all__ = ["Config", "Context", "GapaError", "EXPORTS", "FLAG_ROWWISE", "load", "make_config", "threshold"]
+__all__ = ["Batch", "Config", "Context", "GapaError", "EXPORTS", "FLAG_ROWWISE", "load", "make_config", "threshold"]

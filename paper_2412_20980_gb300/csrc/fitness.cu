@@ -14,53 +14,15 @@
 #include <mutex>
 
 #include "gapa_internal.cuh"
+#include "tree16.cuh"
 
 namespace {
 
 constexpr int kDead = INT_MIN;
-
-// Path halving.  Invariant: a non-root's parent has a smaller id, so the
-// walk terminates; roots change only by CAS in uf_unite.
-__device__ __forceinline__ int uf_find(volatile int* lab, int x) {
-    while (true) {
-        const int p = lab[x];
-        if (p == x) return x;
-        const int gp = lab[p];
-        if (gp == p) return p;
-        lab[x] = gp;
-        x = gp;
-    }
-}
-
-// Root of x by a read-only walk.  Used once no hooking is left: every write
-// then is an owner storing its node's final root, so no walk can leave a
-// stale (non-root) ancestor behind, which path halving could.
-__device__ __forceinline__ int uf_root(volatile int* lab, int x) {
-    int p = lab[x];
-    while (p != x) {
-        x = p;
-        p = lab[x];
-    }
-    return x;
-}
-
-// Union of the trees of live nodes a and b: hook the larger root under the
-// smaller with a CAS on the root's slot; retry from the new parent on a race.
-__device__ __forceinline__ void uf_unite(volatile int* lab, int a, int b) {
-    a = uf_find(lab, a);
-    b = uf_find(lab, b);
-    while (a != b) {
-        if (a < b) {
-            const int t = a;
-            a = b;
-            b = t;
-        }
-        const int old = atomicCAS((int*)&lab[a], a, b);
-        if (old == a) return;
-        a = uf_find(lab, old);
-        b = uf_find(lab, b);
-    }
-}
+using gapa_dev::bm_test;
+using gapa_dev::uf_find;
+using gapa_dev::uf_root;
+using gapa_dev::uf_unite;
 
 __device__ __forceinline__ void edge_op(volatile int* lab, int u, int v) {
     if (lab[u] == kDead || lab[v] == kDead) return;
@@ -167,14 +129,14 @@ __device__ __forceinline__ void hook_sampled(volatile int* lab, int n, const int
     __syncthreads();
 }
 
-// Hooking, tree: labels start as the parents of a BFS spanning forest of G in
+// Hooking, tree (32-bit ids; the 16-bit shared-memory pipeline is in
+// tree16.cuh): labels start as the parents of a BFS spanning forest of G in
 // BFS numbering (parent < child), so the forest already joins every live node
 // to its live ancestors.  A live node whose tree parent is deleted takes its
 // first live lower-numbered neighbour as parent instead (the top of a new
 // piece only if there is none).  Each piece is flattened onto its top node,
 // and the pieces are joined along the non-tree edges; an edge whose endpoints
-// already share a label costs two shared-memory reads.  kDeadV marks deleted
-// nodes (-1 for the 16-bit counting path, INT_MIN otherwise).
+// already share a label costs two shared-memory reads.
 template <int kDeadV>
 __device__ __forceinline__ void join_edge(volatile int* lab, int a, int b) {
     const int la = lab[a], lb = lab[b];
@@ -182,87 +144,13 @@ __device__ __forceinline__ void join_edge(volatile int* lab, int a, int b) {
     uf_unite(lab, la, lb);
 }
 
-// Initial labels with a deleted-node bitmap (shared memory, n bits) built
-// first.  A live node takes its tree parent; a node whose tree parent is
-// deleted takes its first live lower-numbered neighbour (the pair array holds
-// the second one, the full list is read only beyond it), or itself.  Every
-// label is smaller than its node (or equal at a top).
-__device__ __forceinline__ bool bm_test(const unsigned* bm, int v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
-
-__device__ __forceinline__ void init_tree_labels_bitmap(volatile int* lab, unsigned* dead, int n,
-                                                        const int2* __restrict__ palt,
-                                                        const int* __restrict__ lo_ptr,
-                                                        const int* __restrict__ lo_col,
-                                                        const int* __restrict__ perm,
-                                                        const int* __restrict__ genes, int k, int* status) {
-    const int tid = threadIdx.x, T = blockDim.x;
-    const int words = (n + 31) >> 5;
-    for (int w = tid; w < words; w += T) dead[w] = 0u;
-    __syncthreads();
-    // perturbation P^(A, p) of Eq. 13 in BFS numbering
-    for (int j = tid; j < k; j += T) {
-        const int d = __ldg(&genes[j]);
-        if ((unsigned)d < (unsigned)n) {
-            const int b = __ldg(&perm[d]);
-            atomicOr(&dead[b >> 5], 1u << (b & 31));
-        } else {
-            atomicOr(status, GAPA_DEV_BAD_GENE);
-        }
-    }
-    __syncthreads();
-    // four nodes per thread per step, their pair loads issued together
-    constexpr int kU = 4;
-    for (int base = tid; base < n; base += kU * T) {
-        int2 pa[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int v = base + u * T;
-            pa[u] = v < n ? __ldg(&palt[v]) : make_int2(0, -1);
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int v = base + u * T;
-            if (v >= n) break;
-            int q;
-            if (bm_test(dead, v)) {
-                q = -1;
-            } else if (pa[u].x == v || !bm_test(dead, pa[u].x)) {
-                q = pa[u].x;  // forest root (itself) or live parent
-            } else {
-                // parent deleted: first live lower-numbered neighbour after it
-                q = v;
-                if (pa[u].y >= 0) {
-                    if (!bm_test(dead, pa[u].y)) {
-                        q = pa[u].y;
-                    } else {
-                        const int beg = __ldg(&lo_ptr[v]) + 2, end = __ldg(&lo_ptr[v + 1]);
-                        for (int e = beg; e < end; ++e) {
-                            const int w = __ldg(&lo_col[e]);
-                            if (!bm_test(dead, w)) {
-                                q = w;
-                                break;
-                            }
-                        }
-                    }
-                }
-            }
-            lab[v] = q;
-        }
-    }
-    __syncthreads();
-}
-
 template <bool kPacked16, int kDeadV>
 __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* __restrict__ tparent,
                                           const int2* __restrict__ palt,
                                           const int* __restrict__ lo_ptr, const int* __restrict__ lo_col,
                                           const int* __restrict__ perm, const void* __restrict__ nontree,
-                                          int num_nontree, const int* __restrict__ genes, int k, int* status,
-                                          unsigned* dead_bitmap) {
+                                          int num_nontree, const int* __restrict__ genes, int k, int* status) {
     const int tid = threadIdx.x, T = blockDim.x;
-    if (dead_bitmap) {
-        init_tree_labels_bitmap(lab, dead_bitmap, n, palt, lo_ptr, lo_col, perm, genes, k, status);
-    } else {
     for (int v = tid; v < n; v += T) lab[v] = __ldg(&tparent[v]);
     __syncthreads();
     // perturbation P^(A, p) of Eq. 13 in BFS numbering
@@ -292,7 +180,6 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
         lab[v] = q;
     }
     __syncthreads();
-    }
     // flatten every piece onto its top node (owner writes only)
     for (int v = tid; v < n; v += T) {
         const int p = lab[v];
@@ -344,46 +231,6 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
         }
     }
     __syncthreads();
-}
-
-// Counting for n <= 65536 (ids fit 16 bits): a root's slot becomes
-// (members below it) << 16 | its id, built in one pass in which every live
-// non-root walks to its root (masking the count bits) and adds itself, warp-
-// aggregated; deleted nodes hold -1, which no root slot can equal because a
-// root id is below 65535.  Then the int64 sum of C(size, 2) over roots.
-__device__ __forceinline__ void count_pc16(volatile int* lab, int n, long long* out, long long* red) {
-    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
-    for (int base = 0; base < n; base += T) {
-        const int v = base + tid;
-        int key = -1;
-        if (v < n) {
-            // a root's own slot may already carry count bits: classify by the
-            // masked id; a non-root's slot is never written in this pass
-            const int l = lab[v];
-            if (l != -1 && (l & 0xFFFF) != v) {
-                int x = l & 0xFFFF;
-                while (true) {
-                    const int q = lab[x] & 0xFFFF;
-                    if (q == x) break;
-                    x = q;
-                }
-                key = x;
-            }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd((unsigned*)&lab[key], (unsigned)__popc(peers) << 16);
-    }
-    __syncthreads();
-    long long acc = 0;
-    for (int v = tid; v < n; v += T) {
-        const unsigned l = (unsigned)lab[v];
-        if (l != 0xFFFFFFFFu && (int)(l & 0xFFFFu) == v) {
-            const long long c = (long long)(l >> 16) + 1;
-            acc += c * (c - 1) / 2;
-        }
-    }
-    const long long tot = block_sum_ll(acc, red);
-    if (tid == 0) *out = tot;
 }
 
 // Component sizes and the int64 sum of C(size, 2) (PC(G) of Table "Whole").
@@ -453,15 +300,16 @@ template <int kVar>
 __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k,
                                           long long* out, int* status, long long* red, int* sh_root) {
     if (kVar == V_TREE16) {
-        // shared-memory path: the deleted-node bitmap sits right after the labels
-        hook_tree<true, -1>(lab, g.n, g.tparent, g.palt, g.lo_ptr, g.lo_col, g.perm, g.nontree,
-                            g.num_nontree, genes, k, status, (unsigned*)(lab + g.n));
-        count_pc16(lab, g.n, out, red);
+        // the whole CTA is one team; the deleted-node bitmap sits right after the labels
+        const gapa_dev::Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
+        const gapa_dev::Tree16Graph t16{g.n,      g.perm,   g.palt, g.lo_ptr, g.lo_col,
+                                        (const unsigned*)g.nontree, g.num_nontree};
+        gapa_dev::tree16_member(tm, lab, (unsigned*)(lab + g.n), t16, genes, k, out, red, status);
         return;
     }
     if (kVar == V_TREE32) {
         hook_tree<false, kDead>(lab, g.n, g.tparent, g.palt, g.lo_ptr, g.lo_col, g.perm,
-                                g.nontree, g.num_nontree, genes, k, status, nullptr);
+                                g.nontree, g.num_nontree, genes, k, status);
     } else {
         init_labels(lab, g.n, genes, k, status);
         if (kVar == V_SAMPLED)
@@ -688,4 +536,64 @@ extern "C" int gapa_fitness_noalloc(int device, void* cuda_stream, int32_t n, in
     if (h & GAPA_DEV_BAD_EDGE) return restore(gapa_fail(GAPA_ERR_DEVICE, "an edge endpoint outside [0, n)"));
     if (h & GAPA_DEV_BAD_GENE) return restore(gapa_fail(GAPA_ERR_DEVICE, "a gene outside [0, n)"));
     return restore(GAPA_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Batched instances: a persistent kernel pulls packets (instance, members)
+// from a work queue ordered by decreasing graph size; a CTA of 1024 threads
+// splits into `teams` teams of 1024/teams threads, each evaluating one member
+// of the packet with its own slice of shared memory and its own named barrier
+// (1 + team), so small graphs run several members per CTA.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(1024, 1) fitness_batched_kernel(const BatchDesc* __restrict__ d,
+                                                                  const BatchPacket* __restrict__ pk, int npk,
+                                                                  int* head, int buf, unsigned smem_bytes,
+                                                                  int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long red[8][32];
+    __shared__ int sh_p;
+    while (true) {
+        if (threadIdx.x == 0) sh_p = atomicAdd(head, 1);
+        __syncthreads();
+        const int p = sh_p;
+        __syncthreads();
+        if (p >= npk) break;
+        const BatchPacket q = pk[p];
+        const BatchDesc& bd = d[q.b];
+        const int T = (int)blockDim.x / q.teams;
+        const int team = (int)threadIdx.x / T;
+        if (team < q.cnt) {
+            const gapa_dev::Team tm{(int)threadIdx.x - team * T, T, 1 + team};
+            const unsigned slice = (smem_bytes / (unsigned)q.teams) & ~15u;
+            int* lab = reinterpret_cast<int*>(smem + (size_t)team * slice);
+            const gapa_dev::Tree16Graph g{bd.n, bd.perm, bd.palt, bd.lo_ptr, bd.lo_col, bd.nontree, bd.num_nontree};
+            const int member = q.i0 + team;
+            gapa_dev::tree16_member(tm, lab, reinterpret_cast<unsigned*>(lab + bd.n), g,
+                                    bd.pop[buf] + (size_t)member * bd.p.k, bd.p.k,
+                                    reinterpret_cast<long long*>(bd.fit[buf]) + member, red[team], status);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int gapa_launch_fitness_batched(const BatchDesc* d, const BatchPacket* pk, int npk, int* head, int buf,
+                                size_t smem, int grid, int* status, cudaStream_t st) {
+    if (npk <= 0) return GAPA_OK;
+    GAPA_CUDA(cudaMemsetAsync(head, 0, sizeof(int), st));
+    fitness_batched_kernel<<<grid, 1024, smem, st>>>(d, pk, npk, head, buf, (unsigned)smem, status);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_fitness_batched_init(size_t optin, size_t* max_dyn) {
+    return gapa_set_smem_limit((const void*)fitness_batched_kernel, optin, max_dyn);
+}
+
+int gapa_fitness_batched_occupancy(size_t smem, int* blocks_per_sm) {
+    GAPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fitness_batched_kernel, 1024, smem));
+    return GAPA_OK;
 }

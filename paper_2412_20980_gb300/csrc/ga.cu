@@ -124,10 +124,9 @@ __device__ __forceinline__ void clear_bitmap(unsigned* kept, int n) {
     for (int w = threadIdx.x; w < words; w += blockDim.x) kept[w] = 0u;
 }
 
-// Population initialisation (Eq. 2): every position open, candidates from tag INIT.
-__global__ void __launch_bounds__(kGaBlock) init_kernel(GaParams p, int* __restrict__ pop) {
+// Population initialisation (Eq. 2) of row i: every position open, candidates from tag INIT.
+__device__ void init_row(const GaParams& p, int i, int* __restrict__ pop) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int i = blockIdx.x;
     RowSmem sm = carve(smem, p.n, p.k);
     clear_bitmap(sm.kept, p.n);
     for (int j = threadIdx.x; j < p.k; j += blockDim.x) sm.holes[j] = j;
@@ -136,6 +135,8 @@ __global__ void __launch_bounds__(kGaBlock) init_kernel(GaParams p, int* __restr
     InitCand cand{p.key, i, p.n};
     repair_warp(sm.kept, sm.holes, p.k, pop + (size_t)i * p.k, cand, p.key, i, 0, p.n);
 }
+
+__global__ void __launch_bounds__(kGaBlock) init_kernel(GaParams p, int* __restrict__ pop) { init_row(p, blockIdx.x, pop); }
 
 // Tournament of size t for parent slot `slot` of child i.
 __device__ int tournament(const GaParams& p, int i, int g, int slot, const long long* fit) {
@@ -201,16 +202,13 @@ __device__ void block_argmin(const long long* __restrict__ fit, int s, long long
     *out_idx = si[0];
 }
 
-// One generation's rows: CTA 0 = elite copy, CTA i >= 1 = child i.
-__global__ void __launch_bounds__(kGaBlock) offspring_kernel(GaParams p, const int* __restrict__ pop_in,
-                                                             const long long* __restrict__ fit_in,
-                                                             int* __restrict__ pop_out,
-                                                             long long* __restrict__ fit_out, int* status) {
+// Row i of one generation g: row 0 = elite copy, row i >= 1 = child i.
+__device__ void offspring_row(const GaParams& p, int i, int g, const int* __restrict__ pop_in,
+                              const long long* __restrict__ fit_in, int* __restrict__ pop_out,
+                              long long* __restrict__ fit_out, int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sh_parent[2];
     __shared__ int sh_warp_cnt[kGaBlock / 32];
-    const int i = blockIdx.x;
-    const int g = p.g_ptr ? *p.g_ptr : p.g;
     const int n = p.n, k = p.k;
     if (i == 0) {
         long long v;
@@ -295,6 +293,48 @@ __global__ void __launch_bounds__(kGaBlock) offspring_kernel(GaParams p, const i
     repair_warp(sm.kept, sm.holes, total, C, cand, p.key, i, g, n);
 }
 
+__global__ void __launch_bounds__(kGaBlock) offspring_kernel(GaParams p, const int* __restrict__ pop_in,
+                                                             const long long* __restrict__ fit_in,
+                                                             int* __restrict__ pop_out,
+                                                             long long* __restrict__ fit_out, int* status) {
+    offspring_row(p, blockIdx.x, p.g_ptr ? *p.g_ptr : p.g, pop_in, fit_in, pop_out, fit_out, status);
+}
+
+// ---------------------------------------------------------------------------
+// Batched instances: one launch covers the rows of every instance; rows[r] =
+// (instance, row) and each instance has its own parameters and buffers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGaBlock) init_batched_kernel(const BatchDesc* __restrict__ d,
+                                                                const int2* __restrict__ rows, int buf) {
+    const int2 r = rows[blockIdx.x];
+    const BatchDesc& bd = d[r.x];
+    init_row(bd.p, r.y, bd.pop[buf]);
+}
+
+__global__ void __launch_bounds__(kGaBlock) offspring_batched_kernel(const BatchDesc* __restrict__ d,
+                                                                     const int2* __restrict__ rows, int src,
+                                                                     const int* gen, int* status) {
+    const int2 r = rows[blockIdx.x];
+    const BatchDesc& bd = d[r.x];
+    offspring_row(bd.p, r.y, *gen, bd.pop[src], reinterpret_cast<const long long*>(bd.fit[src]), bd.pop[src ^ 1],
+                  reinterpret_cast<long long*>(bd.fit[src ^ 1]), status);
+}
+
+// Per instance: trajectory[gen] = lowest fitness, best = its index.
+__global__ void __launch_bounds__(1024) record_batched_kernel(const BatchDesc* __restrict__ d, int buf,
+                                                              const int* gen) {
+    const BatchDesc& bd = d[blockIdx.x];
+    long long v;
+    int e;
+    block_argmin(reinterpret_cast<const long long*>(bd.fit[buf]), bd.p.s, &v, &e);
+    if (threadIdx.x == 0) {
+        if (bd.traj) bd.traj[*gen] = v;
+        *bd.best = e;
+    }
+}
+
+__global__ void advance_kernel(int* gen) { *gen += 1; }
+
 // Lowest fitness of a population: traj[*gen] = min, *best = argmin, then ++*gen.
 __global__ void __launch_bounds__(1024) record_kernel(const long long* __restrict__ fit, int s, int* gen,
                                                       long long* traj, int* best) {
@@ -346,6 +386,35 @@ int gapa_launch_record(gapa_ctx* c, const int64_t* fit, int s, int* gen, int64_t
                                       reinterpret_cast<long long*>(traj), best);
     GAPA_CUDA(cudaGetLastError());
     return GAPA_OK;
+}
+
+int gapa_launch_init_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int buf,
+                             cudaStream_t st) {
+    init_batched_kernel<<<total_rows, kGaBlock, smem, st>>>(d, rows, buf);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_launch_offspring_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int src,
+                                  const int* gen, int* status, cudaStream_t st) {
+    offspring_batched_kernel<<<total_rows, kGaBlock, smem, st>>>(d, rows, src, gen, status);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_launch_record_batched(const BatchDesc* d, int num, int buf, int* gen, bool advance, cudaStream_t st) {
+    record_batched_kernel<<<num, 1024, 0, st>>>(d, buf, gen);
+    if (advance) advance_kernel<<<1, 1, 0, st>>>(gen);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+size_t gapa_row_smem_bytes(int n, int k) { return row_smem_bytes(n, k); }
+
+int gapa_ga_batched_init(size_t optin, size_t* max_dyn) {
+    int rc = gapa_set_smem_limit((const void*)init_batched_kernel, optin, max_dyn);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)offspring_batched_kernel, optin, max_dyn);
+    return rc;
 }
 
 int gapa_ga_kernels_init(gapa_ctx* c) {

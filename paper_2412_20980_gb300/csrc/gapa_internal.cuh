@@ -165,7 +165,41 @@ struct GaParams {
     const int* g_ptr;    // device-resident generation counter (CUDA-graph replay)
 };
 
+// One instance of a batched run (device-side descriptor).
+struct BatchDesc {
+    GaParams p;          // operator parameters; p.g unused (generation from the device counter)
+    int32_t* pop[2];     // ping-pong populations [s][k]
+    int64_t* fit[2];     // ping-pong fitness [s]
+    int64_t* traj;       // [gens + 1]
+    int* best;           // index of the lowest fitness after the last record
+    // fitness graph in 16-bit BFS numbering (tree16.cuh)
+    int n;
+    const int* perm;
+    const int2* palt;
+    const int* lo_ptr;
+    const int* lo_col;
+    const unsigned* nontree;
+    int num_nontree;
+    int teams;           // members per CTA in the batched fitness kernel (1, 2, 4 or 8)
+};
+
+// A packet of the batched fitness work queue: members i0 .. i0+cnt-1 of instance b.
+struct BatchPacket {
+    int b, i0, cnt, teams;
+};
+
 int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st);
+int gapa_launch_init_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int buf,
+                             cudaStream_t st);
+int gapa_launch_offspring_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int src,
+                                  const int* gen, int* status, cudaStream_t st);
+int gapa_launch_record_batched(const BatchDesc* d, int num, int buf, int* gen, bool advance, cudaStream_t st);
+int gapa_launch_fitness_batched(const BatchDesc* d, const BatchPacket* pk, int npk, int* head, int buf,
+                                size_t smem, int grid, int* status, cudaStream_t st);
+int gapa_fitness_batched_init(size_t optin, size_t* max_dyn);
+int gapa_fitness_batched_occupancy(size_t smem, int* blocks_per_sm);
+int gapa_ga_batched_init(size_t optin, size_t* max_dyn);
+size_t gapa_row_smem_bytes(int n, int k);
 int gapa_fitness_prepare(gapa_ctx* c, int s);  // allocate scratch before capture
 int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st);
 int gapa_ig_prepare(gapa_ctx* c, int s);

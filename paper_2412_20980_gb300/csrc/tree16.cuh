@@ -1,0 +1,232 @@
+// Shared-memory TREE fitness pipeline for graphs of at most 65536 nodes,
+// written for a "team": a group of warps of one CTA that evaluates one
+// population member with its own slice of shared memory and its own named
+// barrier.  A whole CTA is one team (barrier 0); the batched persistent kernel
+// splits a CTA into 2, 4 or 8 teams so that small graphs run several members
+// per CTA.
+//
+// Fitness (Section III-C, Eq. 13; PC(G) of Table "Whole"): pairwise
+// connectivity of G with the member's genes deleted.  Nodes are in BFS
+// numbering (every tree parent precedes its child); see fitness.cu for the
+// phases.
+#pragma once
+
+#include "gapa_internal.cuh"
+
+namespace gapa_dev {
+
+struct Team {
+    int tid;  // thread index within the team
+    int T;    // team size (a multiple of 32)
+    int bar;  // named barrier id (0 = the whole CTA)
+    __device__ __forceinline__ void sync() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory");
+    }
+};
+
+// Path halving.  Invariant: a non-root's parent has a smaller id, so the
+// walk terminates; roots change only by CAS in uf_unite.
+__device__ __forceinline__ int uf_find(volatile int* lab, int x) {
+    while (true) {
+        const int p = lab[x];
+        if (p == x) return x;
+        const int gp = lab[p];
+        if (gp == p) return p;
+        lab[x] = gp;
+        x = gp;
+    }
+}
+
+// Root of x by a read-only walk.  Used once no hooking is left: every write
+// then is an owner storing its node's final root, so no walk can leave a
+// stale (non-root) ancestor behind, which path halving could.
+__device__ __forceinline__ int uf_root(volatile int* lab, int x) {
+    int p = lab[x];
+    while (p != x) {
+        x = p;
+        p = lab[x];
+    }
+    return x;
+}
+
+// Union of the trees of live nodes a and b: hook the larger root under the
+// smaller with a CAS on the root's slot; retry from the new parent on a race.
+__device__ __forceinline__ void uf_unite(volatile int* lab, int a, int b) {
+    a = uf_find(lab, a);
+    b = uf_find(lab, b);
+    while (a != b) {
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS((int*)&lab[a], a, b);
+        if (old == a) return;
+        a = uf_find(lab, old);
+        b = uf_find(lab, b);
+    }
+}
+
+__device__ __forceinline__ bool bm_test(const unsigned* bm, int v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
+
+// Sum over the team; valid in team thread 0.  red: 32 slots of this team.
+__device__ __forceinline__ long long team_sum_ll(const Team& tm, long long v, long long* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = tm.tid >> 5, lane = tm.tid & 31;
+    if (lane == 0) red[warp] = v;
+    tm.sync();
+    long long tot = 0;
+    if (warp == 0) {
+        tot = lane < (tm.T >> 5) ? red[lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+    }
+    return tot;
+}
+
+struct Tree16Graph {
+    int n;
+    const int* perm;     // original id -> BFS number
+    const int2* palt;    // (tree parent, second lower-numbered neighbour or -1)
+    const int* lo_ptr;   // lower-numbered neighbours (CSR)
+    const int* lo_col;
+    const unsigned* nontree;  // non-tree edges a<<16|b
+    int num_nontree;
+};
+
+// Shared-memory bytes of one member: labels + deleted-node bitmap.
+__host__ __device__ __forceinline__ size_t tree16_smem_bytes(int n) {
+    return (size_t)n * 4 + (size_t)((n + 31) >> 5) * 4;
+}
+
+// One member: lab = n labels, dead = (n+31)/32 bitmap words (both this team's
+// shared memory).  Deleted nodes end as -1.
+__device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab, unsigned* dead, const Tree16Graph& g,
+                                              const int* __restrict__ genes, int k, long long* out, long long* red,
+                                              int* status) {
+    const int tid = tm.tid, T = tm.T, n = g.n;
+    const int words = (n + 31) >> 5;
+    for (int w = tid; w < words; w += T) dead[w] = 0u;
+    tm.sync();
+    // perturbation P^(A, p) of Eq. 13 in BFS numbering
+    for (int j = tid; j < k; j += T) {
+        const int d = __ldg(&genes[j]);
+        if ((unsigned)d < (unsigned)n) {
+            const int b = __ldg(&g.perm[d]);
+            atomicOr(&dead[b >> 5], 1u << (b & 31));
+        } else {
+            atomicOr(status, GAPA_DEV_BAD_GENE);
+        }
+    }
+    tm.sync();
+    // labels: tree parent, or on a deleted parent the first live lower-numbered
+    // neighbour, or the node itself; four nodes per thread per step
+    constexpr int kU = 4;
+    for (int base = tid; base < n; base += kU * T) {
+        int2 pa[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int v = base + u * T;
+            pa[u] = v < n ? __ldg(&g.palt[v]) : make_int2(0, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int v = base + u * T;
+            if (v >= n) break;
+            int q;
+            if (bm_test(dead, v)) {
+                q = -1;
+            } else if (pa[u].x == v || !bm_test(dead, pa[u].x)) {
+                q = pa[u].x;
+            } else {
+                q = v;
+                if (pa[u].y >= 0) {
+                    if (!bm_test(dead, pa[u].y)) {
+                        q = pa[u].y;
+                    } else {
+                        const int beg = __ldg(&g.lo_ptr[v]) + 2, end = __ldg(&g.lo_ptr[v + 1]);
+                        for (int e = beg; e < end; ++e) {
+                            const int w = __ldg(&g.lo_col[e]);
+                            if (!bm_test(dead, w)) {
+                                q = w;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
+            lab[v] = q;
+        }
+    }
+    tm.sync();
+    // flatten every piece onto its top node (owner writes only)
+    for (int v = tid; v < n; v += T) {
+        const int p = lab[v];
+        if (p != -1 && p != v) lab[v] = uf_root(lab, p);
+    }
+    tm.sync();
+    // join the pieces along the non-tree edges, four per 16-byte load
+    {
+        const uint4* e4 = reinterpret_cast<const uint4*>(g.nontree);
+        const int quads = g.num_nontree >> 2;
+        int q = tid;
+        uint4 w = q < quads ? __ldg(&e4[q]) : make_uint4(0, 0, 0, 0);
+        while (q < quads) {
+            const int qn = q + T;
+            const uint4 wn = qn < quads ? __ldg(&e4[qn]) : make_uint4(0, 0, 0, 0);
+            const int a0 = (int)(w.x >> 16), b0 = (int)(w.x & 0xFFFFu), a1 = (int)(w.y >> 16), b1 = (int)(w.y & 0xFFFFu);
+            const int a2 = (int)(w.z >> 16), b2 = (int)(w.z & 0xFFFFu), a3 = (int)(w.w >> 16), b3 = (int)(w.w & 0xFFFFu);
+            const int la0 = lab[a0], lb0 = lab[b0], la1 = lab[a1], lb1 = lab[b1];
+            const int la2 = lab[a2], lb2 = lab[b2], la3 = lab[a3], lb3 = lab[b3];
+            if (la0 != lb0 && la0 != -1 && lb0 != -1) uf_unite(lab, la0, lb0);
+            if (la1 != lb1 && la1 != -1 && lb1 != -1) uf_unite(lab, la1, lb1);
+            if (la2 != lb2 && la2 != -1 && lb2 != -1) uf_unite(lab, la2, lb2);
+            if (la3 != lb3 && la3 != -1 && lb3 != -1) uf_unite(lab, la3, lb3);
+            q = qn;
+            w = wn;
+        }
+        for (int e = quads * 4 + tid; e < g.num_nontree; e += T) {
+            const unsigned x = __ldg(&g.nontree[e]);
+            const int a = (int)(x >> 16), b = (int)(x & 0xFFFFu);
+            const int la = lab[a], lb = lab[b];
+            if (la != lb && la != -1 && lb != -1) uf_unite(lab, la, lb);
+        }
+    }
+    tm.sync();
+    // sizes: a root's slot becomes (members below it) << 16 | its id; every
+    // live non-root walks to its root (masking the count bits) and adds
+    // itself, warp-aggregated.  A root's own slot may already carry count
+    // bits, so it is classified by the masked id; -1 (deleted) can equal no
+    // root slot because root ids are below 65535.
+    const int lane = tid & 31;
+    for (int base = 0; base < n; base += T) {
+        const int v = base + tid;
+        int key = -1;
+        if (v < n) {
+            const int l = lab[v];
+            if (l != -1 && (l & 0xFFFF) != v) {
+                int x = l & 0xFFFF;
+                while (true) {
+                    const int q = lab[x] & 0xFFFF;
+                    if (q == x) break;
+                    x = q;
+                }
+                key = x;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd((unsigned*)&lab[key], (unsigned)__popc(peers) << 16);
+    }
+    tm.sync();
+    long long acc = 0;
+    for (int v = tid; v < n; v += T) {
+        const unsigned l = (unsigned)lab[v];
+        if (l != 0xFFFFFFFFu && (int)(l & 0xFFFFu) == v) {
+            const long long c = (long long)(l >> 16) + 1;
+            acc += c * (c - 1) / 2;
+        }
+    }
+    const long long tot = team_sum_ll(tm, acc, red);
+    if (tid == 0) *out = tot;
+}
+
+}  // namespace gapa_dev

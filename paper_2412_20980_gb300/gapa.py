@@ -35,6 +35,8 @@ EXPORTS = [
     "gapa_fitness", "gapa_fitness_host", "gapa_generation", "gapa_generation_host", "gapa_run",
     "gapa_sync", "gapa_last_error", "gapa_version", "gapa_profile_begin", "gapa_profile_end",
     "gapa_set_fitness_kernel", "gapa_fitness_noalloc",
+    "gapa_batch_create", "gapa_batch_destroy", "gapa_batch_set_teams", "gapa_batch_get_teams",
+    "gapa_batch_autotune", "gapa_batch_run",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE = 0, 1, 2, 3
 
@@ -117,6 +119,12 @@ def load(path: str | None = None):
             "gapa_profile_begin": ([V], U),
             "gapa_set_fitness_kernel": ([V, U], U),
             "gapa_fitness_noalloc": ([U, V, I32, I32, V, V, I32, I32, V], U),
+            "gapa_batch_create": ([ctypes.POINTER(V), I32, V, V], U),
+            "gapa_batch_destroy": ([V], None),
+            "gapa_batch_set_teams": ([V, V], U),
+            "gapa_batch_get_teams": ([V, V], U),
+            "gapa_batch_autotune": ([V, ctypes.c_char_p], U),
+            "gapa_batch_run": ([V, I32, V, V, V], U),
             "gapa_profile_end": ([V, ctypes.POINTER(Profile)], U),
             "gapa_last_error": ([], ctypes.c_char_p),
             "gapa_version": ([], ctypes.c_char_p),
@@ -312,3 +320,68 @@ class Context:
         prof = Profile()
         _check(self.lib.gapa_profile_end(self.handle, ctypes.byref(prof)))
         return prof.as_dict()
+
+
+class Batch:
+    """Many independent GA instances advanced together (wraps gapa_batch).
+
+    `contexts` hold the uploaded graphs (they must outlive the batch); `configs`
+    one Config per instance.
+    """
+
+    def __init__(self, contexts, configs):
+        self.lib = load()
+        self.contexts = list(contexts)
+        self.configs = list(configs)
+        n = len(self.contexts)
+        arr = (ctypes.c_void_p * n)(*[c.handle.value for c in self.contexts])
+        cfg_arr = (Config * n)(*self.configs)
+        self._keep = (arr, cfg_arr)
+        h = ctypes.c_void_p()
+        _check(self.lib.gapa_batch_create(ctypes.byref(h), n, ctypes.cast(arr, ctypes.c_void_p),
+                                          ctypes.cast(cfg_arr, ctypes.c_void_p)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gapa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def teams(self) -> list[int]:
+        out = np.zeros(len(self.contexts), dtype=np.int32)
+        _check(self.lib.gapa_batch_get_teams(self.handle, _host_ptr(out)))
+        return out.tolist()
+
+    @teams.setter
+    def teams(self, values):
+        arr = np.ascontiguousarray(values, dtype=np.int32)
+        _check(self.lib.gapa_batch_set_teams(self.handle, _host_ptr(arr)))
+
+    def autotune(self, cache_path: str | None = None):
+        _check(self.lib.gapa_batch_autotune(self.handle, cache_path.encode() if cache_path else None))
+
+    def run(self, gens: int) -> dict:
+        num = len(self.contexts)
+        best_fit = np.zeros(num, dtype=np.int64)
+        ks = [c.k for c in self.configs]
+        best_sets = np.zeros(max(1, sum(ks)), dtype=np.int32)
+        traj = np.zeros((num, gens + 1), dtype=np.int64)
+        _check(self.lib.gapa_batch_run(self.handle, gens, _host_ptr(best_fit), _host_ptr(best_sets), _host_ptr(traj)))
+        sets, off = [], 0
+        for k in ks:
+            sets.append(best_sets[off:off + k].copy())
+            off += k
+        return {"best_fit": best_fit, "best_sets": sets, "traj": traj}
