@@ -474,19 +474,21 @@ def run_batched(args, gs, dist, ws, rank, local, dev):
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
 
-        # bounded sample: the four smallest instances, 20 generations each
-        idx = sorted(range(len(specs)), key=lambda i: specs[i]["n"])[:4]
+        # bounded sample: eight instances spread over the size range, 3 generations each
+        order = sorted(range(len(specs)), key=lambda i: specs[i]["n"])
+        idx = [order[round(q * (len(order) - 1) / 7)] for q in range(8)]
         t0 = time.perf_counter()
         units = 0
         for i in idx:
             d = specs[i]
             pc_thr, pm_thr = oracle.thresholds(PC, PM)
-            oracle.run(gs[i].row_ptr, gs[i].col, k=d["k"], pop=d["pop"], gens=20, tourn=TOURN, pc_thr=pc_thr,
+            oracle.run(gs[i].row_ptr, gs[i].col, k=d["k"], pop=d["pop"], gens=3, tourn=TOURN, pc_thr=pc_thr,
                        pm_thr=pm_thr, seed=d["index"], nthreads=oracle.max_threads())
-            units += d["pop"] + (d["pop"] - 1) * 20
+            units += d["pop"] + (d["pop"] - 1) * 3
         el = time.perf_counter() - t0
         cpu = {"value": units / el, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-               "sample": f"oracle runs of the 4 smallest instances, 20 generations each: {units} evals in {el:.1f} s"}
+               "sample": f"oracle runs of 8 instances at the size octiles, 3 generations each: {units} evals "
+                         f"in {el:.1f} s"}
     line = {"metric": w["metric"], "value": value, "unit": w["unit"], "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
