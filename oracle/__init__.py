@@ -22,8 +22,8 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-TAG_INIT, TAG_SEL, TAG_XOVER, TAG_MUT, TAG_MUTVAL, TAG_REPAIR = 1, 2, 3, 4, 5, 6
-FLAG_ROWWISE = 1
+TAG_INIT, TAG_SEL, TAG_XOVER, TAG_MUT, TAG_MUTVAL, TAG_REPAIR, TAG_ROULETTE = 1, 2, 3, 4, 5, 6, 7
+FLAG_ROWWISE, FLAG_MU_PLUS_LAMBDA, FLAG_ROULETTE = 1, 2, 4
 
 
 class OracleError(RuntimeError):
@@ -61,10 +61,10 @@ def _load():
         lib.oracle_fitness.restype = ctypes.c_int
         lib.oracle_pop_init.argtypes = [i32, i32, i32, u64, P]
         lib.oracle_pop_init.restype = ctypes.c_int
-        lib.oracle_generation.argtypes = [i32, P, P, i32, i32, i32, u32, u32, u64, u32, i32,
+        lib.oracle_generation.argtypes = [i32, P, P, i32, i32, i32, u32, u32, u64, u32, i32, i32,
                                           P, P, P, P, i32]
         lib.oracle_generation.restype = ctypes.c_int
-        lib.oracle_run.argtypes = [i32, P, P, i32, i32, i32, i32, u32, u32, u64, u32,
+        lib.oracle_run.argtypes = [i32, P, P, i32, i32, i32, i32, u32, u32, u64, u32, i32,
                                    P, P, P, P, P, i32]
         lib.oracle_run.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
@@ -151,7 +151,7 @@ def thresholds(pc_rate: float, pm_rate: float) -> tuple[int, int]:
 
 
 def generation(row_ptr, col, pop_in, fit_in, g: int, *, tourn: int, pc_thr: int, pm_thr: int,
-               seed: int, flags: int = 0, nthreads: int = 1):
+               seed: int, flags: int = 0, lam: int = 0, nthreads: int = 1):
     row_ptr, col, pop_in = _i32(row_ptr), _i32(col), _i32(pop_in)
     fit_in = np.ascontiguousarray(fit_in, dtype=np.int64)
     n = row_ptr.shape[0] - 1
@@ -159,14 +159,14 @@ def generation(row_ptr, col, pop_in, fit_in, g: int, *, tourn: int, pc_thr: int,
     pop_out = np.zeros_like(pop_in)
     fit_out = np.zeros(s, dtype=np.int64)
     rc = _load().oracle_generation(n, _ptr(row_ptr), _ptr(col), k, s, tourn, pc_thr, pm_thr, seed,
-                                   flags, g, _ptr(pop_in), _ptr(fit_in), _ptr(pop_out), _ptr(fit_out),
+                                   flags, g, lam, _ptr(pop_in), _ptr(fit_in), _ptr(pop_out), _ptr(fit_out),
                                    nthreads)
     _check(rc, "generation")
     return pop_out, fit_out
 
 
 def run(row_ptr, col, *, k: int, pop: int, gens: int, tourn: int, pc_thr: int, pm_thr: int,
-        seed: int, flags: int = 0, nthreads: int = 1) -> dict:
+        seed: int, flags: int = 0, lam: int = 0, nthreads: int = 1) -> dict:
     row_ptr, col = _i32(row_ptr), _i32(col)
     n = row_ptr.shape[0] - 1
     best = np.zeros(k, dtype=np.int32)
@@ -175,7 +175,7 @@ def run(row_ptr, col, *, k: int, pop: int, gens: int, tourn: int, pc_thr: int, p
     pop_final = np.zeros((pop, k), dtype=np.int32)
     fit_final = np.zeros(pop, dtype=np.int64)
     rc = _load().oracle_run(n, _ptr(row_ptr), _ptr(col), k, pop, gens, tourn, pc_thr, pm_thr, seed,
-                            flags, _ptr(best), ctypes.cast(ctypes.pointer(best_fit), ctypes.c_void_p),
+                            flags, lam, _ptr(best), ctypes.cast(ctypes.pointer(best_fit), ctypes.c_void_p),
                             _ptr(traj), _ptr(pop_final), _ptr(fit_final), nthreads)
     _check(rc, "run")
     return {"best_set": best, "best_fit": int(best_fit.value), "traj": traj,

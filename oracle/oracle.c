@@ -71,7 +71,7 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-enum { TAG_INIT = 1, TAG_SEL = 2, TAG_XOVER = 3, TAG_MUT = 4, TAG_MUTVAL = 5, TAG_REPAIR = 6 };
+enum { TAG_INIT = 1, TAG_SEL = 2, TAG_XOVER = 3, TAG_MUT = 4, TAG_MUTVAL = 5, TAG_REPAIR = 6, TAG_ROULETTE = 7 };
 #define REPAIR_ROUNDS 32
 
 static uint32_t draw(uint64_t seed, uint32_t j, uint32_t i, uint32_t g, uint32_t tag, uint32_t round)
@@ -81,6 +81,16 @@ static uint32_t draw(uint64_t seed, uint32_t j, uint32_t i, uint32_t g, uint32_t
     uint32_t out[4];
     oracle_philox4x32_10(ctr, key, out);
     return out[0];
+}
+
+/* Words 0 and 1 of the same counter as one 64-bit number (word 0 high). */
+static uint64_t draw64(uint64_t seed, uint32_t j, uint32_t i, uint32_t g, uint32_t tag, uint32_t round)
+{
+    uint32_t ctr[4] = { j, i, g, (tag << 24) | round };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return ((uint64_t)out[0] << 32) | (uint64_t)out[1];
 }
 
 static int32_t uniform_below(uint32_t x, int32_t n)
@@ -297,72 +307,166 @@ static int32_t tournament(uint64_t seed, int32_t i, int32_t g, int32_t slot, int
 }
 
 #define ORACLE_FLAG_ROWWISE 1u
+#define ORACLE_FLAG_MU_PLUS_LAMBDA 2u
+#define ORACLE_FLAG_ROULETTE 4u
 
-/* One generation g >= 1 (Fig. 1's loop body), producing (pop_out, fit_out)
- * from (pop_in, fit_in):
- *   elitism  - row 0 = the member with the lowest fitness (lowest index on
- *              ties), fitness carried over;
- *   for each child i = 1 .. s-1:
- *   selection - parents A and B by two tournaments (slot 0 and slot 1); with
- *              the row-wise flag, A = member i itself (Eq. 6 read literally);
+/* Roulette-wheel selection (Eq. 5) for minimisation with integer weights:
+ * w_x = (max F - F_x) + 1, cumulative sums cum[x] = w_0 + ... + w_x (int64);
+ * a 64-bit draw u (words 0, 1 of draw(slot, i, g, ROULETTE, 0)) gives
+ * r = floor(u * W / 2^64) with W = cum[s-1]; the parent is the smallest x with
+ * cum[x] > r. */
+static void roulette_weights(const int64_t* fit, int32_t s, int64_t* cum)
+{
+    int64_t mx = fit[0];
+    for (int32_t x = 1; x < s; x++) if (fit[x] > mx) mx = fit[x];
+    int64_t acc = 0;
+    for (int32_t x = 0; x < s; x++) { acc += (mx - fit[x]) + 1; cum[x] = acc; }
+}
+
+static int32_t roulette(uint64_t seed, int32_t i, int32_t g, int32_t slot, int32_t s, const int64_t* cum)
+{
+    uint64_t u = draw64(seed, (uint32_t)slot, (uint32_t)i, (uint32_t)g, TAG_ROULETTE, 0);
+    uint64_t W = (uint64_t)cum[s - 1];
+    uint64_t r = (uint64_t)(((unsigned __int128)u * (unsigned __int128)W) >> 64);
+    int32_t x = 0;
+    while ((uint64_t)cum[x] <= r) x++;
+    return x;
+}
+
+/* One child with counter index i from parents A and B (Eqs. 3-9 with the
+ * duplicate rule):
  *   crossover - gene j is B[j] where draw(j,i,g,XOVER,0) < pc_thr, else A[j];
  *   mutation  - gene j becomes a hole where draw(j,i,g,MUT,0) < pm_thr, with
  *              round-0 candidate uniform over [0,n) from draw(j,i,g,MUTVAL,0);
  *   duplicates - a gene taken from B that equals a kept gene taken from A
  *              becomes a hole whose round-0 candidate is A[j];
- *   repair    - as in repair();
- *   fitness   - PC of every child (BFS).
- */
+ *   repair    - as in repair(). */
+typedef struct {
+    keptset kept;
+    int32_t* holes;
+    int32_t* cand0;
+    uint8_t* from_b;
+    uint8_t* mutated;
+} child_scratch;
+
+static void make_child(uint64_t seed, int32_t n, int32_t k, int32_t i, int32_t g, uint32_t pc_thr, uint32_t pm_thr,
+                       const int32_t* A, const int32_t* B, int32_t* row, child_scratch* w)
+{
+    memset(w->kept.in, 0, (size_t)n);
+    for (int32_t j = 0; j < k; j++) {
+        w->from_b[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_XOVER, 0) < pc_thr;
+        w->mutated[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUT, 0) < pm_thr;
+        row[j] = -1;
+    }
+    /* genes kept from A first, then genes from B that do not repeat one */
+    for (int32_t j = 0; j < k; j++)
+        if (!w->mutated[j] && !w->from_b[j]) { row[j] = A[j]; w->kept.in[A[j]] = 1; }
+    for (int32_t j = 0; j < k; j++)
+        if (!w->mutated[j] && w->from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }
+    int32_t nh = 0;
+    for (int32_t j = 0; j < k; j++) {
+        if (row[j] >= 0) continue;
+        w->holes[nh] = j;
+        w->cand0[nh] = w->mutated[j] ? uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)
+                                     : A[j];
+        nh++;
+    }
+    repair(seed, i, g, n, &w->kept, row, w->holes, nh, w->cand0);
+}
+
+/* Parent for slot 0 (A) or 1 (B) of the child with counter index i, chosen
+ * from the s members of (pop, fit): tournament, or roulette with the flag. */
+static int32_t select_parent(uint64_t seed, uint32_t flags, int32_t i, int32_t g, int32_t slot, int32_t t,
+                             int32_t s, const int64_t* fit, const int64_t* cum)
+{
+    if (flags & ORACLE_FLAG_ROULETTE) return roulette(seed, i, g, slot, s, cum);
+    return tournament(seed, i, g, slot, t, s, fit);
+}
+
+/* One generation g >= 1 (Fig. 1's loop body), producing (pop_out, fit_out)
+ * from (pop_in, fit_in) of s members.
+ * Default (one elite):
+ *   elitism  - row 0 = the member with the lowest fitness (lowest index on
+ *              ties), fitness carried over;
+ *   children - rows i = 1 .. s-1 from parents A and B chosen by select_parent
+ *              (with the row-wise flag A = member i itself, Eq. 6 read
+ *              literally), built by make_child with counter index i;
+ *   fitness  - PC of every child (BFS).
+ * With ORACLE_FLAG_MU_PLUS_LAMBDA (Eqs. 10-11): lambda children c = 0 ..
+ * lambda-1 (counter index c) from parents among the s members, their
+ * fitness, then the s members of lowest fitness among [members; children]
+ * by a stable ascending sort (members before children, lower index first on
+ * ties) form the next population. */
+static int cmp_key(const void* a, const void* b)
+{
+    const int64_t* x = (const int64_t*)a;
+    const int64_t* y = (const int64_t*)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    return x[1] < y[1] ? -1 : (x[1] > y[1]);
+}
+
 int oracle_generation(int32_t n, const int32_t* row_ptr, const int32_t* col,
                       int32_t k, int32_t s, int32_t t, uint32_t pc_thr, uint32_t pm_thr,
-                      uint64_t seed, uint32_t flags, int32_t g,
+                      uint64_t seed, uint32_t flags, int32_t g, int32_t lambda,
                       const int32_t* pop_in, const int64_t* fit_in,
                       int32_t* pop_out, int64_t* fit_out, int32_t nthreads)
 {
-    if (n < 1 || k < 0 || k >= n || s < 2 || t < 1 || g < 1) return ORACLE_EINVAL;
-    int32_t elite = 0;
-    for (int32_t x = 1; x < s; x++)
-        if (fit_in[x] < fit_in[elite]) elite = x;
-    memcpy(pop_out, pop_in + (size_t)elite * (size_t)k, sizeof(int32_t) * (size_t)k);
-    fit_out[0] = fit_in[elite];
-
+    const int mpl = (flags & ORACLE_FLAG_MU_PLUS_LAMBDA) != 0;
+    if (n < 1 || k < 0 || k >= n || s < 2 || t < 1 || g < 1 || (mpl && lambda < 1)) return ORACLE_EINVAL;
+    if (mpl && (flags & ORACLE_FLAG_ROWWISE)) return ORACLE_EINVAL;
+    const int32_t nchild = mpl ? lambda : s - 1;
     int err = ORACLE_OK;
-    keptset kept = { n, (uint8_t*)malloc((size_t)n) };
-    int32_t* holes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
-    int32_t* cand0 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
-    uint8_t* from_b = (uint8_t*)malloc((size_t)k + 1);
-    uint8_t* mutated = (uint8_t*)malloc((size_t)k + 1);
-    if (!kept.in || !holes || !cand0 || !from_b || !mutated) err = ORACLE_ENOMEM;
-    for (int32_t i = 1; i < s && err == ORACLE_OK; i++) {
-        int32_t pa = (flags & ORACLE_FLAG_ROWWISE) ? i : tournament(seed, i, g, 0, t, s, fit_in);
-        int32_t pb = tournament(seed, i, g, 1, t, s, fit_in);
-        const int32_t* A = pop_in + (size_t)pa * (size_t)k;
-        const int32_t* B = pop_in + (size_t)pb * (size_t)k;
-        int32_t* row = pop_out + (size_t)i * (size_t)k;
-        memset(kept.in, 0, (size_t)n);
-        for (int32_t j = 0; j < k; j++) {
-            from_b[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_XOVER, 0) < pc_thr;
-            mutated[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUT, 0) < pm_thr;
-            row[j] = -1;
+    child_scratch w;
+    w.kept.n = n;
+    w.kept.in = (uint8_t*)malloc((size_t)n);
+    w.holes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    w.cand0 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    w.from_b = (uint8_t*)malloc((size_t)k + 1);
+    w.mutated = (uint8_t*)malloc((size_t)k + 1);
+    int64_t* cum = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
+    int32_t* kids = (int32_t*)malloc(sizeof(int32_t) * ((size_t)nchild * (size_t)k + 1));
+    int64_t* kfit = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nchild + 1));
+    if (!w.kept.in || !w.holes || !w.cand0 || !w.from_b || !w.mutated || !cum || !kids || !kfit) err = ORACLE_ENOMEM;
+    if (err == ORACLE_OK) {
+        roulette_weights(fit_in, s, cum);
+        for (int32_t c = 0; c < nchild; c++) {
+            const int32_t i = mpl ? c : c + 1;
+            int32_t pa = (flags & ORACLE_FLAG_ROWWISE) ? i : select_parent(seed, flags, i, g, 0, t, s, fit_in, cum);
+            int32_t pb = select_parent(seed, flags, i, g, 1, t, s, fit_in, cum);
+            make_child(seed, n, k, i, g, pc_thr, pm_thr, pop_in + (size_t)pa * (size_t)k,
+                       pop_in + (size_t)pb * (size_t)k, kids + (size_t)c * (size_t)k, &w);
         }
-        /* genes kept from A first, then genes from B that do not repeat one */
-        for (int32_t j = 0; j < k; j++)
-            if (!mutated[j] && !from_b[j]) { row[j] = A[j]; kept.in[A[j]] = 1; }
-        for (int32_t j = 0; j < k; j++)
-            if (!mutated[j] && from_b[j] && !kept.in[B[j]]) { row[j] = B[j]; kept.in[B[j]] = 1; }
-        int32_t nh = 0;
-        for (int32_t j = 0; j < k; j++) {
-            if (row[j] >= 0) continue;
-            holes[nh] = j;
-            cand0[nh] = mutated[j] ? uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)
-                                   : A[j];
-            nh++;
-        }
-        repair(seed, i, g, n, &kept, row, holes, nh, cand0);
+        err = oracle_fitness(n, row_ptr, col, kids, nchild, k, kfit, 0, nthreads);
     }
-    free(kept.in); free(holes); free(cand0); free(from_b); free(mutated);
-    if (err != ORACLE_OK) return err;
-    return oracle_fitness(n, row_ptr, col, pop_out + k, s - 1, k, fit_out + 1, 0, nthreads);
+    if (err == ORACLE_OK && !mpl) {
+        int32_t elite = 0;
+        for (int32_t x = 1; x < s; x++)
+            if (fit_in[x] < fit_in[elite]) elite = x;
+        memcpy(pop_out, pop_in + (size_t)elite * (size_t)k, sizeof(int32_t) * (size_t)k);
+        fit_out[0] = fit_in[elite];
+        memcpy(pop_out + k, kids, sizeof(int32_t) * (size_t)(s - 1) * (size_t)k);
+        memcpy(fit_out + 1, kfit, sizeof(int64_t) * (size_t)(s - 1));
+    } else if (err == ORACLE_OK) {
+        int32_t tot = s + nchild;
+        int64_t* key = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)tot);
+        if (!key) err = ORACLE_ENOMEM;
+        else {
+            for (int32_t x = 0; x < tot; x++) {
+                key[2 * x] = x < s ? fit_in[x] : kfit[x - s];
+                key[2 * x + 1] = x;
+            }
+            qsort(key, (size_t)tot, 2 * sizeof(int64_t), cmp_key);
+            for (int32_t r = 0; r < s; r++) {
+                int32_t x = (int32_t)key[2 * r + 1];
+                const int32_t* src = x < s ? pop_in + (size_t)x * (size_t)k : kids + (size_t)(x - s) * (size_t)k;
+                memcpy(pop_out + (size_t)r * (size_t)k, src, sizeof(int32_t) * (size_t)k);
+                fit_out[r] = key[2 * r];
+            }
+            free(key);
+        }
+    }
+    free(w.kept.in); free(w.holes); free(w.cand0); free(w.from_b); free(w.mutated); free(cum); free(kids); free(kfit);
+    return err;
 }
 
 /* A whole run: initialisation, fitness, then `gens` generations.
@@ -378,7 +482,7 @@ static int cmp_i32(const void* a, const void* b)
 
 int oracle_run(int32_t n, const int32_t* row_ptr, const int32_t* col,
                int32_t k, int32_t s, int32_t gens, int32_t t, uint32_t pc_thr, uint32_t pm_thr,
-               uint64_t seed, uint32_t flags, int32_t* best_set, int64_t* best_fit,
+               uint64_t seed, uint32_t flags, int32_t lambda, int32_t* best_set, int64_t* best_fit,
                int64_t* traj_best, int32_t* pop_final, int64_t* fit_final, int32_t nthreads)
 {
     if (n < 1 || k < 0 || k >= n || s < 2 || t < 1 || gens < 0) return ORACLE_EINVAL;
@@ -392,7 +496,7 @@ int oracle_run(int32_t n, const int32_t* row_ptr, const int32_t* col,
     if (err == ORACLE_OK) err = oracle_fitness(n, row_ptr, col, pa, s, k, fa, 0, nthreads);
     for (int32_t g = 0; g <= gens && err == ORACLE_OK; g++) {
         if (g > 0) {
-            err = oracle_generation(n, row_ptr, col, k, s, t, pc_thr, pm_thr, seed, flags, g,
+            err = oracle_generation(n, row_ptr, col, k, s, t, pc_thr, pm_thr, seed, flags, g, lambda,
                                     pa, fa, pb, fb, nthreads);
             int32_t* tp = pa; pa = pb; pb = tp;
             int64_t* tf = fa; fa = fb; fb = tf;

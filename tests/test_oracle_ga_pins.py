@@ -269,3 +269,74 @@ def test_run_is_generation_composition():
         pop, fit = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr,
                                      seed=SEED)
     assert np.array_equal(pop, r["pop"]) and np.array_equal(fit, r["fit"])
+
+
+def test_roulette_selection_law_with_pc0_pm0():
+    """Eq. 5 roulette for minimisation: P(parent = x) = w_x / sum w with w_x = max F - F_x + 1."""
+    g = synth.named_graph("empty", 3000)
+    s, k = 12, 3
+    pop = _distinct_population(g.n, k, s, 4)
+    fit = np.array([5, 0, 9, 3, 3, 7, 1, 12, 4, 8, 2, 6], dtype=np.int64)
+    rows = {tuple(pop[i].tolist()): i for i in range(s)}
+    counts = np.zeros(s, dtype=np.int64)
+    for gen in range(1, 301):
+        out, _ = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=0, pm_thr=0, seed=SEED,
+                                   flags=oracle.FLAG_ROULETTE)
+        for i in range(1, s):
+            counts[rows[tuple(out[i].tolist())]] += 1
+    w = (fit.max() - fit + 1).astype(float)
+    e = counts.sum() * w / w.sum()
+    assert ((counts - e) ** 2 / e).sum() < 11 + 6 * np.sqrt(22)
+
+
+def test_mu_plus_lambda_closed_form_with_pc0_pm0():
+    """Eqs. 10-11 with pc = pm = 0: every child copies a member.  With all fitness equal, the
+    stable sort keeps members before children, so the next population is the members in order;
+    with distinct fitness it is ascending, made of member rows, and starts with the best member
+    (which precedes its copies)."""
+    g = synth.named_graph("empty", 2000)  # every deletion set has PC 0: all tied
+    s, k, lam = 10, 8, 25
+    pop = _distinct_population(g.n, k, s, 7)
+    tied = oracle.fitness(g.row_ptr, g.col, pop)
+    out, fout = oracle.generation(g.row_ptr, g.col, pop, tied, 1, tourn=2, pc_thr=0, pm_thr=0, seed=SEED,
+                                  flags=oracle.FLAG_MU_PLUS_LAMBDA, lam=lam)
+    assert np.array_equal(out, pop) and np.array_equal(fout, tied)
+    g = synth.ba_graph(400, 1, 3)  # a tree: deletions split it, so the members' PC differ
+    pop = _distinct_population(g.n, k, s, 8)
+    fit = oracle.fitness(g.row_ptr, g.col, pop)
+    assert len(set(fit.tolist())) > 3
+    out, fout = oracle.generation(g.row_ptr, g.col, pop, fit, 2, tourn=2, pc_thr=0, pm_thr=0, seed=SEED,
+                                  flags=oracle.FLAG_MU_PLUS_LAMBDA, lam=lam)
+    rows = {tuple(pop[i].tolist()): i for i in range(s)}
+    src = [rows[tuple(r.tolist())] for r in out]  # every kept row is a member row
+    assert np.array_equal(fout, fit[src]) and np.all(np.diff(fout) >= 0)
+    assert src[0] == int(np.argmin(fit))
+
+
+def test_mu_plus_lambda_truncation_properties():
+    g = _graph()
+    s, k, lam = 16, 20, 40
+    pc_thr, pm_thr = oracle.thresholds(0.8, 0.1)
+    pop = oracle.pop_init(g.n, k, s, SEED)
+    fit = oracle.fitness(g.row_ptr, g.col, pop)
+    for gen in range(1, 6):
+        out, fout = oracle.generation(g.row_ptr, g.col, pop, fit, gen, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr,
+                                      seed=SEED, flags=oracle.FLAG_MU_PLUS_LAMBDA, lam=lam)
+        assert np.all(np.diff(fout) >= 0)  # ascending
+        assert np.array_equal(fout, oracle.fitness(g.row_ptr, g.col, out, "uf"))
+        # the kept fitness values dominate the previous members: i-th best never gets worse
+        assert np.all(fout <= np.sort(fit))
+        assert all(len(set(r.tolist())) == k for r in out)
+        pop, fit = out, fout
+
+
+def test_roulette_and_mu_plus_lambda_run_reaches_optimum():
+    g = synth.er_graph(14, 22, 5)
+    k = 3
+    best = min(oracle.pc(g.row_ptr, g.col, np.array(c, dtype=np.int32))
+               for c in __import__("itertools").combinations(range(14), k))
+    pc_thr, pm_thr = oracle.thresholds(0.8, 0.1)
+    r = oracle.run(g.row_ptr, g.col, k=k, pop=20, gens=60, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr, seed=SEED,
+                   flags=oracle.FLAG_MU_PLUS_LAMBDA | oracle.FLAG_ROULETTE, lam=30)
+    assert r["best_fit"] == best
+    assert np.all(np.diff(r["traj"]) <= 0)
