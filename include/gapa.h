@@ -55,7 +55,9 @@ extern "C" {
 #define GAPA_WHERE_DEVICE 1
 
 /* gapa_config.flags */
-#define GAPA_FLAG_ROWWISE 1u  /* parent A of child i is member i itself (Eq. 6 read literally) */
+#define GAPA_FLAG_ROWWISE 1u        /* parent A of child i is member i itself (Eq. 6 read literally) */
+#define GAPA_FLAG_MU_PLUS_LAMBDA 2u /* (mu+lambda) elitism of Eqs. 10-11 with `lambda` children, below */
+#define GAPA_FLAG_ROULETTE 4u       /* roulette-wheel selection of Eq. 5 instead of tournaments */
 
 typedef struct gapa_ctx gapa_ctx; /* opaque, library-owned */
 
@@ -71,7 +73,20 @@ typedef struct gapa_config {
     uint32_t pm_thr; /* mutation mask threshold floor(pm * 2^32) (Eq. 8): mask = draw < pm_thr */
     uint64_t seed;   /* Philox key */
     uint32_t flags;  /* GAPA_FLAG_* */
+    int32_t lambda;  /* children per generation with GAPA_FLAG_MU_PLUS_LAMBDA (>= 1; mu + lambda <= 16384) */
 } gapa_config;
+
+/* Selection variants.  Tournament (default): t draws with replacement, lower
+ * fitness wins, ties to the lower index.  Roulette (GAPA_FLAG_ROULETTE,
+ * Eq. 5): for minimisation the weight of member x is (max F - F_x) + 1, the
+ * cumulative weights are int64, and a 64-bit Philox draw u (words 0 and 1 of
+ * counter (slot, child, g, 7 << 24)) picks the first member whose cumulative
+ * weight exceeds floor(u * W / 2^64).
+ * Generation variants.  Default: row 0 = the elite, rows 1..s-1 = children.
+ * GAPA_FLAG_MU_PLUS_LAMBDA (Eqs. 10-11): `lambda` children (counter index
+ * 0..lambda-1) are bred from the s = mu members, and the mu rows of lowest
+ * fitness among [members; children] (stable: members first, lower index
+ * first) form the next population, sorted ascending. */
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * (NULL = the legacy default stream) that the context borrows for all work;

@@ -9,10 +9,12 @@ from .gapa import (
     Context,
     GapaError,
     EXPORTS,
+    FLAG_MU_PLUS_LAMBDA,
+    FLAG_ROULETTE,
     FLAG_ROWWISE,
     load,
     make_config,
     threshold,
 )
 
-__all__ = ["Batch", "Config", "Context", "GapaError", "EXPORTS", "FLAG_ROWWISE", "load", "make_config", "threshold"]
+__all__ = ["Batch", "Config", "Context", "GapaError", "EXPORTS", "FLAG_MU_PLUS_LAMBDA", "FLAG_ROULETTE", "FLAG_ROWWISE", "load", "make_config", "threshold"]

@@ -170,7 +170,16 @@ int check_cfg(gapa_ctx* c, const gapa_config* cfg) {
     if (cfg->tourn < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "tournament size must be >= 1");
     if (cfg->elite != 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "elite count must be 1 (got %d)", cfg->elite);
     if (cfg->gens < 0) return gapa_fail(GAPA_ERR_INVALID_ARG, "gens must be >= 0");
-    if (cfg->flags & ~GAPA_FLAG_ROWWISE) return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
+    if (cfg->flags & ~(GAPA_FLAG_ROWWISE | GAPA_FLAG_MU_PLUS_LAMBDA | GAPA_FLAG_ROULETTE))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
+    if (cfg->flags & GAPA_FLAG_MU_PLUS_LAMBDA) {
+        if (cfg->lambda < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "(mu+lambda) needs lambda >= 1");
+        if (cfg->flags & GAPA_FLAG_ROWWISE)
+            return gapa_fail(GAPA_ERR_INVALID_ARG, "the row-wise flag has no meaning with (mu+lambda)");
+        if ((long long)cfg->pop + cfg->lambda > 16384)
+            return gapa_fail(GAPA_ERR_INVALID_ARG, "mu + lambda must be at most 16384");
+        if ((long long)cfg->lambda * cfg->k >= (1LL << 31)) return gapa_fail(GAPA_ERR_INVALID_ARG, "lambda*k too large");
+    }
     return gapa_ga_check_limits(c, c->g.n, cfg->k, cfg->pop);
 }
 
@@ -186,13 +195,46 @@ GaParams make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_pt
     p.flags = cfg->flags;
     p.g = g;
     p.g_ptr = g_ptr;
+    p.cum = nullptr;
     return p;
 }
 
-// One generation on stream st: offspring rows, then fitness of rows 1..s-1.
-int enqueue_generation(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,
+// Scratch of the (mu+lambda) and roulette variants, reserved outside any capture.
+int ensure_variant_scratch(gapa_ctx* c, const gapa_config* cfg) {
+    int rc = GAPA_OK;
+    if (cfg->flags & GAPA_FLAG_ROULETTE) rc = gapa_reserve((void**)&c->cum, &c->cum_cap, (size_t)cfg->pop, 8);
+    if (rc == GAPA_OK && (cfg->flags & GAPA_FLAG_MU_PLUS_LAMBDA)) {
+        rc = gapa_reserve((void**)&c->kids, &c->kids_cap, (size_t)cfg->lambda * cfg->k, 4);
+        if (rc == GAPA_OK) rc = gapa_reserve((void**)&c->kfit, &c->kfit_cap, (size_t)cfg->lambda, 8);
+        if (rc == GAPA_OK) rc = gapa_reserve((void**)&c->src, &c->src_cap, (size_t)cfg->pop, 4);
+    }
+    if (rc == GAPA_OK)
+        rc = gapa_fitness_prepare(c, (cfg->flags & GAPA_FLAG_MU_PLUS_LAMBDA) ? std::max(cfg->pop, cfg->lambda)
+                                                                             : cfg->pop);
+    return rc;
+}
+
+// One generation on stream st.  Default: offspring rows (elite + children),
+// then fitness of rows 1..s-1.  (mu+lambda): lambda children, their fitness,
+// then the truncation of members + children.  Roulette weights first if used.
+int enqueue_generation(gapa_ctx* c, const GaParams& p0, int lambda, const int32_t* pop_in, const int64_t* fit_in,
                        int32_t* pop_out, int64_t* fit_out, cudaStream_t st) {
-    int rc = gapa_launch_offspring(c, p, pop_in, fit_in, pop_out, fit_out, st);
+    GaParams p = p0;
+    int rc = GAPA_OK;
+    if (p.flags & GAPA_FLAG_ROULETTE) {
+        rc = gapa_launch_roulette_prefix(fit_in, p.s, c->cum, st);
+        p.cum = reinterpret_cast<const long long*>(c->cum);
+        if (rc != GAPA_OK) return rc;
+    }
+    if (p.flags & GAPA_FLAG_MU_PLUS_LAMBDA) {
+        rc = gapa_launch_children(c, p, lambda, pop_in, fit_in, c->kids, st);
+        if (rc == GAPA_OK) rc = gapa_launch_fitness(c, c->kids, lambda, p.k, c->kfit, st);
+        if (rc == GAPA_OK)
+            rc = gapa_launch_mpl_replace(c, p.s, lambda, p.k, pop_in, fit_in, c->kids, c->kfit, c->src, pop_out,
+                                         fit_out, st);
+        return rc;
+    }
+    rc = gapa_launch_offspring(c, p, pop_in, fit_in, pop_out, fit_out, st);
     if (rc != GAPA_OK) return rc;
     return gapa_launch_fitness(c, pop_out + p.k, p.s - 1, p.k, fit_out + 1, st);
 }
@@ -346,6 +388,10 @@ void gapa_destroy(gapa_ctx* c) {
     cudaFree(c->run_gen);
     cudaFree(c->run_best);
     cudaFree(c->run_traj);
+    cudaFree(c->kids);
+    cudaFree(c->kfit);
+    cudaFree(c->cum);
+    cudaFree(c->src);
     for (auto& t : c->timed) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
@@ -516,7 +562,10 @@ int gapa_generation(gapa_ctx* c, const gapa_config* cfg, int32_t g, const int32_
         return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL pointer");
     if (pop_in == pop_out || fit_in == fit_out) return gapa_fail(GAPA_ERR_INVALID_ARG, "outputs alias inputs");
     DeviceGuard guard(c->device);
-    return enqueue_generation(c, make_params(c, cfg, g, nullptr), pop_in, fit_in, pop_out, fit_out, c->stream);
+    rc = ensure_variant_scratch(c, cfg);
+    if (rc != GAPA_OK) return rc;
+    return enqueue_generation(c, make_params(c, cfg, g, nullptr), cfg->lambda, pop_in, fit_in, pop_out, fit_out,
+                              c->stream);
 }
 
 int gapa_generation_host(gapa_ctx* c, const gapa_config* cfg, int32_t g, const int32_t* pop_in_host,
@@ -531,11 +580,13 @@ int gapa_generation_host(gapa_ctx* c, const gapa_config* cfg, int32_t g, const i
     const size_t cells = (size_t)cfg->pop * cfg->k;
     rc = ensure_stage(c, cells, (size_t)cfg->pop);
     if (rc != GAPA_OK) return rc;
+    rc = ensure_variant_scratch(c, cfg);
+    if (rc != GAPA_OK) return rc;
     cudaStream_t st = c->stream;
     if (cells) GAPA_CUDA(cudaMemcpyAsync(c->stage_pop[0], pop_in_host, sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
     GAPA_CUDA(cudaMemcpyAsync(c->stage_fit[0], fit_in_host, sizeof(int64_t) * cfg->pop, cudaMemcpyHostToDevice, st));
-    rc = enqueue_generation(c, make_params(c, cfg, g, nullptr), c->stage_pop[0], c->stage_fit[0], c->stage_pop[1],
-                            c->stage_fit[1], st);
+    rc = enqueue_generation(c, make_params(c, cfg, g, nullptr), cfg->lambda, c->stage_pop[0], c->stage_fit[0],
+                            c->stage_pop[1], c->stage_fit[1], st);
     if (rc != GAPA_OK) return rc;
     if (cells) GAPA_CUDA(cudaMemcpyAsync(pop_out_host, c->stage_pop[1], sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st));
     GAPA_CUDA(cudaMemcpyAsync(fit_out_host, c->stage_fit[1], sizeof(int64_t) * cfg->pop, cudaMemcpyDeviceToHost, st));
@@ -553,7 +604,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
     const size_t cells = (size_t)s * k;
     rc = ensure_stage(c, cells, (size_t)s);
     if (rc == GAPA_OK) rc = gapa_reserve((void**)&c->run_traj, &c->run_traj_cap, (size_t)G + 1, sizeof(int64_t));
-    if (rc == GAPA_OK) rc = gapa_fitness_prepare(c, s);
+    if (rc == GAPA_OK) rc = ensure_variant_scratch(c, cfg);
     if (rc != GAPA_OK) return rc;
     cudaStream_t st = c->own_stream;
     // order after the caller's pending work
@@ -576,7 +627,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
         c->capturing = true;
         int crc = GAPA_OK;
         for (int h = 0; h < 2 && crc == GAPA_OK; ++h) {
-            crc = enqueue_generation(c, pg, P[h], F[h], P[h ^ 1], F[h ^ 1], st);
+            crc = enqueue_generation(c, pg, cfg->lambda, P[h], F[h], P[h ^ 1], F[h ^ 1], st);
             if (crc == GAPA_OK) crc = gapa_launch_record(c, F[h ^ 1], s, c->run_gen, c->run_traj, c->run_best, st);
         }
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
@@ -598,7 +649,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
     }
     if (G % 2 == 1) {
         // the last (odd) generation, launched directly: P0 -> P1
-        rc = enqueue_generation(c, pg, P[0], F[0], P[1], F[1], st);
+        rc = enqueue_generation(c, pg, cfg->lambda, P[0], F[0], P[1], F[1], st);
         if (rc == GAPA_OK) rc = gapa_launch_record(c, F[1], s, c->run_gen, c->run_traj, c->run_best, st);
         if (rc != GAPA_OK) return rc;
     }

@@ -229,6 +229,7 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         if (!c->g.packed16)
             return gapa_fail(GAPA_ERR_INVALID_ARG, "instance %d: batched runs need graphs whose labels fit in shared memory (n=%d)", i, c->g.n);
         const gapa_config& g = cfgs[i];
+        // batched runs implement the default generation (one elite, tournaments) and the row-wise flag
         if (g.k < 0 || g.k >= c->g.n || g.pop < 2 || g.tourn < 1 || g.elite != 1 || (g.flags & ~GAPA_FLAG_ROWWISE))
             return gapa_fail(GAPA_ERR_INVALID_ARG, "instance %d: invalid configuration", i);
     }

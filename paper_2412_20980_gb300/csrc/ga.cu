@@ -153,6 +153,28 @@ __device__ int tournament(const GaParams& p, int i, int g, int slot, const long 
     return best;
 }
 
+// Roulette-wheel draw (Eq. 5) for parent slot `slot` of child i: the first
+// member whose cumulative weight exceeds floor(u * W / 2^64).
+__device__ int roulette(const GaParams& p, int i, int g, int slot) {
+    const unsigned long long u =
+        philox_word01((uint32_t)slot, (uint32_t)i, (uint32_t)g, (uint32_t)TAG_ROULETTE << 24, p.key.lo, p.key.hi);
+    const unsigned long long W = (unsigned long long)p.cum[p.s - 1];
+    const unsigned long long r = __umul64hi(u, W);
+    int lo = 0, hi = p.s - 1;  // smallest x with cum[x] > r
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((unsigned long long)p.cum[mid] > r)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ int select_parent(const GaParams& p, int i, int g, int slot, const long long* fit) {
+    return (p.flags & GAPA_FLAG_ROULETTE) ? roulette(p, i, g, slot) : tournament(p, i, g, slot, fit);
+}
+
 // Block argmin of fit[0..s) (lowest value, lowest index); result valid in all threads.
 __device__ void block_argmin(const long long* __restrict__ fit, int s, long long* out_val, int* out_idx) {
     __shared__ long long sv[32];
@@ -202,15 +224,16 @@ __device__ void block_argmin(const long long* __restrict__ fit, int s, long long
     *out_idx = si[0];
 }
 
-// Row i of one generation g: row 0 = elite copy, row i >= 1 = child i.
+// Row i of one generation g: with an elite, row 0 = elite copy and row i >= 1
+// = child i; without (the (mu+lambda) children), row i = child with counter i.
 __device__ void offspring_row(const GaParams& p, int i, int g, const int* __restrict__ pop_in,
                               const long long* __restrict__ fit_in, int* __restrict__ pop_out,
-                              long long* __restrict__ fit_out, int* status) {
+                              long long* __restrict__ fit_out, int* status, bool has_elite = true) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sh_parent[2];
     __shared__ int sh_warp_cnt[kGaBlock / 32];
     const int n = p.n, k = p.k;
-    if (i == 0) {
+    if (has_elite && i == 0) {
         long long v;
         int e;
         block_argmin(fit_in, p.s, &v, &e);
@@ -221,8 +244,8 @@ __device__ void offspring_row(const GaParams& p, int i, int g, const int* __rest
     }
     RowSmem sm = carve(smem, n, k);
     if (threadIdx.x == 0) {
-        sh_parent[0] = (p.flags & GAPA_FLAG_ROWWISE) ? i : tournament(p, i, g, 0, fit_in);
-        sh_parent[1] = tournament(p, i, g, 1, fit_in);
+        sh_parent[0] = (p.flags & GAPA_FLAG_ROWWISE) ? i : select_parent(p, i, g, 0, fit_in);
+        sh_parent[1] = select_parent(p, i, g, 1, fit_in);
     }
     clear_bitmap(sm.kept, n);
     __syncthreads();
@@ -298,6 +321,104 @@ __global__ void __launch_bounds__(kGaBlock) offspring_kernel(GaParams p, const i
                                                              int* __restrict__ pop_out,
                                                              long long* __restrict__ fit_out, int* status) {
     offspring_row(p, blockIdx.x, p.g_ptr ? *p.g_ptr : p.g, pop_in, fit_in, pop_out, fit_out, status);
+}
+
+// (mu+lambda) children: row i = child with counter index i, parents among the s members.
+__global__ void __launch_bounds__(kGaBlock) children_kernel(GaParams p, const int* __restrict__ pop_in,
+                                                            const long long* __restrict__ fit_in,
+                                                            int* __restrict__ kids, int* status) {
+    offspring_row(p, blockIdx.x, p.g_ptr ? *p.g_ptr : p.g, pop_in, fit_in, kids, nullptr, status, false);
+}
+
+// Roulette weights w_x = (max F - F_x) + 1 and their int64 inclusive prefix sums (one CTA).
+__global__ void __launch_bounds__(1024) roulette_prefix_kernel(const long long* __restrict__ fit, int s,
+                                                               long long* __restrict__ cum) {
+    __shared__ long long sh[32];
+    __shared__ long long carry;
+    long long mx = LLONG_MIN;
+    for (int x = threadIdx.x; x < s; x += blockDim.x) mx = fit[x] > mx ? fit[x] : mx;
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long m = sh[0];
+        for (int w = 1; w < nw; ++w) m = sh[w] > m ? sh[w] : m;
+        sh[0] = m;
+        carry = 0;
+    }
+    __syncthreads();
+    const long long fmax = sh[0];
+    __syncthreads();
+    for (int base = 0; base < s; base += blockDim.x) {
+        const int x = base + threadIdx.x;
+        long long v = x < s ? (fmax - fit[x]) + 1 : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) sh[warp] = v;
+        __syncthreads();
+        long long off = carry;
+        for (int w = 0; w < warp; ++w) off += sh[w];
+        if (x < s) cum[x] = v + off;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = v + off;
+        __syncthreads();
+    }
+}
+
+// (mu+lambda) truncation (Eqs. 10-11): bitonic sort of (fitness, index) over
+// members (index x) and children (index mu + c); the first mu give the source
+// rows (src) and the new fitness.  One CTA, keys in shared memory.
+__global__ void __launch_bounds__(1024) mpl_sort_kernel(int mu, int lambda, const long long* __restrict__ fit_in,
+                                                        const long long* __restrict__ kfit, int* __restrict__ src,
+                                                        long long* __restrict__ fit_out, int P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long* key = reinterpret_cast<long long*>(smem);
+    int* idx = reinterpret_cast<int*>(key + P);
+    const int tot = mu + lambda;
+    for (int x = threadIdx.x; x < P; x += blockDim.x) {
+        key[x] = x < mu ? fit_in[x] : (x < tot ? kfit[x - mu] : LLONG_MAX);
+        idx[x] = x < tot ? x : INT_MAX;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int x = threadIdx.x; x < P; x += blockDim.x) {
+                const int y = x ^ stride;
+                if (y > x) {
+                    const bool up = (x & size) == 0;
+                    const bool gt = key[x] > key[y] || (key[x] == key[y] && idx[x] > idx[y]);
+                    if (gt == up) {
+                        const long long tk = key[x];
+                        key[x] = key[y];
+                        key[y] = tk;
+                        const int ti = idx[x];
+                        idx[x] = idx[y];
+                        idx[y] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = threadIdx.x; r < mu; r += blockDim.x) {
+        src[r] = idx[r];
+        fit_out[r] = key[r];
+    }
+}
+
+// Next population rows from members (src < mu) or children.
+__global__ void __launch_bounds__(kGaBlock) mpl_gather_kernel(int mu, int k, const int* __restrict__ pop_in,
+                                                              const int* __restrict__ kids, const int* __restrict__ src,
+                                                              int* __restrict__ pop_out) {
+    const int r = blockIdx.x, x = src[r];
+    const int* from = x < mu ? pop_in + (size_t)x * k : kids + (size_t)(x - mu) * k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) pop_out[(size_t)r * k + j] = from[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -417,8 +538,42 @@ int gapa_ga_batched_init(size_t optin, size_t* max_dyn) {
     return rc;
 }
 
+int gapa_launch_roulette_prefix(const int64_t* fit, int s, int64_t* cum, cudaStream_t st) {
+    roulette_prefix_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const long long*>(fit), s,
+                                               reinterpret_cast<long long*>(cum));
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_launch_children(gapa_ctx* c, const GaParams& p, int lambda, const int32_t* pop_in, const int64_t* fit_in,
+                         int32_t* kids, cudaStream_t st) {
+    ProfileScope prof(c, st, 1, 0);
+    children_kernel<<<lambda, kGaBlock, row_smem_bytes(p.n, p.k), st>>>(p, pop_in,
+                                                                       reinterpret_cast<const long long*>(fit_in),
+                                                                       kids, c->status);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int gapa_launch_mpl_replace(gapa_ctx* c, int mu, int lambda, int k, const int32_t* pop_in, const int64_t* fit_in,
+                            const int32_t* kids, const int64_t* kfit, int* src, int32_t* pop_out, int64_t* fit_out,
+                            cudaStream_t st) {
+    int P = 1;
+    while (P < mu + lambda) P <<= 1;
+    const size_t smem = (size_t)P * (sizeof(long long) + sizeof(int));
+    if (smem > c->sort_smem_max) return gapa_fail(GAPA_ERR_INVALID_ARG, "mu + lambda = %d is too large", mu + lambda);
+    mpl_sort_kernel<<<1, 1024, smem, st>>>(mu, lambda, reinterpret_cast<const long long*>(fit_in),
+                                           reinterpret_cast<const long long*>(kfit), src,
+                                           reinterpret_cast<long long*>(fit_out), P);
+    if (k > 0) mpl_gather_kernel<<<mu, kGaBlock, 0, st>>>(mu, k, pop_in, kids, src, pop_out);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
 int gapa_ga_kernels_init(gapa_ctx* c) {
     int rc = gapa_set_smem_limit((const void*)init_kernel, c->smem_optin, &c->ga_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)offspring_kernel, c->smem_optin, &c->ga_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)children_kernel, c->smem_optin, &c->ga_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)mpl_sort_kernel, c->smem_optin, &c->sort_smem_max);
     return rc;
 }

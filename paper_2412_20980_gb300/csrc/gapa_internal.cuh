@@ -27,6 +27,7 @@ enum : uint32_t {
     TAG_MUT = 4,
     TAG_MUTVAL = 5,
     TAG_REPAIR = 6,
+    TAG_ROULETTE = 7,
 };
 
 constexpr int kRepairRounds = 32;
@@ -60,6 +61,26 @@ struct RngKey {
 __device__ __forceinline__ uint32_t gapa_draw(RngKey key, uint32_t j, uint32_t i, uint32_t g, uint32_t tag,
                                               uint32_t round) {
     return philox_word0(j, i, g, (tag << 24) | round, key.lo, key.hi);
+}
+
+// Words 0 and 1 of Philox4x32-10 as one 64-bit number (word 0 high).
+__device__ __forceinline__ unsigned long long philox_word01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                           uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        const uint32_t hi0 = __umulhi(m0, c0), lo0 = m0 * c0;
+        const uint32_t hi1 = __umulhi(m1, c2), lo1 = m1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return ((unsigned long long)c0 << 32) | c1;
 }
 
 // Uniform integer in [0, n): multiply-high of a 32-bit word by n.
@@ -115,6 +136,16 @@ struct gapa_ctx {
     int64_t* run_traj = nullptr;
     size_t run_traj_cap = 0;
     int fitness_variant = 0;  // 0 = auto
+    // (mu+lambda) and roulette scratch
+    int32_t* kids = nullptr;
+    size_t kids_cap = 0;      // ints
+    int64_t* kfit = nullptr;
+    size_t kfit_cap = 0;
+    int64_t* cum = nullptr;
+    size_t cum_cap = 0;
+    int* src = nullptr;
+    size_t src_cap = 0;
+    size_t sort_smem_max = 0;
     // profiling (gapa_profile_begin/end): event pairs around launches
     bool profiling = false;
     bool capturing = false;
@@ -163,6 +194,7 @@ struct GaParams {
     uint32_t flags;
     int g;               // generation when g_ptr is null
     const int* g_ptr;    // device-resident generation counter (CUDA-graph replay)
+    const long long* cum;  // roulette cumulative weights [s] (GAPA_FLAG_ROULETTE)
 };
 
 // One instance of a batched run (device-side descriptor).
@@ -208,5 +240,11 @@ int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in,
                           int32_t* pop_out, int64_t* fit_out, cudaStream_t st);
 int gapa_launch_record(gapa_ctx* c, const int64_t* fit, int s, int* gen, int64_t* traj, int* best,
                        cudaStream_t st);
+int gapa_launch_roulette_prefix(const int64_t* fit, int s, int64_t* cum, cudaStream_t st);
+int gapa_launch_children(gapa_ctx* c, const GaParams& p, int lambda, const int32_t* pop_in, const int64_t* fit_in,
+                         int32_t* kids, cudaStream_t st);
+int gapa_launch_mpl_replace(gapa_ctx* c, int mu, int lambda, int k, const int32_t* pop_in, const int64_t* fit_in,
+                            const int32_t* kids, const int64_t* kfit, int* src, int32_t* pop_out, int64_t* fit_out,
+                            cudaStream_t st);
 int gapa_ga_check_limits(gapa_ctx* c, int n, int k, int s);
 int gapa_kernels_init(gapa_ctx* c);

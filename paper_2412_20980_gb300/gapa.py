@@ -27,7 +27,7 @@ ERRORS = {
     -7: "DEVICE",
 }
 WHERE_HOST, WHERE_DEVICE = 0, 1
-FLAG_ROWWISE = 1
+FLAG_ROWWISE, FLAG_MU_PLUS_LAMBDA, FLAG_ROULETTE = 1, 2, 4
 
 # every entry point declared in include/gapa.h
 EXPORTS = [
@@ -75,6 +75,7 @@ class Config(ctypes.Structure):
         ("pm_thr", ctypes.c_uint32),
         ("seed", ctypes.c_uint64),
         ("flags", ctypes.c_uint32),
+        ("lam", ctypes.c_int32),
     ]
 
 
@@ -84,8 +85,8 @@ def threshold(p: float) -> int:
 
 
 def make_config(k: int, pop: int, gens: int = 0, tourn: int = 2, pc: float = 0.8, pm: float = 0.02,
-                seed: int = 0, flags: int = 0, elite: int = 1) -> Config:
-    return Config(k, pop, gens, tourn, elite, threshold(pc), threshold(pm), seed & (2**64 - 1), flags)
+                seed: int = 0, flags: int = 0, elite: int = 1, lam: int = 0) -> Config:
+    return Config(k, pop, gens, tourn, elite, threshold(pc), threshold(pm), seed & (2**64 - 1), flags, lam)
 
 
 _lock = threading.Lock()

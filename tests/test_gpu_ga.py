@@ -39,11 +39,11 @@ def test_pop_init_bit_exact(ctx, n, k, s, seed):
     assert np.array_equal(pop.cpu().numpy(), oracle.pop_init(n, k, s, seed))
 
 
-def _gen_case(ctx, g, k, s, pc, pm, tourn, seed, flags, gens):
+def _gen_case(ctx, g, k, s, pc, pm, tourn, seed, flags, gens, lam=0):
     import torch
 
     ctx.graph_upload(g.row_ptr, g.col)
-    cfg = _cfg(k=k, pop=s, tourn=tourn, pc=pc, pm=pm, seed=seed, flags=flags)
+    cfg = _cfg(k=k, pop=s, tourn=tourn, pc=pc, pm=pm, seed=seed, flags=flags, lam=lam)
     pop = ctx.pop_init(cfg)
     fit = ctx.fitness(pop)
     wp = oracle.pop_init(g.n, k, s, seed)
@@ -51,7 +51,7 @@ def _gen_case(ctx, g, k, s, pc, pm, tourn, seed, flags, gens):
     for gen in range(1, gens + 1):
         pop, fit = ctx.generation(cfg, gen, pop, fit)
         wp, wf = oracle.generation(g.row_ptr, g.col, wp, wf, gen, tourn=tourn, pc_thr=cfg.pc_thr, pm_thr=cfg.pm_thr,
-                                   seed=seed, flags=flags)
+                                   seed=seed, flags=flags, lam=lam, nthreads=oracle.max_threads())
         ctx.sync()
         assert np.array_equal(pop.cpu().numpy(), wp), gen
         assert np.array_equal(fit.cpu().numpy(), wf), gen
@@ -132,3 +132,44 @@ def test_invalid_configs(ctx):
         with pytest.raises(GapaError) as ei:
             ctx.pop_init(_cfg(**kw), out=out)
         assert ei.value.code == -1
+
+
+ROULETTE, MPL = 4, 2
+
+
+@pytest.mark.parametrize("flags,lam,pm", [(ROULETTE, 0, 0.02), (MPL, 150, 0.02), (MPL | ROULETTE, 64, 0.1),
+                                          (MPL, 1, 0.02), (MPL, 400, 0.3)])
+def test_selection_and_elitism_variants_bit_exact(ctx, flags, lam, pm):
+    """Roulette (Eq. 5) and (mu+lambda) truncation (Eqs. 10-11) against the oracle."""
+    _gen_case(ctx, synth.ba_graph(1000, 3, 1), 50, 100, 0.8, pm, 2, 3, flags, 4, lam=lam)
+
+
+def test_mu_plus_lambda_large_graph(ctx):
+    _gen_case(ctx, synth.ba_graph(100000, 3, 1), 2000, 16, 0.8, 0.02, 2, 4, MPL | ROULETTE, 2, lam=40)
+
+
+@pytest.mark.parametrize("gens", [1, 6])
+def test_run_variants_bit_exact(ctx, gens):
+    g = synth.hk_graph(3000, 3, 0.3, 6)
+    ctx.graph_upload(g.row_ptr, g.col)
+    cfg = _cfg(k=150, pop=64, gens=gens, tourn=2, pc=0.8, pm=0.05, seed=8, flags=MPL | ROULETTE, lam=192)
+    got = ctx.run(cfg, want_pop=True)
+    want = oracle.run(g.row_ptr, g.col, k=150, pop=64, gens=gens, tourn=2, pc_thr=cfg.pc_thr, pm_thr=cfg.pm_thr,
+                      seed=8, flags=MPL | ROULETTE, lam=192, nthreads=oracle.max_threads())
+    assert np.array_equal(got["traj"], want["traj"])
+    assert np.array_equal(got["pop"].cpu().numpy(), want["pop"])
+    assert np.array_equal(got["best_set"], want["best_set"])
+
+
+def test_variant_configs_rejected(ctx):
+    import torch
+
+    from paper_2412_20980_gb300 import GapaError
+
+    g = synth.ba_graph(500, 2, 1)
+    ctx.graph_upload(g.row_ptr, g.col)
+    out = torch.empty((16, 8), dtype=torch.int32, device="cuda")
+    for kw in (dict(k=5, pop=10, flags=MPL, lam=0), dict(k=5, pop=10, flags=MPL | 1, lam=5),
+               dict(k=5, pop=10000, flags=MPL, lam=7000)):
+        with pytest.raises(GapaError):
+            ctx.pop_init(_cfg(**kw), out=out)
