@@ -1,0 +1,121 @@
+"""Plain fp64 reference of the fitness surrogate (test infrastructure only).
+
+The surrogate is not part of the paper: it pre-screens children so that only
+the most promising fraction gets the exact pairwise-connectivity fitness of
+Section III-C.  Definition shared with the CUDA implementation:
+
+  features of a deletion set D (k genes) on a graph with degrees d and E edges
+    e(D)  = (1 / sqrt(k)) * sum_{v in D} Emb[v]                 (64 values)
+    q_v   = log1p(d_v);  f1 = mean q, f2 = max q,
+    f3    = sqrt(max(mean q^2 - f1^2, 0)),  f4 = sum d_v / (2E)
+    x     = [e(D), f1, f2, f3, f4, 0 x 12]                       (80 values)
+  model   z1 = x W1 + b1, h1 = relu(z1)   (W1: 80 x 256)
+          z2 = h1 W2 + b2, h2 = relu(z2)  (W2: 256 x 256)
+          y  = h2 . w3 + b3
+  loss    mean over the batch of (y - t)^2
+  AdamW   (Loshchilov & Hutter, ICLR 2019) on every parameter, step tau >= 1:
+          m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2
+          p = p - lr * ( (m / (1 - b1^tau)) / (sqrt(v / (1 - b2^tau)) + eps) + wd * p )
+
+Parameters are a dict of numpy arrays: W1 (80, 256), b1 (256,), W2 (256, 256),
+b2 (256,), w3 (256,), b3 (1,), E (n, 64).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+IN, HID, EMB = 80, 256, 64
+
+
+def degrees_from_csr(row_ptr) -> np.ndarray:
+    return np.diff(np.asarray(row_ptr, dtype=np.int64)).astype(np.float64)
+
+
+def features(pop: np.ndarray, E: np.ndarray, deg: np.ndarray, num_edges: int) -> np.ndarray:
+    """x for every row of pop (int32[s][k]) -> float64[s][80]."""
+    pop = np.asarray(pop)
+    s, k = pop.shape
+    x = np.zeros((s, IN), dtype=np.float64)
+    q = np.log1p(deg)
+    for i in range(s):
+        genes = pop[i]
+        x[i, :EMB] = E[genes].sum(axis=0) / np.sqrt(k)
+        qi = q[genes]
+        f1 = qi.mean()
+        x[i, 64] = f1
+        x[i, 65] = qi.max()
+        x[i, 66] = np.sqrt(max((qi * qi).mean() - f1 * f1, 0.0))
+        x[i, 67] = deg[genes].sum() / (2.0 * num_edges)
+    return x
+
+
+def forward(params: dict, x: np.ndarray) -> tuple[np.ndarray, dict]:
+    z1 = x @ params["W1"] + params["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ params["W2"] + params["b2"]
+    h2 = np.maximum(z2, 0.0)
+    y = h2 @ params["w3"] + params["b3"][0]
+    return y, {"x": x, "z1": z1, "h1": h1, "z2": z2, "h2": h2}
+
+
+def loss_and_grads(params: dict, pop: np.ndarray, t: np.ndarray, deg: np.ndarray, num_edges: int):
+    """MSE loss of the batch and the gradient of every parameter (fp64)."""
+    k = pop.shape[1]
+    x = features(pop, params["E"], deg, num_edges)
+    y, c = forward(params, x)
+    B = y.shape[0]
+    loss = float(np.mean((y - t) ** 2))
+    dy = 2.0 * (y - t) / B
+    g = {"w3": c["h2"].T @ dy, "b3": np.array([dy.sum()])}
+    dz2 = np.outer(dy, params["w3"]) * (c["z2"] > 0)
+    g["W2"] = c["h1"].T @ dz2
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ params["W2"].T) * (c["z1"] > 0)
+    g["W1"] = x.T @ dz1
+    g["b1"] = dz1.sum(axis=0)
+    dx = dz1 @ params["W1"].T
+    gE = np.zeros_like(params["E"])
+    for b in range(B):
+        np.add.at(gE, pop[b], dx[b, :EMB] / np.sqrt(k))
+    g["E"] = gE
+    return loss, g, y
+
+
+def adamw_step(params: dict, grads: dict, state: dict, tau: int, lr=1e-3, b1=0.9, b2=0.999, wd=0.01, eps=1e-8):
+    """One AdamW step in place; state holds m and v per parameter."""
+    for name, p in params.items():
+        gr = grads[name]
+        m = state.setdefault(("m", name), np.zeros_like(p))
+        v = state.setdefault(("v", name), np.zeros_like(p))
+        m *= b1
+        m += (1 - b1) * gr
+        v *= b2
+        v += (1 - b2) * gr * gr
+        mh = m / (1 - b1 ** tau)
+        vh = v / (1 - b2 ** tau)
+        p -= lr * (mh / (np.sqrt(vh) + eps) + wd * p)
+
+
+def spearman(a, b) -> float:
+    """Spearman rank correlation (average ranks for ties)."""
+    def ranks(x):
+        x = np.asarray(x, dtype=np.float64)
+        order = np.argsort(x, kind="stable")
+        r = np.empty_like(x)
+        r[order] = np.arange(x.size, dtype=np.float64)
+        # average ties
+        xs = x[order]
+        i = 0
+        while i < x.size:
+            j = i
+            while j + 1 < x.size and xs[j + 1] == xs[i]:
+                j += 1
+            if j > i:
+                r[order[i:j + 1]] = (i + j) / 2.0
+            i = j + 1
+        return r
+    ra, rb = ranks(a), ranks(b)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = np.sqrt((ra * ra).sum() * (rb * rb).sum())
+    return float((ra * rb).sum() / den) if den > 0 else 0.0
