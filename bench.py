@@ -99,7 +99,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("fitness.cu", "fitness_ig.cu", "gapa_internal.cuh"):
+    for f in ("fitness.cu", "fitness_ig.cu", "tree16.cuh", "gapa_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2412_20980_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

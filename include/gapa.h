@@ -190,6 +190,63 @@ int gapa_batch_autotune(gapa_batch* batch, const char* cache_path);
  * and after every generation (may be NULL).  Synchronous. */
 int gapa_batch_run(gapa_batch* batch, int32_t gens, int64_t* best_fit, int32_t* best_sets, int64_t* traj);
 
+/* ---- Learned fitness surrogate (an extension; the paper has no surrogate) ----
+ * A small MLP scores children so that only the most promising fraction gets
+ * the exact fitness of Section III-C; exact fitness stays the judge of every
+ * member kept.  Input of a deletion set D of k genes (80 values):
+ * (1/sqrt k) * sum of the 64-d embeddings of its genes, then the mean, maximum
+ * and standard deviation of log1p(degree) over D and sum(degree)/(2E), then
+ * zeros.  Model: 80 -> 256 ReLU -> 256 ReLU -> 1, BF16 weights on the tensor
+ * cores with FP32 accumulation; FP32 master weights, AdamW (Loshchilov &
+ * Hutter) on every parameter, MSE against the z-scored log1p of the exact
+ * fitness.  Training is deterministic (fixed-order reductions, fixed-point
+ * embedding-gradient sums). */
+typedef struct gapa_surrogate_config {
+    int32_t screened;     /* children evaluated exactly per generation once screening starts */
+    int32_t warmup;       /* generations in which every child is evaluated exactly */
+    int32_t train_steps;  /* AdamW steps per generation */
+    int32_t batch;        /* minibatch rows, a multiple of 16 */
+    int32_t ring;         /* replay ring capacity (rows of (deletion set, exact fitness)) */
+    float lr, beta1, beta2, weight_decay, eps;
+    float init_scale_emb; /* embeddings start uniform in [-a, a] */
+    int32_t diag_every;   /* every diag_every-th generation evaluates all children exactly and records
+                             (score, fitness) pairs; 0 = never */
+} gapa_surrogate_config;
+
+typedef struct gapa_surrogate gapa_surrogate;
+
+/* A surrogate for the context's graph, weights initialised from Philox(seed). */
+int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrogate_config* scfg, uint64_t seed);
+void gapa_surrogate_destroy(gapa_surrogate* sg);
+
+/* scores_dev[r] = model output for row r of pop_dev[rows][k].  Asynchronous. */
+int gapa_surrogate_predict(gapa_surrogate* sg, const int32_t* pop_dev, int32_t rows, int32_t k, float* scores_dev);
+
+/* One AdamW step on a minibatch (rows a multiple of 16) with device targets;
+ * *loss_host (may be NULL) receives the batch MSE before the step. */
+int gapa_surrogate_train_step(gapa_surrogate* sg, const int32_t* pop_dev, int32_t rows, int32_t k,
+                              const float* target_dev, float* loss_host);
+
+/* Copy a parameter (grad = 0) or its last gradient (grad = 1) to (set = 0)
+ * or from (set = 1) host memory.  which: 0 W1 [80][256], 1 b1, 2 W2
+ * [256][256] ([in][out]), 3 b2, 4 w3, 5 b3, 6 embeddings [n][64]. */
+int gapa_surrogate_tensor(gapa_surrogate* sg, int32_t which, int32_t grad, float* host, int64_t count, int32_t set);
+
+/* A (mu+lambda) run (cfg->flags must hold GAPA_FLAG_MU_PLUS_LAMBDA) whose
+ * children are screened by the surrogate: after `warmup` generations only
+ * the `screened` children with the lowest scores are evaluated exactly, the
+ * others are excluded from the truncation; every exactly evaluated child
+ * enters the replay ring and the model takes `train_steps` AdamW steps per
+ * generation.  sg = NULL runs the plain (mu+lambda) GA (every child exact) -
+ * the fallback - with the same outputs.  Outputs: best fitness and set,
+ * traj[gens+1], gen_ms[gens+1] (elapsed device time at the end of
+ * initialisation and of every generation, may be NULL), exact_evals[gens+1]
+ * (may be NULL), and diagnostic pairs (diag_pred, diag_exact, capacity
+ * diag_cap rows).  Synchronous. */
+int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg, int64_t* best_fit,
+                       int32_t* best_set, int64_t* traj, double* gen_ms, int64_t* exact_evals, float* diag_pred,
+                       int64_t* diag_exact, int32_t diag_cap);
+
 /* Fitness kernel selection (all are exact and give identical results):
  * TREE starts every member from a BFS spanning forest of G (numbered so that
  * parents precede children), cuts it at the deleted nodes and then joins the

@@ -8,6 +8,10 @@ from .gapa import (
     Config,
     Context,
     GapaError,
+    Surrogate,
+    SurrogateConfig,
+    make_surrogate_config,
+    run_surrogate,
     EXPORTS,
     FLAG_MU_PLUS_LAMBDA,
     FLAG_ROULETTE,
@@ -17,4 +21,5 @@ from .gapa import (
     threshold,
 )
 
-__all__ = ["Batch", "Config", "Context", "GapaError", "EXPORTS", "FLAG_MU_PLUS_LAMBDA", "FLAG_ROULETTE", "FLAG_ROWWISE", "load", "make_config", "threshold"]
+__all__ = ["Batch", "Config", "Context", "GapaError", "Surrogate", "SurrogateConfig", "make_surrogate_config",
+           "run_surrogate", "EXPORTS", "FLAG_MU_PLUS_LAMBDA", "FLAG_ROULETTE", "FLAG_ROWWISE", "load", "make_config", "threshold"]

@@ -273,6 +273,21 @@ int ensure_stage(gapa_ctx* c, size_t pop_elems, size_t fit_elems) {
 
 }  // namespace
 
+GaParams gapa_make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_ptr) {
+    return make_params(c, cfg, g, g_ptr);
+}
+
+// Validation and buffers of a whole run (outside any capture).
+int gapa_run_prepare(gapa_ctx* c, const gapa_config* cfg) {
+    int rc = check_cfg(c, cfg);
+    if (rc != GAPA_OK) return rc;
+    const size_t cells = (size_t)cfg->pop * cfg->k;
+    rc = ensure_stage(c, cells, (size_t)cfg->pop);
+    if (rc == GAPA_OK) rc = gapa_reserve((void**)&c->run_traj, &c->run_traj_cap, (size_t)cfg->gens + 1, sizeof(int64_t));
+    if (rc == GAPA_OK) rc = ensure_variant_scratch(c, cfg);
+    return rc;
+}
+
 int gapa_fail(int code, const char* fmt, ...) {
     char buf[1024];
     va_list ap;

@@ -247,4 +247,6 @@ int gapa_launch_mpl_replace(gapa_ctx* c, int mu, int lambda, int k, const int32_
                             const int32_t* kids, const int64_t* kfit, int* src, int32_t* pop_out, int64_t* fit_out,
                             cudaStream_t st);
 int gapa_ga_check_limits(gapa_ctx* c, int n, int k, int s);
+GaParams gapa_make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_ptr);
+int gapa_run_prepare(gapa_ctx* c, const gapa_config* cfg);
 int gapa_kernels_init(gapa_ctx* c);

@@ -1,0 +1,856 @@
+// Learned fitness surrogate and the surrogate-screened (mu+lambda) GA.
+//
+// Not part of the paper: a small MLP scores every child of a generation so
+// that only the most promising fraction receives the exact pairwise-
+// connectivity fitness of Section III-C; exact fitness stays the judge of
+// every member kept (Eqs. 10-11 truncation over members and evaluated
+// children).  The model is trained online on the (deletion set, exact
+// fitness) pairs the GA produces.
+//
+// Model (same definition as the fp64 reference):
+//   x  = [ (1/sqrt k) sum_{v in D} Emb[v] (64) | mean, max, std of log1p(deg)
+//          over D, sum deg / 2E | 0 x 12 ]                       (80)
+//   h1 = relu(x W1 + b1) (256), h2 = relu(h1 W2 + b2) (256), y = h2 . w3 + b3
+//   target t = z-score of log1p(PC) over the replay ring; loss = mean (y-t)^2
+//   AdamW on every parameter (FP32 masters and moments).
+// Precision: the matrix products run on the tensor cores (mma.sync m16n8k16,
+// BF16 operands, FP32 accumulation) with BF16 copies of the weights and
+// activations; biases, the output layer and the optimiser are FP32.  All
+// reductions run in a fixed order and the embedding gradient is accumulated
+// in 2^-40 fixed point with integer atomics, so training is deterministic.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "gapa_internal.cuh"
+
+namespace {
+
+constexpr int kIn = 80, kHid = 256, kEmb = 64;
+constexpr double kFix = 1099511627776.0;  // 2^40
+using bf16 = __nv_bfloat16;
+
+struct Layout {
+    size_t W1, b1, W2, b2, w3, b3, E, total;
+};
+
+Layout make_layout(int n) {
+    Layout L;
+    size_t o = 0;
+    L.W1 = o; o += (size_t)kIn * kHid;
+    L.b1 = o; o += kHid;
+    L.W2 = o; o += (size_t)kHid * kHid;
+    L.b2 = o; o += kHid;
+    L.w3 = o; o += kHid;
+    L.b3 = o; o += 4;
+    L.E = o; o += (size_t)n * kEmb;
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ unsigned ld32(const bf16* p, size_t idx) {
+    return *reinterpret_cast<const unsigned*>(p + idx);
+}
+
+// ---------------------------------------------------------------------------
+// C[M][N] = A[M][K] * B^T, A row-major (lda), B stored as [N][K] (ldb): the
+// tensor-core tile is mma.sync m16n8k16 (A row, B col, FP32 accumulate).
+// One warp computes 16 rows x 32 columns; a CTA has 4 warps (64 x 32).
+// M, K multiples of 16, N multiple of 8.  Epilogue: + bias[n], * (mask > 0),
+// relu, then FP32 and/or BF16 and/or transposed BF16 stores.
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+    int M, N, K;
+    const bf16* A;
+    int lda;
+    const bf16* B;
+    int ldb;
+    float* Cf;
+    int ldc;
+    bf16* Cb;
+    int ldcb;
+    bf16* CbT;
+    int ldct;
+    const float* bias;
+    const bf16* mask;
+    int ldm;
+    int relu;
+};
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+    const int r0 = blockIdx.y * 64 + warp * 16;
+    const int n_base = blockIdx.x * 32;
+    if (r0 >= a.M) return;
+    float acc[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
+    for (int k0 = 0; k0 < a.K; k0 += 16) {
+        const unsigned a0 = ld32(a.A, (size_t)(r0 + g) * a.lda + k0 + tig * 2);
+        const unsigned a1 = ld32(a.A, (size_t)(r0 + g + 8) * a.lda + k0 + tig * 2);
+        const unsigned a2 = ld32(a.A, (size_t)(r0 + g) * a.lda + k0 + 8 + tig * 2);
+        const unsigned a3 = ld32(a.A, (size_t)(r0 + g + 8) * a.lda + k0 + 8 + tig * 2);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int n0 = n_base + nt * 8;
+            if (n0 >= a.N) break;
+            const unsigned b0 = ld32(a.B, (size_t)(n0 + g) * a.ldb + k0 + tig * 2);
+            const unsigned b1 = ld32(a.B, (size_t)(n0 + g) * a.ldb + k0 + 8 + tig * 2);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int n0 = n_base + nt * 8;
+        if (n0 >= a.N) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int row = r0 + g + ((u & 2) ? 8 : 0);
+            const int col = n0 + tig * 2 + (u & 1);
+            float v = acc[nt][u];
+            if (a.bias) v += a.bias[col];
+            if (a.mask && !(__bfloat162float(a.mask[(size_t)row * a.ldm + col]) > 0.f)) v = 0.f;
+            if (a.relu) v = fmaxf(v, 0.f);
+            if (a.Cf) a.Cf[(size_t)row * a.ldc + col] = v;
+            if (a.Cb) a.Cb[(size_t)row * a.ldcb + col] = __float2bfloat16(v);
+            if (a.CbT) a.CbT[(size_t)col * a.ldct + row] = __float2bfloat16(v);
+        }
+    }
+}
+
+// Features of each row of pop (k genes): x (BF16 [rows_pad][80]) and its
+// transpose (BF16 [80][rows_pad]); rows >= rows are zero.
+__global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ pop, int rows, int k,
+                                                       const bf16* __restrict__ Eb, const float* __restrict__ logdeg,
+                                                       const float* __restrict__ deg, float inv2E, float invsqrtk,
+                                                       bf16* __restrict__ X, bf16* __restrict__ XT, int rows_pad) {
+    __shared__ float part[2][kEmb];
+    __shared__ float st[4][4];
+    const int r = blockIdx.x, t = threadIdx.x;
+    if (r >= rows) {
+        for (int c = t; c < kIn; c += blockDim.x) {
+            X[(size_t)r * kIn + c] = __float2bfloat16(0.f);
+            XT[(size_t)c * rows_pad + r] = __float2bfloat16(0.f);
+        }
+        return;
+    }
+    const int* genes = pop + (size_t)r * k;
+    const int d = t & 63, half = t >> 6;
+    float s = 0.f;
+    for (int j = half; j < k; j += 2) s += __bfloat162float(Eb[(size_t)genes[j] * kEmb + d]);
+    part[half][d] = s;
+    // degree statistics: thread-strided partial sums, then a fixed warp tree
+    float q1 = 0.f, q2 = 0.f, qmax = -1.f, dsum = 0.f;
+    for (int j = t; j < k; j += blockDim.x) {
+        const int v = genes[j];
+        const float q = logdeg[v];
+        q1 += q;
+        q2 += q * q;
+        qmax = fmaxf(qmax, q);
+        dsum += deg[v];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        q1 += __shfl_down_sync(0xffffffffu, q1, o);
+        q2 += __shfl_down_sync(0xffffffffu, q2, o);
+        qmax = fmaxf(qmax, __shfl_down_sync(0xffffffffu, qmax, o));
+        dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+    }
+    if ((t & 31) == 0) {
+        st[t >> 5][0] = q1;
+        st[t >> 5][1] = q2;
+        st[t >> 5][2] = qmax;
+        st[t >> 5][3] = dsum;
+    }
+    __syncthreads();
+    if (t < kEmb) {
+        const float e = (part[0][t] + part[1][t]) * invsqrtk;
+        X[(size_t)r * kIn + t] = __float2bfloat16(e);
+        XT[(size_t)t * rows_pad + r] = __float2bfloat16(e);
+    } else if (t < kIn) {
+        float f = 0.f;
+        const float Q1 = st[0][0] + st[1][0] + st[2][0] + st[3][0];
+        const float Q2 = st[0][1] + st[1][1] + st[2][1] + st[3][1];
+        const float QM = fmaxf(fmaxf(st[0][2], st[1][2]), fmaxf(st[2][2], st[3][2]));
+        const float DS = st[0][3] + st[1][3] + st[2][3] + st[3][3];
+        const float mean = k > 0 ? Q1 / k : 0.f;
+        if (t == 64) f = mean;
+        if (t == 65) f = k > 0 ? QM : 0.f;
+        if (t == 66) f = k > 0 ? sqrtf(fmaxf(Q2 / k - mean * mean, 0.f)) : 0.f;
+        if (t == 67) f = DS * inv2E;
+        X[(size_t)r * kIn + t] = __float2bfloat16(f);
+        XT[(size_t)t * rows_pad + r] = __float2bfloat16(f);
+    }
+}
+
+// y[r] = h2[r] . w3 + b3 (FP32), one warp per row.
+__global__ void head_kernel(const bf16* __restrict__ H2, int rows, const float* __restrict__ w3,
+                            const float* __restrict__ b3, float* __restrict__ y) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float s = 0.f;
+    for (int h = lane; h < kHid; h += 32) s += __bfloat162float(H2[(size_t)r * kHid + h]) * w3[h];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[r] = s + b3[0];
+}
+
+// dy = 2 (y - t) / B and the batch loss (one CTA, fixed order).
+__global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y, const float* __restrict__ t, int B,
+                                                   float* __restrict__ dy, float* __restrict__ loss) {
+    __shared__ float red[8];
+    float s = 0.f;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const float e = y[b] - t[b];
+        dy[b] = 2.f * e / B;
+        s += e * e;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.f;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        *loss = tot / B;
+    }
+}
+
+// dz2 = dy * w3 where h2 > 0 (BF16 and transposed BF16).
+__global__ void __launch_bounds__(256) dz2_kernel(const bf16* __restrict__ H2, const float* __restrict__ dy,
+                                                  const float* __restrict__ w3, int B, bf16* __restrict__ dZ2,
+                                                  bf16* __restrict__ dZ2T) {
+    const int b = blockIdx.x, h = threadIdx.x;
+    const float v = __bfloat162float(H2[(size_t)b * kHid + h]) > 0.f ? dy[b] * w3[h] : 0.f;
+    dZ2[(size_t)b * kHid + h] = __float2bfloat16(v);
+    dZ2T[(size_t)h * B + b] = __float2bfloat16(v);
+}
+
+// Column sums over the batch in a fixed order: dw3 = H2^T dy, db2 = sum dz2,
+// db3 = sum dy (db1 with H2 = nullptr and Z = dz1).
+__global__ void __launch_bounds__(256) colsum_kernel(const bf16* __restrict__ H2, const float* __restrict__ dy,
+                                                     const bf16* __restrict__ Z, int B, float* __restrict__ dw3,
+                                                     float* __restrict__ db, float* __restrict__ db3) {
+    const int h = threadIdx.x;
+    float sw = 0.f, sb = 0.f;
+    for (int b = 0; b < B; ++b) {
+        if (H2) sw += __bfloat162float(H2[(size_t)b * kHid + h]) * dy[b];
+        sb += __bfloat162float(Z[(size_t)b * kHid + h]);
+    }
+    if (dw3) dw3[h] = sw;
+    db[h] = sb;
+    if (db3 && h == 0) {
+        float s = 0.f;
+        for (int b = 0; b < B; ++b) s += dy[b];
+        db3[0] = s;
+    }
+}
+
+// Embedding gradient: every gene v of row b gets dx[b][0:64] / sqrt(k), summed
+// in 2^-40 fixed point with integer atomics (order-independent).
+__global__ void __launch_bounds__(256) emb_grad_kernel(const int* __restrict__ pop, int k,
+                                                       const float* __restrict__ dX, float invsqrtk,
+                                                       unsigned long long* __restrict__ Gi) {
+    const int b = blockIdx.x, d = threadIdx.x & 63, jj = threadIdx.x >> 6;
+    const long long q = llrint((double)dX[(size_t)b * kIn + d] * invsqrtk * kFix);
+    if (q == 0) return;
+    const int* genes = pop + (size_t)b * k;
+    for (int j = jj; j < k; j += 4) atomicAdd(&Gi[(size_t)genes[j] * kEmb + d], (unsigned long long)q);
+}
+
+__global__ void emb_grad_convert_kernel(unsigned long long* __restrict__ Gi, float* __restrict__ G, size_t count) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        G[i] = (float)((double)(long long)Gi[i] / kFix);
+        Gi[i] = 0ull;
+    }
+}
+
+__global__ void adamw_kernel(float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
+                             const float* __restrict__ G, size_t count, float lr, float b1, float b2, float wd,
+                             float eps, float bc1, float bc2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const float g = G[i];
+        const float m = b1 * M[i] + (1.f - b1) * g;
+        const float v = b2 * V[i] + (1.f - b2) * g * g;
+        M[i] = m;
+        V[i] = v;
+        const float p = P[i];
+        P[i] = p - lr * ((m / bc1) / (sqrtf(v / bc2) + eps) + wd * p);
+    }
+}
+
+// BF16 copies: W (rows x cols) and its transpose; E.
+__global__ void to_bf16_kernel(const float* __restrict__ W, int rows, int cols, bf16* __restrict__ Wb,
+                               bf16* __restrict__ WbT) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * cols; i += gridDim.x * blockDim.x) {
+        const int r = i / cols, c = i % cols;
+        const bf16 v = __float2bfloat16(W[i]);
+        if (Wb) Wb[i] = v;
+        if (WbT) WbT[(size_t)c * rows + r] = v;
+    }
+}
+
+__global__ void to_bf16_flat_kernel(const float* __restrict__ W, size_t count, bf16* __restrict__ Wb) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        Wb[i] = __float2bfloat16(W[i]);
+}
+
+// Uniform initialisation U(-a, a) from Philox (tag 8, counter (i lo, i hi, tensor, 0)).
+__global__ void init_uniform_kernel(float* __restrict__ P, size_t count, float a, RngKey key, uint32_t tensor) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t x = philox_word0((uint32_t)i, (uint32_t)(i >> 32), tensor, 8u << 24, key.lo, key.hi);
+        P[i] = a * (2.f * ((float)x * 2.3283064365386963e-10f) - 1.f);
+    }
+}
+
+// Lowest `m` of `cnt` scores (ties to the lower index): bitonic sort of
+// (order-preserving score bits << 32 | index) in shared memory; one CTA.
+__global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ score, int cnt, int m,
+                                                    int* __restrict__ sel, int P) {
+    extern __shared__ unsigned long long keys[];
+    for (int x = threadIdx.x; x < P; x += blockDim.x) {
+        unsigned long long key = ~0ull;
+        if (x < cnt) {
+            unsigned u = __float_as_uint(score[x]);
+            u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+            key = ((unsigned long long)u << 32) | (unsigned)x;
+        }
+        keys[x] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int x = threadIdx.x; x < P; x += blockDim.x) {
+                const int y = x ^ stride;
+                if (y > x) {
+                    const bool up = (x & size) == 0;
+                    if ((keys[x] > keys[y]) == up) {
+                        const unsigned long long t = keys[x];
+                        keys[x] = keys[y];
+                        keys[y] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int r = threadIdx.x; r < m; r += blockDim.x) sel[r] = (int)(keys[r] & 0xFFFFFFFFu);
+}
+
+// dst row r = src row idx[r] (idx may be null: identity), k genes.
+__global__ void gather_rows_kernel(const int* __restrict__ src, const int* __restrict__ idx, int k,
+                                   int* __restrict__ dst, int dst_stride_rows, int dst_first, int dst_cap) {
+    const int r = blockIdx.x;
+    const int from = idx ? idx[r] : r;
+    const int to = dst_cap > 0 ? (dst_first + r) % dst_cap : r;
+    (void)dst_stride_rows;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) dst[(size_t)to * k + j] = src[(size_t)from * k + j];
+}
+
+// kfit[i] = +inf for every child, then the evaluated ones.
+__global__ void scatter_fit_kernel(const long long* __restrict__ fsel, const int* __restrict__ sel, int m, int lambda,
+                                   long long* __restrict__ kfit) {
+    for (int i = threadIdx.x; i < lambda; i += blockDim.x) kfit[i] = LLONG_MAX;
+    __syncthreads();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) kfit[sel[r]] = fsel[r];
+}
+
+// Ring fitness append.
+__global__ void ring_fit_kernel(const int64_t* __restrict__ f, const int* __restrict__ idx, int cnt,
+                                int64_t* __restrict__ ring_fit, int first, int cap) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x)
+        ring_fit[(first + r) % cap] = f[idx ? idx[r] : r];
+}
+
+// Mean and standard deviation of log1p(fitness) over the ring (one CTA, FP64).
+__global__ void __launch_bounds__(256) target_stats_kernel(const int64_t* __restrict__ ring_fit, int valid,
+                                                           double* __restrict__ stats) {
+    __shared__ double s1[256], s2[256];
+    double a = 0, b = 0;
+    for (int i = threadIdx.x; i < valid; i += blockDim.x) {
+        const double l = log1p((double)ring_fit[i]);
+        a += l;
+        b += l * l;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0, Bq = 0;
+        for (int i = 0; i < 256; ++i) {
+            A += s1[i];
+            Bq += s2[i];
+        }
+        const double mu = A / valid;
+        const double var = Bq / valid - mu * mu;
+        stats[0] = mu;
+        stats[1] = var > 1e-24 ? sqrt(var) : 1.0;
+    }
+}
+
+// Minibatch: rows drawn uniformly from the valid ring entries (Philox tag 8,
+// counter (b, step, g, 8 << 24 | 1)), targets z-scored.
+__global__ void batch_kernel(const int* __restrict__ ring, const int64_t* __restrict__ ring_fit, int valid, int k,
+                             int B, RngKey key, int step, int g, const double* __restrict__ stats,
+                             int* __restrict__ rows, float* __restrict__ t) {
+    const int b = blockIdx.x;
+    const int idx = uniform_below(philox_word0((uint32_t)b, (uint32_t)step, (uint32_t)g, (8u << 24) | 1u, key.lo, key.hi),
+                                  valid);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) rows[(size_t)b * k + j] = ring[(size_t)idx * k + j];
+    if (threadIdx.x == 0) t[b] = (float)((log1p((double)ring_fit[idx]) - stats[0]) / stats[1]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct gapa_surrogate {
+    gapa_ctx* ctx = nullptr;
+    gapa_surrogate_config cfg;
+    RngKey key;
+    Layout L;
+    int n = 0, k_max = 0, rows_cap = 0;
+    float *P = nullptr, *M = nullptr, *V = nullptr, *G = nullptr;
+    unsigned long long* Gi = nullptr;
+    bf16 *W1b = nullptr, *W1tb = nullptr, *W2b = nullptr, *W2tb = nullptr, *Eb = nullptr;
+    float *logdeg = nullptr, *deg = nullptr;
+    float inv2E = 0.f;
+    // activations for up to rows_cap rows
+    bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
+         *dZ1 = nullptr, *dZ1T = nullptr;
+    float *y = nullptr, *dy = nullptr, *dX = nullptr, *loss = nullptr, *tbuf = nullptr;
+    int* batch_rows = nullptr;
+    double* stats = nullptr;
+    int tau = 0;
+};
+
+namespace {
+
+int launch_gemm(const GemmArgs& a, cudaStream_t st) {
+    dim3 grid((a.N + 31) / 32, (a.M + 63) / 64);
+    gemm_bf16_kernel<<<grid, 128, 0, st>>>(a);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+GemmArgs gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb) {
+    GemmArgs a;
+    memset(&a, 0, sizeof a);
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = A;
+    a.lda = lda;
+    a.B = B;
+    a.ldb = ldb;
+    return a;
+}
+
+int refresh_bf16(gapa_surrogate* s, cudaStream_t st) {
+    to_bf16_kernel<<<64, 256, 0, st>>>(s->P + s->L.W1, kIn, kHid, s->W1b, s->W1tb);
+    to_bf16_kernel<<<128, 256, 0, st>>>(s->P + s->L.W2, kHid, kHid, s->W2b, s->W2tb);
+    to_bf16_flat_kernel<<<s->ctx->num_sms * 4, 256, 0, st>>>(s->P + s->L.E, (size_t)s->n * kEmb, s->Eb);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+int round16(int x) { return (x + 15) & ~15; }
+
+// Features + forward; keeps the transposed copies for a training step.
+int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, cudaStream_t st) {
+    const int R = round16(rows);
+    features_kernel<<<R, 128, 0, st>>>(pop, rows, k, s->Eb, s->logdeg, s->deg, s->inv2E, 1.f / sqrtf((float)std::max(k, 1)),
+                                       s->X, s->XT, R);
+    GemmArgs a = gemm(R, kHid, kIn, s->X, kIn, s->W1tb, kIn);
+    a.Cb = s->H1;
+    a.ldcb = kHid;
+    if (keep) {
+        a.CbT = s->H1T;
+        a.ldct = R;
+    }
+    a.bias = s->P + s->L.b1;
+    a.relu = 1;
+    int rc = launch_gemm(a, st);
+    if (rc != GAPA_OK) return rc;
+    a = gemm(R, kHid, kHid, s->H1, kHid, s->W2tb, kHid);
+    a.Cb = s->H2;
+    a.ldcb = kHid;
+    a.bias = s->P + s->L.b2;
+    a.relu = 1;
+    rc = launch_gemm(a, st);
+    if (rc != GAPA_OK) return rc;
+    head_kernel<<<(rows + 7) / 8, 256, 0, st>>>(s->H2, rows, s->P + s->L.w3, s->P + s->L.b3, s->y);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+// One AdamW step on a batch (rows a multiple of 16) with targets t.
+int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float* t, cudaStream_t st) {
+    int rc = forward(s, pop, B, k, true, st);
+    if (rc != GAPA_OK) return rc;
+    float* G = s->G;
+    const Layout& L = s->L;
+    loss_kernel<<<1, 256, 0, st>>>(s->y, t, B, s->dy, s->loss);
+    dz2_kernel<<<B, kHid, 0, st>>>(s->H2, s->dy, s->P + L.w3, B, s->dZ2, s->dZ2T);
+    colsum_kernel<<<1, kHid, 0, st>>>(s->H2, s->dy, s->dZ2, B, G + L.w3, G + L.b2, G + L.b3);
+    // dW2 = h1^T dz2  ([in][out])
+    GemmArgs a = gemm(kHid, kHid, B, s->H1T, B, s->dZ2T, B);
+    a.Cf = G + L.W2;
+    a.ldc = kHid;
+    if ((rc = launch_gemm(a, st)) != GAPA_OK) return rc;
+    // dz1 = (dz2 W2^T) where h1 > 0
+    a = gemm(B, kHid, kHid, s->dZ2, kHid, s->W2b, kHid);
+    a.Cb = s->dZ1;
+    a.ldcb = kHid;
+    a.CbT = s->dZ1T;
+    a.ldct = B;
+    a.mask = s->H1;
+    a.ldm = kHid;
+    if ((rc = launch_gemm(a, st)) != GAPA_OK) return rc;
+    colsum_kernel<<<1, kHid, 0, st>>>(nullptr, nullptr, s->dZ1, B, nullptr, G + L.b1, nullptr);
+    // dW1 = x^T dz1  ([80][256])
+    a = gemm(kIn, kHid, B, s->XT, B, s->dZ1T, B);
+    a.Cf = G + L.W1;
+    a.ldc = kHid;
+    if ((rc = launch_gemm(a, st)) != GAPA_OK) return rc;
+    // dx = dz1 W1^T ([B][80])
+    a = gemm(B, kIn, kHid, s->dZ1, kHid, s->W1b, kHid);
+    a.Cf = s->dX;
+    a.ldc = kIn;
+    if ((rc = launch_gemm(a, st)) != GAPA_OK) return rc;
+    emb_grad_kernel<<<B, 256, 0, st>>>(pop, k, s->dX, 1.f / sqrtf((float)std::max(k, 1)), s->Gi);
+    emb_grad_convert_kernel<<<s->ctx->num_sms * 4, 256, 0, st>>>(s->Gi, G + L.E, (size_t)s->n * kEmb);
+    s->tau += 1;
+    const float bc1 = 1.f - powf(s->cfg.beta1, (float)s->tau), bc2 = 1.f - powf(s->cfg.beta2, (float)s->tau);
+    adamw_kernel<<<s->ctx->num_sms * 4, 256, 0, st>>>(s->P, s->M, s->V, G, L.total, s->cfg.lr, s->cfg.beta1,
+                                                      s->cfg.beta2, s->cfg.weight_decay, s->cfg.eps, bc1, bc2);
+    GAPA_CUDA(cudaGetLastError());
+    return refresh_bf16(s, st);
+}
+
+int ensure_rows(gapa_surrogate* s, int rows) {
+    const int R = round16(rows);
+    if (R <= s->rows_cap) return GAPA_OK;
+    bf16** bfs[] = {&s->X, &s->XT, &s->H1, &s->H1T, &s->H2, &s->dZ2, &s->dZ2T, &s->dZ1, &s->dZ1T};
+    for (bf16** p : bfs) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    float** fps[] = {&s->y, &s->dy, &s->dX, &s->tbuf};
+    for (float** p : fps) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    const size_t e80 = (size_t)R * kIn, e256 = (size_t)R * kHid;
+    if (cudaMalloc(&s->X, e80 * 2) || cudaMalloc(&s->XT, e80 * 2) || cudaMalloc(&s->H1, e256 * 2) ||
+        cudaMalloc(&s->H1T, e256 * 2) || cudaMalloc(&s->H2, e256 * 2) || cudaMalloc(&s->dZ2, e256 * 2) ||
+        cudaMalloc(&s->dZ2T, e256 * 2) || cudaMalloc(&s->dZ1, e256 * 2) || cudaMalloc(&s->dZ1T, e256 * 2) ||
+        cudaMalloc(&s->y, (size_t)R * 4) || cudaMalloc(&s->dy, (size_t)R * 4) || cudaMalloc(&s->dX, e80 * 4) ||
+        cudaMalloc(&s->tbuf, (size_t)R * 4)) {
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "surrogate activations for %d rows", R);
+    }
+    s->rows_cap = R;
+    return GAPA_OK;
+}
+
+void free_surrogate(gapa_surrogate* s) {
+    void* ps[] = {s->P, s->M, s->V, s->G, s->Gi, s->W1b, s->W1tb, s->W2b, s->W2tb, s->Eb, s->logdeg, s->deg,
+                  s->X, s->XT, s->H1, s->H1T, s->H2, s->dZ2, s->dZ2T, s->dZ1, s->dZ1T, s->y, s->dy, s->dX,
+                  s->loss, s->tbuf, s->batch_rows, s->stats};
+    for (void* p : ps) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrogate_config* scfg, uint64_t seed) {
+    if (!out || !ctx || !scfg) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (ctx->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "no graph uploaded");
+    if (scfg->batch < 16 || scfg->batch % 16 || scfg->ring < scfg->batch || scfg->train_steps < 0 ||
+        scfg->screened < 1 || scfg->warmup < 0 || !(scfg->lr > 0.f))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "invalid surrogate configuration");
+    cudaSetDevice(ctx->device);
+    gapa_surrogate* s = new gapa_surrogate();
+    s->ctx = ctx;
+    s->cfg = *scfg;
+    s->key = RngKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
+    s->n = ctx->g.n;
+    s->L = make_layout(s->n);
+    auto bail = [&](int rc) {
+        free_surrogate(s);
+        delete s;
+        return rc;
+    };
+    const size_t np = s->L.total;
+    if (cudaMalloc(&s->P, np * 4) || cudaMalloc(&s->M, np * 4) || cudaMalloc(&s->V, np * 4) ||
+        cudaMalloc(&s->G, np * 4) || cudaMalloc(&s->Gi, (size_t)s->n * kEmb * 8) ||
+        cudaMalloc(&s->W1b, (size_t)kIn * kHid * 2) || cudaMalloc(&s->W1tb, (size_t)kIn * kHid * 2) ||
+        cudaMalloc(&s->W2b, (size_t)kHid * kHid * 2) || cudaMalloc(&s->W2tb, (size_t)kHid * kHid * 2) ||
+        cudaMalloc(&s->Eb, (size_t)s->n * kEmb * 2) || cudaMalloc(&s->logdeg, (size_t)s->n * 4) ||
+        cudaMalloc(&s->deg, (size_t)s->n * 4) || cudaMalloc(&s->loss, 4) || cudaMalloc(&s->stats, 16)) {
+        cudaGetLastError();
+        return bail(gapa_fail(GAPA_ERR_OOM, "surrogate parameters"));
+    }
+    // degrees (original ids) from the uploaded CSR
+    std::vector<int32_t> rp((size_t)s->n + 1);
+    if (cudaMemcpy(rp.data(), ctx->g.row_ptr, rp.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_CUDA, "reading degrees"));
+    std::vector<float> lg(s->n), dg(s->n);
+    for (int v = 0; v < s->n; ++v) {
+        dg[v] = (float)(rp[v + 1] - rp[v]);
+        lg[v] = (float)std::log1p((double)dg[v]);
+    }
+    s->inv2E = ctx->g.num_edges > 0 ? (float)(1.0 / (2.0 * ctx->g.num_edges)) : 0.f;
+    cudaMemcpy(s->logdeg, lg.data(), lg.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->deg, dg.data(), dg.size() * 4, cudaMemcpyHostToDevice);
+    cudaStream_t st = ctx->stream;
+    cudaMemsetAsync(s->P, 0, np * 4, st);
+    cudaMemsetAsync(s->M, 0, np * 4, st);
+    cudaMemsetAsync(s->V, 0, np * 4, st);
+    cudaMemsetAsync(s->Gi, 0, (size_t)s->n * kEmb * 8, st);
+    const int grid = ctx->num_sms * 4;
+    init_uniform_kernel<<<grid, 256, 0, st>>>(s->P + s->L.W1, (size_t)kIn * kHid, sqrtf(6.f / kIn), s->key, 1);
+    init_uniform_kernel<<<grid, 256, 0, st>>>(s->P + s->L.W2, (size_t)kHid * kHid, sqrtf(6.f / kHid), s->key, 2);
+    init_uniform_kernel<<<grid, 256, 0, st>>>(s->P + s->L.w3, kHid, sqrtf(3.f / kHid), s->key, 3);
+    init_uniform_kernel<<<grid, 256, 0, st>>>(s->P + s->L.E, (size_t)s->n * kEmb, scfg->init_scale_emb, s->key, 4);
+    int rc = refresh_bf16(s, st);
+    if (rc == GAPA_OK && cudaGetLastError() != cudaSuccess) rc = gapa_fail(GAPA_ERR_CUDA, "surrogate initialisation");
+    if (rc == GAPA_OK) rc = ensure_rows(s, std::max(scfg->batch, 16));
+    if (rc != GAPA_OK) return bail(rc);
+    *out = s;
+    return GAPA_OK;
+}
+
+void gapa_surrogate_destroy(gapa_surrogate* s) {
+    if (!s) return;
+    cudaSetDevice(s->ctx->device);
+    cudaStreamSynchronize(s->ctx->stream);
+    free_surrogate(s);
+    delete s;
+}
+
+int gapa_surrogate_predict(gapa_surrogate* s, const int32_t* pop_dev, int32_t rows, int32_t k, float* scores_dev) {
+    if (!s || rows < 0 || k < 0 || (rows > 0 && (!pop_dev || !scores_dev))) return gapa_fail(GAPA_ERR_INVALID_ARG, "bad predict arguments");
+    if (rows == 0) return GAPA_OK;
+    cudaSetDevice(s->ctx->device);
+    int rc = ensure_rows(s, rows);
+    if (rc != GAPA_OK) return rc;
+    cudaStream_t st = s->ctx->stream;
+    rc = forward(s, pop_dev, rows, k, false, st);
+    if (rc != GAPA_OK) return rc;
+    GAPA_CUDA(cudaMemcpyAsync(scores_dev, s->y, (size_t)rows * 4, cudaMemcpyDeviceToDevice, st));
+    return GAPA_OK;
+}
+
+int gapa_surrogate_train_step(gapa_surrogate* s, const int32_t* pop_dev, int32_t rows, int32_t k,
+                              const float* target_dev, float* loss_host) {
+    if (!s || rows < 16 || rows % 16 || k < 1 || !pop_dev || !target_dev)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "training batches need a multiple of 16 rows and k >= 1");
+    cudaSetDevice(s->ctx->device);
+    int rc = ensure_rows(s, rows);
+    if (rc != GAPA_OK) return rc;
+    cudaStream_t st = s->ctx->stream;
+    rc = train_step(s, pop_dev, rows, k, target_dev, st);
+    if (rc != GAPA_OK) return rc;
+    if (loss_host) {
+        GAPA_CUDA(cudaMemcpyAsync(loss_host, s->loss, 4, cudaMemcpyDeviceToHost, st));
+        GAPA_CUDA(cudaStreamSynchronize(st));
+    }
+    return GAPA_OK;
+}
+
+int gapa_surrogate_tensor(gapa_surrogate* s, int32_t which, int32_t grad, float* host, int64_t count, int32_t set) {
+    if (!s || !host || which < 0 || which > 6) return gapa_fail(GAPA_ERR_INVALID_ARG, "bad tensor arguments");
+    const Layout& L = s->L;
+    const size_t offs[] = {L.W1, L.b1, L.W2, L.b2, L.w3, L.b3, L.E};
+    const size_t sizes[] = {(size_t)kIn * kHid, kHid, (size_t)kHid * kHid, kHid, kHid, 1, (size_t)s->n * kEmb};
+    if ((size_t)count != sizes[which]) return gapa_fail(GAPA_ERR_INVALID_ARG, "tensor %d holds %zu values", which, sizes[which]);
+    cudaSetDevice(s->ctx->device);
+    float* base = (grad ? s->G : s->P) + offs[which];
+    cudaStream_t st = s->ctx->stream;
+    if (set) {
+        GAPA_CUDA(cudaMemcpyAsync(base, host, sizes[which] * 4, cudaMemcpyHostToDevice, st));
+        if (!grad) {
+            int rc = refresh_bf16(s, st);
+            if (rc != GAPA_OK) return rc;
+        }
+    } else {
+        GAPA_CUDA(cudaMemcpyAsync(host, base, sizes[which] * 4, cudaMemcpyDeviceToHost, st));
+    }
+    GAPA_CUDA(cudaStreamSynchronize(st));
+    return GAPA_OK;
+}
+
+int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, int64_t* best_fit_host,
+                       int32_t* best_set_host, int64_t* traj_host, double* gen_ms_host, int64_t* exact_evals_host,
+                       float* diag_pred_host, int64_t* diag_exact_host, int32_t diag_cap) {
+    if (!c || !cfg || !best_fit_host) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL argument");
+    if (!(cfg->flags & GAPA_FLAG_MU_PLUS_LAMBDA) || cfg->lambda < 1)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "surrogate runs use (mu+lambda) with lambda >= 1");
+    if (s && s->ctx != c) return gapa_fail(GAPA_ERR_INVALID_ARG, "surrogate belongs to another context");
+    if (s && s->cfg.ring < std::max(cfg->pop, cfg->lambda))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "the replay ring must hold at least max(mu, lambda) rows");
+    cudaSetDevice(c->device);
+    const int mu = cfg->pop, lam = cfg->lambda, k = cfg->k, G = cfg->gens;
+    const int screened = s ? std::min(s->cfg.screened, lam) : lam;
+    // the generation machinery of gapa_run: init, fitness, and the (mu+lambda) step pieces
+    gapa_config c2 = *cfg;
+    int rc = gapa_run_prepare(c, &c2);
+    if (rc != GAPA_OK) return rc;
+    cudaStream_t st = c->stream;
+    int32_t* P[2] = {c->stage_pop[0], c->stage_pop[1]};
+    int64_t* F[2] = {c->stage_fit[0], c->stage_fit[1]};
+    // surrogate buffers
+    int32_t *ring = nullptr, *sel = nullptr, *sel_rows = nullptr, *batch_rows = nullptr;
+    int64_t *ring_fit = nullptr, *fsel = nullptr;
+    float* scores = nullptr;
+    const int ring_cap = s ? s->cfg.ring : 0;
+    auto cleanup = [&]() {
+        cudaFree(ring);
+        cudaFree(sel);
+        cudaFree(sel_rows);
+        cudaFree(batch_rows);
+        cudaFree(ring_fit);
+        cudaFree(fsel);
+        cudaFree(scores);
+    };
+    if (cudaMalloc(&sel, (size_t)lam * 4) || cudaMalloc(&sel_rows, (size_t)lam * k * 4 + 4) ||
+        cudaMalloc(&fsel, (size_t)lam * 8) || cudaMalloc(&scores, (size_t)lam * 4) ||
+        (s && (cudaMalloc(&ring, (size_t)ring_cap * k * 4 + 4) || cudaMalloc(&ring_fit, (size_t)ring_cap * 8) ||
+               cudaMalloc(&batch_rows, (size_t)s->cfg.batch * k * 4 + 4)))) {
+        cudaGetLastError();
+        cleanup();
+        return gapa_fail(GAPA_ERR_OOM, "surrogate run buffers");
+    }
+    if (s && (rc = ensure_rows(s, std::max(lam, s->cfg.batch))) != GAPA_OK) {
+        cleanup();
+        return rc;
+    }
+    int topk_P = 1;
+    while (topk_P < lam) topk_P <<= 1;
+    if ((size_t)topk_P * 8 > 48 * 1024) {
+        cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(topk_P * 8));
+    }
+    std::vector<cudaEvent_t> ev((size_t)G + 2);
+    for (auto& e : ev) cudaEventCreate(&e);
+    std::vector<int64_t> exact((size_t)G + 1, 0);
+    int ring_pos = 0, ring_valid = 0, diag_rows = 0;
+    auto fail = [&](int code) {
+        for (auto e : ev) cudaEventDestroy(e);
+        cleanup();
+        return code;
+    };
+    GAPA_CUDA(cudaEventRecord(ev[0], st));
+    GAPA_CUDA(cudaMemsetAsync(c->run_gen, 0, sizeof(int), st));
+    const GaParams p0 = gapa_make_params(c, &c2, 0, nullptr);
+    rc = gapa_launch_init(c, p0, P[0], st);
+    if (rc == GAPA_OK) rc = gapa_launch_fitness(c, P[0], mu, k, F[0], st);
+    if (rc == GAPA_OK) rc = gapa_launch_record(c, F[0], mu, c->run_gen, c->run_traj, c->run_best, st);
+    if (rc != GAPA_OK) return fail(rc);
+    exact[0] = mu;
+    if (s) {  // the initial population enters the ring
+        gather_rows_kernel<<<mu, 256, 0, st>>>(P[0], nullptr, k, ring, 0, ring_pos, ring_cap);
+        ring_fit_kernel<<<1, 256, 0, st>>>(F[0], nullptr, mu, ring_fit, ring_pos, ring_cap);
+        ring_pos = (ring_pos + mu) % ring_cap;
+        ring_valid = std::min(ring_cap, ring_valid + mu);
+    }
+    GAPA_CUDA(cudaEventRecord(ev[1], st));
+    int cur = 0;
+    for (int g = 1; g <= G && rc == GAPA_OK; ++g) {
+        GaParams p = gapa_make_params(c, &c2, g, nullptr);
+        if (p.flags & GAPA_FLAG_ROULETTE) {
+            rc = gapa_launch_roulette_prefix(F[cur], mu, c->cum, st);
+            p.cum = reinterpret_cast<const long long*>(c->cum);
+        }
+        if (rc == GAPA_OK) rc = gapa_launch_children(c, p, lam, P[cur], F[cur], c->kids, st);
+        if (rc != GAPA_OK) break;
+        const bool screen = s && g > s->cfg.warmup && screened < lam;
+        const bool diag = s && s->cfg.diag_every > 0 && g % s->cfg.diag_every == 0 && diag_pred_host &&
+                          diag_exact_host && diag_rows + lam <= diag_cap;
+        int evaluated = lam;
+        if (screen || diag) rc = forward(s, c->kids, lam, k, false, st);
+        if (rc == GAPA_OK && screen && !diag) {
+            topk_kernel<<<1, 1024, (size_t)topk_P * 8, st>>>(s->y, lam, screened, sel, topk_P);
+            gather_rows_kernel<<<screened, 256, 0, st>>>(c->kids, sel, k, sel_rows, 0, 0, 0);
+            rc = gapa_launch_fitness(c, sel_rows, screened, k, fsel, st);
+            scatter_fit_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const long long*>(fsel), sel, screened, lam,
+                                                   reinterpret_cast<long long*>(c->kfit));
+            evaluated = screened;
+        } else if (rc == GAPA_OK) {
+            rc = gapa_launch_fitness(c, c->kids, lam, k, c->kfit, st);
+            if (rc == GAPA_OK && diag) {
+                // diagnostic generation: every child is evaluated exactly (and used by the
+                // truncation), and the (score, fitness) pairs are recorded
+                GAPA_CUDA(cudaMemcpyAsync(diag_pred_host + diag_rows, s->y, (size_t)lam * 4, cudaMemcpyDeviceToHost, st));
+                GAPA_CUDA(cudaMemcpyAsync(diag_exact_host + diag_rows, c->kfit, (size_t)lam * 8, cudaMemcpyDeviceToHost, st));
+                diag_rows += lam;
+            }
+        }
+        if (rc != GAPA_OK) break;
+        exact[g] = evaluated;
+        if (s) {  // evaluated children enter the ring
+            if (evaluated == lam) {
+                gather_rows_kernel<<<lam, 256, 0, st>>>(c->kids, nullptr, k, ring, 0, ring_pos, ring_cap);
+                ring_fit_kernel<<<(lam + 255) / 256, 256, 0, st>>>(c->kfit, nullptr, lam, ring_fit, ring_pos, ring_cap);
+            } else {
+                gather_rows_kernel<<<evaluated, 256, 0, st>>>(sel_rows, nullptr, k, ring, 0, ring_pos, ring_cap);
+                ring_fit_kernel<<<(evaluated + 255) / 256, 256, 0, st>>>(fsel, nullptr, evaluated, ring_fit, ring_pos,
+                                                                        ring_cap);
+            }
+            ring_pos = (ring_pos + evaluated) % ring_cap;
+            ring_valid = std::min(ring_cap, ring_valid + evaluated);
+        }
+        rc = gapa_launch_mpl_replace(c, mu, lam, k, P[cur], F[cur], c->kids, c->kfit, c->src, P[cur ^ 1], F[cur ^ 1], st);
+        if (rc == GAPA_OK) rc = gapa_launch_record(c, F[cur ^ 1], mu, c->run_gen, c->run_traj, c->run_best, st);
+        cur ^= 1;
+        // online training on the ring
+        if (rc == GAPA_OK && s && ring_valid >= s->cfg.batch && s->cfg.train_steps > 0) {
+            target_stats_kernel<<<1, 256, 0, st>>>(ring_fit, ring_valid, s->stats);
+            for (int step = 0; step < s->cfg.train_steps && rc == GAPA_OK; ++step) {
+                batch_kernel<<<s->cfg.batch, 256, 0, st>>>(ring, ring_fit, ring_valid, k, s->cfg.batch, s->key, step, g,
+                                                           s->stats, batch_rows, s->tbuf);
+                rc = train_step(s, batch_rows, s->cfg.batch, k, s->tbuf, st);
+            }
+        }
+        if (cudaEventRecord(ev[(size_t)g + 1], st) != cudaSuccess) rc = gapa_fail(GAPA_ERR_CUDA, "event record");
+    }
+    if (rc != GAPA_OK) return fail(rc);
+    GAPA_CUDA(cudaStreamSynchronize(st));
+    int best = 0;
+    GAPA_CUDA(cudaMemcpy(&best, c->run_best, sizeof(int), cudaMemcpyDeviceToHost));
+    GAPA_CUDA(cudaMemcpy(best_fit_host, F[cur] + best, 8, cudaMemcpyDeviceToHost));
+    if (best_set_host && k) {
+        GAPA_CUDA(cudaMemcpy(best_set_host, P[cur] + (size_t)best * k, (size_t)k * 4, cudaMemcpyDeviceToHost));
+        std::sort(best_set_host, best_set_host + k);
+    }
+    if (traj_host) GAPA_CUDA(cudaMemcpy(traj_host, c->run_traj, 8 * ((size_t)G + 1), cudaMemcpyDeviceToHost));
+    if (gen_ms_host)
+        for (int g = 0; g <= G; ++g) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[(size_t)g + 1]);
+            gen_ms_host[g] = ms;
+        }
+    if (exact_evals_host)
+        for (int g = 0; g <= G; ++g) exact_evals_host[g] = exact[g];
+    int h = 0;
+    cudaMemcpy(&h, c->status, 4, cudaMemcpyDeviceToHost);
+    for (auto e : ev) cudaEventDestroy(e);
+    cleanup();
+    if (h) {
+        cudaMemset(c->status, 0, 4);
+        return gapa_fail(GAPA_ERR_DEVICE, "device status 0x%x", h);
+    }
+    return GAPA_OK;
+}
+
+}  // extern "C"

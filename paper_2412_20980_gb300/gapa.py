@@ -37,6 +37,8 @@ EXPORTS = [
     "gapa_set_fitness_kernel", "gapa_fitness_noalloc",
     "gapa_batch_create", "gapa_batch_destroy", "gapa_batch_set_teams", "gapa_batch_get_teams",
     "gapa_batch_autotune", "gapa_batch_run",
+    "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
+    "gapa_surrogate_tensor", "gapa_run_surrogate",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE = 0, 1, 2, 3
 
@@ -60,6 +62,31 @@ class Profile(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SurrogateConfig(ctypes.Structure):
+    """Mirror of gapa_surrogate_config."""
+
+    _fields_ = [
+        ("screened", ctypes.c_int32),
+        ("warmup", ctypes.c_int32),
+        ("train_steps", ctypes.c_int32),
+        ("batch", ctypes.c_int32),
+        ("ring", ctypes.c_int32),
+        ("lr", ctypes.c_float),
+        ("beta1", ctypes.c_float),
+        ("beta2", ctypes.c_float),
+        ("weight_decay", ctypes.c_float),
+        ("eps", ctypes.c_float),
+        ("init_scale_emb", ctypes.c_float),
+        ("diag_every", ctypes.c_int32),
+    ]
+
+
+def make_surrogate_config(screened=512, warmup=3, train_steps=4, batch=512, ring=16384, lr=1e-3, beta1=0.9,
+                          beta2=0.999, weight_decay=0.01, eps=1e-8, init_scale_emb=0.1, diag_every=0):
+    return SurrogateConfig(screened, warmup, train_steps, batch, ring, lr, beta1, beta2, weight_decay, eps,
+                           init_scale_emb, diag_every)
 
 
 class Config(ctypes.Structure):
@@ -126,6 +153,12 @@ def load(path: str | None = None):
             "gapa_batch_get_teams": ([V, V], U),
             "gapa_batch_autotune": ([V, ctypes.c_char_p], U),
             "gapa_batch_run": ([V, I32, V, V, V], U),
+            "gapa_surrogate_create": ([ctypes.POINTER(V), V, ctypes.POINTER(SurrogateConfig), ctypes.c_uint64], U),
+            "gapa_surrogate_destroy": ([V], None),
+            "gapa_surrogate_predict": ([V, V, I32, I32, V], U),
+            "gapa_surrogate_train_step": ([V, V, I32, I32, V, V], U),
+            "gapa_surrogate_tensor": ([V, I32, I32, V, I64, I32], U),
+            "gapa_run_surrogate": ([V, cfgp, V, V, V, V, V, V, V, V, I32], U),
             "gapa_profile_end": ([V, ctypes.POINTER(Profile)], U),
             "gapa_last_error": ([], ctypes.c_char_p),
             "gapa_version": ([], ctypes.c_char_p),
@@ -386,3 +419,84 @@ class Batch:
             sets.append(best_sets[off:off + k].copy())
             off += k
         return {"best_fit": best_fit, "best_sets": sets, "traj": traj}
+
+
+SURROGATE_TENSORS = {"W1": (0, (80, 256)), "b1": (1, (256,)), "W2": (2, (256, 256)), "b2": (3, (256,)),
+                     "w3": (4, (256,)), "b3": (5, (1,)), "E": (6, None)}
+
+
+class Surrogate:
+    """The learned fitness surrogate of a context's graph (wraps gapa_surrogate)."""
+
+    def __init__(self, ctx: "Context", scfg: SurrogateConfig, seed: int = 0):
+        self.lib = load()
+        self.ctx = ctx
+        self.scfg = scfg
+        h = ctypes.c_void_p()
+        _check(self.lib.gapa_surrogate_create(ctypes.byref(h), ctx.handle, ctypes.byref(scfg), seed & (2**64 - 1)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gapa_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def predict(self, pop, out=None):
+        torch = _torch()
+        s, k = pop.shape
+        if out is None:
+            out = torch.empty(s, dtype=torch.float32, device=pop.device)
+        _check(self.lib.gapa_surrogate_predict(self.handle, _dev_ptr(pop, torch.int32, "pop", self.ctx.device), s, k,
+                                               _dev_ptr(out, torch.float32, "scores", self.ctx.device)))
+        return out
+
+    def train_step(self, pop, target) -> float:
+        torch = _torch()
+        s, k = pop.shape
+        loss = ctypes.c_float(0.0)
+        _check(self.lib.gapa_surrogate_train_step(self.handle, _dev_ptr(pop, torch.int32, "pop", self.ctx.device), s,
+                                                  k, _dev_ptr(target, torch.float32, "target", self.ctx.device),
+                                                  ctypes.byref(loss)))
+        return float(loss.value)
+
+    def _shape(self, name):
+        which, shape = SURROGATE_TENSORS[name]
+        return which, (shape if shape is not None else (self.ctx.n, 64))
+
+    def tensor(self, name: str, grad: bool = False) -> np.ndarray:
+        which, shape = self._shape(name)
+        out = np.zeros(shape, dtype=np.float32)
+        _check(self.lib.gapa_surrogate_tensor(self.handle, which, int(grad), _host_ptr(out), out.size, 0))
+        return out
+
+    def set_tensor(self, name: str, value: np.ndarray):
+        which, shape = self._shape(name)
+        arr = np.ascontiguousarray(value, dtype=np.float32).reshape(shape)
+        _check(self.lib.gapa_surrogate_tensor(self.handle, which, 0, _host_ptr(arr), arr.size, 1))
+
+    def params(self) -> dict:
+        return {name: self.tensor(name).astype(np.float64) for name in SURROGATE_TENSORS}
+
+
+def run_surrogate(ctx: "Context", cfg: Config, sg: "Surrogate | None" = None, diag_cap: int = 0) -> dict:
+    """gapa_run_surrogate: the surrogate-screened (mu+lambda) run, or the plain one with sg=None."""
+    G = cfg.gens
+    best_fit = np.zeros(1, dtype=np.int64)
+    best = np.zeros(max(1, cfg.k), dtype=np.int32)
+    traj = np.zeros(G + 1, dtype=np.int64)
+    gen_ms = np.zeros(G + 1, dtype=np.float64)
+    evals = np.zeros(G + 1, dtype=np.int64)
+    dp = np.zeros(max(1, diag_cap), dtype=np.float32)
+    de = np.zeros(max(1, diag_cap), dtype=np.int64)
+    _check(load().gapa_run_surrogate(ctx.handle, ctypes.byref(cfg), sg.handle if sg else None, _host_ptr(best_fit),
+                                     _host_ptr(best), _host_ptr(traj), _host_ptr(gen_ms), _host_ptr(evals),
+                                     _host_ptr(dp) if diag_cap else None, _host_ptr(de) if diag_cap else None,
+                                     diag_cap))
+    return {"best_fit": int(best_fit[0]), "best_set": best[: cfg.k].copy(), "traj": traj, "gen_ms": gen_ms,
+            "exact_evals": evals, "diag_pred": dp[:diag_cap], "diag_exact": de[:diag_cap]}
