@@ -13,7 +13,14 @@ Default workload "throughput" (one step = one GA generation on each of two graph
 Other workloads (for the design notes, not the headline line):
   "large": one GA generation on R-MAT scale 20 (2^24 edges), k = 10000, s = 256;
   "small": one whole run (init + 100 generations, CUDA-graph replay) on
-           BA n=1000, m=3, k = 50, s = 100; metric GA generations per second.
+           BA n=1000, m=3, k = 50, s = 100; metric GA generations per second;
+  "batched": 64 independent instances advanced by one batched run;
+  "surrogate": (mu+lambda) GA on BA n=100000, m=3, k = 2000, mu = 512,
+           lambda = 2048, 300 generations, plain (every child exact) against
+           surrogate-screened (top 512 children exact); metric: the plain
+           run's time to its final best over the screened run's time to reach
+           that same value (the screened run may take up to 600 generations);
+           the 1.01 x tolerance is reported beside it.
 
 ``--impl reference`` times the CPU oracle (plain C, OpenMP over members) on a
 bounded sample of the same workload.  Under torchrun every rank runs its own
@@ -54,6 +61,13 @@ WORKLOADS = {
                          "k = round(0.05 n), populations from {32,64,128,256,512}, 200 generations each, "
                          "one batched run per step (CUDA-graph replay, persistent fitness kernel, autotuned teams)",
                     graphs=["64 BA instances (synth.batched_instances, seed 0)"]),
+    "surrogate": dict(k=2000, pop=512, lam=2048, screened=512, gens=300,
+                      metric="surrogate vs plain GA time-to-target speedup", unit="x",
+                      desc="(mu+lambda) GA on BA(n=100000,m=3), k=2000, mu=512, lambda=2048 children per generation, "
+                           "tournament 2, pc=0.8, pm=0.02, 300 generations, seed = rank: plain (all 2048 children "
+                           "exact) vs surrogate-screened (the 512 lowest-scored children exact after 3 warm-up "
+                           "generations; 4 AdamW steps of 512 rows per generation on a 16384-row replay ring)",
+                      graphs=["ba_n100000_m3_seed1 (E=299991)"]),
     "small": dict(k=50, pop=100, gens=100, metric="GA gens/s", unit="gens/s",
                   desc="whole GA run: init + 100 generations on BA(n=1000,m=3), k=50, s=100, tournament 2, "
                        "pc=0.8, pm=0.02, elitism 1, Philox seed 0",
@@ -80,6 +94,8 @@ def graphs(workload: str):
         return [synth.rmat_graph(20, 1 << 24, seed=1)]
     if workload == "small":
         return [synth.ba_graph(1000, 3, 1)]
+    if workload == "surrogate":
+        return [synth.ba_graph(100000, 3, 1)]
     return [synth.ba_graph(20000, 4, 1), synth.hk_graph(20000, 4, 0.3, 1)]
 
 
@@ -298,6 +314,8 @@ def run_gapa(args):
     gs = graphs(wl)
     if wl == "batched":
         return run_batched(args, gs, dist, ws, rank, local, dev)
+    if wl == "surrogate":
+        return run_surrogate_bench(args, gs, dist, ws, rank, local, dev)
     k, pop = w["k"], w["pop"]
     cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=PC, pm=PM, seed=rank)
     ctxs, state = [], []
@@ -503,6 +521,204 @@ def run_batched(args, gs, dist, ws, rank, local, dev):
             "clocks": clocks, "best_fit_first8": out["best_fit"][:8].tolist()}
     print(json.dumps(line), flush=True)
     bt.close()
+    return 0
+
+
+def _spearman(a, b) -> float:
+    """Spearman rank correlation (average ranks for ties)."""
+    def ranks(x):
+        x = np.asarray(x, dtype=np.float64)
+        order = np.argsort(x, kind="stable")
+        xs = x[order]
+        r = np.empty(x.size)
+        i = 0
+        while i < x.size:
+            j = i
+            while j + 1 < x.size and xs[j + 1] == xs[i]:
+                j += 1
+            r[order[i:j + 1]] = (i + j) / 2.0
+            i = j + 1
+        return r
+    ra, rb = ranks(a), ranks(b)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = np.sqrt((ra * ra).sum() * (rb * rb).sum())
+    return float((ra * rb).sum() / den) if den > 0 else 0.0
+
+
+def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
+    """Time-to-target of the surrogate-screened GA against the plain GA (same seed, same graph)."""
+    import torch
+
+    from paper_2412_20980_gb300 import (FLAG_MU_PLUS_LAMBDA, Context, Surrogate, make_config,
+                                        make_surrogate_config, run_surrogate)
+
+    w = WORKLOADS["surrogate"]
+    g = gs[0]
+    G, lam = w["gens"], w["lam"]
+    ctx = Context(local)
+    ctx.graph_upload(g.row_ptr, g.col)
+
+    def config(gens):
+        return make_config(k=w["k"], pop=w["pop"], gens=gens, tourn=TOURN, pc=PC, pm=PM, seed=rank,
+                           flags=FLAG_MU_PLUS_LAMBDA, lam=lam)
+
+    def scfg(diag_every=0):
+        return make_surrogate_config(screened=w["screened"], warmup=3, train_steps=4, batch=512, ring=16384,
+                                     diag_every=diag_every)
+
+    cfg = config(G)
+    cfg_long = config(2 * G)  # the screened run may need more (cheaper) generations
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for t in range(args.warmup):  # short runs of both kinds: module load, allocations, autotuned limits
+        run_surrogate(ctx, config(5), None)
+        sg = Surrogate(ctx, scfg(), seed=1000 + t)
+        run_surrogate(ctx, config(5), sg)
+        sg.close()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    runs = []
+    for t in range(args.steps):
+        flush.fill_(t & 0xFF)
+        torch.cuda.synchronize()
+        ctx.profile_begin()  # CUDA events around every launch: the phase split and the launch count
+        t0 = time.perf_counter()
+        plain = run_surrogate(ctx, cfg, None)
+        plain_wall = time.perf_counter() - t0
+        plain["prof"] = ctx.profile_end()
+        flush.fill_((t + 1) & 0xFF)
+        sg = Surrogate(ctx, scfg(), seed=t)
+        torch.cuda.synchronize()
+        ctx.profile_begin()
+        t0 = time.perf_counter()
+        sur = run_surrogate(ctx, cfg_long, sg)
+        sur_wall = time.perf_counter() - t0
+        sur["prof"] = ctx.profile_end()
+        sg.close()
+        runs.append((plain, plain_wall, sur, sur_wall))
+    clocks = sampler.stop()
+    # per step: the plain run's device time to its final best, the screened run's time to reach it
+    speedups, rows = [], []
+    for plain, plain_wall, sur, sur_wall in runs:
+        final = int(plain["traj"][-1])
+        t_plain = float(plain["gen_ms"][np.nonzero(plain["traj"] == final)[0][0]])
+        hit = np.nonzero(sur["traj"] <= final)[0]
+        hit1 = np.nonzero(sur["traj"] <= final * 1.01)[0]
+        t_sur = float(sur["gen_ms"][hit[0]]) if hit.size else None
+        t_sur1 = float(sur["gen_ms"][hit1[0]]) if hit1.size else None
+        speedups.append(t_plain / t_sur if t_sur else 0.0)
+        rows.append({"plain_final_pc": final, "plain_initial_best_pc": int(plain["traj"][0]),
+                     "surrogate_pc_at_300": int(sur["traj"][min(G, len(sur["traj"]) - 1)]),
+                     "surrogate_final_pc": int(sur["traj"][-1]),
+                     "plain_ms_to_final": t_plain, "surrogate_ms_to_plain_final": t_sur,
+                     "surrogate_generation_at_plain_final": int(hit[0]) if hit.size else None,
+                     "speedup_to_plain_final": t_plain / t_sur if t_sur else 0.0,
+                     "surrogate_ms_to_1.01x": t_sur1,
+                     "surrogate_generation_at_1.01x": int(hit1[0]) if hit1.size else None,
+                     "speedup_to_1.01x": t_plain / t_sur1 if t_sur1 else 0.0,
+                     "plain_run_ms": float(plain["gen_ms"][-1]), "surrogate_run_ms": float(sur["gen_ms"][-1]),
+                     "plain_wall_s": plain_wall, "surrogate_wall_s": sur_wall,
+                     "plain_exact_evals_per_s": float(plain["exact_evals"].sum() / (plain["gen_ms"][-1] / 1e3)),
+                     "surrogate_exact_evals_per_s": float(sur["exact_evals"].sum() / (sur["gen_ms"][-1] / 1e3)),
+                     "surrogate_children_per_s": float(lam * 2 * G / (sur["gen_ms"][-1] / 1e3))})
+    # worst rank decides (max-over-ranks time, min speedup)
+    value = float(min(speedups))
+    tot_ms = sum(r["plain_run_ms"] + r["surrogate_run_ms"] for r in rows)
+    t_max = torch.tensor([value, tot_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        t_min = t_max.clone()
+        dist.all_reduce(t_min, op=dist.ReduceOp.MIN)
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        value, tot_ms = float(t_min[0].item()), float(t_max[1].item())
+    # untimed: a diagnostic run (surrogate quality)
+    prof = runs[-1][2]["prof"]
+    sg = Surrogate(ctx, scfg(diag_every=10), seed=0)
+    diag = run_surrogate(ctx, cfg, sg, diag_cap=(G // 10) * lam)
+    sg.close()
+    rhos, relerr = [], []
+    for i in range(G // 10):
+        pr = diag["diag_pred"][i * lam:(i + 1) * lam].astype(np.float64)
+        ex = diag["diag_exact"][i * lam:(i + 1) * lam].astype(np.float64)
+        if ex.size and np.all(ex > 0):
+            rhos.append(_spearman(pr, ex))
+            relerr.append(float(np.median(np.abs(pr - ex) / ex)))
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        ctx.close()
+        return 0
+    beval = bytes_per_eval(g.n, g.num_edges, w["k"])
+    peak, peak_src = measured_peaks()
+    roofline = None
+    if prof["fitness_launches"]:
+        avg_launch_s = prof["fitness_ms"] / 1e3 / prof["fitness_launches"]
+        achieved = beval * prof["evals"] / prof["fitness_launches"] / avg_launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic("surrogate"), "kernel": "fitness (screened children)",
+                    "bytes_per_eval": beval, "evals_per_launch": prof["evals"] / prof["fitness_launches"],
+                    "avg_launch_ms": avg_launch_s * 1e3, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    run_ms = prof["fitness_ms"] + prof["operators_ms"] + prof["surrogate_ms"]
+    launches = sum(int(r["prof"][a] + r["prof"][b] + r["prof"][c]) for p_, _, s_, _ in runs for r in (p_, s_)
+                   for a, b, c in [("fitness_launches", "operator_launches", "surrogate_launches")])
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        # bounded sample: oracle (mu+lambda) generations of the plain GA on the same graph
+        pc_thr, pm_thr = oracle.thresholds(PC, PM)
+        nt = oracle.max_threads()
+        t0 = time.perf_counter()
+        pop = oracle.pop_init(g.n, w["k"], w["pop"], 0)
+        fit = oracle.fitness(g.row_ptr, g.col, pop, nthreads=nt)
+        units, gens_done = w["pop"], 0
+        while time.perf_counter() - t0 < args.cpu_seconds and gens_done < 3:
+            gens_done += 1
+            pop, fit = oracle.generation(g.row_ptr, g.col, pop, fit, gens_done, tourn=TOURN, pc_thr=pc_thr,
+                                         pm_thr=pm_thr, seed=0, flags=oracle.FLAG_MU_PLUS_LAMBDA, lam=lam,
+                                         nthreads=nt)
+            units += lam
+        el = time.perf_counter() - t0
+        cpu = {"value": units / el, "unit": "exact evals/s", "cores": nt, "kind": "oracle",
+               "sample": f"oracle plain (mu+lambda) GA on the same graph: init + {gens_done} generations = "
+                         f"{units} exact evals in {el:.1f} s; the 300-generation plain run extrapolates to "
+                         f"{(w['pop'] + lam * G) / (units / el):.0f} s"}
+    line = {"metric": w["metric"], "value": value, "unit": w["unit"], "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32 fitness; bf16/fp32 surrogate",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "graphs": w["graphs"], "k": w["k"], "mu": w["pop"], "lambda": lam,
+                       "screened": w["screened"], "generations": G,
+                       "l2": "flushed before every timed run", "parallelism": "dp (independent runs per rank)",
+                       "timing": "device time from CUDA events recorded by gapa_run_surrogate on its stream"},
+            "runs": rows,
+            "surrogate_quality": {"spearman_mean": float(np.mean(rhos)) if rhos else None,
+                                  "spearman_min": float(np.min(rhos)) if rhos else None,
+                                  "median_relative_error_mean": float(np.mean(relerr)) if relerr else None,
+                                  "diagnostic_generations": len(rhos),
+                                  "method": "diagnostic run (same seed) evaluating all 2048 children exactly every "
+                                            "10th generation; Spearman and median |estimate - PC| / PC per "
+                                            "generation"},
+            "phase_split_ms": {"screened_run": {"fitness": prof["fitness_ms"], "operators": prof["operators_ms"],
+                                                "surrogate": prof["surrogate_ms"], "sum": run_ms},
+                               "plain_run": {"fitness": runs[-1][0]["prof"]["fitness_ms"],
+                                             "operators": runs[-1][0]["prof"]["operators_ms"]}},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": float(min(
+                        (r["plain_wall_s"] * r["plain_ms_to_final"] / r["plain_run_ms"]) /
+                        (r["surrogate_wall_s"] * r["surrogate_ms_to_plain_final"] / r["surrogate_run_ms"])
+                        if r["surrogate_ms_to_plain_final"] else 0.0 for r in rows)), "unit": "x",
+                    "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(2 * (8 + 4 * w["k"]) + 3 * 8 * (3 * G + 2)),
+                    "note": "host wall clock of each gapa_run_surrogate call (graph resident; results copied to the "
+                            "host inside the call), apportioned to the target generation by the run's device-time "
+                            "fraction"},
+            "gpu_launches": launches,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    ctx.close()
     return 0
 
 

@@ -196,7 +196,9 @@ int gapa_batch_run(gapa_batch* batch, int32_t gens, int64_t* best_fit, int32_t* 
  * member kept.  Input of a deletion set D of k genes (80 values):
  * (1/sqrt k) * sum of the 64-d embeddings of its genes, then the mean, maximum
  * and standard deviation of log1p(degree) over D and sum(degree)/(2E), then
- * zeros.  Model: 80 -> 256 ReLU -> 256 ReLU -> 1, BF16 weights on the tensor
+ * log1p(r0) and log1p(r1), the numbers of live neighbours of D that G[V\D]
+ * leaves with no live neighbour and with exactly one, then zeros.
+ * Model: 80 -> 256 ReLU -> 256 ReLU -> 1, BF16 weights on the tensor
  * cores with FP32 accumulation; FP32 master weights, AdamW (Loshchilov &
  * Hutter) on every parameter, MSE against the z-scored log1p of the exact
  * fitness.  Training is deterministic (fixed-order reductions, fixed-point
@@ -210,17 +212,25 @@ typedef struct gapa_surrogate_config {
     float lr, beta1, beta2, weight_decay, eps;
     float init_scale_emb; /* embeddings start uniform in [-a, a] */
     int32_t diag_every;   /* every diag_every-th generation evaluates all children exactly and records
-                             (score, fitness) pairs; 0 = never */
+                             (estimate, fitness) pairs; 0 = never */
 } gapa_surrogate_config;
 
 typedef struct gapa_surrogate gapa_surrogate;
 
-/* A surrogate for the context's graph, weights initialised from Philox(seed). */
+/* A surrogate for the context's graph, weights initialised from Philox(seed).
+ * Every call but gapa_surrogate_destroy needs the context alive and holding
+ * the same graph (GAPA_ERR_STATE after a new upload); destruction is safe in
+ * any order. */
 int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrogate_config* scfg, uint64_t seed);
 void gapa_surrogate_destroy(gapa_surrogate* sg);
 
-/* scores_dev[r] = model output for row r of pop_dev[rows][k].  Asynchronous. */
+/* scores_dev[r] = model output for row r of pop_dev[rows][k].  Asynchronous.
+ * Genes outside [0, n) are ignored by the features. */
 int gapa_surrogate_predict(gapa_surrogate* sg, const int32_t* pop_dev, int32_t rows, int32_t k, float* scores_dev);
+
+/* Residual-degree counts of the rows of pop_dev[rows][k]: counts_dev[2r] = r0,
+ * counts_dev[2r+1] = r1 (device int32 [rows][2]).  Asynchronous. */
+int gapa_surrogate_residual(gapa_surrogate* sg, const int32_t* pop_dev, int32_t rows, int32_t k, int32_t* counts_dev);
 
 /* One AdamW step on a minibatch (rows a multiple of 16) with device targets;
  * *loss_host (may be NULL) receives the batch MSE before the step. */
@@ -241,8 +251,11 @@ int gapa_surrogate_tensor(gapa_surrogate* sg, int32_t which, int32_t grad, float
  * the fallback - with the same outputs.  Outputs: best fitness and set,
  * traj[gens+1], gen_ms[gens+1] (elapsed device time at the end of
  * initialisation and of every generation, may be NULL), exact_evals[gens+1]
- * (may be NULL), and diagnostic pairs (diag_pred, diag_exact, capacity
- * diag_cap rows).  Synchronous. */
+ * (may be NULL), and diagnostic pairs: in every diag_every-th generation
+ * (while diag_cap rows remain) all lambda children are evaluated exactly and
+ * used, and diag_pred receives the model's estimate of each child's pairwise
+ * connectivity (expm1 of the de-normalised score, FP32) beside its exact
+ * value in diag_exact.  Synchronous. */
 int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg, int64_t* best_fit,
                        int32_t* best_set, int64_t* traj, double* gen_ms, int64_t* exact_evals, float* diag_pred,
                        int64_t* diag_exact, int32_t diag_cap);
@@ -262,15 +275,18 @@ int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
 /* Per-kernel timing of the calls made between gapa_profile_begin() and
  * gapa_profile_end(): CUDA events are recorded on the launching stream around
- * every fitness launch and every genetic-operator launch (not inside the
- * graph replays of gapa_run).  gapa_profile_end() synchronises and returns
- * the totals. */
+ * every fitness launch, every genetic-operator launch and every phase of
+ * the learned surrogate (not inside the graph replays of gapa_run).
+ * gapa_profile_end() synchronises and returns the totals. */
 typedef struct gapa_profile {
     double fitness_ms;          /* summed duration of fitness launches */
-    double operators_ms;        /* summed duration of init/offspring launches */
+    double operators_ms;        /* summed duration of genetic-operator launches (init, offspring, children,
+                                   (mu+lambda) replacement, best-so-far record) */
     int64_t fitness_launches;   /* fitness kernel launches */
-    int64_t operator_launches;  /* init/offspring kernel launches */
+    int64_t operator_launches;  /* genetic-operator kernel launches */
     int64_t evals;              /* population members evaluated by those fitness launches */
+    double surrogate_ms;        /* summed duration of surrogate phases (features, MLP, selection, training) */
+    int64_t surrogate_launches; /* kernels launched by those phases */
 } gapa_profile;
 
 int gapa_profile_begin(gapa_ctx* ctx);

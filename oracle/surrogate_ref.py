@@ -8,7 +8,16 @@ Section III-C.  Definition shared with the CUDA implementation:
     e(D)  = (1 / sqrt(k)) * sum_{v in D} Emb[v]                 (64 values)
     q_v   = log1p(d_v);  f1 = mean q, f2 = max q,
     f3    = sqrt(max(mean q^2 - f1^2, 0)),  f4 = sum d_v / (2E)
-    x     = [e(D), f1, f2, f3, f4, 0 x 12]                       (80 values)
+    residual degrees of the live nodes u (u not in D) adjacent to D, in G[V - D]:
+    r0    = #{u : some neighbour in D, no live neighbour}      (isolated by the deletion)
+    r1    = #{u : some neighbour in D, exactly one live one}   (made pendant by the deletion)
+    f5    = log1p(r0),  f6 = log1p(r1)
+    x     = [e(D), f1, f2, f3, f4, f5, f6, 0 x 10]                 (80 values)
+
+  On sparse graphs most children of one generation share the giant
+  component's size up to a few nodes that the deletion isolates, so their
+  pairwise connectivity is ordered by r0 (each isolated node removes about
+  n pairs); r1 counts the nodes one more deletion would isolate.
   model   z1 = x W1 + b1, h1 = relu(z1)   (W1: 80 x 256)
           z2 = h1 W2 + b2, h2 = relu(z2)  (W2: 256 x 256)
           y  = h2 . w3 + b3
@@ -31,10 +40,28 @@ def degrees_from_csr(row_ptr) -> np.ndarray:
     return np.diff(np.asarray(row_ptr, dtype=np.int64)).astype(np.float64)
 
 
-def features(pop: np.ndarray, E: np.ndarray, deg: np.ndarray, num_edges: int) -> np.ndarray:
-    """x for every row of pop (int32[s][k]) -> float64[s][80]."""
+def residual_degree_counts(row_ptr, col, genes) -> tuple[int, int]:
+    """(r0, r1): live nodes adjacent to the deletion set left with no live neighbour, and with exactly one."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    n = row_ptr.size - 1
+    dead = np.zeros(n, dtype=bool)
+    dead[np.asarray(genes, dtype=np.int64)] = True
+    owner = np.repeat(np.arange(n), np.diff(row_ptr))
+    dead_arc = dead[np.asarray(col)]
+    live_nb = np.bincount(owner, weights=(~dead_arc).astype(np.float64), minlength=n)
+    dead_nb = np.bincount(owner, weights=dead_arc.astype(np.float64), minlength=n)
+    touched = ~dead & (dead_nb > 0)
+    r0 = int(np.count_nonzero(touched & (live_nb == 0)))
+    r1 = int(np.count_nonzero(touched & (live_nb == 1)))
+    return r0, r1
+
+
+def features(pop: np.ndarray, E: np.ndarray, row_ptr, col) -> np.ndarray:
+    """x for every row of pop (int32[s][k]) on the CSR graph (row_ptr, col) -> float64[s][80]."""
     pop = np.asarray(pop)
     s, k = pop.shape
+    deg = degrees_from_csr(row_ptr)
+    num_edges = np.asarray(col).size // 2
     x = np.zeros((s, IN), dtype=np.float64)
     q = np.log1p(deg)
     for i in range(s):
@@ -46,6 +73,9 @@ def features(pop: np.ndarray, E: np.ndarray, deg: np.ndarray, num_edges: int) ->
         x[i, 65] = qi.max()
         x[i, 66] = np.sqrt(max((qi * qi).mean() - f1 * f1, 0.0))
         x[i, 67] = deg[genes].sum() / (2.0 * num_edges)
+        r0, r1 = residual_degree_counts(row_ptr, col, genes)
+        x[i, 68] = np.log1p(r0)
+        x[i, 69] = np.log1p(r1)
     return x
 
 
@@ -58,10 +88,10 @@ def forward(params: dict, x: np.ndarray) -> tuple[np.ndarray, dict]:
     return y, {"x": x, "z1": z1, "h1": h1, "z2": z2, "h2": h2}
 
 
-def loss_and_grads(params: dict, pop: np.ndarray, t: np.ndarray, deg: np.ndarray, num_edges: int):
+def loss_and_grads(params: dict, pop: np.ndarray, t: np.ndarray, row_ptr, col):
     """MSE loss of the batch and the gradient of every parameter (fp64)."""
     k = pop.shape[1]
-    x = features(pop, params["E"], deg, num_edges)
+    x = features(pop, params["E"], row_ptr, col)
     y, c = forward(params, x)
     B = y.shape[0]
     loss = float(np.mean((y - t) ** 2))

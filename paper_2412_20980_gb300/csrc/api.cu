@@ -346,7 +346,7 @@ ProfileScope::~ProfileScope() {
         return;
     }
     cudaEventRecord(b, st);
-    c->timed.push_back(gapa_ctx::Timed{a, b, kind, evals});
+    c->timed.push_back(gapa_ctx::Timed{a, b, kind, evals, kernels});
 }
 
 extern "C" {
@@ -706,7 +706,7 @@ int gapa_profile_end(gapa_ctx* c, gapa_profile* out) {
     if (!c || !out) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard guard(c->device);
     c->profiling = false;
-    *out = gapa_profile{0.0, 0.0, 0, 0, 0};
+    *out = gapa_profile{0.0, 0.0, 0, 0, 0, 0.0, 0};
     int rc = GAPA_OK;
     for (auto& t : c->timed) {
         float ms = 0.f;
@@ -715,11 +715,14 @@ int gapa_profile_end(gapa_ctx* c, gapa_profile* out) {
         if (e != cudaSuccess && rc == GAPA_OK) rc = gapa_cuda_fail(e, "profile event");
         if (t.kind == 0) {
             out->fitness_ms += ms;
-            out->fitness_launches += 1;
+            out->fitness_launches += t.kernels;
             out->evals += t.evals;
-        } else {
+        } else if (t.kind == 1) {  // `evals` holds the kernel count when it is above 1
             out->operators_ms += ms;
-            out->operator_launches += 1;
+            out->operator_launches += std::max(1, t.evals);
+        } else {  // surrogate phase: `evals` holds its kernel count
+            out->surrogate_ms += ms;
+            out->surrogate_launches += t.evals;
         }
         c->event_pool.push_back(t.a);
         c->event_pool.push_back(t.b);

@@ -409,7 +409,7 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
             if (c->g.packed16) return launch_variant<V_TREE16>(c, ga, pop, s, k, f, st);
             if ((size_t)n * 4 <= c->fit_smem_max) return launch_variant<V_TREE32>(c, ga, pop, s, k, f, st);
             // labels too large for shared memory: interleaved member groups in global memory
-            return gapa_launch_fitness_ig(c, pop, s, k, fit, st);
+            return gapa_launch_fitness_ig(c, pop, s, k, fit, st, &prof.kernels);
     }
 }
 

@@ -240,7 +240,8 @@ int gapa_ig_prepare(gapa_ctx* c, int s) {
     return gapa_reserve((void**)&c->labels, &c->labels_cap, (size_t)groups * c->g.n * kM, sizeof(int));
 }
 
-int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st) {
+int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
+                           int* kernels) {
     const int n = c->g.n;
     int rc = gapa_ig_prepare(c, s);
     if (rc != GAPA_OK) return rc;
@@ -285,6 +286,7 @@ int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_
         ig_count_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_sum_kernel<<<grid, kIgBlock, 0, st>>>(a);
         GAPA_CUDA(cudaGetLastError());
+        if (kernels) *kernels = (g0 == 0 ? 0 : *kernels) + (a.num_nontree > 0 ? 9 : 8);
     }
     return GAPA_OK;
 }

@@ -503,6 +503,7 @@ int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in,
 
 int gapa_launch_record(gapa_ctx* c, const int64_t* fit, int s, int* gen, int64_t* traj, int* best,
                        cudaStream_t st) {
+    ProfileScope prof(c, st, 1, 1);
     record_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const long long*>(fit), s, gen,
                                       reinterpret_cast<long long*>(traj), best);
     GAPA_CUDA(cudaGetLastError());
@@ -562,6 +563,7 @@ int gapa_launch_mpl_replace(gapa_ctx* c, int mu, int lambda, int k, const int32_
     while (P < mu + lambda) P <<= 1;
     const size_t smem = (size_t)P * (sizeof(long long) + sizeof(int));
     if (smem > c->sort_smem_max) return gapa_fail(GAPA_ERR_INVALID_ARG, "mu + lambda = %d is too large", mu + lambda);
+    ProfileScope prof(c, st, 1, k > 0 ? 2 : 1);
     mpl_sort_kernel<<<1, 1024, smem, st>>>(mu, lambda, reinterpret_cast<const long long*>(fit_in),
                                            reinterpret_cast<const long long*>(kfit), src,
                                            reinterpret_cast<long long*>(fit_out), P);

@@ -151,8 +151,9 @@ struct gapa_ctx {
     bool capturing = false;
     struct Timed {
         cudaEvent_t a, b;
-        int kind;  // 0 = fitness, 1 = operators
+        int kind;  // 0 = fitness, 1 = operators, 2 = surrogate phase
         int evals;
+        int kernels;
     };
     std::vector<Timed> timed;
     std::vector<cudaEvent_t> event_pool;
@@ -163,6 +164,7 @@ struct ProfileScope {
     gapa_ctx* c;
     cudaStream_t st;
     int kind, evals;
+    int kernels = 1;  // kernels launched inside the scope (set by launchers that issue several)
     cudaEvent_t a = nullptr, b = nullptr;
     ProfileScope(gapa_ctx* c_, cudaStream_t st_, int kind_, int evals_);
     ~ProfileScope();
@@ -233,7 +235,8 @@ int gapa_fitness_batched_occupancy(size_t smem, int* blocks_per_sm);
 int gapa_ga_batched_init(size_t optin, size_t* max_dyn);
 size_t gapa_row_smem_bytes(int n, int k);
 int gapa_fitness_prepare(gapa_ctx* c, int s);  // allocate scratch before capture
-int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st);
+int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
+                           int* kernels = nullptr);
 int gapa_ig_prepare(gapa_ctx* c, int s);
 int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);
 int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,

@@ -9,7 +9,8 @@
 //
 // Model (same definition as the fp64 reference):
 //   x  = [ (1/sqrt k) sum_{v in D} Emb[v] (64) | mean, max, std of log1p(deg)
-//          over D, sum deg / 2E | 0 x 12 ]                       (80)
+//          over D, sum deg / 2E | log1p(r0), log1p(r1) | 0 x 10 ]  (80)
+//   r0 / r1 = live neighbours of D left with no / exactly one live neighbour
 //   h1 = relu(x W1 + b1) (256), h2 = relu(h1 W2 + b2) (256), y = h2 . w3 + b3
 //   target t = z-score of log1p(PC) over the replay ring; loss = mean (y-t)^2
 //   AdamW on every parameter (FP32 masters and moments).
@@ -47,6 +48,7 @@ Layout make_layout(int n) {
     L.b2 = o; o += kHid;
     L.w3 = o; o += kHid;
     L.b3 = o; o += 4;
+    o = (o + 63) & ~(size_t)63;  // the table starts on a 256-byte boundary (vector accesses)
     L.E = o; o += (size_t)n * kEmb;
     L.total = o;
     return L;
@@ -59,9 +61,11 @@ __device__ __forceinline__ unsigned ld32(const bf16* p, size_t idx) {
 // ---------------------------------------------------------------------------
 // C[M][N] = A[M][K] * B^T, A row-major (lda), B stored as [N][K] (ldb): the
 // tensor-core tile is mma.sync m16n8k16 (A row, B col, FP32 accumulate).
-// One warp computes 16 rows x 32 columns; a CTA has 4 warps (64 x 32).
-// M, K multiples of 16, N multiple of 8.  Epilogue: + bias[n], * (mask > 0),
-// relu, then FP32 and/or BF16 and/or transposed BF16 stores.
+// One warp computes 16 rows x 16 columns; a CTA has 4 warps (64 x 16).  The
+// operand fragments of four k-steps are loaded before their products so that
+// the loads overlap.  M, K multiples of 16, N multiple of 8.  Epilogue:
+// + bias[n], * (mask > 0), relu, then FP32 and/or BF16 and/or transposed
+// BF16 stores.
 // ---------------------------------------------------------------------------
 struct GemmArgs {
     int M, N, K;
@@ -81,36 +85,59 @@ struct GemmArgs {
     int relu;
 };
 
+constexpr int kGemmRowsPerCta = 64, kGemmCols = 16, kGemmUnroll = 4;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
-    const int r0 = blockIdx.y * 64 + warp * 16;
-    const int n_base = blockIdx.x * 32;
+    const int r0 = blockIdx.y * kGemmRowsPerCta + warp * 16;
+    const int n_base = blockIdx.x * kGemmCols;
     if (r0 >= a.M) return;
-    float acc[4][4];
+    const bool has_n1 = n_base + 8 < a.N;
+    float acc[2][4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
-    for (int k0 = 0; k0 < a.K; k0 += 16) {
-        const unsigned a0 = ld32(a.A, (size_t)(r0 + g) * a.lda + k0 + tig * 2);
-        const unsigned a1 = ld32(a.A, (size_t)(r0 + g + 8) * a.lda + k0 + tig * 2);
-        const unsigned a2 = ld32(a.A, (size_t)(r0 + g) * a.lda + k0 + 8 + tig * 2);
-        const unsigned a3 = ld32(a.A, (size_t)(r0 + g + 8) * a.lda + k0 + 8 + tig * 2);
+    const bf16* A0 = a.A + (size_t)(r0 + g) * a.lda + tig * 2;
+    const bf16* A1 = A0 + (size_t)8 * a.lda;
+    const bf16* B0 = a.B + (size_t)(n_base + g) * a.ldb + tig * 2;
+    const bf16* B1 = B0 + (size_t)8 * a.ldb;
+    int k0 = 0;
+    for (; k0 + 16 * kGemmUnroll <= a.K; k0 += 16 * kGemmUnroll) {
+        unsigned af[kGemmUnroll][4], bf[kGemmUnroll][4];
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int n0 = n_base + nt * 8;
-            if (n0 >= a.N) break;
-            const unsigned b0 = ld32(a.B, (size_t)(n0 + g) * a.ldb + k0 + tig * 2);
-            const unsigned b1 = ld32(a.B, (size_t)(n0 + g) * a.ldb + k0 + 8 + tig * 2);
-            asm volatile(
-                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                "{%0,%1,%2,%3};"
-                : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        for (int u = 0; u < kGemmUnroll; ++u) {
+            const int kk = k0 + 16 * u;
+            af[u][0] = ld32(A0, kk);
+            af[u][1] = ld32(A1, kk);
+            af[u][2] = ld32(A0, kk + 8);
+            af[u][3] = ld32(A1, kk + 8);
+            bf[u][0] = ld32(B0, kk);
+            bf[u][1] = ld32(B0, kk + 8);
+            bf[u][2] = has_n1 ? ld32(B1, kk) : 0u;
+            bf[u][3] = has_n1 ? ld32(B1, kk + 8) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kGemmUnroll; ++u) {
+            mma_bf16(acc[0], af[u], bf[u][0], bf[u][1]);
+            mma_bf16(acc[1], af[u], bf[u][2], bf[u][3]);
         }
     }
+    for (; k0 < a.K; k0 += 16) {
+        const unsigned af[4] = {ld32(A0, k0), ld32(A1, k0), ld32(A0, k0 + 8), ld32(A1, k0 + 8)};
+        mma_bf16(acc[0], af, ld32(B0, k0), ld32(B0, k0 + 8));
+        if (has_n1) mma_bf16(acc[1], af, ld32(B1, k0), ld32(B1, k0 + 8));
+    }
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
+    for (int nt = 0; nt < 2; ++nt) {
         const int n0 = n_base + nt * 8;
         if (n0 >= a.N) break;
 #pragma unroll
@@ -128,15 +155,141 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs a) {
     }
 }
 
+// Residual degrees of each row's deletion set D: among the live nodes with a
+// neighbour in D, r0 counts those with no live neighbour left and r1 those
+// with exactly one.  Every (gene v, neighbour u) pair with u live scans N(u)
+// until a second live neighbour shows up; u is counted by the first deleted
+// node of its adjacency list, so exactly once.  The deletion bitmap sits in
+// shared memory (ceil(n/32) words); one CTA per row.  A warp takes 32 genes
+// at a time: the (gene, neighbour) pairs of the genes of degree below 32 are
+// laid end to end and dealt out one per lane (a lane finds its gene by binary
+// search over the warp's degree prefix sums), and the whole warp walks each
+// larger adjacency together.  Genes outside [0, n) are ignored.
+__device__ __forceinline__ bool bm_dead(const unsigned* bm, int w) { return (bm[w >> 5] >> (w & 31)) & 1u; }
+
+// Per node: {first arc, degree, first neighbour, second neighbour} (-1 when absent).
+__global__ void nbr_table_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col, int n,
+                                 int4* __restrict__ T) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int b = row_ptr[u], d = row_ptr[u + 1] - b;
+        T[u] = make_int4(b, d, d > 0 ? col[b] : -1, d > 1 ? col[b + 1] : -1);
+    }
+}
+
+// (u live) -> +1 to c0 or c1 when u has at most one live neighbour and v is its first deleted one.
+// Most live u keep their first two neighbours: one 16-byte table read settles them.
+__device__ __forceinline__ void resid_pair(const unsigned* bm, const int4* __restrict__ T,
+                                           const int* __restrict__ col, int v, int u, int& c0, int& c1) {
+    if (bm_dead(bm, u)) return;
+    const int4 tu = __ldg(T + u);
+    if (tu.w >= 0 && !bm_dead(bm, tu.z) && !bm_dead(bm, tu.w)) return;
+    const int ub = tu.x, ue = tu.x + tu.y;
+    int live = 0, first_dead = -1;
+    for (int q = ub; q < ue; ++q) {
+        const int w = __ldg(col + q);
+        if (bm_dead(bm, w)) {
+            if (first_dead < 0) first_dead = w;
+        } else if (++live >= 2) {
+            return;
+        }
+    }
+    if (first_dead == v) {
+        c0 += live == 0;
+        c1 += live == 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop, int rows, int k, int n,
+                                                    const int4* __restrict__ T, const int* __restrict__ col,
+                                                    int2* __restrict__ out) {
+    extern __shared__ unsigned bm[];
+    __shared__ int red[2][8];
+    const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (r >= rows) return;
+    const int words = (n + 31) >> 5;
+    for (int w = t; w < words; w += blockDim.x) bm[w] = 0u;
+    __syncthreads();
+    const int* genes = pop + (size_t)r * k;
+    for (int j = t; j < k; j += blockDim.x) {
+        const int v = genes[j];
+        if (v >= 0 && v < n) atomicOr(&bm[v >> 5], 1u << (v & 31));
+    }
+    __syncthreads();
+    int c0 = 0, c1 = 0;
+    const int nwarps = blockDim.x >> 5;
+    for (int j0 = warp * 32; j0 < k; j0 += nwarps * 32) {
+        const int j = j0 + lane;
+        int v = j < k ? genes[j] : -1;
+        if (v >= n) v = -1;
+        int b = 0, e = 0;
+        if (v >= 0) {
+            const int4 tv = __ldg(T + v);
+            b = tv.x;
+            e = tv.x + tv.y;
+        }
+        const bool big = e - b >= 32;
+        // small adjacencies: flatten the pairs over the lanes
+        const int d = big ? 0 : e - b;
+        int incl = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            // owner = the first lane whose inclusive prefix exceeds idx
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const int pm = __shfl_sync(0xffffffffu, incl, mid);
+                if (pm > idx) hi = mid; else lo = mid + 1;
+            }
+            const int ov = __shfl_sync(0xffffffffu, v, lo), ob = __shfl_sync(0xffffffffu, b, lo),
+                      oi = __shfl_sync(0xffffffffu, incl, lo), od = __shfl_sync(0xffffffffu, d, lo);
+            if (idx < total) resid_pair(bm, T, col, ov, __ldg(col + ob + (idx - (oi - od))), c0, c1);
+        }
+        unsigned many = __ballot_sync(0xffffffffu, big);
+        while (many) {
+            const int src = __ffs(many) - 1;
+            many &= many - 1;
+            const int vb = __shfl_sync(0xffffffffu, v, src), bb = __shfl_sync(0xffffffffu, b, src),
+                      eb = __shfl_sync(0xffffffffu, e, src);
+            for (int p = bb + lane; p < eb; p += 32) resid_pair(bm, T, col, vb, __ldg(col + p), c0, c1);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_down_sync(0xffffffffu, c0, o);
+        c1 += __shfl_down_sync(0xffffffffu, c1, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = c0;
+        red[1][warp] = c1;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int x = 0, y = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            x += red[0][w];
+            y += red[1][w];
+        }
+        out[r] = make_int2(x, y);
+    }
+}
+
 // Features of each row of pop (k genes): x (BF16 [rows_pad][80]) and its
-// transpose (BF16 [80][rows_pad]); rows >= rows are zero.
-__global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ pop, int rows, int k,
+// transpose (BF16 [80][rows_pad]); rows >= rows are zero.  resid[r] holds
+// the row's residual-degree counts.  Genes outside [0, n) are ignored.
+__global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ pop, int rows, int k, int n,
                                                        const bf16* __restrict__ Eb, const float* __restrict__ logdeg,
                                                        const float* __restrict__ deg, float inv2E, float invsqrtk,
-                                                       bf16* __restrict__ X, bf16* __restrict__ XT, int rows_pad) {
-    __shared__ float part[2][kEmb];
+                                                       const int2* __restrict__ resid, bf16* __restrict__ X,
+                                                       bf16* __restrict__ XT, int rows_pad) {
+    __shared__ float2 part[4][32];
     __shared__ float st[4][4];
-    const int r = blockIdx.x, t = threadIdx.x;
+    const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (r >= rows) {
         for (int c = t; c < kIn; c += blockDim.x) {
             X[(size_t)r * kIn + c] = __float2bfloat16(0.f);
@@ -145,14 +298,40 @@ __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ p
         return;
     }
     const int* genes = pop + (size_t)r * k;
-    const int d = t & 63, half = t >> 6;
-    float s = 0.f;
-    for (int j = half; j < k; j += 2) s += __bfloat162float(Eb[(size_t)genes[j] * kEmb + d]);
-    part[half][d] = s;
+    // embedding sum: a warp reads whole 128-byte rows (lane = two dimensions),
+    // warp w takes genes w, w + 4, ...; four loads in flight per lane
+    const unsigned* E2 = reinterpret_cast<const unsigned*>(Eb);
+    float sx = 0.f, sy = 0.f;
+    int j = warp;
+    for (; j + 12 < k; j += 16) {
+        int v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = genes[j + 4 * u];
+        unsigned w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = (v[u] >= 0 && v[u] < n) ? __ldg(E2 + (size_t)v[u] * (kEmb / 2) + lane) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[u]));
+            sx += f.x;
+            sy += f.y;
+        }
+    }
+    for (; j < k; j += 4) {
+        const int v = genes[j];
+        if (v >= 0 && v < n) {
+            const unsigned w = __ldg(E2 + (size_t)v * (kEmb / 2) + lane);
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+            sx += f.x;
+            sy += f.y;
+        }
+    }
+    part[warp][lane] = make_float2(sx, sy);
     // degree statistics: thread-strided partial sums, then a fixed warp tree
     float q1 = 0.f, q2 = 0.f, qmax = -1.f, dsum = 0.f;
-    for (int j = t; j < k; j += blockDim.x) {
-        const int v = genes[j];
+    for (int i = t; i < k; i += blockDim.x) {
+        const int v = genes[i];
+        if (v < 0 || v >= n) continue;
         const float q = logdeg[v];
         q1 += q;
         q2 += q * q;
@@ -165,17 +344,19 @@ __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ p
         qmax = fmaxf(qmax, __shfl_down_sync(0xffffffffu, qmax, o));
         dsum += __shfl_down_sync(0xffffffffu, dsum, o);
     }
-    if ((t & 31) == 0) {
-        st[t >> 5][0] = q1;
-        st[t >> 5][1] = q2;
-        st[t >> 5][2] = qmax;
-        st[t >> 5][3] = dsum;
+    if (lane == 0) {
+        st[warp][0] = q1;
+        st[warp][1] = q2;
+        st[warp][2] = qmax;
+        st[warp][3] = dsum;
     }
     __syncthreads();
     if (t < kEmb) {
-        const float e = (part[0][t] + part[1][t]) * invsqrtk;
-        X[(size_t)r * kIn + t] = __float2bfloat16(e);
-        XT[(size_t)t * rows_pad + r] = __float2bfloat16(e);
+        const int l = t >> 1;
+        const float e = (t & 1) ? ((part[0][l].y + part[1][l].y) + (part[2][l].y + part[3][l].y))
+                                : ((part[0][l].x + part[1][l].x) + (part[2][l].x + part[3][l].x));
+        X[(size_t)r * kIn + t] = __float2bfloat16(e * invsqrtk);
+        XT[(size_t)t * rows_pad + r] = __float2bfloat16(e * invsqrtk);
     } else if (t < kIn) {
         float f = 0.f;
         const float Q1 = st[0][0] + st[1][0] + st[2][0] + st[3][0];
@@ -187,6 +368,8 @@ __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ p
         if (t == 65) f = k > 0 ? QM : 0.f;
         if (t == 66) f = k > 0 ? sqrtf(fmaxf(Q2 / k - mean * mean, 0.f)) : 0.f;
         if (t == 67) f = DS * inv2E;
+        if (t == 68) f = log1pf((float)resid[r].x);
+        if (t == 69) f = log1pf((float)resid[r].y);
         X[(size_t)r * kIn + t] = __float2bfloat16(f);
         XT[(size_t)t * rows_pad + r] = __float2bfloat16(f);
     }
@@ -234,22 +417,34 @@ __global__ void __launch_bounds__(256) dz2_kernel(const bf16* __restrict__ H2, c
 }
 
 // Column sums over the batch in a fixed order: dw3 = H2^T dy, db2 = sum dz2,
-// db3 = sum dy (db1 with H2 = nullptr and Z = dz1).
+// db3 = sum dy (db1 with H2 = nullptr and Z = dz1).  CTA c takes columns
+// 32c..32c+31; its 8 warps sum interleaved row groups, combined in order.
 __global__ void __launch_bounds__(256) colsum_kernel(const bf16* __restrict__ H2, const float* __restrict__ dy,
                                                      const bf16* __restrict__ Z, int B, float* __restrict__ dw3,
                                                      float* __restrict__ db, float* __restrict__ db3) {
-    const int h = threadIdx.x;
+    __shared__ float pw[8][32], pb[8][32];
+    const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5, h = blockIdx.x * 32 + lane;
     float sw = 0.f, sb = 0.f;
-    for (int b = 0; b < B; ++b) {
+    for (int b = rg; b < B; b += 8) {
         if (H2) sw += __bfloat162float(H2[(size_t)b * kHid + h]) * dy[b];
         sb += __bfloat162float(Z[(size_t)b * kHid + h]);
     }
-    if (dw3) dw3[h] = sw;
-    db[h] = sb;
-    if (db3 && h == 0) {
+    pw[rg][lane] = sw;
+    pb[rg][lane] = sb;
+    __syncthreads();
+    if (rg == 0) {
+        float w = 0.f, c = 0.f;
+        for (int g = 0; g < 8; ++g) {
+            w += pw[g][lane];
+            c += pb[g][lane];
+        }
+        if (dw3) dw3[h] = w;
+        db[h] = c;
+    } else if (rg == 1 && db3 && blockIdx.x == 0) {
         float s = 0.f;
-        for (int b = 0; b < B; ++b) s += dy[b];
-        db3[0] = s;
+        for (int b = lane; b < B; b += 32) s += dy[b];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) db3[0] = s;
     }
 }
 
@@ -265,11 +460,46 @@ __global__ void __launch_bounds__(256) emb_grad_kernel(const int* __restrict__ p
     for (int j = jj; j < k; j += 4) atomicAdd(&Gi[(size_t)genes[j] * kEmb + d], (unsigned long long)q);
 }
 
-__global__ void emb_grad_convert_kernel(unsigned long long* __restrict__ Gi, float* __restrict__ G, size_t count) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        G[i] = (float)((double)(long long)Gi[i] / kFix);
-        Gi[i] = 0ull;
+// Fixed point (2^-40) to FP32 without the FP64 pipe: hi * 2^32 + lo in one
+// rounding, then the exact scaling by 2^-40.
+__device__ __forceinline__ float fix_to_float(unsigned long long u) {
+    const long long x = (long long)u;
+    return fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned)x) * 9.094947017729282e-13f;
+}
+
+__device__ __forceinline__ float adamw_one(float p, float g, float& m, float& v, float lr, float b1, float b2,
+                                           float wd, float eps, float bc1, float bc2) {
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    return p - lr * ((m / bc1) / (sqrtf(v / bc2) + eps) + wd * p);
+}
+
+// The embedding table's step in one pass over 4-element groups: the
+// fixed-point gradient, AdamW on the FP32 master and moments, the BF16 copy.
+// The accumulator keeps the gradient until the next step clears it.
+__global__ void __launch_bounds__(256) emb_update_kernel(const ulonglong2* __restrict__ Gi, float4* __restrict__ P,
+                                                         float4* __restrict__ M, float4* __restrict__ V,
+                                                         uint2* __restrict__ Eb, size_t groups, float lr, float b1,
+                                                         float b2, float wd, float eps, float bc1, float bc2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < groups; i += (size_t)gridDim.x * blockDim.x) {
+        const ulonglong2 g01 = Gi[2 * i], g23 = Gi[2 * i + 1];
+        float4 p = P[i], m = M[i], v = V[i];
+        p.x = adamw_one(p.x, fix_to_float(g01.x), m.x, v.x, lr, b1, b2, wd, eps, bc1, bc2);
+        p.y = adamw_one(p.y, fix_to_float(g01.y), m.y, v.y, lr, b1, b2, wd, eps, bc1, bc2);
+        p.z = adamw_one(p.z, fix_to_float(g23.x), m.z, v.z, lr, b1, b2, wd, eps, bc1, bc2);
+        p.w = adamw_one(p.w, fix_to_float(g23.y), m.w, v.w, lr, b1, b2, wd, eps, bc1, bc2);
+        P[i] = p;
+        M[i] = m;
+        V[i] = v;
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(p.x, p.y), hi = __floats2bfloat162_rn(p.z, p.w);
+        Eb[i] = make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
     }
+}
+
+// The last embedding gradient as FP32 (for gapa_surrogate_tensor).
+__global__ void emb_grad_float_kernel(const unsigned long long* __restrict__ Gi, float* __restrict__ G, size_t count) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        G[i] = fix_to_float(Gi[i]);
 }
 
 __global__ void adamw_kernel(float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
@@ -343,14 +573,16 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ sc
     for (int r = threadIdx.x; r < m; r += blockDim.x) sel[r] = (int)(keys[r] & 0xFFFFFFFFu);
 }
 
-// dst row r = src row idx[r] (idx may be null: identity), k genes.
-__global__ void gather_rows_kernel(const int* __restrict__ src, const int* __restrict__ idx, int k,
-                                   int* __restrict__ dst, int dst_stride_rows, int dst_first, int dst_cap) {
+// dst row r = src row idx[r] (idx may be null: identity), k genes, with its
+// residual-degree counts; dst_cap > 0 writes ring slots (dst_first + r) mod dst_cap.
+__global__ void gather_rows_kernel(const int* __restrict__ src, const int2* __restrict__ rsrc,
+                                   const int* __restrict__ idx, int k, int* __restrict__ dst, int2* __restrict__ rdst,
+                                   int dst_first, int dst_cap) {
     const int r = blockIdx.x;
     const int from = idx ? idx[r] : r;
     const int to = dst_cap > 0 ? (dst_first + r) % dst_cap : r;
-    (void)dst_stride_rows;
     for (int j = threadIdx.x; j < k; j += blockDim.x) dst[(size_t)to * k + j] = src[(size_t)from * k + j];
+    if (threadIdx.x == 0) rdst[to] = rsrc[from];
 }
 
 // kfit[i] = +inf for every child, then the evaluated ones.
@@ -361,34 +593,37 @@ __global__ void scatter_fit_kernel(const long long* __restrict__ fsel, const int
     for (int r = threadIdx.x; r < m; r += blockDim.x) kfit[sel[r]] = fsel[r];
 }
 
-// Ring fitness append.
+// Ring append: log1p of each exact fitness (FP64), the training target before normalisation.
 __global__ void ring_fit_kernel(const int64_t* __restrict__ f, const int* __restrict__ idx, int cnt,
-                                int64_t* __restrict__ ring_fit, int first, int cap) {
+                                double* __restrict__ ring_lp, int first, int cap) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x)
-        ring_fit[(first + r) % cap] = f[idx ? idx[r] : r];
+        ring_lp[(first + r) % cap] = log1p((double)f[idx ? idx[r] : r]);
 }
 
-// Mean and standard deviation of log1p(fitness) over the ring (one CTA, FP64).
-__global__ void __launch_bounds__(256) target_stats_kernel(const int64_t* __restrict__ ring_fit, int valid,
-                                                           double* __restrict__ stats) {
-    __shared__ double s1[256], s2[256];
+// Mean and standard deviation of log1p(fitness) over the ring (one CTA, FP64,
+// fixed-order reduction).
+__global__ void __launch_bounds__(1024) target_stats_kernel(const double* __restrict__ ring_lp, int valid,
+                                                            double* __restrict__ stats) {
+    __shared__ double s1[1024], s2[1024];
     double a = 0, b = 0;
     for (int i = threadIdx.x; i < valid; i += blockDim.x) {
-        const double l = log1p((double)ring_fit[i]);
+        const double l = ring_lp[i];
         a += l;
         b += l * l;
     }
     s1[threadIdx.x] = a;
     s2[threadIdx.x] = b;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double A = 0, Bq = 0;
-        for (int i = 0; i < 256; ++i) {
-            A += s1[i];
-            Bq += s2[i];
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
         }
-        const double mu = A / valid;
-        const double var = Bq / valid - mu * mu;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mu = s1[0] / valid;
+        const double var = s2[0] / valid - mu * mu;
         stats[0] = mu;
         stats[1] = var > 1e-24 ? sqrt(var) : 1.0;
     }
@@ -396,14 +631,26 @@ __global__ void __launch_bounds__(256) target_stats_kernel(const int64_t* __rest
 
 // Minibatch: rows drawn uniformly from the valid ring entries (Philox tag 8,
 // counter (b, step, g, 8 << 24 | 1)), targets z-scored.
-__global__ void batch_kernel(const int* __restrict__ ring, const int64_t* __restrict__ ring_fit, int valid, int k,
-                             int B, RngKey key, int step, int g, const double* __restrict__ stats,
-                             int* __restrict__ rows, float* __restrict__ t) {
+__global__ void batch_kernel(const int* __restrict__ ring, const int2* __restrict__ ring_resid,
+                             const double* __restrict__ ring_lp, int valid, int k, int B, RngKey key, int step,
+                             int g, const double* __restrict__ stats, int* __restrict__ rows,
+                             int2* __restrict__ resid, float* __restrict__ t) {
     const int b = blockIdx.x;
     const int idx = uniform_below(philox_word0((uint32_t)b, (uint32_t)step, (uint32_t)g, (8u << 24) | 1u, key.lo, key.hi),
                                   valid);
     for (int j = threadIdx.x; j < k; j += blockDim.x) rows[(size_t)b * k + j] = ring[(size_t)idx * k + j];
-    if (threadIdx.x == 0) t[b] = (float)((log1p((double)ring_fit[idx]) - stats[0]) / stats[1]);
+    if (threadIdx.x == 0) {
+        t[b] = (float)((ring_lp[idx] - stats[0]) / stats[1]);
+        resid[b] = ring_resid[idx];
+    }
+}
+
+// Scores back to pairwise-connectivity estimates: expm1(mean + std * y) with
+// the target statistics of the last training step.
+__global__ void decode_kernel(const float* __restrict__ y, int rows, const double* __restrict__ stats,
+                              float* __restrict__ out) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+        out[r] = (float)expm1(stats[0] + stats[1] * (double)y[r]);
 }
 
 }  // namespace
@@ -413,6 +660,7 @@ __global__ void batch_kernel(const int* __restrict__ ring, const int64_t* __rest
 // ---------------------------------------------------------------------------
 struct gapa_surrogate {
     gapa_ctx* ctx = nullptr;
+    int device = 0;  // the context's device, kept so that destruction never reads the context
     gapa_surrogate_config cfg;
     RngKey key;
     Layout L;
@@ -426,6 +674,11 @@ struct gapa_surrogate {
     bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
          *dZ1 = nullptr, *dZ1T = nullptr;
     float *y = nullptr, *dy = nullptr, *dX = nullptr, *loss = nullptr, *tbuf = nullptr;
+    int2* resid = nullptr;       // residual-degree counts of the rows of the last forward
+    int4* nbr = nullptr;         // per node: first arc, degree, first two neighbours
+    const int* row_ptr = nullptr;  // the context's CSR (original node ids)
+    const int* col = nullptr;
+    size_t resid_smem = 0;       // deletion bitmap bytes of resid_kernel
     int* batch_rows = nullptr;
     double* stats = nullptr;
     int tau = 0;
@@ -434,7 +687,7 @@ struct gapa_surrogate {
 namespace {
 
 int launch_gemm(const GemmArgs& a, cudaStream_t st) {
-    dim3 grid((a.N + 31) / 32, (a.M + 63) / 64);
+    dim3 grid((a.N + kGemmCols - 1) / kGemmCols, (a.M + kGemmRowsPerCta - 1) / kGemmRowsPerCta);
     gemm_bf16_kernel<<<grid, 128, 0, st>>>(a);
     GAPA_CUDA(cudaGetLastError());
     return GAPA_OK;
@@ -464,10 +717,28 @@ int refresh_bf16(gapa_surrogate* s, cudaStream_t st) {
 int round16(int x) { return (x + 15) & ~15; }
 
 // Features + forward; keeps the transposed copies for a training step.
-int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, cudaStream_t st) {
+// Residual-degree counts of `rows` deletion sets into s->resid.
+int compute_resid(gapa_surrogate* s, const int32_t* pop, int rows, int k, cudaStream_t st) {
+    if (rows <= 0) return GAPA_OK;
+    ProfileScope prof(s->ctx, st, 2, 1);
+    resid_kernel<<<rows, 256, s->resid_smem, st>>>(pop, rows, k, s->n, s->nbr, s->col, s->resid);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
+// Features + forward; keeps the transposed copies for a training step.  With
+// resid == nullptr the residual-degree counts are computed into s->resid first.
+int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, cudaStream_t st,
+            const int2* resid = nullptr) {
+    if (!resid) {
+        int rc = compute_resid(s, pop, rows, k, st);
+        if (rc != GAPA_OK) return rc;
+        resid = s->resid;
+    }
+    ProfileScope prof(s->ctx, st, 2, 4);
     const int R = round16(rows);
-    features_kernel<<<R, 128, 0, st>>>(pop, rows, k, s->Eb, s->logdeg, s->deg, s->inv2E, 1.f / sqrtf((float)std::max(k, 1)),
-                                       s->X, s->XT, R);
+    features_kernel<<<R, 128, 0, st>>>(pop, rows, k, s->n, s->Eb, s->logdeg, s->deg, s->inv2E,
+                                       1.f / sqrtf((float)std::max(k, 1)), resid, s->X, s->XT, R);
     GemmArgs a = gemm(R, kHid, kIn, s->X, kIn, s->W1tb, kIn);
     a.Cb = s->H1;
     a.ldcb = kHid;
@@ -492,14 +763,16 @@ int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, c
 }
 
 // One AdamW step on a batch (rows a multiple of 16) with targets t.
-int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float* t, cudaStream_t st) {
-    int rc = forward(s, pop, B, k, true, st);
+int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float* t, cudaStream_t st,
+               const int2* resid = nullptr) {
+    int rc = forward(s, pop, B, k, true, st, resid);
     if (rc != GAPA_OK) return rc;
+    ProfileScope prof(s->ctx, st, 2, 13);
     float* G = s->G;
     const Layout& L = s->L;
     loss_kernel<<<1, 256, 0, st>>>(s->y, t, B, s->dy, s->loss);
     dz2_kernel<<<B, kHid, 0, st>>>(s->H2, s->dy, s->P + L.w3, B, s->dZ2, s->dZ2T);
-    colsum_kernel<<<1, kHid, 0, st>>>(s->H2, s->dy, s->dZ2, B, G + L.w3, G + L.b2, G + L.b3);
+    colsum_kernel<<<kHid / 32, 256, 0, st>>>(s->H2, s->dy, s->dZ2, B, G + L.w3, G + L.b2, G + L.b3);
     // dW2 = h1^T dz2  ([in][out])
     GemmArgs a = gemm(kHid, kHid, B, s->H1T, B, s->dZ2T, B);
     a.Cf = G + L.W2;
@@ -514,7 +787,7 @@ int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float*
     a.mask = s->H1;
     a.ldm = kHid;
     if ((rc = launch_gemm(a, st)) != GAPA_OK) return rc;
-    colsum_kernel<<<1, kHid, 0, st>>>(nullptr, nullptr, s->dZ1, B, nullptr, G + L.b1, nullptr);
+    colsum_kernel<<<kHid / 32, 256, 0, st>>>(nullptr, nullptr, s->dZ1, B, nullptr, G + L.b1, nullptr);
     // dW1 = x^T dz1  ([80][256])
     a = gemm(kIn, kHid, B, s->XT, B, s->dZ1T, B);
     a.Cf = G + L.W1;
@@ -525,14 +798,21 @@ int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float*
     a.Cf = s->dX;
     a.ldc = kIn;
     if ((rc = launch_gemm(a, st)) != GAPA_OK) return rc;
+    GAPA_CUDA(cudaMemsetAsync(s->Gi, 0, (size_t)s->n * kEmb * sizeof(unsigned long long), st));
     emb_grad_kernel<<<B, 256, 0, st>>>(pop, k, s->dX, 1.f / sqrtf((float)std::max(k, 1)), s->Gi);
-    emb_grad_convert_kernel<<<s->ctx->num_sms * 4, 256, 0, st>>>(s->Gi, G + L.E, (size_t)s->n * kEmb);
     s->tau += 1;
     const float bc1 = 1.f - powf(s->cfg.beta1, (float)s->tau), bc2 = 1.f - powf(s->cfg.beta2, (float)s->tau);
-    adamw_kernel<<<s->ctx->num_sms * 4, 256, 0, st>>>(s->P, s->M, s->V, G, L.total, s->cfg.lr, s->cfg.beta1,
-                                                      s->cfg.beta2, s->cfg.weight_decay, s->cfg.eps, bc1, bc2);
+    // dense parameters (W1 .. b3), then the embedding table in one fused pass
+    adamw_kernel<<<64, 256, 0, st>>>(s->P, s->M, s->V, G, L.E, s->cfg.lr, s->cfg.beta1, s->cfg.beta2,
+                                     s->cfg.weight_decay, s->cfg.eps, bc1, bc2);
+    emb_update_kernel<<<s->ctx->num_sms * 8, 256, 0, st>>>(
+        reinterpret_cast<const ulonglong2*>(s->Gi), reinterpret_cast<float4*>(s->P + L.E),
+        reinterpret_cast<float4*>(s->M + L.E), reinterpret_cast<float4*>(s->V + L.E), reinterpret_cast<uint2*>(s->Eb),
+        (size_t)s->n * kEmb / 4, s->cfg.lr, s->cfg.beta1, s->cfg.beta2, s->cfg.weight_decay, s->cfg.eps, bc1, bc2);
+    to_bf16_kernel<<<64, 256, 0, st>>>(s->P + L.W1, kIn, kHid, s->W1b, s->W1tb);
+    to_bf16_kernel<<<128, 256, 0, st>>>(s->P + L.W2, kHid, kHid, s->W2b, s->W2tb);
     GAPA_CUDA(cudaGetLastError());
-    return refresh_bf16(s, st);
+    return GAPA_OK;
 }
 
 int ensure_rows(gapa_surrogate* s, int rows) {
@@ -548,12 +828,14 @@ int ensure_rows(gapa_surrogate* s, int rows) {
         cudaFree(*p);
         *p = nullptr;
     }
+    cudaFree(s->resid);
+    s->resid = nullptr;
     const size_t e80 = (size_t)R * kIn, e256 = (size_t)R * kHid;
     if (cudaMalloc(&s->X, e80 * 2) || cudaMalloc(&s->XT, e80 * 2) || cudaMalloc(&s->H1, e256 * 2) ||
         cudaMalloc(&s->H1T, e256 * 2) || cudaMalloc(&s->H2, e256 * 2) || cudaMalloc(&s->dZ2, e256 * 2) ||
         cudaMalloc(&s->dZ2T, e256 * 2) || cudaMalloc(&s->dZ1, e256 * 2) || cudaMalloc(&s->dZ1T, e256 * 2) ||
         cudaMalloc(&s->y, (size_t)R * 4) || cudaMalloc(&s->dy, (size_t)R * 4) || cudaMalloc(&s->dX, e80 * 4) ||
-        cudaMalloc(&s->tbuf, (size_t)R * 4)) {
+        cudaMalloc(&s->tbuf, (size_t)R * 4) || cudaMalloc(&s->resid, (size_t)R * sizeof(int2))) {
         cudaGetLastError();
         return gapa_fail(GAPA_ERR_OOM, "surrogate activations for %d rows", R);
     }
@@ -561,10 +843,17 @@ int ensure_rows(gapa_surrogate* s, int rows) {
     return GAPA_OK;
 }
 
+// The surrogate reads the context's CSR: a graph uploaded after creation invalidates it.
+int check_graph(const gapa_surrogate* s) {
+    if (s->ctx->g.row_ptr != s->row_ptr || s->ctx->g.n != s->n)
+        return gapa_fail(GAPA_ERR_STATE, "the context's graph changed after the surrogate was created");
+    return GAPA_OK;
+}
+
 void free_surrogate(gapa_surrogate* s) {
     void* ps[] = {s->P, s->M, s->V, s->G, s->Gi, s->W1b, s->W1tb, s->W2b, s->W2tb, s->Eb, s->logdeg, s->deg,
                   s->X, s->XT, s->H1, s->H1T, s->H2, s->dZ2, s->dZ2T, s->dZ1, s->dZ1T, s->y, s->dy, s->dX,
-                  s->loss, s->tbuf, s->batch_rows, s->stats};
+                  s->loss, s->tbuf, s->batch_rows, s->stats, s->resid, s->nbr};
     for (void* p : ps) cudaFree(p);
 }
 
@@ -582,9 +871,24 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
     cudaSetDevice(ctx->device);
     gapa_surrogate* s = new gapa_surrogate();
     s->ctx = ctx;
+    s->device = ctx->device;
     s->cfg = *scfg;
     s->key = RngKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
     s->n = ctx->g.n;
+    s->row_ptr = ctx->g.row_ptr;
+    s->col = ctx->g.col;
+    s->resid_smem = (((size_t)s->n + 31) / 32) * 4;
+    if (s->resid_smem > ctx->smem_optin) {
+        delete s;
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "n = %d: the deletion bitmap does not fit in shared memory", ctx->g.n);
+    }
+    if (s->resid_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->resid_smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return gapa_fail(GAPA_ERR_CUDA, "shared memory limit of the residual-degree kernel");
+    }
     s->L = make_layout(s->n);
     auto bail = [&](int rc) {
         free_surrogate(s);
@@ -597,7 +901,8 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
         cudaMalloc(&s->W1b, (size_t)kIn * kHid * 2) || cudaMalloc(&s->W1tb, (size_t)kIn * kHid * 2) ||
         cudaMalloc(&s->W2b, (size_t)kHid * kHid * 2) || cudaMalloc(&s->W2tb, (size_t)kHid * kHid * 2) ||
         cudaMalloc(&s->Eb, (size_t)s->n * kEmb * 2) || cudaMalloc(&s->logdeg, (size_t)s->n * 4) ||
-        cudaMalloc(&s->deg, (size_t)s->n * 4) || cudaMalloc(&s->loss, 4) || cudaMalloc(&s->stats, 16)) {
+        cudaMalloc(&s->deg, (size_t)s->n * 4) || cudaMalloc(&s->loss, 4) || cudaMalloc(&s->stats, 16) ||
+        cudaMalloc(&s->nbr, (size_t)s->n * sizeof(int4))) {
         cudaGetLastError();
         return bail(gapa_fail(GAPA_ERR_OOM, "surrogate parameters"));
     }
@@ -614,10 +919,13 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
     cudaMemcpy(s->logdeg, lg.data(), lg.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(s->deg, dg.data(), dg.size() * 4, cudaMemcpyHostToDevice);
     cudaStream_t st = ctx->stream;
+    nbr_table_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(s->row_ptr, s->col, s->n, s->nbr);
     cudaMemsetAsync(s->P, 0, np * 4, st);
     cudaMemsetAsync(s->M, 0, np * 4, st);
     cudaMemsetAsync(s->V, 0, np * 4, st);
     cudaMemsetAsync(s->Gi, 0, (size_t)s->n * kEmb * 8, st);
+    const double unit_stats[2] = {0.0, 1.0};  // targets before the first training step: identity
+    cudaMemcpy(s->stats, unit_stats, sizeof unit_stats, cudaMemcpyHostToDevice);
     const int grid = ctx->num_sms * 4;
     init_uniform_kernel<<<grid, 256, 0, st>>>(s->P + s->L.W1, (size_t)kIn * kHid, sqrtf(6.f / kIn), s->key, 1);
     init_uniform_kernel<<<grid, 256, 0, st>>>(s->P + s->L.W2, (size_t)kHid * kHid, sqrtf(6.f / kHid), s->key, 2);
@@ -633,8 +941,8 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
 
 void gapa_surrogate_destroy(gapa_surrogate* s) {
     if (!s) return;
-    cudaSetDevice(s->ctx->device);
-    cudaStreamSynchronize(s->ctx->stream);
+    cudaSetDevice(s->device);
+    cudaDeviceSynchronize();  // the context (and its stream) may already be gone
     free_surrogate(s);
     delete s;
 }
@@ -643,7 +951,8 @@ int gapa_surrogate_predict(gapa_surrogate* s, const int32_t* pop_dev, int32_t ro
     if (!s || rows < 0 || k < 0 || (rows > 0 && (!pop_dev || !scores_dev))) return gapa_fail(GAPA_ERR_INVALID_ARG, "bad predict arguments");
     if (rows == 0) return GAPA_OK;
     cudaSetDevice(s->ctx->device);
-    int rc = ensure_rows(s, rows);
+    int rc = check_graph(s);
+    if (rc == GAPA_OK) rc = ensure_rows(s, rows);
     if (rc != GAPA_OK) return rc;
     cudaStream_t st = s->ctx->stream;
     rc = forward(s, pop_dev, rows, k, false, st);
@@ -652,12 +961,27 @@ int gapa_surrogate_predict(gapa_surrogate* s, const int32_t* pop_dev, int32_t ro
     return GAPA_OK;
 }
 
+int gapa_surrogate_residual(gapa_surrogate* s, const int32_t* pop_dev, int32_t rows, int32_t k, int32_t* counts_dev) {
+    if (!s || rows < 0 || k < 0 || (rows > 0 && (!pop_dev || !counts_dev)))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "bad residual arguments");
+    if (rows == 0) return GAPA_OK;
+    cudaSetDevice(s->ctx->device);
+    int rc = check_graph(s);
+    if (rc == GAPA_OK) rc = ensure_rows(s, rows);
+    if (rc == GAPA_OK) rc = compute_resid(s, pop_dev, rows, k, s->ctx->stream);
+    if (rc != GAPA_OK) return rc;
+    GAPA_CUDA(cudaMemcpyAsync(counts_dev, s->resid, (size_t)rows * sizeof(int2), cudaMemcpyDeviceToDevice,
+                              s->ctx->stream));
+    return GAPA_OK;
+}
+
 int gapa_surrogate_train_step(gapa_surrogate* s, const int32_t* pop_dev, int32_t rows, int32_t k,
                               const float* target_dev, float* loss_host) {
     if (!s || rows < 16 || rows % 16 || k < 1 || !pop_dev || !target_dev)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "training batches need a multiple of 16 rows and k >= 1");
     cudaSetDevice(s->ctx->device);
-    int rc = ensure_rows(s, rows);
+    int rc = check_graph(s);
+    if (rc == GAPA_OK) rc = ensure_rows(s, rows);
     if (rc != GAPA_OK) return rc;
     cudaStream_t st = s->ctx->stream;
     rc = train_step(s, pop_dev, rows, k, target_dev, st);
@@ -678,6 +1002,8 @@ int gapa_surrogate_tensor(gapa_surrogate* s, int32_t which, int32_t grad, float*
     cudaSetDevice(s->ctx->device);
     float* base = (grad ? s->G : s->P) + offs[which];
     cudaStream_t st = s->ctx->stream;
+    if (grad && which == 6 && !set)  // the embedding gradient lives in fixed point until asked for
+        emb_grad_float_kernel<<<s->ctx->num_sms * 4, 256, 0, st>>>(s->Gi, base, sizes[which]);
     if (set) {
         GAPA_CUDA(cudaMemcpyAsync(base, host, sizes[which] * 4, cudaMemcpyHostToDevice, st));
         if (!grad) {
@@ -698,6 +1024,7 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     if (!(cfg->flags & GAPA_FLAG_MU_PLUS_LAMBDA) || cfg->lambda < 1)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "surrogate runs use (mu+lambda) with lambda >= 1");
     if (s && s->ctx != c) return gapa_fail(GAPA_ERR_INVALID_ARG, "surrogate belongs to another context");
+    if (s && check_graph(s) != GAPA_OK) return GAPA_ERR_STATE;
     if (s && s->cfg.ring < std::max(cfg->pop, cfg->lambda))
         return gapa_fail(GAPA_ERR_INVALID_ARG, "the replay ring must hold at least max(mu, lambda) rows");
     cudaSetDevice(c->device);
@@ -712,7 +1039,9 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     int64_t* F[2] = {c->stage_fit[0], c->stage_fit[1]};
     // surrogate buffers
     int32_t *ring = nullptr, *sel = nullptr, *sel_rows = nullptr, *batch_rows = nullptr;
-    int64_t *ring_fit = nullptr, *fsel = nullptr;
+    int64_t* fsel = nullptr;
+    double* ring_lp = nullptr;  // log1p(exact fitness) of every ring row
+    int2 *ring_resid = nullptr, *sel_resid = nullptr, *batch_resid = nullptr;
     float* scores = nullptr;
     const int ring_cap = s ? s->cfg.ring : 0;
     auto cleanup = [&]() {
@@ -720,14 +1049,20 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
         cudaFree(sel);
         cudaFree(sel_rows);
         cudaFree(batch_rows);
-        cudaFree(ring_fit);
+        cudaFree(ring_lp);
         cudaFree(fsel);
         cudaFree(scores);
+        cudaFree(ring_resid);
+        cudaFree(sel_resid);
+        cudaFree(batch_resid);
     };
     if (cudaMalloc(&sel, (size_t)lam * 4) || cudaMalloc(&sel_rows, (size_t)lam * k * 4 + 4) ||
         cudaMalloc(&fsel, (size_t)lam * 8) || cudaMalloc(&scores, (size_t)lam * 4) ||
-        (s && (cudaMalloc(&ring, (size_t)ring_cap * k * 4 + 4) || cudaMalloc(&ring_fit, (size_t)ring_cap * 8) ||
-               cudaMalloc(&batch_rows, (size_t)s->cfg.batch * k * 4 + 4)))) {
+        (s && (cudaMalloc(&ring, (size_t)ring_cap * k * 4 + 4) || cudaMalloc(&ring_lp, (size_t)ring_cap * 8) ||
+               cudaMalloc(&batch_rows, (size_t)s->cfg.batch * k * 4 + 4) ||
+               cudaMalloc(&ring_resid, (size_t)ring_cap * sizeof(int2)) ||
+               cudaMalloc(&sel_resid, (size_t)lam * sizeof(int2)) ||
+               cudaMalloc(&batch_resid, (size_t)s->cfg.batch * sizeof(int2))))) {
         cudaGetLastError();
         cleanup();
         return gapa_fail(GAPA_ERR_OOM, "surrogate run buffers");
@@ -759,8 +1094,9 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     if (rc != GAPA_OK) return fail(rc);
     exact[0] = mu;
     if (s) {  // the initial population enters the ring
-        gather_rows_kernel<<<mu, 256, 0, st>>>(P[0], nullptr, k, ring, 0, ring_pos, ring_cap);
-        ring_fit_kernel<<<1, 256, 0, st>>>(F[0], nullptr, mu, ring_fit, ring_pos, ring_cap);
+        if ((rc = compute_resid(s, P[0], mu, k, st)) != GAPA_OK) return fail(rc);
+        gather_rows_kernel<<<mu, 256, 0, st>>>(P[0], s->resid, nullptr, k, ring, ring_resid, ring_pos, ring_cap);
+        ring_fit_kernel<<<(mu + 255) / 256, 256, 0, st>>>(F[0], nullptr, mu, ring_lp, ring_pos, ring_cap);
         ring_pos = (ring_pos + mu) % ring_cap;
         ring_valid = std::min(ring_cap, ring_valid + mu);
     }
@@ -779,19 +1115,27 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
                           diag_exact_host && diag_rows + lam <= diag_cap;
         int evaluated = lam;
         if (screen || diag) rc = forward(s, c->kids, lam, k, false, st);
+        else if (s) rc = compute_resid(s, c->kids, lam, k, st);  // for the ring
         if (rc == GAPA_OK && screen && !diag) {
-            topk_kernel<<<1, 1024, (size_t)topk_P * 8, st>>>(s->y, lam, screened, sel, topk_P);
-            gather_rows_kernel<<<screened, 256, 0, st>>>(c->kids, sel, k, sel_rows, 0, 0, 0);
+            {
+                ProfileScope prof(c, st, 2, 2);
+                topk_kernel<<<1, 1024, (size_t)topk_P * 8, st>>>(s->y, lam, screened, sel, topk_P);
+                gather_rows_kernel<<<screened, 256, 0, st>>>(c->kids, s->resid, sel, k, sel_rows, sel_resid, 0, 0);
+            }
             rc = gapa_launch_fitness(c, sel_rows, screened, k, fsel, st);
-            scatter_fit_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const long long*>(fsel), sel, screened, lam,
-                                                   reinterpret_cast<long long*>(c->kfit));
+            {
+                ProfileScope prof(c, st, 2, 1);
+                scatter_fit_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const long long*>(fsel), sel, screened, lam,
+                                                       reinterpret_cast<long long*>(c->kfit));
+            }
             evaluated = screened;
         } else if (rc == GAPA_OK) {
             rc = gapa_launch_fitness(c, c->kids, lam, k, c->kfit, st);
             if (rc == GAPA_OK && diag) {
                 // diagnostic generation: every child is evaluated exactly (and used by the
-                // truncation), and the (score, fitness) pairs are recorded
-                GAPA_CUDA(cudaMemcpyAsync(diag_pred_host + diag_rows, s->y, (size_t)lam * 4, cudaMemcpyDeviceToHost, st));
+                // truncation), and the (estimate, fitness) pairs are recorded
+                decode_kernel<<<(lam + 255) / 256, 256, 0, st>>>(s->y, lam, s->stats, scores);
+                GAPA_CUDA(cudaMemcpyAsync(diag_pred_host + diag_rows, scores, (size_t)lam * 4, cudaMemcpyDeviceToHost, st));
                 GAPA_CUDA(cudaMemcpyAsync(diag_exact_host + diag_rows, c->kfit, (size_t)lam * 8, cudaMemcpyDeviceToHost, st));
                 diag_rows += lam;
             }
@@ -799,12 +1143,15 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
         if (rc != GAPA_OK) break;
         exact[g] = evaluated;
         if (s) {  // evaluated children enter the ring
+            ProfileScope prof(c, st, 2, 2);
             if (evaluated == lam) {
-                gather_rows_kernel<<<lam, 256, 0, st>>>(c->kids, nullptr, k, ring, 0, ring_pos, ring_cap);
-                ring_fit_kernel<<<(lam + 255) / 256, 256, 0, st>>>(c->kfit, nullptr, lam, ring_fit, ring_pos, ring_cap);
+                gather_rows_kernel<<<lam, 256, 0, st>>>(c->kids, s->resid, nullptr, k, ring, ring_resid, ring_pos,
+                                                        ring_cap);
+                ring_fit_kernel<<<(lam + 255) / 256, 256, 0, st>>>(c->kfit, nullptr, lam, ring_lp, ring_pos, ring_cap);
             } else {
-                gather_rows_kernel<<<evaluated, 256, 0, st>>>(sel_rows, nullptr, k, ring, 0, ring_pos, ring_cap);
-                ring_fit_kernel<<<(evaluated + 255) / 256, 256, 0, st>>>(fsel, nullptr, evaluated, ring_fit, ring_pos,
+                gather_rows_kernel<<<evaluated, 256, 0, st>>>(sel_rows, sel_resid, nullptr, k, ring, ring_resid,
+                                                              ring_pos, ring_cap);
+                ring_fit_kernel<<<(evaluated + 255) / 256, 256, 0, st>>>(fsel, nullptr, evaluated, ring_lp, ring_pos,
                                                                         ring_cap);
             }
             ring_pos = (ring_pos + evaluated) % ring_cap;
@@ -815,11 +1162,18 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
         cur ^= 1;
         // online training on the ring
         if (rc == GAPA_OK && s && ring_valid >= s->cfg.batch && s->cfg.train_steps > 0) {
-            target_stats_kernel<<<1, 256, 0, st>>>(ring_fit, ring_valid, s->stats);
+            {
+                ProfileScope prof(c, st, 2, 1);
+                target_stats_kernel<<<1, 1024, 0, st>>>(ring_lp, ring_valid, s->stats);
+            }
             for (int step = 0; step < s->cfg.train_steps && rc == GAPA_OK; ++step) {
-                batch_kernel<<<s->cfg.batch, 256, 0, st>>>(ring, ring_fit, ring_valid, k, s->cfg.batch, s->key, step, g,
-                                                           s->stats, batch_rows, s->tbuf);
-                rc = train_step(s, batch_rows, s->cfg.batch, k, s->tbuf, st);
+                {
+                    ProfileScope prof(c, st, 2, 1);
+                    batch_kernel<<<s->cfg.batch, 256, 0, st>>>(ring, ring_resid, ring_lp, ring_valid, k, s->cfg.batch,
+                                                               s->key, step, g, s->stats, batch_rows, batch_resid,
+                                                               s->tbuf);
+                }
+                rc = train_step(s, batch_rows, s->cfg.batch, k, s->tbuf, st, batch_resid);
             }
         }
         if (cudaEventRecord(ev[(size_t)g + 1], st) != cudaSuccess) rc = gapa_fail(GAPA_ERR_CUDA, "event record");

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -38,7 +39,7 @@ EXPORTS = [
     "gapa_batch_create", "gapa_batch_destroy", "gapa_batch_set_teams", "gapa_batch_get_teams",
     "gapa_batch_autotune", "gapa_batch_run",
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
-    "gapa_surrogate_tensor", "gapa_run_surrogate",
+    "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE = 0, 1, 2, 3
 
@@ -58,6 +59,8 @@ class Profile(ctypes.Structure):
         ("fitness_launches", ctypes.c_int64),
         ("operator_launches", ctypes.c_int64),
         ("evals", ctypes.c_int64),
+        ("surrogate_ms", ctypes.c_double),
+        ("surrogate_launches", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -157,6 +160,7 @@ def load(path: str | None = None):
             "gapa_surrogate_destroy": ([V], None),
             "gapa_surrogate_predict": ([V, V, I32, I32, V], U),
             "gapa_surrogate_train_step": ([V, V, I32, I32, V, V], U),
+            "gapa_surrogate_residual": ([V, V, I32, I32, V], U),
             "gapa_surrogate_tensor": ([V, I32, I32, V, I64, I32], U),
             "gapa_run_surrogate": ([V, cfgp, V, V, V, V, V, V, V, V, I32], U),
             "gapa_profile_end": ([V, ctypes.POINTER(Profile)], U),
@@ -236,8 +240,11 @@ class Context:
         self.handle = h
         self.n = 0
         self.num_edges = 0
+        self._dependents = weakref.WeakSet()  # surrogates built on this context: closed first
 
     def close(self):
+        for dep in list(getattr(self, "_dependents", ())):
+            dep.close()
         if getattr(self, "handle", None):
             self.lib.gapa_destroy(self.handle)
             self.handle = None
@@ -435,6 +442,7 @@ class Surrogate:
         h = ctypes.c_void_p()
         _check(self.lib.gapa_surrogate_create(ctypes.byref(h), ctx.handle, ctypes.byref(scfg), seed & (2**64 - 1)))
         self.handle = h
+        ctx._dependents.add(self)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -454,6 +462,16 @@ class Surrogate:
             out = torch.empty(s, dtype=torch.float32, device=pop.device)
         _check(self.lib.gapa_surrogate_predict(self.handle, _dev_ptr(pop, torch.int32, "pop", self.ctx.device), s, k,
                                                _dev_ptr(out, torch.float32, "scores", self.ctx.device)))
+        return out
+
+    def residual(self, pop, out=None):
+        """(r0, r1) residual-degree counts of every row: int32 [rows][2] on the device."""
+        torch = _torch()
+        s, k = pop.shape
+        if out is None:
+            out = torch.empty((s, 2), dtype=torch.int32, device=pop.device)
+        _check(self.lib.gapa_surrogate_residual(self.handle, _dev_ptr(pop, torch.int32, "pop", self.ctx.device), s,
+                                                k, _dev_ptr(out, torch.int32, "counts", self.ctx.device)))
         return out
 
     def train_step(self, pop, target) -> float:

@@ -64,10 +64,10 @@ def _bf16(x):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def _bf16_model(params, pop, t, deg, num_edges):
+def _bf16_model(params, pop, t, row_ptr, col):
     """The reference formulas with BF16 roundings where the GPU stores BF16 tensors."""
     k = pop.shape[1]
-    x = _bf16(sr.features(pop, _bf16(params["E"]), deg, num_edges))
+    x = _bf16(sr.features(pop, _bf16(params["E"]), row_ptr, col))
     W1, W2 = _bf16(params["W1"]), _bf16(params["W2"])
     h1 = _bf16(np.maximum(x @ W1 + params["b1"], 0.0))
     h2 = _bf16(np.maximum(h1 @ W2 + params["b2"], 0.0))
@@ -98,12 +98,36 @@ def test_forward_matches_reference(setup):
     pop, pop_d = _batch(g, 64, 100, 1)
     y = sg.predict(pop_d).cpu().numpy()
     params = sg.params()
-    deg = sr.degrees_from_csr(g.row_ptr)
-    x = sr.features(pop, params["E"], deg, g.num_edges)
+    x = sr.features(pop, params["E"], g.row_ptr, g.col)
     want, _ = sr.forward(params, x)
     assert _rel(y, want) < 1e-1, _rel(y, want)
-    same, _ = _bf16_model(params, pop, None, deg, g.num_edges)
+    same, _ = _bf16_model(params, pop, None, g.row_ptr, g.col)
     assert _rel(y, same) < 1e-2, _rel(y, same)
+
+
+@pytest.mark.parametrize("graph", ["ba", "path", "star", "er"])
+def test_residual_counts_bit_exact(graph):
+    """r0 / r1 are integers: the GPU counts equal the reference's on random and adversarial sets."""
+    import torch
+
+    from paper_2412_20980_gb300 import Context, Surrogate, make_surrogate_config
+
+    g = {"ba": lambda: synth.ba_graph(3000, 2, 6), "path": lambda: synth.named_graph("path", 5000),
+         "star": lambda: synth.named_graph("star", 2000), "er": lambda: synth.er_graph(4000, 6000, 3)}[graph]()
+    ctx = Context(0)
+    ctx.graph_upload(g.row_ptr, g.col)
+    sg = Surrogate(ctx, make_surrogate_config(batch=16, ring=1024), seed=1)
+    rng = np.random.default_rng(2)
+    rows = [rng.choice(g.n, 300, replace=False) for _ in range(40)]
+    hubs = np.argsort(-g.degrees(), kind="stable")
+    rows.append(hubs[:300])  # the hubs: many isolated leaves
+    rows.append(np.arange(0, 600, 2)[:300])  # every other node of a prefix
+    pop = np.stack(rows).astype(np.int32)
+    got = sg.residual(torch.from_numpy(pop).cuda()).cpu().numpy()
+    want = np.array([sr.residual_degree_counts(g.row_ptr, g.col, r) for r in pop])
+    assert np.array_equal(got, want)
+    sg.close()
+    ctx.close()
 
 
 def test_gradients_and_adamw_match_reference(setup):
@@ -114,9 +138,8 @@ def test_gradients_and_adamw_match_reference(setup):
     t = np.random.default_rng(3).normal(0, 1, 64).astype(np.float32)
     before = sg.params()
     loss = sg.train_step(pop_d, torch.from_numpy(t).cuda())
-    deg = sr.degrees_from_csr(g.row_ptr)
-    want_loss, want_g, _ = sr.loss_and_grads(before, pop, t.astype(np.float64), deg, g.num_edges)
-    _, same_g = _bf16_model(before, pop, t.astype(np.float64), deg, g.num_edges)
+    want_loss, want_g, _ = sr.loss_and_grads(before, pop, t.astype(np.float64), g.row_ptr, g.col)
+    _, same_g = _bf16_model(before, pop, t.astype(np.float64), g.row_ptr, g.col)
     assert abs(loss - want_loss) <= 5e-2 * abs(want_loss)
     got_g = {name: sg.tensor(name, grad=True).astype(np.float64) for name in sr_names()}
     touched = np.unique(pop)
@@ -255,5 +278,9 @@ def test_diagnostic_pairs_recorded():
     res = run_surrogate(ctx, cfg, sg, diag_cap=2 * 128)
     assert res["diag_exact"].shape == (256,)
     assert np.all(res["diag_exact"] > 0)
+    # estimates are expm1 of a de-normalised score: finite and above -1
+    assert np.all(np.isfinite(res["diag_pred"])) and np.all(res["diag_pred"] > -1)
+    # the first diagnostic generation (g = 5) evaluates all 128 children exactly
+    assert res["exact_evals"][5] == 128 and res["exact_evals"][10] == 128 and res["exact_evals"][6] == 32
     sg.close()
     ctx.close()

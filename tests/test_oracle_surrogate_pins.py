@@ -22,8 +22,7 @@ def _setup(seed=0, n=60, k=6, B=9):
 
 def test_gradients_match_central_differences():
     g, params, pop, t = _setup()
-    deg = sr.degrees_from_csr(g.row_ptr)
-    loss, grads, _ = sr.loss_and_grads(params, pop, t, deg, g.num_edges)
+    loss, grads, _ = sr.loss_and_grads(params, pop, t, g.row_ptr, g.col)
     rng = np.random.default_rng(1)
     h = 1e-6
     for name, p in params.items():
@@ -35,26 +34,64 @@ def test_gradients_match_central_differences():
         for ix in idx:
             old = p[ix]
             p[ix] = old + h
-            lp, _, _ = sr.loss_and_grads(params, pop, t, deg, g.num_edges)
+            lp, _, _ = sr.loss_and_grads(params, pop, t, g.row_ptr, g.col)
             p[ix] = old - h
-            lm, _, _ = sr.loss_and_grads(params, pop, t, deg, g.num_edges)
+            lm, _, _ = sr.loss_and_grads(params, pop, t, g.row_ptr, g.col)
             p[ix] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - grads[name][ix]) <= 1e-6 + 1e-5 * abs(fd), (name, ix, fd, grads[name][ix])
 
 
 def test_features_closed_forms():
-    g = synth.named_graph("star", 9)
-    deg = sr.degrees_from_csr(g.row_ptr)  # centre 8, leaves 1
+    g = synth.named_graph("star", 9)  # centre 0 (degree 8), leaves 1..8
     E = np.zeros((9, sr.EMB))
     E[0, 0] = 3.0
     E[4, 1] = 2.0
-    x = sr.features(np.array([[0, 4]]), E, deg, g.num_edges)[0]
+    x = sr.features(np.array([[0, 4]]), E, g.row_ptr, g.col)[0]
     assert np.isclose(x[0], 3 / np.sqrt(2)) and np.isclose(x[1], 2 / np.sqrt(2))
     q = np.log1p([8.0, 1.0])
     assert np.isclose(x[64], q.mean()) and np.isclose(x[65], q.max())
     assert np.isclose(x[66], np.std(q)) and np.isclose(x[67], 9 / 16)
-    assert np.all(x[68:] == 0)
+    # deleting the centre isolates the 7 live leaves; none keeps exactly one live neighbour
+    assert np.isclose(x[68], np.log1p(7)) and x[69] == 0
+    assert np.all(x[70:] == 0)
+
+
+def test_residual_degree_counts_closed_forms():
+    path = synth.named_graph("path", 5)  # 0-1-2-3-4
+    assert sr.residual_degree_counts(path.row_ptr, path.col, []) == (0, 0)  # the ends were pendant already
+    assert sr.residual_degree_counts(path.row_ptr, path.col, [2]) == (0, 2)  # 1 and 3; not the ends 0 and 4
+    assert sr.residual_degree_counts(path.row_ptr, path.col, [1, 3]) == (3, 0)
+    assert sr.residual_degree_counts(path.row_ptr, path.col, [0]) == (0, 1)
+    # a node of degree 0 is never counted: it has no deleted neighbour
+    lone = synth.graphs.disjoint_union(synth.named_graph("path", 2), synth.named_graph("path", 1))
+    assert sr.residual_degree_counts(lone.row_ptr, lone.col, []) == (0, 0)
+    assert sr.residual_degree_counts(lone.row_ptr, lone.col, [0]) == (1, 0)
+    star = synth.named_graph("star", 6)  # centre 0
+    assert sr.residual_degree_counts(star.row_ptr, star.col, [1]) == (0, 0)  # the centre keeps 4 leaves
+    assert sr.residual_degree_counts(star.row_ptr, star.col, [1, 2, 3, 4]) == (0, 1)
+    assert sr.residual_degree_counts(star.row_ptr, star.col, [0]) == (5, 0)
+
+
+def test_residual_degree_counts_brute_force():
+    """Adjacency-list loops over every node on small random graphs and deletion sets."""
+    rng = np.random.default_rng(5)
+    for trial in range(30):
+        n = int(rng.integers(2, 40))
+        g = synth.er_graph(n, int(rng.integers(0, min(2 * n, n * (n - 1) // 2) + 1)), seed=trial)
+        k = int(rng.integers(0, n))
+        genes = rng.choice(n, k, replace=False)
+        dead = set(genes.tolist())
+        r0 = r1 = 0
+        for u in range(n):
+            if u in dead:
+                continue
+            nb = g.col[g.row_ptr[u]:g.row_ptr[u + 1]].tolist()
+            live = sum(1 for w in nb if w not in dead)
+            if live < len(nb):  # u has a deleted neighbour
+                r0 += int(live == 0)
+                r1 += int(live == 1)
+        assert sr.residual_degree_counts(g.row_ptr, g.col, genes) == (r0, r1)
 
 
 def test_first_adamw_step_closed_form():
