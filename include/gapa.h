@@ -196,12 +196,13 @@ int gapa_batch_run(gapa_batch* batch, int32_t gens, int64_t* best_fit, int32_t* 
  * member kept.  Input of a deletion set D of k genes (80 values):
  * (1/sqrt k) * sum of the 64-d embeddings of its genes, then the mean, maximum
  * and standard deviation of log1p(degree) over D and sum(degree)/(2E), then
- * log1p(r0) and log1p(r1), the numbers of live neighbours of D that G[V\D]
- * leaves with no live neighbour and with exactly one, then zeros.
+ * log1p(r0), log1p(r1) and log1p(r2): the numbers of live neighbours of D
+ * that G[V\D] leaves with no live neighbour and with exactly one, and the
+ * number of two-node components of G[V\D] adjacent to D; then zeros.
  * Model: 80 -> 256 ReLU -> 256 ReLU -> 1, BF16 weights on the tensor
  * cores with FP32 accumulation; FP32 master weights, AdamW (Loshchilov &
  * Hutter) on every parameter, MSE against the z-scored log1p of the exact
- * fitness.  Training is deterministic (fixed-order reductions, fixed-point
+ * fitness (over the replay ring or among siblings, see target_mode).  Training is deterministic (fixed-order reductions, fixed-point
  * embedding-gradient sums). */
 typedef struct gapa_surrogate_config {
     int32_t screened;     /* children evaluated exactly per generation once screening starts */
@@ -213,6 +214,9 @@ typedef struct gapa_surrogate_config {
     float init_scale_emb; /* embeddings start uniform in [-a, a] */
     int32_t diag_every;   /* every diag_every-th generation evaluates all children exactly and records
                              (estimate, fitness) pairs; 0 = never */
+    int32_t target_mode;  /* training target: 0 = log1p(PC) z-scored over the whole replay ring,
+                             1 = z-scored among the exactly evaluated children of the row's own
+                             generation (only the order of siblings matters for screening) */
 } gapa_surrogate_config;
 
 typedef struct gapa_surrogate gapa_surrogate;
@@ -228,8 +232,8 @@ void gapa_surrogate_destroy(gapa_surrogate* sg);
  * Genes outside [0, n) are ignored by the features. */
 int gapa_surrogate_predict(gapa_surrogate* sg, const int32_t* pop_dev, int32_t rows, int32_t k, float* scores_dev);
 
-/* Residual-degree counts of the rows of pop_dev[rows][k]: counts_dev[2r] = r0,
- * counts_dev[2r+1] = r1 (device int32 [rows][2]).  Asynchronous. */
+/* Residual counts of the rows of pop_dev[rows][k]: counts_dev[3r .. 3r+2] =
+ * (r0, r1, r2) (device int32 [rows][3]).  Asynchronous. */
 int gapa_surrogate_residual(gapa_surrogate* sg, const int32_t* pop_dev, int32_t rows, int32_t k, int32_t* counts_dev);
 
 /* One AdamW step on a minibatch (rows a multiple of 16) with device targets;

@@ -11,13 +11,15 @@ Section III-C.  Definition shared with the CUDA implementation:
     residual degrees of the live nodes u (u not in D) adjacent to D, in G[V - D]:
     r0    = #{u : some neighbour in D, no live neighbour}      (isolated by the deletion)
     r1    = #{u : some neighbour in D, exactly one live one}   (made pendant by the deletion)
-    f5    = log1p(r0),  f6 = log1p(r1)
-    x     = [e(D), f1, f2, f3, f4, f5, f6, 0 x 10]                 (80 values)
+    r2    = #{components of G[V - D] of exactly two nodes, one of them adjacent to D}
+    f5    = log1p(r0),  f6 = log1p(r1),  f7 = log1p(r2)
+    x     = [e(D), f1, f2, f3, f4, f5, f6, f7, 0 x 9]              (80 values)
 
   On sparse graphs most children of one generation share the giant
   component's size up to a few nodes that the deletion isolates, so their
-  pairwise connectivity is ordered by r0 (each isolated node removes about
-  n pairs); r1 counts the nodes one more deletion would isolate.
+  pairwise connectivity is ordered by r0 and r2 (an isolated node removes
+  about n pairs from the giant component, an isolated pair about 2n); r1
+  counts the nodes one more deletion would isolate.
   model   z1 = x W1 + b1, h1 = relu(z1)   (W1: 80 x 256)
           z2 = h1 W2 + b2, h2 = relu(z2)  (W2: 256 x 256)
           y  = h2 . w3 + b3
@@ -40,8 +42,9 @@ def degrees_from_csr(row_ptr) -> np.ndarray:
     return np.diff(np.asarray(row_ptr, dtype=np.int64)).astype(np.float64)
 
 
-def residual_degree_counts(row_ptr, col, genes) -> tuple[int, int]:
-    """(r0, r1): live nodes adjacent to the deletion set left with no live neighbour, and with exactly one."""
+def residual_degree_counts(row_ptr, col, genes) -> tuple[int, int, int]:
+    """(r0, r1, r2): live nodes adjacent to the deletion set left with no live neighbour, and with
+    exactly one; and two-node components of G[V - D] with a node adjacent to the deletion set."""
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     n = row_ptr.size - 1
     dead = np.zeros(n, dtype=bool)
@@ -53,7 +56,12 @@ def residual_degree_counts(row_ptr, col, genes) -> tuple[int, int]:
     touched = ~dead & (dead_nb > 0)
     r0 = int(np.count_nonzero(touched & (live_nb == 0)))
     r1 = int(np.count_nonzero(touched & (live_nb == 1)))
-    return r0, r1
+    # two-node components: a live arc (u, w), u < w, whose ends have exactly one live neighbour each
+    colv = np.asarray(col, dtype=np.int64)
+    arc = (owner < colv) & ~dead[owner] & ~dead[colv] & (live_nb[owner] == 1) & (live_nb[colv] == 1)
+    arc &= (dead_nb[owner] > 0) | (dead_nb[colv] > 0)
+    r2 = int(np.count_nonzero(arc))
+    return r0, r1, r2
 
 
 def features(pop: np.ndarray, E: np.ndarray, row_ptr, col) -> np.ndarray:
@@ -73,9 +81,10 @@ def features(pop: np.ndarray, E: np.ndarray, row_ptr, col) -> np.ndarray:
         x[i, 65] = qi.max()
         x[i, 66] = np.sqrt(max((qi * qi).mean() - f1 * f1, 0.0))
         x[i, 67] = deg[genes].sum() / (2.0 * num_edges)
-        r0, r1 = residual_degree_counts(row_ptr, col, genes)
+        r0, r1, r2 = residual_degree_counts(row_ptr, col, genes)
         x[i, 68] = np.log1p(r0)
         x[i, 69] = np.log1p(r1)
+        x[i, 70] = np.log1p(r2)
     return x
 
 

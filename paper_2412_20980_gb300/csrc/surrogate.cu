@@ -9,8 +9,9 @@
 //
 // Model (same definition as the fp64 reference):
 //   x  = [ (1/sqrt k) sum_{v in D} Emb[v] (64) | mean, max, std of log1p(deg)
-//          over D, sum deg / 2E | log1p(r0), log1p(r1) | 0 x 10 ]  (80)
-//   r0 / r1 = live neighbours of D left with no / exactly one live neighbour
+//          over D, sum deg / 2E | log1p(r0), log1p(r1), log1p(r2) | 0 x 9 ]  (80)
+//   r0 / r1 = live neighbours of D left with no / exactly one live neighbour,
+//   r2 = two-node components of G[V\D] adjacent to D
 //   h1 = relu(x W1 + b1) (256), h2 = relu(h1 W2 + b2) (256), y = h2 . w3 + b3
 //   target t = z-score of log1p(PC) over the replay ring; loss = mean (y-t)^2
 //   AdamW on every parameter (FP32 masters and moments).
@@ -157,9 +158,12 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs a) {
 
 // Residual degrees of each row's deletion set D: among the live nodes with a
 // neighbour in D, r0 counts those with no live neighbour left and r1 those
-// with exactly one.  Every (gene v, neighbour u) pair with u live scans N(u)
-// until a second live neighbour shows up; u is counted by the first deleted
-// node of its adjacency list, so exactly once.  The deletion bitmap sits in
+// with exactly one; r2 counts the two-node components of G[V\D] adjacent to
+// D.  Every (gene v, neighbour u) pair with u live scans N(u) until a second
+// live neighbour shows up; u is counted by the first deleted node of its
+// adjacency list, so exactly once.  A pendant u whose live neighbour w has no
+// other live neighbour closes a two-node component, counted at u when u < w
+// or when w has no deleted neighbour (degree 1), so once.  The deletion bitmap sits in
 // shared memory (ceil(n/32) words); one CTA per row.  A warp takes 32 genes
 // at a time: the (gene, neighbour) pairs of the genes of degree below 32 are
 // laid end to end and dealt out one per lane (a lane finds its gene by binary
@@ -176,34 +180,47 @@ __global__ void nbr_table_kernel(const int* __restrict__ row_ptr, const int* __r
     }
 }
 
-// (u live) -> +1 to c0 or c1 when u has at most one live neighbour and v is its first deleted one.
-// Most live u keep their first two neighbours: one 16-byte table read settles them.
-__device__ __forceinline__ void resid_pair(const unsigned* bm, const int4* __restrict__ T,
-                                           const int* __restrict__ col, int v, int u, int& c0, int& c1) {
-    if (bm_dead(bm, u)) return;
+// Live neighbours of u, counted up to two (the last one seen in *w).
+__device__ __forceinline__ int live_upto2(const unsigned* bm, const int4* __restrict__ T, const int* __restrict__ col,
+                                          int u, int* first_dead, int* w) {
     const int4 tu = __ldg(T + u);
-    if (tu.w >= 0 && !bm_dead(bm, tu.z) && !bm_dead(bm, tu.w)) return;
-    const int ub = tu.x, ue = tu.x + tu.y;
-    int live = 0, first_dead = -1;
-    for (int q = ub; q < ue; ++q) {
-        const int w = __ldg(col + q);
-        if (bm_dead(bm, w)) {
-            if (first_dead < 0) first_dead = w;
-        } else if (++live >= 2) {
-            return;
+    if (tu.w >= 0 && !bm_dead(bm, tu.z) && !bm_dead(bm, tu.w)) return 2;
+    int live = 0;
+    for (int q = tu.x; q < tu.x + tu.y; ++q) {
+        const int x = __ldg(col + q);
+        if (bm_dead(bm, x)) {
+            if (first_dead && *first_dead < 0) *first_dead = x;
+        } else {
+            *w = x;
+            if (++live >= 2) return 2;
         }
     }
-    if (first_dead == v) {
-        c0 += live == 0;
-        c1 += live == 1;
+    return live;
+}
+
+// (u live) -> +1 to c0 or c1 when u has at most one live neighbour and v is its
+// first deleted one; +1 to c2 when that neighbour closes a two-node component.
+// Most live u keep their first two neighbours: one 16-byte table read settles them.
+__device__ __forceinline__ void resid_pair(const unsigned* bm, const int4* __restrict__ T,
+                                           const int* __restrict__ col, int v, int u, int& c0, int& c1, int& c2) {
+    if (bm_dead(bm, u)) return;
+    int first_dead = -1, w = -1;
+    const int live = live_upto2(bm, T, col, u, &first_dead, &w);
+    if (live >= 2 || first_dead != v) return;
+    c0 += live == 0;
+    if (live == 1) {
+        c1 += 1;
+        int wl = -1;
+        const int4 tw = __ldg(T + w);
+        if ((u < w || tw.y == 1) && live_upto2(bm, T, col, w, nullptr, &wl) == 1) c2 += 1;
     }
 }
 
 __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop, int rows, int k, int n,
                                                     const int4* __restrict__ T, const int* __restrict__ col,
-                                                    int2* __restrict__ out) {
+                                                    int4* __restrict__ out) {
     extern __shared__ unsigned bm[];
-    __shared__ int red[2][8];
+    __shared__ int red[3][8];
     const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (r >= rows) return;
     const int words = (n + 31) >> 5;
@@ -215,7 +232,7 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
         if (v >= 0 && v < n) atomicOr(&bm[v >> 5], 1u << (v & 31));
     }
     __syncthreads();
-    int c0 = 0, c1 = 0;
+    int c0 = 0, c1 = 0, c2 = 0;
     const int nwarps = blockDim.x >> 5;
     for (int j0 = warp * 32; j0 < k; j0 += nwarps * 32) {
         const int j = j0 + lane;
@@ -249,7 +266,7 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
             }
             const int ov = __shfl_sync(0xffffffffu, v, lo), ob = __shfl_sync(0xffffffffu, b, lo),
                       oi = __shfl_sync(0xffffffffu, incl, lo), od = __shfl_sync(0xffffffffu, d, lo);
-            if (idx < total) resid_pair(bm, T, col, ov, __ldg(col + ob + (idx - (oi - od))), c0, c1);
+            if (idx < total) resid_pair(bm, T, col, ov, __ldg(col + ob + (idx - (oi - od))), c0, c1, c2);
         }
         unsigned many = __ballot_sync(0xffffffffu, big);
         while (many) {
@@ -257,25 +274,28 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
             many &= many - 1;
             const int vb = __shfl_sync(0xffffffffu, v, src), bb = __shfl_sync(0xffffffffu, b, src),
                       eb = __shfl_sync(0xffffffffu, e, src);
-            for (int p = bb + lane; p < eb; p += 32) resid_pair(bm, T, col, vb, __ldg(col + p), c0, c1);
+            for (int p = bb + lane; p < eb; p += 32) resid_pair(bm, T, col, vb, __ldg(col + p), c0, c1, c2);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         c0 += __shfl_down_sync(0xffffffffu, c0, o);
         c1 += __shfl_down_sync(0xffffffffu, c1, o);
+        c2 += __shfl_down_sync(0xffffffffu, c2, o);
     }
     if (lane == 0) {
         red[0][warp] = c0;
         red[1][warp] = c1;
+        red[2][warp] = c2;
     }
     __syncthreads();
     if (t == 0) {
-        int x = 0, y = 0;
+        int x = 0, y = 0, z = 0;
         for (int w = 0; w < nwarps; ++w) {
             x += red[0][w];
             y += red[1][w];
+            z += red[2][w];
         }
-        out[r] = make_int2(x, y);
+        out[r] = make_int4(x, y, z, 0);
     }
 }
 
@@ -285,7 +305,7 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
 __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ pop, int rows, int k, int n,
                                                        const bf16* __restrict__ Eb, const float* __restrict__ logdeg,
                                                        const float* __restrict__ deg, float inv2E, float invsqrtk,
-                                                       const int2* __restrict__ resid, bf16* __restrict__ X,
+                                                       const int4* __restrict__ resid, bf16* __restrict__ X,
                                                        bf16* __restrict__ XT, int rows_pad) {
     __shared__ float2 part[4][32];
     __shared__ float st[4][4];
@@ -370,6 +390,7 @@ __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ p
         if (t == 67) f = DS * inv2E;
         if (t == 68) f = log1pf((float)resid[r].x);
         if (t == 69) f = log1pf((float)resid[r].y);
+        if (t == 70) f = log1pf((float)resid[r].z);
         X[(size_t)r * kIn + t] = __float2bfloat16(f);
         XT[(size_t)t * rows_pad + r] = __float2bfloat16(f);
     }
@@ -575,8 +596,8 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ sc
 
 // dst row r = src row idx[r] (idx may be null: identity), k genes, with its
 // residual-degree counts; dst_cap > 0 writes ring slots (dst_first + r) mod dst_cap.
-__global__ void gather_rows_kernel(const int* __restrict__ src, const int2* __restrict__ rsrc,
-                                   const int* __restrict__ idx, int k, int* __restrict__ dst, int2* __restrict__ rdst,
+__global__ void gather_rows_kernel(const int* __restrict__ src, const int4* __restrict__ rsrc,
+                                   const int* __restrict__ idx, int k, int* __restrict__ dst, int4* __restrict__ rdst,
                                    int dst_first, int dst_cap) {
     const int r = blockIdx.x;
     const int from = idx ? idx[r] : r;
@@ -593,11 +614,40 @@ __global__ void scatter_fit_kernel(const long long* __restrict__ fsel, const int
     for (int r = threadIdx.x; r < m; r += blockDim.x) kfit[sel[r]] = fsel[r];
 }
 
-// Ring append: log1p of each exact fitness (FP64), the training target before normalisation.
-__global__ void ring_fit_kernel(const int64_t* __restrict__ f, const int* __restrict__ idx, int cnt,
-                                double* __restrict__ ring_lp, int first, int cap) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x)
-        ring_lp[(first + r) % cap] = log1p((double)f[idx ? idx[r] : r]);
+// Ring append of one generation's exactly evaluated rows (one CTA, FP64,
+// fixed-order reductions): l = log1p(fitness); gstats = (mean, std) of l over
+// these rows; the ring keeps l (target mode 0: normalised later over the whole
+// ring) or (l - mean) / std (mode 1: z-score among the row's siblings).
+__global__ void __launch_bounds__(1024) ring_target_kernel(const int64_t* __restrict__ f, int cnt, int mode,
+                                                           double* __restrict__ ring_lp, int first, int cap,
+                                                           double* __restrict__ gstats) {
+    __shared__ double s1[1024], s2[1024];
+    double a = 0, b = 0;
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+        const double l = log1p((double)f[r]);
+        a += l;
+        b += l * l;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    const double mu = s1[0] / cnt, var = s2[0] / cnt - mu * mu;
+    const double sd = var > 1e-24 ? sqrt(var) : 1.0;
+    if (threadIdx.x == 0) {
+        gstats[0] = mu;
+        gstats[1] = sd;
+    }
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+        const double l = log1p((double)f[r]);
+        ring_lp[(first + r) % cap] = mode == 1 ? (l - mu) / sd : l;
+    }
 }
 
 // Mean and standard deviation of log1p(fitness) over the ring (one CTA, FP64,
@@ -631,10 +681,10 @@ __global__ void __launch_bounds__(1024) target_stats_kernel(const double* __rest
 
 // Minibatch: rows drawn uniformly from the valid ring entries (Philox tag 8,
 // counter (b, step, g, 8 << 24 | 1)), targets z-scored.
-__global__ void batch_kernel(const int* __restrict__ ring, const int2* __restrict__ ring_resid,
+__global__ void batch_kernel(const int* __restrict__ ring, const int4* __restrict__ ring_resid,
                              const double* __restrict__ ring_lp, int valid, int k, int B, RngKey key, int step,
                              int g, const double* __restrict__ stats, int* __restrict__ rows,
-                             int2* __restrict__ resid, float* __restrict__ t) {
+                             int4* __restrict__ resid, float* __restrict__ t) {
     const int b = blockIdx.x;
     const int idx = uniform_below(philox_word0((uint32_t)b, (uint32_t)step, (uint32_t)g, (8u << 24) | 1u, key.lo, key.hi),
                                   valid);
@@ -674,7 +724,7 @@ struct gapa_surrogate {
     bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
          *dZ1 = nullptr, *dZ1T = nullptr;
     float *y = nullptr, *dy = nullptr, *dX = nullptr, *loss = nullptr, *tbuf = nullptr;
-    int2* resid = nullptr;       // residual-degree counts of the rows of the last forward
+    int4* resid = nullptr;       // residual-degree counts of the rows of the last forward
     int4* nbr = nullptr;         // per node: first arc, degree, first two neighbours
     const int* row_ptr = nullptr;  // the context's CSR (original node ids)
     const int* col = nullptr;
@@ -729,7 +779,7 @@ int compute_resid(gapa_surrogate* s, const int32_t* pop, int rows, int k, cudaSt
 // Features + forward; keeps the transposed copies for a training step.  With
 // resid == nullptr the residual-degree counts are computed into s->resid first.
 int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, cudaStream_t st,
-            const int2* resid = nullptr) {
+            const int4* resid = nullptr) {
     if (!resid) {
         int rc = compute_resid(s, pop, rows, k, st);
         if (rc != GAPA_OK) return rc;
@@ -764,7 +814,7 @@ int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, c
 
 // One AdamW step on a batch (rows a multiple of 16) with targets t.
 int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float* t, cudaStream_t st,
-               const int2* resid = nullptr) {
+               const int4* resid = nullptr) {
     int rc = forward(s, pop, B, k, true, st, resid);
     if (rc != GAPA_OK) return rc;
     ProfileScope prof(s->ctx, st, 2, 13);
@@ -835,7 +885,7 @@ int ensure_rows(gapa_surrogate* s, int rows) {
         cudaMalloc(&s->H1T, e256 * 2) || cudaMalloc(&s->H2, e256 * 2) || cudaMalloc(&s->dZ2, e256 * 2) ||
         cudaMalloc(&s->dZ2T, e256 * 2) || cudaMalloc(&s->dZ1, e256 * 2) || cudaMalloc(&s->dZ1T, e256 * 2) ||
         cudaMalloc(&s->y, (size_t)R * 4) || cudaMalloc(&s->dy, (size_t)R * 4) || cudaMalloc(&s->dX, e80 * 4) ||
-        cudaMalloc(&s->tbuf, (size_t)R * 4) || cudaMalloc(&s->resid, (size_t)R * sizeof(int2))) {
+        cudaMalloc(&s->tbuf, (size_t)R * 4) || cudaMalloc(&s->resid, (size_t)R * sizeof(int4))) {
         cudaGetLastError();
         return gapa_fail(GAPA_ERR_OOM, "surrogate activations for %d rows", R);
     }
@@ -866,7 +916,8 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
     *out = nullptr;
     if (ctx->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "no graph uploaded");
     if (scfg->batch < 16 || scfg->batch % 16 || scfg->ring < scfg->batch || scfg->train_steps < 0 ||
-        scfg->screened < 1 || scfg->warmup < 0 || !(scfg->lr > 0.f))
+        scfg->screened < 1 || scfg->warmup < 0 || !(scfg->lr > 0.f) || scfg->target_mode < 0 ||
+        scfg->target_mode > 1)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "invalid surrogate configuration");
     cudaSetDevice(ctx->device);
     gapa_surrogate* s = new gapa_surrogate();
@@ -962,6 +1013,7 @@ int gapa_surrogate_predict(gapa_surrogate* s, const int32_t* pop_dev, int32_t ro
 }
 
 int gapa_surrogate_residual(gapa_surrogate* s, const int32_t* pop_dev, int32_t rows, int32_t k, int32_t* counts_dev) {
+    // counts_dev: [rows][3] (the kernel's rows carry a fourth, unused lane)
     if (!s || rows < 0 || k < 0 || (rows > 0 && (!pop_dev || !counts_dev)))
         return gapa_fail(GAPA_ERR_INVALID_ARG, "bad residual arguments");
     if (rows == 0) return GAPA_OK;
@@ -970,8 +1022,8 @@ int gapa_surrogate_residual(gapa_surrogate* s, const int32_t* pop_dev, int32_t r
     if (rc == GAPA_OK) rc = ensure_rows(s, rows);
     if (rc == GAPA_OK) rc = compute_resid(s, pop_dev, rows, k, s->ctx->stream);
     if (rc != GAPA_OK) return rc;
-    GAPA_CUDA(cudaMemcpyAsync(counts_dev, s->resid, (size_t)rows * sizeof(int2), cudaMemcpyDeviceToDevice,
-                              s->ctx->stream));
+    GAPA_CUDA(cudaMemcpy2DAsync(counts_dev, 3 * sizeof(int32_t), s->resid, sizeof(int4), 3 * sizeof(int32_t),
+                                (size_t)rows, cudaMemcpyDeviceToDevice, s->ctx->stream));
     return GAPA_OK;
 }
 
@@ -1040,8 +1092,9 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     // surrogate buffers
     int32_t *ring = nullptr, *sel = nullptr, *sel_rows = nullptr, *batch_rows = nullptr;
     int64_t* fsel = nullptr;
-    double* ring_lp = nullptr;  // log1p(exact fitness) of every ring row
-    int2 *ring_resid = nullptr, *sel_resid = nullptr, *batch_resid = nullptr;
+    double* ring_lp = nullptr;  // log1p(exact fitness) of every ring row (mode 1: its sibling z-score)
+    double* gstats = nullptr;   // (mean, std) of log1p(fitness) over the last appended generation
+    int4 *ring_resid = nullptr, *sel_resid = nullptr, *batch_resid = nullptr;
     float* scores = nullptr;
     const int ring_cap = s ? s->cfg.ring : 0;
     auto cleanup = [&]() {
@@ -1050,6 +1103,7 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
         cudaFree(sel_rows);
         cudaFree(batch_rows);
         cudaFree(ring_lp);
+        cudaFree(gstats);
         cudaFree(fsel);
         cudaFree(scores);
         cudaFree(ring_resid);
@@ -1058,11 +1112,11 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     };
     if (cudaMalloc(&sel, (size_t)lam * 4) || cudaMalloc(&sel_rows, (size_t)lam * k * 4 + 4) ||
         cudaMalloc(&fsel, (size_t)lam * 8) || cudaMalloc(&scores, (size_t)lam * 4) ||
-        (s && (cudaMalloc(&ring, (size_t)ring_cap * k * 4 + 4) || cudaMalloc(&ring_lp, (size_t)ring_cap * 8) ||
+        (s && (cudaMalloc(&ring, (size_t)ring_cap * k * 4 + 4) || cudaMalloc(&ring_lp, (size_t)ring_cap * 8) || cudaMalloc(&gstats, 16) ||
                cudaMalloc(&batch_rows, (size_t)s->cfg.batch * k * 4 + 4) ||
-               cudaMalloc(&ring_resid, (size_t)ring_cap * sizeof(int2)) ||
-               cudaMalloc(&sel_resid, (size_t)lam * sizeof(int2)) ||
-               cudaMalloc(&batch_resid, (size_t)s->cfg.batch * sizeof(int2))))) {
+               cudaMalloc(&ring_resid, (size_t)ring_cap * sizeof(int4)) ||
+               cudaMalloc(&sel_resid, (size_t)lam * sizeof(int4)) ||
+               cudaMalloc(&batch_resid, (size_t)s->cfg.batch * sizeof(int4))))) {
         cudaGetLastError();
         cleanup();
         return gapa_fail(GAPA_ERR_OOM, "surrogate run buffers");
@@ -1096,7 +1150,7 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     if (s) {  // the initial population enters the ring
         if ((rc = compute_resid(s, P[0], mu, k, st)) != GAPA_OK) return fail(rc);
         gather_rows_kernel<<<mu, 256, 0, st>>>(P[0], s->resid, nullptr, k, ring, ring_resid, ring_pos, ring_cap);
-        ring_fit_kernel<<<(mu + 255) / 256, 256, 0, st>>>(F[0], nullptr, mu, ring_lp, ring_pos, ring_cap);
+        ring_target_kernel<<<1, 1024, 0, st>>>(F[0], mu, s->cfg.target_mode, ring_lp, ring_pos, ring_cap, gstats);
         ring_pos = (ring_pos + mu) % ring_cap;
         ring_valid = std::min(ring_cap, ring_valid + mu);
     }
@@ -1131,14 +1185,6 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
             evaluated = screened;
         } else if (rc == GAPA_OK) {
             rc = gapa_launch_fitness(c, c->kids, lam, k, c->kfit, st);
-            if (rc == GAPA_OK && diag) {
-                // diagnostic generation: every child is evaluated exactly (and used by the
-                // truncation), and the (estimate, fitness) pairs are recorded
-                decode_kernel<<<(lam + 255) / 256, 256, 0, st>>>(s->y, lam, s->stats, scores);
-                GAPA_CUDA(cudaMemcpyAsync(diag_pred_host + diag_rows, scores, (size_t)lam * 4, cudaMemcpyDeviceToHost, st));
-                GAPA_CUDA(cudaMemcpyAsync(diag_exact_host + diag_rows, c->kfit, (size_t)lam * 8, cudaMemcpyDeviceToHost, st));
-                diag_rows += lam;
-            }
         }
         if (rc != GAPA_OK) break;
         exact[g] = evaluated;
@@ -1147,22 +1193,33 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
             if (evaluated == lam) {
                 gather_rows_kernel<<<lam, 256, 0, st>>>(c->kids, s->resid, nullptr, k, ring, ring_resid, ring_pos,
                                                         ring_cap);
-                ring_fit_kernel<<<(lam + 255) / 256, 256, 0, st>>>(c->kfit, nullptr, lam, ring_lp, ring_pos, ring_cap);
+                ring_target_kernel<<<1, 1024, 0, st>>>(c->kfit, lam, s->cfg.target_mode, ring_lp, ring_pos, ring_cap,
+                                                       gstats);
             } else {
                 gather_rows_kernel<<<evaluated, 256, 0, st>>>(sel_rows, sel_resid, nullptr, k, ring, ring_resid,
                                                               ring_pos, ring_cap);
-                ring_fit_kernel<<<(evaluated + 255) / 256, 256, 0, st>>>(fsel, nullptr, evaluated, ring_lp, ring_pos,
-                                                                        ring_cap);
+                ring_target_kernel<<<1, 1024, 0, st>>>(fsel, evaluated, s->cfg.target_mode, ring_lp, ring_pos,
+                                                       ring_cap, gstats);
             }
             ring_pos = (ring_pos + evaluated) % ring_cap;
             ring_valid = std::min(ring_cap, ring_valid + evaluated);
+        }
+        if (diag) {
+            // diagnostic generation: every child was evaluated exactly (and is used by the
+            // truncation); record (estimate, fitness) pairs.  In target mode 1 the estimate
+            // de-normalises with the statistics of this generation's children.
+            decode_kernel<<<(lam + 255) / 256, 256, 0, st>>>(s->y, lam, s->cfg.target_mode == 1 ? gstats : s->stats,
+                                                             scores);
+            GAPA_CUDA(cudaMemcpyAsync(diag_pred_host + diag_rows, scores, (size_t)lam * 4, cudaMemcpyDeviceToHost, st));
+            GAPA_CUDA(cudaMemcpyAsync(diag_exact_host + diag_rows, c->kfit, (size_t)lam * 8, cudaMemcpyDeviceToHost, st));
+            diag_rows += lam;
         }
         rc = gapa_launch_mpl_replace(c, mu, lam, k, P[cur], F[cur], c->kids, c->kfit, c->src, P[cur ^ 1], F[cur ^ 1], st);
         if (rc == GAPA_OK) rc = gapa_launch_record(c, F[cur ^ 1], mu, c->run_gen, c->run_traj, c->run_best, st);
         cur ^= 1;
         // online training on the ring
         if (rc == GAPA_OK && s && ring_valid >= s->cfg.batch && s->cfg.train_steps > 0) {
-            {
+            if (s->cfg.target_mode == 0) {  // mode 1 keeps the identity statistics
                 ProfileScope prof(c, st, 2, 1);
                 target_stats_kernel<<<1, 1024, 0, st>>>(ring_lp, ring_valid, s->stats);
             }

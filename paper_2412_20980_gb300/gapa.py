@@ -83,13 +83,14 @@ class SurrogateConfig(ctypes.Structure):
         ("eps", ctypes.c_float),
         ("init_scale_emb", ctypes.c_float),
         ("diag_every", ctypes.c_int32),
+        ("target_mode", ctypes.c_int32),
     ]
 
 
 def make_surrogate_config(screened=512, warmup=3, train_steps=4, batch=512, ring=16384, lr=1e-3, beta1=0.9,
-                          beta2=0.999, weight_decay=0.01, eps=1e-8, init_scale_emb=0.1, diag_every=0):
+                          beta2=0.999, weight_decay=0.01, eps=1e-8, init_scale_emb=0.1, diag_every=0, target_mode=0):
     return SurrogateConfig(screened, warmup, train_steps, batch, ring, lr, beta1, beta2, weight_decay, eps,
-                           init_scale_emb, diag_every)
+                           init_scale_emb, diag_every, target_mode)
 
 
 class Config(ctypes.Structure):
@@ -465,11 +466,11 @@ class Surrogate:
         return out
 
     def residual(self, pop, out=None):
-        """(r0, r1) residual-degree counts of every row: int32 [rows][2] on the device."""
+        """(r0, r1, r2) residual counts of every row: int32 [rows][3] on the device."""
         torch = _torch()
         s, k = pop.shape
         if out is None:
-            out = torch.empty((s, 2), dtype=torch.int32, device=pop.device)
+            out = torch.empty((s, 3), dtype=torch.int32, device=pop.device)
         _check(self.lib.gapa_surrogate_residual(self.handle, _dev_ptr(pop, torch.int32, "pop", self.ctx.device), s,
                                                 k, _dev_ptr(out, torch.int32, "counts", self.ctx.device)))
         return out

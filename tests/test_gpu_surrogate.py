@@ -107,7 +107,7 @@ def test_forward_matches_reference(setup):
 
 @pytest.mark.parametrize("graph", ["ba", "path", "star", "er"])
 def test_residual_counts_bit_exact(graph):
-    """r0 / r1 are integers: the GPU counts equal the reference's on random and adversarial sets."""
+    """r0 / r1 / r2 are integers: the GPU counts equal the reference's on random and adversarial sets."""
     import torch
 
     from paper_2412_20980_gb300 import Context, Surrogate, make_surrogate_config
@@ -122,6 +122,7 @@ def test_residual_counts_bit_exact(graph):
     hubs = np.argsort(-g.degrees(), kind="stable")
     rows.append(hubs[:300])  # the hubs: many isolated leaves
     rows.append(np.arange(0, 600, 2)[:300])  # every other node of a prefix
+    rows.append(np.arange(0, 900, 3)[:300])  # every third node: isolated pairs on a path
     pop = np.stack(rows).astype(np.int32)
     got = sg.residual(torch.from_numpy(pop).cuda()).cpu().numpy()
     want = np.array([sr.residual_degree_counts(g.row_ptr, g.col, r) for r in pop])

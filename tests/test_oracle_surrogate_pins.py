@@ -53,24 +53,24 @@ def test_features_closed_forms():
     assert np.isclose(x[64], q.mean()) and np.isclose(x[65], q.max())
     assert np.isclose(x[66], np.std(q)) and np.isclose(x[67], 9 / 16)
     # deleting the centre isolates the 7 live leaves; none keeps exactly one live neighbour
-    assert np.isclose(x[68], np.log1p(7)) and x[69] == 0
-    assert np.all(x[70:] == 0)
+    assert np.isclose(x[68], np.log1p(7)) and x[69] == 0 and x[70] == 0
+    assert np.all(x[71:] == 0)
 
 
 def test_residual_degree_counts_closed_forms():
     path = synth.named_graph("path", 5)  # 0-1-2-3-4
-    assert sr.residual_degree_counts(path.row_ptr, path.col, []) == (0, 0)  # the ends were pendant already
-    assert sr.residual_degree_counts(path.row_ptr, path.col, [2]) == (0, 2)  # 1 and 3; not the ends 0 and 4
-    assert sr.residual_degree_counts(path.row_ptr, path.col, [1, 3]) == (3, 0)
-    assert sr.residual_degree_counts(path.row_ptr, path.col, [0]) == (0, 1)
+    assert sr.residual_degree_counts(path.row_ptr, path.col, []) == (0, 0, 0)  # the ends were pendant already
+    assert sr.residual_degree_counts(path.row_ptr, path.col, [2]) == (0, 2, 2)  # 1 and 3; the pairs {0,1} and {3,4}
+    assert sr.residual_degree_counts(path.row_ptr, path.col, [1, 3]) == (3, 0, 0)
+    assert sr.residual_degree_counts(path.row_ptr, path.col, [0]) == (0, 1, 0)
     # a node of degree 0 is never counted: it has no deleted neighbour
     lone = synth.graphs.disjoint_union(synth.named_graph("path", 2), synth.named_graph("path", 1))
-    assert sr.residual_degree_counts(lone.row_ptr, lone.col, []) == (0, 0)
-    assert sr.residual_degree_counts(lone.row_ptr, lone.col, [0]) == (1, 0)
+    assert sr.residual_degree_counts(lone.row_ptr, lone.col, []) == (0, 0, 0)
+    assert sr.residual_degree_counts(lone.row_ptr, lone.col, [0]) == (1, 0, 0)
     star = synth.named_graph("star", 6)  # centre 0
-    assert sr.residual_degree_counts(star.row_ptr, star.col, [1]) == (0, 0)  # the centre keeps 4 leaves
-    assert sr.residual_degree_counts(star.row_ptr, star.col, [1, 2, 3, 4]) == (0, 1)
-    assert sr.residual_degree_counts(star.row_ptr, star.col, [0]) == (5, 0)
+    assert sr.residual_degree_counts(star.row_ptr, star.col, [1]) == (0, 0, 0)  # the centre keeps 4 leaves
+    assert sr.residual_degree_counts(star.row_ptr, star.col, [1, 2, 3, 4]) == (0, 1, 1)  # {0, 5} is left
+    assert sr.residual_degree_counts(star.row_ptr, star.col, [0]) == (5, 0, 0)
 
 
 def test_residual_degree_counts_brute_force():
@@ -91,7 +91,24 @@ def test_residual_degree_counts_brute_force():
             if live < len(nb):  # u has a deleted neighbour
                 r0 += int(live == 0)
                 r1 += int(live == 1)
-        assert sr.residual_degree_counts(g.row_ptr, g.col, genes) == (r0, r1)
+        # two-node components by a BFS over the live graph
+        seen, r2 = set(), 0
+        for u in range(n):
+            if u in dead or u in seen:
+                continue
+            comp, stack = [], [u]
+            seen.add(u)
+            while stack:
+                x = stack.pop()
+                comp.append(x)
+                for w in g.col[g.row_ptr[x]:g.row_ptr[x + 1]].tolist():
+                    if w not in dead and w not in seen:
+                        seen.add(w)
+                        stack.append(w)
+            if len(comp) == 2:
+                touches = any(w in dead for x in comp for w in g.col[g.row_ptr[x]:g.row_ptr[x + 1]].tolist())
+                r2 += int(touches)
+        assert sr.residual_degree_counts(g.row_ptr, g.col, genes) == (r0, r1, r2)
 
 
 def test_first_adamw_step_closed_form():
