@@ -298,6 +298,7 @@ def run_gapa(args):
 
     from paper_2412_20980_gb300 import Context, make_config
     from paper_2412_20980_gb300 import build as b
+    from paper_2412_20980_gb300 import dist as gd
 
     wl = args.workload
     w = WORKLOADS[wl]
@@ -319,7 +320,7 @@ def run_gapa(args):
     if wl == "surrogate":
         return run_surrogate_bench(args, gs, dist, ws, rank, local, dev)
     k, pop = w["k"], w["pop"]
-    cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=PC, pm=PM, seed=rank)
+    cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=PC, pm=PM, seed=gd.rank_seed(0, rank))
     ctxs, state = [], []
     for g in gs:
         c = Context(local)
@@ -367,11 +368,7 @@ def run_gapa(args):
         dist.barrier()
     profs = [c.profile_end() for c in ctxs]
     clocks = sampler.stop()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    total_ms = gd.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device=dev)
     for c in ctxs:
         c.sync()
     value = units * ws / (total_ms / 1000.0)

@@ -145,6 +145,17 @@ int gapa_generation(gapa_ctx* ctx, const gapa_config* cfg, int32_t g, const int3
 int gapa_generation_host(gapa_ctx* ctx, const gapa_config* cfg, int32_t g, const int32_t* pop_in_host,
                          const int64_t* fit_in_host, int32_t* pop_out_host, int64_t* fit_out_host);
 
+/* The operators of one generation without the children's fitness (elitism
+ * mode only; GAPA_ERR_INVALID_ARG with GAPA_FLAG_MU_PLUS_LAMBDA): writes
+ * pop_out[s][k] and fit_out[0] (the elite's carried fitness) exactly as
+ * gapa_generation does; fit_out[1..s-1] are left to gapa_fitness on
+ * pop_out + k.  Because every draw is counter-based, several processes that
+ * call this with the same inputs produce the same children and can each
+ * evaluate a slice of them (the member partition of Section III-D) and
+ * exchange the int64 fitness.  Asynchronous. */
+int gapa_offspring(gapa_ctx* ctx, const gapa_config* cfg, int32_t g, const int32_t* pop_in, const int64_t* fit_in,
+                   int32_t* pop_out, int64_t* fit_out);
+
 /* A whole run: initialisation, fitness, then cfg->gens generations, each one
  * replayed from a captured CUDA graph with the generation counter kept on
  * the device.  Outputs: best_set_host[k] = genes of the final best member

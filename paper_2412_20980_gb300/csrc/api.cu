@@ -583,6 +583,28 @@ int gapa_generation(gapa_ctx* c, const gapa_config* cfg, int32_t g, const int32_
                               c->stream);
 }
 
+int gapa_offspring(gapa_ctx* c, const gapa_config* cfg, int32_t g, const int32_t* pop_in, const int64_t* fit_in,
+                   int32_t* pop_out, int64_t* fit_out) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_cfg(c, cfg);
+    if (rc != GAPA_OK) return rc;
+    if (cfg->flags & GAPA_FLAG_MU_PLUS_LAMBDA)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "gapa_offspring covers the elitism mode only");
+    if (g < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "generation index must be >= 1 (got %d)", g);
+    if (!fit_in || !fit_out || (cfg->k > 0 && (!pop_in || !pop_out)))
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL pointer");
+    if (pop_in == pop_out || fit_in == fit_out) return gapa_fail(GAPA_ERR_INVALID_ARG, "outputs alias inputs");
+    DeviceGuard guard(c->device);
+    GaParams p = make_params(c, cfg, g, nullptr);
+    if (p.flags & GAPA_FLAG_ROULETTE) {
+        rc = gapa_reserve((void**)&c->cum, &c->cum_cap, (size_t)cfg->pop, sizeof(int64_t));
+        if (rc == GAPA_OK) rc = gapa_launch_roulette_prefix(fit_in, p.s, c->cum, c->stream);
+        if (rc != GAPA_OK) return rc;
+        p.cum = reinterpret_cast<const long long*>(c->cum);
+    }
+    return gapa_launch_offspring(c, p, pop_in, fit_in, pop_out, fit_out, c->stream);
+}
+
 int gapa_generation_host(gapa_ctx* c, const gapa_config* cfg, int32_t g, const int32_t* pop_in_host,
                          const int64_t* fit_in_host, int32_t* pop_out_host, int64_t* fit_out_host) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");

@@ -39,7 +39,7 @@ EXPORTS = [
     "gapa_batch_create", "gapa_batch_destroy", "gapa_batch_set_teams", "gapa_batch_get_teams",
     "gapa_batch_autotune", "gapa_batch_run",
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
-    "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual",
+    "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual", "gapa_offspring",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE = 0, 1, 2, 3
 
@@ -146,6 +146,7 @@ def load(path: str | None = None):
             "gapa_fitness_host": ([V, V, I32, I32, V], U),
             "gapa_generation": ([V, cfgp, I32, V, V, V, V], U),
             "gapa_generation_host": ([V, cfgp, I32, V, V, V, V], U),
+            "gapa_offspring": ([V, cfgp, I32, V, V, V, V], U),
             "gapa_run": ([V, cfgp, V, V, V, V], U),
             "gapa_sync": ([V], U),
             "gapa_profile_begin": ([V], U),
@@ -324,6 +325,16 @@ class Context:
                                         _dev_ptr(fit_in, torch.int64, "fit_in", self.device),
                                         _dev_ptr(pop_out, torch.int32, "pop_out", self.device),
                                         _dev_ptr(fit_out, torch.int64, "fit_out", self.device)))
+        return pop_out, fit_out
+
+    def offspring(self, cfg: Config, g: int, pop_in, fit_in, pop_out, fit_out):
+        """gapa_offspring: the operators of generation g; fit_out[1:] is left for fitness()."""
+        torch = _torch()
+        _check(self.lib.gapa_offspring(self.handle, ctypes.byref(cfg), g,
+                                       _dev_ptr(pop_in, torch.int32, "pop_in", self.device),
+                                       _dev_ptr(fit_in, torch.int64, "fit_in", self.device),
+                                       _dev_ptr(pop_out, torch.int32, "pop_out", self.device),
+                                       _dev_ptr(fit_out, torch.int64, "fit_out", self.device)))
         return pop_out, fit_out
 
     def generation_host(self, cfg: Config, g: int, pop_in: np.ndarray, fit_in: np.ndarray,

@@ -173,3 +173,28 @@ def test_variant_configs_rejected(ctx):
                dict(k=5, pop=10000, flags=MPL, lam=7000)):
         with pytest.raises(GapaError):
             ctx.pop_init(_cfg(**kw), out=out)
+
+
+@pytest.mark.parametrize("flags", [0, 4])
+def test_offspring_plus_sliced_fitness_equals_generation(ctx, flags):
+    """The member split of one population: operators once, fitness by slices (two simulated ranks)."""
+    import torch
+
+    from paper_2412_20980_gb300 import GapaError
+    from paper_2412_20980_gb300 import dist as gd
+
+    g = synth.ba_graph(3000, 3, 5)
+    ctx.graph_upload(g.row_ptr, g.col)
+    cfg = _cfg(k=150, pop=77, tourn=2, pc=0.8, pm=0.03, seed=4, flags=flags)
+    pop = ctx.pop_init(cfg)
+    fit = ctx.fitness(pop)
+    want_p, want_f = ctx.generation(cfg, 3, pop, fit)
+    p2, f2 = torch.empty_like(pop), torch.full_like(fit, -7)
+    ctx.offspring(cfg, 3, pop, fit, p2, f2)
+    for r in range(2):
+        lo, hi = gd.shard_bounds(cfg.pop - 1, 2, r)
+        ctx.fitness(p2[1 + lo:1 + hi], out=f2[1 + lo:1 + hi])
+    ctx.sync()
+    assert torch.equal(p2, want_p) and torch.equal(f2, want_f)
+    with pytest.raises(GapaError):
+        ctx.offspring(_cfg(k=150, pop=77, seed=4, flags=2, lam=64), 3, pop, fit, p2, f2)
