@@ -277,15 +277,22 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
 
 /* Fitness kernel selection (all are exact and give identical results):
  * TREE starts every member from a BFS spanning forest of G (numbered so that
- * parents precede children), cuts it at the deleted nodes and then joins the
- * pieces along the non-tree edges; SAMPLED joins every live node to its first
- * two live neighbours, takes the tree of the highest-degree live node as the
- * giant tree and lets only nodes outside it scan their whole adjacency; EDGES
- * runs union-find over every undirected edge.  AUTO (the default) is TREE. */
+ * parents precede children), cuts it at the deleted nodes, reattaches each
+ * piece to a live lower-numbered neighbour where it can, and then joins what
+ * is left: per member it either lets the nodes outside the piece of the
+ * first live node scan their adjacency (when their adjacency is shorter than
+ * the list of non-tree edges) or unites along every non-tree edge.
+ * TREE_JOIN and TREE_SCAN force one of the two (for tests and measurement).
+ * SAMPLED joins every live node to its first two live neighbours, takes the
+ * tree of the highest-degree live node as the giant tree and lets only nodes
+ * outside it scan their whole adjacency; EDGES runs union-find over every
+ * undirected edge.  AUTO (the default) is TREE. */
 #define GAPA_FITNESS_AUTO 0
 #define GAPA_FITNESS_EDGES 1
 #define GAPA_FITNESS_SAMPLED 2
 #define GAPA_FITNESS_TREE 3
+#define GAPA_FITNESS_TREE_JOIN 4
+#define GAPA_FITNESS_TREE_SCAN 5
 int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
 /* Per-kernel timing of the calls made between gapa_profile_begin() and

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "gapa_internal.cuh"
+#include "tree16.cuh"
 
 int gapa_fitness_kernels_init(gapa_ctx* c);
 int gapa_ga_kernels_init(gapa_ctx* c);
@@ -36,6 +37,8 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.perm);
     cudaFree(g.tparent);
     cudaFree(g.nontree);
+    cudaFree(g.fptr);
+    cudaFree(g.fcol16);
     cudaFree(g.lo_ptr);
     cudaFree(g.lo_col);
     cudaFree(g.palt);
@@ -485,8 +488,9 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     BfsForest bf = bfs_forest(n, rp, sorted);
     g.bfs_depth = bf.depth;
     g.num_nontree = (int)bf.nontree.size();
+    g.mean_deg_x16 = n > 0 ? (int)((16 * nnz + n - 1) / n) : 0;
     // 16-bit ids only on the shared-memory path (labels + deleted-node bitmap)
-    g.packed16 = n <= 65536 && (size_t)n * 4 + (size_t)((n + 31) / 32) * 4 <= c->fit_smem_max;
+    g.packed16 = n <= 65536 && gapa_dev::tree16_smem_bytes(n) <= c->fit_smem_max;
     const size_t nt_bytes = (g.packed16 ? 4 : 8) * std::max<size_t>(bf.nontree.size(), 4);
     if (cudaMalloc(&g.perm, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
         cudaMalloc(&g.tparent, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
@@ -517,6 +521,24 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     if (!bf.lo_col.empty())
         GAPA_CUDA(cudaMemcpy(g.lo_col, bf.lo_col.data(), sizeof(int32_t) * bf.lo_col.size(), cudaMemcpyHostToDevice));
     if (g.packed16) {
+        // full adjacency in BFS numbers, 16-bit ids (the TREE kernel's scan of the nodes outside the giant piece)
+        std::vector<int32_t> fptr((size_t)n + 1, 0), inv((size_t)n);
+        for (int32_t v = 0; v < n; ++v) inv[bf.perm[v]] = v;
+        std::vector<uint16_t> fcol((size_t)std::max<int64_t>(nnz, 1));
+        for (int32_t b = 0; b < n; ++b) {
+            const int32_t v = inv[b];
+            int32_t o = fptr[b];
+            for (int32_t e = rp[v]; e < rp[v + 1]; ++e) fcol[o++] = (uint16_t)bf.perm[sorted[e]];
+            fptr[b + 1] = o;
+        }
+        if (cudaMalloc(&g.fptr, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+            cudaMalloc(&g.fcol16, sizeof(uint16_t) * fcol.size()) != cudaSuccess) {
+            free_graph(g);
+            cudaGetLastError();
+            return gapa_fail(GAPA_ERR_OOM, "BFS-numbered adjacency of %d nodes", n);
+        }
+        GAPA_CUDA(cudaMemcpy(g.fptr, fptr.data(), sizeof(int32_t) * fptr.size(), cudaMemcpyHostToDevice));
+        GAPA_CUDA(cudaMemcpy(g.fcol16, fcol.data(), sizeof(uint16_t) * fcol.size(), cudaMemcpyHostToDevice));
         std::vector<uint32_t> w(bf.nontree.size());
         for (size_t i = 0; i < w.size(); ++i)
             w[i] = ((uint32_t)bf.nontree[i].first << 16) | (uint32_t)bf.nontree[i].second;
@@ -712,7 +734,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
 
 int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
-    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_TREE)
+    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_TREE_SCAN)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown fitness kernel %d", variant);
     c->fitness_variant = variant;
     return GAPA_OK;

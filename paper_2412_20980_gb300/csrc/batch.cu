@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "gapa_internal.cuh"
+#include "tree16.cuh"
 
 struct gapa_batch {
     int device = 0;
@@ -49,7 +50,7 @@ struct gapa_batch {
 
 namespace {
 
-size_t need16(int n) { return (size_t)n * 4 + (size_t)((n + 31) / 32) * 4; }
+size_t need16(int n) { return gapa_dev::tree16_smem_bytes(n); }
 
 // Largest team count (1, 2, 4, 8) whose slices hold the graph and keep >= 128 threads per team
 // and at least ~8 nodes per thread.
@@ -305,6 +306,9 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         d.lo_col = dg.lo_col;
         d.nontree = (const unsigned*)dg.nontree;
         d.num_nontree = dg.num_nontree;
+        d.fptr = dg.fptr;
+        d.fcol16 = dg.fcol16;
+        d.mean_deg_x16 = dg.mean_deg_x16;
         b->teams[i] = default_teams(dg.n, b->fit_max_dyn);
         for (int r = 0; r < g.pop; ++r) rows.push_back(make_int2(i, r));
     }

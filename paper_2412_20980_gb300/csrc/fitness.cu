@@ -292,6 +292,10 @@ struct GraphArgs {
     const int2* palt;
     const void* nontree;
     int num_nontree;
+    const int* fptr;
+    const unsigned short* fcol16;
+    int join_mode;
+    int mean_deg_x16;
 };
 
 enum Variant : int { V_EDGES = 0, V_SAMPLED = 1, V_TREE16 = 2, V_TREE32 = 3 };
@@ -302,8 +306,9 @@ __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g,
     if (kVar == V_TREE16) {
         // the whole CTA is one team; the deleted-node bitmap sits right after the labels
         const gapa_dev::Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
-        const gapa_dev::Tree16Graph t16{g.n,      g.perm,   g.palt, g.lo_ptr, g.lo_col,
-                                        (const unsigned*)g.nontree, g.num_nontree};
+        const gapa_dev::Tree16Graph t16{g.n,      g.perm,          g.palt, g.lo_ptr, g.lo_col,
+                                        (const unsigned*)g.nontree, g.num_nontree, g.fptr, g.fcol16, g.join_mode,
+                                        g.mean_deg_x16};
         gapa_dev::tree16_member(tm, lab, (unsigned*)(lab + g.n), t16, genes, k, out, red, status);
         return;
     }
@@ -346,7 +351,7 @@ template <int kVar>
 int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, int k, long long* f,
                    cudaStream_t st) {
     const int n = ga.n;
-    const size_t lab_bytes = (size_t)n * 4 + (kVar == V_TREE16 ? (size_t)((n + 31) >> 5) * 4 : 0);
+    const size_t lab_bytes = kVar == V_TREE16 ? gapa_dev::tree16_smem_bytes(n) : (size_t)n * 4;
     if (lab_bytes <= c->fit_smem_max) {
         cc_smem_kernel<kVar><<<s, smem_block_for(n), lab_bytes, st>>>(ga, pop, k, f, c->status);
         GAPA_CUDA(cudaGetLastError());
@@ -400,6 +405,10 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ga.palt = c->g.palt;
     ga.nontree = c->g.nontree;
     ga.num_nontree = c->g.num_nontree;
+    ga.fptr = c->g.fptr;
+    ga.fcol16 = c->g.fcol16;
+    ga.join_mode = c->fitness_variant == GAPA_FITNESS_TREE_JOIN ? 1 : c->fitness_variant == GAPA_FITNESS_TREE_SCAN ? 2 : 0;
+    ga.mean_deg_x16 = c->g.mean_deg_x16;
     switch (c->fitness_variant) {
         case GAPA_FITNESS_EDGES:
             return launch_variant<V_EDGES>(c, ga, pop, s, k, f, st);
@@ -568,7 +577,8 @@ __global__ void __launch_bounds__(1024, 1) fitness_batched_kernel(const BatchDes
             const gapa_dev::Team tm{(int)threadIdx.x - team * T, T, 1 + team};
             const unsigned slice = (smem_bytes / (unsigned)q.teams) & ~15u;
             int* lab = reinterpret_cast<int*>(smem + (size_t)team * slice);
-            const gapa_dev::Tree16Graph g{bd.n, bd.perm, bd.palt, bd.lo_ptr, bd.lo_col, bd.nontree, bd.num_nontree};
+            const gapa_dev::Tree16Graph g{bd.n,       bd.perm,        bd.palt, bd.lo_ptr, bd.lo_col,
+                                          bd.nontree, bd.num_nontree, bd.fptr, bd.fcol16, 0, bd.mean_deg_x16};
             const int member = q.i0 + team;
             gapa_dev::tree16_member(tm, lab, reinterpret_cast<unsigned*>(lab + bd.n), g,
                                     bd.pop[buf] + (size_t)member * bd.p.k, bd.p.k,

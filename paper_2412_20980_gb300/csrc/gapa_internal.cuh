@@ -108,6 +108,9 @@ struct DeviceGraph {
     int2* palt = nullptr;       // [n] (tree parent, second lower-numbered neighbour or -1)
     void* nontree = nullptr;    // non-tree edges (a < b, BFS numbers): uint32 a<<16|b if packed16, else int2
     int num_nontree = 0;
+    int* fptr = nullptr;                // [n+1] full adjacency in BFS numbers (packed16 graphs only)
+    unsigned short* fcol16 = nullptr;   // [2E]
+    int mean_deg_x16 = 0;               // 16 * 2E / n, rounded up
     bool packed16 = false;      // n <= 65536
     int bfs_depth = 0;          // largest BFS level
 };
@@ -214,6 +217,9 @@ struct BatchDesc {
     const int* lo_col;
     const unsigned* nontree;
     int num_nontree;
+    const int* fptr;
+    const unsigned short* fcol16;
+    int mean_deg_x16;
     int teams;           // members per CTA in the batched fitness kernel (1, 2, 4 or 8)
 };
 

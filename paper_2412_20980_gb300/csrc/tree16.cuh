@@ -91,20 +91,26 @@ struct Tree16Graph {
     const int* lo_col;
     const unsigned* nontree;  // non-tree edges a<<16|b
     int num_nontree;
+    const int* fptr;          // full adjacency in BFS numbering (CSR, 16-bit ids)
+    const unsigned short* fcol;
+    int join_mode;            // 0: per member, 1: non-tree edges, 2: scan outside the giant piece
+    int mean_deg_x16;         // 16 * 2E / n, rounded up
 };
 
-// Shared-memory bytes of one member: labels + deleted-node bitmap.
+// Shared-memory bytes of one member: labels + deleted-node bitmap + two
+// team-wide scalars.
 __host__ __device__ __forceinline__ size_t tree16_smem_bytes(int n) {
-    return (size_t)n * 4 + (size_t)((n + 31) >> 5) * 4;
+    return (size_t)n * 4 + (size_t)((n + 31) >> 5) * 4 + 8;
 }
 
-// One member: lab = n labels, dead = (n+31)/32 bitmap words (both this team's
-// shared memory).  Deleted nodes end as -1.
+// One member: lab = n labels, dead = (n+31)/32 bitmap words followed by two
+// scalars (all in this team's shared memory).  Deleted nodes end as -1.
 __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab, unsigned* dead, const Tree16Graph& g,
                                               const int* __restrict__ genes, int k, long long* out, long long* red,
                                               int* status) {
     const int tid = tm.tid, T = tm.T, n = g.n;
     const int words = (n + 31) >> 5;
+    volatile int* scalar = reinterpret_cast<volatile int*>(dead + words);
     for (int w = tid; w < words; w += T) dead[w] = 0u;
     tm.sync();
     // perturbation P^(A, p) of Eq. 13 in BFS numbering
@@ -158,14 +164,81 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
         }
     }
     tm.sync();
-    // flatten every piece onto its top node (owner writes only)
-    for (int v = tid; v < n; v += T) {
-        const int p = lab[v];
-        if (p != -1 && p != v) lab[v] = uf_root(lab, p);
+    // The piece of the first live node is taken as the giant one.  That node
+    // has no live lower-numbered neighbour, so it is its piece's root and the
+    // smallest live id: no union ever hooks it under another root.
+    if (tid == 0) {
+        int f = -1;
+        for (int w = 0; w < words; ++w) {
+            const unsigned live = ~dead[w];
+            if (live) {
+                f = (w << 5) + __ffs(live) - 1;
+                break;
+            }
+        }
+        scalar[0] = f < n ? f : -1;
     }
     tm.sync();
-    // join the pieces along the non-tree edges, four per 16-byte load
-    {
+    const int R = scalar[0];
+    // flatten every piece onto its top node (owner writes only), and count
+    // the nodes outside the giant piece
+    long long outside = 0;
+    for (int v = tid; v < n; v += T) {
+        const int p = lab[v];
+        if (p == -1) continue;
+        const int r = p == v ? v : uf_root(lab, p);
+        if (p != v) lab[v] = r;
+        outside += r != R;
+    }
+    outside = team_sum_ll(tm, outside, red);
+    // their adjacency (estimated at the mean degree) against the non-tree edges
+    if (tid == 0)
+        scalar[1] = g.join_mode == 2 || (g.join_mode == 0 && outside * g.mean_deg_x16 <= 16ll * g.num_nontree) ? 1 : 0;
+    tm.sync();
+    if (scalar[1]) {
+        // few nodes outside the giant piece: only they scan their adjacency (an
+        // edge inside the giant piece cannot join anything).  A warp takes 32
+        // consecutive nodes; the arcs of those outside are laid end to end and
+        // dealt out one per lane (a lane finds its node by binary search over
+        // the warp's degree prefix sums).
+        const int lane = tid & 31, nw = T >> 5;
+        for (int base = (tid >> 5) * 32; base < n; base += nw * 32) {
+            const int v = base + lane;
+            const int l = v < n ? lab[v] : -1;
+            const bool out = l != -1 && l != R;
+            if (!__ballot_sync(0xffffffffu, out)) continue;
+            int b = 0, d = 0;
+            if (out) {
+                b = __ldg(&g.fptr[v]);
+                d = __ldg(&g.fptr[v + 1]) - b;
+            }
+            int incl = d;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int s0 = 0; s0 < total; s0 += 32) {
+                const int idx = s0 + lane;
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__shfl_sync(0xffffffffu, incl, mid) > idx) hi = mid; else lo = mid + 1;
+                }
+                const int ob = __shfl_sync(0xffffffffu, b, lo), oi = __shfl_sync(0xffffffffu, incl, lo),
+                          od = __shfl_sync(0xffffffffu, d, lo);
+                if (idx < total) {
+                    const int ov = base + lo;
+                    const int w = __ldg(&g.fcol[ob + idx - (oi - od)]);
+                    const int lw = lab[w];
+                    if (lw != -1 && lw != lab[ov]) uf_unite(lab, ov, w);
+                }
+            }
+        }
+    } else {
+        // join the pieces along the non-tree edges, four per 16-byte load
         const uint4* e4 = reinterpret_cast<const uint4*>(g.nontree);
         const int quads = g.num_nontree >> 2;
         int q = tid;

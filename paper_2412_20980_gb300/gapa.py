@@ -41,7 +41,7 @@ EXPORTS = [
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
     "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual", "gapa_offspring",
 ]
-FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE = 0, 1, 2, 3
+FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_SCAN = 0, 1, 2, 3, 4, 5
 
 
 class GapaError(RuntimeError):
