@@ -97,20 +97,94 @@ struct Tree16Graph {
     int mean_deg_x16;         // 16 * 2E / n, rounded up
 };
 
-// Shared-memory bytes of one member: labels + deleted-node bitmap + two
-// team-wide scalars.
+// Shared-memory bytes of one member: labels + deleted-node bitmap (reused as
+// a node list once the labels are set) + four team-wide scalars.
 __host__ __device__ __forceinline__ size_t tree16_smem_bytes(int n) {
-    return (size_t)n * 4 + (size_t)((n + 31) >> 5) * 4 + 8;
+    return (size_t)n * 4 + (size_t)((n + 31) >> 5) * 4 + 16;
 }
 
-// One member: lab = n labels, dead = (n+31)/32 bitmap words followed by two
+// The label pick of live node v: its tree parent if live, else its first
+// live lower-numbered neighbour, else v; -1 for a deleted v.
+__device__ __forceinline__ int tree16_pick(const unsigned* dead, const Tree16Graph& g, int v, int2 pa) {
+    if (bm_test(dead, v)) return -1;
+    if (pa.x == v || !bm_test(dead, pa.x)) return pa.x;
+    if (pa.y < 0) return v;
+    if (!bm_test(dead, pa.y)) return pa.y;
+    const int beg = __ldg(&g.lo_ptr[v]) + 2, end = __ldg(&g.lo_ptr[v + 1]);
+    for (int e = beg; e < end; ++e) {
+        const int w = __ldg(&g.lo_col[e]);
+        if (!bm_test(dead, w)) return w;
+    }
+    return v;
+}
+
+// Unite every live node of a warp's `cnt` nodes (node of lane j: nodes[j],
+// -1 for none) with its live neighbours.  The arcs of the warp's nodes are
+// laid end to end and dealt out one per lane; a lane finds its node by binary
+// search over the warp's degree prefix sums.
+__device__ __forceinline__ void tree16_scan_warp(volatile int* lab, const Tree16Graph& g, int v, int lane) {
+    int b = 0, d = 0;
+    if (v >= 0) {
+        b = __ldg(&g.fptr[v]);
+        d = __ldg(&g.fptr[v + 1]) - b;
+    }
+    int incl = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int s0 = 0; s0 < total; s0 += 32) {
+        const int idx = s0 + lane;
+        int lo = 0, hi = 31;
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo + hi) >> 1;
+            if (__shfl_sync(0xffffffffu, incl, mid) > idx) hi = mid; else lo = mid + 1;
+        }
+        const int ov = __shfl_sync(0xffffffffu, v, lo), ob = __shfl_sync(0xffffffffu, b, lo),
+                  oi = __shfl_sync(0xffffffffu, incl, lo), od = __shfl_sync(0xffffffffu, d, lo);
+        if (idx < total) {
+            const int w = __ldg(&g.fcol[ob + idx - (oi - od)]);
+            const int lw = lab[w];
+            if (lw != -1 && lw != lab[ov]) uf_unite(lab, ov, w);
+        }
+    }
+}
+
+// Root of live node v (labels may carry count bits above bit 16).
+__device__ __forceinline__ int tree16_root16(volatile int* lab, int v) {
+    int x = lab[v] & 0xFFFF;
+    while (true) {
+        const int q = lab[x] & 0xFFFF;
+        if (q == x) return x;
+        x = q;
+    }
+}
+
+// One member: lab = n labels, dead = (n+31)/32 bitmap words followed by four
 // scalars (all in this team's shared memory).  Deleted nodes end as -1.
+//
+// Phases: deletion bitmap; labels (tree parent, or on a deleted parent the
+// first live lower-numbered neighbour, or the node itself); flatten every
+// piece onto its top node.  The piece of the first live node R is the giant
+// candidate: R has no live lower-numbered neighbour, so it is its piece's
+// root and the smallest live id, and no union ever hooks it under another
+// root.  The live nodes outside R's piece are listed (in the bitmap's words,
+// which nothing reads any more) and counted; then the pieces are joined,
+// either by letting only the listed nodes scan their adjacency (an edge
+// inside R's piece joins nothing) or along every non-tree edge, whichever is
+// cheaper (an arc scan costs about half a non-tree edge).  Sizes: only listed nodes can end outside R's
+// component, so only they walk to their roots; R's component has the other
+// live nodes plus the listed ones that reached R.  Without room for the list
+// every live node walks and counts.
 __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab, unsigned* dead, const Tree16Graph& g,
                                               const int* __restrict__ genes, int k, long long* out, long long* red,
                                               int* status) {
-    const int tid = tm.tid, T = tm.T, n = g.n;
+    const int tid = tm.tid, T = tm.T, n = g.n, lane = tid & 31;
     const int words = (n + 31) >> 5;
-    volatile int* scalar = reinterpret_cast<volatile int*>(dead + words);
+    volatile int* scalar = reinterpret_cast<volatile int*>(dead + words);  // R, mode, list length, live
     for (int w = tid; w < words; w += T) dead[w] = 0u;
     tm.sync();
     // perturbation P^(A, p) of Eq. 13 in BFS numbering
@@ -124,8 +198,19 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
         }
     }
     tm.sync();
-    // labels: tree parent, or on a deleted parent the first live lower-numbered
-    // neighbour, or the node itself; four nodes per thread per step
+    if (tid == 0) {
+        int f = -1;
+        for (int w = 0; w < words; ++w) {
+            const unsigned live = ~dead[w];
+            if (live) {
+                f = (w << 5) + __ffs(live) - 1;
+                break;
+            }
+        }
+        scalar[0] = f < n ? f : -1;
+        scalar[2] = 0;
+    }
+    // labels, four nodes per thread per step
     constexpr int kU = 4;
     for (int base = tid; base < n; base += kU * T) {
         int2 pa[kU];
@@ -137,105 +222,59 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int v = base + u * T;
-            if (v >= n) break;
-            int q;
-            if (bm_test(dead, v)) {
-                q = -1;
-            } else if (pa[u].x == v || !bm_test(dead, pa[u].x)) {
-                q = pa[u].x;
-            } else {
-                q = v;
-                if (pa[u].y >= 0) {
-                    if (!bm_test(dead, pa[u].y)) {
-                        q = pa[u].y;
-                    } else {
-                        const int beg = __ldg(&g.lo_ptr[v]) + 2, end = __ldg(&g.lo_ptr[v + 1]);
-                        for (int e = beg; e < end; ++e) {
-                            const int w = __ldg(&g.lo_col[e]);
-                            if (!bm_test(dead, w)) {
-                                q = w;
-                                break;
-                            }
-                        }
-                    }
-                }
-            }
-            lab[v] = q;
+            if (v < n) lab[v] = tree16_pick(dead, g, v, pa[u]);
         }
-    }
-    tm.sync();
-    // The piece of the first live node is taken as the giant one.  That node
-    // has no live lower-numbered neighbour, so it is its piece's root and the
-    // smallest live id: no union ever hooks it under another root.
-    if (tid == 0) {
-        int f = -1;
-        for (int w = 0; w < words; ++w) {
-            const unsigned live = ~dead[w];
-            if (live) {
-                f = (w << 5) + __ffs(live) - 1;
-                break;
-            }
-        }
-        scalar[0] = f < n ? f : -1;
     }
     tm.sync();
     const int R = scalar[0];
-    // flatten every piece onto its top node (owner writes only), and count
-    // the nodes outside the giant piece
-    long long outside = 0;
-    for (int v = tid; v < n; v += T) {
-        const int p = lab[v];
-        if (p == -1) continue;
-        const int r = p == v ? v : uf_root(lab, p);
-        if (p != v) lab[v] = r;
-        outside += r != R;
+    // flatten (owner writes only) and list the live nodes outside R's piece
+    int* list = reinterpret_cast<int*>(dead);
+    long long live_out = 0;  // live << 32 | outside
+    for (int base = 0; base < n; base += T) {
+        const int v = base + tid;
+        int r = -1;
+        if (v < n) {
+            const int p = lab[v];
+            if (p != -1) {
+                r = p == v ? v : uf_root(lab, p);
+                if (p != v) lab[v] = r;
+            }
+        }
+        const bool outside = r >= 0 && r != R;
+        live_out += (r >= 0 ? (1ll << 32) : 0) + (outside ? 1 : 0);
+        const unsigned m = __ballot_sync(0xffffffffu, outside);
+        if (m) {
+            int first = 0;
+            if (lane == 0) first = atomicAdd((int*)&scalar[2], __popc(m));
+            first = __shfl_sync(0xffffffffu, first, 0);
+            const int slot = first + __popc(m & ((1u << lane) - 1));
+            if (outside && slot < words) list[slot] = v;
+        }
     }
-    outside = team_sum_ll(tm, outside, red);
-    // their adjacency (estimated at the mean degree) against the non-tree edges
-    if (tid == 0)
-        scalar[1] = g.join_mode == 2 || (g.join_mode == 0 && outside * g.mean_deg_x16 <= 16ll * g.num_nontree) ? 1 : 0;
+    live_out = team_sum_ll(tm, live_out, red);
+    if (tid == 0) {
+        const long long outside = live_out & 0xFFFFFFFFll;
+        // scanning costs about half as much per arc as uniting along a non-tree edge
+        const bool scan = g.join_mode == 2 || (g.join_mode == 0 && outside * g.mean_deg_x16 <= 32ll * g.num_nontree);
+        scalar[1] = (scan ? 1 : 0) | (outside <= words ? 2 : 0);
+        scalar[3] = (int)(live_out >> 32);
+    }
     tm.sync();
-    if (scalar[1]) {
-        // few nodes outside the giant piece: only they scan their adjacency (an
-        // edge inside the giant piece cannot join anything).  A warp takes 32
-        // consecutive nodes; the arcs of those outside are laid end to end and
-        // dealt out one per lane (a lane finds its node by binary search over
-        // the warp's degree prefix sums).
-        const int lane = tid & 31, nw = T >> 5;
+    const int mode = scalar[1], listed = scalar[2];
+    const bool have_list = (mode & 2) != 0;
+    const int nw = T >> 5;
+    if ((mode & 1) && have_list) {
+        // the listed nodes scan their adjacency, 32 per warp step
+        for (int i0 = (tid >> 5) * 32; i0 < listed; i0 += nw * 32)
+            tree16_scan_warp(lab, g, i0 + lane < listed ? list[i0 + lane] : -1, lane);
+    } else if (mode & 1) {
+        // the same over every node, skipping the groups of 32 with nobody outside R's piece
         for (int base = (tid >> 5) * 32; base < n; base += nw * 32) {
             const int v = base + lane;
             const int l = v < n ? lab[v] : -1;
-            const bool out = l != -1 && l != R;
-            if (!__ballot_sync(0xffffffffu, out)) continue;
-            int b = 0, d = 0;
-            if (out) {
-                b = __ldg(&g.fptr[v]);
-                d = __ldg(&g.fptr[v + 1]) - b;
-            }
-            int incl = d;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int x = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += x;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int s0 = 0; s0 < total; s0 += 32) {
-                const int idx = s0 + lane;
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int step = 0; step < 5; ++step) {
-                    const int mid = (lo + hi) >> 1;
-                    if (__shfl_sync(0xffffffffu, incl, mid) > idx) hi = mid; else lo = mid + 1;
-                }
-                const int ob = __shfl_sync(0xffffffffu, b, lo), oi = __shfl_sync(0xffffffffu, incl, lo),
-                          od = __shfl_sync(0xffffffffu, d, lo);
-                if (idx < total) {
-                    const int ov = base + lo;
-                    const int w = __ldg(&g.fcol[ob + idx - (oi - od)]);
-                    const int lw = lab[w];
-                    if (lw != -1 && lw != lab[ov]) uf_unite(lab, ov, w);
-                }
-            }
+            const bool outside = l != -1 && l != R;
+            if (!__ballot_sync(0xffffffffu, outside)) continue;
+            tree16_scan_warp(lab, g, outside ? v : -1, lane);
         }
     } else {
         // join the pieces along the non-tree edges, four per 16-byte load
@@ -265,37 +304,58 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
         }
     }
     tm.sync();
-    // sizes: a root's slot becomes (members below it) << 16 | its id; every
-    // live non-root walks to its root (masking the count bits) and adds
-    // itself, warp-aggregated.  A root's own slot may already carry count
-    // bits, so it is classified by the masked id; -1 (deleted) can equal no
-    // root slot because root ids are below 65535.
-    const int lane = tid & 31;
-    for (int base = 0; base < n; base += T) {
-        const int v = base + tid;
-        int key = -1;
-        if (v < n) {
-            const int l = lab[v];
-            if (l != -1 && (l & 0xFFFF) != v) {
-                int x = l & 0xFFFF;
-                while (true) {
-                    const int q = lab[x] & 0xFFFF;
-                    if (q == x) break;
-                    x = q;
-                }
-                key = x;
+    // sizes: a root's slot becomes (members below it) << 16 | its id; a
+    // root's own slot may already carry count bits, so it is classified by
+    // the masked id; -1 (deleted) can equal no root slot because root ids are
+    // below 65535.
+    long long acc = 0;
+    if (have_list) {
+        long long joined = 0;  // listed nodes whose component is R's
+        for (int i = tid; i < listed; i += T) {
+            const int v = list[i];
+            const int x = tree16_root16(lab, v);
+            if (x == R) ++joined;
+            else if (x != v) atomicAdd((unsigned*)&lab[x], 1u << 16);
+        }
+        joined = team_sum_ll(tm, joined, red);
+        if (tid == 0) {
+            const long long c = (long long)scalar[3] - listed + joined;  // R's component
+            acc = c * (c - 1) / 2;
+        }
+        tm.sync();
+        for (int i = tid; i < listed; i += T) {
+            const int v = list[i];
+            const unsigned l = (unsigned)lab[v];
+            if ((int)(l & 0xFFFFu) == v) {
+                const long long c = (long long)(l >> 16) + 1;
+                acc += c * (c - 1) / 2;
             }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd((unsigned*)&lab[key], (unsigned)__popc(peers) << 16);
-    }
-    tm.sync();
-    long long acc = 0;
-    for (int v = tid; v < n; v += T) {
-        const unsigned l = (unsigned)lab[v];
-        if (l != 0xFFFFFFFFu && (int)(l & 0xFFFFu) == v) {
-            const long long c = (long long)(l >> 16) + 1;
-            acc += c * (c - 1) / 2;
+    } else {
+        // every live non-root walks to its root and adds itself: R's members by
+        // one ballot, the other roots grouped with match_any
+        for (int base = 0; base < n; base += T) {
+            const int v = base + tid;
+            int key = -1;
+            if (v < n) {
+                const int l = lab[v];
+                if (l != -1 && (l & 0xFFFF) != v) key = tree16_root16(lab, v);
+            }
+            const unsigned giant = __ballot_sync(0xffffffffu, key >= 0 && key == R);
+            if (giant && lane == 0) atomicAdd((unsigned*)&lab[R], (unsigned)__popc(giant) << 16);
+            const bool other = key >= 0 && key != R;
+            if (__any_sync(0xffffffffu, other)) {
+                const unsigned peers = __match_any_sync(0xffffffffu, other ? key : -1);
+                if (other && lane == __ffs(peers) - 1) atomicAdd((unsigned*)&lab[key], (unsigned)__popc(peers) << 16);
+            }
+        }
+        tm.sync();
+        for (int v = tid; v < n; v += T) {
+            const unsigned l = (unsigned)lab[v];
+            if (l != 0xFFFFFFFFu && (int)(l & 0xFFFFu) == v) {
+                const long long c = (long long)(l >> 16) + 1;
+                acc += c * (c - 1) / 2;
+            }
         }
     }
     const long long tot = team_sum_ll(tm, acc, red);
