@@ -23,7 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 TAG_INIT, TAG_SEL, TAG_XOVER, TAG_MUT, TAG_MUTVAL, TAG_REPAIR, TAG_ROULETTE = 1, 2, 3, 4, 5, 6, 7
-FLAG_ROWWISE, FLAG_MU_PLUS_LAMBDA, FLAG_ROULETTE = 1, 2, 4
+FLAG_ROWWISE, FLAG_MU_PLUS_LAMBDA, FLAG_ROULETTE, FLAG_MCN = 1, 2, 4, 8
 
 
 class OracleError(RuntimeError):
@@ -57,6 +57,8 @@ def _load():
         lib.oracle_pc_bfs.restype = i64
         lib.oracle_pc_uf.argtypes = [i32, P, P, P, i32]
         lib.oracle_pc_uf.restype = i64
+        lib.oracle_mcn_bfs.argtypes = [i32, P, P, P, i32]
+        lib.oracle_mcn_bfs.restype = i64
         lib.oracle_fitness.argtypes = [i32, P, P, P, i32, i32, P, i32, i32]
         lib.oracle_fitness.restype = ctypes.c_int
         lib.oracle_pop_init.argtypes = [i32, i32, i32, u64, P]
@@ -126,14 +128,24 @@ def pc(row_ptr, col, genes, method: str = "bfs") -> int:
     return int(r)
 
 
+def mcn(row_ptr, col, genes) -> int:
+    """Maximum connectivity number: nodes of the largest component with the genes deleted."""
+    row_ptr, col, genes = _i32(row_ptr), _i32(col), _i32(genes)
+    n = row_ptr.shape[0] - 1
+    r = _load().oracle_mcn_bfs(n, _ptr(row_ptr), _ptr(col), _ptr(genes), genes.shape[0])
+    if r < 0:
+        raise OracleError(f"mcn failed with status {r}")
+    return int(r)
+
+
 def fitness(row_ptr, col, pop, method: str = "bfs", nthreads: int = 1) -> np.ndarray:
-    """PC of every row of ``pop`` (int32[s][k]) -> int64[s]."""
+    """PC ("bfs", "uf") or MCN ("mcn") of every row of ``pop`` (int32[s][k]) -> int64[s]."""
     row_ptr, col, pop = _i32(row_ptr), _i32(col), _i32(pop)
     n = row_ptr.shape[0] - 1
     s, k = pop.shape
     fit = np.zeros(s, dtype=np.int64)
     rc = _load().oracle_fitness(n, _ptr(row_ptr), _ptr(col), _ptr(pop), s, k, _ptr(fit),
-                                0 if method == "bfs" else 1, nthreads)
+                                {"bfs": 0, "uf": 1, "mcn": 2}[method], nthreads)
     _check(rc, "fitness")
     return fit
 

@@ -149,6 +149,22 @@ int64_t oracle_components_bfs(int32_t n, const int32_t* row_ptr, const int32_t* 
     return ncomp;
 }
 
+/* Maximum connectivity number (end of Section III-C; MCN rows of Table
+ * "Whole"): the number of nodes of the largest connected component of
+ * G[V \ D], 0 when every node is deleted. */
+int64_t oracle_mcn_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                       const int32_t* genes, int32_t k)
+{
+    int32_t* sizes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (!sizes) return ORACLE_ENOMEM;
+    int64_t ncomp = oracle_components_bfs(n, row_ptr, col, genes, k, sizes);
+    if (ncomp < 0) { free(sizes); return ncomp; }
+    int64_t best = 0;
+    for (int64_t c = 0; c < ncomp; c++) if (sizes[c] > best) best = sizes[c];
+    free(sizes);
+    return best;
+}
+
 int64_t oracle_pc_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col,
                       const int32_t* genes, int32_t k)
 {
@@ -199,8 +215,8 @@ int64_t oracle_pc_uf(int32_t n, const int32_t* row_ptr, const int32_t* col,
 }
 
 /* Fitness of s members (rows of k genes) with the chosen method
- * (0 = BFS, 1 = union-find), in parallel over members when nthreads > 1.
- * Returns ORACLE_OK or the first error. */
+ * (0 = PC by BFS, 1 = PC by union-find, 2 = MCN by BFS), in parallel over
+ * members when nthreads > 1.  Returns ORACLE_OK or the first error. */
 int oracle_fitness(int32_t n, const int32_t* row_ptr, const int32_t* col,
                    const int32_t* pop, int32_t s, int32_t k, int64_t* fit,
                    int32_t method, int32_t nthreads)
@@ -212,8 +228,9 @@ int oracle_fitness(int32_t n, const int32_t* row_ptr, const int32_t* col,
 #endif
     for (int32_t i = 0; i < s; i++) {
         const int32_t* genes = pop + (size_t)i * (size_t)k;
-        int64_t v = method == 0 ? oracle_pc_bfs(n, row_ptr, col, genes, k)
-                                : oracle_pc_uf(n, row_ptr, col, genes, k);
+        int64_t v = method == 0   ? oracle_pc_bfs(n, row_ptr, col, genes, k)
+                    : method == 1 ? oracle_pc_uf(n, row_ptr, col, genes, k)
+                                  : oracle_mcn_bfs(n, row_ptr, col, genes, k);
         fit[i] = v;
         if (v < 0) {
 #ifdef _OPENMP
@@ -309,6 +326,7 @@ static int32_t tournament(uint64_t seed, int32_t i, int32_t g, int32_t slot, int
 #define ORACLE_FLAG_ROWWISE 1u
 #define ORACLE_FLAG_MU_PLUS_LAMBDA 2u
 #define ORACLE_FLAG_ROULETTE 4u
+#define ORACLE_FLAG_MCN 8u      /* fitness = MCN instead of PC */
 
 /* Roulette-wheel selection (Eq. 5) for minimisation with integer weights:
  * w_x = (max F - F_x) + 1, cumulative sums cum[x] = w_0 + ... + w_x (int64);
@@ -436,7 +454,7 @@ int oracle_generation(int32_t n, const int32_t* row_ptr, const int32_t* col,
             make_child(seed, n, k, i, g, pc_thr, pm_thr, pop_in + (size_t)pa * (size_t)k,
                        pop_in + (size_t)pb * (size_t)k, kids + (size_t)c * (size_t)k, &w);
         }
-        err = oracle_fitness(n, row_ptr, col, kids, nchild, k, kfit, 0, nthreads);
+        err = oracle_fitness(n, row_ptr, col, kids, nchild, k, kfit, (flags & ORACLE_FLAG_MCN) ? 2 : 0, nthreads);
     }
     if (err == ORACLE_OK && !mpl) {
         int32_t elite = 0;
@@ -493,7 +511,7 @@ int oracle_run(int32_t n, const int32_t* row_ptr, const int32_t* col,
     int64_t* fb = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
     int err = (!pa || !pb || !fa || !fb) ? ORACLE_ENOMEM : ORACLE_OK;
     if (err == ORACLE_OK) err = oracle_pop_init(n, k, s, seed, pa);
-    if (err == ORACLE_OK) err = oracle_fitness(n, row_ptr, col, pa, s, k, fa, 0, nthreads);
+    if (err == ORACLE_OK) err = oracle_fitness(n, row_ptr, col, pa, s, k, fa, (flags & ORACLE_FLAG_MCN) ? 2 : 0, nthreads);
     for (int32_t g = 0; g <= gens && err == ORACLE_OK; g++) {
         if (g > 0) {
             err = oracle_generation(n, row_ptr, col, k, s, t, pc_thr, pm_thr, seed, flags, g, lambda,

@@ -210,3 +210,68 @@ def test_fitness_threads_agree():
     a = oracle.fitness(g.row_ptr, g.col, pop, "bfs", nthreads=1)
     b = oracle.fitness(g.row_ptr, g.col, pop, "uf", nthreads=4)
     assert np.array_equal(a, b)
+
+
+def _dense_mcn(adj, alive):
+    """MCN from the reachability matrix of Eq. 17: the largest row sum of Normalizer((A+I)^N) over
+    live nodes (end of Section III-C), 0 with no live node."""
+    n = adj.shape[0]
+    a = adj[None, :, :].astype(np.int64) * alive[:, :, None] * alive[:, None, :]
+    m = a + np.eye(n, dtype=np.int64)[None] * alive[:, :, None]
+    steps = 0
+    while (1 << steps) < n:
+        m = np.minimum(m @ m, 1)
+        steps += 1
+    return m.sum(axis=2).max(axis=1)
+
+
+@pytest.mark.parametrize("seed,n,edges", [(1, 12, 16), (3, 14, 20), (5, 11, 8)])
+def test_mcn_exhaustive_against_dense_reachability(seed, n, edges):
+    g = synth.er_graph(n, edges, seed)
+    adj = np.zeros((n, n), dtype=np.int64)
+    u, v = g.edge_list()
+    adj[u, v] = 1
+    adj[v, u] = 1
+    masks = np.arange(1 << n, dtype=np.int64)
+    dead = ((masks[:, None] >> np.arange(n)[None, :]) & 1).astype(bool)
+    want = _dense_mcn(adj, ~dead)
+    for k in range(n + 1):
+        idx = np.flatnonzero(dead.sum(axis=1) == k)
+        pop = np.stack([np.flatnonzero(dead[i]).astype(np.int32) for i in idx]) if k > 0 else \
+            np.zeros((idx.size, 0), np.int32)
+        assert np.array_equal(oracle.fitness(g.row_ptr, g.col, pop, "mcn"), want[idx]), k
+
+
+def test_mcn_closed_forms():
+    path = synth.named_graph("path", 10)
+    assert oracle.mcn(path.row_ptr, path.col, []) == 10
+    assert oracle.mcn(path.row_ptr, path.col, [4]) == 5  # {0..3} and {5..9}
+    assert oracle.mcn(path.row_ptr, path.col, [2, 6]) == 3
+    star = synth.named_graph("star", 9)
+    assert oracle.mcn(star.row_ptr, star.col, [0]) == 1
+    assert oracle.mcn(star.row_ptr, star.col, [1, 2]) == 7
+    kn = synth.named_graph("complete", 8)
+    assert oracle.mcn(kn.row_ptr, kn.col, [0, 3, 5]) == 5
+    assert oracle.mcn(kn.row_ptr, kn.col, list(range(8))) == 0
+    both = disjoint_union(synth.named_graph("path", 4), synth.named_graph("cycle", 7))
+    assert oracle.mcn(both.row_ptr, both.col, []) == 7
+    assert oracle.mcn(both.row_ptr, both.col, [4]) == 6
+
+
+def test_mcn_against_scipy_and_pc():
+    sp = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    g = synth.ba_graph(1500, 2, 8)
+    rng = np.random.default_rng(2)
+    pops = np.stack([rng.choice(g.n, size=200, replace=False) for _ in range(6)]).astype(np.int32)
+    got = oracle.fitness(g.row_ptr, g.col, pops, "mcn")
+    pc = oracle.fitness(g.row_ptr, g.col, pops)
+    for r in range(6):
+        alive = np.ones(g.n, dtype=bool)
+        alive[pops[r]] = False
+        keep = np.flatnonzero(alive)
+        m = sp.csr_matrix((np.ones(g.col.size), g.col, g.row_ptr), shape=(g.n, g.n))[keep][:, keep]
+        _, lab = csgraph.connected_components(m, directed=False)
+        assert got[r] == np.bincount(lab).max()
+        c = int(got[r])
+        assert c * (c - 1) // 2 <= pc[r]  # the largest component alone contributes C(MCN, 2)

@@ -340,3 +340,19 @@ def test_roulette_and_mu_plus_lambda_run_reaches_optimum():
                    flags=oracle.FLAG_MU_PLUS_LAMBDA | oracle.FLAG_ROULETTE, lam=30)
     assert r["best_fit"] == best
     assert np.all(np.diff(r["traj"]) <= 0)
+
+
+def test_mcn_objective_generation():
+    """With the MCN flag every fitness the GA carries is the MCN of its row, and the best
+    trajectory is monotone."""
+    g = synth.ba_graph(400, 2, 3)
+    pc_thr, pm_thr = oracle.thresholds(0.8, 0.05)
+    res = oracle.run(g.row_ptr, g.col, k=30, pop=24, gens=6, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr, seed=3,
+                     flags=oracle.FLAG_MCN)
+    assert np.all(np.diff(res["traj"]) <= 0)
+    assert res["best_fit"] == oracle.mcn(g.row_ptr, g.col, res["best_set"])
+    pop = oracle.pop_init(g.n, 30, 24, 3)
+    fit = oracle.fitness(g.row_ptr, g.col, pop, "mcn")
+    p2, f2 = oracle.generation(g.row_ptr, g.col, pop, fit, 1, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr, seed=3,
+                               flags=oracle.FLAG_MCN)
+    assert np.array_equal(f2, oracle.fitness(g.row_ptr, g.col, p2, "mcn"))
