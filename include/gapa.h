@@ -295,6 +295,16 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
 #define GAPA_FITNESS_TREE_SCAN 5
 int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
+/* Fitness objective of the context (both minimised; the end of Section III-C
+ * and the PC(G) and MCN rows of Table "Whole"): PC = pairwise connectivity
+ * Σ C(|C|, 2) over the components C of G[V\D] (the default); MCN = maximum
+ * connectivity number, the number of nodes of the largest component (0 when
+ * every node is deleted).  Applies to gapa_fitness, the generation and run
+ * calls and batches built from the context; gapa_fitness_noalloc computes PC. */
+#define GAPA_OBJECTIVE_PC 0
+#define GAPA_OBJECTIVE_MCN 1
+int gapa_set_objective(gapa_ctx* ctx, int objective);
+
 /* Per-kernel timing of the calls made between gapa_profile_begin() and
  * gapa_profile_end(): CUDA events are recorded on the launching stream around
  * every fitness launch, every genetic-operator launch and every phase of

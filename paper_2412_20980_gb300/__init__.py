@@ -18,8 +18,10 @@ from .gapa import (
     FLAG_ROWWISE,
     load,
     make_config,
+    preset_config,
+    PRESETS,
     threshold,
 )
 
 __all__ = ["Batch", "Config", "Context", "GapaError", "Surrogate", "SurrogateConfig", "make_surrogate_config",
-           "run_surrogate", "EXPORTS", "FLAG_MU_PLUS_LAMBDA", "FLAG_ROULETTE", "FLAG_ROWWISE", "load", "make_config", "threshold"]
+           "run_surrogate", "EXPORTS", "FLAG_MU_PLUS_LAMBDA", "FLAG_ROULETTE", "FLAG_ROWWISE", "load", "make_config", "preset_config", "PRESETS", "threshold"]

@@ -740,6 +740,14 @@ int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
     return GAPA_OK;
 }
 
+int gapa_set_objective(gapa_ctx* c, int objective) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (objective != GAPA_OBJECTIVE_PC && objective != GAPA_OBJECTIVE_MCN)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown objective %d", objective);
+    c->objective = objective;
+    return GAPA_OK;
+}
+
 int gapa_profile_begin(gapa_ctx* c) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
     c->profiling = true;

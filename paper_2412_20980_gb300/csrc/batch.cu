@@ -309,6 +309,7 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         d.fptr = dg.fptr;
         d.fcol16 = dg.fcol16;
         d.mean_deg_x16 = dg.mean_deg_x16;
+        d.objective = b->ctxs[i]->objective;
         b->teams[i] = default_teams(dg.n, b->fit_max_dyn);
         for (int r = 0; r < g.pop; ++r) rows.push_back(make_int2(i, r));
     }

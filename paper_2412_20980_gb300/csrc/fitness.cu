@@ -29,17 +29,9 @@ __device__ __forceinline__ void edge_op(volatile int* lab, int u, int v) {
     uf_unite(lab, u, v);
 }
 
-__device__ __forceinline__ long long block_sum_ll(long long v, long long* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    long long tot = 0;
-    if (warp == 0) {
-        tot = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-    }
-    return tot;  // valid in thread 0
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* red, bool mx = false) {
+    const gapa_dev::Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
+    return gapa_dev::team_sum_ll(tm, v, red, mx);  // valid in thread 0
 }
 
 // Labels: every node its own root, then the perturbation P^(A, p) of Eq. 13
@@ -234,7 +226,7 @@ __device__ __forceinline__ void hook_tree(volatile int* lab, int n, const int* _
 }
 
 // Component sizes and the int64 sum of C(size, 2) (PC(G) of Table "Whole").
-__device__ __forceinline__ void count_pc(volatile int* lab, int n, long long* out, long long* red) {
+__device__ __forceinline__ void count_pc(volatile int* lab, int n, long long* out, long long* red, int objective) {
     const int tid = threadIdx.x, T = blockDim.x;
     // flatten: every live node points at its root
     for (int v = tid; v < n; v += T) {
@@ -263,12 +255,9 @@ __device__ __forceinline__ void count_pc(volatile int* lab, int n, long long* ou
     long long acc = 0;
     for (int v = tid; v < n; v += T) {
         const int l = lab[v];
-        if (l < 0 && l != kDead) {
-            const long long c = -(long long)l;
-            acc += c * (c - 1) / 2;
-        }
+        if (l < 0 && l != kDead) acc = gapa_dev::objective_add(acc, -(long long)l, objective);
     }
-    const long long tot = block_sum_ll(acc, red);
+    const long long tot = block_sum_ll(acc, red, objective != 0);
     if (tid == 0) *out = tot;
 }
 
@@ -296,6 +285,7 @@ struct GraphArgs {
     const unsigned short* fcol16;
     int join_mode;
     int mean_deg_x16;
+    int objective;
 };
 
 enum Variant : int { V_EDGES = 0, V_SAMPLED = 1, V_TREE16 = 2, V_TREE32 = 3 };
@@ -308,7 +298,7 @@ __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g,
         const gapa_dev::Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
         const gapa_dev::Tree16Graph t16{g.n,      g.perm,          g.palt, g.lo_ptr, g.lo_col,
                                         (const unsigned*)g.nontree, g.num_nontree, g.fptr, g.fcol16, g.join_mode,
-                                        g.mean_deg_x16};
+                                        g.mean_deg_x16, g.objective};
         gapa_dev::tree16_member(tm, lab, (unsigned*)(lab + g.n), t16, genes, k, out, red, status);
         return;
     }
@@ -322,7 +312,7 @@ __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g,
         else
             hook_all_edges(lab, g.num_edges, g.edges);
     }
-    count_pc(lab, g.n, out, red);
+    count_pc(lab, g.n, out, red, g.objective);
 }
 
 // One CTA per member, labels in shared memory.
@@ -409,6 +399,7 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ga.fcol16 = c->g.fcol16;
     ga.join_mode = c->fitness_variant == GAPA_FITNESS_TREE_JOIN ? 1 : c->fitness_variant == GAPA_FITNESS_TREE_SCAN ? 2 : 0;
     ga.mean_deg_x16 = c->g.mean_deg_x16;
+    ga.objective = c->objective;
     switch (c->fitness_variant) {
         case GAPA_FITNESS_EDGES:
             return launch_variant<V_EDGES>(c, ga, pop, s, k, f, st);
@@ -478,7 +469,7 @@ __global__ void __launch_bounds__(1024) cc_noalloc_kernel(int n, int num_edges, 
     volatile int* lab = labels + (size_t)blockIdx.x * n;
     init_labels(lab, n, pop + (size_t)i * k, k, status);
     hook_edge_list_checked(lab, n, num_edges, edges, status);
-    count_pc(lab, n, &fit[i], red);
+    count_pc(lab, n, &fit[i], red, 0);  // pairwise connectivity
 }
 
 // Device addresses of the static arrays on the current device, looked up once.
@@ -578,7 +569,8 @@ __global__ void __launch_bounds__(1024, 1) fitness_batched_kernel(const BatchDes
             const unsigned slice = (smem_bytes / (unsigned)q.teams) & ~15u;
             int* lab = reinterpret_cast<int*>(smem + (size_t)team * slice);
             const gapa_dev::Tree16Graph g{bd.n,       bd.perm,        bd.palt, bd.lo_ptr, bd.lo_col,
-                                          bd.nontree, bd.num_nontree, bd.fptr, bd.fcol16, 0, bd.mean_deg_x16};
+                                          bd.nontree, bd.num_nontree, bd.fptr, bd.fcol16, 0, bd.mean_deg_x16,
+                                          bd.objective};
             const int member = q.i0 + team;
             gapa_dev::tree16_member(tm, lab, reinterpret_cast<unsigned*>(lab + bd.n), g,
                                     bd.pop[buf] + (size_t)member * bd.p.k, bd.p.k,

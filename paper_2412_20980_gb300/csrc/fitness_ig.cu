@@ -74,6 +74,7 @@ struct IgArgs {
     int* L;  // [groups][n][8]
     long long* fit;
     int* status;
+    int objective;  // 0: PC, 1: MCN
 };
 
 __device__ __forceinline__ int* group_labels(const IgArgs& a) { return a.L + (size_t)blockIdx.y * a.n * kM; }
@@ -194,7 +195,8 @@ __global__ void __launch_bounds__(kIgBlock) ig_count_kernel(IgArgs a) {
     if (run) atomicAdd(L + (size_t)run_root * kM + m, -run);
 }
 
-// int64 sum of C(size, 2) over roots, per member: block reduce, then one atomic per member
+// Per member, the int64 sum of C(size, 2) over roots (PC) or the largest size
+// (MCN): block reduce, then one atomic per member.
 __global__ void __launch_bounds__(kIgBlock) ig_sum_kernel(IgArgs a) {
     int* L = group_labels(a);
     __shared__ unsigned long long acc_m[kM];
@@ -202,22 +204,31 @@ __global__ void __launch_bounds__(kIgBlock) ig_sum_kernel(IgArgs a) {
     __syncthreads();
     const size_t total = (size_t)a.n * kM;
     const int m = (int)(gtid() % kM);
+    const bool mx = a.objective != 0;
     unsigned long long acc = 0;
     for (size_t t = gtid(); t < total; t += gthreads()) {
         const int l = *slot(L, (int)(t / kM), m);
         if (l < 0 && l != kDead) {
             const unsigned long long c = (unsigned long long)(-(long long)l);
-            acc += c * (c - 1) / 2;
+            acc = mx ? (c > acc ? c : acc) : acc + c * (c - 1) / 2;
         }
     }
     // lanes with equal (lane % 8) share a member: reduce over lanes 8 apart
-    acc += __shfl_down_sync(0xffffffffu, acc, 16);
-    acc += __shfl_down_sync(0xffffffffu, acc, 8);
-    if ((threadIdx.x & 31) < kM) atomicAdd(&acc_m[threadIdx.x & 31], acc);
+    for (int o = 16; o >= 8; o >>= 1) {
+        const unsigned long long x = __shfl_down_sync(0xffffffffu, acc, o);
+        acc = mx ? (x > acc ? x : acc) : acc + x;
+    }
+    if ((threadIdx.x & 31) < kM) {
+        if (mx) atomicMax(&acc_m[threadIdx.x & 31], acc);
+        else atomicAdd(&acc_m[threadIdx.x & 31], acc);
+    }
     __syncthreads();
     if (threadIdx.x < kM) {
         const int member = a.member_base + blockIdx.y * kM + threadIdx.x;
-        if (member < a.s) atomicAdd((unsigned long long*)&a.fit[member], acc_m[threadIdx.x]);
+        if (member < a.s) {
+            if (mx) atomicMax((unsigned long long*)&a.fit[member], acc_m[threadIdx.x]);
+            else atomicAdd((unsigned long long*)&a.fit[member], acc_m[threadIdx.x]);
+        }
     }
 }
 
@@ -261,6 +272,7 @@ int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_
     a.L = c->labels;
     a.fit = reinterpret_cast<long long*>(fit);
     a.status = c->status;
+    a.objective = c->objective;
     // grid: enough CTAs to fill the GPU a few times over, a multiple of the SM count
     const size_t work = (size_t)n * kM;
     int bx = (int)((work + kIgBlock - 1) / kIgBlock);

@@ -139,6 +139,7 @@ struct gapa_ctx {
     int64_t* run_traj = nullptr;
     size_t run_traj_cap = 0;
     int fitness_variant = 0;  // 0 = auto
+    int objective = 0;        // GAPA_OBJECTIVE_PC or GAPA_OBJECTIVE_MCN
     // (mu+lambda) and roulette scratch
     int32_t* kids = nullptr;
     size_t kids_cap = 0;      // ints
@@ -220,6 +221,7 @@ struct BatchDesc {
     const int* fptr;
     const unsigned short* fcol16;
     int mean_deg_x16;
+    int objective;       // GAPA_OBJECTIVE_*
     int teams;           // members per CTA in the batched fitness kernel (1, 2, 4 or 8)
 };
 

@@ -69,18 +69,30 @@ __device__ __forceinline__ void uf_unite(volatile int* lab, int a, int b) {
 
 __device__ __forceinline__ bool bm_test(const unsigned* bm, int v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
 
-// Sum over the team; valid in team thread 0.  red: 32 slots of this team.
-__device__ __forceinline__ long long team_sum_ll(const Team& tm, long long v, long long* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+// Sum (or, with mx, maximum) of non-negative values over the team; valid in
+// team thread 0.  red: 32 slots of this team.
+__device__ __forceinline__ long long team_sum_ll(const Team& tm, long long v, long long* red, bool mx = false) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long x = __shfl_down_sync(0xffffffffu, v, o);
+        v = mx ? (x > v ? x : v) : v + x;
+    }
     const int warp = tm.tid >> 5, lane = tm.tid & 31;
     if (lane == 0) red[warp] = v;
     tm.sync();
     long long tot = 0;
     if (warp == 0) {
         tot = lane < (tm.T >> 5) ? red[lane] : 0;
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long x = __shfl_down_sync(0xffffffffu, tot, o);
+            tot = mx ? (x > tot ? x : tot) : tot + x;
+        }
     }
     return tot;
+}
+
+// A component of c nodes in the objective: C(c, 2) summed for PC, c maxed for MCN.
+__device__ __forceinline__ long long objective_add(long long acc, long long c, int objective) {
+    return objective ? (c > acc ? c : acc) : acc + c * (c - 1) / 2;
 }
 
 struct Tree16Graph {
@@ -95,6 +107,7 @@ struct Tree16Graph {
     const unsigned short* fcol;
     int join_mode;            // 0: per member, 1: non-tree edges, 2: scan outside the giant piece
     int mean_deg_x16;         // 16 * 2E / n, rounded up
+    int objective;            // 0: PC, 1: MCN
 };
 
 // Shared-memory bytes of one member: labels + deleted-node bitmap (reused as
@@ -320,16 +333,13 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
         joined = team_sum_ll(tm, joined, red);
         if (tid == 0) {
             const long long c = (long long)scalar[3] - listed + joined;  // R's component
-            acc = c * (c - 1) / 2;
+            acc = objective_add(0, c, g.objective);
         }
         tm.sync();
         for (int i = tid; i < listed; i += T) {
             const int v = list[i];
             const unsigned l = (unsigned)lab[v];
-            if ((int)(l & 0xFFFFu) == v) {
-                const long long c = (long long)(l >> 16) + 1;
-                acc += c * (c - 1) / 2;
-            }
+            if ((int)(l & 0xFFFFu) == v) acc = objective_add(acc, (long long)(l >> 16) + 1, g.objective);
         }
     } else {
         // every live non-root walks to its root and adds itself: R's members by
@@ -352,13 +362,11 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
         tm.sync();
         for (int v = tid; v < n; v += T) {
             const unsigned l = (unsigned)lab[v];
-            if (l != 0xFFFFFFFFu && (int)(l & 0xFFFFu) == v) {
-                const long long c = (long long)(l >> 16) + 1;
-                acc += c * (c - 1) / 2;
-            }
+            if (l != 0xFFFFFFFFu && (int)(l & 0xFFFFu) == v)
+                acc = objective_add(acc, (long long)(l >> 16) + 1, g.objective);
         }
     }
-    const long long tot = team_sum_ll(tm, acc, red);
+    const long long tot = team_sum_ll(tm, acc, red, g.objective != 0);
     if (tid == 0) *out = tot;
 }
 

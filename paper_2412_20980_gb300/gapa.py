@@ -40,8 +40,10 @@ EXPORTS = [
     "gapa_batch_autotune", "gapa_batch_run",
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
     "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual", "gapa_offspring",
+    "gapa_set_objective",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_SCAN = 0, 1, 2, 3, 4, 5
+OBJECTIVE_PC, OBJECTIVE_MCN = 0, 1
 
 
 class GapaError(RuntimeError):
@@ -120,6 +122,25 @@ def make_config(k: int, pop: int, gens: int = 0, tourn: int = 2, pc: float = 0.8
     return Config(k, pop, gens, tourn, elite, threshold(pc), threshold(pm), seed & (2**64 - 1), flags, lam)
 
 
+# GA parameters of the CND algorithms in the paper's parameter table (Table "Params"):
+# crossover and mutation rates, iterations, population size and perturbation rate k / n.
+PRESETS = {
+    "cutoff": {"pc": 0.6, "pm": 0.2, "gens": 5000, "pop": 80, "rate": 0.1},
+    "sixdst": {"pc": 0.5, "pm": 0.3, "gens": 5000, "pop": 80, "rate": 0.1},
+    "tde": {"pc": 0.5, "pm": 0.3, "gens": 5000, "pop": 10, "rate": 0.1},
+}
+
+
+def preset_config(name: str, n: int, seed: int = 0, tourn: int = 2, flags: int = 0, **overrides) -> Config:
+    """A Config with the named preset's rates, iterations and population for a graph of n nodes;
+    the budget is k = round(rate * n) (at least 1, below n).  Keyword arguments override fields."""
+    p = dict(PRESETS[name])
+    p.update(overrides)
+    k = min(max(1, int(round(p["rate"] * n))), max(n - 1, 0))
+    return make_config(k=p.get("k", k), pop=p["pop"], gens=p["gens"], tourn=tourn, pc=p["pc"], pm=p["pm"],
+                       seed=seed, flags=flags)
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -151,6 +172,7 @@ def load(path: str | None = None):
             "gapa_sync": ([V], U),
             "gapa_profile_begin": ([V], U),
             "gapa_set_fitness_kernel": ([V, U], U),
+            "gapa_set_objective": ([V, U], U),
             "gapa_fitness_noalloc": ([U, V, I32, I32, V, V, I32, I32, V], U),
             "gapa_batch_create": ([ctypes.POINTER(V), I32, V, V], U),
             "gapa_batch_destroy": ([V], None),
@@ -365,6 +387,10 @@ class Context:
 
     def set_fitness_kernel(self, variant: int):
         _check(self.lib.gapa_set_fitness_kernel(self.handle, variant))
+
+    def set_objective(self, objective: int):
+        """OBJECTIVE_PC (pairwise connectivity, the default) or OBJECTIVE_MCN (largest component)."""
+        _check(self.lib.gapa_set_objective(self.handle, objective))
 
     def profile_begin(self):
         _check(self.lib.gapa_profile_begin(self.handle))

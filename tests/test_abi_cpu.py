@@ -72,3 +72,14 @@ def test_oracle_builds_and_is_separate():
     for f in glob.glob(os.path.join(ROOT, "paper_2412_20980_gb300", "**", "*.*"), recursive=True):
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             assert "import oracle" not in open(f).read(), f
+
+
+def test_presets_follow_the_parameter_table():
+    from paper_2412_20980_gb300 import PRESETS, preset_config, threshold
+
+    cfg = preset_config("sixdst", 500, seed=3)
+    assert (cfg.k, cfg.pop, cfg.gens) == (50, 80, 5000)
+    assert cfg.pc_thr == threshold(0.5) and cfg.pm_thr == threshold(0.3)
+    cfg = preset_config("cutoff", 2018)
+    assert (cfg.k, cfg.pop) == (202, 80) and cfg.pc_thr == threshold(0.6) and cfg.pm_thr == threshold(0.2)
+    assert preset_config("tde", 1000, gens=10).gens == 10 and PRESETS["tde"]["pop"] == 10

@@ -217,3 +217,27 @@ def test_invalid_graphs_rejected(ctx):
     # repeated arc
     with pytest.raises(GapaError):
         ctx.graph_upload(np.array([0, 2, 4], dtype=np.int32), np.array([1, 1, 0, 0], dtype=np.int32))
+
+
+@pytest.mark.parametrize("graph", ["ba", "path", "star", "hub_deleted", "large"])
+def test_mcn_objective_matches_oracle(ctx, graph):
+    """The maximum connectivity number objective, on the shared-memory and the global-label paths."""
+    from paper_2412_20980_gb300.gapa import OBJECTIVE_MCN, OBJECTIVE_PC
+
+    if graph == "large" and ctx.variant_name != "tree":
+        pytest.skip("global-label path runs on the default kernel only")
+    g = {"ba": lambda: synth.ba_graph(3000, 2, 4), "path": lambda: synth.named_graph("path", 4000),
+         "star": lambda: synth.named_graph("star", 2500), "hub_deleted": lambda: synth.ba_graph(2000, 1, 6),
+         "large": lambda: synth.ba_graph(100000, 3, 2)}[graph]()
+    k = max(1, g.n // 20)
+    pop = synth.random_deletion_sets(g.n, k, 40, 11)
+    if graph in ("star", "hub_deleted"):
+        hubs = np.argsort(-g.degrees(), kind="stable")[:k].astype(np.int32)
+        pop[0] = hubs  # the centre / the hubs: many small components
+    ctx.set_objective(OBJECTIVE_MCN)
+    try:
+        got = gpu_fit(ctx, g, pop)
+    finally:
+        ctx.set_objective(OBJECTIVE_PC)
+    want = oracle.fitness(g.row_ptr, g.col, pop, "mcn", nthreads=oracle.max_threads())
+    assert np.array_equal(got, want)

@@ -198,3 +198,22 @@ def test_offspring_plus_sliced_fitness_equals_generation(ctx, flags):
     assert torch.equal(p2, want_p) and torch.equal(f2, want_f)
     with pytest.raises(GapaError):
         ctx.offspring(_cfg(k=150, pop=77, seed=4, flags=2, lam=64), 3, pop, fit, p2, f2)
+
+
+def test_mcn_run_bit_exact(ctx):
+    """A whole run under the MCN objective follows the oracle's MCN run."""
+    from paper_2412_20980_gb300.gapa import OBJECTIVE_MCN, OBJECTIVE_PC
+
+    g = synth.ba_graph(1500, 2, 9)
+    ctx.graph_upload(g.row_ptr, g.col)
+    cfg = _cfg(k=75, pop=64, gens=20, tourn=2, pc=0.8, pm=0.02, seed=6)
+    ctx.set_objective(OBJECTIVE_MCN)
+    try:
+        got = ctx.run(cfg, want_pop=True)
+    finally:
+        ctx.set_objective(OBJECTIVE_PC)
+    want = oracle.run(g.row_ptr, g.col, k=75, pop=64, gens=20, tourn=2, pc_thr=cfg.pc_thr, pm_thr=cfg.pm_thr,
+                      seed=6, flags=oracle.FLAG_MCN, nthreads=oracle.max_threads())
+    assert np.array_equal(got["traj"], want["traj"]) and got["best_fit"] == want["best_fit"]
+    assert np.array_equal(got["best_set"], want["best_set"])
+    assert np.array_equal(got["pop"].cpu().numpy(), want["pop"])
