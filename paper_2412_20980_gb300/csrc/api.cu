@@ -39,6 +39,7 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.nontree);
     cudaFree(g.fptr);
     cudaFree(g.fcol16);
+    cudaFree(g.fcol32);
     cudaFree(g.lo_ptr);
     cudaFree(g.lo_col);
     cudaFree(g.palt);
@@ -401,6 +402,7 @@ void gapa_destroy(gapa_ctx* c) {
     free_graph(c->g);
     cudaFree(c->status);
     cudaFree(c->labels);
+    cudaFree(c->ig_aux);
     for (auto p : c->stage_pop) cudaFree(p);
     for (auto p : c->stage_fit) cudaFree(p);
     cudaFree(c->run_gen);
@@ -520,25 +522,36 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     }
     if (!bf.lo_col.empty())
         GAPA_CUDA(cudaMemcpy(g.lo_col, bf.lo_col.data(), sizeof(int32_t) * bf.lo_col.size(), cudaMemcpyHostToDevice));
-    if (g.packed16) {
-        // full adjacency in BFS numbers, 16-bit ids (the TREE kernel's scan of the nodes outside the giant piece)
-        std::vector<int32_t> fptr((size_t)n + 1, 0), inv((size_t)n);
+    {
+        // full adjacency in BFS numbers (the scans of the nodes outside the giant piece): 16-bit ids
+        // for the shared-memory kernel, 32-bit ids for the global-label one
+        std::vector<int32_t> fptr((size_t)n + 1, 0), inv((size_t)n), fcol((size_t)std::max<int64_t>(nnz, 1));
         for (int32_t v = 0; v < n; ++v) inv[bf.perm[v]] = v;
-        std::vector<uint16_t> fcol((size_t)std::max<int64_t>(nnz, 1));
         for (int32_t b = 0; b < n; ++b) {
             const int32_t v = inv[b];
             int32_t o = fptr[b];
-            for (int32_t e = rp[v]; e < rp[v + 1]; ++e) fcol[o++] = (uint16_t)bf.perm[sorted[e]];
+            for (int32_t e = rp[v]; e < rp[v + 1]; ++e) fcol[o++] = bf.perm[sorted[e]];
             fptr[b + 1] = o;
         }
-        if (cudaMalloc(&g.fptr, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
-            cudaMalloc(&g.fcol16, sizeof(uint16_t) * fcol.size()) != cudaSuccess) {
+        bool ok = cudaMalloc(&g.fptr, sizeof(int32_t) * ((size_t)n + 1)) == cudaSuccess;
+        if (ok && g.packed16) {
+            std::vector<uint16_t> f16(fcol.begin(), fcol.end());
+            ok = cudaMalloc(&g.fcol16, sizeof(uint16_t) * f16.size()) == cudaSuccess &&
+                 cudaMemcpy(g.fcol16, f16.data(), sizeof(uint16_t) * f16.size(), cudaMemcpyHostToDevice) ==
+                     cudaSuccess;
+        } else if (ok) {
+            ok = cudaMalloc(&g.fcol32, sizeof(int32_t) * fcol.size()) == cudaSuccess &&
+                 cudaMemcpy(g.fcol32, fcol.data(), sizeof(int32_t) * fcol.size(), cudaMemcpyHostToDevice) ==
+                     cudaSuccess;
+        }
+        if (!ok) {
             free_graph(g);
             cudaGetLastError();
             return gapa_fail(GAPA_ERR_OOM, "BFS-numbered adjacency of %d nodes", n);
         }
         GAPA_CUDA(cudaMemcpy(g.fptr, fptr.data(), sizeof(int32_t) * fptr.size(), cudaMemcpyHostToDevice));
-        GAPA_CUDA(cudaMemcpy(g.fcol16, fcol.data(), sizeof(uint16_t) * fcol.size(), cudaMemcpyHostToDevice));
+    }
+    if (g.packed16) {
         std::vector<uint32_t> w(bf.nontree.size());
         for (size_t i = 0; i < w.size(); ++i)
             w[i] = ((uint32_t)bf.nontree[i].first << 16) | (uint32_t)bf.nontree[i].second;

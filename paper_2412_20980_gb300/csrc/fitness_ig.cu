@@ -12,6 +12,17 @@
 // int64 sums of C(size, 2) are reduced per member.  Each phase is one
 // grid-wide kernel; thread t of a group handles (node t/8, member t%8) in a
 // grid-stride loop, so the eight lanes of a node share one sector.
+//
+// Deleting hubs near the top of the BFS tree shatters it into many pieces,
+// and uniting them edge by edge in L2 is slow, so two steps come between the
+// cut and the join: every live node also links to up to two live neighbours
+// among the first entries of its adjacency (neighbour sampling), and the
+// first live node of each member - the smallest live id, hence a root
+// forever - names the giant candidate.  The nodes outside its piece then scan
+// their adjacency, unless that is more work than the non-tree edge list, in
+// which case the group joins along the non-tree edges as before.  These steps
+// pay off on graphs with many non-tree edges per node (at least 4); sparser
+// graphs go straight from the cut to the join.
 #include <climits>
 
 #include "gapa_internal.cuh"
@@ -75,7 +86,28 @@ struct IgArgs {
     long long* fit;
     int* status;
     int objective;  // 0: PC, 1: MCN
+    const int* fptr;  // full adjacency in BFS numbers (CSR)
+    const int* fcol;
+    int* giant;                  // [groups][8] first live node of each member (-1: none)
+    unsigned long long* work;    // [groups][8] adjacency entries of the nodes outside the giant piece
+    int sampled;                 // 1: the sampling / giant / scan steps run before the join
 };
+
+constexpr int kLinkScan = 4;  // adjacency entries a node looks at for its sampled links
+
+// a group's last slots may hold no member of the population
+__device__ __forceinline__ bool ig_real_member(const IgArgs& a, int m) {
+    return a.member_base + (int)blockIdx.y * kM + m < a.s;
+}
+
+// whether the group's piece scan replaces the join (decided from the work counts)
+__device__ __forceinline__ bool ig_group_scans(const IgArgs& a) {
+    const unsigned long long* w = a.work + (size_t)blockIdx.y * kM;
+    unsigned long long tot = 0;
+#pragma unroll
+    for (int m = 0; m < kM; ++m) tot += w[m];
+    return tot <= 2ull * kM * (unsigned long long)a.num_nontree;
+}
 
 __device__ __forceinline__ int* group_labels(const IgArgs& a) { return a.L + (size_t)blockIdx.y * a.n * kM; }
 __device__ __forceinline__ size_t gthreads() { return (size_t)gridDim.x * blockDim.x; }
@@ -148,8 +180,96 @@ __global__ void __launch_bounds__(kIgBlock) ig_flatten_kernel(IgArgs a) {
     }
 }
 
+// first live node of every member of the group (one warp per member; the
+// smallest live id), and the work counters cleared
+__global__ void __launch_bounds__(kIgBlock) ig_giant_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const int m = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (m >= kM) return;
+    const int member = a.member_base + blockIdx.y * kM + m;
+    int f = -1;
+    if (member < a.s) {
+        for (int base = 0; base < a.n; base += 32) {
+            const int v = base + lane;
+            const unsigned live = __ballot_sync(0xffffffffu, v < a.n && *slot(L, v, m) != kDead);
+            if (live) {
+                f = base + __ffs(live) - 1;
+                break;
+            }
+        }
+    }
+    if (lane == 0) {
+        a.giant[(size_t)blockIdx.y * kM + m] = f;
+        a.work[(size_t)blockIdx.y * kM + m] = 0ull;
+    }
+}
+
+// neighbour sampling: every live node unites with up to two live neighbours of
+// another piece among its first kLinkScan adjacency entries
+__global__ void __launch_bounds__(kIgBlock) ig_link_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.n * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int v = (int)(t / kM), m = (int)(t % kM);
+        if (!ig_real_member(a, m) || *slot(L, v, m) == kDead) continue;
+        const int beg = __ldg(&a.fptr[v]);
+        const int end = min(__ldg(&a.fptr[v + 1]), beg + kLinkScan);
+        int linked = 0;
+        for (int e = beg; e < end && linked < 2; ++e) {
+            const int w = __ldg(&a.fcol[e]);
+            const int lw = *slot(L, w, m);
+            if (lw == kDead) continue;
+            if (lw != *slot(L, v, m)) ig_unite(L, m, v, w);
+            ++linked;
+        }
+    }
+}
+
+// adjacency entries of the live nodes outside the giant candidate's piece, per member
+__global__ void __launch_bounds__(kIgBlock) ig_outside_kernel(IgArgs a) {
+    int* L = group_labels(a);
+    __shared__ unsigned long long acc_m[kM];
+    if (threadIdx.x < kM) acc_m[threadIdx.x] = 0ull;
+    __syncthreads();
+    const size_t total = (size_t)a.n * kM;
+    const int m = (int)(gtid() % kM);
+    const int R = a.giant[(size_t)blockIdx.y * kM + m];
+    unsigned long long acc = 0;
+    for (size_t t = ig_real_member(a, m) ? gtid() : total; t < total; t += gthreads()) {
+        const int v = (int)(t / kM);
+        const int l = *slot(L, v, m);
+        if (l != kDead && l != R) acc += (unsigned long long)(__ldg(&a.fptr[v + 1]) - __ldg(&a.fptr[v]));
+    }
+    acc += __shfl_down_sync(0xffffffffu, acc, 16);
+    acc += __shfl_down_sync(0xffffffffu, acc, 8);
+    if ((threadIdx.x & 31) < kM) atomicAdd(&acc_m[threadIdx.x & 31], acc);
+    __syncthreads();
+    if (threadIdx.x < kM && acc_m[threadIdx.x])
+        atomicAdd(&a.work[(size_t)blockIdx.y * kM + threadIdx.x], acc_m[threadIdx.x]);
+}
+
+// the nodes outside the giant candidate's piece unite with their live
+// neighbours (an edge inside that piece joins nothing)
+__global__ void __launch_bounds__(kIgBlock) ig_scan_kernel(IgArgs a) {
+    if (!ig_group_scans(a)) return;
+    int* L = group_labels(a);
+    const size_t total = (size_t)a.n * kM;
+    for (size_t t = gtid(); t < total; t += gthreads()) {
+        const int v = (int)(t / kM), m = (int)(t % kM);
+        const int l = *slot(L, v, m);
+        if (l == kDead || l == a.giant[(size_t)blockIdx.y * kM + m] || !ig_real_member(a, m)) continue;
+        const int end = __ldg(&a.fptr[v + 1]);
+        for (int e = __ldg(&a.fptr[v]); e < end; ++e) {
+            const int w = __ldg(&a.fcol[e]);
+            const int lw = *slot(L, w, m);
+            if (lw != kDead && lw != *slot(L, v, m)) ig_unite(L, m, v, w);
+        }
+    }
+}
+
 // join the pieces along the non-tree edges: lane m of an edge handles member m
 __global__ void __launch_bounds__(kIgBlock) ig_join_kernel(IgArgs a) {
+    if (a.sampled && ig_group_scans(a)) return;
     int* L = group_labels(a);
     const size_t total = (size_t)a.num_nontree * kM;
     for (size_t t = gtid(); t < total; t += gthreads()) {
@@ -248,7 +368,10 @@ int ig_groups_per_batch(int n, int s) {
 
 int gapa_ig_prepare(gapa_ctx* c, int s) {
     const int groups = ig_groups_per_batch(c->g.n, s < 1 ? 1 : s);
-    return gapa_reserve((void**)&c->labels, &c->labels_cap, (size_t)groups * c->g.n * kM, sizeof(int));
+    int rc = gapa_reserve((void**)&c->labels, &c->labels_cap, (size_t)groups * c->g.n * kM, sizeof(int));
+    // work counters (8 bytes) and giant ids (4 bytes) per member of a batch
+    if (rc == GAPA_OK) rc = gapa_reserve(&c->ig_aux, &c->ig_aux_cap, (size_t)groups * kM, 12);
+    return rc;
 }
 
 int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
@@ -273,6 +396,11 @@ int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_
     a.fit = reinterpret_cast<long long*>(fit);
     a.status = c->status;
     a.objective = c->objective;
+    a.fptr = c->g.fptr;
+    a.fcol = c->g.fcol32;
+    a.work = reinterpret_cast<unsigned long long*>(c->ig_aux);
+    a.giant = reinterpret_cast<int*>(a.work + (size_t)gpb * kM);
+    a.sampled = (long long)a.num_nontree >= 4ll * n ? 1 : 0;
     // grid: enough CTAs to fill the GPU a few times over, a multiple of the SM count
     const size_t work = (size_t)n * kM;
     int bx = (int)((work + kIgBlock - 1) / kIgBlock);
@@ -292,13 +420,20 @@ int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_
         ig_dead_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_cut_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        if (a.sampled) {
+            ig_giant_kernel<<<dim3(1, gcount), kIgBlock, 0, st>>>(a);
+            ig_link_kernel<<<grid, kIgBlock, 0, st>>>(a);
+            ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
+            ig_outside_kernel<<<grid, kIgBlock, 0, st>>>(a);
+            ig_scan_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        }
         if (a.num_nontree > 0) ig_join_kernel<<<egrid, kIgBlock, 0, st>>>(a);
         ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_roots_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_count_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_sum_kernel<<<grid, kIgBlock, 0, st>>>(a);
         GAPA_CUDA(cudaGetLastError());
-        if (kernels) *kernels = (g0 == 0 ? 0 : *kernels) + (a.num_nontree > 0 ? 9 : 8);
+        if (kernels) *kernels = (g0 == 0 ? 0 : *kernels) + (a.num_nontree > 0 ? 9 : 8) + (a.sampled ? 5 : 0);
     }
     return GAPA_OK;
 }

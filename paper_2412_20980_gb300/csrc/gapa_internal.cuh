@@ -110,6 +110,7 @@ struct DeviceGraph {
     int num_nontree = 0;
     int* fptr = nullptr;                // [n+1] full adjacency in BFS numbers (packed16 graphs only)
     unsigned short* fcol16 = nullptr;   // [2E]
+    int* fcol32 = nullptr;              // [2E] the same with 32-bit ids (graphs that are not packed16)
     int mean_deg_x16 = 0;               // 16 * 2E / n, rounded up
     bool packed16 = false;      // n <= 65536
     int bfs_depth = 0;          // largest BFS level
@@ -131,6 +132,8 @@ struct gapa_ctx {
     // scratch owned by the context
     int* labels = nullptr;  // global label scratch for graphs too large for shared memory
     size_t labels_cap = 0;  // ints
+    void* ig_aux = nullptr;  // per-member work counters and giant ids of the global-label fitness
+    size_t ig_aux_cap = 0;
     int32_t* stage_pop[2] = {nullptr, nullptr};
     int64_t* stage_fit[2] = {nullptr, nullptr};
     size_t stage_pop_cap = 0, stage_fit_cap = 0;  // elements

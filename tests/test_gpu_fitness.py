@@ -132,6 +132,26 @@ def test_global_label_path_rmat(ctx):
     assert np.array_equal(gpu_fit(ctx, g, pop), want)
 
 
+@pytest.mark.parametrize("hubs", [0, 20, 200, 1300])
+def test_global_label_path_hub_heavy(ctx, hubs):
+    """A dense R-MAT graph (8 edges per node, so the sampling / giant / scan steps run) whose
+    deletion sets hold the top hubs: the BFS tree shatters and the groups move between the
+    outside-node scan and the non-tree join; sizes 17 members, a group and a ragged tail."""
+    if ctx.variant_name != "tree":
+        pytest.skip("global-label path runs on the default kernel only")
+    g = synth.rmat_graph(17, 1 << 20, seed=3, chunk=1 << 20)
+    top = np.argsort(-g.degrees(), kind="stable")
+    rng = np.random.default_rng(hubs)
+    rows = []
+    for r in range(17):
+        h = min(hubs, 1300) if r % 2 == 0 else hubs // 2
+        rest = rng.choice(top[h:], 1300 - h, replace=False)
+        rows.append(np.concatenate([top[:h], rest]))
+    pop = np.stack(rows).astype(np.int32)
+    want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
+    assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
 def test_adversarial_graphs(ctx):
     path = synth.named_graph("path", 30000)  # deep union-find chains
     pop = np.zeros((1, 0), dtype=np.int32)
