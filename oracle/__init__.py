@@ -23,7 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 TAG_INIT, TAG_SEL, TAG_XOVER, TAG_MUT, TAG_MUTVAL, TAG_REPAIR, TAG_ROULETTE = 1, 2, 3, 4, 5, 6, 7
-FLAG_ROWWISE, FLAG_MU_PLUS_LAMBDA, FLAG_ROULETTE, FLAG_MCN = 1, 2, 4, 8
+FLAG_ROWWISE, FLAG_MU_PLUS_LAMBDA, FLAG_ROULETTE, FLAG_MCN, FLAG_EDGES = 1, 2, 4, 8, 16
 
 
 class OracleError(RuntimeError):
@@ -59,6 +59,8 @@ def _load():
         lib.oracle_pc_uf.restype = i64
         lib.oracle_mcn_bfs.argtypes = [i32, P, P, P, i32]
         lib.oracle_mcn_bfs.restype = i64
+        lib.oracle_edge_fitness.argtypes = [i32, P, P, P, i32, i32]
+        lib.oracle_edge_fitness.restype = i64
         lib.oracle_fitness.argtypes = [i32, P, P, P, i32, i32, P, i32, i32]
         lib.oracle_fitness.restype = ctypes.c_int
         lib.oracle_pop_init.argtypes = [i32, i32, i32, u64, P]
@@ -138,14 +140,27 @@ def mcn(row_ptr, col, genes) -> int:
     return int(r)
 
 
+def edge_fitness(row_ptr, col, edge_genes, objective: str = "pc") -> int:
+    """PC or MCN of the graph with the edges ``edge_genes`` removed; edge ids number the edges
+    {u, v}, u < v, in CSR order (u, then v ascending)."""
+    row_ptr, col, genes = _i32(row_ptr), _i32(col), _i32(edge_genes)
+    n = row_ptr.shape[0] - 1
+    r = _load().oracle_edge_fitness(n, _ptr(row_ptr), _ptr(col), _ptr(genes), genes.shape[0],
+                                    1 if objective == "mcn" else 0)
+    if r < 0:
+        raise OracleError(f"edge fitness failed with status {r}")
+    return int(r)
+
+
 def fitness(row_ptr, col, pop, method: str = "bfs", nthreads: int = 1) -> np.ndarray:
-    """PC ("bfs", "uf") or MCN ("mcn") of every row of ``pop`` (int32[s][k]) -> int64[s]."""
+    """PC ("bfs", "uf") or MCN ("mcn") of every row of ``pop`` (int32[s][k], node genes), or with
+    edge genes PC ("edges") or MCN ("edges_mcn") -> int64[s]."""
     row_ptr, col, pop = _i32(row_ptr), _i32(col), _i32(pop)
     n = row_ptr.shape[0] - 1
     s, k = pop.shape
     fit = np.zeros(s, dtype=np.int64)
     rc = _load().oracle_fitness(n, _ptr(row_ptr), _ptr(col), _ptr(pop), s, k, _ptr(fit),
-                                {"bfs": 0, "uf": 1, "mcn": 2}[method], nthreads)
+                                {"bfs": 0, "uf": 1, "mcn": 2, "edges": 3, "edges_mcn": 4}[method], nthreads)
     _check(rc, "fitness")
     return fit
 

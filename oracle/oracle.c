@@ -214,9 +214,80 @@ int64_t oracle_pc_uf(int32_t n, const int32_t* row_ptr, const int32_t* col,
     return pc;
 }
 
+/* ------------------------------------------------------------------ */
+/* Edge perturbation (Section III-C: node and edge perturbations both  */
+/* act on the adjacency matrix; Fig. 1: genes are nodes or edges)      */
+/* ------------------------------------------------------------------ */
+/* Edge ids: the undirected edges {u, v}, u < v, numbered in CSR order
+ * (u ascending, then v ascending; rows are sorted).  arc_id[e] = id of the
+ * edge of arc e, for both orientations (the reverse arc is found by binary
+ * search in the sorted row).  Returns the number of edges, or < 0. */
+static int64_t edge_ids(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t* arc_id)
+{
+    int32_t next = 0;
+    for (int32_t u = 0; u < n; u++)
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; e++)
+            if (col[e] > u) arc_id[e] = next++;
+    for (int32_t u = 0; u < n; u++)
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+            const int32_t v = col[e];
+            if (v >= u) continue;
+            int32_t lo = row_ptr[v], hi = row_ptr[v + 1];
+            while (lo < hi) {
+                const int32_t mid = lo + (hi - lo) / 2;
+                if (col[mid] < u) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= row_ptr[v + 1] || col[lo] != u) return ORACLE_EINVAL;  /* not symmetric */
+            arc_id[e] = arc_id[lo];
+        }
+    return next;
+}
+
+/* PC (objective 0) or MCN (objective 1) of G with the edges `egenes` removed
+ * (every node stays): BFS over the remaining arcs. */
+int64_t oracle_edge_fitness(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                            const int32_t* egenes, int32_t k, int32_t objective)
+{
+    const int64_t nnz = row_ptr[n];
+    int32_t* arc_id = (int32_t*)malloc(sizeof(int32_t) * ((size_t)nnz + 1));
+    uint8_t* seen = (uint8_t*)calloc((size_t)n + 1, 1);
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    uint8_t* gone = NULL;
+    int64_t result = ORACLE_ENOMEM;
+    if (!arc_id || !seen || !queue) goto done;
+    const int64_t m = edge_ids(n, row_ptr, col, arc_id);
+    if (m < 0) { result = m; goto done; }
+    gone = (uint8_t*)calloc((size_t)m + 1, 1);
+    if (!gone) goto done;
+    for (int32_t j = 0; j < k; j++) {
+        if (egenes[j] < 0 || egenes[j] >= m) { result = ORACLE_EINVAL; goto done; }
+        gone[egenes[j]] = 1;
+    }
+    result = 0;
+    for (int32_t start = 0; start < n; start++) {
+        if (seen[start]) continue;
+        int32_t head = 0, tail = 0;
+        queue[tail++] = start;
+        seen[start] = 1;
+        while (head < tail) {
+            const int32_t u = queue[head++];
+            for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+                const int32_t v = col[e];
+                if (!gone[arc_id[e]] && !seen[v]) { seen[v] = 1; queue[tail++] = v; }
+            }
+        }
+        if (objective) { if (tail > result) result = tail; }
+        else result += (int64_t)tail * (int64_t)(tail - 1) / 2;
+    }
+done:
+    free(arc_id); free(seen); free(queue); free(gone);
+    return result;
+}
+
 /* Fitness of s members (rows of k genes) with the chosen method
- * (0 = PC by BFS, 1 = PC by union-find, 2 = MCN by BFS), in parallel over
- * members when nthreads > 1.  Returns ORACLE_OK or the first error. */
+ * (0 = PC by BFS, 1 = PC by union-find, 2 = MCN by BFS; genes are nodes;
+ * 3 = PC, 4 = MCN with genes that are edge ids), in parallel over members
+ * when nthreads > 1.  Returns ORACLE_OK or the first error. */
 int oracle_fitness(int32_t n, const int32_t* row_ptr, const int32_t* col,
                    const int32_t* pop, int32_t s, int32_t k, int64_t* fit,
                    int32_t method, int32_t nthreads)
@@ -230,7 +301,8 @@ int oracle_fitness(int32_t n, const int32_t* row_ptr, const int32_t* col,
         const int32_t* genes = pop + (size_t)i * (size_t)k;
         int64_t v = method == 0   ? oracle_pc_bfs(n, row_ptr, col, genes, k)
                     : method == 1 ? oracle_pc_uf(n, row_ptr, col, genes, k)
-                                  : oracle_mcn_bfs(n, row_ptr, col, genes, k);
+                    : method == 2 ? oracle_mcn_bfs(n, row_ptr, col, genes, k)
+                                  : oracle_edge_fitness(n, row_ptr, col, genes, k, method == 4);
         fit[i] = v;
         if (v < 0) {
 #ifdef _OPENMP
@@ -327,6 +399,19 @@ static int32_t tournament(uint64_t seed, int32_t i, int32_t g, int32_t slot, int
 #define ORACLE_FLAG_MU_PLUS_LAMBDA 2u
 #define ORACLE_FLAG_ROULETTE 4u
 #define ORACLE_FLAG_MCN 8u      /* fitness = MCN instead of PC */
+#define ORACLE_FLAG_EDGES 16u   /* genes are edge ids in [0, E) instead of node ids */
+
+/* Gene universe and fitness method of a run under `flags`. */
+static int32_t gene_universe(int32_t n, const int32_t* row_ptr, uint32_t flags)
+{
+    return (flags & ORACLE_FLAG_EDGES) ? row_ptr[n] / 2 : n;
+}
+
+static int32_t fitness_method(uint32_t flags)
+{
+    const int mcn = (flags & ORACLE_FLAG_MCN) != 0;
+    return (flags & ORACLE_FLAG_EDGES) ? (mcn ? 4 : 3) : (mcn ? 2 : 0);
+}
 
 /* Roulette-wheel selection (Eq. 5) for minimisation with integer weights:
  * w_x = (max F - F_x) + 1, cumulative sums cum[x] = w_0 + ... + w_x (int64);
@@ -430,13 +515,14 @@ int oracle_generation(int32_t n, const int32_t* row_ptr, const int32_t* col,
                       int32_t* pop_out, int64_t* fit_out, int32_t nthreads)
 {
     const int mpl = (flags & ORACLE_FLAG_MU_PLUS_LAMBDA) != 0;
-    if (n < 1 || k < 0 || k >= n || s < 2 || t < 1 || g < 1 || (mpl && lambda < 1)) return ORACLE_EINVAL;
+    const int32_t u = n >= 1 ? gene_universe(n, row_ptr, flags) : 0;  /* genes are drawn from [0, u) */
+    if (n < 1 || k < 0 || k >= u || s < 2 || t < 1 || g < 1 || (mpl && lambda < 1)) return ORACLE_EINVAL;
     if (mpl && (flags & ORACLE_FLAG_ROWWISE)) return ORACLE_EINVAL;
     const int32_t nchild = mpl ? lambda : s - 1;
     int err = ORACLE_OK;
     child_scratch w;
-    w.kept.n = n;
-    w.kept.in = (uint8_t*)malloc((size_t)n);
+    w.kept.n = u;
+    w.kept.in = (uint8_t*)malloc((size_t)u);
     w.holes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
     w.cand0 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
     w.from_b = (uint8_t*)malloc((size_t)k + 1);
@@ -451,10 +537,10 @@ int oracle_generation(int32_t n, const int32_t* row_ptr, const int32_t* col,
             const int32_t i = mpl ? c : c + 1;
             int32_t pa = (flags & ORACLE_FLAG_ROWWISE) ? i : select_parent(seed, flags, i, g, 0, t, s, fit_in, cum);
             int32_t pb = select_parent(seed, flags, i, g, 1, t, s, fit_in, cum);
-            make_child(seed, n, k, i, g, pc_thr, pm_thr, pop_in + (size_t)pa * (size_t)k,
+            make_child(seed, u, k, i, g, pc_thr, pm_thr, pop_in + (size_t)pa * (size_t)k,
                        pop_in + (size_t)pb * (size_t)k, kids + (size_t)c * (size_t)k, &w);
         }
-        err = oracle_fitness(n, row_ptr, col, kids, nchild, k, kfit, (flags & ORACLE_FLAG_MCN) ? 2 : 0, nthreads);
+        err = oracle_fitness(n, row_ptr, col, kids, nchild, k, kfit, fitness_method(flags), nthreads);
     }
     if (err == ORACLE_OK && !mpl) {
         int32_t elite = 0;
@@ -503,15 +589,16 @@ int oracle_run(int32_t n, const int32_t* row_ptr, const int32_t* col,
                uint64_t seed, uint32_t flags, int32_t lambda, int32_t* best_set, int64_t* best_fit,
                int64_t* traj_best, int32_t* pop_final, int64_t* fit_final, int32_t nthreads)
 {
-    if (n < 1 || k < 0 || k >= n || s < 2 || t < 1 || gens < 0) return ORACLE_EINVAL;
+    const int32_t u = n >= 1 ? gene_universe(n, row_ptr, flags) : 0;  /* genes are drawn from [0, u) */
+    if (n < 1 || k < 0 || k >= u || s < 2 || t < 1 || gens < 0) return ORACLE_EINVAL;
     size_t cells = (size_t)s * (size_t)k;
     int32_t* pa = (int32_t*)malloc(sizeof(int32_t) * (cells + 1));
     int32_t* pb = (int32_t*)malloc(sizeof(int32_t) * (cells + 1));
     int64_t* fa = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
     int64_t* fb = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
     int err = (!pa || !pb || !fa || !fb) ? ORACLE_ENOMEM : ORACLE_OK;
-    if (err == ORACLE_OK) err = oracle_pop_init(n, k, s, seed, pa);
-    if (err == ORACLE_OK) err = oracle_fitness(n, row_ptr, col, pa, s, k, fa, (flags & ORACLE_FLAG_MCN) ? 2 : 0, nthreads);
+    if (err == ORACLE_OK) err = oracle_pop_init(u, k, s, seed, pa);
+    if (err == ORACLE_OK) err = oracle_fitness(n, row_ptr, col, pa, s, k, fa, fitness_method(flags), nthreads);
     for (int32_t g = 0; g <= gens && err == ORACLE_OK; g++) {
         if (g > 0) {
             err = oracle_generation(n, row_ptr, col, k, s, t, pc_thr, pm_thr, seed, flags, g, lambda,

@@ -275,3 +275,60 @@ def test_mcn_against_scipy_and_pc():
         assert got[r] == np.bincount(lab).max()
         c = int(got[r])
         assert c * (c - 1) // 2 <= pc[r]  # the largest component alone contributes C(MCN, 2)
+
+
+# ---- edge genes (Section III-C: node and edge perturbations both act on the adjacency matrix) ----
+
+def test_edge_fitness_closed_forms():
+    n = 9
+    path = synth.named_graph("path", n)  # edge i joins i and i+1
+    for i in range(n - 1):
+        assert oracle.edge_fitness(path.row_ptr, path.col, [i]) == comb(i + 1, 2) + comb(n - i - 1, 2)
+        assert oracle.edge_fitness(path.row_ptr, path.col, [i], "mcn") == max(i + 1, n - i - 1)
+    cyc = synth.named_graph("cycle", 10)
+    assert oracle.edge_fitness(cyc.row_ptr, cyc.col, [3]) == comb(10, 2)  # one cut keeps a cycle connected
+    star = synth.named_graph("star", 7)
+    assert oracle.edge_fitness(star.row_ptr, star.col, [0, 1, 2]) == comb(4, 2)  # three leaves cut off
+    all_edges = list(range(star.num_edges))
+    assert oracle.edge_fitness(star.row_ptr, star.col, all_edges) == 0
+    assert oracle.edge_fitness(star.row_ptr, star.col, all_edges, "mcn") == 1
+
+
+def test_node_deletion_equals_removing_its_edges():
+    """The paper's statement that deleting a node is removing its incident edges: the deleted
+    nodes are left isolated, which adds nothing to PC."""
+    g = synth.ba_graph(300, 2, 5)
+    u, v = g.edge_list()
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        genes = rng.choice(g.n, 25, replace=False)
+        hit = np.flatnonzero(np.isin(u, genes) | np.isin(v, genes)).astype(np.int32)
+        assert oracle.edge_fitness(g.row_ptr, g.col, hit) == oracle.pc(g.row_ptr, g.col, genes)
+
+
+@pytest.mark.parametrize("seed,n,edges", [(2, 9, 11), (6, 10, 12)])
+def test_edge_fitness_exhaustive_against_dense_reachability(seed, n, edges):
+    """All 2^E edge subsets: Eq. 17 on the perturbed adjacency matrix (every node alive)."""
+    g = synth.er_graph(n, edges, seed)
+    u, v = g.edge_list()
+    E = u.size
+    masks = np.arange(1 << E, dtype=np.int64)
+    gone = ((masks[:, None] >> np.arange(E)[None, :]) & 1).astype(bool)
+    adj = np.zeros((masks.size, n, n), dtype=np.int64)
+    for e in range(E):
+        keep = ~gone[:, e]
+        adj[keep, u[e], v[e]] = 1
+        adj[keep, v[e], u[e]] = 1
+    m = adj + np.eye(n, dtype=np.int64)[None]
+    steps = 0
+    while (1 << steps) < n:
+        m = np.minimum(m @ m, 1)
+        steps += 1
+    want_pc = (m.sum(axis=(1, 2)) - n) // 2
+    want_mcn = m.sum(axis=2).max(axis=1)
+    for k in range(E + 1):
+        idx = np.flatnonzero(gone.sum(axis=1) == k)
+        pop = np.stack([np.flatnonzero(gone[i]).astype(np.int32) for i in idx]) if k > 0 else \
+            np.zeros((idx.size, 0), np.int32)
+        assert np.array_equal(oracle.fitness(g.row_ptr, g.col, pop, "edges"), want_pc[idx]), k
+        assert np.array_equal(oracle.fitness(g.row_ptr, g.col, pop, "edges_mcn"), want_mcn[idx]), k

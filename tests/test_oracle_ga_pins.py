@@ -356,3 +356,17 @@ def test_mcn_objective_generation():
     p2, f2 = oracle.generation(g.row_ptr, g.col, pop, fit, 1, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr, seed=3,
                                flags=oracle.FLAG_MCN)
     assert np.array_equal(f2, oracle.fitness(g.row_ptr, g.col, p2, "mcn"))
+
+
+def test_edge_gene_generation():
+    """With edge genes the population draws ids in [0, E) and every fitness is the edge fitness."""
+    g = synth.ba_graph(300, 3, 2)
+    E = g.num_edges
+    pc_thr, pm_thr = oracle.thresholds(0.8, 0.05)
+    res = oracle.run(g.row_ptr, g.col, k=40, pop=20, gens=5, tourn=2, pc_thr=pc_thr, pm_thr=pm_thr, seed=8,
+                     flags=oracle.FLAG_EDGES)
+    assert np.all(np.diff(res["traj"]) <= 0)
+    assert res["best_fit"] == oracle.edge_fitness(g.row_ptr, g.col, res["best_set"])
+    pop = res["pop"]
+    assert pop.min() >= 0 and pop.max() < E and all(len(set(r)) == 40 for r in pop.tolist())
+    assert np.array_equal(res["fit"], oracle.fitness(g.row_ptr, g.col, pop, "edges"))
