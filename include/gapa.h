@@ -305,6 +305,20 @@ int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 #define GAPA_OBJECTIVE_MCN 1
 int gapa_set_objective(gapa_ctx* ctx, int objective);
 
+/* Gene type of the context (Fig. 1: the gene pool holds nodes or edges; end
+ * of Section III-A: both perturbations act on the adjacency matrix).  NODES
+ * (the default): genes are node ids in [0, n), deleting a node removes its
+ * edges.  EDGES: genes are edge ids in [0, E) - the undirected edges {u, v},
+ * u < v, numbered in CSR order (u ascending, then v ascending) - and every
+ * node stays; the fitness is the objective of G without those edges.  With
+ * EDGES, cfg->k must be below E, the population and initialisation draw from
+ * [0, E), and the labels plus an E-bit mask must fit in shared memory
+ * (GAPA_ERR_INVALID_ARG otherwise); batches, the surrogate and
+ * gapa_fitness_noalloc use node genes only. */
+#define GAPA_GENES_NODES 0
+#define GAPA_GENES_EDGES 1
+int gapa_set_genes(gapa_ctx* ctx, int gene_type);
+
 /* Per-kernel timing of the calls made between gapa_profile_begin() and
  * gapa_profile_end(): CUDA events are recorded on the launching stream around
  * every fitness launch, every genetic-operator launch and every phase of

@@ -169,7 +169,9 @@ int validate_csr(int32_t n, int64_t nnz, const int32_t* rp, const int32_t* col_i
 int check_cfg(gapa_ctx* c, const gapa_config* cfg) {
     if (!cfg) return gapa_fail(GAPA_ERR_INVALID_ARG, "config is NULL");
     if (c->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "no graph uploaded");
-    if (cfg->k < 0 || cfg->k >= c->g.n) return gapa_fail(GAPA_ERR_INVALID_ARG, "need 0 <= k < n (k=%d, n=%d)", cfg->k, c->g.n);
+    const int universe = gapa_gene_universe(c);
+    if (cfg->k < 0 || cfg->k >= universe)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "need 0 <= k < %s (k=%d, %d)", c->genes ? "E" : "n", cfg->k, universe);
     if (cfg->pop < 2) return gapa_fail(GAPA_ERR_INVALID_ARG, "population must be >= 2 (got %d)", cfg->pop);
     if (cfg->tourn < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "tournament size must be >= 1");
     if (cfg->elite != 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "elite count must be 1 (got %d)", cfg->elite);
@@ -184,12 +186,12 @@ int check_cfg(gapa_ctx* c, const gapa_config* cfg) {
             return gapa_fail(GAPA_ERR_INVALID_ARG, "mu + lambda must be at most 16384");
         if ((long long)cfg->lambda * cfg->k >= (1LL << 31)) return gapa_fail(GAPA_ERR_INVALID_ARG, "lambda*k too large");
     }
-    return gapa_ga_check_limits(c, c->g.n, cfg->k, cfg->pop);
+    return gapa_ga_check_limits(c, universe, cfg->k, cfg->pop);
 }
 
 GaParams make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_ptr) {
     GaParams p;
-    p.n = c->g.n;
+    p.n = gapa_gene_universe(c);  // genes are drawn from [0, p.n)
     p.k = cfg->k;
     p.s = cfg->pop;
     p.t = cfg->tourn;
@@ -750,6 +752,14 @@ int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
     if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_TREE_SCAN)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown fitness kernel %d", variant);
     c->fitness_variant = variant;
+    return GAPA_OK;
+}
+
+int gapa_set_genes(gapa_ctx* c, int gene_type) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (gene_type != GAPA_GENES_NODES && gene_type != GAPA_GENES_EDGES)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown gene type %d", gene_type);
+    c->genes = gene_type;
     return GAPA_OK;
 }
 

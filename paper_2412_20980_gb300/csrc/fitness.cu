@@ -315,6 +315,41 @@ __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g,
     count_pc(lab, g.n, out, red, g.objective);
 }
 
+// Edge genes: every node stays; a member's genes are edge ids (CSR order of
+// the edges {u, v}, u < v, the order of g.edges) whose edges are removed.
+// Labels and the removed-edge mask in shared memory; union-find over the
+// remaining edges, then the sizes and the objective.
+__global__ void __launch_bounds__(1024) cc_edge_genes_kernel(GraphArgs g, const int* __restrict__ pop, int k,
+                                                             long long* __restrict__ fit, int* status) {
+    extern __shared__ int smem_lab[];
+    __shared__ long long red[32];
+    volatile int* lab = smem_lab;
+    unsigned* gone = reinterpret_cast<unsigned*>(smem_lab + g.n);
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int words = (g.num_edges + 31) >> 5;
+    const int* genes = pop + (size_t)blockIdx.x * k;
+    for (int v = tid; v < g.n; v += T) lab[v] = v;
+    for (int w = tid; w < words; w += T) gone[w] = 0u;
+    __syncthreads();
+    for (int j = tid; j < k; j += T) {
+        const int e = __ldg(&genes[j]);
+        if ((unsigned)e < (unsigned)g.num_edges)
+            atomicOr(&gone[e >> 5], 1u << (e & 31));
+        else
+            atomicOr(status, GAPA_DEV_BAD_GENE);
+    }
+    __syncthreads();
+    for (int e = tid; e < g.num_edges; e += T) {
+        if ((gone[e >> 5] >> (e & 31)) & 1u) continue;
+        const int2 ed = __ldg(&g.edges[e]);
+        if (lab[ed.x] != lab[ed.y]) uf_unite(lab, ed.x, ed.y);
+    }
+    __syncthreads();
+    count_pc(lab, g.n, &fit[blockIdx.x], red, g.objective);
+}
+
+size_t edge_genes_smem(int n, int num_edges) { return (size_t)n * 4 + (size_t)((num_edges + 31) / 32) * 4; }
+
 // One CTA per member, labels in shared memory.
 template <int kVar>
 __global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* __restrict__ pop, int k,
@@ -400,6 +435,15 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ga.join_mode = c->fitness_variant == GAPA_FITNESS_TREE_JOIN ? 1 : c->fitness_variant == GAPA_FITNESS_TREE_SCAN ? 2 : 0;
     ga.mean_deg_x16 = c->g.mean_deg_x16;
     ga.objective = c->objective;
+    if (c->genes == GAPA_GENES_EDGES) {
+        const size_t bytes = edge_genes_smem(n, c->g.num_edges);
+        if (bytes > c->fit_smem_max)
+            return gapa_fail(GAPA_ERR_INVALID_ARG, "edge genes: labels and edge mask (%zu bytes) exceed shared memory",
+                             bytes);
+        cc_edge_genes_kernel<<<s, smem_block_for(n), bytes, st>>>(ga, pop, k, f, c->status);
+        GAPA_CUDA(cudaGetLastError());
+        return GAPA_OK;
+    }
     switch (c->fitness_variant) {
         case GAPA_FITNESS_EDGES:
             return launch_variant<V_EDGES>(c, ga, pop, s, k, f, st);
@@ -418,6 +462,7 @@ int gapa_fitness_kernels_init(gapa_ctx* c) {
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_SAMPLED>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE16>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE32>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_edge_genes_kernel, c->smem_optin, &c->fit_smem_max);
     return rc;
 }
 

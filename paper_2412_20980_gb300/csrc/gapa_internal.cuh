@@ -143,6 +143,7 @@ struct gapa_ctx {
     size_t run_traj_cap = 0;
     int fitness_variant = 0;  // 0 = auto
     int objective = 0;        // GAPA_OBJECTIVE_PC or GAPA_OBJECTIVE_MCN
+    int genes = 0;            // GAPA_GENES_NODES or GAPA_GENES_EDGES
     // (mu+lambda) and roulette scratch
     int32_t* kids = nullptr;
     size_t kids_cap = 0;      // ints
@@ -167,6 +168,9 @@ struct gapa_ctx {
 };
 
 // Event pair around one launch when profiling is on (no-op otherwise).
+// Genes are drawn from [0, universe): n node ids, or E edge ids.
+inline int gapa_gene_universe(const gapa_ctx* c) { return c->genes ? c->g.num_edges : c->g.n; }
+
 struct ProfileScope {
     gapa_ctx* c;
     cudaStream_t st;

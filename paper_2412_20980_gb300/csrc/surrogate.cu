@@ -915,6 +915,7 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
     if (!out || !ctx || !scfg) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (ctx->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "no graph uploaded");
+    if (ctx->genes != GAPA_GENES_NODES) return gapa_fail(GAPA_ERR_INVALID_ARG, "the surrogate takes node genes only");
     if (scfg->batch < 16 || scfg->batch % 16 || scfg->ring < scfg->batch || scfg->train_steps < 0 ||
         scfg->screened < 1 || scfg->warmup < 0 || !(scfg->lr > 0.f) || scfg->target_mode < 0 ||
         scfg->target_mode > 1)

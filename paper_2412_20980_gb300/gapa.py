@@ -40,10 +40,11 @@ EXPORTS = [
     "gapa_batch_autotune", "gapa_batch_run",
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
     "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual", "gapa_offspring",
-    "gapa_set_objective",
+    "gapa_set_objective", "gapa_set_genes",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_SCAN = 0, 1, 2, 3, 4, 5
 OBJECTIVE_PC, OBJECTIVE_MCN = 0, 1
+GENES_NODES, GENES_EDGES = 0, 1
 
 
 class GapaError(RuntimeError):
@@ -173,6 +174,7 @@ def load(path: str | None = None):
             "gapa_profile_begin": ([V], U),
             "gapa_set_fitness_kernel": ([V, U], U),
             "gapa_set_objective": ([V, U], U),
+            "gapa_set_genes": ([V, U], U),
             "gapa_fitness_noalloc": ([U, V, I32, I32, V, V, I32, I32, V], U),
             "gapa_batch_create": ([ctypes.POINTER(V), I32, V, V], U),
             "gapa_batch_destroy": ([V], None),
@@ -387,6 +389,10 @@ class Context:
 
     def set_fitness_kernel(self, variant: int):
         _check(self.lib.gapa_set_fitness_kernel(self.handle, variant))
+
+    def set_genes(self, gene_type: int):
+        """GENES_NODES (node ids, the default) or GENES_EDGES (edge ids in CSR order of {u, v}, u < v)."""
+        _check(self.lib.gapa_set_genes(self.handle, gene_type))
 
     def set_objective(self, objective: int):
         """OBJECTIVE_PC (pairwise connectivity, the default) or OBJECTIVE_MCN (largest component)."""
