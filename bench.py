@@ -15,6 +15,11 @@ Other workloads (for the design notes, not the headline line):
   "small": one whole run (init + 100 generations, CUDA-graph replay) on
            BA n=1000, m=3, k = 50, s = 100; metric GA generations per second;
   "batched": 64 independent instances advanced by one batched run;
+  "sixdst": one GA generation under the SixDST objective (Eqs. 14-17: N = 6
+           hops, dense 0/1 reachability products on the tensor cores) on an
+           Erdos-Renyi n = 2018, E = 2705 graph (the size of the paper's
+           Yeast1), the paper's SixDST parameters (population 80, pc = 0.5,
+           pm = 0.3, k = 10 % of n);
   "surrogate": (mu+lambda) GA on BA n=100000, m=3, k = 2000, mu = 512,
            lambda = 2048, 300 generations, plain (every child exact) against
            surrogate-screened (top 512 children exact); metric: the plain
@@ -70,6 +75,10 @@ WORKLOADS = {
                            "rows per generation, lr 1e-3, on a 16384-row replay ring; targets z-scored among "
                            "siblings); value = median over the steps",
                       graphs=["ba_n100000_m3_seed1 (E=299991)"]),
+    "sixdst": dict(k=202, pop=80, gens=1, metric="SixDST fitness evals/s", unit="evals/s",
+                   desc="GA generation step under the SixDST objective (N = 6 hops) on ER(n=2018,E=2705), k=202, "
+                        "s=80, tournament 2, pc=0.5, pm=0.3, elitism 1",
+                   graphs=["er_n2018_e2705_seed1"]),
     "small": dict(k=50, pop=100, gens=100, metric="GA gens/s", unit="gens/s",
                   desc="whole GA run: init + 100 generations on BA(n=1000,m=3), k=50, s=100, tournament 2, "
                        "pc=0.8, pm=0.02, elitism 1, Philox seed 0",
@@ -98,6 +107,8 @@ def graphs(workload: str):
         return [synth.ba_graph(1000, 3, 1)]
     if workload == "surrogate":
         return [synth.ba_graph(100000, 3, 1)]
+    if workload == "sixdst":
+        return [synth.er_graph(2018, 2705, 1)]
     return [synth.ba_graph(20000, 4, 1), synth.hk_graph(20000, 4, 0.3, 1)]
 
 
@@ -208,6 +219,15 @@ def oracle_step_fn(wl: str, gs, s_ref: int):
     w = WORKLOADS[wl]
     pc_thr, pm_thr = oracle.thresholds(PC, PM)
     nt = oracle.max_threads()
+    if wl == "sixdst":  # the dense reference on the members of the initial population (the evaluations dominate)
+        from oracle import sixdst_ref
+
+        pop0 = oracle.pop_init(gs[0].n, w["k"], s_ref, 0)
+
+        def step(t):
+            sixdst_ref.fitness(gs[0].row_ptr, gs[0].col, pop0[: s_ref - 1])
+            return s_ref - 1
+        return step, nt
     if wl == "small":
         def step(t):
             oracle.run(gs[0].row_ptr, gs[0].col, k=w["k"], pop=s_ref, gens=w["gens"], tourn=TOURN, pc_thr=pc_thr,
@@ -232,6 +252,8 @@ def sample_population(wl: str, gs, seconds: float) -> int:
     w = WORKLOADS[wl]
     if wl == "small":
         return w["pop"]
+    if wl == "sixdst":  # about 0.6 s per dense evaluation
+        return max(2, min(w["pop"], int(seconds / 0.6) + 1))
     rows = min(4, w["pop"])
     pop = oracle.pop_init(gs[0].n, w["k"], rows, 0)
     t0 = time.perf_counter()
@@ -320,11 +342,16 @@ def run_gapa(args):
     if wl == "surrogate":
         return run_surrogate_bench(args, gs, dist, ws, rank, local, dev)
     k, pop = w["k"], w["pop"]
-    cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=PC, pm=PM, seed=gd.rank_seed(0, rank))
+    pc, pm = (0.5, 0.3) if wl == "sixdst" else (PC, PM)
+    cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=pc, pm=pm, seed=gd.rank_seed(0, rank))
     ctxs, state = [], []
     for g in gs:
         c = Context(local)
         c.graph_upload(g.row_ptr, g.col)
+        if wl == "sixdst":
+            from paper_2412_20980_gb300.gapa import OBJECTIVE_SIXDST_PC
+
+            c.set_objective(OBJECTIVE_SIXDST_PC)
         pa = c.pop_init(cfg)
         fa = c.fitness(pa)
         state.append([pa, fa, torch.empty_like(pa), torch.empty_like(fa)])
@@ -378,7 +405,21 @@ def run_gapa(args):
     fit_launches = sum(p["fitness_launches"] for p in profs)
     fit_evals = sum(p["evals"] for p in profs)
     roofline = None
-    if fit_launches:
+    if fit_launches and wl == "sixdst":
+        # tensor-bound: 3 dense products of n x n 0/1 matrices per evaluation ((A+I)^2, ^4, ^6)
+        flop = 3 * 2.0 * float(gs[0].n) ** 3
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+        peak = 2.0 * float(d["bf16_tflops"])
+        achieved = flop * fit_evals / (fit_ms / 1000.0) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "sdst_gemm_kernel (mma.sync m16n8k32 E4M3, FP32 accumulation)",
+                    "flop_per_eval": flop, "evals": fit_evals, "fitness_ms": fit_ms,
+                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json bf16_tflops) x 2, the FP8/BF16 nominal "
+                                   "ratio" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else
+                                   "fallback 1.9 PFLOP/s bf16 x 2",
+                    "fitness_share_of_step": fit_ms / max(1e-9, total_ms)}
+    elif fit_launches:
         beval = bytes_per_eval(gs[0].n, gs[0].num_edges, k)
         peak, peak_src = measured_peaks()
         avg_launch_s = fit_ms / 1000.0 / fit_launches

@@ -295,15 +295,24 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
 #define GAPA_FITNESS_TREE_SCAN 5
 int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
-/* Fitness objective of the context (both minimised; the end of Section III-C
+/* Fitness objective of the context (all minimised; the end of Section III-C
  * and the PC(G) and MCN rows of Table "Whole"): PC = pairwise connectivity
  * Σ C(|C|, 2) over the components C of G[V\D] (the default); MCN = maximum
  * connectivity number, the number of nodes of the largest component (0 when
- * every node is deleted).  Applies to gapa_fitness, the generation and run
- * calls and batches built from the context; gapa_fitness_noalloc computes PC. */
+ * every node is deleted).  SIXDST_PC / SIXDST_MCN: the same read from the
+ * dense accessibility matrix M = Normalizer((A + I)^N) of the perturbed
+ * adjacency matrix (Eqs. 14-17), N = gapa_set_sixdst_hops (default 6):
+ * with rowsum(v) = the live nodes within N hops of live v (itself included),
+ * PC_N = (Σ_live rowsum - live) / 2 and MCN_N = max_live rowsum, equal to PC
+ * and MCN once N reaches every component's diameter; node genes, n <= 8192,
+ * tensor-core products.  Applies to gapa_fitness and the generation and run
+ * calls (batches take PC and MCN); gapa_fitness_noalloc computes PC. */
 #define GAPA_OBJECTIVE_PC 0
 #define GAPA_OBJECTIVE_MCN 1
+#define GAPA_OBJECTIVE_SIXDST_PC 2
+#define GAPA_OBJECTIVE_SIXDST_MCN 3
 int gapa_set_objective(gapa_ctx* ctx, int objective);
+int gapa_set_sixdst_hops(gapa_ctx* ctx, int hops);
 
 /* Gene type of the context (Fig. 1: the gene pool holds nodes or edges; end
  * of Section III-A: both perturbations act on the adjacency matrix).  NODES

@@ -14,7 +14,8 @@ component.  From M:
 so that PC_N = PC and MCN_N = MCN once N reaches every component's diameter.
 N = 6 gives the paper's six-degrees-of-separation fitness.  This reference
 multiplies N - 1 times and normalises after every product (which leaves the
-boolean result of the whole power unchanged).
+boolean result of the whole power unchanged); the products run in float64,
+exact for 0/1 matrices (sums of at most n < 2^53 ones).
 """
 from __future__ import annotations
 
@@ -38,11 +39,11 @@ def perturbed_adjacency(row_ptr, col, genes) -> tuple[np.ndarray, np.ndarray]:
 def reachability(a: np.ndarray, hops: int) -> np.ndarray:
     """Normalizer((A + I)^hops) by hops - 1 products, normalised after each one."""
     n = a.shape[0]
-    base = np.minimum(a + np.eye(n, dtype=np.int64), 1)
+    base = np.minimum(a + np.eye(n, dtype=np.int64), 1).astype(np.float64)
     m = base.copy()
     for _ in range(hops - 1):
-        m = np.minimum(m @ base, 1)
-    return m
+        m = np.minimum(m @ base, 1.0)
+    return m.astype(np.int64)
 
 
 def sixdst_fitness(row_ptr, col, genes, hops: int = 6, objective: str = "pc") -> int:

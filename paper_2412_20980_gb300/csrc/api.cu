@@ -405,6 +405,7 @@ void gapa_destroy(gapa_ctx* c) {
     cudaFree(c->status);
     cudaFree(c->labels);
     cudaFree(c->ig_aux);
+    cudaFree(c->sdst_buf);
     for (auto p : c->stage_pop) cudaFree(p);
     for (auto p : c->stage_fit) cudaFree(p);
     cudaFree(c->run_gen);
@@ -765,9 +766,16 @@ int gapa_set_genes(gapa_ctx* c, int gene_type) {
 
 int gapa_set_objective(gapa_ctx* c, int objective) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
-    if (objective != GAPA_OBJECTIVE_PC && objective != GAPA_OBJECTIVE_MCN)
+    if (objective < GAPA_OBJECTIVE_PC || objective > GAPA_OBJECTIVE_SIXDST_MCN)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown objective %d", objective);
     c->objective = objective;
+    return GAPA_OK;
+}
+
+int gapa_set_sixdst_hops(gapa_ctx* c, int hops) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (hops < 1) return gapa_fail(GAPA_ERR_INVALID_ARG, "hops must be >= 1 (got %d)", hops);
+    c->sixdst_hops = hops;
     return GAPA_OK;
 }
 

@@ -229,6 +229,8 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         if (c->g.n <= 0) return gapa_fail(GAPA_ERR_STATE, "context %d has no graph", i);
         if (c->genes != GAPA_GENES_NODES)
             return gapa_fail(GAPA_ERR_INVALID_ARG, "instance %d: batched runs take node genes only", i);
+        if (c->objective != GAPA_OBJECTIVE_PC && c->objective != GAPA_OBJECTIVE_MCN)
+            return gapa_fail(GAPA_ERR_INVALID_ARG, "instance %d: batched runs take the PC or MCN objective", i);
         if (!c->g.packed16)
             return gapa_fail(GAPA_ERR_INVALID_ARG, "instance %d: batched runs need graphs whose labels fit in shared memory (n=%d)", i, c->g.n);
         const gapa_config& g = cfgs[i];

@@ -435,6 +435,10 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ga.join_mode = c->fitness_variant == GAPA_FITNESS_TREE_JOIN ? 1 : c->fitness_variant == GAPA_FITNESS_TREE_SCAN ? 2 : 0;
     ga.mean_deg_x16 = c->g.mean_deg_x16;
     ga.objective = c->objective;
+    if (c->objective == GAPA_OBJECTIVE_SIXDST_PC || c->objective == GAPA_OBJECTIVE_SIXDST_MCN) {
+        if (c->genes != GAPA_GENES_NODES) return gapa_fail(GAPA_ERR_INVALID_ARG, "SixDST objectives take node genes");
+        return gapa_launch_fitness_sixdst(c, pop, s, k, fit, st, &prof.kernels);
+    }
     if (c->genes == GAPA_GENES_EDGES) {
         const size_t bytes = edge_genes_smem(n, c->g.num_edges);
         if (bytes > c->fit_smem_max)

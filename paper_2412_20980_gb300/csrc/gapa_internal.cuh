@@ -144,6 +144,9 @@ struct gapa_ctx {
     int fitness_variant = 0;  // 0 = auto
     int objective = 0;        // GAPA_OBJECTIVE_PC or GAPA_OBJECTIVE_MCN
     int genes = 0;            // GAPA_GENES_NODES or GAPA_GENES_EDGES
+    int sixdst_hops = 6;      // N of the SixDST objectives
+    void* sdst_buf = nullptr;  // SixDST matrices and deletion bitmaps of a member batch
+    size_t sdst_cap = 0;
     // (mu+lambda) and roulette scratch
     int32_t* kids = nullptr;
     size_t kids_cap = 0;      // ints
@@ -252,6 +255,8 @@ size_t gapa_row_smem_bytes(int n, int k);
 int gapa_fitness_prepare(gapa_ctx* c, int s);  // allocate scratch before capture
 int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
                            int* kernels = nullptr);
+int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
+                               int* kernels = nullptr);
 int gapa_ig_prepare(gapa_ctx* c, int s);
 int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);
 int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,

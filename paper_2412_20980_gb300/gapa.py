@@ -40,10 +40,10 @@ EXPORTS = [
     "gapa_batch_autotune", "gapa_batch_run",
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
     "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual", "gapa_offspring",
-    "gapa_set_objective", "gapa_set_genes",
+    "gapa_set_objective", "gapa_set_genes", "gapa_set_sixdst_hops",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_SCAN = 0, 1, 2, 3, 4, 5
-OBJECTIVE_PC, OBJECTIVE_MCN = 0, 1
+OBJECTIVE_PC, OBJECTIVE_MCN, OBJECTIVE_SIXDST_PC, OBJECTIVE_SIXDST_MCN = 0, 1, 2, 3
 GENES_NODES, GENES_EDGES = 0, 1
 
 
@@ -175,6 +175,7 @@ def load(path: str | None = None):
             "gapa_set_fitness_kernel": ([V, U], U),
             "gapa_set_objective": ([V, U], U),
             "gapa_set_genes": ([V, U], U),
+            "gapa_set_sixdst_hops": ([V, U], U),
             "gapa_fitness_noalloc": ([U, V, I32, I32, V, V, I32, I32, V], U),
             "gapa_batch_create": ([ctypes.POINTER(V), I32, V, V], U),
             "gapa_batch_destroy": ([V], None),
@@ -395,8 +396,13 @@ class Context:
         _check(self.lib.gapa_set_genes(self.handle, gene_type))
 
     def set_objective(self, objective: int):
-        """OBJECTIVE_PC (pairwise connectivity, the default) or OBJECTIVE_MCN (largest component)."""
+        """OBJECTIVE_PC (pairwise connectivity, the default), OBJECTIVE_MCN (largest component), or their
+        N-hop SixDST forms OBJECTIVE_SIXDST_PC / OBJECTIVE_SIXDST_MCN (dense reachability, Eqs. 14-17)."""
         _check(self.lib.gapa_set_objective(self.handle, objective))
+
+    def set_sixdst_hops(self, hops: int):
+        """N of Normalizer((A + I)^N) for the SixDST objectives (default 6)."""
+        _check(self.lib.gapa_set_sixdst_hops(self.handle, hops))
 
     def profile_begin(self):
         _check(self.lib.gapa_profile_begin(self.handle))
