@@ -313,6 +313,13 @@ int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 #define GAPA_OBJECTIVE_SIXDST_MCN 3
 int gapa_set_objective(gapa_ctx* ctx, int objective);
 int gapa_set_sixdst_hops(gapa_ctx* ctx, int hops);
+/* Tensor-core path of the SixDST products (identical results): TCGEN05
+ * (tcgen05.mma with the accumulator in tensor memory, the default; a
+ * device-side wait that runs out is reported as GAPA_ERR_TIMEOUT) or MMA_SYNC
+ * (warp-level mma.sync). */
+#define GAPA_SIXDST_MMA_SYNC 0
+#define GAPA_SIXDST_TCGEN05 1
+int gapa_set_sixdst_kernel(gapa_ctx* ctx, int kernel);
 
 /* Gene type of the context (Fig. 1: the gene pool holds nodes or edges; end
  * of Section III-A: both perturbations act on the adjacency matrix).  NODES

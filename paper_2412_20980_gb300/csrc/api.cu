@@ -391,6 +391,7 @@ int gapa_create(gapa_ctx** out, int device, void* cuda_stream) {
     if (cudaMalloc(&c->run_gen, sizeof(int)) != cudaSuccess || cudaMalloc(&c->run_best, sizeof(int)) != cudaSuccess)
         return bail(gapa_fail(GAPA_ERR_OOM, "run counters"));
     int rc = gapa_fitness_kernels_init(c);
+    if (rc == GAPA_OK) rc = gapa_sixdst_init(c);
     if (rc == GAPA_OK) rc = gapa_ga_kernels_init(c);
     if (rc != GAPA_OK) return bail(rc);
     *out = c;
@@ -769,6 +770,16 @@ int gapa_set_objective(gapa_ctx* c, int objective) {
     if (objective < GAPA_OBJECTIVE_PC || objective > GAPA_OBJECTIVE_SIXDST_MCN)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown objective %d", objective);
     c->objective = objective;
+    return GAPA_OK;
+}
+
+int gapa_set_sixdst_kernel(gapa_ctx* c, int kernel) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (kernel != GAPA_SIXDST_MMA_SYNC && kernel != GAPA_SIXDST_TCGEN05)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown SixDST kernel %d", kernel);
+    if (kernel == GAPA_SIXDST_TCGEN05 && !c->sixdst_t5_ok)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "the tcgen05 product does not fit in this device's shared memory");
+    c->sixdst_kernel = kernel;
     return GAPA_OK;
 }
 

@@ -145,6 +145,8 @@ struct gapa_ctx {
     int objective = 0;        // GAPA_OBJECTIVE_PC or GAPA_OBJECTIVE_MCN
     int genes = 0;            // GAPA_GENES_NODES or GAPA_GENES_EDGES
     int sixdst_hops = 6;      // N of the SixDST objectives
+    int sixdst_kernel = 0;    // SixDST products: 0 = mma.sync, 1 = tcgen05 (the default when it fits)
+    bool sixdst_t5_ok = false;  // the tcgen05 product's shared memory fits on this device
     void* sdst_buf = nullptr;  // SixDST matrices and deletion bitmaps of a member batch
     size_t sdst_cap = 0;
     // (mu+lambda) and roulette scratch
@@ -257,6 +259,7 @@ int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_
                            int* kernels = nullptr);
 int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
                                int* kernels = nullptr);
+int gapa_sixdst_init(gapa_ctx* c);
 int gapa_ig_prepare(gapa_ctx* c, int s);
 int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);
 int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,

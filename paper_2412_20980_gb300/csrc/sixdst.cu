@@ -176,6 +176,194 @@ __global__ void __launch_bounds__(kThreads) sdst_gemm_kernel(const unsigned char
             }
 }
 
+// ---------------------------------------------------------------------------
+// The same product on the 5th-generation tensor cores: tcgen05.mma
+// kind::f8f6f4 (E4M3 x E4M3, FP32 accumulator in tensor memory), one elected
+// thread issuing, operands in shared memory in the canonical K-major layout
+// without swizzle (8-row x 16-byte core matrices; the next 16 bytes of K
+// 128 bytes on, the next 8 rows 1024 bytes on), 128-byte k chunks in three
+// stages filled by cp.async, each stage released by a tcgen05.commit on its
+// mbarrier.  Every wait is bounded: on expiry the kernel records
+// GAPA_DEV_TIMEOUT, still waits (bounded) for its own products and frees its
+// tensor memory.  A CTA of 4 warps owns one 128 x 128 tile; warp w reads
+// accumulator lanes 32w .. 32w + 31 (rows) back with tcgen05.ld.
+// ---------------------------------------------------------------------------
+constexpr int kT5Chunk = 128, kT5Stages = 3, kT5Threads = 128;
+constexpr int kT5StageBytes = kTile * kT5Chunk;  // 16 KB per operand per stage
+constexpr long long kT5SpinLimit = 1ll << 26;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// K-major, no-swizzle shared-memory matrix descriptor: start, leading (K) and
+// stride (8-row) byte offsets >> 4, descriptor version 1, layout type 0.
+__device__ __forceinline__ unsigned long long t5_desc(unsigned addr) {
+    const unsigned long long lbo = 128, sbo = 1024;
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFull) << 16) |
+           (((sbo >> 4) & 0x3FFFull) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: FP32 accumulator, A and B E4M3, both K-major, N = 128, M = 128
+constexpr unsigned kT5Idesc = (1u << 4) | ((unsigned)(kTile >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
+
+__device__ __forceinline__ bool t5_wait(unsigned bar, unsigned parity) {
+    for (long long i = 0; i < kT5SpinLimit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kT5Threads) sdst_gemm_t5_kernel(const unsigned char* __restrict__ X,
+                                                                  const unsigned char* __restrict__ Y,
+                                                                  unsigned char* __restrict__ C, int np, size_t mat,
+                                                                  int* status) {
+    extern __shared__ __align__(16) unsigned char t5_smem[];
+    unsigned char* sA = t5_smem;                                 // [stages][16 KB]
+    unsigned char* sB = t5_smem + kT5Stages * kT5StageBytes;     // [stages][16 KB]
+    __shared__ __align__(8) unsigned long long bars[kT5Stages];
+    __shared__ unsigned tmem_base;
+    __shared__ int failed;
+    const int T = np / kTile;
+    int ty = 0, rem = (int)blockIdx.x;
+    while (rem >= T - ty) {
+        rem -= T - ty;
+        ++ty;
+    }
+    const int tx = ty + rem;
+    const size_t off = (size_t)blockIdx.y * mat;
+    const unsigned char* x = X + off + (size_t)ty * kTile * np;
+    const unsigned char* y = Y + off + (size_t)tx * kTile * np;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        failed = 0;
+        for (int s = 0; s < kT5Stages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kTile)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    // chunk -> stage: 128 rows x 8 pieces of 16 bytes per operand, piece (row, q) at
+    // (row / 8) * 1024 + q * 128 + (row % 8) * 16
+    auto load = [&](int chunk) {
+        const int st = chunk % kT5Stages, k0 = chunk * kT5Chunk;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int piece = tid + r * kT5Threads, row = piece >> 3, q = piece & 7;
+            const int so = (row >> 3) * 1024 + q * 128 + (row & 7) * 16;
+            cp_async16(sA + st * kT5StageBytes + so, x + (size_t)row * np + k0 + q * 16);
+            cp_async16(sB + st * kT5StageBytes + so, y + (size_t)row * np + k0 + q * 16);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int chunks = np / kT5Chunk;
+    load(0);
+    if (chunks > 1) load(1);
+    int issued = -1;  // last chunk whose products were committed
+    for (int c = 0; c < chunks; ++c) {
+        const int st = c % kT5Stages;
+        if (c + 2 < chunks) {
+            // the stage of chunk c + 2 was last read by the products of chunk c - 1: one thread
+            // waits for them (bounded) and the verdict goes to all
+            if (c >= 1) {
+                if (tid == 0 &&
+                    !t5_wait(smem_u32(&bars[(c + 2) % kT5Stages]), (unsigned)(((c - 1) / kT5Stages) & 1)))
+                    failed = 1;
+                __syncthreads();
+                if (failed) break;
+            }
+            load(c + 2);
+            asm volatile("cp.async.wait_group 2;" ::: "memory");
+        } else if (c + 1 < chunks) {
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = smem_u32(sA + st * kT5StageBytes), b0 = smem_u32(sB + st * kT5StageBytes);
+#pragma unroll
+            for (int j = 0; j < kT5Chunk / 32; ++j) {
+                const unsigned long long da = t5_desc(a0 + 256u * j), db = t5_desc(b0 + 256u * j);
+                const unsigned acc = (c > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                    ::"r"(tmem), "l"(da), "l"(db), "r"(kT5Idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[st]))
+                         : "memory");
+        }
+        issued = c;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the last commit covers every product issued before it; one thread waits (bounded)
+    if (tid == 0 && issued >= 0 && !t5_wait(smem_u32(&bars[issued % kT5Stages]), (unsigned)((issued / kT5Stages) & 1)))
+        failed = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, GAPA_DEV_TIMEOUT);
+            // the products in flight must end before their tensor memory is freed: wait once more (bounded)
+            if (issued >= 0) t5_wait(smem_u32(&bars[issued % kT5Stages]), (unsigned)((issued / kT5Stages) & 1));
+        }
+    } else {
+        unsigned char* c = C + off;
+        const int row = ty * kTile + warp * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < kTile / 32; ++q) {
+            unsigned v[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(q * 32)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            unsigned w[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                unsigned word = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    word |= (__uint_as_float(v[4 * b + e]) > 0.5f ? (unsigned)kOne : 0u) << (8 * e);
+                w[b] = word;
+            }
+            const int col0 = tx * kTile + q * 32;
+            uint4* dst = reinterpret_cast<uint4*>(c + (size_t)row * np + col0);
+            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            if (tx != ty)  // the mirrored tile below the diagonal: column -> row
+#pragma unroll
+                for (int e = 0; e < 32; ++e) c[(size_t)(col0 + e) * np + row] = (unsigned char)(w[e >> 2] >> (8 * (e & 3)));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile) : "memory");
+}
+
 // per member: the live rows' non-zero counts, then PC_N (sum) or MCN_N (max)
 __global__ void __launch_bounds__(256) sdst_objective_kernel(const unsigned char* __restrict__ M, int n, int np,
                                                              size_t mat, int words, const unsigned* __restrict__ dead,
@@ -217,6 +405,15 @@ __global__ void __launch_bounds__(256) sdst_objective_kernel(const unsigned char
 
 }  // namespace
 
+int gapa_sixdst_init(gapa_ctx* c) {
+    const int bytes = 2 * kT5Stages * kT5StageBytes;
+    if ((size_t)bytes + 1024 > c->smem_optin) return GAPA_OK;  // the tcgen05 product stays unavailable
+    GAPA_CUDA(cudaFuncSetAttribute(sdst_gemm_t5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    c->sixdst_t5_ok = true;
+    c->sixdst_kernel = 1;
+    return GAPA_OK;
+}
+
 int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
                                int* kernels) {
     const int n = c->g.n;
@@ -243,6 +440,14 @@ int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, in
         int base = 0, res = -1;
         const int tiles = np / kTile;
         const dim3 grid(tiles * (tiles + 1) / 2, bm);
+        const bool t5 = c->sixdst_kernel == 1;
+        auto launch_gemm = [&](const unsigned char* xa, const unsigned char* yb, unsigned char* cc) {
+            if (t5)
+                sdst_gemm_t5_kernel<<<grid, kT5Threads, 2 * kT5Stages * kT5StageBytes, st>>>(xa, yb, cc, np, mat,
+                                                                                             c->status);
+            else
+                sdst_gemm_kernel<<<grid, kThreads, 0, st>>>(xa, yb, cc, np, mat);
+        };
         auto free_buf = [&](int a, int b) {
             for (int i = 0; i < 3; ++i)
                 if (i != a && i != b) return i;
@@ -254,14 +459,14 @@ int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, in
                     res = base;
                 } else {
                     const int dst = free_buf(res, base);
-                    sdst_gemm_kernel<<<grid, kThreads, 0, st>>>(buf[res], buf[base], buf[dst], np, mat);
+                    launch_gemm(buf[res], buf[base], buf[dst]);
                     ++launched;
                     res = dst;
                 }
             }
             if (e > 1) {
                 const int dst = free_buf(res, base);
-                sdst_gemm_kernel<<<grid, kThreads, 0, st>>>(buf[base], buf[base], buf[dst], np, mat);
+                launch_gemm(buf[base], buf[base], buf[dst]);
                 ++launched;
                 base = dst;
             }

@@ -10,8 +10,8 @@ from oracle import sixdst_ref as sx
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["mma_sync", "tcgen05"])
+def ctx(request):
     import torch
 
     from paper_2412_20980_gb300 import Context
@@ -19,6 +19,7 @@ def ctx():
 
     b.build()
     c = Context(0)
+    c.set_sixdst_kernel({"mma_sync": 0, "tcgen05": 1}[request.param])
     yield c
     torch.cuda.synchronize()
     c.close()
