@@ -321,6 +321,13 @@ int gapa_set_sixdst_hops(gapa_ctx* ctx, int hops);
 #define GAPA_SIXDST_TCGEN05 1
 int gapa_set_sixdst_kernel(gapa_ctx* ctx, int kernel);
 
+/* Failure-path check of the device-side bounded waits (the paper has no
+ * counterpart): one thread waits at most spin_limit polls (1 .. 2^26) on an
+ * mbarrier that nothing completes - the wait the tcgen05 products use - and
+ * records the timeout; returns GAPA_ERR_TIMEOUT, after which the context stays
+ * usable.  Synchronous. */
+int gapa_selftest_wait(gapa_ctx* ctx, int64_t spin_limit);
+
 /* Gene type of the context (Fig. 1: the gene pool holds nodes or edges; end
  * of Section III-A: both perturbations act on the adjacency matrix).  NODES
  * (the default): genes are node ids in [0, n), deleting a node removes its

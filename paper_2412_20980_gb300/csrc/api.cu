@@ -773,6 +773,15 @@ int gapa_set_objective(gapa_ctx* c, int objective) {
     return GAPA_OK;
 }
 
+int gapa_selftest_wait(gapa_ctx* c, int64_t spin_limit) {
+    if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
+    if (spin_limit < 1 || spin_limit > (1LL << 26)) return gapa_fail(GAPA_ERR_INVALID_ARG, "spin limit out of range");
+    DeviceGuard guard(c->device);
+    int rc = gapa_launch_selftest_wait(c, (long long)spin_limit, c->stream);
+    if (rc != GAPA_OK) return rc;
+    return read_status(c, c->stream);
+}
+
 int gapa_set_sixdst_kernel(gapa_ctx* c, int kernel) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
     if (kernel != GAPA_SIXDST_MMA_SYNC && kernel != GAPA_SIXDST_TCGEN05)

@@ -205,8 +205,8 @@ __device__ __forceinline__ unsigned long long t5_desc(unsigned addr) {
 // instruction descriptor: FP32 accumulator, A and B E4M3, both K-major, N = 128, M = 128
 constexpr unsigned kT5Idesc = (1u << 4) | ((unsigned)(kTile >> 3) << 17) | ((unsigned)(kTile >> 4) << 24);
 
-__device__ __forceinline__ bool t5_wait(unsigned bar, unsigned parity) {
-    for (long long i = 0; i < kT5SpinLimit; ++i) {
+__device__ __forceinline__ bool t5_wait(unsigned bar, unsigned parity, long long limit = kT5SpinLimit) {
+    for (long long i = 0; i < limit; ++i) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -364,6 +364,17 @@ __global__ void __launch_bounds__(kT5Threads) sdst_gemm_t5_kernel(const unsigned
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile) : "memory");
 }
 
+// The bounded wait on an mbarrier that nothing completes: it must run out and
+// report GAPA_DEV_TIMEOUT (gapa_selftest_wait).
+__global__ void t5_selftest_kernel(long long limit, int* status) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!t5_wait(smem_u32(&bar), 0u, limit)) atomicOr(status, GAPA_DEV_TIMEOUT);
+    }
+}
+
 // per member: the live rows' non-zero counts, then PC_N (sum) or MCN_N (max)
 __global__ void __launch_bounds__(256) sdst_objective_kernel(const unsigned char* __restrict__ M, int n, int np,
                                                              size_t mat, int words, const unsigned* __restrict__ dead,
@@ -404,6 +415,12 @@ __global__ void __launch_bounds__(256) sdst_objective_kernel(const unsigned char
 }
 
 }  // namespace
+
+int gapa_launch_selftest_wait(gapa_ctx* c, long long limit, cudaStream_t st) {
+    t5_selftest_kernel<<<1, 32, 0, st>>>(limit, c->status);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
 
 int gapa_sixdst_init(gapa_ctx* c) {
     const int bytes = 2 * kT5Stages * kT5StageBytes;

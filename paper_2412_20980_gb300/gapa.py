@@ -40,7 +40,7 @@ EXPORTS = [
     "gapa_batch_autotune", "gapa_batch_run",
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
     "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual", "gapa_offspring",
-    "gapa_set_objective", "gapa_set_genes", "gapa_set_sixdst_hops", "gapa_set_sixdst_kernel",
+    "gapa_set_objective", "gapa_set_genes", "gapa_set_sixdst_hops", "gapa_set_sixdst_kernel", "gapa_selftest_wait",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_SCAN = 0, 1, 2, 3, 4, 5
 OBJECTIVE_PC, OBJECTIVE_MCN, OBJECTIVE_SIXDST_PC, OBJECTIVE_SIXDST_MCN = 0, 1, 2, 3
@@ -177,6 +177,7 @@ def load(path: str | None = None):
             "gapa_set_genes": ([V, U], U),
             "gapa_set_sixdst_hops": ([V, U], U),
             "gapa_set_sixdst_kernel": ([V, U], U),
+            "gapa_selftest_wait": ([V, I64], U),
             "gapa_fitness_noalloc": ([U, V, I32, I32, V, V, I32, I32, V], U),
             "gapa_batch_create": ([ctypes.POINTER(V), I32, V, V], U),
             "gapa_batch_destroy": ([V], None),
@@ -400,6 +401,11 @@ class Context:
         """OBJECTIVE_PC (pairwise connectivity, the default), OBJECTIVE_MCN (largest component), or their
         N-hop SixDST forms OBJECTIVE_SIXDST_PC / OBJECTIVE_SIXDST_MCN (dense reachability, Eqs. 14-17)."""
         _check(self.lib.gapa_set_objective(self.handle, objective))
+
+    def selftest_wait(self, spin_limit: int = 1 << 16) -> int:
+        """Runs a bounded device-side wait that must time out; returns the library's status code
+        (GAPA_ERR_TIMEOUT = -5 expected) without raising."""
+        return int(self.lib.gapa_selftest_wait(self.handle, spin_limit))
 
     def set_sixdst_kernel(self, kernel: int):
         """0: mma.sync products (default), 1: tcgen05 products (same results)."""

@@ -91,3 +91,16 @@ def test_sixdst_run_and_limits(ctx):
             ctx.fitness(torch.zeros((2, 3), dtype=torch.int32, device="cuda"))
     finally:
         ctx.set_objective(OBJECTIVE_PC)
+
+
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    """The device-side wait of the tcgen05 products on a barrier that nothing completes runs out,
+    is reported as a timeout, and the context keeps working."""
+    from paper_2412_20980_gb300.gapa import OBJECTIVE_PC
+
+    assert ctx.selftest_wait(1 << 12) == -5  # GAPA_ERR_TIMEOUT
+    g = synth.ba_graph(400, 2, 8)
+    ctx.graph_upload(g.row_ptr, g.col)
+    ctx.set_objective(OBJECTIVE_PC)
+    pop = synth.random_deletion_sets(g.n, 20, 4, 1)
+    assert np.array_equal(ctx.fitness_host(pop), oracle.fitness(g.row_ptr, g.col, pop))
