@@ -22,7 +22,7 @@ Other workloads (for the design notes, not the headline line):
            pm = 0.3, k = 10 % of n);
   "surrogate": (mu+lambda) GA on BA n=100000, m=3, k = 2000, mu = 512,
            lambda = 2048, 300 generations, plain (every child exact) against
-           surrogate-screened (top 512 children exact); metric: the plain
+           surrogate-screened (top 256 children exact); metric: the plain
            run's time to its final best over the screened run's time to reach
            that same value (the screened run may take up to 600 generations);
            the 1.01 x tolerance is reported beside it.
@@ -66,14 +66,14 @@ WORKLOADS = {
                          "k = round(0.05 n), populations from {32,64,128,256,512}, 200 generations each, "
                          "one batched run per step (CUDA-graph replay, persistent fitness kernel, autotuned teams)",
                     graphs=["64 BA instances (synth.batched_instances, seed 0)"]),
-    "surrogate": dict(k=2000, pop=512, lam=2048, screened=512, gens=300,
+    "surrogate": dict(k=2000, pop=512, lam=2048, screened=256, gens=300,
                       metric="surrogate vs plain GA time-to-target speedup", unit="x",
                       desc="(mu+lambda) GA on BA(n=100000,m=3), k=2000, mu=512, lambda=2048 children per generation, "
                            "tournament 2, pc=0.8, pm=0.02, 300 generations; one step = one GA seed "
                            "(1000 rank + step) run both ways: plain (all 2048 children exact) vs surrogate-screened "
-                           "(the 512 lowest-scored children exact after 3 warm-up generations; 4 AdamW steps of 512 "
-                           "rows per generation, lr 1e-3, on a 16384-row replay ring; targets z-scored among "
-                           "siblings); value = median over the steps",
+                           "(the 256 lowest-scored children exact after 3 warm-up generations; 2 AdamW steps of 512 "
+                           "rows per generation, lr 1e-3, on a 16384-row replay ring; targets z-scored over the "
+                           "ring); value = median over the steps",
                       graphs=["ba_n100000_m3_seed1 (E=299991)"]),
     "sixdst": dict(k=202, pop=80, gens=1, metric="SixDST fitness evals/s", unit="evals/s",
                    desc="GA generation step under the SixDST objective (N = 6 hops) on ER(n=2018,E=2705), k=202, "
@@ -605,8 +605,8 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
                            flags=FLAG_MU_PLUS_LAMBDA, lam=lam)
 
     def scfg(diag_every=0):
-        return make_surrogate_config(screened=w["screened"], warmup=3, train_steps=4, batch=512, ring=16384,
-                                     lr=1e-3, init_scale_emb=0.01, target_mode=1, diag_every=diag_every)
+        return make_surrogate_config(screened=w["screened"], warmup=3, train_steps=2, batch=512, ring=16384,
+                                     lr=1e-3, init_scale_emb=0.01, target_mode=0, diag_every=diag_every)
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     for t in range(args.warmup):  # short runs of both kinds: module load, allocations, autotuned limits

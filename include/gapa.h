@@ -209,7 +209,10 @@ int gapa_batch_run(gapa_batch* batch, int32_t gens, int64_t* best_fit, int32_t* 
  * and standard deviation of log1p(degree) over D and sum(degree)/(2E), then
  * log1p(r0), log1p(r1) and log1p(r2): the numbers of live neighbours of D
  * that G[V\D] leaves with no live neighbour and with exactly one, and the
- * number of two-node components of G[V\D] adjacent to D; then zeros.
+ * number of two-node components of G[V\D] adjacent to D; then the same three
+ * counts standardised over the rows scored together ((r_j - mean_j) /
+ * max(sd_j, 1), population statistics over the rows of one predict or
+ * training call, or of one generation's children); then zeros.
  * Model: 80 -> 256 ReLU -> 256 ReLU -> 1, BF16 weights on the tensor
  * cores with FP32 accumulation; FP32 master weights, AdamW (Loshchilov &
  * Hutter) on every parameter, MSE against the z-scored log1p of the exact
@@ -240,7 +243,8 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
 void gapa_surrogate_destroy(gapa_surrogate* sg);
 
 /* scores_dev[r] = model output for row r of pop_dev[rows][k].  Asynchronous.
- * Genes outside [0, n) are ignored by the features. */
+ * Genes outside [0, n) are ignored by the features.  The standardised counts
+ * make a score relative to the other rows of the same call. */
 int gapa_surrogate_predict(gapa_surrogate* sg, const int32_t* pop_dev, int32_t rows, int32_t k, float* scores_dev);
 
 /* Residual counts of the rows of pop_dev[rows][k]: counts_dev[3r .. 3r+2] =

@@ -13,13 +13,20 @@ Section III-C.  Definition shared with the CUDA implementation:
     r1    = #{u : some neighbour in D, exactly one live one}   (made pendant by the deletion)
     r2    = #{components of G[V - D] of exactly two nodes, one of them adjacent to D}
     f5    = log1p(r0),  f6 = log1p(r1),  f7 = log1p(r2)
-    x     = [e(D), f1, f2, f3, f4, f5, f6, f7, 0 x 9]              (80 values)
+    z_j   = (r_j - m_j) / max(s_j, 1) for j = 0, 1, 2, where m_j and s_j are the
+            mean and the population standard deviation of r_j over the rows
+            scored together (one generation's children, or one training
+            batch), so that z compares a child with its siblings
+    x     = [e(D), f1, f2, f3, f4, f5, f6, f7, z0, z1, z2, 0 x 6]  (80 values)
 
   On sparse graphs most children of one generation share the giant
   component's size up to a few nodes that the deletion isolates, so their
   pairwise connectivity is ordered by r0 and r2 (an isolated node removes
   about n pairs from the giant component, an isolated pair about 2n); r1
-  counts the nodes one more deletion would isolate.
+  counts the nodes one more deletion would isolate.  The counts drift upward
+  over a run while the differences between siblings stay a few units, so the
+  log1p values squeeze those differences late in a run; z keeps them at a
+  fixed scale, matching the sibling-relative training target.
   model   z1 = x W1 + b1, h1 = relu(z1)   (W1: 80 x 256)
           z2 = h1 W2 + b2, h2 = relu(z2)  (W2: 256 x 256)
           y  = h2 . w3 + b3
@@ -72,6 +79,7 @@ def features(pop: np.ndarray, E: np.ndarray, row_ptr, col) -> np.ndarray:
     num_edges = np.asarray(col).size // 2
     x = np.zeros((s, IN), dtype=np.float64)
     q = np.log1p(deg)
+    counts = np.zeros((s, 3), dtype=np.int64)
     for i in range(s):
         genes = pop[i]
         x[i, :EMB] = E[genes].sum(axis=0) / np.sqrt(k)
@@ -82,10 +90,29 @@ def features(pop: np.ndarray, E: np.ndarray, row_ptr, col) -> np.ndarray:
         x[i, 66] = np.sqrt(max((qi * qi).mean() - f1 * f1, 0.0))
         x[i, 67] = deg[genes].sum() / (2.0 * num_edges)
         r0, r1, r2 = residual_degree_counts(row_ptr, col, genes)
+        counts[i] = (r0, r1, r2)
         x[i, 68] = np.log1p(r0)
         x[i, 69] = np.log1p(r1)
         x[i, 70] = np.log1p(r2)
+    x[:, 71:74] = standardised_counts(counts)
     return x
+
+
+def standardised_counts(counts: np.ndarray) -> np.ndarray:
+    """z_j = (r_j - mean_j) / max(sd_j, 1) per column of counts (int[s][3]), the mean and the
+    population standard deviation taken over the s rows; float32 values, as the model reads them."""
+    counts = np.asarray(counts, dtype=np.int64)
+    z = np.zeros(counts.shape, dtype=np.float64)
+    rows = counts.shape[0]
+    if rows == 0:
+        return z
+    for j in range(counts.shape[1]):
+        c = counts[:, j]
+        mean = float(c.sum()) / rows
+        var = float((c * c).sum()) / rows - mean * mean
+        sd = max(np.sqrt(max(var, 0.0)), 1.0)
+        z[:, j] = ((c - mean) / sd).astype(np.float32)
+    return z
 
 
 def forward(params: dict, x: np.ndarray) -> tuple[np.ndarray, dict]:

@@ -198,6 +198,14 @@ __device__ __forceinline__ int live_upto2(const unsigned* bm, const int4* __rest
     return live;
 }
 
+// One row's residual-degree counts c = (r0, r1, r2, 0) and their
+// standardised values z = ((r_j - mean_j) / max(sd_j, 1), 0) over the rows
+// computed together (mean and population standard deviation of each count).
+struct __align__(16) ResidRow {
+    int4 c;
+    float4 z;
+};
+
 // (u live) -> +1 to c0 or c1 when u has at most one live neighbour and v is its
 // first deleted one; +1 to c2 when that neighbour closes a two-node component.
 // Most live u keep their first two neighbours: one 16-byte table read settles them.
@@ -218,7 +226,7 @@ __device__ __forceinline__ void resid_pair(const unsigned* bm, const int4* __res
 
 __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop, int rows, int k, int n,
                                                     const int4* __restrict__ T, const int* __restrict__ col,
-                                                    int4* __restrict__ out) {
+                                                    ResidRow* __restrict__ out) {
     extern __shared__ unsigned bm[];
     __shared__ int red[3][8];
     const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -295,7 +303,52 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
             y += red[1][w];
             z += red[2][w];
         }
-        out[r] = make_int4(x, y, z, 0);
+        out[r].c = make_int4(x, y, z, 0);
+    }
+}
+
+// z of `rows` residual records from their counts (one CTA, exact int64 sums,
+// then FP64 in a fixed order with explicit rounding: mean = S1 / rows,
+// var = S2 / rows - mean^2, sd = max(sqrt(var), 1), z = float((c - mean) / sd)).
+__global__ void __launch_bounds__(256) resid_stats_kernel(ResidRow* __restrict__ r, int rows) {
+    __shared__ long long s1[3][256], s2[3][256];
+    long long a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const int4 c = r[i].c;
+        const long long v[3] = {c.x, c.y, c.z};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            a[j] += v[j];
+            b[j] += v[j] * v[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        s1[j][threadIdx.x] = a[j];
+        s2[j][threadIdx.x] = b[j];
+    }
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                s1[j][threadIdx.x] += s1[j][threadIdx.x + w];
+                s2[j][threadIdx.x] += s2[j][threadIdx.x + w];
+            }
+        __syncthreads();
+    }
+    double mean[3], sd[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        mean[j] = __ddiv_rn((double)s1[j][0], (double)rows);
+        const double var = __dsub_rn(__ddiv_rn((double)s2[j][0], (double)rows), __dmul_rn(mean[j], mean[j]));
+        sd[j] = fmax(__dsqrt_rn(fmax(var, 0.0)), 1.0);
+    }
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const int4 c = r[i].c;
+        r[i].z = make_float4(__double2float_rn(__ddiv_rn(__dsub_rn((double)c.x, mean[0]), sd[0])),
+                             __double2float_rn(__ddiv_rn(__dsub_rn((double)c.y, mean[1]), sd[1])),
+                             __double2float_rn(__ddiv_rn(__dsub_rn((double)c.z, mean[2]), sd[2])), 0.f);
     }
 }
 
@@ -305,7 +358,7 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
 __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ pop, int rows, int k, int n,
                                                        const bf16* __restrict__ Eb, const float* __restrict__ logdeg,
                                                        const float* __restrict__ deg, float inv2E, float invsqrtk,
-                                                       const int4* __restrict__ resid, bf16* __restrict__ X,
+                                                       const ResidRow* __restrict__ resid, bf16* __restrict__ X,
                                                        bf16* __restrict__ XT, int rows_pad) {
     __shared__ float2 part[4][32];
     __shared__ float st[4][4];
@@ -388,9 +441,12 @@ __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ p
         if (t == 65) f = k > 0 ? QM : 0.f;
         if (t == 66) f = k > 0 ? sqrtf(fmaxf(Q2 / k - mean * mean, 0.f)) : 0.f;
         if (t == 67) f = DS * inv2E;
-        if (t == 68) f = log1pf((float)resid[r].x);
-        if (t == 69) f = log1pf((float)resid[r].y);
-        if (t == 70) f = log1pf((float)resid[r].z);
+        if (t == 68) f = log1pf((float)resid[r].c.x);
+        if (t == 69) f = log1pf((float)resid[r].c.y);
+        if (t == 70) f = log1pf((float)resid[r].c.z);
+        if (t == 71) f = resid[r].z.x;
+        if (t == 72) f = resid[r].z.y;
+        if (t == 73) f = resid[r].z.z;
         X[(size_t)r * kIn + t] = __float2bfloat16(f);
         XT[(size_t)t * rows_pad + r] = __float2bfloat16(f);
     }
@@ -596,8 +652,8 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ sc
 
 // dst row r = src row idx[r] (idx may be null: identity), k genes, with its
 // residual-degree counts; dst_cap > 0 writes ring slots (dst_first + r) mod dst_cap.
-__global__ void gather_rows_kernel(const int* __restrict__ src, const int4* __restrict__ rsrc,
-                                   const int* __restrict__ idx, int k, int* __restrict__ dst, int4* __restrict__ rdst,
+__global__ void gather_rows_kernel(const int* __restrict__ src, const ResidRow* __restrict__ rsrc,
+                                   const int* __restrict__ idx, int k, int* __restrict__ dst, ResidRow* __restrict__ rdst,
                                    int dst_first, int dst_cap) {
     const int r = blockIdx.x;
     const int from = idx ? idx[r] : r;
@@ -681,10 +737,10 @@ __global__ void __launch_bounds__(1024) target_stats_kernel(const double* __rest
 
 // Minibatch: rows drawn uniformly from the valid ring entries (Philox tag 8,
 // counter (b, step, g, 8 << 24 | 1)), targets z-scored.
-__global__ void batch_kernel(const int* __restrict__ ring, const int4* __restrict__ ring_resid,
+__global__ void batch_kernel(const int* __restrict__ ring, const ResidRow* __restrict__ ring_resid,
                              const double* __restrict__ ring_lp, int valid, int k, int B, RngKey key, int step,
                              int g, const double* __restrict__ stats, int* __restrict__ rows,
-                             int4* __restrict__ resid, float* __restrict__ t) {
+                             ResidRow* __restrict__ resid, float* __restrict__ t) {
     const int b = blockIdx.x;
     const int idx = uniform_below(philox_word0((uint32_t)b, (uint32_t)step, (uint32_t)g, (8u << 24) | 1u, key.lo, key.hi),
                                   valid);
@@ -724,7 +780,7 @@ struct gapa_surrogate {
     bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
          *dZ1 = nullptr, *dZ1T = nullptr;
     float *y = nullptr, *dy = nullptr, *dX = nullptr, *loss = nullptr, *tbuf = nullptr;
-    int4* resid = nullptr;       // residual-degree counts of the rows of the last forward
+    ResidRow* resid = nullptr;   // residual-degree counts (and their z) of the rows of the last forward
     int4* nbr = nullptr;         // per node: first arc, degree, first two neighbours
     const int* row_ptr = nullptr;  // the context's CSR (original node ids)
     const int* col = nullptr;
@@ -767,11 +823,12 @@ int refresh_bf16(gapa_surrogate* s, cudaStream_t st) {
 int round16(int x) { return (x + 15) & ~15; }
 
 // Features + forward; keeps the transposed copies for a training step.
-// Residual-degree counts of `rows` deletion sets into s->resid.
+// Residual-degree counts of `rows` deletion sets into s->resid, standardised over those rows.
 int compute_resid(gapa_surrogate* s, const int32_t* pop, int rows, int k, cudaStream_t st) {
     if (rows <= 0) return GAPA_OK;
-    ProfileScope prof(s->ctx, st, 2, 1);
+    ProfileScope prof(s->ctx, st, 2, 2);
     resid_kernel<<<rows, 256, s->resid_smem, st>>>(pop, rows, k, s->n, s->nbr, s->col, s->resid);
+    resid_stats_kernel<<<1, 256, 0, st>>>(s->resid, rows);
     GAPA_CUDA(cudaGetLastError());
     return GAPA_OK;
 }
@@ -779,7 +836,7 @@ int compute_resid(gapa_surrogate* s, const int32_t* pop, int rows, int k, cudaSt
 // Features + forward; keeps the transposed copies for a training step.  With
 // resid == nullptr the residual-degree counts are computed into s->resid first.
 int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, cudaStream_t st,
-            const int4* resid = nullptr) {
+            const ResidRow* resid = nullptr) {
     if (!resid) {
         int rc = compute_resid(s, pop, rows, k, st);
         if (rc != GAPA_OK) return rc;
@@ -814,7 +871,7 @@ int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, c
 
 // One AdamW step on a batch (rows a multiple of 16) with targets t.
 int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float* t, cudaStream_t st,
-               const int4* resid = nullptr) {
+               const ResidRow* resid = nullptr) {
     int rc = forward(s, pop, B, k, true, st, resid);
     if (rc != GAPA_OK) return rc;
     ProfileScope prof(s->ctx, st, 2, 13);
@@ -885,7 +942,7 @@ int ensure_rows(gapa_surrogate* s, int rows) {
         cudaMalloc(&s->H1T, e256 * 2) || cudaMalloc(&s->H2, e256 * 2) || cudaMalloc(&s->dZ2, e256 * 2) ||
         cudaMalloc(&s->dZ2T, e256 * 2) || cudaMalloc(&s->dZ1, e256 * 2) || cudaMalloc(&s->dZ1T, e256 * 2) ||
         cudaMalloc(&s->y, (size_t)R * 4) || cudaMalloc(&s->dy, (size_t)R * 4) || cudaMalloc(&s->dX, e80 * 4) ||
-        cudaMalloc(&s->tbuf, (size_t)R * 4) || cudaMalloc(&s->resid, (size_t)R * sizeof(int4))) {
+        cudaMalloc(&s->tbuf, (size_t)R * 4) || cudaMalloc(&s->resid, (size_t)R * sizeof(ResidRow))) {
         cudaGetLastError();
         return gapa_fail(GAPA_ERR_OOM, "surrogate activations for %d rows", R);
     }
@@ -1023,7 +1080,7 @@ int gapa_surrogate_residual(gapa_surrogate* s, const int32_t* pop_dev, int32_t r
     if (rc == GAPA_OK) rc = ensure_rows(s, rows);
     if (rc == GAPA_OK) rc = compute_resid(s, pop_dev, rows, k, s->ctx->stream);
     if (rc != GAPA_OK) return rc;
-    GAPA_CUDA(cudaMemcpy2DAsync(counts_dev, 3 * sizeof(int32_t), s->resid, sizeof(int4), 3 * sizeof(int32_t),
+    GAPA_CUDA(cudaMemcpy2DAsync(counts_dev, 3 * sizeof(int32_t), s->resid, sizeof(ResidRow), 3 * sizeof(int32_t),
                                 (size_t)rows, cudaMemcpyDeviceToDevice, s->ctx->stream));
     return GAPA_OK;
 }
@@ -1095,7 +1152,7 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     int64_t* fsel = nullptr;
     double* ring_lp = nullptr;  // log1p(exact fitness) of every ring row (mode 1: its sibling z-score)
     double* gstats = nullptr;   // (mean, std) of log1p(fitness) over the last appended generation
-    int4 *ring_resid = nullptr, *sel_resid = nullptr, *batch_resid = nullptr;
+    ResidRow *ring_resid = nullptr, *sel_resid = nullptr, *batch_resid = nullptr;
     float* scores = nullptr;
     const int ring_cap = s ? s->cfg.ring : 0;
     auto cleanup = [&]() {
@@ -1115,9 +1172,9 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
         cudaMalloc(&fsel, (size_t)lam * 8) || cudaMalloc(&scores, (size_t)lam * 4) ||
         (s && (cudaMalloc(&ring, (size_t)ring_cap * k * 4 + 4) || cudaMalloc(&ring_lp, (size_t)ring_cap * 8) || cudaMalloc(&gstats, 16) ||
                cudaMalloc(&batch_rows, (size_t)s->cfg.batch * k * 4 + 4) ||
-               cudaMalloc(&ring_resid, (size_t)ring_cap * sizeof(int4)) ||
-               cudaMalloc(&sel_resid, (size_t)lam * sizeof(int4)) ||
-               cudaMalloc(&batch_resid, (size_t)s->cfg.batch * sizeof(int4))))) {
+               cudaMalloc(&ring_resid, (size_t)ring_cap * sizeof(ResidRow)) ||
+               cudaMalloc(&sel_resid, (size_t)lam * sizeof(ResidRow)) ||
+               cudaMalloc(&batch_resid, (size_t)s->cfg.batch * sizeof(ResidRow))))) {
         cudaGetLastError();
         cleanup();
         return gapa_fail(GAPA_ERR_OOM, "surrogate run buffers");

@@ -57,6 +57,22 @@ def test_features_closed_forms():
     assert np.all(x[71:] == 0)
 
 
+def test_standardised_counts_closed_forms():
+    z = sr.standardised_counts([[0, 3, 7], [2, 3, 7]])  # r0: mean 1, sd 1; r1, r2 constant
+    assert z[:, 0].tolist() == [-1.0, 1.0] and np.all(z[:, 1:] == 0)
+    z = sr.standardised_counts([[0, 0, 0], [0, 0, 0], [0, 0, 0], [1, 0, 0]])  # sd 0.433 < 1: divided by 1
+    assert z[:, 0].tolist() == [-0.25, -0.25, -0.25, 0.75]
+    z = sr.standardised_counts([[0, 0, 0], [10, 0, 0]])  # mean 5, sd 5
+    assert z[:, 0].tolist() == [-1.0, 1.0]
+    # features standardise over the rows passed together: star with centre 0 and 5 leaves
+    g = synth.named_graph("star", 6)
+    x = sr.features(np.array([[0], [1], [2], [3]]), np.zeros((6, sr.EMB)), g.row_ptr, g.col)
+    # r0 = 5, 0, 0, 0: mean 1.25, sd sqrt(25/4 - 1.5625) = 2.165
+    sd = np.sqrt(25 / 4 - 1.25 ** 2)
+    assert np.allclose(x[:, 71], (np.array([5, 0, 0, 0]) - 1.25) / sd, atol=1e-6)
+    assert np.all(x[:, 72:] == 0)
+
+
 def test_residual_degree_counts_closed_forms():
     path = synth.named_graph("path", 5)  # 0-1-2-3-4
     assert sr.residual_degree_counts(path.row_ptr, path.col, []) == (0, 0, 0)  # the ends were pendant already
