@@ -287,16 +287,25 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
  * first live node scan their adjacency (when their adjacency is shorter than
  * the list of non-tree edges) or unites along every non-tree edge.
  * TREE_JOIN and TREE_SCAN force one of the two (for tests and measurement).
+ * TREE_LOCAL reaches the same pieces with work local to the deletion: the
+ * tree parents are bulk-copied into the labels, only the children of deleted
+ * nodes are re-picked, and only the pieces whose root is not the first live
+ * node are listed (level by level down the tree) and scanned; a member whose
+ * list outgrows the kernel's shared memory, or with repeated genes, takes
+ * the TREE path.  It needs n <= 65536 and a BFS tree whose children carry
+ * consecutive numbers (always so for the upload's numbering).
  * SAMPLED joins every live node to its first two live neighbours, takes the
  * tree of the highest-degree live node as the giant tree and lets only nodes
  * outside it scan their whole adjacency; EDGES runs union-find over every
- * undirected edge.  AUTO (the default) is TREE. */
+ * undirected edge.  AUTO (the default) is TREE_LOCAL where it applies, else
+ * TREE. */
 #define GAPA_FITNESS_AUTO 0
 #define GAPA_FITNESS_EDGES 1
 #define GAPA_FITNESS_SAMPLED 2
 #define GAPA_FITNESS_TREE 3
 #define GAPA_FITNESS_TREE_JOIN 4
 #define GAPA_FITNESS_TREE_SCAN 5
+#define GAPA_FITNESS_TREE_LOCAL 6
 int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
 /* Fitness objective of the context (all minimised; the end of Section III-C

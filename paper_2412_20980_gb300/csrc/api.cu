@@ -36,6 +36,10 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.probe);
     cudaFree(g.perm);
     cudaFree(g.tparent);
+    cudaFree(g.kids);
+    cudaFree(g.roots);
+    cudaFree(g.cut);
+    cudaFree(g.order);
     cudaFree(g.nontree);
     cudaFree(g.fptr);
     cudaFree(g.fcol16);
@@ -56,7 +60,7 @@ void free_graph(DeviceGraph& g) {
 // lower-numbered neighbours (ascending; the first one is the parent), the
 // non-parent edges (a < b, sorted) and the deepest parent chain.
 struct BfsForest {
-    std::vector<int32_t> perm, tparent, lo_ptr, lo_col;
+    std::vector<int32_t> perm, tparent, lo_ptr, lo_col, roots;
     std::vector<std::pair<int32_t, int32_t>> nontree;
     int depth = 0;
 };
@@ -77,6 +81,7 @@ BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vecto
             if (f.perm[root] >= 0) continue;
             size_t head = queue.size();
             queue.push_back(root);
+            f.roots.push_back(next);
             f.perm[root] = next++;
             while (head < queue.size()) {
                 const int32_t u = queue[head++];
@@ -90,6 +95,7 @@ BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vecto
     } else {
         for (int32_t r = 0; r < n; ++r) f.perm[by_deg[r]] = r;
     }
+    // (roots of the degree order are filled in with the parents below)
     std::vector<int32_t> inv((size_t)n);
     for (int32_t v = 0; v < n; ++v) inv[f.perm[v]] = v;
     // lower-numbered neighbours, ascending; parent = the first of them
@@ -106,6 +112,7 @@ BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vecto
         }
         std::sort(tmp.begin(), tmp.end());
         f.tparent[b] = tmp.empty() ? b : tmp[0];
+        if (!bfs_order && tmp.empty()) f.roots.push_back(b);
         level[b] = tmp.empty() ? 0 : level[tmp[0]] + 1;
         f.depth = std::max(f.depth, level[b]);
         f.lo_col.insert(f.lo_col.end(), tmp.begin(), tmp.end());
@@ -382,6 +389,12 @@ int gapa_create(gapa_ctx** out, int device, void* cuda_stream) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
         return bail(gapa_fail(GAPA_ERR_CUDA, "device attribute query failed"));
     c->smem_optin = (size_t)v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_CUDA, "device attribute query failed"));
+    c->smem_per_sm = (size_t)v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess)
+        return bail(gapa_fail(GAPA_ERR_CUDA, "device attribute query failed"));
+    c->smem_reserved = (size_t)v;
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming) != cudaSuccess)
@@ -498,8 +511,9 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     // 16-bit ids only on the shared-memory path (labels + deleted-node bitmap)
     g.packed16 = n <= 65536 && gapa_dev::tree16_smem_bytes(n) <= c->fit_smem_max;
     const size_t nt_bytes = (g.packed16 ? 4 : 8) * std::max<size_t>(bf.nontree.size(), 4);
+    const size_t par_ints = gapa_dev::tree16l_lab_ints(n);  // padded for the bulk copy of the cut-local kernel
     if (cudaMalloc(&g.perm, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&g.tparent, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&g.tparent, sizeof(int32_t) * par_ints) != cudaSuccess ||
         cudaMalloc(&g.lo_ptr, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
         cudaMalloc(&g.lo_col, sizeof(int32_t) * std::max<size_t>(bf.lo_col.size(), 1)) != cudaSuccess ||
         cudaMalloc(&g.nontree, nt_bytes) != cudaSuccess) {
@@ -508,7 +522,60 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
         return gapa_fail(GAPA_ERR_OOM, "BFS forest of %d nodes", n);
     }
     GAPA_CUDA(cudaMemcpy(g.perm, bf.perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
-    GAPA_CUDA(cudaMemcpy(g.tparent, bf.tparent.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+    {
+        std::vector<int32_t> par(bf.tparent);
+        par.resize(par_ints, 0);
+        GAPA_CUDA(cudaMemcpy(g.tparent, par.data(), sizeof(int32_t) * par_ints, cudaMemcpyHostToDevice));
+    }
+    if (g.packed16) {
+        // cut-local TREE kernel: children ranges (consecutive in BFS order), component roots, and a
+        // list region as large as two members per SM allow (one per SM when the labels need it)
+        std::vector<int2> kids((size_t)n);
+        bool contiguous = true;
+        for (int32_t b = 0; b < n; ++b) kids[b] = make_int2(b, 0);
+        for (int32_t x = 0; x < n && contiguous; ++x) {
+            const int32_t p = bf.tparent[x];
+            if (p == x) continue;
+            if (kids[p].y == 0) kids[p].x = x;
+            else if (kids[p].x + kids[p].y != x) contiguous = false;
+            kids[p].y += 1;
+        }
+        const size_t fixed = par_ints * 4 + 48, min_list = gapa_dev::tree16l_min_list_bytes(n);
+        const size_t want = std::max(min_list, ((((size_t)n * 2) + 15) & ~(size_t)15) + gapa_dev::tree16l_bitmap_bytes(n) +
+                                                   gapa_dev::tree16l_scratch_bytes());
+        // two members per SM: half the SM's shared memory, less the runtime's reserve and the
+        // kernel's static shared memory (under 1 KB)
+        const size_t per_block = c->smem_per_sm / 2, other = c->smem_reserved + 1024;
+        const size_t two_per_sm = per_block > other ? per_block - other : 0;
+        size_t budget = fixed + min_list <= two_per_sm ? two_per_sm : c->fit_smem_max;
+        budget = std::min(budget, c->fit_smem_max);
+        size_t list_bytes = 0;
+        if (contiguous && fixed + min_list <= budget) list_bytes = std::min(want, (budget - fixed) & ~(size_t)15);
+        if (list_bytes) {
+            // cost estimate of deleting node b: the nodes below those children of b whose only lower
+            // neighbour is b (they become roots of pieces to be listed)
+            std::vector<int32_t> below((size_t)n, 1), cut((size_t)n, 0);
+            for (int32_t v = n - 1; v >= 0; --v)
+                if (bf.tparent[v] != v) below[bf.tparent[v]] += below[v];
+            for (int32_t v = 0; v < n; ++v)
+                if (bf.tparent[v] != v && bf.lo_ptr[v + 1] - bf.lo_ptr[v] == 1) cut[bf.tparent[v]] += below[v];
+            if (cudaMalloc(&g.kids, sizeof(int2) * std::max<size_t>((size_t)n, 1)) != cudaSuccess ||
+                cudaMalloc(&g.cut, sizeof(int32_t) * std::max<size_t>((size_t)n, 1)) != cudaSuccess ||
+                cudaMalloc(&g.order, sizeof(int32_t) * 2 * (size_t)kOrderCap) != cudaSuccess ||
+                cudaMalloc(&g.roots, sizeof(int32_t) * std::max<size_t>(bf.roots.size(), 1)) != cudaSuccess) {
+                free_graph(g);
+                cudaGetLastError();
+                return gapa_fail(GAPA_ERR_OOM, "children ranges of %d nodes", n);
+            }
+            GAPA_CUDA(cudaMemcpy(g.kids, kids.data(), sizeof(int2) * (size_t)n, cudaMemcpyHostToDevice));
+            GAPA_CUDA(cudaMemcpy(g.cut, cut.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+            if (!bf.roots.empty())
+                GAPA_CUDA(cudaMemcpy(g.roots, bf.roots.data(), sizeof(int32_t) * bf.roots.size(),
+                                     cudaMemcpyHostToDevice));
+            g.num_roots = (int)bf.roots.size();
+            g.local_list_bytes = (int)list_bytes;
+        }
+    }
     GAPA_CUDA(cudaMemcpy(g.lo_ptr, bf.lo_ptr.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice));
     {
         // (tree parent, second lower neighbour) pairs
@@ -751,7 +818,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
 
 int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
-    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_TREE_SCAN)
+    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_TREE_LOCAL)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown fitness kernel %d", variant);
     c->fitness_variant = variant;
     return GAPA_OK;

@@ -286,20 +286,36 @@ struct GraphArgs {
     int join_mode;
     int mean_deg_x16;
     int objective;
+    const int2* kids;
+    const int* roots;
+    int num_roots;
+    int list_bytes;
+    const unsigned* est;  // cut-local kernel: per-member cost estimates (may be null)
 };
 
-enum Variant : int { V_EDGES = 0, V_SAMPLED = 1, V_TREE16 = 2, V_TREE32 = 3 };
+enum Variant : int { V_EDGES = 0, V_SAMPLED = 1, V_TREE16 = 2, V_TREE32 = 3, V_TREE16L = 4 };
 
 template <int kVar>
-__device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k,
+__device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k, int m,
                                           long long* out, int* status, long long* red, int* sh_root) {
-    if (kVar == V_TREE16) {
+    if (kVar == V_TREE16 || kVar == V_TREE16L) {
         // the whole CTA is one team; the deleted-node bitmap sits right after the labels
         const gapa_dev::Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
-        const gapa_dev::Tree16Graph t16{g.n,      g.perm,          g.palt, g.lo_ptr, g.lo_col,
-                                        (const unsigned*)g.nontree, g.num_nontree, g.fptr, g.fcol16, g.join_mode,
-                                        g.mean_deg_x16, g.objective};
-        gapa_dev::tree16_member(tm, lab, (unsigned*)(lab + g.n), t16, genes, k, out, red, status);
+        const gapa_dev::Tree16Graph t16{g.n,           g.perm,          g.palt,          g.lo_ptr,
+                                        g.lo_col,      (const unsigned*)g.nontree,      g.num_nontree,
+                                        g.fptr,        g.fcol16,        g.join_mode,     g.mean_deg_x16,
+                                        g.objective,   g.tparent,       g.kids,          g.roots,
+                                        g.num_roots,   g.list_bytes};
+        // the cut-local kernel leaves members expected to list over a quarter of the nodes (the
+        // BFS tree shattered) to the full pipeline from the start
+        const bool full = kVar == V_TREE16 || (g.est && __ldg(&g.est[m]) > (unsigned)(g.n / 4));
+        if (full) {
+            gapa_dev::tree16_member(tm, lab, (unsigned*)(lab + g.n), t16, genes, k, out, red, status);
+        } else {
+            unsigned* region = (unsigned*)(lab + gapa_dev::tree16l_lab_ints(g.n));
+            int* scal = (int*)region + g.list_bytes / 4;
+            gapa_dev::tree16_member_local(tm, lab, region, scal, t16, genes, k, out, red, status);
+        }
         return;
     }
     if (kVar == V_TREE32) {
@@ -350,15 +366,57 @@ __global__ void __launch_bounds__(1024) cc_edge_genes_kernel(GraphArgs g, const 
 
 size_t edge_genes_smem(int n, int num_edges) { return (size_t)n * 4 + (size_t)((num_edges + 31) / 32) * 4; }
 
-// One CTA per member, labels in shared memory.
+// One CTA per member, labels in shared memory; with `order`, CTA i takes
+// member order[i] (CTAs start roughly in index order, so the members
+// expected to be costliest start first and the launch has no long tail).
 template <int kVar>
 __global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* __restrict__ pop, int k,
-                                                       long long* __restrict__ fit, int* status) {
+                                                       long long* __restrict__ fit, int* status,
+                                                       const int* __restrict__ order) {
     extern __shared__ int smem_lab[];
     __shared__ long long red[32];
     __shared__ int sh_root;
-    const int i = blockIdx.x;
-    member_pc<kVar>(smem_lab, g, pop + (size_t)i * k, k, &fit[i], status, red, &sh_root);
+    const int i = order ? __ldg(&order[blockIdx.x]) : (int)blockIdx.x;
+    member_pc<kVar>(smem_lab, g, pop + (size_t)i * k, k, i, &fit[i], status, red, &sh_root);
+}
+
+// Cost estimate of every member for the cut-local kernel: the sum over its
+// genes of the nodes that deleting the gene alone leaves in pieces to be
+// listed (one warp per member; saturates at 2^31 - 1).
+__global__ void __launch_bounds__(256) local_cost_kernel(const int* __restrict__ pop, int s, int k, int n,
+                                                         const int* __restrict__ perm, const int* __restrict__ cut,
+                                                         unsigned* __restrict__ est) {
+    const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (m >= s) return;
+    long long c = 0;
+    for (int j = lane; j < k; j += 32) {
+        const int d = __ldg(&pop[(size_t)m * k + j]);
+        if ((unsigned)d < (unsigned)n) c += __ldg(&cut[__ldg(&perm[d])]);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) est[m] = (unsigned)(c < 0x7FFFFFFFll ? c : 0x7FFFFFFFll);
+}
+
+// Members by decreasing bit length of their estimate (a counting sort over
+// the 33 values of its count of leading zeros, in one CTA; the order within a
+// class is arbitrary).
+__global__ void __launch_bounds__(1024) local_order_kernel(const unsigned* __restrict__ est, int s,
+                                                           int* __restrict__ order) {
+    __shared__ int cnt[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < s; m += blockDim.x) atomicAdd(&cnt[__clz(est[m])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < 33; ++c) {
+            const int x = cnt[c];
+            cnt[c] = acc;
+            acc += x;
+        }
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < s; m += blockDim.x) order[atomicAdd(&cnt[__clz(est[m])], 1)] = m;
 }
 
 // One CTA per member, labels in a global scratch slice per CTA.
@@ -369,20 +427,32 @@ __global__ void __launch_bounds__(1024) cc_global_kernel(GraphArgs g, const int*
     __shared__ long long red[32];
     __shared__ int sh_root;
     const int i = member_base + blockIdx.x;
-    member_pc<kVar>(labels + (size_t)blockIdx.x * g.n, g, pop + (size_t)i * k, k, &fit[i], status, red, &sh_root);
+    member_pc<kVar>(labels + (size_t)blockIdx.x * g.n, g, pop + (size_t)i * k, k, i, &fit[i], status, red, &sh_root);
 }
 
 template <int kVar>
 int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, int k, long long* f,
-                   cudaStream_t st) {
+                   cudaStream_t st, int* kernels = nullptr) {
     const int n = ga.n;
-    const size_t lab_bytes = kVar == V_TREE16 ? gapa_dev::tree16_smem_bytes(n) : (size_t)n * 4;
+    const size_t lab_bytes = kVar == V_TREE16    ? gapa_dev::tree16_smem_bytes(n)
+                             : kVar == V_TREE16L ? gapa_dev::tree16l_smem_bytes(n, (size_t)ga.list_bytes)
+                                                 : (size_t)n * 4;
     if (lab_bytes <= c->fit_smem_max) {
-        cc_smem_kernel<kVar><<<s, smem_block_for(n), lab_bytes, st>>>(ga, pop, k, f, c->status);
+        const int* order = nullptr;
+        if (kVar == V_TREE16L && s > 1 && s <= kOrderCap) {
+            unsigned* est = reinterpret_cast<unsigned*>(c->g.order + kOrderCap);
+            local_cost_kernel<<<(s + 7) / 8, 256, 0, st>>>(pop, s, k, n, c->g.perm, c->g.cut, est);
+            local_order_kernel<<<1, 1024, 0, st>>>(est, s, c->g.order);
+            order = c->g.order;
+            if (kernels) *kernels += 2;
+        }
+        GraphArgs gl = ga;
+        gl.est = order ? reinterpret_cast<const unsigned*>(c->g.order + kOrderCap) : nullptr;
+        cc_smem_kernel<kVar><<<s, smem_block_for(n), lab_bytes, st>>>(gl, pop, k, f, c->status, order);
         GAPA_CUDA(cudaGetLastError());
         return GAPA_OK;
     }
-    if constexpr (kVar == V_TREE16) {
+    if constexpr (kVar == V_TREE16 || kVar == V_TREE16L) {
         // 16-bit ids are chosen at upload only when the labels fit in shared memory
         return gapa_fail(GAPA_ERR_STATE, "16-bit tree labels need shared memory");
     } else {
@@ -435,6 +505,11 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ga.join_mode = c->fitness_variant == GAPA_FITNESS_TREE_JOIN ? 1 : c->fitness_variant == GAPA_FITNESS_TREE_SCAN ? 2 : 0;
     ga.mean_deg_x16 = c->g.mean_deg_x16;
     ga.objective = c->objective;
+    ga.kids = c->g.kids;
+    ga.roots = c->g.roots;
+    ga.num_roots = c->g.num_roots;
+    ga.list_bytes = c->g.local_list_bytes;
+    ga.est = nullptr;
     if (c->objective == GAPA_OBJECTIVE_SIXDST_PC || c->objective == GAPA_OBJECTIVE_SIXDST_MCN) {
         if (c->genes != GAPA_GENES_NODES) return gapa_fail(GAPA_ERR_INVALID_ARG, "SixDST objectives take node genes");
         return gapa_launch_fitness_sixdst(c, pop, s, k, fit, st, &prof.kernels);
@@ -454,7 +529,12 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
         case GAPA_FITNESS_SAMPLED:
             return launch_variant<V_SAMPLED>(c, ga, pop, s, k, f, st);
         default:
-            if (c->g.packed16) return launch_variant<V_TREE16>(c, ga, pop, s, k, f, st);
+            if (c->g.packed16) {
+                const bool local = c->g.local_list_bytes > 0 && (c->fitness_variant == GAPA_FITNESS_AUTO ||
+                                                                  c->fitness_variant == GAPA_FITNESS_TREE_LOCAL);
+                if (local) return launch_variant<V_TREE16L>(c, ga, pop, s, k, f, st, &prof.kernels);
+                return launch_variant<V_TREE16>(c, ga, pop, s, k, f, st);
+            }
             if ((size_t)n * 4 <= c->fit_smem_max) return launch_variant<V_TREE32>(c, ga, pop, s, k, f, st);
             // labels too large for shared memory: interleaved member groups in global memory
             return gapa_launch_fitness_ig(c, pop, s, k, fit, st, &prof.kernels);
@@ -465,6 +545,7 @@ int gapa_fitness_kernels_init(gapa_ctx* c) {
     int rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_EDGES>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_SAMPLED>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE16>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE16L>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE32>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_edge_genes_kernel, c->smem_optin, &c->fit_smem_max);
     return rc;

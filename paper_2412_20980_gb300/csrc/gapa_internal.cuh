@@ -102,7 +102,13 @@ struct DeviceGraph {
     // order from the highest-degree node of each component, so every tree
     // parent has a smaller number than its child.
     int* perm = nullptr;        // [n] original id -> BFS number
-    int* tparent = nullptr;     // [n] BFS number -> BFS number of its tree parent (roots: itself)
+    int* tparent = nullptr;     // [n rounded up to 4] BFS number -> BFS number of its tree parent (roots: itself)
+    int2* kids = nullptr;       // [n] (first child, number of children); children have consecutive numbers
+    int* roots = nullptr;       // [num_roots] BFS number of every component's root
+    int num_roots = 0;
+    int local_list_bytes = 0;   // list region of the cut-local TREE kernel (0: that kernel does not fit)
+    int* cut = nullptr;         // [n] per node: nodes below its children that have no other lower neighbour
+    int* order = nullptr;       // [2 * kOrderCap] member cost estimates, then the members, costliest first
     int* lo_ptr = nullptr;      // [n+1] CSR of lower-numbered neighbours (BFS numbers, ascending;
     int* lo_col = nullptr;      //        the first one is the tree parent)
     int2* palt = nullptr;       // [n] (tree parent, second lower-numbered neighbour or -1)
@@ -117,6 +123,7 @@ struct DeviceGraph {
 };
 
 constexpr int kProbe = 8;
+constexpr int kOrderCap = 1 << 16;  // members ordered by cost per fitness launch (larger batches: in order)
 
 struct gapa_ctx {
     int device = 0;
@@ -125,6 +132,8 @@ struct gapa_ctx {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     int num_sms = 0;
     size_t smem_optin = 0;  // max shared memory per block (opt-in)
+    size_t smem_per_sm = 0;     // shared memory per SM
+    size_t smem_reserved = 0;   // shared memory the runtime reserves per block
     size_t fit_smem_max = 0;  // max dynamic shared memory of the shared-memory fitness kernel
     size_t ga_smem_max = 0;   // max dynamic shared memory of the operator kernels
     DeviceGraph g;

@@ -108,6 +108,12 @@ struct Tree16Graph {
     int join_mode;            // 0: per member, 1: non-tree edges, 2: scan outside the giant piece
     int mean_deg_x16;         // 16 * 2E / n, rounded up
     int objective;            // 0: PC, 1: MCN
+    // cut-local variant only
+    const int* tparent;       // tree parent per node (roots: itself), padded to a multiple of 4 entries
+    const int2* kids;         // (first child, number of children): a node's children have consecutive numbers
+    const int* roots;         // the BFS root of every component
+    int num_roots;
+    int list_bytes;           // bytes of the member's list region
 };
 
 // Shared-memory bytes of one member: labels + deleted-node bitmap (reused as
@@ -370,4 +376,439 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
     if (tid == 0) *out = tot;
 }
 
+// ---------------------------------------------------------------------------
+// Cut-local variant.  Same fitness as tree16_member, with work proportional
+// to what the deletion disturbs instead of to n:
+//  * the tree-parent array is copied into the labels by one bulk copy
+//    (cp.async.bulk, completion on an mbarrier), so every live node whose
+//    parent is live already holds its final pick;
+//  * only the children of deleted nodes are re-picked (first live lower-
+//    numbered neighbour, else themselves); these "tops" start the pieces the
+//    deletion cut off;
+//  * each top walks to its root; a top whose root is not R (the first live
+//    node, a root forever) seeds the list of nodes outside R's piece, and so
+//    does every other live component root;
+//  * the list grows level by level down the tree (a node's children have
+//    consecutive numbers), each listed node taking its piece root as label;
+//  * the pieces are joined either by the listed nodes' adjacency (an arc to
+//    an unlisted live node unites with R directly, since every unlisted live
+//    node lies in R's piece) or, for long lists, by giving every unlisted
+//    live node R as label and uniting along the non-tree edges as
+//    tree16_member does; then the sizes are counted on the list.
+// Work items (children of a set of nodes, arcs of the listed nodes) are dealt
+// out over the whole team through a team-wide prefix sum, so that one deleted
+// hub with hundreds of children does not hold up a single warp.
+// A member with repeated genes, or whose list outgrows its region or half the
+// graph, or whose tree below the seeds is deeper than kLocalLevels, runs
+// tree16_member (and so does, by the caller's choice, one whose cost
+// estimate says the list will be long).
+
+constexpr int kLocalLevels = 256;
+constexpr int kLocalChunk = 1024;  // owners per dealing round: the largest team
+constexpr long long kLocalSpinLimit = 1ll << 24;
+
+// Layout of one member: labels (n rounded up to a multiple of 4, so the bulk
+// copy moves whole 16-byte units), the list region, eight team scalars and
+// the mbarrier.  The list region holds, from its start, the deletion bitmap
+// (until the re-picks are done) and then the list (16-bit node ids); at its
+// end three kLocalChunk-int arrays for the dealing rounds and the bitmap of
+// listed nodes.
+__host__ __device__ __forceinline__ size_t tree16l_lab_ints(int n) { return ((size_t)n + 3) & ~(size_t)3; }
+__host__ __device__ __forceinline__ size_t tree16l_bitmap_bytes(int n) {
+    return ((((size_t)n + 31) >> 5) * 4 + 15) & ~(size_t)15;
+}
+__host__ __device__ __forceinline__ size_t tree16l_scratch_bytes() { return (size_t)3 * kLocalChunk * 4; }
+__host__ __device__ __forceinline__ size_t tree16l_min_list_bytes(int n) {
+    return 2 * tree16l_bitmap_bytes(n) + tree16l_scratch_bytes();
+}
+__host__ __device__ __forceinline__ size_t tree16l_smem_bytes(int n, size_t list_bytes) {
+    return tree16l_lab_ints(n) * 4 + list_bytes + 32 + 16;
+}
+
+__device__ __forceinline__ unsigned tree16l_smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool tree16l_wait(unsigned bar, unsigned parity) {
+    for (long long i = 0; i < kLocalSpinLimit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Exclusive prefix sum of v over the team in thread order; *total = the sum.
+// ws: 32 ints of team scratch, free again after the caller's next barrier.
+// Contains two team barriers.
+__device__ __forceinline__ int tree16l_scan(const Team& tm, int v, int* ws, int* total) {
+    const int lane = tm.tid & 31, warp = tm.tid >> 5, nw = tm.T >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) ws[warp] = incl;
+    tm.sync();
+    if (warp == 0) {
+        int x = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < nw) ws[lane] = x;
+    }
+    tm.sync();
+    *total = ws[nw - 1];
+    return (warp ? ws[warp - 1] : 0) + incl - v;
+}
+
+// The owner of item i among `owners` owners with exclusive offsets off[]:
+// the last owner whose offset is at most i (owners without items share the
+// next one's offset and come before it).
+__device__ __forceinline__ int tree16l_owner(const int* off, int owners, int i) {
+    int lo = 0, hi = owners - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Warp-aggregated append of val (where want) to the 16-bit list, marking it
+// in the listed-node bitmap; entries past cap are dropped (the caller sees
+// the count exceed cap).  Called by all lanes of a warp.
+__device__ __forceinline__ void tree16l_append(bool want, int val, int lane, volatile int* count,
+                                               unsigned short* list, int cap, unsigned* listed_bm) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    int first = 0;
+    if (lane == 0) first = atomicAdd((int*)count, __popc(m));
+    first = __shfl_sync(0xffffffffu, first, 0);
+    const int slot = first + __popc(m & ((1u << lane) - 1));
+    if (want && slot < cap) {
+        list[slot] = (unsigned short)val;
+        atomicOr(&listed_bm[val >> 5], 1u << (val & 31));
+    }
+}
+
+// Join step for the arc (a, b) of a listed node once the list is complete:
+// two listed ends unite their sets; a listed end and an unlisted live one
+// unite with R.
+__device__ __forceinline__ void tree16l_join_edge(volatile int* lab, const unsigned* listed_bm, int R, int a, int b) {
+    const bool la = bm_test(listed_bm, a), lb = bm_test(listed_bm, b);
+    if (!la && !lb) return;
+    if (la && lb) {
+        if (lab[a] != lab[b]) uf_unite(lab, a, b);
+        return;
+    }
+    const int x = la ? a : b, y = la ? b : a;
+    if (lab[y] != -1 && lab[x] != R) uf_unite(lab, x, R);
+}
+
+// lab: the member's labels; region: its list region (g.list_bytes); scal_base:
+// its eight scalars followed by the mbarrier.  Returns through *out like
+// tree16_member.
+__device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int* lab, unsigned* region,
+                                                    int* scal_base, const Tree16Graph& g,
+                                                    const int* __restrict__ genes, int k, long long* out,
+                                                    long long* red, int* status) {
+    const int tid = tm.tid, T = tm.T, n = g.n, lane = tid & 31;
+    const int words = (n + 31) >> 5;
+    volatile int* scalar = scal_base;  // 0 R, 1 list length, 2 repeated genes, 3 live
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(scal_base + 8);
+    const unsigned bar_a = tree16l_smem_u32(bar);
+    unsigned* dead = region;
+    unsigned short* list = reinterpret_cast<unsigned short*>(region);
+    const int bm_bytes = (int)tree16l_bitmap_bytes(n);
+    char* tail_area = reinterpret_cast<char*>(region) + g.list_bytes - bm_bytes - (int)tree16l_scratch_bytes();
+    int* s_off = reinterpret_cast<int*>(tail_area);
+    int* s_first = s_off + kLocalChunk;
+    int* s_own = s_first + kLocalChunk;
+    unsigned* listed_bm = reinterpret_cast<unsigned*>(s_own + kLocalChunk);
+    const int cap = (int)((tail_area - reinterpret_cast<char*>(region)) >> 1);
+    int* ws = reinterpret_cast<int*>(red);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int w = tid; w < words; w += T) {
+        dead[w] = 0u;
+        listed_bm[w] = 0u;
+    }
+    tm.sync();
+    if (tid == 0) {
+        // labels <- tree parents, in chunks of at most 32 KB
+        const unsigned bytes = (unsigned)(tree16l_lab_ints(n) * 4);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
+        const unsigned dst = tree16l_smem_u32((const void*)lab);
+        for (unsigned o = 0; o < bytes; o += 32768u) {
+            const unsigned len = bytes - o < 32768u ? bytes - o : 32768u;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst + o),
+                "l"(reinterpret_cast<const char*>(g.tparent) + o), "r"(len), "r"(bar_a)
+                : "memory");
+        }
+    }
+    // perturbation P^(A, p) of Eq. 13 in BFS numbering; count the distinct
+    // deleted nodes and the repeated genes.  The first T genes keep their
+    // node, first child and number of children in registers.
+    long long fresh_dup = 0;  // distinct << 32 | repeated
+    int b0 = -1, first0 = 0, cnt0 = 0;
+    for (int j = tid; j < k; j += T) {
+        const int d = __ldg(&genes[j]);
+        if ((unsigned)d < (unsigned)n) {
+            const int b = __ldg(&g.perm[d]);
+            const unsigned bit = 1u << (b & 31);
+            const unsigned old = atomicOr(&dead[b >> 5], bit);
+            fresh_dup += (old & bit) ? 1 : (1ll << 32);
+            if (j == tid) {
+                const int2 ch = __ldg(&g.kids[b]);
+                b0 = b;
+                first0 = ch.x;
+                cnt0 = ch.y;
+            }
+        } else {
+            atomicOr(status, GAPA_DEV_BAD_GENE);
+        }
+    }
+    fresh_dup = team_sum_ll(tm, fresh_dup, red);  // (includes a team barrier: the bitmap is complete)
+    if ((tid >> 5) == 0) {
+        // R = the first live node
+        int f = -1;
+        for (int w0 = 0; w0 < words && f < 0; w0 += 32) {
+            const int w = w0 + lane;
+            unsigned live = w < words ? ~dead[w] : 0u;
+            if (w == words - 1 && (n & 31)) live &= (1u << (n & 31)) - 1u;
+            const unsigned m = __ballot_sync(0xffffffffu, live != 0u);
+            if (m) {
+                const int src = __ffs(m) - 1;
+                const unsigned lw = __shfl_sync(0xffffffffu, live, src);
+                f = ((w0 + src) << 5) + __ffs(lw) - 1;
+            }
+        }
+        if (lane == 0) {
+            scalar[0] = f;
+            scalar[1] = 0;
+            scalar[2] = (fresh_dup & 0xFFFFFFFFll) != 0;
+            scalar[3] = n - (int)(fresh_dup >> 32);
+        }
+    }
+    // the labels must have landed before anyone reads or writes them
+    const bool ok = tree16l_wait(bar_a, 0u);
+    if (!ok) {
+        atomicOr(status, GAPA_DEV_TIMEOUT);
+        tree16l_wait(bar_a, 0u);  // bounded: the copy may still be in flight
+    }
+    tm.sync();
+    if (!ok) {
+        if (tid == 0) *out = -1;
+        return;
+    }
+    const int R = scalar[0];
+    if (R < 0) {  // every node deleted
+        if (tid == 0) *out = 0;
+        return;
+    }
+    if (scalar[2]) {  // repeated genes: the per-gene passes below would list tops twice
+        tree16_member(tm, lab, region, g, genes, k, out, red, status);
+        return;
+    }
+    // genes in chunks of T: (node, first child, children) of the team's genes,
+    // their children dealt out over the team
+    auto gene_chunk = [&](int j0, int& total) {
+        int b = b0, first = first0, cnt = cnt0;
+        if (j0 > 0) {
+            b = -1;
+            first = cnt = 0;
+            const int j = j0 + tid;
+            if (j < k) {
+                const int d = __ldg(&genes[j]);
+                if ((unsigned)d < (unsigned)n) {
+                    b = __ldg(&g.perm[d]);
+                    const int2 ch = __ldg(&g.kids[b]);
+                    first = ch.x;
+                    cnt = ch.y;
+                }
+            }
+        }
+        const int off = tree16l_scan(tm, cnt, ws, &total);
+        s_off[tid] = off;
+        s_first[tid] = first;
+        tm.sync();
+        return b;
+    };
+    // re-pick the children of the deleted nodes
+    int tops_total = 0;
+    for (int j0 = 0; j0 < k; j0 += T) {
+        const int b = gene_chunk(j0, tops_total);
+        if (b >= 0) lab[b] = -1;
+        const int owners = min(T, k - j0);
+        for (int i = tid; i < tops_total; i += T) {
+            const int o = tree16l_owner(s_off, owners, i);
+            const int c = s_first[o] + i - s_off[o];
+            if (!bm_test(dead, c)) lab[c] = tree16_pick(dead, g, c, __ldg(&g.palt[c]));
+        }
+        tm.sync();
+    }
+    // from here a deleted node is a label of -1; the bitmap's words become the list.
+    // Seeds: tops whose root is not R (each top takes its root as label)
+    for (int j0 = 0; j0 < k; j0 += T) {
+        if (k > T) gene_chunk(j0, tops_total);  // one chunk: the offsets are still in place
+        const int owners = min(T, k - j0);
+        for (int i0 = tid & ~31; i0 < tops_total; i0 += T) {
+            const int i = i0 + lane;
+            bool want = false;
+            int c = 0;
+            if (i < tops_total) {
+                const int o = tree16l_owner(s_off, owners, i);
+                c = s_first[o] + i - s_off[o];
+                const int l = lab[c];
+                if (l != -1) {
+                    const int r = l == c ? c : uf_root(lab, l);
+                    if (r != l) lab[c] = r;
+                    want = r != R;
+                }
+            }
+            tree16l_append(want, c, lane, &scalar[1], list, cap, listed_bm);
+        }
+        tm.sync();
+    }
+    for (int i0 = tid & ~31; i0 < g.num_roots; i0 += T) {
+        const int i = i0 + lane;
+        const int rho = i < g.num_roots ? __ldg(&g.roots[i]) : -1;
+        tree16l_append(rho >= 0 && rho != R && lab[rho] == rho, rho, lane, &scalar[1], list, cap, listed_bm);
+    }
+    tm.sync();
+    // the list grows one tree level per round; the children of up to T listed
+    // nodes per dealing step
+    // (a list past half the graph is cheaper in the full pipeline)
+    const int lim = min(cap, max(n / 2, 256));
+    int head = 0, tail = scalar[1], level = 0;
+    while (head < tail && tail <= lim && level < kLocalLevels) {
+        for (int u0 = head; u0 < tail; u0 += T) {
+            const int idx = u0 + tid;
+            int2 ch = make_int2(0, 0);
+            int r = 0;
+            if (idx < tail) {
+                const int u = list[idx];
+                ch = __ldg(&g.kids[u]);
+                r = lab[u];
+            }
+            int total;
+            const int off = tree16l_scan(tm, ch.y, ws, &total);
+            s_off[tid] = off;
+            s_first[tid] = ch.x;
+            s_own[tid] = r;
+            tm.sync();
+            const int owners = min(T, tail - u0);
+            for (int i0 = tid & ~31; i0 < total; i0 += T) {
+                const int i = i0 + lane;
+                bool want = false;
+                int x = 0;
+                if (i < total) {
+                    const int o = tree16l_owner(s_off, owners, i);
+                    x = s_first[o] + i - s_off[o];
+                    if (lab[x] != -1) {
+                        lab[x] = s_own[o];
+                        want = true;
+                    }
+                }
+                tree16l_append(want, x, lane, &scalar[1], list, cap, listed_bm);
+            }
+            tm.sync();
+        }
+        head = tail;
+        tail = scalar[1];
+        ++level;
+        tm.sync();  // every thread has read the new length before the next round appends
+    }
+    if (tail > lim || head < tail) {  // list overflow or a tree too deep: the full pipeline
+        tree16_member(tm, lab, region, g, genes, k, out, red, status);
+        return;
+    }
+    const int listed = tail;
+    // join: the listed nodes' arcs, or (long lists) the non-tree edges, four
+    // per 16-byte load, after a pass that labels R's piece
+    if ((long long)listed * g.mean_deg_x16 <= 4ll * g.num_nontree) {
+        for (int v0 = 0; v0 < listed; v0 += T) {
+            const int idx = v0 + tid;
+            int v = 0, b = 0, d = 0;
+            if (idx < listed) {
+                v = list[idx];
+                b = __ldg(&g.fptr[v]);
+                d = __ldg(&g.fptr[v + 1]) - b;
+            }
+            int total;
+            const int off = tree16l_scan(tm, d, ws, &total);
+            s_off[tid] = off;
+            s_first[tid] = b;
+            s_own[tid] = v;
+            tm.sync();
+            const int owners = min(T, listed - v0);
+            for (int i = tid; i < total; i += T) {
+                const int o = tree16l_owner(s_off, owners, i);
+                const int w = __ldg(&g.fcol[s_first[o] + i - s_off[o]]);
+                tree16l_join_edge(lab, listed_bm, R, s_own[o], w);
+            }
+            tm.sync();
+        }
+    } else {
+        // every unlisted live node lies in R's piece: give it R as label, then
+        // unite along the non-tree edges whose ends carry different labels
+        for (int v = tid; v < n; v += T)
+            if (!bm_test(listed_bm, v) && lab[v] != -1) lab[v] = R;
+        tm.sync();
+        const uint4* e4 = reinterpret_cast<const uint4*>(g.nontree);
+        const int quads = g.num_nontree >> 2;
+        int q = tid;
+        uint4 w = q < quads ? __ldg(&e4[q]) : make_uint4(0, 0, 0, 0);
+        while (q < quads) {
+            const int qn = q + T;
+            const uint4 wn = qn < quads ? __ldg(&e4[qn]) : make_uint4(0, 0, 0, 0);
+            const int a0 = (int)(w.x >> 16), b0 = (int)(w.x & 0xFFFFu), a1 = (int)(w.y >> 16), b1 = (int)(w.y & 0xFFFFu);
+            const int a2 = (int)(w.z >> 16), b2 = (int)(w.z & 0xFFFFu), a3 = (int)(w.w >> 16), b3 = (int)(w.w & 0xFFFFu);
+            const int la0 = lab[a0], lb0 = lab[b0], la1 = lab[a1], lb1 = lab[b1];
+            const int la2 = lab[a2], lb2 = lab[b2], la3 = lab[a3], lb3 = lab[b3];
+            if (la0 != lb0 && la0 != -1 && lb0 != -1) uf_unite(lab, la0, lb0);
+            if (la1 != lb1 && la1 != -1 && lb1 != -1) uf_unite(lab, la1, lb1);
+            if (la2 != lb2 && la2 != -1 && lb2 != -1) uf_unite(lab, la2, lb2);
+            if (la3 != lb3 && la3 != -1 && lb3 != -1) uf_unite(lab, la3, lb3);
+            q = qn;
+            w = wn;
+        }
+        for (int e = quads * 4 + tid; e < g.num_nontree; e += T) {
+            const unsigned x = __ldg(&g.nontree[e]);
+            const int a = (int)(x >> 16), b = (int)(x & 0xFFFFu);
+            const int la = lab[a], lb = lab[b];
+            if (la != lb && la != -1 && lb != -1) uf_unite(lab, la, lb);
+        }
+        tm.sync();
+    }
+    // sizes on the list (see tree16_member)
+    long long joined = 0;
+    for (int i = tid; i < listed; i += T) {
+        const int v = list[i];
+        const int x = tree16_root16(lab, v);
+        if (x == R) ++joined;
+        else if (x != v) atomicAdd((unsigned*)&lab[x], 1u << 16);
+    }
+    joined = team_sum_ll(tm, joined, red);
+    long long acc = 0;
+    if (tid == 0) acc = objective_add(0, (long long)scalar[3] - listed + joined, g.objective);
+    tm.sync();
+    for (int i = tid; i < listed; i += T) {
+        const int v = list[i];
+        const unsigned l = (unsigned)lab[v];
+        if ((int)(l & 0xFFFFu) == v) acc = objective_add(acc, (long long)(l >> 16) + 1, g.objective);
+    }
+    const long long tot = team_sum_ll(tm, acc, red, g.objective != 0);
+    if (tid == 0) *out = tot;
+}
 }  // namespace gapa_dev

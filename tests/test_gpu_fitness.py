@@ -20,19 +20,20 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pc_worked_examples.json")
 
 
-@pytest.fixture(scope="module", params=["tree", "tree_join", "tree_scan", "sampled", "edges"])
+@pytest.fixture(scope="module", params=["tree_local", "tree", "tree_join", "tree_scan", "sampled", "edges"])
 def ctx(request):
     import torch
 
     from paper_2412_20980_gb300 import Context
     from paper_2412_20980_gb300 import build as b
     from paper_2412_20980_gb300.gapa import (FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN,
-                                             FITNESS_TREE_SCAN)
+                                             FITNESS_TREE_LOCAL, FITNESS_TREE_SCAN)
 
     b.build()
     c = Context(0)
     c.set_fitness_kernel({"tree": FITNESS_TREE, "tree_join": FITNESS_TREE_JOIN, "tree_scan": FITNESS_TREE_SCAN,
-                          "sampled": FITNESS_SAMPLED, "edges": FITNESS_EDGES}[request.param])
+                          "tree_local": FITNESS_TREE_LOCAL, "sampled": FITNESS_SAMPLED,
+                          "edges": FITNESS_EDGES}[request.param])
     c.variant_name = request.param
     yield c
     torch.cuda.synchronize()
@@ -75,6 +76,26 @@ def test_exhaustive_subsets(ctx, seed, n, m):
 def test_benchmark_graphs_full_population(ctx, make):
     g = make()
     pop = synth.random_deletion_sets(g.n, 1000, 1024, 0)
+    want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
+    assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
+@pytest.mark.parametrize("graph", ["ba", "hk"])
+@pytest.mark.parametrize("hubs", [0, 100, 500, 1000])
+def test_benchmark_graphs_hub_heavy(ctx, graph, hubs):
+    """Deletion sets holding the top hubs of the benchmark graphs (what an evolved population
+    deletes): the BFS tree shatters, the list of nodes outside the first live node's piece grows
+    from a few hundred to most of the graph, and the cut-local kernel moves from its list to the
+    full pipeline; 33 members (a ragged last warp of genes), odd rows with half the hubs."""
+    g = synth.ba_graph(20000, 4, 1) if graph == "ba" else synth.hk_graph(20000, 4, 0.3, 1)
+    top = np.argsort(-g.degrees(), kind="stable")
+    rng = np.random.default_rng(hubs + 7)
+    rows = []
+    for r in range(33):
+        h = hubs if r % 2 == 0 else hubs // 2
+        rest = rng.choice(top[h:], 1000 - h, replace=False)
+        rows.append(rng.permutation(np.concatenate([top[:h], rest])))
+    pop = np.stack(rows).astype(np.int32)
     want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
     assert np.array_equal(gpu_fit(ctx, g, pop), want)
 
