@@ -369,6 +369,8 @@ typedef struct gapa_profile {
     int64_t evals;              /* population members evaluated by those fitness launches */
     double surrogate_ms;        /* summed duration of surrogate phases (features, MLP, selection, training) */
     int64_t surrogate_launches; /* kernels launched by those phases */
+    int64_t fitness_calls;      /* fitness phases (one per batch of members evaluated; a phase may launch
+                                   several kernels, counted in fitness_launches) */
 } gapa_profile;
 
 int gapa_profile_begin(gapa_ctx* ctx);

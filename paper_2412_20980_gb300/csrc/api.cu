@@ -886,6 +886,7 @@ int gapa_profile_end(gapa_ctx* c, gapa_profile* out) {
         if (t.kind == 0) {
             out->fitness_ms += ms;
             out->fitness_launches += t.kernels;
+            out->fitness_calls += 1;
             out->evals += t.evals;
         } else if (t.kind == 1) {  // `evals` holds the kernel count when it is above 1
             out->operators_ms += ms;

@@ -382,19 +382,37 @@ __global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* _
 
 // Cost estimate of every member for the cut-local kernel: the sum over its
 // genes of the nodes that deleting the gene alone leaves in pieces to be
-// listed (one warp per member; saturates at 2^31 - 1).
-__global__ void __launch_bounds__(256) local_cost_kernel(const int* __restrict__ pop, int s, int k, int n,
+// listed (one 128-thread CTA per member, four independent gathers in flight
+// per thread; saturates at 2^31 - 1).
+__global__ void __launch_bounds__(128) local_cost_kernel(const int* __restrict__ pop, int k, int n,
                                                          const int* __restrict__ perm, const int* __restrict__ cut,
                                                          unsigned* __restrict__ est) {
-    const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (m >= s) return;
+    __shared__ long long part[4];
+    const int m = blockIdx.x, t = threadIdx.x;
+    const int* genes = pop + (size_t)m * k;
     long long c = 0;
-    for (int j = lane; j < k; j += 32) {
-        const int d = __ldg(&pop[(size_t)m * k + j]);
+    int j = t;
+    for (; j + 384 < k; j += 512) {
+        int d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = __ldg(&genes[j + 128 * u]);
+        int b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = (unsigned)d[u] < (unsigned)n ? __ldg(&perm[d[u]]) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c += b[u] >= 0 ? __ldg(&cut[b[u]]) : 0;
+    }
+    for (; j < k; j += 128) {
+        const int d = __ldg(&genes[j]);
         if ((unsigned)d < (unsigned)n) c += __ldg(&cut[__ldg(&perm[d])]);
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if (lane == 0) est[m] = (unsigned)(c < 0x7FFFFFFFll ? c : 0x7FFFFFFFll);
+    if ((t & 31) == 0) part[t >> 5] = c;
+    __syncthreads();
+    if (t == 0) {
+        const long long s = (part[0] + part[1]) + (part[2] + part[3]);
+        est[m] = (unsigned)(s < 0x7FFFFFFFll ? s : 0x7FFFFFFFll);
+    }
 }
 
 // Members by decreasing bit length of their estimate (a counting sort over
@@ -441,7 +459,7 @@ int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, 
         const int* order = nullptr;
         if (kVar == V_TREE16L && s > 1 && s <= kOrderCap) {
             unsigned* est = reinterpret_cast<unsigned*>(c->g.order + kOrderCap);
-            local_cost_kernel<<<(s + 7) / 8, 256, 0, st>>>(pop, s, k, n, c->g.perm, c->g.cut, est);
+            local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.perm, c->g.cut, est);
             local_order_kernel<<<1, 1024, 0, st>>>(est, s, c->g.order);
             order = c->g.order;
             if (kernels) *kernels += 2;

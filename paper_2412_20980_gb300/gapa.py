@@ -65,6 +65,7 @@ class Profile(ctypes.Structure):
         ("evals", ctypes.c_int64),
         ("surrogate_ms", ctypes.c_double),
         ("surrogate_launches", ctypes.c_int64),
+        ("fitness_calls", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
