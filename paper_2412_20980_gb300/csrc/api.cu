@@ -209,6 +209,9 @@ GaParams make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_pt
     p.g = g;
     p.g_ptr = g_ptr;
     p.cum = nullptr;
+    p.est_perm = nullptr;
+    p.est_cut = nullptr;
+    p.est_out = nullptr;
     return p;
 }
 
@@ -239,9 +242,17 @@ int enqueue_generation(gapa_ctx* c, const GaParams& p0, int lambda, const int32_
         p.cum = reinterpret_cast<const long long*>(c->cum);
         if (rc != GAPA_OK) return rc;
     }
+    // the operator kernels also write the children's cost estimates for the cut-local fitness kernel
+    const int evaluated = (p.flags & GAPA_FLAG_MU_PLUS_LAMBDA) ? lambda : p.s;
+    unsigned* est = gapa_fitness_uses_estimates(c, evaluated) ? gapa_estimate_buffer(c) : nullptr;
+    if (est) {
+        p.est_perm = c->g.perm;
+        p.est_cut = c->g.cut;
+        p.est_out = est;
+    }
     if (p.flags & GAPA_FLAG_MU_PLUS_LAMBDA) {
         rc = gapa_launch_children(c, p, lambda, pop_in, fit_in, c->kids, st);
-        if (rc == GAPA_OK) rc = gapa_launch_fitness(c, c->kids, lambda, p.k, c->kfit, st);
+        if (rc == GAPA_OK) rc = gapa_launch_fitness(c, c->kids, lambda, p.k, c->kfit, st, est);
         if (rc == GAPA_OK)
             rc = gapa_launch_mpl_replace(c, p.s, lambda, p.k, pop_in, fit_in, c->kids, c->kfit, c->src, pop_out,
                                          fit_out, st);
@@ -249,7 +260,7 @@ int enqueue_generation(gapa_ctx* c, const GaParams& p0, int lambda, const int32_
     }
     rc = gapa_launch_offspring(c, p, pop_in, fit_in, pop_out, fit_out, st);
     if (rc != GAPA_OK) return rc;
-    return gapa_launch_fitness(c, pop_out + p.k, p.s - 1, p.k, fit_out + 1, st);
+    return gapa_launch_fitness(c, pop_out + p.k, p.s - 1, p.k, fit_out + 1, st, est ? est + 1 : nullptr);
 }
 
 int read_status(gapa_ctx* c, cudaStream_t st) {

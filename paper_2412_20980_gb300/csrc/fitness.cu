@@ -450,22 +450,28 @@ __global__ void __launch_bounds__(1024) cc_global_kernel(GraphArgs g, const int*
 
 template <int kVar>
 int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, int k, long long* f,
-                   cudaStream_t st, int* kernels = nullptr) {
+                   cudaStream_t st, int* kernels = nullptr, const unsigned* est_in = nullptr) {
     const int n = ga.n;
     const size_t lab_bytes = kVar == V_TREE16    ? gapa_dev::tree16_smem_bytes(n)
                              : kVar == V_TREE16L ? gapa_dev::tree16l_smem_bytes(n, (size_t)ga.list_bytes)
                                                  : (size_t)n * 4;
     if (lab_bytes <= c->fit_smem_max) {
         const int* order = nullptr;
+        const unsigned* est = nullptr;
         if (kVar == V_TREE16L && s > 1 && s <= kOrderCap) {
-            unsigned* est = reinterpret_cast<unsigned*>(c->g.order + kOrderCap);
-            local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.perm, c->g.cut, est);
+            est = est_in;
+            if (!est) {
+                unsigned* e = gapa_estimate_buffer(c);
+                local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.perm, c->g.cut, e);
+                est = e;
+                if (kernels) *kernels += 1;
+            }
             local_order_kernel<<<1, 1024, 0, st>>>(est, s, c->g.order);
             order = c->g.order;
-            if (kernels) *kernels += 2;
+            if (kernels) *kernels += 1;
         }
         GraphArgs gl = ga;
-        gl.est = order ? reinterpret_cast<const unsigned*>(c->g.order + kOrderCap) : nullptr;
+        gl.est = order ? est : nullptr;
         cc_smem_kernel<kVar><<<s, smem_block_for(n), lab_bytes, st>>>(gl, pop, k, f, c->status, order);
         GAPA_CUDA(cudaGetLastError());
         return GAPA_OK;
@@ -499,7 +505,17 @@ int gapa_fitness_prepare(gapa_ctx* c, int s) {
     return gapa_reserve((void**)&c->labels, &c->labels_cap, wave * (size_t)c->g.n, sizeof(int));
 }
 
-int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st) {
+bool gapa_fitness_uses_estimates(const gapa_ctx* c, int s) {
+    return c->g.packed16 && c->g.local_list_bytes > 0 && s > 1 && s <= kOrderCap &&
+           c->genes == GAPA_GENES_NODES &&
+           (c->objective == GAPA_OBJECTIVE_PC || c->objective == GAPA_OBJECTIVE_MCN) &&
+           (c->fitness_variant == GAPA_FITNESS_AUTO || c->fitness_variant == GAPA_FITNESS_TREE_LOCAL);
+}
+
+unsigned* gapa_estimate_buffer(gapa_ctx* c) { return reinterpret_cast<unsigned*>(c->g.order + kOrderCap); }
+
+int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
+                        const unsigned* est) {
     if (s <= 0) return GAPA_OK;
     ProfileScope prof(c, st, 0, s);
     const int n = c->g.n;
@@ -550,7 +566,7 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
             if (c->g.packed16) {
                 const bool local = c->g.local_list_bytes > 0 && (c->fitness_variant == GAPA_FITNESS_AUTO ||
                                                                   c->fitness_variant == GAPA_FITNESS_TREE_LOCAL);
-                if (local) return launch_variant<V_TREE16L>(c, ga, pop, s, k, f, st, &prof.kernels);
+                if (local) return launch_variant<V_TREE16L>(c, ga, pop, s, k, f, st, &prof.kernels, est);
                 return launch_variant<V_TREE16>(c, ga, pop, s, k, f, st);
             }
             if ((size_t)n * 4 <= c->fit_smem_max) return launch_variant<V_TREE32>(c, ga, pop, s, k, f, st);

@@ -226,6 +226,26 @@ __device__ void block_argmin(const long long* __restrict__ fit, int s, long long
 
 // Row i of one generation g: with an elite, row 0 = elite copy and row i >= 1
 // = child i; without (the (mu+lambda) children), row i = child with counter i.
+// Cost estimate of a finished row for the cut-local fitness kernel (whole
+// CTA; the row was written by this CTA before the barrier inside).
+__device__ void row_estimate(const GaParams& p, const int* row, int i) {
+    __shared__ long long part[kGaBlock / 32];
+    __syncthreads();
+    long long c = 0;
+    for (int j = threadIdx.x; j < p.k; j += blockDim.x) {
+        const int d = row[j];
+        if ((unsigned)d < (unsigned)p.n) c += __ldg(&p.est_cut[__ldg(&p.est_perm[d])]);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        p.est_out[i] = (unsigned)(t < 0x7FFFFFFFll ? t : 0x7FFFFFFFll);
+    }
+}
+
 __device__ void offspring_row(const GaParams& p, int i, int g, const int* __restrict__ pop_in,
                               const long long* __restrict__ fit_in, int* __restrict__ pop_out,
                               long long* __restrict__ fit_out, int* status, bool has_elite = true) {
@@ -240,6 +260,7 @@ __device__ void offspring_row(const GaParams& p, int i, int g, const int* __rest
         const int* src = pop_in + (size_t)e * k;
         for (int j = threadIdx.x; j < k; j += blockDim.x) pop_out[j] = src[j];
         if (threadIdx.x == 0) fit_out[0] = v;
+        if (p.est_out) row_estimate(p, pop_out, 0);
         return;
     }
     RowSmem sm = carve(smem, n, k);
@@ -311,9 +332,11 @@ __device__ void offspring_row(const GaParams& p, int i, int g, const int* __rest
     for (int j = j0; j < j1; ++j)
         if (sm.flags[j] & F_HOLE) sm.holes[pos++] = j;
     __syncthreads();
-    if (warp != 0) return;
-    ChildCand cand{p.key, i, g, n, sm.flags, A, status};
-    repair_warp(sm.kept, sm.holes, total, C, cand, p.key, i, g, n);
+    if (warp == 0) {
+        ChildCand cand{p.key, i, g, n, sm.flags, A, status};
+        repair_warp(sm.kept, sm.holes, total, C, cand, p.key, i, g, n);
+    }
+    if (p.est_out) row_estimate(p, C, i);
 }
 
 __global__ void __launch_bounds__(kGaBlock) offspring_kernel(GaParams p, const int* __restrict__ pop_in,

@@ -222,6 +222,11 @@ struct GaParams {
     int g;               // generation when g_ptr is null
     const int* g_ptr;    // device-resident generation counter (CUDA-graph replay)
     const long long* cum;  // roulette cumulative weights [s] (GAPA_FLAG_ROULETTE)
+    // cost estimates of the rows for the cut-local fitness kernel (all null: none):
+    // est_out[row] = sum over the row's genes of est_cut[est_perm[gene]]
+    const int* est_perm;
+    const int* est_cut;
+    unsigned* est_out;
 };
 
 // One instance of a batched run (device-side descriptor).
@@ -251,7 +256,13 @@ struct BatchPacket {
     int b, i0, cnt, teams;
 };
 
-int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st);
+int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
+                        const unsigned* est = nullptr);
+// True when gapa_launch_fitness runs the cut-local TREE kernel on this context (which then uses
+// per-member cost estimates; callers that produce the rows may pass them precomputed).
+bool gapa_fitness_uses_estimates(const gapa_ctx* c, int s);
+// Device buffer of kOrderCap cost estimates owned by the graph (valid when the above is true).
+unsigned* gapa_estimate_buffer(gapa_ctx* c);
 int gapa_launch_init_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int buf,
                              cudaStream_t st);
 int gapa_launch_offspring_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int src,
