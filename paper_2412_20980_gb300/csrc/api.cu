@@ -551,9 +551,10 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
             else if (kids[p].x + kids[p].y != x) contiguous = false;
             kids[p].y += 1;
         }
-        const size_t fixed = par_ints * 4 + 48, min_list = gapa_dev::tree16l_min_list_bytes(n);
+        const int team = gapa_fitness_block_for(n);
+        const size_t fixed = par_ints * 4 + 48, min_list = gapa_dev::tree16l_min_list_bytes(n, team);
         const size_t want = std::max(min_list, ((((size_t)n * 2) + 15) & ~(size_t)15) + gapa_dev::tree16l_bitmap_bytes(n) +
-                                                   gapa_dev::tree16l_scratch_bytes());
+                                                   gapa_dev::tree16l_scratch_bytes(team));
         // two members per SM: half the SM's shared memory, less the runtime's reserve and the
         // kernel's static shared memory (under 1 KB)
         const size_t per_block = c->smem_per_sm / 2, other = c->smem_reserved + 1024;

@@ -29,6 +29,7 @@ struct gapa_batch {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     int* status = nullptr;          // ctxs[0]'s status word
     std::vector<int> teams;         // members per CTA per instance
+    std::vector<int> use_local;     // per instance: the cut-local kernel (context set to TREE_LOCAL)
     // device memory
     BatchDesc* d_desc = nullptr;
     int2* d_rows = nullptr;
@@ -51,6 +52,15 @@ struct gapa_batch {
 namespace {
 
 size_t need16(int n) { return gapa_dev::tree16_smem_bytes(n); }
+
+// Slice of one team of T threads that also holds the cut-local kernel's layout (minimum list region).
+size_t need_local(int n, int T) {
+    return gapa_dev::tree16l_lab_ints(n) * 4 + gapa_dev::tree16l_min_list_bytes(n, T) + 48;
+}
+
+// Slice bytes of instance x at c teams: the cut-local layout where the graph has it and c slices of
+// it fit, else the full pipeline's.
+size_t slice_need(const gapa_batch* b, int x, int c);
 
 // Largest team count (1, 2, 4, 8) whose slices hold the graph and keep >= 128 threads per team
 // and at least ~8 nodes per thread.
@@ -81,6 +91,14 @@ void free_batch_device(gapa_batch* b) {
     b->d_buf = nullptr;
 }
 
+size_t slice_need(const gapa_batch* b, int x, int c) {
+    const DeviceGraph& g = b->ctxs[x]->g;
+    const size_t full = need16(g.n);
+    if (!b->desc[x].kids || !b->use_local[x]) return full;  // the instance runs the full pipeline
+    const size_t local = std::max(full, need_local(g.n, 1024 / c));
+    return (size_t)c * ((local + 15) & ~(size_t)15) <= b->fit_max_dyn ? local : full;
+}
+
 // Work-queue packets for the current team counts, largest graphs first.
 int build_packets(gapa_batch* b) {
     std::vector<int> order(b->num);
@@ -94,7 +112,7 @@ int build_packets(gapa_batch* b) {
     size_t smem = 0;
     for (int x : order) {
         const int c = b->teams[x];
-        smem = std::max(smem, (size_t)c * ((need16(b->ctxs[x]->g.n) + 15) & ~(size_t)15));
+        smem = std::max(smem, (size_t)c * ((slice_need(b, x, c) + 15) & ~(size_t)15));
         for (int first = 0; first <= 1; ++first) {
             auto& list = first == 0 ? all : kids;
             for (int i0 = first; i0 < b->cfgs[x].pop; i0 += c)
@@ -115,7 +133,17 @@ int build_packets(gapa_batch* b) {
     if (cudaMalloc(&b->d_pk, sizeof(BatchPacket) * std::max<size_t>(all.size(), 1)) != cudaSuccess)
         return gapa_fail(GAPA_ERR_OOM, "batch packets");
     GAPA_CUDA(cudaMemcpy(b->d_pk, all.data(), sizeof(BatchPacket) * all.size(), cudaMemcpyHostToDevice));
-    for (int i = 0; i < b->num; ++i) b->desc[i].teams = b->teams[i];
+    for (int i = 0; i < b->num; ++i) {
+        BatchDesc& d = b->desc[i];
+        d.teams = b->teams[i];
+        // the cut-local kernel where the instance's slice holds its layout
+        const int n = b->ctxs[i]->g.n, T = 1024 / d.teams;
+        const size_t slice = (b->fit_smem / (size_t)d.teams) & ~(size_t)15;
+        const size_t fixed = gapa_dev::tree16l_lab_ints(n) * 4 + 48;
+        d.list_bytes = 0;
+        if (d.kids && b->use_local[i] && slice >= fixed + gapa_dev::tree16l_min_list_bytes(n, T))
+            d.list_bytes = (int)((slice - fixed) & ~(size_t)15);
+    }
     return GAPA_OK;
 }
 
@@ -282,6 +310,7 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
     size_t fo = 0;
     b->desc.resize(num);
     b->teams.resize(num);
+    b->use_local.assign(num, 0);
     for (int i = 0; i < num; ++i) {
         const gapa_config& g = cfgs[i];
         const DeviceGraph& dg = ctxs[i]->g;
@@ -314,6 +343,16 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         d.fcol16 = dg.fcol16;
         d.mean_deg_x16 = dg.mean_deg_x16;
         d.objective = b->ctxs[i]->objective;
+        if (dg.local_list_bytes > 0 && b->ctxs[i]->fitness_variant == GAPA_FITNESS_TREE_LOCAL) {
+            // the cut-local kernel only where the context asks for it: inside a packet every team waits
+            // for its slowest member, and without cost ordering the cut-local kernel's uneven member
+            // times lost to the full pipeline on the batched workload (213-252 ms against 208 ms)
+            b->use_local[i] = 1;
+            d.tparent = dg.tparent;
+            d.kids = dg.kids;
+            d.roots = dg.roots;
+            d.num_roots = dg.num_roots;
+        }
         b->teams[i] = default_teams(dg.n, b->fit_max_dyn);
         for (int r = 0; r < g.pop; ++r) rows.push_back(make_int2(i, r));
     }

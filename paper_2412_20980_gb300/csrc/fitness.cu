@@ -505,6 +505,8 @@ int gapa_fitness_prepare(gapa_ctx* c, int s) {
     return gapa_reserve((void**)&c->labels, &c->labels_cap, wave * (size_t)c->g.n, sizeof(int));
 }
 
+int gapa_fitness_block_for(int n) { return smem_block_for(n); }
+
 bool gapa_fitness_uses_estimates(const gapa_ctx* c, int s) {
     return c->g.packed16 && c->g.local_list_bytes > 0 && s > 1 && s <= kOrderCap &&
            c->genes == GAPA_GENES_NODES &&
@@ -732,13 +734,21 @@ __global__ void __launch_bounds__(1024, 1) fitness_batched_kernel(const BatchDes
             const gapa_dev::Team tm{(int)threadIdx.x - team * T, T, 1 + team};
             const unsigned slice = (smem_bytes / (unsigned)q.teams) & ~15u;
             int* lab = reinterpret_cast<int*>(smem + (size_t)team * slice);
-            const gapa_dev::Tree16Graph g{bd.n,       bd.perm,        bd.palt, bd.lo_ptr, bd.lo_col,
-                                          bd.nontree, bd.num_nontree, bd.fptr, bd.fcol16, 0, bd.mean_deg_x16,
-                                          bd.objective};
+            const gapa_dev::Tree16Graph g{bd.n,        bd.perm,      bd.palt,        bd.lo_ptr,   bd.lo_col,
+                                          bd.nontree,  bd.num_nontree, bd.fptr,      bd.fcol16,   0,
+                                          bd.mean_deg_x16, bd.objective, bd.tparent, bd.kids,     bd.roots,
+                                          bd.num_roots, bd.list_bytes};
             const int member = q.i0 + team;
-            gapa_dev::tree16_member(tm, lab, reinterpret_cast<unsigned*>(lab + bd.n), g,
-                                    bd.pop[buf] + (size_t)member * bd.p.k, bd.p.k,
-                                    reinterpret_cast<long long*>(bd.fit[buf]) + member, red[team], status);
+            const int* genes = bd.pop[buf] + (size_t)member * bd.p.k;
+            long long* out = reinterpret_cast<long long*>(bd.fit[buf]) + member;
+            if (bd.list_bytes > 0) {
+                unsigned* region = reinterpret_cast<unsigned*>(lab + gapa_dev::tree16l_lab_ints(bd.n));
+                int* scal = reinterpret_cast<int*>(region) + bd.list_bytes / 4;
+                gapa_dev::tree16_member_local(tm, lab, region, scal, g, genes, bd.p.k, out, red[team], status);
+            } else {
+                gapa_dev::tree16_member(tm, lab, reinterpret_cast<unsigned*>(lab + bd.n), g, genes, bd.p.k, out,
+                                        red[team], status);
+            }
         }
         __syncthreads();
     }

@@ -249,6 +249,12 @@ struct BatchDesc {
     int mean_deg_x16;
     int objective;       // GAPA_OBJECTIVE_*
     int teams;           // members per CTA in the batched fitness kernel (1, 2, 4 or 8)
+    // cut-local TREE kernel (tree16_member_local): list_bytes > 0 when each team's slice holds it
+    const int* tparent;
+    const int2* kids;
+    const int* roots;
+    int num_roots;
+    int list_bytes;
 };
 
 // A packet of the batched fitness work queue: members i0 .. i0+cnt-1 of instance b.
@@ -261,6 +267,8 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
 // True when gapa_launch_fitness runs the cut-local TREE kernel on this context (which then uses
 // per-member cost estimates; callers that produce the rows may pass them precomputed).
 bool gapa_fitness_uses_estimates(const gapa_ctx* c, int s);
+// Threads of the one-member-per-CTA fitness kernels for a graph of n nodes.
+int gapa_fitness_block_for(int n);
 // Device buffer of kOrderCap cost estimates owned by the graph (valid when the above is true).
 unsigned* gapa_estimate_buffer(gapa_ctx* c);
 int gapa_launch_init_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int buf,

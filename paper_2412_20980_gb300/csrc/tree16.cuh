@@ -404,22 +404,21 @@ __device__ __forceinline__ void tree16_member(const Team& tm, volatile int* lab,
 // estimate says the list will be long).
 
 constexpr int kLocalLevels = 256;
-constexpr int kLocalChunk = 1024;  // owners per dealing round: the largest team
 constexpr long long kLocalSpinLimit = 1ll << 24;
 
 // Layout of one member: labels (n rounded up to a multiple of 4, so the bulk
 // copy moves whole 16-byte units), the list region, eight team scalars and
 // the mbarrier.  The list region holds, from its start, the deletion bitmap
 // (until the re-picks are done) and then the list (16-bit node ids); at its
-// end three kLocalChunk-int arrays for the dealing rounds and the bitmap of
-// listed nodes.
+// end three arrays of one int per team thread for the dealing rounds, and
+// the bitmap of listed nodes.
 __host__ __device__ __forceinline__ size_t tree16l_lab_ints(int n) { return ((size_t)n + 3) & ~(size_t)3; }
 __host__ __device__ __forceinline__ size_t tree16l_bitmap_bytes(int n) {
     return ((((size_t)n + 31) >> 5) * 4 + 15) & ~(size_t)15;
 }
-__host__ __device__ __forceinline__ size_t tree16l_scratch_bytes() { return (size_t)3 * kLocalChunk * 4; }
-__host__ __device__ __forceinline__ size_t tree16l_min_list_bytes(int n) {
-    return 2 * tree16l_bitmap_bytes(n) + tree16l_scratch_bytes();
+__host__ __device__ __forceinline__ size_t tree16l_scratch_bytes(int team) { return (size_t)3 * team * 4; }
+__host__ __device__ __forceinline__ size_t tree16l_min_list_bytes(int n, int team) {
+    return 2 * tree16l_bitmap_bytes(n) + tree16l_scratch_bytes(team);
 }
 __host__ __device__ __forceinline__ size_t tree16l_smem_bytes(int n, size_t list_bytes) {
     return tree16l_lab_ints(n) * 4 + list_bytes + 32 + 16;
@@ -520,17 +519,17 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
                                                     long long* red, int* status) {
     const int tid = tm.tid, T = tm.T, n = g.n, lane = tid & 31;
     const int words = (n + 31) >> 5;
-    volatile int* scalar = scal_base;  // 0 R, 1 list length, 2 repeated genes, 3 live
+    volatile int* scalar = scal_base;  // 0 R, 1 list length, 2 repeated genes, 3 live, 4 labels landed
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(scal_base + 8);
     const unsigned bar_a = tree16l_smem_u32(bar);
     unsigned* dead = region;
     unsigned short* list = reinterpret_cast<unsigned short*>(region);
     const int bm_bytes = (int)tree16l_bitmap_bytes(n);
-    char* tail_area = reinterpret_cast<char*>(region) + g.list_bytes - bm_bytes - (int)tree16l_scratch_bytes();
+    char* tail_area = reinterpret_cast<char*>(region) + g.list_bytes - bm_bytes - (int)tree16l_scratch_bytes(T);
     int* s_off = reinterpret_cast<int*>(tail_area);
-    int* s_first = s_off + kLocalChunk;
-    int* s_own = s_first + kLocalChunk;
-    unsigned* listed_bm = reinterpret_cast<unsigned*>(s_own + kLocalChunk);
+    int* s_first = s_off + T;
+    int* s_own = s_first + T;
+    unsigned* listed_bm = reinterpret_cast<unsigned*>(s_own + T);
     const int cap = (int)((tail_area - reinterpret_cast<char*>(region)) >> 1);
     int* ws = reinterpret_cast<int*>(red);
     if (tid == 0) {
@@ -543,7 +542,9 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
     }
     tm.sync();
     if (tid == 0) {
-        // labels <- tree parents, in chunks of at most 32 KB
+        // labels <- tree parents, in chunks of at most 32 KB (the fence orders this team's earlier
+        // generic-proxy use of the labels before the async-proxy writes)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         const unsigned bytes = (unsigned)(tree16l_lab_ints(n) * 4);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
         const unsigned dst = tree16l_smem_u32((const void*)lab);
@@ -601,12 +602,16 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
         }
     }
     // the labels must have landed before anyone reads or writes them
-    const bool ok = tree16l_wait(bar_a, 0u);
+    bool ok = tree16l_wait(bar_a, 0u);
     if (!ok) {
         atomicOr(status, GAPA_DEV_TIMEOUT);
         tree16l_wait(bar_a, 0u);  // bounded: the copy may still be in flight
     }
+    if (tid == 0) scalar[4] = ok;
     tm.sync();
+    ok = scalar[4] != 0;  // thread 0's view, the same for the whole team
+    // the copy has landed: the mbarrier's memory may be reused
+    if (tid == 0 && ok) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar_a) : "memory");
     if (!ok) {
         if (tid == 0) *out = -1;
         return;

@@ -20,7 +20,7 @@ SPECS = [  # (n, m, pop, seed): uneven sizes and populations
 ]
 
 
-def _batch(specs, teams=None):
+def _batch(specs, teams=None, variant=None):
     from paper_2412_20980_gb300 import Batch, Context, make_config
     from paper_2412_20980_gb300 import build as b
 
@@ -29,6 +29,8 @@ def _batch(specs, teams=None):
     for (n, m, pop, seed) in specs:
         g = synth.ba_graph(n, m, seed)
         c = Context(0)
+        if variant is not None:
+            c.set_fitness_kernel(variant)
         c.graph_upload(g.row_ptr, g.col)
         graphs.append(g)
         ctxs.append(c)
@@ -52,6 +54,21 @@ def test_batch_matches_oracle_per_instance(gens):
         want = _oracle(g, cfg, gens)
         assert np.array_equal(got["traj"][i], want["traj"]), i
         assert got["best_fit"][i] == want["best_fit"], i
+        assert np.array_equal(got["best_sets"][i], want["best_set"]), i
+    bt.close()
+
+
+@pytest.mark.parametrize("teams", [[1] * 6, [8, 8, 4, 4, 2, 1], [2, 4, 8, 2, 1, 1]])
+def test_batch_cut_local_kernel_matches_oracle(teams):
+    """Contexts set to the cut-local kernel: every team count runs tree16_member_local in its
+    slice of the persistent kernel (bulk copy and mbarrier reused member after member)."""
+    from paper_2412_20980_gb300.gapa import FITNESS_TREE_LOCAL
+
+    bt, graphs, ctxs, cfgs = _batch(SPECS, teams=teams, variant=FITNESS_TREE_LOCAL)
+    got = bt.run(7)
+    for i, (g, cfg) in enumerate(zip(graphs, cfgs)):
+        want = _oracle(g, cfg, 7)
+        assert np.array_equal(got["traj"][i], want["traj"]), i
         assert np.array_equal(got["best_sets"][i], want["best_set"]), i
     bt.close()
 
