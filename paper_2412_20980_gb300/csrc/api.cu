@@ -40,6 +40,10 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.roots);
     cudaFree(g.cut);
     cudaFree(g.order);
+    DeviceForest& a = g.alt;
+    void* alt_ptrs[] = {a.perm, a.tparent, a.palt, a.lo_ptr, a.lo_col, a.kids, a.roots, a.cut, a.fptr, a.fcol16,
+                        a.nontree};
+    for (void* q : alt_ptrs) cudaFree(q);
     cudaFree(g.nontree);
     cudaFree(g.fptr);
     cudaFree(g.fcol16);
@@ -123,6 +127,152 @@ BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vecto
         for (int32_t e = f.lo_ptr[b] + 1; e < f.lo_ptr[b + 1]; ++e) f.nontree.emplace_back(f.lo_col[e], b);
     std::sort(f.nontree.begin(), f.nontree.end());
     return f;
+}
+
+// The forest of a numbering `perm` (host side, n <= 65536): every node's
+// parent is its lowest-numbered neighbour when that one is lower (a root
+// otherwise), so parents precede children.  `ok` is false when some node's
+// children do not fall into at most two runs of consecutive numbers.
+struct ForestHost {
+    std::vector<int32_t> perm, tparent, lo_ptr, lo_col, roots, cut, fptr, fcol;
+    std::vector<int4> kids;
+    std::vector<int2> palt;
+    std::vector<uint32_t> nontree;
+    bool ok = true;
+};
+
+ForestHost forest_host(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                       const std::vector<int32_t>& perm) {
+    ForestHost f;
+    f.perm = perm;
+    std::vector<int32_t> inv((size_t)n);
+    for (int32_t v = 0; v < n; ++v) inv[perm[v]] = v;
+    f.tparent.assign((size_t)n, 0);
+    f.lo_ptr.assign((size_t)n + 1, 0);
+    f.palt.assign((size_t)n, make_int2(0, -1));
+    f.fptr.assign((size_t)n + 1, 0);
+    f.fcol.reserve(col.size());
+    std::vector<int32_t> tmp;
+    for (int32_t b = 0; b < n; ++b) {
+        const int32_t v = inv[b];
+        tmp.clear();
+        for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
+            const int32_t a = perm[col[e]];
+            f.fcol.push_back(a);
+            if (a < b) tmp.push_back(a);
+        }
+        f.fptr[b + 1] = (int32_t)f.fcol.size();
+        std::sort(tmp.begin(), tmp.end());
+        f.tparent[b] = tmp.empty() ? b : tmp[0];
+        if (tmp.empty()) f.roots.push_back(b);
+        f.palt[b] = make_int2(f.tparent[b], tmp.size() >= 2 ? tmp[1] : -1);
+        for (size_t i = 1; i < tmp.size(); ++i) f.nontree.push_back(((uint32_t)tmp[i] << 16) | (uint32_t)b);
+        f.lo_col.insert(f.lo_col.end(), tmp.begin(), tmp.end());
+        f.lo_ptr[b + 1] = (int32_t)f.lo_col.size();
+    }
+    std::sort(f.nontree.begin(), f.nontree.end());
+    // children runs (children arrive in ascending order)
+    f.kids.assign((size_t)n, make_int4(0, 0, 0, 0));
+    for (int32_t b = 0; b < n; ++b) f.kids[b].x = b;
+    for (int32_t x = 0; x < n && f.ok; ++x) {
+        const int32_t p = f.tparent[x];
+        if (p == x) continue;
+        int4& k = f.kids[p];
+        if (k.y == 0) {
+            k.x = x;
+            k.y = 1;
+        } else if (k.w == 0 && k.x + k.y == x) {
+            k.y += 1;
+        } else if (k.w == 0) {
+            k.z = x;  // start of the second run (stored below as start - first run's length)
+            k.w = 1;
+        } else if (k.z + k.w == x) {
+            k.w += 1;
+        } else {
+            f.ok = false;
+        }
+    }
+    for (int32_t b = 0; b < n; ++b)
+        if (f.kids[b].w) f.kids[b].z -= f.kids[b].y;
+    // cost table: the nodes below those children of b whose only lower neighbour is b
+    std::vector<int32_t> below((size_t)n, 1);
+    f.cut.assign((size_t)n, 0);
+    for (int32_t v = n - 1; v >= 0; --v)
+        if (f.tparent[v] != v) below[f.tparent[v]] += below[v];
+    for (int32_t v = 0; v < n; ++v)
+        if (f.tparent[v] != v && f.lo_ptr[v + 1] - f.lo_ptr[v] == 1) f.cut[f.tparent[v]] += below[v];
+    return f;
+}
+
+// Numbering with the top `hubs` nodes by degree last: BFS over the graph
+// without them (from the highest-degree remaining node of each component),
+// then the hubs by their lowest-numbered non-hub neighbour (hubs without one
+// at the end), so that deleting a hub cuts no tree edge below it.
+std::vector<int32_t> hub_last_perm(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                                   int hubs) {
+    std::vector<int32_t> by_deg((size_t)n), perm((size_t)n, -1);
+    for (int32_t v = 0; v < n; ++v) by_deg[v] = v;
+    std::stable_sort(by_deg.begin(), by_deg.end(),
+                     [&](int32_t a, int32_t b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+    std::vector<char> hub((size_t)n, 0);
+    for (int i = 0; i < hubs && i < n; ++i) hub[by_deg[i]] = 1;
+    std::vector<int32_t> queue;
+    queue.reserve((size_t)n);
+    int32_t next = 0;
+    for (int32_t root : by_deg) {
+        if (perm[root] >= 0 || hub[root]) continue;
+        size_t head = queue.size();
+        queue.push_back(root);
+        perm[root] = next++;
+        while (head < queue.size()) {
+            const int32_t u = queue[head++];
+            for (int32_t e = rp[u]; e < rp[u + 1]; ++e)
+                if (!hub[col[e]] && perm[col[e]] < 0) {
+                    perm[col[e]] = next++;
+                    queue.push_back(col[e]);
+                }
+        }
+    }
+    std::vector<std::pair<int64_t, int32_t>> hk;
+    for (int i = 0; i < hubs && i < n; ++i) {
+        const int32_t h = by_deg[i];
+        int32_t low = INT32_MAX;
+        for (int32_t e = rp[h]; e < rp[h + 1]; ++e)
+            if (!hub[col[e]]) low = std::min(low, perm[col[e]]);
+        hk.emplace_back(((int64_t)low << 20) | i, h);
+    }
+    std::sort(hk.begin(), hk.end());
+    for (auto& x : hk) perm[x.second] = next++;
+    return perm;
+}
+
+// Device copy of a forest (nullptr members on failure, which the caller frees).
+int upload_forest(const ForestHost& f, int32_t n, DeviceForest& d) {
+    const size_t par_ints = gapa_dev::tree16l_lab_ints(n);
+    std::vector<int32_t> par(f.tparent);
+    par.resize(par_ints, 0);
+    std::vector<uint16_t> f16(f.fcol.begin(), f.fcol.end());
+    auto up = [](void** dst, const void* src, size_t bytes) {
+        if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+        return bytes == 0 || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = up((void**)&d.perm, f.perm.data(), 4 * (size_t)n) && up((void**)&d.tparent, par.data(), 4 * par_ints) &&
+              up((void**)&d.palt, f.palt.data(), sizeof(int2) * (size_t)n) &&
+              up((void**)&d.lo_ptr, f.lo_ptr.data(), 4 * ((size_t)n + 1)) &&
+              up((void**)&d.lo_col, f.lo_col.data(), 4 * f.lo_col.size()) &&
+              up((void**)&d.kids, f.kids.data(), sizeof(int4) * (size_t)n) &&
+              up((void**)&d.roots, f.roots.data(), 4 * f.roots.size()) &&
+              up((void**)&d.cut, f.cut.data(), 4 * (size_t)n) &&
+              up((void**)&d.fptr, f.fptr.data(), 4 * ((size_t)n + 1)) &&
+              up((void**)&d.fcol16, f16.data(), 2 * f16.size()) &&
+              up((void**)&d.nontree, f.nontree.data(), 4 * f.nontree.size());
+    d.num_roots = (int)f.roots.size();
+    d.num_nontree = (int)f.nontree.size();
+    if (!ok) {
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "second forest of %d nodes", n);
+    }
+    return GAPA_OK;
 }
 
 // Host-side validation of a symmetric simple CSR; returns the rows sorted.
@@ -211,6 +361,8 @@ GaParams make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_pt
     p.cum = nullptr;
     p.est_perm = nullptr;
     p.est_cut = nullptr;
+    p.est_perm2 = nullptr;
+    p.est_cut2 = nullptr;
     p.est_out = nullptr;
     return p;
 }
@@ -248,6 +400,10 @@ int enqueue_generation(gapa_ctx* c, const GaParams& p0, int lambda, const int32_
     if (est) {
         p.est_perm = c->g.perm;
         p.est_cut = c->g.cut;
+        if (c->g.has_alt) {
+            p.est_perm2 = c->g.alt.perm;
+            p.est_cut2 = c->g.alt.cut;
+        }
         p.est_out = est;
     }
     if (p.flags & GAPA_FLAG_MU_PLUS_LAMBDA) {
@@ -541,9 +697,9 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     if (g.packed16) {
         // cut-local TREE kernel: children ranges (consecutive in BFS order), component roots, and a
         // list region as large as two members per SM allow (one per SM when the labels need it)
-        std::vector<int2> kids((size_t)n);
+        std::vector<int4> kids((size_t)n);
         bool contiguous = true;
-        for (int32_t b = 0; b < n; ++b) kids[b] = make_int2(b, 0);
+        for (int32_t b = 0; b < n; ++b) kids[b] = make_int4(b, 0, 0, 0);
         for (int32_t x = 0; x < n && contiguous; ++x) {
             const int32_t p = bf.tparent[x];
             if (p == x) continue;
@@ -571,21 +727,35 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
                 if (bf.tparent[v] != v) below[bf.tparent[v]] += below[v];
             for (int32_t v = 0; v < n; ++v)
                 if (bf.tparent[v] != v && bf.lo_ptr[v + 1] - bf.lo_ptr[v] == 1) cut[bf.tparent[v]] += below[v];
-            if (cudaMalloc(&g.kids, sizeof(int2) * std::max<size_t>((size_t)n, 1)) != cudaSuccess ||
+            if (cudaMalloc(&g.kids, sizeof(int4) * std::max<size_t>((size_t)n, 1)) != cudaSuccess ||
                 cudaMalloc(&g.cut, sizeof(int32_t) * std::max<size_t>((size_t)n, 1)) != cudaSuccess ||
-                cudaMalloc(&g.order, sizeof(int32_t) * 2 * (size_t)kOrderCap) != cudaSuccess ||
+                cudaMalloc(&g.order, sizeof(int32_t) * 4 * (size_t)kOrderCap) != cudaSuccess ||
                 cudaMalloc(&g.roots, sizeof(int32_t) * std::max<size_t>(bf.roots.size(), 1)) != cudaSuccess) {
                 free_graph(g);
                 cudaGetLastError();
                 return gapa_fail(GAPA_ERR_OOM, "children ranges of %d nodes", n);
             }
-            GAPA_CUDA(cudaMemcpy(g.kids, kids.data(), sizeof(int2) * (size_t)n, cudaMemcpyHostToDevice));
+            GAPA_CUDA(cudaMemcpy(g.kids, kids.data(), sizeof(int4) * (size_t)n, cudaMemcpyHostToDevice));
             GAPA_CUDA(cudaMemcpy(g.cut, cut.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
             if (!bf.roots.empty())
                 GAPA_CUDA(cudaMemcpy(g.roots, bf.roots.data(), sizeof(int32_t) * bf.roots.size(),
                                      cudaMemcpyHostToDevice));
             g.num_roots = (int)bf.roots.size();
             g.local_list_bytes = (int)list_bytes;
+            // the second forest, numbered with the top hubs last (about 0.5 % of the nodes, 8 to 256):
+            // members that delete hubs cut it far less
+            const int hubs = std::max(8, std::min(256, n / 200));
+            if (n > 4 * hubs) {
+                const ForestHost fb = forest_host(n, rp, sorted, hub_last_perm(n, rp, sorted, hubs));
+                if (fb.ok) {
+                    int frc = upload_forest(fb, n, g.alt);
+                    if (frc != GAPA_OK) {
+                        free_graph(g);
+                        return frc;
+                    }
+                    g.has_alt = true;
+                }
+            }
         }
     }
     GAPA_CUDA(cudaMemcpy(g.lo_ptr, bf.lo_ptr.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice));

@@ -286,36 +286,49 @@ struct GraphArgs {
     int join_mode;
     int mean_deg_x16;
     int objective;
-    const int2* kids;
+    const int4* kids;
     const int* roots;
     int num_roots;
     int list_bytes;
     const unsigned* est;  // cut-local kernel: per-member cost estimates (may be null)
+    DeviceForest alt;     // cut-local kernel: the second forest (alt.perm null: none)
 };
 
 enum Variant : int { V_EDGES = 0, V_SAMPLED = 1, V_TREE16 = 2, V_TREE32 = 3, V_TREE16L = 4 };
 
 template <int kVar>
 __device__ __forceinline__ void member_pc(volatile int* lab, const GraphArgs& g, const int* __restrict__ genes, int k, int m,
-                                          long long* out, int* status, long long* red, int* sh_root) {
+                                          long long* out, int* status, long long* red, int* sh_root,
+                                          bool use_alt = false) {
     if (kVar == V_TREE16 || kVar == V_TREE16L) {
         // the whole CTA is one team; the deleted-node bitmap sits right after the labels
         const gapa_dev::Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
+        // the cut-local kernel leaves members expected to list over a quarter of the nodes (the
+        // BFS tree shattered) to the full pipeline from the start
+        const bool full = kVar == V_TREE16 || (g.est && __ldg(&g.est[m]) > (unsigned)(g.n / 4));
+        unsigned* region = (unsigned*)(lab + gapa_dev::tree16l_lab_ints(g.n));
+        int* scal = (int*)region + g.list_bytes / 4;
+        if (kVar == V_TREE16L && use_alt && !full) {
+            // the second forest: the same graph in its own numbering (its own constant record, so
+            // that every field stays a kernel-parameter read)
+            const DeviceForest& a = g.alt;
+            const gapa_dev::Tree16Graph tb{g.n,           a.perm,          a.palt,          a.lo_ptr,
+                                           a.lo_col,      a.nontree,       a.num_nontree,   a.fptr,
+                                           a.fcol16,      g.join_mode,     g.mean_deg_x16,  g.objective,
+                                           a.tparent,     a.kids,          a.roots,         a.num_roots,
+                                           g.list_bytes};
+            gapa_dev::tree16_member_local(tm, lab, region, scal, tb, genes, k, out, red, status);
+            return;
+        }
         const gapa_dev::Tree16Graph t16{g.n,           g.perm,          g.palt,          g.lo_ptr,
                                         g.lo_col,      (const unsigned*)g.nontree,      g.num_nontree,
                                         g.fptr,        g.fcol16,        g.join_mode,     g.mean_deg_x16,
                                         g.objective,   g.tparent,       g.kids,          g.roots,
                                         g.num_roots,   g.list_bytes};
-        // the cut-local kernel leaves members expected to list over a quarter of the nodes (the
-        // BFS tree shattered) to the full pipeline from the start
-        const bool full = kVar == V_TREE16 || (g.est && __ldg(&g.est[m]) > (unsigned)(g.n / 4));
-        if (full) {
+        if (full)
             gapa_dev::tree16_member(tm, lab, (unsigned*)(lab + g.n), t16, genes, k, out, red, status);
-        } else {
-            unsigned* region = (unsigned*)(lab + gapa_dev::tree16l_lab_ints(g.n));
-            int* scal = (int*)region + g.list_bytes / 4;
+        else
             gapa_dev::tree16_member_local(tm, lab, region, scal, t16, genes, k, out, red, status);
-        }
         return;
     }
     if (kVar == V_TREE32) {
@@ -376,54 +389,81 @@ __global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* _
     extern __shared__ int smem_lab[];
     __shared__ long long red[32];
     __shared__ int sh_root;
-    const int i = order ? __ldg(&order[blockIdx.x]) : (int)blockIdx.x;
-    member_pc<kVar>(smem_lab, g, pop + (size_t)i * k, k, i, &fit[i], status, red, &sh_root);
+    const int e = order ? __ldg(&order[blockIdx.x]) : (int)blockIdx.x;
+    const int i = e & 0x3FFFFFFF;  // bit 30: evaluate on the second forest
+    member_pc<kVar>(smem_lab, g, pop + (size_t)i * k, k, i, &fit[i], status, red, &sh_root, (e >> 30) & 1);
 }
 
-// Cost estimate of every member for the cut-local kernel: the sum over its
-// genes of the nodes that deleting the gene alone leaves in pieces to be
-// listed (one 128-thread CTA per member, four independent gathers in flight
-// per thread; saturates at 2^31 - 1).
+// Cost estimate of every member for the cut-local kernel under each forest:
+// the sum over its genes of the nodes that deleting the gene alone leaves in
+// pieces to be listed (one 128-thread CTA per member, four independent
+// gathers in flight per thread; saturates at 2^31 - 1).  perm2 null: one forest.
 __global__ void __launch_bounds__(128) local_cost_kernel(const int* __restrict__ pop, int k, int n,
                                                          const int* __restrict__ perm, const int* __restrict__ cut,
-                                                         unsigned* __restrict__ est) {
-    __shared__ long long part[4];
+                                                         const int* __restrict__ perm2,
+                                                         const int* __restrict__ cut2, unsigned* __restrict__ est,
+                                                         unsigned* __restrict__ est2) {
+    __shared__ long long part[2][4];
     const int m = blockIdx.x, t = threadIdx.x;
     const int* genes = pop + (size_t)m * k;
-    long long c = 0;
+    long long c = 0, c2 = 0;
     int j = t;
     for (; j + 384 < k; j += 512) {
         int d[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) d[u] = __ldg(&genes[j + 128 * u]);
-        int b[4];
+        int b[4], b2[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = (unsigned)d[u] < (unsigned)n ? __ldg(&perm[d[u]]) : -1;
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = (unsigned)d[u] < (unsigned)n;
+            b[u] = ok ? __ldg(&perm[d[u]]) : -1;
+            b2[u] = ok && perm2 ? __ldg(&perm2[d[u]]) : -1;
+        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) c += b[u] >= 0 ? __ldg(&cut[b[u]]) : 0;
+        for (int u = 0; u < 4; ++u) {
+            c += b[u] >= 0 ? __ldg(&cut[b[u]]) : 0;
+            c2 += b2[u] >= 0 ? __ldg(&cut2[b2[u]]) : 0;
+        }
     }
     for (; j < k; j += 128) {
         const int d = __ldg(&genes[j]);
-        if ((unsigned)d < (unsigned)n) c += __ldg(&cut[__ldg(&perm[d])]);
+        if ((unsigned)d < (unsigned)n) {
+            c += __ldg(&cut[__ldg(&perm[d])]);
+            if (perm2) c2 += __ldg(&cut2[__ldg(&perm2[d])]);
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if ((t & 31) == 0) part[t >> 5] = c;
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        c2 += __shfl_down_sync(0xffffffffu, c2, o);
+    }
+    if ((t & 31) == 0) {
+        part[0][t >> 5] = c;
+        part[1][t >> 5] = c2;
+    }
     __syncthreads();
     if (t == 0) {
-        const long long s = (part[0] + part[1]) + (part[2] + part[3]);
-        est[m] = (unsigned)(s < 0x7FFFFFFFll ? s : 0x7FFFFFFFll);
+        const long long s1 = (part[0][0] + part[0][1]) + (part[0][2] + part[0][3]);
+        const long long s2 = (part[1][0] + part[1][1]) + (part[1][2] + part[1][3]);
+        est[m] = (unsigned)(s1 < 0x7FFFFFFFll ? s1 : 0x7FFFFFFFll);
+        est2[m] = perm2 ? (unsigned)(s2 < 0x7FFFFFFFll ? s2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
     }
 }
 
-// Members by decreasing bit length of their estimate (a counting sort over
-// the 33 values of its count of leading zeros, in one CTA; the order within a
-// class is arbitrary).
-__global__ void __launch_bounds__(1024) local_order_kernel(const unsigned* __restrict__ est, int s,
-                                                           int* __restrict__ order) {
+// Members by decreasing bit length of their lower estimate (a counting sort
+// over the 33 values of its count of leading zeros, in one CTA; the order
+// within a class is arbitrary).  order[i] = member | 1 << 30 when the second
+// forest has the lower estimate; est_min[m] = the lower estimate.
+__global__ void __launch_bounds__(1024) local_order_kernel(const unsigned* __restrict__ est,
+                                                           const unsigned* __restrict__ est2, int s,
+                                                           int* __restrict__ order, unsigned* __restrict__ est_min) {
     __shared__ int cnt[33];
     if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int m = threadIdx.x; m < s; m += blockDim.x) atomicAdd(&cnt[__clz(est[m])], 1);
+    for (int m = threadIdx.x; m < s; m += blockDim.x) {
+        const unsigned a = est[m], b = est2[m], e = b < a ? b : a;
+        est_min[m] = e;
+        atomicAdd(&cnt[__clz(e)], 1);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int acc = 0;
@@ -434,7 +474,10 @@ __global__ void __launch_bounds__(1024) local_order_kernel(const unsigned* __res
         }
     }
     __syncthreads();
-    for (int m = threadIdx.x; m < s; m += blockDim.x) order[atomicAdd(&cnt[__clz(est[m])], 1)] = m;
+    for (int m = threadIdx.x; m < s; m += blockDim.x) {
+        const unsigned e = est_min[m];
+        order[atomicAdd(&cnt[__clz(e)], 1)] = m | (est2[m] < est[m] ? (1 << 30) : 0);
+    }
 }
 
 // One CTA per member, labels in a global scratch slice per CTA.
@@ -457,21 +500,25 @@ int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, 
                                                  : (size_t)n * 4;
     if (lab_bytes <= c->fit_smem_max) {
         const int* order = nullptr;
-        const unsigned* est = nullptr;
+        unsigned* est_min = nullptr;
         if (kVar == V_TREE16L && s > 1 && s <= kOrderCap) {
-            est = est_in;
-            if (!est) {
-                unsigned* e = gapa_estimate_buffer(c);
-                local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.perm, c->g.cut, e);
-                est = e;
+            // estimates under both forests (precomputed by the operator kernel, or here), then the order
+            unsigned* e1 = gapa_estimate_buffer(c);
+            unsigned* e2 = e1 + kOrderCap;
+            est_min = e2 + kOrderCap;
+            if (!est_in) {
+                const bool alt = c->g.has_alt;
+                local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.perm, c->g.cut, alt ? c->g.alt.perm : nullptr,
+                                                     alt ? c->g.alt.cut : nullptr, e1, e2);
                 if (kernels) *kernels += 1;
             }
-            local_order_kernel<<<1, 1024, 0, st>>>(est, s, c->g.order);
+            const unsigned* a = est_in ? est_in : e1;
+            local_order_kernel<<<1, 1024, 0, st>>>(a, a + kOrderCap, s, c->g.order, est_min);
             order = c->g.order;
             if (kernels) *kernels += 1;
         }
         GraphArgs gl = ga;
-        gl.est = order ? est : nullptr;
+        gl.est = est_min;
         cc_smem_kernel<kVar><<<s, smem_block_for(n), lab_bytes, st>>>(gl, pop, k, f, c->status, order);
         GAPA_CUDA(cudaGetLastError());
         return GAPA_OK;
@@ -546,6 +593,7 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
     ga.num_roots = c->g.num_roots;
     ga.list_bytes = c->g.local_list_bytes;
     ga.est = nullptr;
+    ga.alt = c->g.alt;
     if (c->objective == GAPA_OBJECTIVE_SIXDST_PC || c->objective == GAPA_OBJECTIVE_SIXDST_MCN) {
         if (c->genes != GAPA_GENES_NODES) return gapa_fail(GAPA_ERR_INVALID_ARG, "SixDST objectives take node genes");
         return gapa_launch_fitness_sixdst(c, pop, s, k, fit, st, &prof.kernels);

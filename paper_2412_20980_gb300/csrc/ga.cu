@@ -226,23 +226,37 @@ __device__ void block_argmin(const long long* __restrict__ fit, int s, long long
 
 // Row i of one generation g: with an elite, row 0 = elite copy and row i >= 1
 // = child i; without (the (mu+lambda) children), row i = child with counter i.
-// Cost estimate of a finished row for the cut-local fitness kernel (whole
-// CTA; the row was written by this CTA before the barrier inside).
+// Cost estimates of a finished row for the cut-local fitness kernel, under
+// the first and (if any) the second forest (whole CTA; the row was written by
+// this CTA before the barrier inside).
 __device__ void row_estimate(const GaParams& p, const int* row, int i) {
-    __shared__ long long part[kGaBlock / 32];
+    __shared__ long long part[2][kGaBlock / 32];
     __syncthreads();
-    long long c = 0;
+    long long c = 0, c2 = 0;
     for (int j = threadIdx.x; j < p.k; j += blockDim.x) {
         const int d = row[j];
-        if ((unsigned)d < (unsigned)p.n) c += __ldg(&p.est_cut[__ldg(&p.est_perm[d])]);
+        if ((unsigned)d < (unsigned)p.n) {
+            c += __ldg(&p.est_cut[__ldg(&p.est_perm[d])]);
+            if (p.est_perm2) c2 += __ldg(&p.est_cut2[__ldg(&p.est_perm2[d])]);
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        c2 += __shfl_down_sync(0xffffffffu, c2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        part[0][threadIdx.x >> 5] = c;
+        part[1][threadIdx.x >> 5] = c2;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        long long t = 0, t2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += part[0][w];
+            t2 += part[1][w];
+        }
         p.est_out[i] = (unsigned)(t < 0x7FFFFFFFll ? t : 0x7FFFFFFFll);
+        p.est_out[kOrderCap + i] = p.est_perm2 ? (unsigned)(t2 < 0x7FFFFFFFll ? t2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
     }
 }
 

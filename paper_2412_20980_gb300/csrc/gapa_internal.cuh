@@ -89,6 +89,25 @@ __device__ __forceinline__ int uniform_below(uint32_t x, int n) { return (int)__
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------
+// A second spanning forest of a graph with n <= 65536, in its own numbering
+// (parents precede children; a node's parent is its lowest-numbered
+// neighbour when that one is lower): the arrays of the TREE kernels.
+struct DeviceForest {
+    int* perm = nullptr;             // [n] original id -> number
+    int* tparent = nullptr;          // [n rounded up to 4]
+    int2* palt = nullptr;            // [n] (parent, second lower-numbered neighbour or -1)
+    int* lo_ptr = nullptr;           // [n+1] lower-numbered neighbours (CSR, ascending)
+    int* lo_col = nullptr;
+    int4* kids = nullptr;            // [n] children in at most two runs (see DeviceGraph::kids)
+    int* roots = nullptr;            // [num_roots]
+    int num_roots = 0;
+    int* cut = nullptr;              // [n] cost table (see DeviceGraph::cut)
+    int* fptr = nullptr;             // [n+1] full adjacency in this numbering
+    unsigned short* fcol16 = nullptr;
+    unsigned* nontree = nullptr;     // non-tree edges a<<16|b (a < b), sorted
+    int num_nontree = 0;
+};
+
 struct DeviceGraph {
     int n = 0;
     long long nnz = 0;        // arcs = 2E
@@ -103,12 +122,16 @@ struct DeviceGraph {
     // parent has a smaller number than its child.
     int* perm = nullptr;        // [n] original id -> BFS number
     int* tparent = nullptr;     // [n rounded up to 4] BFS number -> BFS number of its tree parent (roots: itself)
-    int2* kids = nullptr;       // [n] (first child, number of children); children have consecutive numbers
+    int4* kids = nullptr;       // [n] children: x .. x+y-1, then z+y .. z+y+w-1 (a second run; w = 0 here,
+                                //     where children have consecutive numbers)
     int* roots = nullptr;       // [num_roots] BFS number of every component's root
     int num_roots = 0;
     int local_list_bytes = 0;   // list region of the cut-local TREE kernel (0: that kernel does not fit)
     int* cut = nullptr;         // [n] per node: nodes below its children that have no other lower neighbour
-    int* order = nullptr;       // [2 * kOrderCap] member cost estimates, then the members, costliest first
+    int* order = nullptr;       // [4 * kOrderCap] the members, costliest first (bit 30: use `alt`), then
+                                //     their cost estimates under this forest, under `alt`, and the lower
+    DeviceForest alt;           // the forest numbered with the top hubs last (cut-local kernel only)
+    bool has_alt = false;
     int* lo_ptr = nullptr;      // [n+1] CSR of lower-numbered neighbours (BFS numbers, ascending;
     int* lo_col = nullptr;      //        the first one is the tree parent)
     int2* palt = nullptr;       // [n] (tree parent, second lower-numbered neighbour or -1)
@@ -223,9 +246,12 @@ struct GaParams {
     const int* g_ptr;    // device-resident generation counter (CUDA-graph replay)
     const long long* cum;  // roulette cumulative weights [s] (GAPA_FLAG_ROULETTE)
     // cost estimates of the rows for the cut-local fitness kernel (all null: none):
-    // est_out[row] = sum over the row's genes of est_cut[est_perm[gene]]
+    // est_out[row] = sum over the row's genes of est_cut[est_perm[gene]], and the same under the
+    // second forest at est_out[kOrderCap + row] (est_perm2 null: 0xFFFFFFFF there)
     const int* est_perm;
     const int* est_cut;
+    const int* est_perm2;
+    const int* est_cut2;
     unsigned* est_out;
 };
 
@@ -251,7 +277,7 @@ struct BatchDesc {
     int teams;           // members per CTA in the batched fitness kernel (1, 2, 4 or 8)
     // cut-local TREE kernel (tree16_member_local): list_bytes > 0 when each team's slice holds it
     const int* tparent;
-    const int2* kids;
+    const int4* kids;
     const int* roots;
     int num_roots;
     int list_bytes;
@@ -269,7 +295,9 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
 bool gapa_fitness_uses_estimates(const gapa_ctx* c, int s);
 // Threads of the one-member-per-CTA fitness kernels for a graph of n nodes.
 int gapa_fitness_block_for(int n);
-// Device buffer of kOrderCap cost estimates owned by the graph (valid when the above is true).
+// Device buffer of 2 * kOrderCap cost estimates owned by the graph (valid when the above is true):
+// row m's estimate under the first forest at [m], under the second at [kOrderCap + m] (0xFFFFFFFF
+// when the graph has no second forest).
 unsigned* gapa_estimate_buffer(gapa_ctx* c);
 int gapa_launch_init_batched(const BatchDesc* d, const int2* rows, int total_rows, size_t smem, int buf,
                              cudaStream_t st);

@@ -110,7 +110,7 @@ struct Tree16Graph {
     int objective;            // 0: PC, 1: MCN
     // cut-local variant only
     const int* tparent;       // tree parent per node (roots: itself), padded to a multiple of 4 entries
-    const int2* kids;         // (first child, number of children): a node's children have consecutive numbers
+    const int4* kids;         // children in at most two runs: x .. x+y-1, then z+y .. z+y+w-1
     const int* roots;         // the BFS root of every component
     int num_roots;
     int list_bytes;           // bytes of the member's list region
@@ -410,13 +410,13 @@ constexpr long long kLocalSpinLimit = 1ll << 24;
 // copy moves whole 16-byte units), the list region, eight team scalars and
 // the mbarrier.  The list region holds, from its start, the deletion bitmap
 // (until the re-picks are done) and then the list (16-bit node ids); at its
-// end three arrays of one int per team thread for the dealing rounds, and
+// end four arrays of one int per team thread for the dealing rounds, and
 // the bitmap of listed nodes.
 __host__ __device__ __forceinline__ size_t tree16l_lab_ints(int n) { return ((size_t)n + 3) & ~(size_t)3; }
 __host__ __device__ __forceinline__ size_t tree16l_bitmap_bytes(int n) {
     return ((((size_t)n + 31) >> 5) * 4 + 15) & ~(size_t)15;
 }
-__host__ __device__ __forceinline__ size_t tree16l_scratch_bytes(int team) { return (size_t)3 * team * 4; }
+__host__ __device__ __forceinline__ size_t tree16l_scratch_bytes(int team) { return (size_t)4 * team * 4; }
 __host__ __device__ __forceinline__ size_t tree16l_min_list_bytes(int n, int team) {
     return 2 * tree16l_bitmap_bytes(n) + tree16l_scratch_bytes(team);
 }
@@ -510,6 +510,43 @@ __device__ __forceinline__ void tree16l_join_edge(volatile int* lab, const unsig
     if (lab[y] != -1 && lab[x] != R) uf_unite(lab, x, R);
 }
 
+// Child of owner o for item i of a dealing round (owner records: first item,
+// first run start | length << 16, second run start less the first's length).
+__device__ __forceinline__ int tree16l_child(const int* s_off, const int* s_run, const int* s_run2, int o, int i) {
+    const int r = i - s_off[o];
+    const unsigned run = (unsigned)s_run[o];
+    return r < (int)(run >> 16) ? (int)(run & 0xFFFFu) + r : s_run2[o] + r;
+}
+
+// Owner records of the team's chunk of genes j0 .. j0+T-1 (node, children
+// runs; the first chunk's come from registers), their exclusive offsets and
+// *total items.  Returns the thread's gene node (-1: none).  Ends with a team
+// barrier.
+__device__ __forceinline__ int tree16l_gene_chunk(const Team& tm, const Tree16Graph& g, const int* __restrict__ genes,
+                                                  int k, int j0, int b0, int4 ch0, int* s_off, int* s_run,
+                                                  int* s_run2, int* ws, int* total) {
+    int b = b0;
+    int4 ch = ch0;
+    if (j0 > 0) {
+        b = -1;
+        ch = make_int4(0, 0, 0, 0);
+        const int j = j0 + tm.tid;
+        if (j < k) {
+            const int d = __ldg(&genes[j]);
+            if ((unsigned)d < (unsigned)g.n) {
+                b = __ldg(&g.perm[d]);
+                ch = __ldg(&g.kids[b]);
+            }
+        }
+    }
+    const int off = tree16l_scan(tm, ch.y + ch.w, ws, total);
+    s_off[tm.tid] = off;
+    s_run[tm.tid] = (int)((unsigned)ch.x | ((unsigned)ch.y << 16));
+    s_run2[tm.tid] = ch.z;
+    tm.sync();
+    return b;
+}
+
 // lab: the member's labels; region: its list region (g.list_bytes); scal_base:
 // its eight scalars followed by the mbarrier.  Returns through *out like
 // tree16_member.
@@ -526,10 +563,14 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
     unsigned short* list = reinterpret_cast<unsigned short*>(region);
     const int bm_bytes = (int)tree16l_bitmap_bytes(n);
     char* tail_area = reinterpret_cast<char*>(region) + g.list_bytes - bm_bytes - (int)tree16l_scratch_bytes(T);
+    // dealing rounds: per owner its first item, its children's first run (start | length << 16),
+    // the start of the second run less the first run's length, and a value (piece root, node)
     int* s_off = reinterpret_cast<int*>(tail_area);
-    int* s_first = s_off + T;
-    int* s_own = s_first + T;
+    int* s_run = s_off + T;
+    int* s_run2 = s_run + T;
+    int* s_own = s_run2 + T;
     unsigned* listed_bm = reinterpret_cast<unsigned*>(s_own + T);
+
     const int cap = (int)((tail_area - reinterpret_cast<char*>(region)) >> 1);
     int* ws = reinterpret_cast<int*>(red);
     if (tid == 0) {
@@ -561,7 +602,8 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
     // deleted nodes and the repeated genes.  The first T genes keep their
     // node, first child and number of children in registers.
     long long fresh_dup = 0;  // distinct << 32 | repeated
-    int b0 = -1, first0 = 0, cnt0 = 0;
+    int b0 = -1;
+    int4 ch0 = make_int4(0, 0, 0, 0);
     for (int j = tid; j < k; j += T) {
         const int d = __ldg(&genes[j]);
         if ((unsigned)d < (unsigned)n) {
@@ -570,10 +612,8 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
             const unsigned old = atomicOr(&dead[b >> 5], bit);
             fresh_dup += (old & bit) ? 1 : (1ll << 32);
             if (j == tid) {
-                const int2 ch = __ldg(&g.kids[b]);
                 b0 = b;
-                first0 = ch.x;
-                cnt0 = ch.y;
+                ch0 = __ldg(&g.kids[b]);
             }
         } else {
             atomicOr(status, GAPA_DEV_BAD_GENE);
@@ -625,39 +665,14 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
         tree16_member(tm, lab, region, g, genes, k, out, red, status);
         return;
     }
-    // genes in chunks of T: (node, first child, children) of the team's genes,
-    // their children dealt out over the team
-    auto gene_chunk = [&](int j0, int& total) {
-        int b = b0, first = first0, cnt = cnt0;
-        if (j0 > 0) {
-            b = -1;
-            first = cnt = 0;
-            const int j = j0 + tid;
-            if (j < k) {
-                const int d = __ldg(&genes[j]);
-                if ((unsigned)d < (unsigned)n) {
-                    b = __ldg(&g.perm[d]);
-                    const int2 ch = __ldg(&g.kids[b]);
-                    first = ch.x;
-                    cnt = ch.y;
-                }
-            }
-        }
-        const int off = tree16l_scan(tm, cnt, ws, &total);
-        s_off[tid] = off;
-        s_first[tid] = first;
-        tm.sync();
-        return b;
-    };
     // re-pick the children of the deleted nodes
     int tops_total = 0;
     for (int j0 = 0; j0 < k; j0 += T) {
-        const int b = gene_chunk(j0, tops_total);
+        const int b = tree16l_gene_chunk(tm, g, genes, k, j0, b0, ch0, s_off, s_run, s_run2, ws, &tops_total);
         if (b >= 0) lab[b] = -1;
         const int owners = min(T, k - j0);
         for (int i = tid; i < tops_total; i += T) {
-            const int o = tree16l_owner(s_off, owners, i);
-            const int c = s_first[o] + i - s_off[o];
+            const int c = tree16l_child(s_off, s_run, s_run2, tree16l_owner(s_off, owners, i), i);
             if (!bm_test(dead, c)) lab[c] = tree16_pick(dead, g, c, __ldg(&g.palt[c]));
         }
         tm.sync();
@@ -665,15 +680,15 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
     // from here a deleted node is a label of -1; the bitmap's words become the list.
     // Seeds: tops whose root is not R (each top takes its root as label)
     for (int j0 = 0; j0 < k; j0 += T) {
-        if (k > T) gene_chunk(j0, tops_total);  // one chunk: the offsets are still in place
+        if (k > T)  // one chunk: the offsets are still in place
+            tree16l_gene_chunk(tm, g, genes, k, j0, b0, ch0, s_off, s_run, s_run2, ws, &tops_total);
         const int owners = min(T, k - j0);
         for (int i0 = tid & ~31; i0 < tops_total; i0 += T) {
             const int i = i0 + lane;
             bool want = false;
             int c = 0;
             if (i < tops_total) {
-                const int o = tree16l_owner(s_off, owners, i);
-                c = s_first[o] + i - s_off[o];
+                c = tree16l_child(s_off, s_run, s_run2, tree16l_owner(s_off, owners, i), i);
                 const int l = lab[c];
                 if (l != -1) {
                     const int r = l == c ? c : uf_root(lab, l);
@@ -699,7 +714,7 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
     while (head < tail && tail <= lim && level < kLocalLevels) {
         for (int u0 = head; u0 < tail; u0 += T) {
             const int idx = u0 + tid;
-            int2 ch = make_int2(0, 0);
+            int4 ch = make_int4(0, 0, 0, 0);
             int r = 0;
             if (idx < tail) {
                 const int u = list[idx];
@@ -707,9 +722,10 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
                 r = lab[u];
             }
             int total;
-            const int off = tree16l_scan(tm, ch.y, ws, &total);
+            const int off = tree16l_scan(tm, ch.y + ch.w, ws, &total);
             s_off[tid] = off;
-            s_first[tid] = ch.x;
+            s_run[tid] = (int)((unsigned)ch.x | ((unsigned)ch.y << 16));
+            s_run2[tid] = ch.z;
             s_own[tid] = r;
             tm.sync();
             const int owners = min(T, tail - u0);
@@ -719,7 +735,7 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
                 int x = 0;
                 if (i < total) {
                     const int o = tree16l_owner(s_off, owners, i);
-                    x = s_first[o] + i - s_off[o];
+                    x = tree16l_child(s_off, s_run, s_run2, o, i);
                     if (lab[x] != -1) {
                         lab[x] = s_own[o];
                         want = true;
@@ -753,13 +769,13 @@ __device__ __forceinline__ void tree16_member_local(const Team& tm, volatile int
             int total;
             const int off = tree16l_scan(tm, d, ws, &total);
             s_off[tid] = off;
-            s_first[tid] = b;
+            s_run2[tid] = b;
             s_own[tid] = v;
             tm.sync();
             const int owners = min(T, listed - v0);
             for (int i = tid; i < total; i += T) {
                 const int o = tree16l_owner(s_off, owners, i);
-                const int w = __ldg(&g.fcol[s_first[o] + i - s_off[o]]);
+                const int w = __ldg(&g.fcol[s_run2[o] + i - s_off[o]]);
                 tree16l_join_edge(lab, listed_bm, R, s_own[o], w);
             }
             tm.sync();
