@@ -343,6 +343,15 @@ int gapa_set_sixdst_kernel(gapa_ctx* ctx, int kernel);
  * usable.  Synchronous. */
 int gapa_selftest_wait(gapa_ctx* ctx, int64_t spin_limit);
 
+/* Measurement utility (the paper has no counterpart): read bandwidth of this
+ * device over a buffer of `bytes` (a multiple of 16, 1 MiB .. 1 GiB) that the
+ * library allocates and fills: one warm-up pass, then `reps` timed launches
+ * of 16-byte loads by a grid of 8 CTAs per SM, each reading the buffer
+ * max(1, 2^30 / bytes) times; *gbs = bytes read / the fastest launch.
+ * A buffer well inside L2 gives the L2 read bandwidth, one far above it the
+ * HBM read bandwidth.  Synchronous; frees the buffer. */
+int gapa_read_bandwidth(gapa_ctx* ctx, int64_t bytes, int32_t reps, double* gbs);
+
 /* Gene type of the context (Fig. 1: the gene pool holds nodes or edges; end
  * of Section III-A: both perturbations act on the adjacency matrix).  NODES
  * (the default): genes are node ids in [0, n), deleting a node removes its

@@ -1031,6 +1031,46 @@ int gapa_selftest_wait(gapa_ctx* c, int64_t spin_limit) {
     return read_status(c, c->stream);
 }
 
+int gapa_read_bandwidth(gapa_ctx* c, int64_t bytes, int32_t reps, double* gbs) {
+    if (!c || !gbs) return gapa_fail(GAPA_ERR_INVALID_ARG, "NULL argument");
+    if (bytes < (1 << 20) || bytes > (1LL << 30) || bytes % 16 || reps < 1 || reps > 1000)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "probe size or repetitions out of range");
+    DeviceGuard guard(c->device);
+    const int grid = c->num_sms * 8;
+    const int passes = (int)std::max<int64_t>(1, (1LL << 30) / bytes);  // about 1 GiB read per timed launch
+    void* buf = nullptr;
+    unsigned* sink = nullptr;
+    if (cudaMalloc(&buf, (size_t)bytes) != cudaSuccess || cudaMalloc(&sink, sizeof(unsigned) * grid) != cudaSuccess) {
+        cudaFree(buf);
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "probe buffer of %lld bytes", (long long)bytes);
+    }
+    cudaStream_t st = c->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = GAPA_OK;
+    float best = 1e30f;
+    if (cudaMemsetAsync(buf, 1, (size_t)bytes, st) != cudaSuccess || cudaMemsetAsync(sink, 0, sizeof(unsigned) * grid, st) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = gapa_fail(GAPA_ERR_CUDA, "probe setup");
+    if (rc == GAPA_OK) rc = gapa_launch_read_probe(buf, (size_t)bytes, 1, grid, sink, st);  // warm-up
+    for (int r = 0; r < reps && rc == GAPA_OK; ++r) {
+        float ms = 0.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess) rc = gapa_fail(GAPA_ERR_CUDA, "probe event");
+        if (rc == GAPA_OK) rc = gapa_launch_read_probe(buf, (size_t)bytes, passes, grid, sink, st);
+        if (rc == GAPA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = gapa_fail(GAPA_ERR_CUDA, "probe timing");
+        if (rc == GAPA_OK) best = std::min(best, ms);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    cudaFree(sink);
+    if (rc == GAPA_OK) *gbs = (double)bytes * passes / (best / 1e3) / 1e9;
+    return rc;
+}
+
 int gapa_set_sixdst_kernel(gapa_ctx* c, int kernel) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
     if (kernel != GAPA_SIXDST_MMA_SYNC && kernel != GAPA_SIXDST_TCGEN05)

@@ -554,6 +554,36 @@ int gapa_fitness_prepare(gapa_ctx* c, int s) {
 
 int gapa_fitness_block_for(int n) { return smem_block_for(n); }
 
+namespace {
+// Read-bandwidth probe: 16-byte loads over the buffer, grid-strided, four in
+// flight per thread; one word per CTA keeps the loads live.
+__global__ void __launch_bounds__(256) read_probe_kernel(const uint4* __restrict__ buf, size_t n16, int passes,
+                                                         unsigned* __restrict__ sink) {
+    unsigned acc = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int p = 0; p < passes; ++p) {
+        size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        for (; i + 3 * stride < n16; i += 4 * stride) {
+            const uint4 a = __ldcg(&buf[i]), b = __ldcg(&buf[i + stride]), c = __ldcg(&buf[i + 2 * stride]),
+                        d = __ldcg(&buf[i + 3 * stride]);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+        }
+        for (; i < n16; i += stride) {
+            const uint4 a = __ldcg(&buf[i]);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicXor(&sink[blockIdx.x], acc);
+}
+}  // namespace
+
+int gapa_launch_read_probe(const void* buf, size_t bytes, int passes, int grid, unsigned* sink, cudaStream_t st) {
+    read_probe_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const uint4*>(buf), bytes / 16, passes, sink);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
 bool gapa_fitness_uses_estimates(const gapa_ctx* c, int s) {
     return c->g.packed16 && c->g.local_list_bytes > 0 && s > 1 && s <= kOrderCap &&
            c->genes == GAPA_GENES_NODES &&

@@ -317,6 +317,7 @@ int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, in
                                int* kernels = nullptr);
 int gapa_sixdst_init(gapa_ctx* c);
 int gapa_launch_selftest_wait(gapa_ctx* c, long long limit, cudaStream_t st);
+int gapa_launch_read_probe(const void* buf, size_t bytes, int passes, int grid, unsigned* sink, cudaStream_t st);
 int gapa_ig_prepare(gapa_ctx* c, int s);
 int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);
 int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,

@@ -41,6 +41,7 @@ EXPORTS = [
     "gapa_surrogate_create", "gapa_surrogate_destroy", "gapa_surrogate_predict", "gapa_surrogate_train_step",
     "gapa_surrogate_tensor", "gapa_run_surrogate", "gapa_surrogate_residual", "gapa_offspring",
     "gapa_set_objective", "gapa_set_genes", "gapa_set_sixdst_hops", "gapa_set_sixdst_kernel", "gapa_selftest_wait",
+    "gapa_read_bandwidth",
 ]
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_SCAN = 0, 1, 2, 3, 4, 5
 FITNESS_TREE_LOCAL = 6
@@ -180,6 +181,7 @@ def load(path: str | None = None):
             "gapa_set_sixdst_hops": ([V, U], U),
             "gapa_set_sixdst_kernel": ([V, U], U),
             "gapa_selftest_wait": ([V, I64], U),
+            "gapa_read_bandwidth": ([V, I64, I32, ctypes.POINTER(ctypes.c_double)], U),
             "gapa_fitness_noalloc": ([U, V, I32, I32, V, V, I32, I32, V], U),
             "gapa_batch_create": ([ctypes.POINTER(V), I32, V, V], U),
             "gapa_batch_destroy": ([V], None),
@@ -408,6 +410,12 @@ class Context:
         """Runs a bounded device-side wait that must time out; returns the library's status code
         (GAPA_ERR_TIMEOUT = -5 expected) without raising."""
         return int(self.lib.gapa_selftest_wait(self.handle, spin_limit))
+
+    def read_bandwidth(self, nbytes: int, reps: int = 10) -> float:
+        """gapa_read_bandwidth: GB/s of the fastest of `reps` read passes over an nbytes buffer."""
+        out = ctypes.c_double()
+        _check(self.lib.gapa_read_bandwidth(self.handle, nbytes, reps, ctypes.byref(out)))
+        return float(out.value)
 
     def set_sixdst_kernel(self, kernel: int):
         """0: mma.sync products (default), 1: tcgen05 products (same results)."""

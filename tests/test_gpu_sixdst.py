@@ -104,3 +104,15 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
     ctx.set_objective(OBJECTIVE_PC)
     pop = synth.random_deletion_sets(g.n, 20, 4, 1)
     assert np.array_equal(ctx.fitness_host(pop), oracle.fitness(g.row_ptr, g.col, pop))
+
+
+def test_read_bandwidth_probe(ctx):
+    """The bandwidth probe the bench uses for its L2 denominator: a buffer inside L2 reads faster
+    than one far above it, and both figures are physically plausible for one GPU."""
+    from paper_2412_20980_gb300 import GapaError
+
+    l2 = ctx.read_bandwidth(64 << 20, 5)
+    hbm = ctx.read_bandwidth(1 << 30, 3)
+    assert 500.0 < hbm < 20000.0 and l2 > hbm, (l2, hbm)
+    with pytest.raises(GapaError):
+        ctx.read_bandwidth(1000, 1)  # not a multiple of 16 and below 1 MiB
