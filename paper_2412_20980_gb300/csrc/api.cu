@@ -201,6 +201,10 @@ ForestHost forest_host(int32_t n, const std::vector<int32_t>& rp, const std::vec
         if (f.tparent[v] != v) below[f.tparent[v]] += below[v];
     for (int32_t v = 0; v < n; ++v)
         if (f.tparent[v] != v && f.lo_ptr[v + 1] - f.lo_ptr[v] == 1) f.cut[f.tparent[v]] += below[v];
+    // indexed by original node id, so that a gene's estimate is one load
+    std::vector<int32_t> by_id((size_t)n);
+    for (int32_t v = 0; v < n; ++v) by_id[v] = f.cut[perm[v]];
+    f.cut.swap(by_id);
     return f;
 }
 
@@ -359,9 +363,7 @@ GaParams make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_pt
     p.g = g;
     p.g_ptr = g_ptr;
     p.cum = nullptr;
-    p.est_perm = nullptr;
     p.est_cut = nullptr;
-    p.est_perm2 = nullptr;
     p.est_cut2 = nullptr;
     p.est_out = nullptr;
     return p;
@@ -398,12 +400,8 @@ int enqueue_generation(gapa_ctx* c, const GaParams& p0, int lambda, const int32_
     const int evaluated = (p.flags & GAPA_FLAG_MU_PLUS_LAMBDA) ? lambda : p.s;
     unsigned* est = gapa_fitness_uses_estimates(c, evaluated) ? gapa_estimate_buffer(c) : nullptr;
     if (est) {
-        p.est_perm = c->g.perm;
         p.est_cut = c->g.cut;
-        if (c->g.has_alt) {
-            p.est_perm2 = c->g.alt.perm;
-            p.est_cut2 = c->g.alt.cut;
-        }
+        if (c->g.has_alt) p.est_cut2 = c->g.alt.cut;
         p.est_out = est;
     }
     if (p.flags & GAPA_FLAG_MU_PLUS_LAMBDA) {
@@ -736,7 +734,9 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
                 return gapa_fail(GAPA_ERR_OOM, "children ranges of %d nodes", n);
             }
             GAPA_CUDA(cudaMemcpy(g.kids, kids.data(), sizeof(int4) * (size_t)n, cudaMemcpyHostToDevice));
-            GAPA_CUDA(cudaMemcpy(g.cut, cut.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+            std::vector<int32_t> cut_by_id((size_t)n);  // indexed by original node id
+            for (int32_t v = 0; v < n; ++v) cut_by_id[v] = cut[bf.perm[v]];
+            GAPA_CUDA(cudaMemcpy(g.cut, cut_by_id.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
             if (!bf.roots.empty())
                 GAPA_CUDA(cudaMemcpy(g.roots, bf.roots.data(), sizeof(int32_t) * bf.roots.size(),
                                      cudaMemcpyHostToDevice));

@@ -396,13 +396,12 @@ __global__ void __launch_bounds__(1024) cc_smem_kernel(GraphArgs g, const int* _
 
 // Cost estimate of every member for the cut-local kernel under each forest:
 // the sum over its genes of the nodes that deleting the gene alone leaves in
-// pieces to be listed (one 128-thread CTA per member, four independent
-// gathers in flight per thread; saturates at 2^31 - 1).  perm2 null: one forest.
+// pieces to be listed (cost tables by original node id; one 128-thread CTA
+// per member, four genes in flight per thread; saturates at 2^31 - 1).
+// cut2 null: one forest.
 __global__ void __launch_bounds__(128) local_cost_kernel(const int* __restrict__ pop, int k, int n,
-                                                         const int* __restrict__ perm, const int* __restrict__ cut,
-                                                         const int* __restrict__ perm2,
-                                                         const int* __restrict__ cut2, unsigned* __restrict__ est,
-                                                         unsigned* __restrict__ est2) {
+                                                         const int* __restrict__ cut, const int* __restrict__ cut2,
+                                                         unsigned* __restrict__ est, unsigned* __restrict__ est2) {
     __shared__ long long part[2][4];
     const int m = blockIdx.x, t = threadIdx.x;
     const int* genes = pop + (size_t)m * k;
@@ -412,24 +411,18 @@ __global__ void __launch_bounds__(128) local_cost_kernel(const int* __restrict__
         int d[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) d[u] = __ldg(&genes[j + 128 * u]);
-        int b[4], b2[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool ok = (unsigned)d[u] < (unsigned)n;
-            b[u] = ok ? __ldg(&perm[d[u]]) : -1;
-            b2[u] = ok && perm2 ? __ldg(&perm2[d[u]]) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            c += b[u] >= 0 ? __ldg(&cut[b[u]]) : 0;
-            c2 += b2[u] >= 0 ? __ldg(&cut2[b2[u]]) : 0;
+            c += ok ? __ldg(&cut[d[u]]) : 0;
+            c2 += ok && cut2 ? __ldg(&cut2[d[u]]) : 0;
         }
     }
     for (; j < k; j += 128) {
         const int d = __ldg(&genes[j]);
         if ((unsigned)d < (unsigned)n) {
-            c += __ldg(&cut[__ldg(&perm[d])]);
-            if (perm2) c2 += __ldg(&cut2[__ldg(&perm2[d])]);
+            c += __ldg(&cut[d]);
+            if (cut2) c2 += __ldg(&cut2[d]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -445,7 +438,7 @@ __global__ void __launch_bounds__(128) local_cost_kernel(const int* __restrict__
         const long long s1 = (part[0][0] + part[0][1]) + (part[0][2] + part[0][3]);
         const long long s2 = (part[1][0] + part[1][1]) + (part[1][2] + part[1][3]);
         est[m] = (unsigned)(s1 < 0x7FFFFFFFll ? s1 : 0x7FFFFFFFll);
-        est2[m] = perm2 ? (unsigned)(s2 < 0x7FFFFFFFll ? s2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
+        est2[m] = cut2 ? (unsigned)(s2 < 0x7FFFFFFFll ? s2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
     }
 }
 
@@ -508,8 +501,7 @@ int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, 
             est_min = e2 + kOrderCap;
             if (!est_in) {
                 const bool alt = c->g.has_alt;
-                local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.perm, c->g.cut, alt ? c->g.alt.perm : nullptr,
-                                                     alt ? c->g.alt.cut : nullptr, e1, e2);
+                local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.cut, alt ? c->g.alt.cut : nullptr, e1, e2);
                 if (kernels) *kernels += 1;
             }
             const unsigned* a = est_in ? est_in : e1;

@@ -233,11 +233,25 @@ __device__ void row_estimate(const GaParams& p, const int* row, int i) {
     __shared__ long long part[2][kGaBlock / 32];
     __syncthreads();
     long long c = 0, c2 = 0;
-    for (int j = threadIdx.x; j < p.k; j += blockDim.x) {
+    const int T = blockDim.x;
+    int j = threadIdx.x;
+    // four genes per step, both forests' gathers in flight together
+    for (; j + 3 * T < p.k; j += 4 * T) {
+        int d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = row[j + u * T];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = (unsigned)d[u] < (unsigned)p.n;
+            c += ok ? __ldg(&p.est_cut[d[u]]) : 0;
+            c2 += ok && p.est_cut2 ? __ldg(&p.est_cut2[d[u]]) : 0;
+        }
+    }
+    for (; j < p.k; j += T) {
         const int d = row[j];
         if ((unsigned)d < (unsigned)p.n) {
-            c += __ldg(&p.est_cut[__ldg(&p.est_perm[d])]);
-            if (p.est_perm2) c2 += __ldg(&p.est_cut2[__ldg(&p.est_perm2[d])]);
+            c += __ldg(&p.est_cut[d]);
+            if (p.est_cut2) c2 += __ldg(&p.est_cut2[d]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -256,7 +270,7 @@ __device__ void row_estimate(const GaParams& p, const int* row, int i) {
             t2 += part[1][w];
         }
         p.est_out[i] = (unsigned)(t < 0x7FFFFFFFll ? t : 0x7FFFFFFFll);
-        p.est_out[kOrderCap + i] = p.est_perm2 ? (unsigned)(t2 < 0x7FFFFFFFll ? t2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
+        p.est_out[kOrderCap + i] = p.est_cut2 ? (unsigned)(t2 < 0x7FFFFFFFll ? t2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
     }
 }
 

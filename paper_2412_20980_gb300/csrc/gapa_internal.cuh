@@ -101,7 +101,7 @@ struct DeviceForest {
     int4* kids = nullptr;            // [n] children in at most two runs (see DeviceGraph::kids)
     int* roots = nullptr;            // [num_roots]
     int num_roots = 0;
-    int* cut = nullptr;              // [n] cost table (see DeviceGraph::cut)
+    int* cut = nullptr;              // [n] cost table by original node id (see DeviceGraph::cut)
     int* fptr = nullptr;             // [n+1] full adjacency in this numbering
     unsigned short* fcol16 = nullptr;
     unsigned* nontree = nullptr;     // non-tree edges a<<16|b (a < b), sorted
@@ -127,7 +127,8 @@ struct DeviceGraph {
     int* roots = nullptr;       // [num_roots] BFS number of every component's root
     int num_roots = 0;
     int local_list_bytes = 0;   // list region of the cut-local TREE kernel (0: that kernel does not fit)
-    int* cut = nullptr;         // [n] per node: nodes below its children that have no other lower neighbour
+    int* cut = nullptr;         // [n] per original node id: nodes below those of its tree children that
+                                //     have no other lower neighbour (deleting it alone cuts them off)
     int* order = nullptr;       // [4 * kOrderCap] the members, costliest first (bit 30: use `alt`), then
                                 //     their cost estimates under this forest, under `alt`, and the lower
     DeviceForest alt;           // the forest numbered with the top hubs last (cut-local kernel only)
@@ -246,11 +247,9 @@ struct GaParams {
     const int* g_ptr;    // device-resident generation counter (CUDA-graph replay)
     const long long* cum;  // roulette cumulative weights [s] (GAPA_FLAG_ROULETTE)
     // cost estimates of the rows for the cut-local fitness kernel (all null: none):
-    // est_out[row] = sum over the row's genes of est_cut[est_perm[gene]], and the same under the
-    // second forest at est_out[kOrderCap + row] (est_perm2 null: 0xFFFFFFFF there)
-    const int* est_perm;
+    // est_out[row] = sum over the row's genes of est_cut[gene], and the same under the second
+    // forest at est_out[kOrderCap + row] (est_cut2 null: 0xFFFFFFFF there)
     const int* est_cut;
-    const int* est_perm2;
     const int* est_cut2;
     unsigned* est_out;
 };
