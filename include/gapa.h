@@ -329,11 +329,14 @@ int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 int gapa_set_objective(gapa_ctx* ctx, int objective);
 int gapa_set_sixdst_hops(gapa_ctx* ctx, int hops);
 /* Tensor-core path of the SixDST products (identical results): TCGEN05
- * (tcgen05.mma with the accumulator in tensor memory, the default; a
- * device-side wait that runs out is reported as GAPA_ERR_TIMEOUT) or MMA_SYNC
- * (warp-level mma.sync). */
+ * (tcgen05.mma with the accumulator in tensor memory, the default: 256 x 256
+ * output tiles when the padded size is a multiple of 256, else 128 x 128; a
+ * device-side wait that runs out is reported as GAPA_ERR_TIMEOUT),
+ * TCGEN05_128 (the same with 128 x 128 tiles only) or MMA_SYNC (warp-level
+ * mma.sync). */
 #define GAPA_SIXDST_MMA_SYNC 0
 #define GAPA_SIXDST_TCGEN05 1
+#define GAPA_SIXDST_TCGEN05_128 2
 int gapa_set_sixdst_kernel(gapa_ctx* ctx, int kernel);
 
 /* Failure-path check of the device-side bounded waits (the paper has no

@@ -364,6 +364,201 @@ __global__ void __launch_bounds__(kT5Threads) sdst_gemm_t5_kernel(const unsigned
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// 256 x 256 tiles (np a multiple of 256): the same tcgen05 product with twice
+// the tile edge, so each strip streamed from L2 feeds twice the outputs.  A
+// CTA of 8 warps owns one tile; per 32-byte k step one thread issues two
+// M = 128, N = 256 products (rows 0-127 and 128-255 of the tile against all
+// 256 columns) into two accumulators of 256 tensor-memory columns each (512
+// in all).  Stages: 128-byte k chunks of both 256-row strips (64 KB per
+// stage, three stages, cp.async), released by tcgen05.commit on their
+// mbarriers; every wait bounded as above.  Epilogue: warp w reads lane
+// quarter w % 4 of both accumulators for column half w / 4, writes its rows
+// of the tile to global memory and its 0/1 bytes to a shared-memory copy of
+// the tile (the stages are free by then), from which an off-diagonal tile's
+// mirror below the diagonal is written with 16-byte stores.
+// ---------------------------------------------------------------------------
+constexpr int kT6Tile = 256, kT6Threads = 256;
+constexpr int kT6StageBytes = kT6Tile * kT5Chunk;  // 32 KB per operand per stage
+constexpr int kT6Smem = 2 * kT5Stages * kT6StageBytes;  // 192 KB (the epilogue's 64 KB tile reuses it)
+// instruction descriptor: FP32 accumulator, A and B E4M3, both K-major, N = 256, M = 128
+constexpr unsigned kT6Idesc = (1u << 4) | ((unsigned)(kT6Tile >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+
+__global__ void __launch_bounds__(kT6Threads) sdst_gemm_t6_kernel(const unsigned char* __restrict__ X,
+                                                                  const unsigned char* __restrict__ Y,
+                                                                  unsigned char* __restrict__ C, int np, size_t mat,
+                                                                  int* status) {
+    extern __shared__ __align__(16) unsigned char t6_smem[];
+    unsigned char* sA = t6_smem;                                 // [stages][32 KB]
+    unsigned char* sB = t6_smem + kT5Stages * kT6StageBytes;     // [stages][32 KB]
+    __shared__ __align__(8) unsigned long long bars[kT5Stages];
+    __shared__ unsigned tmem_base;
+    __shared__ int failed;
+    const int T = np / kT6Tile;
+    int ty = 0, rem = (int)blockIdx.x;
+    while (rem >= T - ty) {
+        rem -= T - ty;
+        ++ty;
+    }
+    const int tx = ty + rem;
+    const size_t off = (size_t)blockIdx.y * mat;
+    const unsigned char* x = X + off + (size_t)ty * kT6Tile * np;
+    const unsigned char* y = Y + off + (size_t)tx * kT6Tile * np;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        failed = 0;
+        for (int s = 0; s < kT5Stages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(2 * kT6Tile)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    // chunk -> stage: 256 rows x 8 pieces of 16 bytes per operand, piece (row, q) at
+    // (row / 8) * 1024 + q * 128 + (row % 8) * 16
+    auto load = [&](int chunk) {
+        const int st = chunk % kT5Stages, k0 = chunk * kT5Chunk;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int piece = tid + r * kT6Threads, row = piece >> 3, q = piece & 7;
+            const int so = (row >> 3) * 1024 + q * 128 + (row & 7) * 16;
+            cp_async16(sA + st * kT6StageBytes + so, x + (size_t)row * np + k0 + q * 16);
+            cp_async16(sB + st * kT6StageBytes + so, y + (size_t)row * np + k0 + q * 16);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int chunks = np / kT5Chunk;
+    load(0);
+    if (chunks > 1) load(1);
+    int issued = -1;
+    for (int c = 0; c < chunks; ++c) {
+        const int st = c % kT5Stages;
+        if (c + 2 < chunks) {
+            if (c >= 1) {
+                if (tid == 0 &&
+                    !t5_wait(smem_u32(&bars[(c + 2) % kT5Stages]), (unsigned)(((c - 1) / kT5Stages) & 1)))
+                    failed = 1;
+                __syncthreads();
+                if (failed) break;
+            }
+            load(c + 2);
+            asm volatile("cp.async.wait_group 2;" ::: "memory");
+        } else if (c + 1 < chunks) {
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = smem_u32(sA + st * kT6StageBytes), b0 = smem_u32(sB + st * kT6StageBytes);
+#pragma unroll
+            for (int j = 0; j < kT5Chunk / 32; ++j) {
+                const unsigned long long db = t5_desc(b0 + 256u * j);
+                const unsigned acc = (c > 0 || j > 0) ? 1u : 0u;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {  // tile rows 128h .. 128h + 127: 16 groups of 8 rows on
+                    const unsigned long long da = t5_desc(a0 + 16u * 1024u * h + 256u * j);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                        ::"r"(tmem + (unsigned)(h * kT6Tile)), "l"(da), "l"(db), "r"(kT6Idesc), "r"(acc)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[st]))
+                         : "memory");
+        }
+        issued = c;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (tid == 0 && issued >= 0 && !t5_wait(smem_u32(&bars[issued % kT5Stages]), (unsigned)((issued / kT5Stages) & 1)))
+        failed = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, GAPA_DEV_TIMEOUT);
+            if (issued >= 0) t5_wait(smem_u32(&bars[issued % kT5Stages]), (unsigned)((issued / kT5Stages) & 1));
+        }
+    } else {
+        unsigned char* c = C + off;
+        unsigned char* tile = t6_smem;  // [256 rows][256 bytes], the stages being free
+        const int quarter = warp & 3, half = warp >> 2;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int trow = h * 128 + quarter * 32 + lane;  // row within the tile
+            const int row = ty * kT6Tile + trow;
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                const int tcol = half * 128 + q * 32;
+                unsigned v[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(h * kT6Tile + tcol)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                unsigned w[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    unsigned word = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        word |= (__uint_as_float(v[4 * b + e]) > 0.5f ? (unsigned)kOne : 0u) << (8 * e);
+                    w[b] = word;
+                }
+                uint4* dst = reinterpret_cast<uint4*>(c + (size_t)row * np + tx * kT6Tile + tcol);
+                dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                if (tx != ty) {
+                    uint4* t = reinterpret_cast<uint4*>(tile + trow * kT6Tile + tcol);
+                    t[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    t[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                }
+            }
+        }
+        if (tx != ty) {
+            // the mirror: global row tx * 256 + j, columns ty * 256 .. + 255 = tile column j.  A thread
+            // gathers 32 bytes of one tile column (32 consecutive tile rows; the lanes of a warp take
+            // consecutive columns, so each shared-memory read is 32 adjacent bytes) and stores them as
+            // one 32-byte sector
+            __syncthreads();
+            for (int p = tid; p < kT6Tile * (kT6Tile / 32); p += kT6Threads) {
+                const int j = p & (kT6Tile - 1), r0 = (p / kT6Tile) * 32;  // tile column j, rows r0 .. r0 + 31
+                unsigned w[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    unsigned word = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) word |= (unsigned)tile[(r0 + 4 * b + e) * kT6Tile + j] << (8 * e);
+                    w[b] = word;
+                }
+                uint4* dst = reinterpret_cast<uint4*>(c + (size_t)(tx * kT6Tile + j) * np + ty * kT6Tile + r0);
+                dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kT6Tile) : "memory");
+}
+
 // The bounded wait on an mbarrier that nothing completes: it must run out and
 // report GAPA_DEV_TIMEOUT (gapa_selftest_wait).
 __global__ void t5_selftest_kernel(long long limit, int* status) {
@@ -428,6 +623,10 @@ int gapa_sixdst_init(gapa_ctx* c) {
     GAPA_CUDA(cudaFuncSetAttribute(sdst_gemm_t5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     c->sixdst_t5_ok = true;
     c->sixdst_kernel = 1;
+    if ((size_t)kT6Smem + 1024 <= c->smem_optin) {
+        GAPA_CUDA(cudaFuncSetAttribute(sdst_gemm_t6_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kT6Smem));
+        c->sixdst_t6_ok = true;
+    }
     return GAPA_OK;
 }
 
@@ -457,9 +656,15 @@ int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, in
         int base = 0, res = -1;
         const int tiles = np / kTile;
         const dim3 grid(tiles * (tiles + 1) / 2, bm);
-        const bool t5 = c->sixdst_kernel == 1;
+        const bool t5 = c->sixdst_kernel >= 1;
+        // 256-wide tiles where the padded size allows them
+        const bool t6 = c->sixdst_kernel == 1 && c->sixdst_t6_ok && np % kT6Tile == 0;
+        const int tiles6 = np / kT6Tile;
+        const dim3 grid6(tiles6 * (tiles6 + 1) / 2, bm);
         auto launch_gemm = [&](const unsigned char* xa, const unsigned char* yb, unsigned char* cc) {
-            if (t5)
+            if (t6)
+                sdst_gemm_t6_kernel<<<grid6, kT6Threads, kT6Smem, st>>>(xa, yb, cc, np, mat, c->status);
+            else if (t5)
                 sdst_gemm_t5_kernel<<<grid, kT5Threads, 2 * kT5Stages * kT5StageBytes, st>>>(xa, yb, cc, np, mat,
                                                                                              c->status);
             else

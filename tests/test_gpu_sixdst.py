@@ -10,7 +10,7 @@ from oracle import sixdst_ref as sx
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["mma_sync", "tcgen05"])
+@pytest.fixture(scope="module", params=["mma_sync", "tcgen05", "tcgen05_128"])
 def ctx(request):
     import torch
 
@@ -19,7 +19,9 @@ def ctx(request):
 
     b.build()
     c = Context(0)
-    c.set_sixdst_kernel({"mma_sync": 0, "tcgen05": 1}[request.param])
+    # tcgen05: 256-wide tiles where the padded size is a multiple of 256 (n = 150, 200, 500, 700
+    # below), 128-wide otherwise; tcgen05_128: 128-wide tiles throughout
+    c.set_sixdst_kernel({"mma_sync": 0, "tcgen05": 1, "tcgen05_128": 2}[request.param])
     yield c
     torch.cuda.synchronize()
     c.close()
