@@ -299,8 +299,8 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
  * SAMPLED joins every live node to its first two live neighbours, takes the
  * tree of the highest-degree live node as the giant tree and lets only nodes
  * outside it scan their whole adjacency; EDGES runs union-find over every
- * undirected edge.  AUTO (the default) is TREE_LOCAL where it applies, else
- * TREE. */
+ * undirected edge.  AUTO (the default) is TREE_LOCAL where it applies and
+ * the graph has more than 2048 nodes, else TREE. */
 #define GAPA_FITNESS_AUTO 0
 #define GAPA_FITNESS_EDGES 1
 #define GAPA_FITNESS_SAMPLED 2
