@@ -171,9 +171,32 @@ __global__ void __launch_bounds__(kIgBlock) ig_cut_kernel(IgArgs a) {
 
 // every live node points at the top of its piece / its root (owner writes only)
 __global__ void __launch_bounds__(kIgBlock) ig_flatten_kernel(IgArgs a) {
+    // four items per thread in flight: their labels, then their parents' labels, are loaded
+    // together; only a chain longer than two steps walks on alone.  Parents have smaller numbers
+    // and the items go in increasing node order, so most parents are flat already.
     int* L = group_labels(a);
-    const size_t total = (size_t)a.n * kM;
-    for (size_t t = gtid(); t < total; t += gthreads()) {
+    const size_t total = (size_t)a.n * kM, G = gthreads();
+    size_t t = gtid();
+    for (; t + 3 * G < total; t += 4 * G) {
+        int p[4], q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = *slot(L, (int)((t + u * G) / kM), (int)((t + u * G) % kM));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int v = (int)((t + u * G) / kM), m = (int)((t + u * G) % kM);
+            int x = p[u];
+            if (p[u] != kDead && p[u] != v) x = *slot(L, p[u], m);
+            q[u] = x;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int v = (int)((t + u * G) / kM), m = (int)((t + u * G) % kM);
+            if (p[u] == kDead || p[u] == v) continue;
+            const int r = q[u] == p[u] ? p[u] : ig_root(L, m, q[u]);
+            *slot(L, v, m) = r;
+        }
+    }
+    for (; t < total; t += G) {
         const int v = (int)(t / kM), m = (int)(t % kM);
         const int p = *slot(L, v, m);
         if (p != kDead && p != v) *slot(L, v, m) = ig_root(L, m, p);
@@ -208,8 +231,51 @@ __global__ void __launch_bounds__(kIgBlock) ig_giant_kernel(IgArgs a) {
 // another piece among its first kLinkScan adjacency entries
 __global__ void __launch_bounds__(kIgBlock) ig_link_kernel(IgArgs a) {
     int* L = group_labels(a);
-    const size_t total = (size_t)a.n * kM;
-    for (size_t t = gtid(); t < total; t += gthreads()) {
+    const size_t total = (size_t)a.n * kM, G = gthreads();
+    size_t t = gtid();
+    // four items per thread in flight: their labels, adjacency bounds, first neighbours and those
+    // neighbours' labels are loaded together before any union.  A neighbour's label read early
+    // that equals the node's current label still proves both in one set (sets only merge), so
+    // skipping it is exact.
+    for (; t + 3 * G < total; t += 4 * G) {
+        int v[4], m[4], beg[4], cnt[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v[u] = (int)((t + u * G) / kM);
+            m[u] = (int)((t + u * G) % kM);
+            cnt[u] = (ig_real_member(a, m[u]) && *slot(L, v[u], m[u]) != kDead) ? 1 : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!cnt[u]) continue;
+            beg[u] = __ldg(&a.fptr[v[u]]);
+            cnt[u] = min(__ldg(&a.fptr[v[u] + 1]) - beg[u], kLinkScan);
+        }
+        int w[4][kLinkScan], lw[4][kLinkScan];
+#pragma unroll
+        for (int e = 0; e < kLinkScan; ++e)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u][e] = e < cnt[u] ? __ldg(&a.fcol[beg[u] + e]) : -1;
+#pragma unroll
+        for (int e = 0; e < kLinkScan; ++e)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int x = kDead;
+                if (w[u][e] >= 0) x = *slot(L, w[u][e], m[u]);
+                lw[u][e] = x;
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int linked = 0;
+#pragma unroll
+            for (int e = 0; e < kLinkScan; ++e) {
+                if (e >= cnt[u] || linked >= 2 || lw[u][e] == kDead) continue;
+                if (lw[u][e] != *slot(L, v[u], m[u])) ig_unite(L, m[u], v[u], w[u][e]);
+                ++linked;
+            }
+        }
+    }
+    for (; t < total; t += G) {
         const int v = (int)(t / kM), m = (int)(t % kM);
         if (!ig_real_member(a, m) || *slot(L, v, m) == kDead) continue;
         const int beg = __ldg(&a.fptr[v]);
