@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kIgBlock) ig_sum_kernel(IgArgs a) {
     }
 }
 
-constexpr size_t kIgLabelBudget = 48ull << 20;  // labels of a batch of groups kept within this many bytes
+constexpr size_t kIgLabelBudget = 64ull << 20;  // labels of a batch of groups kept within this many bytes (R-MAT 2^20: two groups; 48 MB (one group) took 11.3 ms per 256 members, 64 MB 8.2, 96 MB 9.8)
 
 int ig_groups_per_batch(int n, int s) {
     const size_t per_group = (size_t)n * kM * sizeof(int);
