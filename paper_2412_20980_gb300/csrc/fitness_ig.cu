@@ -170,26 +170,29 @@ __global__ void __launch_bounds__(kIgBlock) ig_cut_kernel(IgArgs a) {
 }
 
 // every live node points at the top of its piece / its root (owner writes only)
+constexpr int kFlatInFlight = 4;  // items per thread resolved together by ig_flatten_kernel
+constexpr int kLinkInFlight = 4;  // items per thread loaded together by ig_link_kernel
+
 __global__ void __launch_bounds__(kIgBlock) ig_flatten_kernel(IgArgs a) {
-    // four items per thread in flight: their labels, then their parents' labels, are loaded
-    // together; only a chain longer than two steps walks on alone.  Parents have smaller numbers
-    // and the items go in increasing node order, so most parents are flat already.
+    // kFlatInFlight items per thread in flight: their labels, then their parents' labels, are
+    // loaded together; only a chain longer than two steps walks on alone.  Parents have smaller
+    // numbers and the items go in increasing node order, so most parents are flat already.
     int* L = group_labels(a);
     const size_t total = (size_t)a.n * kM, G = gthreads();
     size_t t = gtid();
-    for (; t + 3 * G < total; t += 4 * G) {
-        int p[4], q[4];
+    for (; t + (kFlatInFlight - 1) * G < total; t += kFlatInFlight * G) {
+        int p[kFlatInFlight], q[kFlatInFlight];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) p[u] = *slot(L, (int)((t + u * G) / kM), (int)((t + u * G) % kM));
+        for (int u = 0; u < kFlatInFlight; ++u) p[u] = *slot(L, (int)((t + u * G) / kM), (int)((t + u * G) % kM));
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kFlatInFlight; ++u) {
             const int v = (int)((t + u * G) / kM), m = (int)((t + u * G) % kM);
             int x = p[u];
             if (p[u] != kDead && p[u] != v) x = *slot(L, p[u], m);
             q[u] = x;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kFlatInFlight; ++u) {
             const int v = (int)((t + u * G) / kM), m = (int)((t + u * G) % kM);
             if (p[u] == kDead || p[u] == v) continue;
             const int r = q[u] == p[u] ? p[u] : ig_root(L, m, q[u]);
@@ -233,39 +236,39 @@ __global__ void __launch_bounds__(kIgBlock) ig_link_kernel(IgArgs a) {
     int* L = group_labels(a);
     const size_t total = (size_t)a.n * kM, G = gthreads();
     size_t t = gtid();
-    // four items per thread in flight: their labels, adjacency bounds, first neighbours and those
-    // neighbours' labels are loaded together before any union.  A neighbour's label read early
-    // that equals the node's current label still proves both in one set (sets only merge), so
-    // skipping it is exact.
-    for (; t + 3 * G < total; t += 4 * G) {
-        int v[4], m[4], beg[4], cnt[4];
+    // kLinkInFlight items per thread in flight: their labels, adjacency bounds, first neighbours
+    // and those neighbours' labels are loaded together before any union.  A neighbour's label read
+    // early that equals the node's current label still proves both in one set (sets only merge),
+    // so skipping it is exact.
+    for (; t + (kLinkInFlight - 1) * G < total; t += kLinkInFlight * G) {
+        int v[kLinkInFlight], m[kLinkInFlight], beg[kLinkInFlight], cnt[kLinkInFlight];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kLinkInFlight; ++u) {
             v[u] = (int)((t + u * G) / kM);
             m[u] = (int)((t + u * G) % kM);
             cnt[u] = (ig_real_member(a, m[u]) && *slot(L, v[u], m[u]) != kDead) ? 1 : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kLinkInFlight; ++u) {
             if (!cnt[u]) continue;
             beg[u] = __ldg(&a.fptr[v[u]]);
             cnt[u] = min(__ldg(&a.fptr[v[u] + 1]) - beg[u], kLinkScan);
         }
-        int w[4][kLinkScan], lw[4][kLinkScan];
+        int w[kLinkInFlight][kLinkScan], lw[kLinkInFlight][kLinkScan];
 #pragma unroll
         for (int e = 0; e < kLinkScan; ++e)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) w[u][e] = e < cnt[u] ? __ldg(&a.fcol[beg[u] + e]) : -1;
+            for (int u = 0; u < kLinkInFlight; ++u) w[u][e] = e < cnt[u] ? __ldg(&a.fcol[beg[u] + e]) : -1;
 #pragma unroll
         for (int e = 0; e < kLinkScan; ++e)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kLinkInFlight; ++u) {
                 int x = kDead;
                 if (w[u][e] >= 0) x = *slot(L, w[u][e], m[u]);
                 lw[u][e] = x;
             }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kLinkInFlight; ++u) {
             int linked = 0;
 #pragma unroll
             for (int e = 0; e < kLinkScan; ++e) {
