@@ -431,8 +431,9 @@ def run_gapa(args):
         achieved = beval * (fit_evals / fit_calls) / avg_launch_s / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": ncu_traffic(wl),
-                    "kernel": "fitness phase: local_cost_kernel + local_order_kernel + cc_smem_kernel "
-                              "(cut-local TREE) where the graph fits in shared memory, ig_* kernels otherwise",
+                    "kernel": "fitness phase: local_order_kernel + cc_smem_kernel<4> (cut-local TREE, estimates "
+                              "written by the operator kernel) where the graph fits in shared memory, ig_* "
+                              "kernels otherwise",
                     "kernels_per_phase": fit_launches / fit_calls,
                     "bytes_per_eval": beval, "evals_per_launch": fit_evals / fit_calls,
                     "avg_launch_ms": avg_launch_s * 1000,
