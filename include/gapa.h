@@ -205,7 +205,7 @@ int gapa_batch_run(gapa_batch* batch, int32_t gens, int64_t* best_fit, int32_t* 
 
 /* ---- Learned fitness surrogate (an extension; the paper has no surrogate) ----
  * A small MLP scores children so that only the most promising fraction gets
- * the exact fitness of Section III-C; exact fitness stays the judge of every
+ * the exact fitness of Section III-C; exact fitness stays the arbiter of every
  * member kept.  Input of a deletion set D of k genes (80 values):
  * (1/sqrt k) * sum of the 64-d embeddings of its genes, then the mean, maximum
  * and standard deviation of log1p(degree) over D and sum(degree)/(2E), then

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kT5Threads) sdst_gemm_t5_kernel(const unsigned
         const int st = c % kT5Stages;
         if (c + 2 < chunks) {
             // the stage of chunk c + 2 was last read by the products of chunk c - 1: one thread
-            // waits for them (bounded) and the verdict goes to all
+            // waits for them (bounded) and the outcome goes to all
             if (c >= 1) {
                 if (tid == 0 &&
                     !t5_wait(smem_u32(&bars[(c + 2) % kT5Stages]), (unsigned)(((c - 1) / kT5Stages) & 1)))

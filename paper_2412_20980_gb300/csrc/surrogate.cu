@@ -2,7 +2,7 @@
 //
 // Not part of the paper: a small MLP scores every child of a generation so
 // that only the most promising fraction receives the exact pairwise-
-// connectivity fitness of Section III-C; exact fitness stays the judge of
+// connectivity fitness of Section III-C; exact fitness stays the arbiter of
 // every member kept (Eqs. 10-11 truncation over members and evaluated
 // children).  The model is trained online on the (deletion set, exact
 // fitness) pairs the GA produces.

@@ -259,7 +259,7 @@ def test_screened_run_keeps_exact_fitness_and_plain_fallback_matches_mu_plus_lam
     res = run_surrogate(ctx, cfg, sg)
     assert list(res["exact_evals"][1:4]) == [256] * 3 and np.all(res["exact_evals"][4:] == 64)
     assert np.all(np.diff(res["traj"]) <= 0)
-    # exact fitness is the judge: the reported best is the true PC of the reported set
+    # exact fitness is the arbiter: the reported best is the true PC of the reported set
     assert res["best_fit"] == oracle.pc(g.row_ptr, g.col, res["best_set"])
     assert np.all(np.diff(res["gen_ms"]) >= 0)
     sg.close()
