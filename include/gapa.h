@@ -191,9 +191,11 @@ int gapa_batch_get_teams(gapa_batch* batch, int32_t* teams /* [num] */);
 /* Autotuner: for every graph-size bucket present (n <= 2048, 4096, 8192,
  * 16384, 32768, 65536) time each feasible team count on the initial
  * population and keep the fastest; choices are cached per device name in
- * the JSON file `cache_path` (NULL: no cache).  Batched instances run the
- * full TREE pipeline unless their context is set to GAPA_FITNESS_TREE_LOCAL
- * (then the cut-local kernel, in each team's slice). */
+ * the JSON file `cache_path` (NULL: no cache).  Batched instances follow
+ * their context's fitness kernel setting as single runs do: AUTO takes the
+ * cut-local kernel above 2048 nodes (in each team's slice, with the
+ * operator kernels' cost estimates), TREE_LOCAL always, anything else the
+ * full TREE pipeline. */
 int gapa_batch_autotune(gapa_batch* batch, const char* cache_path);
 
 /* Run every instance for `gens` generations from its initialisation.

@@ -366,6 +366,7 @@ GaParams make_params(gapa_ctx* c, const gapa_config* cfg, int g, const int* g_pt
     p.est_cut = nullptr;
     p.est_cut2 = nullptr;
     p.est_out = nullptr;
+    p.est_stride = 0;
     return p;
 }
 
@@ -403,6 +404,7 @@ int enqueue_generation(gapa_ctx* c, const GaParams& p0, int lambda, const int32_
         p.est_cut = c->g.cut;
         if (c->g.has_alt) p.est_cut2 = c->g.alt.cut;
         p.est_out = est;
+        p.est_stride = kOrderCap;
     }
     if (p.flags & GAPA_FLAG_MU_PLUS_LAMBDA) {
         rc = gapa_launch_children(c, p, lambda, pop_in, fit_in, c->kids, st);

@@ -29,7 +29,8 @@ struct gapa_batch {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     int* status = nullptr;          // ctxs[0]'s status word
     std::vector<int> teams;         // members per CTA per instance
-    std::vector<int> use_local;     // per instance: the cut-local kernel (context set to TREE_LOCAL)
+    std::vector<int> use_local;     // per instance: the cut-local kernel
+    unsigned* d_est = nullptr;      // cost estimates of the local instances' rows (two per row)
     // device memory
     BatchDesc* d_desc = nullptr;
     int2* d_rows = nullptr;
@@ -75,6 +76,8 @@ int default_teams(int n, size_t max_dyn) {
 }
 
 void free_batch_device(gapa_batch* b) {
+    cudaFree(b->d_est);
+    b->d_est = nullptr;
     cudaFree(b->d_desc);
     cudaFree(b->d_rows);
     cudaFree(b->d_pk);
@@ -343,11 +346,13 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         d.fcol16 = dg.fcol16;
         d.mean_deg_x16 = dg.mean_deg_x16;
         d.objective = b->ctxs[i]->objective;
-        if (dg.local_list_bytes > 0 && b->ctxs[i]->fitness_variant == GAPA_FITNESS_TREE_LOCAL) {
-            // the cut-local kernel only where the context asks for it: inside a packet every team waits
-            // for its slowest member, and without cost ordering the cut-local kernel's uneven member
-            // times lost to the full pipeline on the batched workload (213-252 ms against 208 ms)
+        const int variant = b->ctxs[i]->fitness_variant;
+        if (dg.local_list_bytes > 0 && (variant == GAPA_FITNESS_TREE_LOCAL ||
+                                        (variant == GAPA_FITNESS_AUTO && dg.n > 2048))) {
+            // the cut-local kernel as on a single context: the operator kernels write every row's
+            // estimates under both forests, members estimated to shatter both run the full pipeline
             b->use_local[i] = 1;
+            d.alt = dg.alt;
             d.tparent = dg.tparent;
             d.kids = dg.kids;
             d.roots = dg.roots;
@@ -355,6 +360,27 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         }
         b->teams[i] = default_teams(dg.n, b->fit_max_dyn);
         for (int r = 0; r < g.pop; ++r) rows.push_back(make_int2(i, r));
+    }
+    // cost estimates of the cut-local instances' rows: two per row (first forest, second forest)
+    size_t est_total = 0;
+    for (int i = 0; i < num; ++i)
+        if (b->use_local[i]) est_total += 2 * (size_t)cfgs[i].pop;
+    if (est_total) {
+        if (cudaMalloc(&b->d_est, sizeof(unsigned) * est_total) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(gapa_fail(GAPA_ERR_OOM, "batch cost estimates"));
+        }
+        size_t eo = 0;
+        for (int i = 0; i < num; ++i) {
+            if (!b->use_local[i]) continue;
+            BatchDesc& d = b->desc[i];
+            const DeviceGraph& dg = ctxs[i]->g;
+            d.p.est_cut = dg.cut;
+            d.p.est_cut2 = dg.has_alt ? dg.alt.cut : nullptr;
+            d.p.est_out = b->d_est + eo;
+            d.p.est_stride = cfgs[i].pop;
+            eo += 2 * (size_t)cfgs[i].pop;
+        }
     }
     if (cudaMemcpy(b->d_rows, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(gapa_fail(GAPA_ERR_CUDA, "uploading the row table"));

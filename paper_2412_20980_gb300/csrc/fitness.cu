@@ -818,9 +818,26 @@ __global__ void __launch_bounds__(1024, 1) fitness_batched_kernel(const BatchDes
             const int member = q.i0 + team;
             const int* genes = bd.pop[buf] + (size_t)member * bd.p.k;
             long long* out = reinterpret_cast<long long*>(bd.fit[buf]) + member;
-            if (bd.list_bytes > 0) {
-                unsigned* region = reinterpret_cast<unsigned*>(lab + gapa_dev::tree16l_lab_ints(bd.n));
-                int* scal = reinterpret_cast<int*>(region) + bd.list_bytes / 4;
+            // the cut-local kernel with the operator kernels' estimates: the cheaper forest, or the
+            // full pipeline for a member expected to shatter both
+            bool local = bd.list_bytes > 0, alt = false;
+            if (local && bd.p.est_out) {
+                const unsigned e1 = bd.p.est_out[member], e2 = bd.p.est_out[bd.p.est_stride + member];
+                const unsigned e = e2 < e1 ? e2 : e1;
+                if (e > (unsigned)(bd.n / 4)) local = false;
+                alt = e2 < e1 && bd.alt.perm != nullptr;
+            }
+            unsigned* region = reinterpret_cast<unsigned*>(lab + gapa_dev::tree16l_lab_ints(bd.n));
+            int* scal = reinterpret_cast<int*>(region) + bd.list_bytes / 4;
+            if (local && alt) {
+                const DeviceForest& a = bd.alt;
+                const gapa_dev::Tree16Graph tb{bd.n,         a.perm,          a.palt,          a.lo_ptr,
+                                               a.lo_col,     a.nontree,       a.num_nontree,   a.fptr,
+                                               a.fcol16,     0,               bd.mean_deg_x16, bd.objective,
+                                               a.tparent,    a.kids,          a.roots,         a.num_roots,
+                                               bd.list_bytes};
+                gapa_dev::tree16_member_local(tm, lab, region, scal, tb, genes, bd.p.k, out, red[team], status);
+            } else if (local) {
                 gapa_dev::tree16_member_local(tm, lab, region, scal, g, genes, bd.p.k, out, red[team], status);
             } else {
                 gapa_dev::tree16_member(tm, lab, reinterpret_cast<unsigned*>(lab + bd.n), g, genes, bd.p.k, out,

@@ -124,6 +124,54 @@ __device__ __forceinline__ void clear_bitmap(unsigned* kept, int n) {
     for (int w = threadIdx.x; w < words; w += blockDim.x) kept[w] = 0u;
 }
 
+// Cost estimates of a finished row for the cut-local fitness kernel, under
+// the first and (if any) the second forest (whole CTA; the row was written by
+// this CTA before the barrier inside).
+__device__ void row_estimate(const GaParams& p, const int* row, int i) {
+    __shared__ long long part[2][kGaBlock / 32];
+    __syncthreads();
+    long long c = 0, c2 = 0;
+    const int T = blockDim.x;
+    int j = threadIdx.x;
+    // four genes per step, both forests' gathers in flight together
+    for (; j + 3 * T < p.k; j += 4 * T) {
+        int d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = row[j + u * T];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = (unsigned)d[u] < (unsigned)p.n;
+            c += ok ? __ldg(&p.est_cut[d[u]]) : 0;
+            c2 += ok && p.est_cut2 ? __ldg(&p.est_cut2[d[u]]) : 0;
+        }
+    }
+    for (; j < p.k; j += T) {
+        const int d = row[j];
+        if ((unsigned)d < (unsigned)p.n) {
+            c += __ldg(&p.est_cut[d]);
+            if (p.est_cut2) c2 += __ldg(&p.est_cut2[d]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        c2 += __shfl_down_sync(0xffffffffu, c2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        part[0][threadIdx.x >> 5] = c;
+        part[1][threadIdx.x >> 5] = c2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0, t2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += part[0][w];
+            t2 += part[1][w];
+        }
+        p.est_out[i] = (unsigned)(t < 0x7FFFFFFFll ? t : 0x7FFFFFFFll);
+        p.est_out[p.est_stride + i] = p.est_cut2 ? (unsigned)(t2 < 0x7FFFFFFFll ? t2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
+    }
+}
+
 // Population initialisation (Eq. 2) of row i: every position open, candidates from tag INIT.
 __device__ void init_row(const GaParams& p, int i, int* __restrict__ pop) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -131,9 +179,11 @@ __device__ void init_row(const GaParams& p, int i, int* __restrict__ pop) {
     clear_bitmap(sm.kept, p.n);
     for (int j = threadIdx.x; j < p.k; j += blockDim.x) sm.holes[j] = j;
     __syncthreads();
-    if (threadIdx.x >= 32) return;
-    InitCand cand{p.key, i, p.n};
-    repair_warp(sm.kept, sm.holes, p.k, pop + (size_t)i * p.k, cand, p.key, i, 0, p.n);
+    if (threadIdx.x < 32) {
+        InitCand cand{p.key, i, p.n};
+        repair_warp(sm.kept, sm.holes, p.k, pop + (size_t)i * p.k, cand, p.key, i, 0, p.n);
+    }
+    if (p.est_out) row_estimate(p, pop + (size_t)i * p.k, i);
 }
 
 __global__ void __launch_bounds__(kGaBlock) init_kernel(GaParams p, int* __restrict__ pop) { init_row(p, blockIdx.x, pop); }
@@ -226,54 +276,6 @@ __device__ void block_argmin(const long long* __restrict__ fit, int s, long long
 
 // Row i of one generation g: with an elite, row 0 = elite copy and row i >= 1
 // = child i; without (the (mu+lambda) children), row i = child with counter i.
-// Cost estimates of a finished row for the cut-local fitness kernel, under
-// the first and (if any) the second forest (whole CTA; the row was written by
-// this CTA before the barrier inside).
-__device__ void row_estimate(const GaParams& p, const int* row, int i) {
-    __shared__ long long part[2][kGaBlock / 32];
-    __syncthreads();
-    long long c = 0, c2 = 0;
-    const int T = blockDim.x;
-    int j = threadIdx.x;
-    // four genes per step, both forests' gathers in flight together
-    for (; j + 3 * T < p.k; j += 4 * T) {
-        int d[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) d[u] = row[j + u * T];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool ok = (unsigned)d[u] < (unsigned)p.n;
-            c += ok ? __ldg(&p.est_cut[d[u]]) : 0;
-            c2 += ok && p.est_cut2 ? __ldg(&p.est_cut2[d[u]]) : 0;
-        }
-    }
-    for (; j < p.k; j += T) {
-        const int d = row[j];
-        if ((unsigned)d < (unsigned)p.n) {
-            c += __ldg(&p.est_cut[d]);
-            if (p.est_cut2) c2 += __ldg(&p.est_cut2[d]);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        c += __shfl_down_sync(0xffffffffu, c, o);
-        c2 += __shfl_down_sync(0xffffffffu, c2, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        part[0][threadIdx.x >> 5] = c;
-        part[1][threadIdx.x >> 5] = c2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0, t2 = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            t += part[0][w];
-            t2 += part[1][w];
-        }
-        p.est_out[i] = (unsigned)(t < 0x7FFFFFFFll ? t : 0x7FFFFFFFll);
-        p.est_out[kOrderCap + i] = p.est_cut2 ? (unsigned)(t2 < 0x7FFFFFFFll ? t2 : 0x7FFFFFFFll) : 0xFFFFFFFFu;
-    }
-}
-
 __device__ void offspring_row(const GaParams& p, int i, int g, const int* __restrict__ pop_in,
                               const long long* __restrict__ fit_in, int* __restrict__ pop_out,
                               long long* __restrict__ fit_out, int* status, bool has_elite = true) {

@@ -250,10 +250,11 @@ struct GaParams {
     const long long* cum;  // roulette cumulative weights [s] (GAPA_FLAG_ROULETTE)
     // cost estimates of the rows for the cut-local fitness kernel (all null: none):
     // est_out[row] = sum over the row's genes of est_cut[gene], and the same under the second
-    // forest at est_out[kOrderCap + row] (est_cut2 null: 0xFFFFFFFF there)
+    // forest at est_out[est_stride + row] (est_cut2 null: 0xFFFFFFFF there)
     const int* est_cut;
     const int* est_cut2;
     unsigned* est_out;
+    int est_stride;
 };
 
 // One instance of a batched run (device-side descriptor).
@@ -276,12 +277,14 @@ struct BatchDesc {
     int mean_deg_x16;
     int objective;       // GAPA_OBJECTIVE_*
     int teams;           // members per CTA in the batched fitness kernel (1, 2, 4 or 8)
-    // cut-local TREE kernel (tree16_member_local): list_bytes > 0 when each team's slice holds it
+    // cut-local TREE kernel (tree16_member_local): list_bytes > 0 when each team's slice holds it;
+    // the members' cost estimates come from the operator kernels through p.est_out
     const int* tparent;
     const int4* kids;
     const int* roots;
     int num_roots;
     int list_bytes;
+    DeviceForest alt;    // the second forest (alt.perm null: none)
 };
 
 // A packet of the batched fitness work queue: members i0 .. i0+cnt-1 of instance b.
