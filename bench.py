@@ -126,9 +126,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+# sources the fitness kernels of each workload are compiled from: the shared-memory kernels
+# (fitness.cu and its headers) and, for graphs whose labels exceed shared memory, the
+# interleaved-label kernels (fitness_ig.cu, dispatched from fitness.cu)
+TRAFFIC_SOURCES = {
+    "large": ("fitness.cu", "fitness_ig.cu", "gapa_internal.cuh"),
+}
+DEFAULT_TRAFFIC_SOURCES = ("fitness.cu", "tree16.cuh", "gapa_internal.cuh")
+
+
+def kernel_source_hash(workload: str) -> str:
     h = hashlib.sha256()
-    for f in ("fitness.cu", "fitness_ig.cu", "tree16.cuh", "gapa_internal.cuh"):
+    for f in TRAFFIC_SOURCES.get(workload, DEFAULT_TRAFFIC_SOURCES):
         h.update(open(os.path.join(ROOT, "paper_2412_20980_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -140,7 +149,7 @@ def ncu_traffic(workload: str):
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(workload)
-    if not d or d.get("source_hash") != kernel_source_hash():
+    if not d or d.get("source_hash") != kernel_source_hash(workload):
         return None
     return d.get("dram_bytes_per_launch")
 

@@ -8,8 +8,9 @@
 // groups run per batch, as many as keep their labels within an L2-sized
 // budget.  The phases are those of the shared-memory TREE kernel (tree-parent
 // labels in BFS numbering, deleted nodes, cut with fallback parents, flatten,
-// join along non-tree edges), then sizes are counted into the roots and the
-// int64 sums of C(size, 2) are reduced per member.  Each phase is one
+// join along non-tree edges); the last flatten turns the roots into counters,
+// sizes are counted into them and the int64 sums of C(size, 2) are reduced per
+// member.  Each phase is one
 // grid-wide kernel; thread t of a group handles (node t/8, member t%8) in a
 // grid-stride loop, so the eight lanes of a node share one sector.
 //
@@ -47,9 +48,12 @@ __device__ __forceinline__ int ig_find(int* L, int m, int x) {
     }
 }
 
-__device__ __forceinline__ int ig_root(int* L, int m, int x) {
+// The top of x's chain: a node that points at itself or, once roots have
+// become counters, holds a negative count.  No live chain passes a deleted
+// node, so a negative label on a chain is always a counter.
+__device__ __forceinline__ int ig_top(int* L, int m, int x) {
     int p = *slot(L, x, m);
-    while (p != x) {
+    while (p != x && p >= 0) {
         x = p;
         p = *slot(L, x, m);
     }
@@ -169,10 +173,14 @@ __global__ void __launch_bounds__(kIgBlock) ig_cut_kernel(IgArgs a) {
     }
 }
 
-// every live node points at the top of its piece / its root (owner writes only)
+// every live node points at the top of its piece / its root (owner writes only;
+// a label already there is not rewritten).  kCounters: the last flatten also
+// turns every root into a counter (-1), the start of the size count; a
+// concurrent walk stops at a root either way.
 constexpr int kFlatInFlight = 4;  // items per thread resolved together by ig_flatten_kernel
 constexpr int kLinkInFlight = 4;  // items per thread loaded together by ig_link_kernel
 
+template <bool kCounters>
 __global__ void __launch_bounds__(kIgBlock) ig_flatten_kernel(IgArgs a) {
     // kFlatInFlight items per thread in flight: their labels, then their parents' labels, are
     // loaded together; only a chain longer than two steps walks on alone.  Parents have smaller
@@ -194,15 +202,25 @@ __global__ void __launch_bounds__(kIgBlock) ig_flatten_kernel(IgArgs a) {
 #pragma unroll
         for (int u = 0; u < kFlatInFlight; ++u) {
             const int v = (int)((t + u * G) / kM), m = (int)((t + u * G) % kM);
-            if (p[u] == kDead || p[u] == v) continue;
-            const int r = q[u] == p[u] ? p[u] : ig_root(L, m, q[u]);
-            *slot(L, v, m) = r;
+            if (p[u] == kDead) continue;
+            if (p[u] == v) {
+                if (kCounters) *slot(L, v, m) = -1;
+                continue;
+            }
+            const int r = (q[u] == p[u] || q[u] < 0) ? p[u] : ig_top(L, m, q[u]);
+            if (r != p[u]) *slot(L, v, m) = r;
         }
     }
     for (; t < total; t += G) {
         const int v = (int)(t / kM), m = (int)(t % kM);
         const int p = *slot(L, v, m);
-        if (p != kDead && p != v) *slot(L, v, m) = ig_root(L, m, p);
+        if (p == kDead) continue;
+        if (p == v) {
+            if (kCounters) *slot(L, v, m) = -1;
+            continue;
+        }
+        const int r = ig_top(L, m, p);
+        if (r != p) *slot(L, v, m) = r;
     }
 }
 
@@ -352,16 +370,6 @@ __global__ void __launch_bounds__(kIgBlock) ig_join_kernel(IgArgs a) {
     }
 }
 
-// roots become counters (-1 each)
-__global__ void __launch_bounds__(kIgBlock) ig_roots_kernel(IgArgs a) {
-    int* L = group_labels(a);
-    const size_t total = (size_t)a.n * kM;
-    for (size_t t = gtid(); t < total; t += gthreads()) {
-        const int v = (int)(t / kM), m = (int)(t % kM);
-        if (*slot(L, v, m) == v) *slot(L, v, m) = -1;
-    }
-}
-
 // every other live node adds itself to its root's counter; a thread keeps a
 // run of equal roots in a register and flushes it when the root changes
 __global__ void __launch_bounds__(kIgBlock) ig_count_kernel(IgArgs a) {
@@ -381,7 +389,16 @@ __global__ void __launch_bounds__(kIgBlock) ig_count_kernel(IgArgs a) {
         }
         ++run;
     }
-    if (run) atomicAdd(L + (size_t)run_root * kM + m, -run);
+    // the last runs: most threads end on the same root (the giant piece's), so the
+    // four lanes of a warp with this thread's member whose root equals their first
+    // lane's add their runs together, and one atomic carries them
+    const int lane = threadIdx.x & 31;
+    const int r0 = __shfl_sync(0xffffffffu, run_root, lane & (kM - 1));
+    int part = run_root == r0 ? run : 0;
+    if (run && run_root != r0) atomicAdd(L + (size_t)run_root * kM + m, -run);
+    part += __shfl_down_sync(0xffffffffu, part, 16);
+    part += __shfl_down_sync(0xffffffffu, part, 8);
+    if (lane < kM && part) atomicAdd(L + (size_t)r0 * kM + m, -part);
 }
 
 // Per member, the int64 sum of C(size, 2) over roots (PC) or the largest size
@@ -488,21 +505,20 @@ int gapa_launch_fitness_ig(gapa_ctx* c, const int32_t* pop, int s, int k, int64_
         ig_init_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_dead_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_cut_kernel<<<grid, kIgBlock, 0, st>>>(a);
-        ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_flatten_kernel<false><<<grid, kIgBlock, 0, st>>>(a);
         if (a.sampled) {
             ig_giant_kernel<<<dim3(1, gcount), kIgBlock, 0, st>>>(a);
             ig_link_kernel<<<grid, kIgBlock, 0, st>>>(a);
-            ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
+            ig_flatten_kernel<false><<<grid, kIgBlock, 0, st>>>(a);
             ig_outside_kernel<<<grid, kIgBlock, 0, st>>>(a);
             ig_scan_kernel<<<grid, kIgBlock, 0, st>>>(a);
         }
         if (a.num_nontree > 0) ig_join_kernel<<<egrid, kIgBlock, 0, st>>>(a);
-        ig_flatten_kernel<<<grid, kIgBlock, 0, st>>>(a);
-        ig_roots_kernel<<<grid, kIgBlock, 0, st>>>(a);
+        ig_flatten_kernel<true><<<grid, kIgBlock, 0, st>>>(a);
         ig_count_kernel<<<grid, kIgBlock, 0, st>>>(a);
         ig_sum_kernel<<<grid, kIgBlock, 0, st>>>(a);
         GAPA_CUDA(cudaGetLastError());
-        if (kernels) *kernels = (g0 == 0 ? 0 : *kernels) + (a.num_nontree > 0 ? 9 : 8) + (a.sampled ? 5 : 0);
+        if (kernels) *kernels = (g0 == 0 ? 0 : *kernels) + (a.num_nontree > 0 ? 8 : 7) + (a.sampled ? 5 : 0);
     }
     return GAPA_OK;
 }
