@@ -318,7 +318,7 @@ int gapa_batch_create(gapa_batch** out, int32_t num, gapa_ctx* const* ctxs, cons
         const gapa_config& g = cfgs[i];
         const DeviceGraph& dg = ctxs[i]->g;
         BatchDesc& d = b->desc[i];
-        memset(&d, 0, sizeof d);
+        d = BatchDesc{};
         d.p.n = dg.n;
         d.p.k = g.k;
         d.p.s = g.pop;
