@@ -302,7 +302,11 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
  * tree of the highest-degree live node as the giant tree and lets only nodes
  * outside it scan their whole adjacency; EDGES runs union-find over every
  * undirected edge.  AUTO (the default) is TREE_LOCAL where it applies and
- * the graph has more than 2048 nodes, else TREE. */
+ * the graph has more than 2048 nodes, else TREE.  Where the labels do not fit
+ * in shared memory (n above about 56,000 on GB300), the TREE settings run the
+ * same phases on labels in global memory, eight members interleaved per
+ * 32-byte sector, and EDGES and SAMPLED run one CTA per member over a global
+ * label array. */
 #define GAPA_FITNESS_AUTO 0
 #define GAPA_FITNESS_EDGES 1
 #define GAPA_FITNESS_SAMPLED 2
