@@ -1,4 +1,4 @@
-"""The multi-process host logic on CPU: two gloo ranks.
+"""The multi-process host logic on CPU: two and three gloo ranks.
 
 Independent populations (the benchmark's N > 1 mode) need only the rank seeds
 and the max-over-ranks timing; a population split by members needs the shard
@@ -102,10 +102,11 @@ def _free_port():
     return port
 
 
-def test_two_gloo_ranks(tmp_path):
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks(tmp_path, world):
+    """Two ranks split the 40 children 20/20; three ranks split them 14/13/13 (uneven slices)."""
     import torch.multiprocessing as mp
 
-    world = 2
     mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
                        start_method="spawn")
-    assert sorted(os.listdir(tmp_path)) == ["ok0", "ok1"]
+    assert sorted(os.listdir(tmp_path)) == [f"ok{r}" for r in range(world)]
