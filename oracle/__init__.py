@@ -19,6 +19,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
+# A prebuilt library to load instead of oracle.c (the planted-mistake tests point this at a copy
+# of the oracle with one mistake in it, to show that the pins catch it).
+_LIB_OVERRIDE = os.environ.get("GAPA_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -45,8 +48,11 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        build()
-        lib = ctypes.CDLL(_LIB_PATH)
+        if _LIB_OVERRIDE:
+            lib = ctypes.CDLL(_LIB_OVERRIDE)
+        else:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
         P = ctypes.c_void_p
         i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
         lib.oracle_philox4x32_10.argtypes = [P, P, P]

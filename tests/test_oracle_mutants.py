@@ -1,0 +1,136 @@
+"""The oracle's pins are sharp: plausible mistakes planted in a copy of the oracle are caught.
+
+Each mutant below changes one thing in a copy of oracle/oracle.c: a dropped or wrong term, a wrong
+sign or comparison, a wrong constant, or a wrong index.  The copy is compiled into a temporary
+library, and the oracle's own pin tests (tests/test_oracle_fitness_pins.py and
+tests/test_oracle_ga_pins.py) run against it in a subprocess.  The subprocess finds the copy
+through GAPA_ORACLE_LIB.  Every mutant must make at least one pin fail.  The mistakes are planted
+in the oracle, on the CPU, and nowhere else.
+
+One plausible mistake is not caught, by design.  It is the mapping of a Philox word to a gene in
+[0, n): multiply-high against x mod n.  That mapping is this build's own definition, which no law
+of the paper fixes (parity unpinned: reading R9).  Only the bit-exact comparison with the CUDA
+path would notice such a change.
+"""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+PINS = [os.path.join(ROOT, "tests", "test_oracle_fitness_pins.py"),
+        os.path.join(ROOT, "tests", "test_oracle_ga_pins.py")]
+
+# name: (text in oracle.c, replacement)
+MUTANTS = {
+    "pair count C(c+1, 2) in the BFS sum":
+        ("pc += (int64_t)sizes[c] * (int64_t)(sizes[c] - 1) / 2;",
+         "pc += (int64_t)sizes[c] * (int64_t)(sizes[c] + 1) / 2;"),
+    "BFS walks through deleted nodes":
+        ("if (!dead[v] && !seen[v]) { seen[v] = 1; queue[tail++] = v; }",
+         "if (!seen[v]) { seen[v] = 1; queue[tail++] = v; }"),
+    "MCN keeps the smallest component":
+        ("for (int64_t c = 0; c < ncomp; c++) if (sizes[c] > best) best = sizes[c];",
+         "for (int64_t c = 0; c < ncomp; c++) if (best == 0 || sizes[c] < best) best = sizes[c];"),
+    "Philox multiplier constant":
+        ("uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;",
+         "uint64_t p0 = (uint64_t)0xD2511F55u * (uint64_t)c0;"),
+    "Philox nine rounds":
+        ("for (int round = 0; round < 10; round++) {",
+         "for (int round = 0; round < 9; round++) {"),
+    "Philox key schedule constant":
+        ("k1 += 0xBB67AE85u;",
+         "k1 += 0xBB67AE87u;"),
+    "tournament keeps the highest fitness":
+        ("if (best < 0 || fit[x] < fit[best] || (fit[x] == fit[best] && x < best)) best = x;",
+         "if (best < 0 || fit[x] > fit[best] || (fit[x] == fit[best] && x < best)) best = x;"),
+    "tournament ties to the higher index":
+        ("if (best < 0 || fit[x] < fit[best] || (fit[x] == fit[best] && x < best)) best = x;",
+         "if (best < 0 || fit[x] < fit[best] || (fit[x] == fit[best] && x > best)) best = x;"),
+    "elite is the worst member":
+        ("if (fit_in[x] < fit_in[elite]) elite = x;",
+         "if (fit_in[x] > fit_in[elite]) elite = x;"),
+    "crossover mask inverted":
+        ("w->from_b[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_XOVER, 0) < pc_thr;",
+         "w->from_b[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_XOVER, 0) >= pc_thr;"),
+    "mutation never fires":
+        ("w->mutated[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUT, 0) < pm_thr;",
+         "w->mutated[j] = 0;"),
+    "genes from B may repeat kept genes":
+        ("if (!w->mutated[j] && w->from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }",
+         "if (!w->mutated[j] && w->from_b[j]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }"),
+    "roulette weights favour high fitness":
+        ("for (int32_t x = 0; x < s; x++) { acc += (mx - fit[x]) + 1; cum[x] = acc; }",
+         "for (int32_t x = 0; x < s; x++) { acc += fit[x] + 1; cum[x] = acc; }"),
+    "(mu+lambda) keeps the worst":
+        ("if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;",
+         "if (x[0] != y[0]) return x[0] > y[0] ? -1 : 1;"),
+    "union-find joins through deleted nodes":
+        ("if (v <= u || dead[v]) continue;",
+         "if (v <= u) continue;"),
+    "union-find pair count C(c, 2) as c^2 / 2":
+        ("if (!dead[v] && parent[v] == v) pc += size[v] * (size[v] - 1) / 2;",
+         "if (!dead[v] && parent[v] == v) pc += size[v] * size[v] / 2;"),
+    "edge genes leave their edges in place":
+        ("if (!gone[arc_id[e]] && !seen[v]) { seen[v] = 1; queue[tail++] = v; }",
+         "if (!seen[v]) { seen[v] = 1; queue[tail++] = v; }"),
+    "edge ids of reverse arcs looked up off by one":
+        ("if (col[mid] < u) lo = mid + 1; else hi = mid;",
+         "if (col[mid] <= u) lo = mid + 1; else hi = mid;"),
+    "repair does not mark a taken candidate":
+        ("if (!kept->in[c]) {\n                kept->in[c] = 1;\n                row[j] = c;",
+         "if (!kept->in[c]) {\n                row[j] = c;"),
+    "repair fill reuses the smallest free id":
+        ("while (kept->in[next]) next++;\n        kept->in[next] = 1;",
+         "while (kept->in[next]) next++;"),
+    "a mutated position keeps parent A's gene":
+        ("w->cand0[nh] = w->mutated[j] ? uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)\n                                     : A[j];",
+         "w->cand0[nh] = A[j];"),
+    "(mu+lambda) ties prefer children":
+        ("return x[1] < y[1] ? -1 : (x[1] > y[1]);",
+         "return x[1] > y[1] ? -1 : (x[1] < y[1]);"),
+}
+
+
+def _build(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutant text not found once: {name}"
+    tag = "".join(ch if ch.isalnum() else "_" for ch in name)
+    c_path = tmp_path / f"{tag}.c"
+    so_path = tmp_path / f"lib{tag}.so"
+    c_path.write_text(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", str(c_path), "-o", str(so_path)],
+                   check=True)
+    return str(so_path)
+
+
+def _pins_pass(lib):
+    env = dict(os.environ, GAPA_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return r.returncode == 0, r.stdout[-2000:]
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    libs = {name: _build(name, tmp_path) for name in MUTANTS}
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = dict(zip(libs, ex.map(_pins_pass, libs.values())))
+    survivors = [name for name, (ok, _) in results.items() if ok]
+    assert not survivors, f"mistakes no pin catches: {survivors}"
+
+
+def test_unmutated_copy_passes_the_pins(tmp_path):
+    """The harness itself: the oracle compiled the same way from the unchanged source passes."""
+    so_path = tmp_path / "liboracle_copy.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", SRC, "-o", str(so_path)], check=True)
+    ok, out = _pins_pass(str(so_path))
+    assert ok, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_text_present(name):
+    assert open(SRC).read().count(MUTANTS[name][0]) == 1, name
