@@ -1,5 +1,9 @@
 """The oracle's pins are sharp: plausible mistakes planted in a copy of the oracle are caught.
 
+The same holds for the plain references of the SixDST objective and of the surrogate
+(oracle/sixdst_ref.py, oracle/surrogate_ref.py).  For those, a small pytest plugin re-executes the
+module's source with one mistake in it before the pin tests of that module run.
+
 Each mutant below changes one thing in a copy of oracle/oracle.c: a dropped or wrong term, a wrong
 sign or comparison, a wrong constant, or a wrong index.  The copy is compiled into a temporary
 library, and the oracle's own pin tests (tests/test_oracle_fitness_pins.py and
@@ -134,3 +138,84 @@ def test_unmutated_copy_passes_the_pins(tmp_path):
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_text_present(name):
     assert open(SRC).read().count(MUTANTS[name][0]) == 1, name
+
+
+# name: (reference module, text in its source, replacement, pin file)
+PY_MUTANTS = {
+    "SixDST without the identity": (
+        "oracle.sixdst_ref", "base = np.minimum(a + np.eye(n, dtype=np.int64), 1).astype(np.float64)",
+        "base = np.minimum(a, 1).astype(np.float64)", "test_oracle_sixdst_pins.py"),
+    "SixDST one product short": (
+        "oracle.sixdst_ref", "for _ in range(hops - 1):", "for _ in range(hops - 2):", "test_oracle_sixdst_pins.py"),
+    "SixDST without the normalisation": (
+        "oracle.sixdst_ref", "m = np.minimum(m @ base, 1.0)", "m = m @ base", "test_oracle_sixdst_pins.py"),
+    "SixDST PC counts each node with itself": (
+        "oracle.sixdst_ref", "return int((rows.sum() - live.sum()) // 2)", "return int(rows.sum() // 2)",
+        "test_oracle_sixdst_pins.py"),
+    "SixDST keeps arcs into deleted nodes": (
+        "oracle.sixdst_ref", "keep = live[src] & live[col]", "keep = live[src]", "test_oracle_sixdst_pins.py"),
+    "surrogate ReLU mask of the wrong layer": (
+        "oracle.surrogate_ref", 'dz2 = np.outer(dy, params["w3"]) * (c["z2"] > 0)',
+        'dz2 = np.outer(dy, params["w3"]) * (c["z1"] > 0)', "test_oracle_surrogate_pins.py"),
+    "surrogate b1 gradient from the second layer": (
+        "oracle.surrogate_ref", 'g["b1"] = dz1.sum(axis=0)', 'g["b1"] = dz2.sum(axis=0)',
+        "test_oracle_surrogate_pins.py"),
+    "surrogate embedding gradient without 1/sqrt(k)": (
+        "oracle.surrogate_ref", "np.add.at(gE, pop[b], dx[b, :EMB] / np.sqrt(k))", "np.add.at(gE, pop[b], dx[b, :EMB])",
+        "test_oracle_surrogate_pins.py"),
+    "surrogate loss gradient not averaged": (
+        "oracle.surrogate_ref", "dy = 2.0 * (y - t) / B", "dy = 2.0 * (y - t)", "test_oracle_surrogate_pins.py"),
+    "AdamW without bias correction": (
+        "oracle.surrogate_ref", "mh = m / (1 - b1 ** tau)", "mh = m", "test_oracle_surrogate_pins.py"),
+    "AdamW decay outside the learning rate": (
+        "oracle.surrogate_ref", "p -= lr * (mh / (np.sqrt(vh) + eps) + wd * p)",
+        "p -= lr * mh / (np.sqrt(vh) + eps) + wd * p", "test_oracle_surrogate_pins.py"),
+    "residual r1 counts two live neighbours": (
+        "oracle.surrogate_ref", "r1 = int(np.count_nonzero(touched & (live_nb == 1)))",
+        "r1 = int(np.count_nonzero(touched & (live_nb == 2)))", "test_oracle_surrogate_pins.py"),
+    "standardised counts without the floor at 1": (
+        "oracle.surrogate_ref", "sd = max(np.sqrt(max(var, 0.0)), 1.0)", "sd = max(np.sqrt(max(var, 0.0)), 1e-12)",
+        "test_oracle_surrogate_pins.py"),
+    "degree feature: mean instead of max": (
+        "oracle.surrogate_ref", "x[i, 65] = qi.max()", "x[i, 65] = qi.mean()", "test_oracle_surrogate_pins.py"),
+}
+
+PLUGIN = """
+import importlib, inspect, os
+
+
+def pytest_configure(config):
+    mod = importlib.import_module(os.environ["GAPA_MUTANT_MODULE"])
+    src = inspect.getsource(mod)
+    old, new = os.environ["GAPA_MUTANT_OLD"], os.environ["GAPA_MUTANT_NEW"]
+    assert src.count(old) == 1, "mutant text not found once"
+    exec(compile(src.replace(old, new), mod.__file__, "exec"), mod.__dict__)
+"""
+
+
+def _py_pins_pass(tmp_path, module, old, new, pin_file):
+    (tmp_path / "gapa_mutant_plugin.py").write_text(PLUGIN)
+    env = dict(os.environ, GAPA_MUTANT_MODULE=module, GAPA_MUTANT_OLD=old, GAPA_MUTANT_NEW=new,
+               PYTHONPATH=os.pathsep.join([ROOT, str(tmp_path)] + [p for p in [os.environ.get("PYTHONPATH")] if p]))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-p",
+                        "gapa_mutant_plugin", os.path.join(ROOT, "tests", pin_file)],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+def test_every_planted_reference_mistake_fails_a_pin(tmp_path):
+    for name, (module, old, new, _) in PY_MUTANTS.items():
+        src = open(os.path.join(ROOT, *module.split(".")) + ".py").read()
+        assert src.count(old) == 1, name
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = dict(zip(PY_MUTANTS, ex.map(lambda m: _py_pins_pass(tmp_path, *m), PY_MUTANTS.values())))
+    survivors = [name for name, (ok, _) in results.items() if ok]
+    assert not survivors, f"mistakes no pin catches: {survivors}"
+
+
+@pytest.mark.parametrize("module,pin_file", [("oracle.sixdst_ref", "test_oracle_sixdst_pins.py"),
+                                             ("oracle.surrogate_ref", "test_oracle_surrogate_pins.py")])
+def test_reference_plugin_without_a_mistake_passes(tmp_path, module, pin_file):
+    """The plugin itself: re-executing the unchanged source leaves the pins passing."""
+    ok, out = _py_pins_pass(tmp_path, module, "import numpy as np", "import numpy as np", pin_file)
+    assert ok, out
