@@ -77,6 +77,10 @@ def _load():
         lib.oracle_run.argtypes = [i32, P, P, i32, i32, i32, i32, u32, u32, u64, u32, i32,
                                    P, P, P, P, P, i32]
         lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_child_explicit.argtypes = [i32, i32, P, P, P, P, P, P, P]
+        lib.oracle_child_explicit.restype = ctypes.c_int
+        lib.oracle_uniform_below.argtypes = [u32, i32]
+        lib.oracle_uniform_below.restype = i32
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -175,6 +179,32 @@ def pop_init(n: int, k: int, s: int, seed: int) -> np.ndarray:
     pop = np.zeros((s, k), dtype=np.int32)
     _check(_load().oracle_pop_init(n, k, s, seed, _ptr(pop)), "pop_init")
     return pop
+
+
+REPAIR_ROUNDS = 32
+
+
+def child_explicit(n: int, A, B, from_b, mutated, mutval, later) -> np.ndarray:
+    """One child of parents A and B from explicit crossover and mutation masks, the round-0
+    candidates ``mutval`` of mutated positions and the repair candidates ``later`` (31 rounds x k)
+    - the child assembly and repair of a generation with no random numbers (test entry)."""
+    A, B = _i32(A), _i32(B)
+    k = A.shape[0]
+    fb = np.ascontiguousarray(from_b, dtype=np.uint8)
+    mu = np.ascontiguousarray(mutated, dtype=np.uint8)
+    mv = _i32(mutval)
+    lt = _i32(later).reshape(REPAIR_ROUNDS - 1, k)
+    if not (B.shape == fb.shape == mu.shape == mv.shape == (k,)):
+        raise ValueError("A, B, from_b, mutated and mutval must all have k entries")
+    row = np.full(k, -1, dtype=np.int32)
+    _check(_load().oracle_child_explicit(n, k, _ptr(A), _ptr(B), _ptr(fb), _ptr(mu), _ptr(mv),
+                                         _ptr(np.ascontiguousarray(lt)), _ptr(row)), "child_explicit")
+    return row
+
+
+def uniform_below(x: int, n: int) -> int:
+    """The oracle's map of a 32-bit Philox word to [0, n)."""
+    return int(_load().oracle_uniform_below(x & 0xFFFFFFFF, n))
 
 
 def thresholds(pc_rate: float, pm_rate: float) -> tuple[int, int]:

@@ -38,7 +38,9 @@
  * Parity: PC is pinned by closed forms, brute force, scipy and the dense
  * reachability identity of Eqs. 14-17; Philox by an independent
  * implementation; the genetic operators by statistical laws and special
- * cases (see the tests).
+ * cases; the duplicate rule, the word-to-[0, n) map and the counter layout
+ * (this build's own definitions: the paper is silent on them) by hand-worked
+ * children built through oracle_child_explicit (see the tests).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -324,22 +326,37 @@ typedef struct {
     uint8_t* in;
 } keptset;
 
+/* Where the candidates of repair rounds r >= 1 come from: uniform over [0, n)
+ * from draw(j, i, g, REPAIR, r), or - for the hand-worked cases of the tests
+ * (oracle_child_explicit) - an explicit table later[(r - 1) * k + j]. */
+typedef struct {
+    uint64_t seed;
+    int32_t i, g, k;
+    const int32_t* later; /* NULL: Philox */
+} repair_source;
+
+static int32_t repair_candidate(const repair_source* src, int32_t j, int32_t r, int32_t n)
+{
+    if (src->later) return src->later[(size_t)(r - 1) * (size_t)src->k + (size_t)j];
+    return uniform_below(draw(src->seed, (uint32_t)j, (uint32_t)src->i, (uint32_t)src->g, TAG_REPAIR, (uint32_t)r), n);
+}
+
 /* Duplicate repair (the paper is silent on duplicates).  `holes` lists the
  * positions without a gene in ascending order, `cand0` their first
  * candidates.  Round r = 0 .. 31: every remaining hole, in ascending position
  * order, takes its round-r candidate if that node is not in the kept set, and
  * the node joins the kept set at once.  The round-0 candidate is cand0; a
- * later round's candidate is uniform over [0, n) from draw(j, i, g, REPAIR, r).
- * Holes still open after round 31 take, in ascending position order, the
- * smallest node id not in the kept set. */
-static void repair(uint64_t seed, int32_t i, int32_t g, int32_t n, keptset* kept,
+ * later round's candidate comes from repair_candidate().  Holes still open
+ * after round 31 take, in ascending position order, the smallest node id not
+ * in the kept set. */
+static void repair(const repair_source* src, int32_t n, keptset* kept,
                    int32_t* row, int32_t* holes, int32_t nholes, const int32_t* cand0)
 {
     for (int32_t r = 0; r < REPAIR_ROUNDS && nholes > 0; r++) {
         int32_t still = 0;
         for (int32_t h = 0; h < nholes; h++) {
             int32_t j = holes[h];
-            int32_t c = r == 0 ? cand0[h] : uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_REPAIR, (uint32_t)r), n);
+            int32_t c = r == 0 ? cand0[h] : repair_candidate(src, j, r, n);
             if (!kept->in[c]) {
                 kept->in[c] = 1;
                 row[j] = c;
@@ -374,7 +391,8 @@ int oracle_pop_init(int32_t n, int32_t k, int32_t s, uint64_t seed, int32_t* pop
             holes[j] = j;
             cand0[j] = uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, 0, TAG_INIT, 0), n);
         }
-        repair(seed, i, 0, n, &kept, row, holes, k, cand0);
+        const repair_source src = { seed, i, 0, k, NULL };
+        repair(&src, n, &kept, row, holes, k, cand0);
     }
     free(kept.in); free(holes); free(cand0);
     return ORACLE_OK;
@@ -436,45 +454,102 @@ static int32_t roulette(uint64_t seed, int32_t i, int32_t g, int32_t slot, int32
     return x;
 }
 
-/* One child with counter index i from parents A and B (Eqs. 3-9 with the
- * duplicate rule):
- *   crossover - gene j is B[j] where draw(j,i,g,XOVER,0) < pc_thr, else A[j];
- *   mutation  - gene j becomes a hole where draw(j,i,g,MUT,0) < pm_thr, with
- *              round-0 candidate uniform over [0,n) from draw(j,i,g,MUTVAL,0);
- *   duplicates - a gene taken from B that equals a kept gene taken from A
- *              becomes a hole whose round-0 candidate is A[j];
- *   repair    - as in repair(). */
+/* One child from parents A and B, given its crossover mask from_b, its
+ * mutation mask and the round-0 candidates of the mutated positions (Eqs. 6
+ * and 9 with the duplicate rule):
+ *   crossover  - gene j is B[j] where from_b[j], else A[j];
+ *   mutation   - gene j becomes a hole where mutated[j], with round-0
+ *                candidate mutval[j];
+ *   duplicates - every gene kept from A is kept (A's genes are distinct);
+ *                then, in ascending position order, a gene taken from B is
+ *                kept unless it equals a gene already kept, in which case its
+ *                position becomes a hole whose round-0 candidate is A[j];
+ *   repair     - as in repair(), with later candidates from src. */
 typedef struct {
     keptset kept;
     int32_t* holes;
     int32_t* cand0;
     uint8_t* from_b;
     uint8_t* mutated;
+    int32_t* mutval;
 } child_scratch;
 
-static void make_child(uint64_t seed, int32_t n, int32_t k, int32_t i, int32_t g, uint32_t pc_thr, uint32_t pm_thr,
-                       const int32_t* A, const int32_t* B, int32_t* row, child_scratch* w)
+static void assemble_child(int32_t n, int32_t k, const int32_t* A, const int32_t* B, const uint8_t* from_b,
+                           const uint8_t* mutated, const int32_t* mutval, const repair_source* src,
+                           int32_t* row, child_scratch* w)
 {
     memset(w->kept.in, 0, (size_t)n);
-    for (int32_t j = 0; j < k; j++) {
-        w->from_b[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_XOVER, 0) < pc_thr;
-        w->mutated[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUT, 0) < pm_thr;
-        row[j] = -1;
-    }
+    for (int32_t j = 0; j < k; j++) row[j] = -1;
     /* genes kept from A first, then genes from B that do not repeat one */
     for (int32_t j = 0; j < k; j++)
-        if (!w->mutated[j] && !w->from_b[j]) { row[j] = A[j]; w->kept.in[A[j]] = 1; }
+        if (!mutated[j] && !from_b[j]) { row[j] = A[j]; w->kept.in[A[j]] = 1; }
     for (int32_t j = 0; j < k; j++)
-        if (!w->mutated[j] && w->from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }
+        if (!mutated[j] && from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }
     int32_t nh = 0;
     for (int32_t j = 0; j < k; j++) {
         if (row[j] >= 0) continue;
         w->holes[nh] = j;
-        w->cand0[nh] = w->mutated[j] ? uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)
-                                     : A[j];
+        w->cand0[nh] = mutated[j] ? mutval[j] : A[j];
         nh++;
     }
-    repair(seed, i, g, n, &w->kept, row, w->holes, nh, w->cand0);
+    repair(src, n, &w->kept, row, w->holes, nh, w->cand0);
+}
+
+/* One child with counter index i in generation g (Eqs. 3-9): the crossover
+ * mask is draw(j,i,g,XOVER,0) < pc_thr, the mutation mask
+ * draw(j,i,g,MUT,0) < pm_thr, a mutated position's round-0 candidate uniform
+ * over [0,n) from draw(j,i,g,MUTVAL,0); repair candidates from Philox. */
+static void make_child(uint64_t seed, int32_t n, int32_t k, int32_t i, int32_t g, uint32_t pc_thr, uint32_t pm_thr,
+                       const int32_t* A, const int32_t* B, int32_t* row, child_scratch* w)
+{
+    for (int32_t j = 0; j < k; j++) {
+        w->from_b[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_XOVER, 0) < pc_thr;
+        w->mutated[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUT, 0) < pm_thr;
+        w->mutval[j] = w->mutated[j] ? uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)
+                                     : -1;
+    }
+    const repair_source src = { seed, i, g, k, NULL };
+    assemble_child(n, k, A, B, w->from_b, w->mutated, w->mutval, &src, row, w);
+}
+
+/* TEST ENTRY (hand-worked cases, no random numbers): one child of parents A
+ * and B over node ids [0, n) from explicit masks from_b[k], mutated[k] (0/1),
+ * round-0 candidates mutval[k] of the mutated positions, and the candidates
+ * of repair rounds 1 .. 31 in later[31][k].  Every id must lie in [0, n) and
+ * each parent must hold distinct genes; returns ORACLE_EINVAL otherwise. */
+int oracle_child_explicit(int32_t n, int32_t k, const int32_t* A, const int32_t* B, const uint8_t* from_b,
+                          const uint8_t* mutated, const int32_t* mutval, const int32_t* later, int32_t* row)
+{
+    if (n < 1 || k < 0 || k >= n) return ORACLE_EINVAL;
+    for (int32_t j = 0; j < k; j++) {
+        if (A[j] < 0 || A[j] >= n || B[j] < 0 || B[j] >= n) return ORACLE_EINVAL;
+        if (mutated[j] && (mutval[j] < 0 || mutval[j] >= n)) return ORACLE_EINVAL;
+        for (int32_t r = 0; r + 1 < REPAIR_ROUNDS; r++)
+            if (later[(size_t)r * (size_t)k + (size_t)j] < 0 || later[(size_t)r * (size_t)k + (size_t)j] >= n)
+                return ORACLE_EINVAL;
+        for (int32_t q = 0; q < j; q++)
+            if (A[q] == A[j] || B[q] == B[j]) return ORACLE_EINVAL;
+    }
+    child_scratch w;
+    w.kept.n = n;
+    w.kept.in = (uint8_t*)malloc((size_t)n);
+    w.holes = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    w.cand0 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    w.from_b = w.mutated = NULL;
+    w.mutval = NULL;
+    int err = (!w.kept.in || !w.holes || !w.cand0) ? ORACLE_ENOMEM : ORACLE_OK;
+    if (err == ORACLE_OK) {
+        const repair_source src = { 0, 0, 0, k, later };
+        assemble_child(n, k, A, B, from_b, mutated, mutval, &src, row, &w);
+    }
+    free(w.kept.in); free(w.holes); free(w.cand0);
+    return err;
+}
+
+/* TEST ENTRY: the map of a 32-bit Philox word x to [0, n). */
+int32_t oracle_uniform_below(uint32_t x, int32_t n)
+{
+    return uniform_below(x, n);
 }
 
 /* Parent for slot 0 (A) or 1 (B) of the child with counter index i, chosen
@@ -527,10 +602,12 @@ int oracle_generation(int32_t n, const int32_t* row_ptr, const int32_t* col,
     w.cand0 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
     w.from_b = (uint8_t*)malloc((size_t)k + 1);
     w.mutated = (uint8_t*)malloc((size_t)k + 1);
+    w.mutval = (int32_t*)malloc(sizeof(int32_t) * ((size_t)k + 1));
     int64_t* cum = (int64_t*)malloc(sizeof(int64_t) * (size_t)s);
     int32_t* kids = (int32_t*)malloc(sizeof(int32_t) * ((size_t)nchild * (size_t)k + 1));
     int64_t* kfit = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nchild + 1));
-    if (!w.kept.in || !w.holes || !w.cand0 || !w.from_b || !w.mutated || !cum || !kids || !kfit) err = ORACLE_ENOMEM;
+    if (!w.kept.in || !w.holes || !w.cand0 || !w.from_b || !w.mutated || !w.mutval || !cum || !kids || !kfit)
+        err = ORACLE_ENOMEM;
     if (err == ORACLE_OK) {
         roulette_weights(fit_in, s, cum);
         for (int32_t c = 0; c < nchild; c++) {
@@ -569,7 +646,8 @@ int oracle_generation(int32_t n, const int32_t* row_ptr, const int32_t* col,
             free(key);
         }
     }
-    free(w.kept.in); free(w.holes); free(w.cand0); free(w.from_b); free(w.mutated); free(cum); free(kids); free(kfit);
+    free(w.kept.in); free(w.holes); free(w.cand0); free(w.from_b); free(w.mutated); free(w.mutval);
+    free(cum); free(kids); free(kfit);
     return err;
 }
 

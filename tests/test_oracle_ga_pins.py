@@ -370,3 +370,76 @@ def test_edge_gene_generation():
     pop = res["pop"]
     assert pop.min() >= 0 and pop.max() < E and all(len(set(r)) == 40 for r in pop.tolist())
     assert np.array_equal(res["fit"], oracle.fitness(g.row_ptr, g.col, pop, "edges"))
+
+
+# --- Hand-worked children (tests/golden/child_worked_examples.json) -------------------------------
+# The duplicate rule (reading R5) and the word-to-[0, n) map (reading R9) are this build's own
+# definitions: the paper is silent on duplicates (Section III-B, Eqs. 6 and 9) and draws with
+# torch.rand.  These cases fix them by value, each derived by hand in the golden file.
+
+_GOLDEN_CHILD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "child_worked_examples.json")
+
+
+def _later_table(spec, k):
+    table = np.full((oracle.REPAIR_ROUNDS - 1, k), spec["fill"], dtype=np.int32)
+    for rnd, j, v in spec["set"]:
+        table[rnd - 1, j] = v
+    return table
+
+
+def _golden_children():
+    with open(_GOLDEN_CHILD) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", _golden_children()["cases"], ids=lambda c: c["name"][:60])
+def test_child_hand_worked(case):
+    k = len(case["A"])
+    got = oracle.child_explicit(case["n"], case["A"], case["B"], case["from_b"], case["mutated"],
+                                case["mutval"], _later_table(case["later"], k))
+    assert got.tolist() == case["expected"], case["derivation"]
+
+
+def test_uniform_below_hand_worked():
+    for x, n, want in _golden_children()["uniform_below"]["cases"]:
+        assert oracle.uniform_below(x, n) == want, (x, n)
+
+
+def test_child_explicit_rejects_bad_input():
+    later = np.zeros((oracle.REPAIR_ROUNDS - 1, 2), dtype=np.int32)
+    with pytest.raises(oracle.OracleError):  # parent A repeats a gene
+        oracle.child_explicit(5, [1, 1], [2, 3], [0, 0], [0, 0], [0, 0], later)
+    with pytest.raises(oracle.OracleError):  # a mutation candidate outside [0, n)
+        oracle.child_explicit(5, [1, 2], [2, 3], [0, 0], [1, 0], [5, 0], later)
+
+
+def test_generation_children_follow_the_counter_layout():
+    """Every child of an oracle generation equals the hand-worked assembly fed with the masks and
+    candidates that the written counter layout gives: (j, i, g, tag << 24 | round) with tags SEL,
+    XOVER, MUT, MUTVAL and REPAIR, Bernoulli(p) = x < floor(p 2^32), words mapped by
+    uniform_below (pinned above), tournaments of size 2 with replacement, lower fitness and then
+    lower index winning."""
+    g_ = synth.ba_graph(60, 2, 3)
+    n, k, s, t, gen, seed = g_.n, 12, 24, 2, 5, 0xBEEF
+    pc_thr, pm_thr = oracle.thresholds(0.5, 0.15)
+    pop = oracle.pop_init(n, k, s, seed)
+    fit = oracle.fitness(g_.row_ptr, g_.col, pop)
+    pop1, _ = oracle.generation(g_.row_ptr, g_.col, pop, fit, gen, tourn=t, pc_thr=pc_thr, pm_thr=pm_thr,
+                                seed=seed)
+
+    def tour(i, slot):
+        best = -1
+        for r in range(t):
+            x = oracle.uniform_below(oracle.draw(seed, slot * t + r, i, gen, oracle.TAG_SEL), s)
+            if best < 0 or fit[x] < fit[best] or (fit[x] == fit[best] and x < best):
+                best = x
+        return best
+
+    for i in range(1, s):
+        A, B = pop[tour(i, 0)], pop[tour(i, 1)]
+        fb = [oracle.draw(seed, j, i, gen, oracle.TAG_XOVER) < pc_thr for j in range(k)]
+        mu = [oracle.draw(seed, j, i, gen, oracle.TAG_MUT) < pm_thr for j in range(k)]
+        mv = [oracle.uniform_below(oracle.draw(seed, j, i, gen, oracle.TAG_MUTVAL), n) for j in range(k)]
+        later = [[oracle.uniform_below(oracle.draw(seed, j, i, gen, oracle.TAG_REPAIR, r), n) for j in range(k)]
+                 for r in range(1, oracle.REPAIR_ROUNDS)]
+        assert oracle.child_explicit(n, A, B, fb, mu, mv, later).tolist() == pop1[i].tolist(), i

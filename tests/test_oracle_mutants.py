@@ -11,10 +11,12 @@ tests/test_oracle_ga_pins.py) run against it in a subprocess.  The subprocess fi
 through GAPA_ORACLE_LIB.  Every mutant must make at least one pin fail.  The mistakes are planted
 in the oracle, on the CPU, and nowhere else.
 
-One plausible mistake is not caught, by design.  It is the mapping of a Philox word to a gene in
-[0, n): multiply-high against x mod n.  That mapping is this build's own definition, which no law
-of the paper fixes (parity unpinned: reading R9).  Only the bit-exact comparison with the CUDA
-path would notice such a change.
+The build's own definitions, which no law of the paper fixes - the duplicate rule (reading R5),
+the map of a Philox word to [0, n) (reading R9) and the counter layout - are pinned by the
+hand-worked values of tests/golden/child_worked_examples.json; the mutants of those definitions
+below (the other priority between A and B genes, another round-0 candidate, the blueprint's
+lowest-position rule, a fill from the largest id, x mod n, a wrong tag or counter order) are
+caught by them.
 """
 import os
 import subprocess
@@ -64,8 +66,8 @@ MUTANTS = {
         ("w->mutated[j] = draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUT, 0) < pm_thr;",
          "w->mutated[j] = 0;"),
     "genes from B may repeat kept genes":
-        ("if (!w->mutated[j] && w->from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }",
-         "if (!w->mutated[j] && w->from_b[j]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }"),
+        ("if (!mutated[j] && from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }",
+         "if (!mutated[j] && from_b[j]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }"),
     "roulette weights favour high fitness":
         ("for (int32_t x = 0; x < s; x++) { acc += (mx - fit[x]) + 1; cum[x] = acc; }",
          "for (int32_t x = 0; x < s; x++) { acc += fit[x] + 1; cum[x] = acc; }"),
@@ -91,8 +93,56 @@ MUTANTS = {
         ("while (kept->in[next]) next++;\n        kept->in[next] = 1;",
          "while (kept->in[next]) next++;"),
     "a mutated position keeps parent A's gene":
-        ("w->cand0[nh] = w->mutated[j] ? uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)\n                                     : A[j];",
+        ("w->cand0[nh] = mutated[j] ? mutval[j] : A[j];",
          "w->cand0[nh] = A[j];"),
+    "round-0 candidate of a repeated B gene is B[j]":
+        ("w->cand0[nh] = mutated[j] ? mutval[j] : A[j];",
+         "w->cand0[nh] = mutated[j] ? mutval[j] : B[j];"),
+    "B genes win over A genes":
+        ("    for (int32_t j = 0; j < k; j++)\n"
+         "        if (!mutated[j] && !from_b[j]) { row[j] = A[j]; w->kept.in[A[j]] = 1; }\n"
+         "    for (int32_t j = 0; j < k; j++)\n"
+         "        if (!mutated[j] && from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }",
+         "    for (int32_t j = 0; j < k; j++)\n"
+         "        if (!mutated[j] && from_b[j]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }\n"
+         "    for (int32_t j = 0; j < k; j++)\n"
+         "        if (!mutated[j] && !from_b[j] && !w->kept.in[A[j]]) { row[j] = A[j]; w->kept.in[A[j]] = 1; }"),
+    "the lowest position keeps a repeated gene, the other parent's gene as candidate":
+        ("    for (int32_t j = 0; j < k; j++)\n"
+         "        if (!mutated[j] && !from_b[j]) { row[j] = A[j]; w->kept.in[A[j]] = 1; }\n"
+         "    for (int32_t j = 0; j < k; j++)\n"
+         "        if (!mutated[j] && from_b[j] && !w->kept.in[B[j]]) { row[j] = B[j]; w->kept.in[B[j]] = 1; }\n"
+         "    int32_t nh = 0;\n"
+         "    for (int32_t j = 0; j < k; j++) {\n"
+         "        if (row[j] >= 0) continue;\n"
+         "        w->holes[nh] = j;\n"
+         "        w->cand0[nh] = mutated[j] ? mutval[j] : A[j];",
+         "    for (int32_t j = 0; j < k; j++) {\n"
+         "        const int32_t v = from_b[j] ? B[j] : A[j];\n"
+         "        if (!mutated[j] && !w->kept.in[v]) { row[j] = v; w->kept.in[v] = 1; }\n"
+         "    }\n"
+         "    int32_t nh = 0;\n"
+         "    for (int32_t j = 0; j < k; j++) {\n"
+         "        if (row[j] >= 0) continue;\n"
+         "        w->holes[nh] = j;\n"
+         "        w->cand0[nh] = mutated[j] ? mutval[j] : (from_b[j] ? A[j] : B[j]);"),
+    "repair fill from the largest free id":
+        ("    int32_t next = 0;\n    for (int32_t h = 0; h < nholes; h++) {\n        while (kept->in[next]) next++;",
+         "    int32_t next = n - 1;\n    for (int32_t h = 0; h < nholes; h++) {\n        while (kept->in[next]) next--;"),
+    "later repair rounds retry the round-0 candidate":
+        ("int32_t c = r == 0 ? cand0[h] : repair_candidate(src, j, r, n);",
+         "int32_t c = cand0[h];"),
+    "31 repair rounds":
+        ("#define REPAIR_ROUNDS 32", "#define REPAIR_ROUNDS 31"),
+    "word mapped to [0, n) by x mod n":
+        ("return (int32_t)(((uint64_t)x * (uint64_t)(uint32_t)n) >> 32);",
+         "return (int32_t)(x % (uint32_t)n);"),
+    "counter with member and gene swapped":
+        ("uint32_t ctr[4] = { j, i, g, (tag << 24) | round };\n    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };\n    uint32_t out[4];\n    oracle_philox4x32_10(ctr, key, out);\n    return out[0];",
+         "uint32_t ctr[4] = { i, j, g, (tag << 24) | round };\n    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };\n    uint32_t out[4];\n    oracle_philox4x32_10(ctr, key, out);\n    return out[0];"),
+    "mutation candidates drawn with the repair tag":
+        ("uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_MUTVAL, 0), n)",
+         "uniform_below(draw(seed, (uint32_t)j, (uint32_t)i, (uint32_t)g, TAG_REPAIR, 0), n)"),
     "(mu+lambda) ties prefer children":
         ("return x[1] < y[1] ? -1 : (x[1] > y[1]);",
          "return x[1] > y[1] ? -1 : (x[1] < y[1]);"),
