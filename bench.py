@@ -27,10 +27,20 @@ Other workloads (for the design notes, not the headline line):
            that same value (the screened run may take up to 600 generations);
            the 1.01 x tolerance is reported beside it.
 
+The default line (throughput workload, one GPU) also carries, under "workloads", each of the
+other workloads timed in the same run with a short step count of its own: "small" (whole runs
+through gapa_run), "large", "batched", "sixdst" and "surrogate" (screening the top 25 % of the
+children, with 12.5 % beside it).  Rooflines of graphs that fit in L2 are graded against the L2
+read bandwidth measured in the run (the library's probe), with the HBM-denominated figure beside
+it; larger graphs against the measured HBM copy bandwidth.
+
 ``--impl reference`` times the CPU oracle (plain C, OpenMP over members) on a
-bounded sample of the same workload.  Under torchrun every rank runs its own
-populations (weak scaling, no collective on the data path); rank 0 prints one
-JSON line.
+bounded sample of the same workload.  Under torchrun (N > 1) the default mode
+is the member split of Section III-D: one population per graph, every rank
+runs the operators and evaluates its contiguous slice of the children, and the
+int64 fitness is all-gathered over NCCL on the context's stream (strong
+scaling); ``--mode independent`` gives every rank its own populations instead
+(weak scaling, no collective on the data path).  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -66,14 +76,15 @@ WORKLOADS = {
                          "k = round(0.05 n), populations from {32,64,128,256,512}, 200 generations each, "
                          "one batched run per step (CUDA-graph replay, persistent fitness kernel, autotuned teams)",
                     graphs=["64 BA instances (synth.batched_instances, seed 0)"]),
-    "surrogate": dict(k=2000, pop=512, lam=2048, screened=256, gens=300,
+    "surrogate": dict(k=2000, pop=512, lam=2048, screens=(512, 256), gens=300,
                       metric="surrogate vs plain GA time-to-target speedup", unit="x",
                       desc="(mu+lambda) GA on BA(n=100000,m=3), k=2000, mu=512, lambda=2048 children per generation, "
                            "tournament 2, pc=0.8, pm=0.02, 300 generations; one step = one GA seed "
-                           "(1000 rank + step) run both ways: plain (all 2048 children exact) vs surrogate-screened "
-                           "(the 256 lowest-scored children exact after 3 warm-up generations; 2 AdamW steps of 512 "
-                           "rows per generation, lr 1e-3, on a 16384-row replay ring; targets z-scored over the "
-                           "ring); value = median over the steps",
+                           "(1000 rank + step) run plain (all 2048 children exact) and surrogate-screened: the 512 "
+                           "lowest-scored children exact (the top 25 %), and beside it the 256 lowest-scored "
+                           "(12.5 %), after 3 warm-up generations; 2 AdamW steps of 512 rows per generation, lr 1e-3, "
+                           "on a 16384-row replay ring; targets z-scored over the ring; value = median over the steps "
+                           "of the 25 % setting's speedup to the plain run's final best PC",
                       graphs=["ba_n100000_m3_seed1 (E=299991)"]),
     "sixdst": dict(k=202, pop=80, gens=1, metric="SixDST fitness evals/s", unit="evals/s",
                    desc="GA generation step under the SixDST objective (N = 6 hops) on ER(n=2018,E=2705), k=202, "
@@ -116,6 +127,39 @@ def bytes_per_eval(n: int, num_edges: int, k: int) -> int:
     """Algorithmic bytes of one exact evaluation: row pointers, each undirected
     edge once, the deletion bitmap, the genes and the int64 result."""
     return 4 * (n + 1) + 4 * num_edges + (n + 7) // 8 + 4 * k + 8
+
+
+_L2_PEAK = {}
+
+
+def l2_read_peak(ctx) -> float:
+    """L2 read bandwidth (GB/s) measured once per process by the library's probe: 16-byte loads
+    over a 64 MB buffer (L2-resident), fastest of 10 passes."""
+    if "v" not in _L2_PEAK:
+        _L2_PEAK["v"] = float(ctx.read_bandwidth(64 << 20, 10))
+    return _L2_PEAK["v"]
+
+
+L2_PEAK_SOURCE = ("measured here: gapa_read_bandwidth, 16-byte loads over a 64 MB buffer (L2-resident), "
+                  "fastest of 10 passes")
+
+
+def memory_roofline(achieved: float, l2_resident: bool, ctx, **extra) -> dict:
+    """Roofline of a memory-bound fitness phase.  Graphs that fit in L2 are graded against the
+    measured L2 read bandwidth, with the HBM-denominated fraction beside it; larger graphs against
+    the measured HBM copy bandwidth."""
+    hbm, hbm_src = measured_peaks()
+    hbm_part = {"peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    if l2_resident:
+        l2 = l2_read_peak(ctx)
+        r = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+             "peak_source": L2_PEAK_SOURCE, "hbm": hbm_part}
+    else:
+        r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+             "peak_source": hbm_part["peak_source"]}
+    r.update(extra)
+    return r
 
 
 def measured_peaks():
@@ -324,15 +368,18 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
-def run_gapa(args):
+class Env:
+    """Process-level state: the process group (or None), world size, ranks and device."""
+
+    def __init__(self, dist, ws, rank, local, dev):
+        self.dist, self.ws, self.rank, self.local, self.dev = dist, ws, rank, local, dev
+
+
+def setup() -> Env:
     import torch
 
-    from paper_2412_20980_gb300 import Context, make_config
     from paper_2412_20980_gb300 import build as b
-    from paper_2412_20980_gb300 import dist as gd
 
-    wl = args.workload
-    w = WORKLOADS[wl]
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -345,14 +392,36 @@ def run_gapa(args):
         b.build()
     if dist is not None:
         dist.barrier()
-    gs = graphs(wl)
-    if wl == "batched":
-        return run_batched(args, gs, dist, ws, rank, local, dev)
-    if wl == "surrogate":
-        return run_surrogate_bench(args, gs, dist, ws, rank, local, dev)
+    return Env(dist, ws, rank, local, dev)
+
+
+def run_workload(args, env: Env):
+    """One workload's JSON line (rank 0) or None (other ranks)."""
+    gs = graphs(args.workload)
+    if args.workload == "batched":
+        return run_batched(args, gs, env.dist, env.ws, env.rank, env.local, env.dev)
+    if args.workload == "surrogate":
+        return run_surrogate_bench(args, gs, env.dist, env.ws, env.rank, env.local, env.dev)
+    return run_gapa(args, env, gs)
+
+
+def run_gapa(args, env: Env, gs):
+    import torch
+
+    from paper_2412_20980_gb300 import Context, make_config
+    from paper_2412_20980_gb300 import dist as gd
+
+    wl = args.workload
+    w = WORKLOADS[wl]
+    dist, ws, rank, local, dev = env.dist, env.ws, env.rank, env.local, env.dev
+    # member split (Section III-D, SM mode): one population per graph, every rank runs the
+    # operators and evaluates its slice of the children, fitness all-gathered; otherwise every
+    # rank evolves its own populations
+    split = args.mode == "split" and ws > 1 and wl in ("throughput", "large")
     k, pop = w["k"], w["pop"]
     pc, pm = (0.5, 0.3) if wl == "sixdst" else (PC, PM)
-    cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=pc, pm=pm, seed=gd.rank_seed(0, rank))
+    seed = 0 if split else gd.rank_seed(0, rank)
+    cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=pc, pm=pm, seed=seed)
     ctxs, state = [], []
     for g in gs:
         c = Context(local)
@@ -372,6 +441,13 @@ def run_gapa(args):
             for c in ctxs:
                 c.run(cfg)  # synchronous: init + gens generations, best set copied to the host
             return len(ctxs) * w["gens"]
+    elif split:
+        def step(t):
+            for c, st in zip(ctxs, state):
+                gd.sharded_generation(c, cfg, t + 1, st[0], st[1], st[2], st[3])
+                st[0], st[2] = st[2], st[0]
+                st[1], st[3] = st[3], st[1]
+            return len(ctxs) * (pop - 1)
     else:
         def step(t):
             for c, st in zip(ctxs, state):
@@ -407,7 +483,10 @@ def run_gapa(args):
     total_ms = gd.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device=dev)
     for c in ctxs:
         c.sync()
-    value = units * ws / (total_ms / 1000.0)
+    # the split evaluates one population per graph on all ranks together; independent populations
+    # add up over the ranks
+    job_units = units if split else units * ws
+    value = job_units / (total_ms / 1000.0)
 
     # --- dominant kernel: the fitness launches inside the timed region ---
     fit_ms = sum(p["fitness_ms"] for p in profs)
@@ -415,6 +494,10 @@ def run_gapa(args):
     fit_calls = sum(p["fitness_calls"] for p in profs)
     fit_evals = sum(p["evals"] for p in profs)
     roofline = None
+    if wl == "small":
+        # whole runs replay CUDA graphs (the profiler sees only the first fitness launch); a
+        # 1000-node graph is launch- and latency-bound, graded by generations per second
+        fit_launches = 0
     if fit_launches and wl == "sixdst":
         # tensor-bound: 3 dense products of n x n 0/1 matrices per evaluation ((A+I)^2, ^4, ^6)
         flop = 3 * 2.0 * float(gs[0].n) ** 3
@@ -433,28 +516,19 @@ def run_gapa(args):
                     "fitness_share_of_step": fit_ms / max(1e-9, total_ms)}
     elif fit_launches:
         beval = bytes_per_eval(gs[0].n, gs[0].num_edges, k)
-        peak, peak_src = measured_peaks()
         # per fitness phase (one per graph and generation): its kernels together, timed on the
         # launching stream around the phase
         avg_launch_s = fit_ms / 1000.0 / fit_calls
         achieved = beval * (fit_evals / fit_calls) / avg_launch_s / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": ncu_traffic(wl),
-                    "kernel": "fitness phase: local_order_kernel + cc_smem_kernel<4> (cut-local TREE, estimates "
-                              "written by the operator kernel) where the graph fits in shared memory, ig_* "
-                              "kernels otherwise",
-                    "kernels_per_phase": fit_launches / fit_calls,
-                    "bytes_per_eval": beval, "evals_per_launch": fit_evals / fit_calls,
-                    "avg_launch_ms": avg_launch_s * 1000,
-                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                    "fitness_share_of_step": fit_ms / max(1e-9, total_ms)}
-        if wl in ("throughput", "small"):
-            # the graph is L2-resident here: the same algorithmic-bytes rate against the L2 read
-            # bandwidth measured now by the library's probe, beside the HBM-denominated figure
-            l2 = ctxs[0].read_bandwidth(64 << 20, 10)
-            roofline["l2"] = {"achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
-                              "peak_source": "measured here: gapa_read_bandwidth, 16-byte loads over a 64 MB "
-                                             "buffer (L2-resident), fastest of 10 passes"}
+        roofline = memory_roofline(
+            achieved, wl in ("throughput", "small"), ctxs[0],
+            traffic=ncu_traffic(wl),
+            kernel="fitness phase: local_order_kernel + cc_smem_kernel<4> (cut-local TREE, estimates written by the "
+                   "operator kernel) where the graph fits in shared memory and n > 2048, cc_smem_kernel (full TREE) "
+                   "for n <= 2048, ig_* kernels where the labels exceed shared memory",
+            kernels_per_phase=fit_launches / fit_calls, bytes_per_eval=beval,
+            evals_per_launch=fit_evals / fit_calls, avg_launch_ms=avg_launch_s * 1000,
+            fitness_share_of_step=fit_ms / max(1e-9, total_ms))
 
     # --- end to end through the C ABI with pinned host buffers ---
     e2e = None
@@ -472,41 +546,58 @@ def run_gapa(args):
         for t in range(e2e_steps):
             flush.fill_(t & 0xFF)
             torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
             t0 = time.perf_counter()
-            for c, h in zip(ctxs, hp):
-                c.generation_host(cfg, 10_000 + t, h[0], h[1], h[2], h[3])
+            for c, h, ts, st in zip(ctxs, hp, pinned, state):
+                if split:  # host population in, split generation, population and fitness out
+                    st[0].copy_(ts[0], non_blocking=True)
+                    st[1].copy_(ts[1], non_blocking=True)
+                    gd.sharded_generation(c, cfg, 10_000 + t, st[0], st[1], st[2], st[3])
+                    ts[2].copy_(st[2], non_blocking=True)
+                    ts[3].copy_(st[3], non_blocking=True)
+                    torch.cuda.current_stream().synchronize()
+                else:
+                    c.generation_host(cfg, 10_000 + t, h[0], h[1], h[2], h[3])
+                ts[0], ts[2] = ts[2], ts[0]
+                ts[1], ts[3] = ts[3], ts[1]
                 h[0], h[2] = h[2], h[0]
                 h[1], h[3] = h[3], h[1]
             el += time.perf_counter() - t0
+        el = gd.max_over_ranks(el, device=dev)
         per = len(gs) * (pop * k * 4 + pop * 8)
-        e2e = {"value": len(gs) * (pop - 1) * e2e_steps * ws / el, "unit": "evals/s", "h2d_bytes_per_step": per,
-               "d2h_bytes_per_step": per, "steps": e2e_steps,
-               "api": "gapa_generation_host (pinned host population and fitness in and out)"}
+        e2e = {"value": len(gs) * (pop - 1) * e2e_steps * (1 if split else ws) / el, "unit": "evals/s",
+               "h2d_bytes_per_step": per, "d2h_bytes_per_step": per, "steps": e2e_steps,
+               "api": ("Context + dist.sharded_generation with pinned host population and fitness copied in and out"
+                       if split else "gapa_generation_host (pinned host population and fitness in and out)")}
 
     if dist is not None:
         dist.barrier()
     if rank != 0:
-        return 0
+        for c in ctxs:
+            c.close()
+        return None
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, gs, args.cpu_seconds)
+    config = workload_config(wl)
+    if split:
+        config["parallelism"] = (f"member split over {ws} ranks (one population per graph; operators on every "
+                                 "rank, fitness by contiguous slices, int64 fitness all-gathered over NCCL)")
     line = {"metric": w["metric"], "value": value, "unit": w["unit"], "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": workload_config(wl)}
+            "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config}
     if wl == "small":
         line["evals_per_s"] = units * (pop - 1) * ws / (total_ms / 1000.0)
     else:
-        line["gens_per_s"] = args.steps * len(gs) * ws / (total_ms / 1000.0)
+        line["gens_per_s"] = args.steps * len(gs) * (1 if split else ws) / (total_ms / 1000.0)
     line.update({"roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                  "gpu_launches": int(sum(p["fitness_launches"] + p["operator_launches"] for p in profs)),
                  "clocks": clocks})
-    print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    return line
 
 
 def run_batched(args, gs, dist, ws, rank, local, dev):
@@ -530,6 +621,9 @@ def run_batched(args, gs, dist, ws, rank, local, dev):
     tune_s = time.perf_counter() - t0
     gens = w["gens"]
     evals_per_run = sum(d["pop"] + (d["pop"] - 1) * gens for d in specs)
+    # algorithmic bytes of every exact evaluation of a run, instance by instance
+    bytes_per_run = sum((d["pop"] + (d["pop"] - 1) * gens) * bytes_per_eval(g.n, g.num_edges, d["k"])
+                        for d, g in zip(specs, gs))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         bt.run(gens)
@@ -538,21 +632,35 @@ def run_batched(args, gs, dist, ws, rank, local, dev):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    wall = 0.0
+    wall, dev_ms = 0.0, 0.0
     for t in range(args.steps):
         flush.fill_(t & 0xFF)
         torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        ev0.record()  # the batch runs on the first context's stream: torch's current stream
         out = bt.run(gens)  # synchronous: results are on the host when it returns
+        ev1.record()
         wall += time.perf_counter() - t0
+        ev1.synchronize()
+        dev_ms += ev0.elapsed_time(ev1)
     clocks = sampler.stop()
-    t_max = torch.tensor([wall], dtype=torch.float64, device=dev)
+    t_max = torch.tensor([wall, dev_ms], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    wall = float(t_max.item())
+    wall, dev_ms = float(t_max[0].item()), float(t_max[1].item())
     value = evals_per_run * args.steps * ws / wall
+    roofline = memory_roofline(
+        bytes_per_run * args.steps / (dev_ms / 1000.0) / 1e9, True, ctxs[0],
+        traffic=None,
+        kernel="whole batched runs (operators + fitness_batched_kernel + record, CUDA-graph replay) on the device: "
+               "a lower bound on the fitness kernel's own rate",
+        bytes_per_run=bytes_per_run, device_ms_per_run=dev_ms / args.steps,
+        basis="sum over instances of (evaluations x 4(n+1) + 4E + ceil(n/8) + 4k + 8) per run / device time of "
+              "the run")
     if rank != 0:
-        return 0
+        bt.close()
+        return None
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -578,15 +686,17 @@ def run_batched(args, gs, dist, ws, rank, local, dev):
             "config": {"workload": w["desc"], "instances": len(specs), "generations": gens,
                        "evals_per_step": evals_per_run, "teams": bt.teams, "autotune_s": tune_s,
                        "sum_n": sum(d["n"] for d in specs), "l2": "flushed between timed steps"},
-            "gens_per_s": len(specs) * gens * args.steps * ws / wall, "roofline": None, "cpu_baseline": cpu,
+            "gens_per_s": len(specs) * gens * args.steps * ws / wall, "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(8 * len(specs) * (gens + 2) + 4 * sum(d["k"] for d in specs)),
                     "note": "gapa_batch_run is host-synchronous: the timed wall time includes the copies of best "
                             "sets, fitness and trajectories"},
+            "gpu_launches": 3 * gens * args.steps,
             "clocks": clocks, "best_fit_first8": out["best_fit"][:8].tolist()}
-    print(json.dumps(line), flush=True)
     bt.close()
-    return 0
+    for c in ctxs:
+        c.close()
+    return line
 
 
 def _spearman(a, b) -> float:
@@ -611,60 +721,9 @@ def _spearman(a, b) -> float:
     return float((ra * rb).sum() / den) if den > 0 else 0.0
 
 
-def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
-    """Time-to-target of the surrogate-screened GA against the plain GA (same seed, same graph)."""
-    import torch
-
-    from paper_2412_20980_gb300 import (FLAG_MU_PLUS_LAMBDA, Context, Surrogate, make_config,
-                                        make_surrogate_config, run_surrogate)
-
-    w = WORKLOADS["surrogate"]
-    g = gs[0]
-    G, lam = w["gens"], w["lam"]
-    ctx = Context(local)
-    ctx.graph_upload(g.row_ptr, g.col)
-
-    def config(gens, seed):
-        return make_config(k=w["k"], pop=w["pop"], gens=gens, tourn=TOURN, pc=PC, pm=PM, seed=seed,
-                           flags=FLAG_MU_PLUS_LAMBDA, lam=lam)
-
-    def scfg(diag_every=0):
-        return make_surrogate_config(screened=w["screened"], warmup=3, train_steps=2, batch=512, ring=16384,
-                                     lr=1e-3, init_scale_emb=0.01, target_mode=0, diag_every=diag_every)
-
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    for t in range(args.warmup):  # short runs of both kinds: module load, allocations, autotuned limits
-        run_surrogate(ctx, config(5, 999), None)
-        sg = Surrogate(ctx, scfg(), seed=1000 + t)
-        run_surrogate(ctx, config(5, 999), sg)
-        sg.close()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    if dist is not None:
-        dist.barrier()
-    runs = []
-    for t in range(args.steps):  # step t: GA seed 1000 * rank + t for both arms, surrogate weights seed t
-        cfg, cfg_long = config(G, 1000 * rank + t), config(2 * G, 1000 * rank + t)
-        flush.fill_(t & 0xFF)
-        torch.cuda.synchronize()
-        ctx.profile_begin()  # CUDA events around every launch: the phase split and the launch count
-        t0 = time.perf_counter()
-        plain = run_surrogate(ctx, cfg, None)
-        plain_wall = time.perf_counter() - t0
-        plain["prof"] = ctx.profile_end()
-        flush.fill_((t + 1) & 0xFF)
-        sg = Surrogate(ctx, scfg(), seed=t)
-        torch.cuda.synchronize()
-        ctx.profile_begin()
-        t0 = time.perf_counter()
-        sur = run_surrogate(ctx, cfg_long, sg)
-        sur_wall = time.perf_counter() - t0
-        sur["prof"] = ctx.profile_end()
-        sg.close()
-        runs.append((plain, plain_wall, sur, sur_wall))
-    clocks = sampler.stop()
-    # per step: the plain run's device time to its final best, the screened run's time to reach it
+def time_to_target(runs, G: int, lam: int):
+    """Per GA seed: the plain run's device time to its final best PC, and the screened run's
+    device time to reach that same value (and 1.01 x it); returns (speedups, rows)."""
     speedups, rows = [], []
     for plain, plain_wall, sur, sur_wall in runs:
         final = int(plain["traj"][-1])
@@ -688,7 +747,67 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
                      "plain_exact_evals_per_s": float(plain["exact_evals"].sum() / (plain["gen_ms"][-1] / 1e3)),
                      "surrogate_exact_evals_per_s": float(sur["exact_evals"].sum() / (sur["gen_ms"][-1] / 1e3)),
                      "surrogate_children_per_s": float(lam * 2 * G / (sur["gen_ms"][-1] / 1e3))})
-    # median over the seeds; the worst rank decides (max-over-ranks time, min speedup)
+    return speedups, rows
+
+
+def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
+    """Time-to-target of the surrogate-screened GA against the plain GA (same seed, same graph)."""
+    import torch
+
+    from paper_2412_20980_gb300 import (FLAG_MU_PLUS_LAMBDA, Context, Surrogate, make_config,
+                                        make_surrogate_config, run_surrogate)
+
+    w = WORKLOADS["surrogate"]
+    g = gs[0]
+    G, lam = w["gens"], w["lam"]
+    ctx = Context(local)
+    ctx.graph_upload(g.row_ptr, g.col)
+
+    def config(gens, seed):
+        return make_config(k=w["k"], pop=w["pop"], gens=gens, tourn=TOURN, pc=PC, pm=PM, seed=seed,
+                           flags=FLAG_MU_PLUS_LAMBDA, lam=lam)
+
+    screens = list(w["screens"])
+
+    def scfg(diag_every=0, screened=None):
+        return make_surrogate_config(screened=screened or screens[0], warmup=3, train_steps=2, batch=512,
+                                     ring=16384, lr=1e-3, init_scale_emb=0.01, target_mode=0, diag_every=diag_every)
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for t in range(args.warmup):  # short runs of both kinds: module load, allocations, autotuned limits
+        run_surrogate(ctx, config(5, 999), None)
+        sg = Surrogate(ctx, scfg(), seed=1000 + t)
+        run_surrogate(ctx, config(5, 999), sg)
+        sg.close()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    runs = {sc: [] for sc in screens}
+    for t in range(args.steps):  # step t: GA seed 1000 * rank + t for both arms, surrogate weights seed t
+        cfg, cfg_long = config(G, 1000 * rank + t), config(2 * G, 1000 * rank + t)
+        flush.fill_(t & 0xFF)
+        torch.cuda.synchronize()
+        ctx.profile_begin()  # CUDA events around every launch: the phase split and the launch count
+        t0 = time.perf_counter()
+        plain = run_surrogate(ctx, cfg, None)
+        plain_wall = time.perf_counter() - t0
+        plain["prof"] = ctx.profile_end()
+        for sc in screens:
+            flush.fill_((t + 1) & 0xFF)
+            sg = Surrogate(ctx, scfg(screened=sc), seed=t)
+            torch.cuda.synchronize()
+            ctx.profile_begin()
+            t0 = time.perf_counter()
+            sur = run_surrogate(ctx, cfg_long, sg)
+            sur_wall = time.perf_counter() - t0
+            sur["prof"] = ctx.profile_end()
+            sg.close()
+            runs[sc].append((plain, plain_wall, sur, sur_wall))
+    clocks = sampler.stop()
+    by_screen = {sc: time_to_target(runs[sc], G, lam) for sc in screens}
+    speedups, rows = by_screen[screens[0]]
     value = float(np.median(speedups))
     tot_ms = sum(r["plain_run_ms"] + r["surrogate_run_ms"] for r in rows)
     t_max = torch.tensor([value, tot_ms], dtype=torch.float64, device=dev)
@@ -697,6 +816,8 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
         dist.all_reduce(t_min, op=dist.ReduceOp.MIN)
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
         value, tot_ms = float(t_min[0].item()), float(t_max[1].item())
+    all_runs = runs
+    runs = runs[screens[0]]
     # untimed: a diagnostic run (surrogate quality)
     prof = runs[-1][2]["prof"]
     sg = Surrogate(ctx, scfg(diag_every=10), seed=0)
@@ -713,21 +834,25 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
         dist.barrier()
     if rank != 0:
         ctx.close()
-        return 0
+        return None
     beval = bytes_per_eval(g.n, g.num_edges, w["k"])
-    peak, peak_src = measured_peaks()
     roofline = None
     if prof["fitness_calls"]:
+        # the graph (1.2 M arcs) is L2-resident; labels live in global memory (interleaved groups)
         avg_launch_s = prof["fitness_ms"] / 1e3 / prof["fitness_calls"]
         achieved = beval * prof["evals"] / prof["fitness_calls"] / avg_launch_s / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": ncu_traffic("surrogate"), "kernel": "fitness phase (screened children)",
-                    "kernels_per_phase": prof["fitness_launches"] / prof["fitness_calls"],
-                    "bytes_per_eval": beval, "evals_per_launch": prof["evals"] / prof["fitness_calls"],
-                    "avg_launch_ms": avg_launch_s * 1e3, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+        roofline = memory_roofline(achieved, True, ctx, traffic=ncu_traffic("surrogate"),
+                                   kernel="fitness phase (screened children; interleaved global labels)",
+                                   kernels_per_phase=prof["fitness_launches"] / prof["fitness_calls"],
+                                   bytes_per_eval=beval, evals_per_launch=prof["evals"] / prof["fitness_calls"],
+                                   avg_launch_ms=avg_launch_s * 1e3)
     run_ms = prof["fitness_ms"] + prof["operators_ms"] + prof["surrogate_ms"]
-    launches = sum(int(r["prof"][a] + r["prof"][b] + r["prof"][c]) for p_, _, s_, _ in runs for r in (p_, s_)
-                   for a, b, c in [("fitness_launches", "operator_launches", "surrogate_launches")])
+
+    def launches_of(r):
+        return int(r["prof"]["fitness_launches"] + r["prof"]["operator_launches"] + r["prof"]["surrogate_launches"])
+
+    launches = (sum(launches_of(p_) for p_, _, _, _ in runs) +
+                sum(launches_of(s_) for sc in screens for _, _, s_, _ in all_runs[sc]))
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -755,10 +880,19 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32 fitness; bf16/fp32 surrogate",
             "data": "synthetic",
             "config": {"workload": w["desc"], "graphs": w["graphs"], "k": w["k"], "mu": w["pop"], "lambda": lam,
-                       "screened": w["screened"], "generations": G,
+                       "screened": screens[0], "screened_fraction": screens[0] / lam, "generations": G,
                        "l2": "flushed before every timed run", "parallelism": "dp (independent runs per rank)",
                        "timing": "device time from CUDA events recorded by gapa_run_surrogate on its stream"},
             "runs": rows,
+            "by_screen": {str(sc): {"screened_fraction": sc / lam,
+                                    "speedup_to_plain_final_median": float(np.median(by_screen[sc][0])),
+                                    "speedups": by_screen[sc][0],
+                                    "speedup_to_1.01x": [r["speedup_to_1.01x"] for r in by_screen[sc][1]],
+                                    "surrogate_generation_at_plain_final":
+                                        [r["surrogate_generation_at_plain_final"] for r in by_screen[sc][1]],
+                                    "surrogate_generation_at_1.01x":
+                                        [r["surrogate_generation_at_1.01x"] for r in by_screen[sc][1]]}
+                          for sc in screens},
             "surrogate_quality": {"spearman_mean": float(np.mean(rhos)) if rhos else None,
                                   "spearman_min": float(np.min(rhos)) if rhos else None,
                                   "median_relative_error_mean": float(np.mean(relerr)) if relerr else None,
@@ -782,9 +916,33 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
                             "fraction"},
             "gpu_launches": launches,
             "clocks": clocks}
-    print(json.dumps(line), flush=True)
     ctx.close()
-    return 0
+    return line
+
+
+# workloads timed beside the headline in the default line: (steps, warm-up, CPU-baseline seconds)
+EXTRA = {"small": (20, 3, 3.0), "large": (5, 3, 3.0), "batched": (3, 3, 3.0), "sixdst": (10, 3, 3.0),
+         "surrogate": (2, 1, 3.0)}
+EXTRA_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "gens_per_s", "evals_per_s", "roofline",
+              "cpu_baseline", "e2e", "gpu_launches", "clocks", "by_screen", "surrogate_quality", "phase_split_ms")
+
+
+def run_extra(args, env: Env) -> dict:
+    """The other workloads, each timed in this same run with its own short step count."""
+    out = {}
+    for wl, (steps, warmup, cpu_s) in EXTRA.items():
+        sub = argparse.Namespace(**vars(args))
+        sub.workload, sub.steps, sub.warmup, sub.cpu_seconds = wl, steps, warmup, cpu_s
+        t0 = time.perf_counter()
+        line = run_workload(sub, env)
+        if line is None:
+            continue
+        d = {key: line[key] for key in EXTRA_KEYS if key in line}
+        d["config"] = line["config"].get("workload")
+        d["bench_wall_s"] = time.perf_counter() - t0
+        out[wl] = d
+        log(f"{wl}: {line['value']:.4g} {line['unit']} ({d['bench_wall_s']:.1f} s)")
+    return out
 
 
 def main():
@@ -794,16 +952,30 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gapa", "reference"], default="gapa")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="throughput")
+    ap.add_argument("--mode", choices=["split", "independent"], default="split",
+                    help="with several ranks: split one population by members (default) or evolve independent "
+                         "populations per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads that the default line carries under 'workloads'")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gapa":
         log("warm-up raised to 3 steps")
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    return run_gapa(args)
+    env = setup()
+    line = run_workload(args, env)
+    if line is not None and args.workload == "throughput" and env.ws == 1 and not args.no_extra:
+        line["workloads"] = run_extra(args, env)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if env.dist is not None:
+        env.dist.barrier()
+        env.dist.destroy_process_group()
+    return 0
 
 
 if __name__ == "__main__":

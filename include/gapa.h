@@ -396,27 +396,34 @@ typedef struct gapa_profile {
 int gapa_profile_begin(gapa_ctx* ctx);
 int gapa_profile_end(gapa_ctx* ctx, gapa_profile* out);
 
-/* Fitness without any allocation.  The paper has no counterpart: this entry
- * point exists for callers that must not allocate device memory - code that
- * runs while a framework captures the stream into a CUDA graph (cudaMalloc is
- * not allowed there), latency-critical loops that cannot afford cudaMalloc's
- * implicit synchronisation, and processes whose device memory belongs to
- * another allocator under a fixed budget.  It needs no context: the graph
- * comes as a device edge list edges_dev[num_edges][2] (int32 node ids; each
- * undirected edge at least once, either orientation; self-loops ignored), the
- * population pop_dev[s][k] and the output fit_dev[s] are the caller's device
- * arrays on `device`, and work runs on `cuda_stream` (a cudaStream_t, NULL =
- * legacy default stream).  fit_dev[i] is the same pairwise connectivity as
- * gapa_fitness().  Label scratch is a static array of GAPA_NOALLOC_MAX_LABELS
- * int32 (32 MiB) inside the library, held by every GPU that loads it until
- * the process exits; n above that limit is rejected (GAPA_ERR_INVALID_ARG),
- * and members are processed in waves of GAPA_NOALLOC_MAX_LABELS / n.  The
- * call calls no cudaMalloc/cudaFree and returns after the stream is
- * synchronised; an endpoint or gene outside [0, n) gives GAPA_ERR_DEVICE.
- * The first call on a device looks up the scratch's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the one scratch array, so calls that overlap on the GPU
- * (other streams or threads) race and must be serialised by the caller. */
+/* Fitness without any allocation.  The paper has no counterpart.  Some
+ * callers cannot allocate device memory: a plugin or library embedded in a
+ * host program whose device memory belongs to that program's own allocator
+ * under a fixed budget, and latency-critical loops that cannot take the
+ * implicit device-wide synchronisation of cudaMalloc/cudaFree.  This entry
+ * point serves them.  It needs no context: the graph comes as a device edge
+ * list edges_dev[num_edges][2] (int32 node ids; each undirected edge at least
+ * once, either orientation; self-loops ignored), the population pop_dev[s][k]
+ * and the output fit_dev[s] are the caller's device arrays on `device`, and
+ * work runs on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * fit_dev[i] is the same pairwise connectivity as gapa_fitness().
+ * Scratch: the node labels live in a static device array of
+ * GAPA_NOALLOC_MAX_LABELS int32 (32 MiB) inside the library, which every GPU
+ * that loads the library holds until the process exits; n above that limit is
+ * rejected with GAPA_ERR_INVALID_ARG, and members run in waves of
+ * GAPA_NOALLOC_MAX_LABELS / n.  A status word beside it is cleared at the
+ * start of every call.  The call allocates nothing (no cudaMalloc, cudaFree
+ * or allocating library routine) and BLOCKS: it copies the status word to
+ * the host and synchronises `cuda_stream` before returning; an endpoint or a
+ * gene outside [0, n) then gives GAPA_ERR_DEVICE, and the next call starts
+ * clean.  Set-up: the first call on a device, with that device current, looks
+ * up the scratch's device address (cudaGetSymbolAddress) and caches it for
+ * the life of the process; make that first call before any stream capture,
+ * and do not call again after cudaDeviceReset on that device (unsupported:
+ * the cached address may be stale).  All calls share the one scratch array,
+ * which keeps the last call's labels; calls that overlap on the GPU (other
+ * streams, threads or processes sharing the library) race on it and must be
+ * serialised by the caller. */
 #define GAPA_NOALLOC_MAX_LABELS (8 * 1024 * 1024)
 int gapa_fitness_noalloc(int device, void* cuda_stream, int32_t n, int32_t num_edges, const int32_t* edges_dev,
                          const int32_t* pop_dev, int32_t s, int32_t k, int64_t* fit_dev);

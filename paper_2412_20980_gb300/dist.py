@@ -53,15 +53,23 @@ def max_over_ranks(value: float, group=None, device=None) -> float:
     return float(t.item())
 
 
+def _group_active(group) -> bool:
+    import torch.distributed as dist
+
+    return dist.is_available() and dist.is_initialized()
+
+
 def gather_slices(full, lo: int, hi: int, group=None):
     """Every rank owns full[lo:hi] of the 1-D tensor `full` (bounds from shard_bounds);
-    afterwards every rank holds all slices."""
+    afterwards every rank holds all slices.  With NCCL and device tensors the copies and the
+    collective are ordered on torch's current stream (no host synchronisation).  Without a
+    process group this is a no-op; with one, the collective runs even for a single rank."""
     import torch
     import torch.distributed as dist
 
-    world, _ = _world(group)
-    if world == 1:
+    if not _group_active(group):
         return full
+    world, _ = _world(group)
     total = full.numel()
     width = -(-total // world)
     mine = torch.zeros(width, dtype=full.dtype, device=full.device)
@@ -77,14 +85,28 @@ def gather_slices(full, lo: int, hi: int, group=None):
 def sharded_generation(ctx, cfg, g: int, pop_in, fit_in, pop_out, fit_out, group=None):
     """One generation of a population split by members: the operators on every rank
     (identical children), the fitness of this rank's slice of the s-1 children, then an
-    all-gather of the int64 fitness.  `ctx` needs offspring() and fitness() (Context)."""
+    all-gather of the int64 fitness.  `ctx` needs offspring() and fitness() (Context).
+
+    Everything is ordered on the context's stream: the kernels run there, and the all-gather
+    is issued with that stream as torch's current stream, so NCCL waits for the slice's fitness
+    and the next generation's kernels wait for the gathered values without any host
+    synchronisation.  A context without a CUDA stream (a host stand-in) is synchronised
+    instead."""
     world, rank = _world(group)
+    if not _group_active(group):  # one process: the plain generation
+        return ctx.generation(cfg, g, pop_in, fit_in, pop_out, fit_out)
     ctx.offspring(cfg, g, pop_in, fit_in, pop_out, fit_out)
     children = cfg.pop - 1
     lo, hi = shard_bounds(children, world, rank)
     if hi > lo:
         ctx.fitness(pop_out[1 + lo:1 + hi], out=fit_out[1 + lo:1 + hi])
-    if world > 1:
+    stream = getattr(ctx, "stream", None)
+    if stream is None:
         ctx.sync()
         gather_slices(fit_out[1:], lo, hi, group)
+    else:
+        import torch
+
+        with torch.cuda.stream(stream):
+            gather_slices(fit_out[1:], lo, hi, group)
     return pop_out, fit_out

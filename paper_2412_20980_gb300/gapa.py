@@ -248,9 +248,15 @@ def fitness_noalloc(edges, pop, n: int, out, stream=None):
     dev = pop.device.index
     if stream is None:
         stream = torch.cuda.current_stream(dev)
+    if stream.device.index != dev:
+        raise ValueError(f"stream is on cuda:{stream.device.index}, pop on cuda:{dev}")
     if edges.dim() != 2 or edges.shape[1] != 2:
         raise ValueError("edges must be [E, 2]")
+    if pop.dim() != 2:
+        raise ValueError("pop must be [s, k]")
     s, k = pop.shape
+    if out.dim() != 1 or out.shape[0] < s:
+        raise ValueError(f"out must be a 1-D tensor of at least s = {s} elements")
     _check(load().gapa_fitness_noalloc(dev, ctypes.c_void_p(stream.cuda_stream), n, edges.shape[0],
                                        _dev_ptr(edges, torch.int32, "edges", dev),
                                        _dev_ptr(pop, torch.int32, "pop", dev), s, k,
@@ -293,6 +299,11 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+    @property
+    def stream(self):
+        """The torch stream the context borrows (all its work is ordered on it)."""
+        return self._stream
 
     def set_stream(self, stream):
         self._stream = stream
