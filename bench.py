@@ -395,6 +395,15 @@ def setup() -> Env:
     return Env(dist, ws, rank, local, dev)
 
 
+def set_kernel(ctx, args):
+    from paper_2412_20980_gb300 import gapa as gp
+
+    choice = getattr(args, "fitness_kernel", "auto")
+    if choice != "auto":
+        ctx.set_fitness_kernel({"tree_local": gp.FITNESS_TREE_LOCAL, "tree": gp.FITNESS_TREE,
+                                "piece": gp.FITNESS_PIECE}[choice])
+
+
 def run_workload(args, env: Env):
     """One workload's JSON line (rank 0) or None (other ranks)."""
     gs = graphs(args.workload)
@@ -425,6 +434,7 @@ def run_gapa(args, env: Env, gs):
     ctxs, state = [], []
     for g in gs:
         c = Context(local)
+        set_kernel(c, args)
         c.graph_upload(g.row_ptr, g.col)
         if wl == "sixdst":
             from paper_2412_20980_gb300.gapa import OBJECTIVE_SIXDST_PC
@@ -955,6 +965,8 @@ def main():
     ap.add_argument("--mode", choices=["split", "independent"], default="split",
                     help="with several ranks: split one population by members (default) or evolve independent "
                          "populations per rank")
+    ap.add_argument("--fitness-kernel", choices=["auto", "tree_local", "tree", "piece"], default="auto",
+                    help="fitness kernel of the contexts (default: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")

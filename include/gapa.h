@@ -314,6 +314,16 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
 #define GAPA_FITNESS_TREE_JOIN 4
 #define GAPA_FITNESS_TREE_SCAN 5
 #define GAPA_FITNESS_TREE_LOCAL 6
+/* PIECE (selectable only; AUTO never picks it): the forest-piece kernel,
+ * four members per SM with no per-node labels.  Deleting a member's nodes cuts the upload's spanning forest into
+ * pieces rooted at the live children of deleted nodes (and at the live roots
+ * of trees holding deleted nodes); piece sizes follow from subtree sizes by
+ * subtraction, every such child re-picks a live lower-numbered neighbour
+ * (a union of two pieces), and only the nodes outside the largest resulting
+ * class scan their arcs.  Members estimated to list over a quarter of the
+ * nodes, or beyond the kernel's shared-memory capacities, run the TREE_LOCAL
+ * kernel instead.  Same graphs as TREE_LOCAL; PC and MCN objectives. */
+#define GAPA_FITNESS_PIECE 7
 int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
 /* Fitness objective of the context (all minimised; the end of Section III-C

@@ -40,9 +40,15 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.roots);
     cudaFree(g.cut);
     cudaFree(g.order);
+    cudaFree(g.sz);
+    cudaFree(g.pre);
+    cudaFree(g.at);
+    cudaFree(g.crep);
+    cudaFree(g.nroot);
+    cudaFree(g.csize);
     DeviceForest& a = g.alt;
     void* alt_ptrs[] = {a.perm, a.tparent, a.palt, a.lo_ptr, a.lo_col, a.kids, a.roots, a.cut, a.fptr, a.fcol16,
-                        a.nontree};
+                        a.nontree, a.sz, a.pre, a.at, a.crep, a.nroot, a.csize};
     for (void* q : alt_ptrs) cudaFree(q);
     cudaFree(g.nontree);
     cudaFree(g.fptr);
@@ -129,6 +135,81 @@ BfsForest bfs_forest(int32_t n, const std::vector<int32_t>& rp, const std::vecto
     return f;
 }
 
+// Subtree sizes, preorder positions and the node at each position of a forest
+// whose parents precede their children (roots: parent = itself), children
+// visited in ascending order and trees by ascending root, so that a subtree
+// is the interval [pre, pre + sz).  A forest may hold several trees of one
+// component of G (a root need not be a component's only root: a node with no
+// lower-numbered neighbour starts a tree even when later nodes join it to
+// others), so the components come from the lower-neighbour lists: crep = the
+// smallest root of each node's component, nroot = the next root of the same
+// component (ascending; -1 after the last), csize = the component's size at
+// its representative, and tree_pc = the sum over the components of
+// C(size, 2).
+struct ForestIntervals {
+    std::vector<int32_t> sz, pre, crep, nroot, csize;
+    std::vector<uint16_t> at;
+    long long tree_pc = 0;
+};
+
+ForestIntervals forest_intervals(const std::vector<int32_t>& tparent, const std::vector<int32_t>& lo_ptr,
+                                 const std::vector<int32_t>& lo_col) {
+    const int32_t n = (int32_t)tparent.size();
+    ForestIntervals fi;
+    fi.sz.assign((size_t)n, 1);
+    fi.pre.assign((size_t)n, 0);
+    fi.crep.assign((size_t)n, 0);
+    fi.nroot.assign((size_t)n, -1);
+    fi.csize.assign((size_t)n, 0);
+    fi.at.assign((size_t)n, 0);
+    for (int32_t v = n - 1; v >= 0; --v)
+        if (tparent[v] != v) fi.sz[tparent[v]] += fi.sz[v];
+    std::vector<int32_t> next((size_t)n, 0), root((size_t)n, 0);  // next free position below each node
+    int32_t cursor = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        const int32_t p = tparent[v];
+        if (p == v) {
+            fi.pre[v] = cursor;
+            cursor += fi.sz[v];
+            root[v] = v;
+        } else {
+            fi.pre[v] = next[p];
+            next[p] += fi.sz[v];
+            root[v] = root[p];
+        }
+        next[v] = fi.pre[v] + 1;
+        fi.at[fi.pre[v]] = (uint16_t)v;
+    }
+    // components: union of the trees joined by an edge (every edge is in one lower-neighbour list)
+    std::vector<int32_t> uf((size_t)n);
+    for (int32_t v = 0; v < n; ++v) uf[v] = v;
+    auto find = [&](int32_t x) {
+        while (uf[x] != x) {
+            uf[x] = uf[uf[x]];
+            x = uf[x];
+        }
+        return x;
+    };
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t e = lo_ptr[v]; e < lo_ptr[v + 1]; ++e) {
+            int32_t a = find(root[v]), b = find(root[lo_col[e]]);
+            if (a != b) uf[std::max(a, b)] = std::min(a, b);  // the smallest root represents
+        }
+    std::vector<int32_t> last((size_t)n, -1);
+    for (int32_t v = 0; v < n; ++v) {
+        const int32_t c = find(root[v]);
+        fi.crep[v] = c;
+        fi.csize[c] += 1;
+        if (tparent[v] == v) {  // roots in ascending order: link v after the component's last root
+            if (last[c] >= 0) fi.nroot[last[c]] = v;
+            last[c] = v;
+        }
+    }
+    for (int32_t v = 0; v < n; ++v)
+        if (fi.crep[v] == v) fi.tree_pc += (long long)fi.csize[v] * (fi.csize[v] - 1) / 2;
+    return fi;
+}
+
 // The forest of a numbering `perm` (host side, n <= 65536): every node's
 // parent is its lowest-numbered neighbour when that one is lower (a root
 // otherwise), so parents precede children.  `ok` is false when some node's
@@ -138,6 +219,7 @@ struct ForestHost {
     std::vector<int4> kids;
     std::vector<int2> palt;
     std::vector<uint32_t> nontree;
+    ForestIntervals iv;
     bool ok = true;
 };
 
@@ -205,6 +287,7 @@ ForestHost forest_host(int32_t n, const std::vector<int32_t>& rp, const std::vec
     std::vector<int32_t> by_id((size_t)n);
     for (int32_t v = 0; v < n; ++v) by_id[v] = f.cut[perm[v]];
     f.cut.swap(by_id);
+    f.iv = forest_intervals(f.tparent, f.lo_ptr, f.lo_col);
     return f;
 }
 
@@ -269,7 +352,12 @@ int upload_forest(const ForestHost& f, int32_t n, DeviceForest& d) {
               up((void**)&d.cut, f.cut.data(), 4 * (size_t)n) &&
               up((void**)&d.fptr, f.fptr.data(), 4 * ((size_t)n + 1)) &&
               up((void**)&d.fcol16, f16.data(), 2 * f16.size()) &&
-              up((void**)&d.nontree, f.nontree.data(), 4 * f.nontree.size());
+              up((void**)&d.nontree, f.nontree.data(), 4 * f.nontree.size()) &&
+              up((void**)&d.sz, f.iv.sz.data(), 4 * (size_t)n) && up((void**)&d.pre, f.iv.pre.data(), 4 * (size_t)n) &&
+              up((void**)&d.at, f.iv.at.data(), 2 * (size_t)n) &&
+              up((void**)&d.crep, f.iv.crep.data(), 4 * (size_t)n) &&
+              up((void**)&d.nroot, f.iv.nroot.data(), 4 * (size_t)n) &&
+              up((void**)&d.csize, f.iv.csize.data(), 4 * (size_t)n);
     d.num_roots = (int)f.roots.size();
     d.num_nontree = (int)f.nontree.size();
     if (!ok) {
@@ -729,7 +817,7 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
                 if (bf.tparent[v] != v && bf.lo_ptr[v + 1] - bf.lo_ptr[v] == 1) cut[bf.tparent[v]] += below[v];
             if (cudaMalloc(&g.kids, sizeof(int4) * std::max<size_t>((size_t)n, 1)) != cudaSuccess ||
                 cudaMalloc(&g.cut, sizeof(int32_t) * std::max<size_t>((size_t)n, 1)) != cudaSuccess ||
-                cudaMalloc(&g.order, sizeof(int32_t) * 4 * (size_t)kOrderCap) != cudaSuccess ||
+                cudaMalloc(&g.order, sizeof(int32_t) * (5 * (size_t)kOrderCap + 16)) != cudaSuccess ||
                 cudaMalloc(&g.roots, sizeof(int32_t) * std::max<size_t>(bf.roots.size(), 1)) != cudaSuccess) {
                 free_graph(g);
                 cudaGetLastError();
@@ -744,6 +832,24 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
                                      cudaMemcpyHostToDevice));
             g.num_roots = (int)bf.roots.size();
             g.local_list_bytes = (int)list_bytes;
+            {
+                // subtree intervals of the forest-piece kernel
+                const ForestIntervals fi = forest_intervals(bf.tparent, bf.lo_ptr, bf.lo_col);
+                auto up = [](void** dst, const void* src, size_t bytes) {
+                    return cudaMalloc(dst, std::max<size_t>(bytes, 16)) == cudaSuccess &&
+                           cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+                };
+                if (!(up((void**)&g.sz, fi.sz.data(), 4 * (size_t)n) && up((void**)&g.pre, fi.pre.data(), 4 * (size_t)n) &&
+                      up((void**)&g.at, fi.at.data(), 2 * (size_t)n) &&
+                      up((void**)&g.crep, fi.crep.data(), 4 * (size_t)n) &&
+                      up((void**)&g.nroot, fi.nroot.data(), 4 * (size_t)n) &&
+                      up((void**)&g.csize, fi.csize.data(), 4 * (size_t)n))) {
+                    free_graph(g);
+                    cudaGetLastError();
+                    return gapa_fail(GAPA_ERR_OOM, "subtree intervals of %d nodes", n);
+                }
+                g.tree_pc = fi.tree_pc;
+            }
             // the second forest, numbered with the top hubs last (about 0.5 % of the nodes, 8 to 256):
             // members that delete hubs cut it far less
             const int hubs = std::max(8, std::min(256, n / 200));
@@ -1002,7 +1108,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
 
 int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
-    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_TREE_LOCAL)
+    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_PIECE)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown fitness kernel %d", variant);
     c->fitness_variant = variant;
     return GAPA_OK;

@@ -15,6 +15,7 @@
 
 #include "gapa_internal.cuh"
 #include "tree16.cuh"
+#include "piece.cuh"
 
 namespace {
 
@@ -484,6 +485,111 @@ __global__ void __launch_bounds__(1024) cc_global_kernel(GraphArgs g, const int*
     member_pc<kVar>(labels + (size_t)blockIdx.x * g.n, g, pop + (size_t)i * k, k, i, &fit[i], status, red, &sh_root);
 }
 
+// Forest-piece kernel: a persistent CTA of kPieceTeams teams of kPieceThreads threads per SM.
+// The CTA serves one forest: it copies that forest's parents (16-bit) into shared memory, then
+// every team takes members of that forest from the forest's queue (costliest first) and
+// evaluates them (piece.cuh).  Members that exceed the teams' capacities are appended to `defer`
+// for cc_list_kernel.  ctl: [0] deferred count, [1] [2] members per forest, [3] [4] queue heads.
+constexpr int kPieceThreads = 256;
+constexpr int kPieceTeams = 4;
+
+struct PieceArgs {
+    gapa_dev::PieceGraph g1, g2;
+    gapa_dev::PieceLayout L;
+};
+
+__global__ void __launch_bounds__(kPieceThreads* kPieceTeams, 1)
+    cc_piece_kernel(PieceArgs a, const int* __restrict__ pop, int k, long long* __restrict__ fit, int* status,
+                    const int* __restrict__ list, int* __restrict__ defer, int* ctl) {
+    extern __shared__ __align__(16) unsigned char smem_piece[];
+    __shared__ int team_next[kPieceTeams];
+    const int c1 = __ldcg(&ctl[1]), c2 = __ldcg(&ctl[2]), total = c1 + c2;
+    // the first g1 CTAs serve the first forest (at least one CTA per forest with members)
+    int g1 = (int)(((long long)gridDim.x * c1 + total / 2) / (total > 0 ? total : 1));
+    if (c1 > 0 && g1 < 1) g1 = 1;
+    if (c2 > 0 && g1 > (int)gridDim.x - 1) g1 = (int)gridDim.x - 1;
+    if (c2 == 0) g1 = gridDim.x;
+    const int f = (int)blockIdx.x < g1 ? 0 : 1;
+    const gapa_dev::PieceGraph& g = f ? a.g2 : a.g1;
+    const int count = f ? c2 : c1;
+    const int* flist = list + (f ? c1 : 0);
+    unsigned short* tp = reinterpret_cast<unsigned short*>(smem_piece);
+    for (int v = threadIdx.x; v < g.n; v += blockDim.x) tp[v] = (unsigned short)__ldg(&g.tparent[v]);
+    __syncthreads();
+    const int team = threadIdx.x / kPieceThreads;
+    const gapa_dev::Team tm{(int)threadIdx.x - team * kPieceThreads, kPieceThreads, 1 + team};
+    unsigned char* tsm = smem_piece + gapa_dev::piece_parents_bytes(g.n) + (size_t)team * a.L.bytes;
+    while (true) {
+        if (tm.tid == 0) team_next[team] = atomicAdd(&ctl[3 + f], 1);
+        tm.sync();
+        const int idx = team_next[team];
+        tm.sync();
+        if (idx >= count) break;
+        const int e = __ldg(&flist[idx]);
+        const int m = e & 0x3FFFFFFF;
+        const bool done = gapa_dev::piece_member(tm, g, a.L, tsm, tp, pop + (size_t)m * k, k, &fit[m], status);
+        if (!done && tm.tid == 0) defer[atomicAdd(&ctl[0], 1)] = e;
+    }
+}
+
+// Members by forest (the one with the lower estimate; the first forest on ties), and within each
+// forest by decreasing bit length of the estimate (a counting sort over 2 x 33 classes in one CTA;
+// the order within a class is arbitrary); est_min[m] = the lower estimate.  Also resets the
+// forest-piece kernel's counters (see cc_piece_kernel).
+__global__ void __launch_bounds__(1024) piece_order_kernel(const unsigned* __restrict__ est,
+                                                           const unsigned* __restrict__ est2, int s,
+                                                           int* __restrict__ order, unsigned* __restrict__ est_min,
+                                                           int* __restrict__ ctl) {
+    __shared__ int cnt[66];
+    if (threadIdx.x < 66) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < s; m += blockDim.x) {
+        const unsigned a = est[m], b = est2[m];
+        const bool second = b < a;
+        const unsigned e = second ? b : a;
+        est_min[m] = e;
+        atomicAdd(&cnt[33 * second + __clz(e)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < 66; ++c) {
+            const int x = cnt[c];
+            cnt[c] = acc;
+            acc += x;
+            if (c == 32) ctl[1] = acc;
+        }
+        ctl[2] = acc - ctl[1];
+        ctl[0] = 0;
+        ctl[3] = 0;
+        ctl[4] = 0;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < s; m += blockDim.x) {
+        const unsigned a = est[m], b = est2[m];
+        const bool second = b < a;
+        order[atomicAdd(&cnt[33 * second + __clz(second ? b : a)], 1)] = m | (second ? (1 << 30) : 0);
+    }
+}
+
+// The deferred members, with the cut-local TREE kernel (which runs the full pipeline for members
+// estimated to list over a quarter of the nodes): CTAs stride over list[0 .. *count).
+template <int kVar>
+__global__ void __launch_bounds__(1024) cc_list_kernel(GraphArgs g, const int* __restrict__ pop, int k,
+                                                       long long* __restrict__ fit, int* status,
+                                                       const int* __restrict__ list, const int* count) {
+    extern __shared__ int smem_lab[];
+    __shared__ long long red[32];
+    __shared__ int sh_root;
+    const int cnt = *count;
+    for (int x = blockIdx.x; x < cnt; x += gridDim.x) {
+        const int e = list[x];
+        const int i = e & 0x3FFFFFFF;
+        member_pc<kVar>(smem_lab, g, pop + (size_t)i * k, k, i, &fit[i], status, red, &sh_root, (e >> 30) & 1);
+        __syncthreads();  // the shared memory is reused by the next member
+    }
+}
+
 template <int kVar>
 int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, int k, long long* f,
                    cudaStream_t st, int* kernels = nullptr, const unsigned* est_in = nullptr) {
@@ -531,6 +637,92 @@ int launch_variant(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, 
     }
 }
 
+
+gapa_dev::PieceGraph piece_graph(const gapa_ctx* c, bool second) {
+    const DeviceGraph& g = c->g;
+    gapa_dev::PieceGraph p{};
+    p.n = g.n;
+    p.tree_pc = g.tree_pc;
+    p.objective = c->objective;
+    if (!second) {
+        p.perm = g.perm;
+        p.tparent = g.tparent;
+        p.palt = g.palt;
+        p.lo_ptr = g.lo_ptr;
+        p.lo_col = g.lo_col;
+        p.fptr = g.fptr;
+        p.fcol = g.fcol16;
+        p.kids = g.kids;
+        p.sz = g.sz;
+        p.pre = g.pre;
+        p.at = g.at;
+        p.crep = g.crep;
+        p.nroot = g.nroot;
+        p.csize = g.csize;
+        p.roots = g.roots;
+        p.num_roots = g.num_roots;
+    } else {
+        const DeviceForest& a = g.alt;
+        p.perm = a.perm;
+        p.tparent = a.tparent;
+        p.palt = a.palt;
+        p.lo_ptr = a.lo_ptr;
+        p.lo_col = a.lo_col;
+        p.fptr = a.fptr;
+        p.fcol = a.fcol16;
+        p.kids = a.kids;
+        p.sz = a.sz;
+        p.pre = a.pre;
+        p.at = a.at;
+        p.crep = a.crep;
+        p.nroot = a.nroot;
+        p.csize = a.csize;
+        p.roots = a.roots;
+        p.num_roots = a.num_roots;
+    }
+    return p;
+}
+
+// The fitness phase with the forest-piece kernel: estimates (unless the operator kernel wrote
+// them), the order by forest and cost, the piece kernel, then the deferred members.  Falls back to
+// the cut-local TREE kernel when the layout does not fit.
+int launch_piece(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, int k, long long* f, cudaStream_t st,
+                 int* kernels, const unsigned* est_in) {
+    const int n = ga.n;
+    const size_t parents = gapa_dev::piece_parents_bytes(n);
+    const size_t avail = c->piece_smem_max > parents ? c->piece_smem_max - parents : 0;
+    const gapa_dev::PieceLayout L = gapa_dev::piece_layout(n, k, kPieceThreads, avail / kPieceTeams);
+    const size_t lab_bytes = gapa_dev::tree16l_smem_bytes(n, (size_t)ga.list_bytes);
+    if (L.pcap < 512 || s < 2 || s > kOrderCap || lab_bytes > c->fit_smem_max)
+        return launch_variant<V_TREE16L>(c, ga, pop, s, k, f, st, kernels, est_in);
+    unsigned* e1 = gapa_estimate_buffer(c);
+    unsigned* e2 = e1 + kOrderCap;
+    unsigned* est_min = e2 + kOrderCap;
+    int* defer = c->g.order + 4 * kOrderCap;
+    int* ctl = defer + kOrderCap;
+    if (!est_in) {
+        local_cost_kernel<<<s, 128, 0, st>>>(pop, k, n, c->g.cut, c->g.has_alt ? c->g.alt.cut : nullptr, e1, e2);
+        if (kernels) *kernels += 1;
+    }
+    const unsigned* a = est_in ? est_in : e1;
+    piece_order_kernel<<<1, 1024, 0, st>>>(a, a + kOrderCap, s, c->g.order, est_min, ctl);
+    PieceArgs pa;
+    pa.g1 = piece_graph(c, false);
+    pa.g2 = c->g.has_alt ? piece_graph(c, true) : pa.g1;
+    pa.L = L;
+    const int grid = std::max(2, std::min(c->num_sms, (s + kPieceTeams - 1) / kPieceTeams));
+    const size_t bytes = parents + (size_t)kPieceTeams * L.bytes;
+    cc_piece_kernel<<<grid, kPieceThreads * kPieceTeams, bytes, st>>>(pa, pop, k, f, c->status, c->g.order, defer,
+                                                                       ctl);
+    GAPA_CUDA(cudaGetLastError());
+    GraphArgs gl = ga;
+    gl.est = est_min;
+    cc_list_kernel<V_TREE16L><<<std::min(s, 2 * c->num_sms), smem_block_for(n), lab_bytes, st>>>(gl, pop, k, f,
+                                                                                               c->status, defer, ctl);
+    GAPA_CUDA(cudaGetLastError());
+    if (kernels) *kernels += 3;
+    return GAPA_OK;
+}
 
 }  // namespace
 
@@ -587,8 +779,13 @@ static bool local_selected(const gapa_ctx* c) {
             c->fitness_variant == GAPA_FITNESS_TREE_LOCAL);
 }
 
+// The forest-piece kernel: by request only (it needs the cut-local kernel's forests and cost tables).
+static bool piece_selected(const gapa_ctx* c) {
+    return c->g.packed16 && c->g.local_list_bytes > 0 && c->g.sz && c->fitness_variant == GAPA_FITNESS_PIECE;
+}
+
 bool gapa_fitness_uses_estimates(const gapa_ctx* c, int s) {
-    return local_selected(c) && s > 1 && s <= kOrderCap && c->genes == GAPA_GENES_NODES &&
+    return (local_selected(c) || piece_selected(c)) && s > 1 && s <= kOrderCap && c->genes == GAPA_GENES_NODES &&
            (c->objective == GAPA_OBJECTIVE_PC || c->objective == GAPA_OBJECTIVE_MCN);
 }
 
@@ -645,6 +842,8 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
             return launch_variant<V_SAMPLED>(c, ga, pop, s, k, f, st);
         default:
             if (c->g.packed16) {
+                if (piece_selected(c) && c->objective <= GAPA_OBJECTIVE_MCN)
+                    return launch_piece(c, ga, pop, s, k, f, st, &prof.kernels, est);
                 if (local_selected(c)) return launch_variant<V_TREE16L>(c, ga, pop, s, k, f, st, &prof.kernels, est);
                 return launch_variant<V_TREE16>(c, ga, pop, s, k, f, st);
             }
@@ -659,6 +858,8 @@ int gapa_fitness_kernels_init(gapa_ctx* c) {
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_SAMPLED>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE16>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE16L>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_list_kernel<V_TREE16L>, c->smem_optin, &c->fit_smem_max);
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_piece_kernel, c->smem_optin, &c->piece_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_smem_kernel<V_TREE32>, c->smem_optin, &c->fit_smem_max);
     if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_edge_genes_kernel, c->smem_optin, &c->fit_smem_max);
     return rc;

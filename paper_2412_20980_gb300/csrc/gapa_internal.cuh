@@ -106,6 +106,13 @@ struct DeviceForest {
     unsigned short* fcol16 = nullptr;
     unsigned* nontree = nullptr;     // non-tree edges a<<16|b (a < b), sorted
     int num_nontree = 0;
+    // forest-piece kernel (see DeviceGraph::sz)
+    int* sz = nullptr;
+    int* pre = nullptr;
+    unsigned short* at = nullptr;
+    int* crep = nullptr;
+    int* nroot = nullptr;
+    int* csize = nullptr;
 };
 
 struct DeviceGraph {
@@ -129,9 +136,22 @@ struct DeviceGraph {
     int local_list_bytes = 0;   // list region of the cut-local TREE kernel (0: that kernel does not fit)
     int* cut = nullptr;         // [n] per original node id: nodes below those of its tree children that
                                 //     have no other lower neighbour (deleting it alone cuts them off)
-    int* order = nullptr;       // [4 * kOrderCap] the members, costliest first (bit 30: use `alt`), then
-                                //     their cost estimates under this forest, under `alt`, and the lower
+    int* order = nullptr;       // [5 * kOrderCap + 16] the members, costliest first (bit 30: use `alt`), then
+                                //     their cost estimates under this forest, under `alt`, and the lower,
+                                //     then the members deferred by the forest-piece kernel and their count
     DeviceForest alt;           // the forest numbered with the top hubs last (cut-local kernel only)
+    // forest-piece kernel, per forest: the subtree size of every node, its position in a preorder
+    // walk (children in ascending order, roots in ascending order; a subtree is the interval
+    // [pre, pre + sz)), the node at each preorder position, the smallest root of every node's
+    // component (its representative), the next root of the same component (-1: none) and the
+    // component's size (at the representative)
+    int* sz = nullptr;
+    int* pre = nullptr;
+    unsigned short* at = nullptr;
+    int* crep = nullptr;
+    int* nroot = nullptr;
+    int* csize = nullptr;
+    long long tree_pc = 0;      // sum over the components of G of C(size, 2)
     bool has_alt = false;
     int* lo_ptr = nullptr;      // [n+1] CSR of lower-numbered neighbours (BFS numbers, ascending;
     int* lo_col = nullptr;      //        the first one is the tree parent)
@@ -159,6 +179,7 @@ struct gapa_ctx {
     size_t smem_per_sm = 0;     // shared memory per SM
     size_t smem_reserved = 0;   // shared memory the runtime reserves per block
     size_t fit_smem_max = 0;  // max dynamic shared memory of the shared-memory fitness kernel
+    size_t piece_smem_max = 0;  // max dynamic shared memory of the forest-piece kernel
     size_t ga_smem_max = 0;   // max dynamic shared memory of the operator kernels
     DeviceGraph g;
     int* status = nullptr;  // device status word

@@ -20,19 +20,19 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pc_worked_examples.json")
 
 
-@pytest.fixture(scope="module", params=["tree_local", "tree", "tree_join", "tree_scan", "sampled", "edges"])
+@pytest.fixture(scope="module", params=["piece", "tree_local", "tree", "tree_join", "tree_scan", "sampled", "edges"])
 def ctx(request):
     import torch
 
     from paper_2412_20980_gb300 import Context
     from paper_2412_20980_gb300 import build as b
-    from paper_2412_20980_gb300.gapa import (FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN,
-                                             FITNESS_TREE_LOCAL, FITNESS_TREE_SCAN)
+    from paper_2412_20980_gb300.gapa import (FITNESS_EDGES, FITNESS_PIECE, FITNESS_SAMPLED, FITNESS_TREE,
+                                             FITNESS_TREE_JOIN, FITNESS_TREE_LOCAL, FITNESS_TREE_SCAN)
 
     b.build()
     c = Context(0)
     c.set_fitness_kernel({"tree": FITNESS_TREE, "tree_join": FITNESS_TREE_JOIN, "tree_scan": FITNESS_TREE_SCAN,
-                          "tree_local": FITNESS_TREE_LOCAL, "sampled": FITNESS_SAMPLED,
+                          "tree_local": FITNESS_TREE_LOCAL, "piece": FITNESS_PIECE, "sampled": FITNESS_SAMPLED,
                           "edges": FITNESS_EDGES}[request.param])
     c.variant_name = request.param
     yield c
