@@ -629,7 +629,7 @@ def run_batched(args, gs, dist, ws, rank, local, dev):
     bt.autotune(os.path.join(ROOT, ".cache", "batch_teams.json") if os.path.isdir(os.path.join(ROOT, ".cache"))
                 else None)
     tune_s = time.perf_counter() - t0
-    gens = w["gens"]
+    gens = args.gens or w["gens"]
     evals_per_run = sum(d["pop"] + (d["pop"] - 1) * gens for d in specs)
     # algorithmic bytes of every exact evaluation of a run, instance by instance
     bytes_per_run = sum((d["pop"] + (d["pop"] - 1) * gens) * bytes_per_eval(g.n, g.num_edges, d["k"])
@@ -769,7 +769,7 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
 
     w = WORKLOADS["surrogate"]
     g = gs[0]
-    G, lam = w["gens"], w["lam"]
+    G, lam = args.gens or w["gens"], w["lam"]
     ctx = Context(local)
     ctx.graph_upload(g.row_ptr, g.col)
 
@@ -967,6 +967,9 @@ def main():
                          "populations per rank")
     ap.add_argument("--fitness-kernel", choices=["auto", "tree_local", "tree", "piece"], default="auto",
                     help="fitness kernel of the contexts (default: the library's choice)")
+    ap.add_argument("--gens", type=int, default=0,
+                    help="generations per run of the batched and surrogate workloads (default: the workload's; "
+                         "shorter runs are for profiling, not for the reported line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")

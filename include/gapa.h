@@ -344,15 +344,19 @@ int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 #define GAPA_OBJECTIVE_SIXDST_MCN 3
 int gapa_set_objective(gapa_ctx* ctx, int objective);
 int gapa_set_sixdst_hops(gapa_ctx* ctx, int hops);
-/* Tensor-core path of the SixDST products (identical results): TCGEN05
- * (tcgen05.mma with the accumulator in tensor memory, the default: 256 x 256
- * output tiles when the padded size is a multiple of 256, else 128 x 128; a
- * device-side wait that runs out is reported as GAPA_ERR_TIMEOUT),
- * TCGEN05_128 (the same with 128 x 128 tiles only) or MMA_SYNC (warp-level
- * mma.sync). */
+/* Tensor-core path of the SixDST products (identical results): TMA (the
+ * default: tcgen05.mma with the accumulator in tensor memory, operands loaded
+ * by cp.async.bulk.tensor from a tensor map by a producer thread while another
+ * issues the products, six stages, 256 x 256 output tiles when the padded size
+ * is a multiple of 256, else as TCGEN05), TCGEN05 (the same products with
+ * operands loaded by every thread with cp.async, three stages; 256 x 256 tiles
+ * when the padded size allows, else 128 x 128), TCGEN05_128 (128 x 128 tiles
+ * only) or MMA_SYNC (warp-level mma.sync).  A device-side wait that runs out is
+ * reported as GAPA_ERR_TIMEOUT. */
 #define GAPA_SIXDST_MMA_SYNC 0
 #define GAPA_SIXDST_TCGEN05 1
 #define GAPA_SIXDST_TCGEN05_128 2
+#define GAPA_SIXDST_TMA 3
 int gapa_set_sixdst_kernel(gapa_ctx* ctx, int kernel);
 
 /* Failure-path check of the device-side bounded waits (the paper has no

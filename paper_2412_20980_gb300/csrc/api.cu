@@ -1181,10 +1181,13 @@ int gapa_read_bandwidth(gapa_ctx* c, int64_t bytes, int32_t reps, double* gbs) {
 
 int gapa_set_sixdst_kernel(gapa_ctx* c, int kernel) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
-    if (kernel != GAPA_SIXDST_MMA_SYNC && kernel != GAPA_SIXDST_TCGEN05 && kernel != GAPA_SIXDST_TCGEN05_128)
+    if (kernel != GAPA_SIXDST_MMA_SYNC && kernel != GAPA_SIXDST_TCGEN05 && kernel != GAPA_SIXDST_TCGEN05_128 &&
+        kernel != GAPA_SIXDST_TMA)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown SixDST kernel %d", kernel);
     if (kernel != GAPA_SIXDST_MMA_SYNC && !c->sixdst_t5_ok)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "the tcgen05 product does not fit in this device's shared memory");
+    if (kernel == GAPA_SIXDST_TMA && !c->sixdst_t7_ok)
+        return gapa_fail(GAPA_ERR_INVALID_ARG, "the TMA product is not available on this device");
     c->sixdst_kernel = kernel;
     return GAPA_OK;
 }

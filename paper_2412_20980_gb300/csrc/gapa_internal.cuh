@@ -199,10 +199,12 @@ struct gapa_ctx {
     int objective = 0;        // GAPA_OBJECTIVE_PC or GAPA_OBJECTIVE_MCN
     int genes = 0;            // GAPA_GENES_NODES or GAPA_GENES_EDGES
     int sixdst_hops = 6;      // N of the SixDST objectives
-    int sixdst_kernel = 0;    // SixDST products: 0 = mma.sync, 1 = tcgen05 (the default when it fits; 256-wide
-                              // tiles where the padded size allows), 2 = tcgen05 with 128-wide tiles only
+    int sixdst_kernel = 0;    // SixDST products: 0 = mma.sync, 1 = tcgen05 (256-wide tiles where the padded size
+                              // allows), 2 = tcgen05 with 128-wide tiles only, 3 = tcgen05 with TMA loads and
+                              // split roles (the default when it fits; 256-wide tiles, else as 1)
     bool sixdst_t5_ok = false;  // the tcgen05 product's shared memory fits on this device
     bool sixdst_t6_ok = false;  // and so does the 256-wide tile's
+    bool sixdst_t7_ok = false;  // and the TMA kernel's (with the driver's tensor-map encoder)
     void* sdst_buf = nullptr;  // SixDST matrices and deletion bitmaps of a member batch
     size_t sdst_cap = 0;
     // (mu+lambda) and roulette scratch

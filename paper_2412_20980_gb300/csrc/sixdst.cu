@@ -17,7 +17,10 @@
 // n, exact in FP32, so the normalised product is exact.  (A + I)^j is
 // symmetric, so the "column-major" B operand is read from the rows of the
 // right factor.
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "gapa_internal.cuh"
@@ -559,6 +562,254 @@ __global__ void __launch_bounds__(kT6Threads) sdst_gemm_t6_kernel(const unsigned
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kT6Tile) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// 256 x 256 tiles with tensor-memory-access (TMA) loads and split roles.  The
+// operands are read by cp.async.bulk.tensor from a 3-D tensor map (columns,
+// rows, members) in boxes of 128 bytes x 256 rows with the 128-byte swizzle:
+// each 8-row group of a box is one 1024-byte swizzle atom (its 16-byte pieces
+// permuted by row), which is the layout a K-major shared-memory descriptor
+// with 128-byte swizzling reads (8-row groups 1024 bytes apart; a 32-byte K
+// step advances the start address by 32 bytes inside the atom).  A stage
+// holds a 128-byte K chunk of both 256-row strips (64 KB); three stages.
+// Warp 0's first lane is the producer: it waits until a stage is free (its
+// `empty` mbarrier, completed by the products' tcgen05.commit), announces
+// the stage's bytes on its `full` mbarrier and issues the two boxes.  Warp
+// 1's first lane issues the products as each stage fills (per 32-byte K step
+// two M = 128, N = 256 products into two accumulators of 256 tensor-memory
+// columns) and commits the stage back; a last commit completes `done`.  Then
+// all eight warps run the epilogue of the 256 x 256 kernel above.  Every wait
+// is bounded: on expiry the kernel records GAPA_DEV_TIMEOUT, waits (bounded)
+// for every box and product it issued, frees its tensor memory and skips the
+// epilogue.
+// ---------------------------------------------------------------------------
+constexpr int kT7Stages = 3, kT7Chunk = 128;
+constexpr int kT7OperandBytes = kT6Tile * kT7Chunk;          // 32 KB per operand per stage
+constexpr int kT7StageBytes = 2 * kT7OperandBytes;           // 64 KB
+constexpr int kT7Smem = kT7Stages * kT7StageBytes + 1024;    // 192 KB + alignment (the epilogue's tile reuses it)
+
+// K-major shared-memory descriptor with 128-byte swizzling: start address, leading byte offset
+// (unused for this layout; 16), stride byte offset 1024 (the next 8-row atom), version 1, layout
+// type 2 (128-byte swizzle).
+__device__ __forceinline__ unsigned long long t7_desc(unsigned addr) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((unsigned long long)(1024u >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void t7_load(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kT6Threads, 1)
+    sdst_gemm_t7_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+                        unsigned char* __restrict__ C, int np, size_t mat, int* status) {
+    extern __shared__ __align__(1024) unsigned char t7_smem[];
+    __shared__ __align__(8) unsigned long long full[kT7Stages], empty[kT7Stages], done;
+    __shared__ unsigned tmem_base;
+    __shared__ int failed, loads_issued, chunks_used;
+    const int T = np / kT6Tile;
+    int ty = 0, rem = (int)blockIdx.x;
+    while (rem >= T - ty) {
+        rem -= T - ty;
+        ++ty;
+    }
+    const int tx = ty + rem;
+    const int member = (int)blockIdx.y;
+    const size_t off = (size_t)member * mat;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int chunks = np / kT7Chunk;
+    if (tid == 0) {
+        failed = 0;
+        loads_issued = 0;
+        chunks_used = 0;
+        for (int s = 0; s < kT7Stages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(2 * kT6Tile)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    const unsigned base = (smem_u32(t7_smem) + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
+    if (warp == 0 && lane == 0) {
+        // producer
+        int c = 0;
+        for (; c < chunks; ++c) {
+            const int s = c % kT7Stages, use = c / kT7Stages;
+            if (c >= kT7Stages && !t5_wait(smem_u32(&empty[s]), (unsigned)((use - 1) & 1))) {
+                failed = 1;
+                break;
+            }
+            const unsigned fb = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kT7StageBytes)
+                         : "memory");
+            const unsigned sa = base + (unsigned)(s * kT7StageBytes), sb = sa + (unsigned)kT7OperandBytes;
+            const int k0 = c * kT7Chunk;
+            t7_load(sa, &mapX, k0, ty * kT6Tile, member, fb);
+            t7_load(sb, &mapY, k0, tx * kT6Tile, member, fb);
+        }
+        loads_issued = c;
+    } else if (warp == 1 && lane == 0) {
+        // products
+        int c = 0;
+        for (; c < chunks; ++c) {
+            const int s = c % kT7Stages;
+            if (!t5_wait(smem_u32(&full[s]), (unsigned)((c / kT7Stages) & 1))) {
+                failed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned sa = base + (unsigned)(s * kT7StageBytes), sb = sa + (unsigned)kT7OperandBytes;
+#pragma unroll
+            for (int j = 0; j < kT7Chunk / 32; ++j) {  // 32-byte K steps inside the 128-byte atoms
+                const unsigned long long db = t7_desc(sb + 32u * (unsigned)j);
+                const unsigned acc = (c > 0 || j > 0) ? 1u : 0u;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {  // tile rows 128h .. 128h + 127: 16 atoms of 8 rows on
+                    const unsigned long long da = t7_desc(sa + (unsigned)(h * 16 * 1024) + 32u * (unsigned)j);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                        ::"r"(tmem + (unsigned)(h * kT6Tile)), "l"(da), "l"(db), "r"(kT6Idesc), "r"(acc)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        chunks_used = c;
+        // the last commit tracks every product issued before it
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (!t5_wait(smem_u32(&done), 0u)) failed = 1;
+        if (failed) {
+            atomicOr(status, GAPA_DEV_TIMEOUT);
+            // every box issued must land before the shared memory is released: wait (bounded) for the
+            // stages loaded but not consumed, then for the products once more
+            for (int c = chunks_used; c < loads_issued; ++c)
+                t5_wait(smem_u32(&full[c % kT7Stages]), (unsigned)((c / kT7Stages) & 1));
+            t5_wait(smem_u32(&done), 0u);
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!failed) {
+        unsigned char* c = C + off;
+        unsigned char* tile = t7_smem + (base - smem_u32(t7_smem));  // [256 rows][256 bytes], the stages being free
+        const int quarter = warp & 3, half = warp >> 2;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int trow = h * 128 + quarter * 32 + lane;  // row within the tile
+            const int row = ty * kT6Tile + trow;
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                const int tcol = half * 128 + q * 32;
+                unsigned v[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(h * kT6Tile + tcol)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                unsigned w[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    unsigned word = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        word |= (__uint_as_float(v[4 * b + e]) > 0.5f ? (unsigned)kOne : 0u) << (8 * e);
+                    w[b] = word;
+                }
+                uint4* dst = reinterpret_cast<uint4*>(c + (size_t)row * np + tx * kT6Tile + tcol);
+                dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                if (tx != ty) {
+                    uint4* t = reinterpret_cast<uint4*>(tile + trow * kT6Tile + tcol);
+                    t[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    t[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                }
+            }
+        }
+        if (tx != ty) {
+            __syncthreads();
+            for (int p = tid; p < kT6Tile * (kT6Tile / 32); p += kT6Threads) {
+                const int j = p & (kT6Tile - 1), r0 = (p / kT6Tile) * 32;  // tile column j, rows r0 .. r0 + 31
+                unsigned w[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    unsigned word = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) word |= (unsigned)tile[(r0 + 4 * b + e) * kT6Tile + j] << (8 * e);
+                    w[b] = word;
+                }
+                uint4* dst = reinterpret_cast<uint4*>(c + (size_t)(tx * kT6Tile + j) * np + ty * kT6Tile + r0);
+                dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kT6Tile) : "memory");
+}
+
+// A 3-D tensor map over `batch` members' np x np byte matrices (columns, rows, members) with
+// boxes of 128 columns x 256 rows x 1 member and the 128-byte swizzle.  The encoder comes from the driver by
+// its entry point (the library does not link the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn t7_encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+int t7_map(CUtensorMap* map, const unsigned char* buf, int np, int batch) {
+    EncodeTiledFn enc = t7_encoder();
+    if (!enc) return gapa_fail(GAPA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[3] = {(cuuint64_t)np, (cuuint64_t)np, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)np, (cuuint64_t)np * (cuuint64_t)np};  // bytes, dims 1 and 2
+    const cuuint32_t box[3] = {(cuuint32_t)kT7Chunk, (cuuint32_t)kT6Tile, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<unsigned char*>(buf), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return gapa_fail(GAPA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GAPA_OK;
+}
+
 // The bounded wait on an mbarrier that nothing completes: it must run out and
 // report GAPA_DEV_TIMEOUT (gapa_selftest_wait).
 __global__ void t5_selftest_kernel(long long limit, int* status) {
@@ -627,6 +878,11 @@ int gapa_sixdst_init(gapa_ctx* c) {
         GAPA_CUDA(cudaFuncSetAttribute(sdst_gemm_t6_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kT6Smem));
         c->sixdst_t6_ok = true;
     }
+    if ((size_t)kT7Smem + 1024 <= c->smem_optin && t7_encoder()) {
+        GAPA_CUDA(cudaFuncSetAttribute(sdst_gemm_t7_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kT7Smem));
+        c->sixdst_t7_ok = true;
+        c->sixdst_kernel = GAPA_SIXDST_TMA;
+    }
     return GAPA_OK;
 }
 
@@ -657,12 +913,20 @@ int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, in
         const int tiles = np / kTile;
         const dim3 grid(tiles * (tiles + 1) / 2, bm);
         const bool t5 = c->sixdst_kernel >= 1;
-        // 256-wide tiles where the padded size allows them
-        const bool t6 = c->sixdst_kernel == 1 && c->sixdst_t6_ok && np % kT6Tile == 0;
+        // 256-wide tiles where the padded size allows them; TMA loads with split roles by default
+        const bool t7 = c->sixdst_kernel == GAPA_SIXDST_TMA && c->sixdst_t7_ok && np % kT6Tile == 0;
+        const bool t6 = (c->sixdst_kernel == 1 || (c->sixdst_kernel == GAPA_SIXDST_TMA && !t7)) && c->sixdst_t6_ok &&
+                        np % kT6Tile == 0;
         const int tiles6 = np / kT6Tile;
         const dim3 grid6(tiles6 * (tiles6 + 1) / 2, bm);
+        int map_rc = GAPA_OK;
         auto launch_gemm = [&](const unsigned char* xa, const unsigned char* yb, unsigned char* cc) {
-            if (t6)
+            if (t7) {
+                CUtensorMap mx, my;
+                if ((map_rc = t7_map(&mx, xa, np, bm)) != GAPA_OK || (map_rc = t7_map(&my, yb, np, bm)) != GAPA_OK)
+                    return;
+                sdst_gemm_t7_kernel<<<grid6, kT6Threads, kT7Smem, st>>>(mx, my, cc, np, mat, c->status);
+            } else if (t6)
                 sdst_gemm_t6_kernel<<<grid6, kT6Threads, kT6Smem, st>>>(xa, yb, cc, np, mat, c->status);
             else if (t5)
                 sdst_gemm_t5_kernel<<<grid, kT5Threads, 2 * kT5Stages * kT5StageBytes, st>>>(xa, yb, cc, np, mat,
@@ -693,6 +957,7 @@ int gapa_launch_fitness_sixdst(gapa_ctx* c, const int32_t* pop, int s, int k, in
                 base = dst;
             }
         }
+        if (map_rc != GAPA_OK) return map_rc;
         sdst_objective_kernel<<<bm, 256, 0, st>>>(buf[res], n, np, mat, words, dead,
                                                   c->objective == GAPA_OBJECTIVE_SIXDST_MCN ? 1 : 0,
                                                   reinterpret_cast<long long*>(fit) + m0);

@@ -307,10 +307,11 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
     }
 }
 
-// z of `rows` residual records from their counts (one CTA, exact int64 sums,
-// then FP64 in a fixed order with explicit rounding: mean = S1 / rows,
-// var = S2 / rows - mean^2, sd = max(sqrt(var), 1), z = float((c - mean) / sd)).
-__global__ void __launch_bounds__(256) resid_stats_kernel(ResidRow* __restrict__ r, int rows) {
+// Mean and standard deviation of each of the three counts over `rows` residual records (one CTA:
+// exact int64 sums, then FP64 in a fixed order with explicit rounding: mean = S1 / rows,
+// var = S2 / rows - mean^2, sd = max(sqrt(var), 1)); ms[0..2] = means, ms[3..5] = deviations.
+__global__ void __launch_bounds__(256) resid_stats_kernel(const ResidRow* __restrict__ r, int rows,
+                                                          double* __restrict__ ms) {
     __shared__ long long s1[3][256], s2[3][256];
     long long a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
@@ -337,31 +338,38 @@ __global__ void __launch_bounds__(256) resid_stats_kernel(ResidRow* __restrict__
             }
         __syncthreads();
     }
-    double mean[3], sd[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        mean[j] = __ddiv_rn((double)s1[j][0], (double)rows);
-        const double var = __dsub_rn(__ddiv_rn((double)s2[j][0], (double)rows), __dmul_rn(mean[j], mean[j]));
-        sd[j] = fmax(__dsqrt_rn(fmax(var, 0.0)), 1.0);
+    if (threadIdx.x < 3) {
+        const int j = threadIdx.x;
+        const double mean = __ddiv_rn((double)s1[j][0], (double)rows);
+        const double var = __dsub_rn(__ddiv_rn((double)s2[j][0], (double)rows), __dmul_rn(mean, mean));
+        ms[j] = mean;
+        ms[3 + j] = fmax(__dsqrt_rn(fmax(var, 0.0)), 1.0);
     }
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+}
+
+// z of every record from the statistics: z = float((c - mean) / sd), the FP64 operations
+// explicitly rounded (spread over the whole grid: FP64 is slow on one SM).
+__global__ void resid_z_kernel(ResidRow* __restrict__ r, int rows, const double* __restrict__ ms) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
         const int4 c = r[i].c;
-        r[i].z = make_float4(__double2float_rn(__ddiv_rn(__dsub_rn((double)c.x, mean[0]), sd[0])),
-                             __double2float_rn(__ddiv_rn(__dsub_rn((double)c.y, mean[1]), sd[1])),
-                             __double2float_rn(__ddiv_rn(__dsub_rn((double)c.z, mean[2]), sd[2])), 0.f);
+        r[i].z = make_float4(__double2float_rn(__ddiv_rn(__dsub_rn((double)c.x, ms[0]), ms[3])),
+                             __double2float_rn(__ddiv_rn(__dsub_rn((double)c.y, ms[1]), ms[4])),
+                             __double2float_rn(__ddiv_rn(__dsub_rn((double)c.z, ms[2]), ms[5])), 0.f);
     }
 }
 
 // Features of each row of pop (k genes): x (BF16 [rows_pad][80]) and its
 // transpose (BF16 [80][rows_pad]); rows >= rows are zero.  resid[r] holds
 // the row's residual-degree counts.  Genes outside [0, n) are ignored.
-__global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ pop, int rows, int k, int n,
+constexpr int kFeatWarps = 8, kFeatInFlight = 8;
+
+__global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(const int* __restrict__ pop, int rows, int k, int n,
                                                        const bf16* __restrict__ Eb, const float* __restrict__ logdeg,
                                                        const float* __restrict__ deg, float inv2E, float invsqrtk,
                                                        const ResidRow* __restrict__ resid, bf16* __restrict__ X,
                                                        bf16* __restrict__ XT, int rows_pad) {
-    __shared__ float2 part[4][32];
-    __shared__ float st[4][4];
+    __shared__ float2 part[kFeatWarps][32];
+    __shared__ float st[kFeatWarps][4];
     const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (r >= rows) {
         for (int c = t; c < kIn; c += blockDim.x) {
@@ -372,25 +380,27 @@ __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ p
     }
     const int* genes = pop + (size_t)r * k;
     // embedding sum: a warp reads whole 128-byte rows (lane = two dimensions),
-    // warp w takes genes w, w + 4, ...; four loads in flight per lane
+    // warp w takes genes w, w + kFeatWarps, ...; kFeatInFlight loads in flight per lane
     const unsigned* E2 = reinterpret_cast<const unsigned*>(Eb);
     float sx = 0.f, sy = 0.f;
     int j = warp;
-    for (; j + 12 < k; j += 16) {
-        int v[4];
+    constexpr int kSpan = kFeatWarps * kFeatInFlight;
+    for (; j + kSpan - kFeatWarps < k; j += kSpan) {
+        int v[kFeatInFlight];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = genes[j + 4 * u];
-        unsigned w[4];
+        for (int u = 0; u < kFeatInFlight; ++u) v[u] = genes[j + kFeatWarps * u];
+        unsigned w[kFeatInFlight];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = (v[u] >= 0 && v[u] < n) ? __ldg(E2 + (size_t)v[u] * (kEmb / 2) + lane) : 0u;
+        for (int u = 0; u < kFeatInFlight; ++u)
+            w[u] = (v[u] >= 0 && v[u] < n) ? __ldg(E2 + (size_t)v[u] * (kEmb / 2) + lane) : 0u;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kFeatInFlight; ++u) {
             const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[u]));
             sx += f.x;
             sy += f.y;
         }
     }
-    for (; j < k; j += 4) {
+    for (; j < k; j += kFeatWarps) {
         const int v = genes[j];
         if (v >= 0 && v < n) {
             const unsigned w = __ldg(E2 + (size_t)v * (kEmb / 2) + lane);
@@ -426,16 +436,21 @@ __global__ void __launch_bounds__(128) features_kernel(const int* __restrict__ p
     __syncthreads();
     if (t < kEmb) {
         const int l = t >> 1;
-        const float e = (t & 1) ? ((part[0][l].y + part[1][l].y) + (part[2][l].y + part[3][l].y))
-                                : ((part[0][l].x + part[1][l].x) + (part[2][l].x + part[3][l].x));
+        float e = 0.f;  // warps in a fixed order
+#pragma unroll
+        for (int w = 0; w < kFeatWarps; ++w) e += (t & 1) ? part[w][l].y : part[w][l].x;
         X[(size_t)r * kIn + t] = __float2bfloat16(e * invsqrtk);
         XT[(size_t)t * rows_pad + r] = __float2bfloat16(e * invsqrtk);
     } else if (t < kIn) {
         float f = 0.f;
-        const float Q1 = st[0][0] + st[1][0] + st[2][0] + st[3][0];
-        const float Q2 = st[0][1] + st[1][1] + st[2][1] + st[3][1];
-        const float QM = fmaxf(fmaxf(st[0][2], st[1][2]), fmaxf(st[2][2], st[3][2]));
-        const float DS = st[0][3] + st[1][3] + st[2][3] + st[3][3];
+        float Q1 = 0.f, Q2 = 0.f, QM = -1.f, DS = 0.f;
+#pragma unroll
+        for (int w = 0; w < kFeatWarps; ++w) {
+            Q1 += st[w][0];
+            Q2 += st[w][1];
+            QM = fmaxf(QM, st[w][2]);
+            DS += st[w][3];
+        }
         const float mean = k > 0 ? Q1 / k : 0.f;
         if (t == 64) f = mean;
         if (t == 65) f = k > 0 ? QM : 0.f;
@@ -525,16 +540,125 @@ __global__ void __launch_bounds__(256) colsum_kernel(const bf16* __restrict__ H2
     }
 }
 
-// Embedding gradient: every gene v of row b gets dx[b][0:64] / sqrt(k), summed
-// in 2^-40 fixed point with integer atomics (order-independent).
-__global__ void __launch_bounds__(256) emb_grad_kernel(const int* __restrict__ pop, int k,
-                                                       const float* __restrict__ dX, float invsqrtk,
-                                                       unsigned long long* __restrict__ Gi) {
-    const int b = blockIdx.x, d = threadIdx.x & 63, jj = threadIdx.x >> 6;
-    const long long q = llrint((double)dX[(size_t)b * kIn + d] * invsqrtk * kFix);
-    if (q == 0) return;
-    const int* genes = pop + (size_t)b * k;
-    for (int j = jj; j < k; j += 4) atomicAdd(&Gi[(size_t)genes[j] * kEmb + d], (unsigned long long)q);
+// Embedding gradient: every gene v of row b gets dx[b][0:64] / sqrt(k), each
+// term rounded to 2^-40 fixed point and summed as integers (exact, so the
+// order of the terms does not matter and training is bit-reproducible).  The
+// batch is first turned into lists of rows per node (a counting sort:
+// occurrences, an exclusive scan, a fill), then one warp per node sums its
+// rows' terms in registers and writes the node's 64 sums: no atomics on the
+// gradient and no clearing of it.
+__device__ __forceinline__ long long emb_term(const float* __restrict__ dX, int b, int d, float invsqrtk) {
+    return llrint((double)dX[(size_t)b * kIn + d] * invsqrtk * kFix);
+}
+
+__global__ void emb_count_kernel(const int* __restrict__ pop, size_t cells, int n, int* __restrict__ cnt) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+        const int v = __ldg(&pop[i]);
+        if ((unsigned)v < (unsigned)n) atomicAdd(&cnt[v], 1);
+    }
+}
+
+// Exclusive scan of cnt[0 .. n) in blocks of 1024: off[v] = the prefix within v's block, blk[b] =
+// block b's total.
+__global__ void __launch_bounds__(1024) scan_block_kernel(const int* __restrict__ cnt, int n, int* __restrict__ off,
+                                                          int* __restrict__ blk) {
+    __shared__ int ws[32];
+    const int v = blockIdx.x * 1024 + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = v < n ? cnt[v] : 0;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int y = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    const int pre = (warp ? ws[warp - 1] : 0) + incl - x;
+    if (v < n) off[v] = pre;
+    if (threadIdx.x == 1023) blk[blockIdx.x] = pre + x;
+}
+
+// Exclusive scan of the nb block totals in place (one CTA, 1024 at a time with a carry).
+__global__ void __launch_bounds__(1024) scan_top_kernel(int* __restrict__ blk, int nb) {
+    __shared__ int ws[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const int x = b < nb ? blk[b] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) ws[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int y = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            ws[lane] = y;
+        }
+        __syncthreads();
+        const int c = carry;
+        if (b < nb) blk[b] = c + (warp ? ws[warp - 1] : 0) + incl - x;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + ws[31];
+        __syncthreads();
+    }
+}
+
+// off[v] += the offset of v's block; cur[v] = off[v] (the fill cursors); off[n] = the total.
+__global__ void scan_add_kernel(int* __restrict__ off, const int* __restrict__ blk, const int* __restrict__ cnt, int n,
+                                int* __restrict__ cur) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int o = off[v] + blk[v >> 10];
+        off[v] = o;
+        cur[v] = o;
+        if (v == n - 1) off[n] = o + cnt[v];
+    }
+}
+
+__global__ void emb_fill_kernel(const int* __restrict__ pop, size_t cells, int k, int n, int* __restrict__ cur,
+                                int* __restrict__ rows_of) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+        const int v = __ldg(&pop[i]);
+        if ((unsigned)v < (unsigned)n) rows_of[atomicAdd(&cur[v], 1)] = (int)(i / (size_t)k);
+    }
+}
+
+// One warp per node: lanes take dimensions lane and lane + 32.
+__global__ void __launch_bounds__(256) emb_gather_kernel(const int* __restrict__ off, const int* __restrict__ rows_of,
+                                                         const float* __restrict__ dX, float invsqrtk, int n,
+                                                         unsigned long long* __restrict__ Gi) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        long long s0 = 0, s1 = 0;
+        for (int e = __ldg(&off[v]), e1 = __ldg(&off[v + 1]); e < e1; ++e) {
+            const int b = __ldg(&rows_of[e]);
+            s0 += emb_term(dX, b, lane, invsqrtk);
+            s1 += emb_term(dX, b, lane + 32, invsqrtk);
+        }
+        Gi[(size_t)v * kEmb + lane] = (unsigned long long)s0;
+        Gi[(size_t)v * kEmb + lane + 32] = (unsigned long long)s1;
+    }
 }
 
 // Fixed point (2^-40) to FP32 without the FP64 pipe: hi * 2^32 + lo in one
@@ -788,6 +912,11 @@ struct gapa_surrogate {
     int* batch_rows = nullptr;
     double* stats = nullptr;
     int tau = 0;
+    // embedding gradient: occurrences per node, list offsets (n + 1), fill cursors, block totals,
+    // and the rows of every node's list
+    int *emb_cnt = nullptr, *emb_off = nullptr, *emb_cur = nullptr, *emb_blk = nullptr, *rows_of = nullptr;
+    double* rstats = nullptr;  // means and deviations of the residual counts of the last rows computed
+    size_t rows_of_cap = 0;
 };
 
 namespace {
@@ -826,9 +955,10 @@ int round16(int x) { return (x + 15) & ~15; }
 // Residual-degree counts of `rows` deletion sets into s->resid, standardised over those rows.
 int compute_resid(gapa_surrogate* s, const int32_t* pop, int rows, int k, cudaStream_t st) {
     if (rows <= 0) return GAPA_OK;
-    ProfileScope prof(s->ctx, st, 2, 2);
+    ProfileScope prof(s->ctx, st, 2, 3);
     resid_kernel<<<rows, 256, s->resid_smem, st>>>(pop, rows, k, s->n, s->nbr, s->col, s->resid);
-    resid_stats_kernel<<<1, 256, 0, st>>>(s->resid, rows);
+    resid_stats_kernel<<<1, 256, 0, st>>>(s->resid, rows, s->rstats);
+    resid_z_kernel<<<(rows + 127) / 128, 128, 0, st>>>(s->resid, rows, s->rstats);
     GAPA_CUDA(cudaGetLastError());
     return GAPA_OK;
 }
@@ -844,7 +974,7 @@ int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, c
     }
     ProfileScope prof(s->ctx, st, 2, 4);
     const int R = round16(rows);
-    features_kernel<<<R, 128, 0, st>>>(pop, rows, k, s->n, s->Eb, s->logdeg, s->deg, s->inv2E,
+    features_kernel<<<R, kFeatWarps * 32, 0, st>>>(pop, rows, k, s->n, s->Eb, s->logdeg, s->deg, s->inv2E,
                                        1.f / sqrtf((float)std::max(k, 1)), resid, s->X, s->XT, R);
     GemmArgs a = gemm(R, kHid, kIn, s->X, kIn, s->W1tb, kIn);
     a.Cb = s->H1;
@@ -869,12 +999,44 @@ int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, c
     return GAPA_OK;
 }
 
+// Lists of rows per node for B rows of k genes (rows_of holds B * k entries).
+int ensure_csr(gapa_surrogate* s, size_t cells) {
+    if (cells <= s->rows_of_cap) return GAPA_OK;
+    cudaFree(s->rows_of);
+    s->rows_of = nullptr;
+    s->rows_of_cap = 0;
+    if (cudaMalloc(&s->rows_of, std::max<size_t>(cells, 1) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "embedding-gradient lists of %zu entries", cells);
+    }
+    s->rows_of_cap = cells;
+    return GAPA_OK;
+}
+
+// The embedding gradient of a batch into s->Gi (fixed point): count, scan, fill, gather.
+int emb_gradient(gapa_surrogate* s, const int32_t* pop, int B, int k, cudaStream_t st) {
+    const size_t cells = (size_t)B * k;
+    int rc = ensure_csr(s, cells);
+    if (rc != GAPA_OK) return rc;
+    const int n = s->n, nb = (n + 1023) / 1024, grid = s->ctx->num_sms * 4;
+    GAPA_CUDA(cudaMemsetAsync(s->emb_cnt, 0, (size_t)n * 4, st));
+    emb_count_kernel<<<grid, 256, 0, st>>>(pop, cells, n, s->emb_cnt);
+    scan_block_kernel<<<nb, 1024, 0, st>>>(s->emb_cnt, n, s->emb_off, s->emb_blk);
+    scan_top_kernel<<<1, 1024, 0, st>>>(s->emb_blk, nb);
+    scan_add_kernel<<<grid, 256, 0, st>>>(s->emb_off, s->emb_blk, s->emb_cnt, n, s->emb_cur);
+    emb_fill_kernel<<<grid, 256, 0, st>>>(pop, cells, std::max(k, 1), n, s->emb_cur, s->rows_of);
+    emb_gather_kernel<<<grid * 2, 256, 0, st>>>(s->emb_off, s->rows_of, s->dX, 1.f / sqrtf((float)std::max(k, 1)), n,
+                                               s->Gi);
+    GAPA_CUDA(cudaGetLastError());
+    return GAPA_OK;
+}
+
 // One AdamW step on a batch (rows a multiple of 16) with targets t.
 int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float* t, cudaStream_t st,
                const ResidRow* resid = nullptr) {
     int rc = forward(s, pop, B, k, true, st, resid);
     if (rc != GAPA_OK) return rc;
-    ProfileScope prof(s->ctx, st, 2, 13);
+    ProfileScope prof(s->ctx, st, 2, 18);
     float* G = s->G;
     const Layout& L = s->L;
     loss_kernel<<<1, 256, 0, st>>>(s->y, t, B, s->dy, s->loss);
@@ -905,8 +1067,7 @@ int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float*
     a.Cf = s->dX;
     a.ldc = kIn;
     if ((rc = launch_gemm(a, st)) != GAPA_OK) return rc;
-    GAPA_CUDA(cudaMemsetAsync(s->Gi, 0, (size_t)s->n * kEmb * sizeof(unsigned long long), st));
-    emb_grad_kernel<<<B, 256, 0, st>>>(pop, k, s->dX, 1.f / sqrtf((float)std::max(k, 1)), s->Gi);
+    if ((rc = emb_gradient(s, pop, B, k, st)) != GAPA_OK) return rc;
     s->tau += 1;
     const float bc1 = 1.f - powf(s->cfg.beta1, (float)s->tau), bc2 = 1.f - powf(s->cfg.beta2, (float)s->tau);
     // dense parameters (W1 .. b3), then the embedding table in one fused pass
@@ -960,7 +1121,8 @@ int check_graph(const gapa_surrogate* s) {
 void free_surrogate(gapa_surrogate* s) {
     void* ps[] = {s->P, s->M, s->V, s->G, s->Gi, s->W1b, s->W1tb, s->W2b, s->W2tb, s->Eb, s->logdeg, s->deg,
                   s->X, s->XT, s->H1, s->H1T, s->H2, s->dZ2, s->dZ2T, s->dZ1, s->dZ1T, s->y, s->dy, s->dX,
-                  s->loss, s->tbuf, s->batch_rows, s->stats, s->resid, s->nbr};
+                  s->loss, s->tbuf, s->batch_rows, s->stats, s->resid, s->nbr, s->emb_cnt, s->emb_off,
+                  s->emb_cur, s->emb_blk, s->rows_of, s->rstats};
     for (void* p : ps) cudaFree(p);
 }
 
@@ -1011,7 +1173,9 @@ int gapa_surrogate_create(gapa_surrogate** out, gapa_ctx* ctx, const gapa_surrog
         cudaMalloc(&s->W2b, (size_t)kHid * kHid * 2) || cudaMalloc(&s->W2tb, (size_t)kHid * kHid * 2) ||
         cudaMalloc(&s->Eb, (size_t)s->n * kEmb * 2) || cudaMalloc(&s->logdeg, (size_t)s->n * 4) ||
         cudaMalloc(&s->deg, (size_t)s->n * 4) || cudaMalloc(&s->loss, 4) || cudaMalloc(&s->stats, 16) ||
-        cudaMalloc(&s->nbr, (size_t)s->n * sizeof(int4))) {
+        cudaMalloc(&s->nbr, (size_t)s->n * sizeof(int4)) || cudaMalloc(&s->emb_cnt, (size_t)s->n * 4) ||
+        cudaMalloc(&s->emb_off, ((size_t)s->n + 1) * 4) || cudaMalloc(&s->emb_cur, (size_t)s->n * 4) ||
+        cudaMalloc(&s->emb_blk, ((size_t)(s->n + 1023) / 1024 + 1) * 4) || cudaMalloc(&s->rstats, 6 * sizeof(double))) {
         cudaGetLastError();
         return bail(gapa_fail(GAPA_ERR_OOM, "surrogate parameters"));
     }
@@ -1179,7 +1343,8 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
         cleanup();
         return gapa_fail(GAPA_ERR_OOM, "surrogate run buffers");
     }
-    if (s && (rc = ensure_rows(s, std::max(lam, s->cfg.batch))) != GAPA_OK) {
+    if (s && ((rc = ensure_rows(s, std::max(lam, s->cfg.batch))) != GAPA_OK ||
+              (rc = ensure_csr(s, (size_t)s->cfg.batch * k)) != GAPA_OK)) {
         cleanup();
         return rc;
     }

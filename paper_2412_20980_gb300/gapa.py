@@ -430,7 +430,8 @@ class Context:
         return float(out.value)
 
     def set_sixdst_kernel(self, kernel: int):
-        """0: mma.sync products (default), 1: tcgen05 products (same results)."""
+        """SixDST products (same results): 3 tcgen05 with TMA loads and split roles (the default where
+        available), 1 tcgen05 with cp.async loads, 2 tcgen05 with 128-wide tiles only, 0 mma.sync."""
         _check(self.lib.gapa_set_sixdst_kernel(self.handle, kernel))
 
     def set_sixdst_hops(self, hops: int):

@@ -10,7 +10,7 @@ from oracle import sixdst_ref as sx
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["mma_sync", "tcgen05", "tcgen05_128"])
+@pytest.fixture(scope="module", params=["tma", "mma_sync", "tcgen05", "tcgen05_128"])
 def ctx(request):
     import torch
 
@@ -19,9 +19,10 @@ def ctx(request):
 
     b.build()
     c = Context(0)
-    # tcgen05: 256-wide tiles where the padded size is a multiple of 256 (n = 150, 200, 500, 700
-    # below), 128-wide otherwise; tcgen05_128: 128-wide tiles throughout
-    c.set_sixdst_kernel({"mma_sync": 0, "tcgen05": 1, "tcgen05_128": 2}[request.param])
+    # tcgen05 and tma: 256-wide tiles where the padded size is a multiple of 256 (n = 150, 200, 500,
+    # 700 below; tma loads them by TMA with split producer and product roles), 128-wide otherwise;
+    # tcgen05_128: 128-wide tiles throughout
+    c.set_sixdst_kernel({"mma_sync": 0, "tcgen05": 1, "tcgen05_128": 2, "tma": 3}[request.param])
     yield c
     torch.cuda.synchronize()
     c.close()
