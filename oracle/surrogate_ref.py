@@ -40,6 +40,8 @@ b2 (256,), w3 (256,), b3 (1,), E (n, 64).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 IN, HID, EMB = 80, 256, 64
@@ -143,6 +145,46 @@ def loss_and_grads(params: dict, pop: np.ndarray, t: np.ndarray, row_ptr, col):
     gE = np.zeros_like(params["E"])
     for b in range(B):
         np.add.at(gE, pop[b], dx[b, :EMB] / np.sqrt(k))
+    g["E"] = gE
+    return loss, g, y
+
+
+def round_bf16(x) -> np.ndarray:
+    """Round to the nearest BF16 value (8 significant bits, ties to even) via the float32 bit
+    pattern: add 0x7FFF plus the lowest kept bit, drop the low 16 bits; returned as float64."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def loss_and_grads_stored(params: dict, pop: np.ndarray, t, row_ptr, col, rnd=round_bf16):
+    """loss_and_grads with `rnd` applied to every tensor the GPU keeps in BF16: the embedding
+    table, the features, W1, W2, the activations h1 and h2 and the backward signals dz2 and dz1
+    (products and sums in fp64, as the GPU accumulates in FP32).  With rnd = identity it is
+    loss_and_grads.  t = None gives the scores only: (None, None, y)."""
+    k = pop.shape[1]
+    x = rnd(features(pop, rnd(params["E"]), row_ptr, col))
+    W1, W2 = rnd(params["W1"]), rnd(params["W2"])
+    z1 = x @ W1 + params["b1"]
+    h1 = rnd(np.maximum(z1, 0.0))
+    z2 = h1 @ W2 + params["b2"]
+    h2 = rnd(np.maximum(z2, 0.0))
+    y = h2 @ params["w3"] + params["b3"][0]
+    if t is None:
+        return None, None, y
+    loss = float(np.mean((y - t) ** 2))
+    dy = 2.0 * (y - t) / y.shape[0]
+    g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()])}
+    dz2 = rnd(np.outer(dy, params["w3"]) * (z2 > 0))
+    g["W2"] = h1.T @ dz2
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = rnd((dz2 @ W2.T) * (z1 > 0))
+    g["W1"] = x.T @ dz1
+    g["b1"] = np.sum(dz1, axis=0)
+    dx = dz1 @ W1.T
+    gE = np.zeros_like(params["E"])
+    for b in range(y.shape[0]):
+        np.add.at(gE, pop[b], dx[b, :EMB] / math.sqrt(k))
     g["E"] = gE
     return loss, g, y
 

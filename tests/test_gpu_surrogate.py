@@ -8,8 +8,9 @@ stored tensors alone moves the gradients of this model by 4-5 % in relative L2
 norm from the exact fp64 values (the batch sums cancel), while the
 accumulation order moves them by about 1e-5.  So every output is checked twice:
 against the fp64 reference within 1e-1 (cosine >= 0.995), and against the same
-formulas with the BF16 roundings applied at the same places (computed here in
-fp64) within 1e-2.  The optimiser runs in FP32 and is compared elementwise
+formulas with the BF16 roundings applied at the same places (the reference's
+loss_and_grads_stored, in fp64, pinned by tests/test_oracle_surrogate_pins.py)
+within 1e-2.  The optimiser runs in FP32 and is compared elementwise
 within 1e-5 relative.
 """
 import numpy as np
@@ -57,37 +58,6 @@ def _batch(g, rows, k, seed):
     return pop, torch.from_numpy(pop).cuda()
 
 
-def _bf16(x):
-    """Round to the nearest BF16 value (ties to even), returned as float64."""
-    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return r.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
-def _bf16_model(params, pop, t, row_ptr, col):
-    """The reference formulas with BF16 roundings where the GPU stores BF16 tensors."""
-    k = pop.shape[1]
-    x = _bf16(sr.features(pop, _bf16(params["E"]), row_ptr, col))
-    W1, W2 = _bf16(params["W1"]), _bf16(params["W2"])
-    h1 = _bf16(np.maximum(x @ W1 + params["b1"], 0.0))
-    h2 = _bf16(np.maximum(h1 @ W2 + params["b2"], 0.0))
-    y = h2 @ params["w3"] + params["b3"][0]
-    if t is None:
-        return y, None
-    B = y.shape[0]
-    dy = 2.0 * (y - t) / B
-    dz2 = _bf16(np.outer(dy, params["w3"]) * (h2 > 0))
-    dz1 = _bf16((dz2 @ W2.T) * (h1 > 0))
-    g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()]), "W2": h1.T @ dz2, "b2": dz2.sum(axis=0),
-         "W1": x.T @ dz1, "b1": dz1.sum(axis=0)}
-    dx = dz1 @ W1.T
-    gE = np.zeros_like(params["E"])
-    for b in range(B):
-        np.add.at(gE, pop[b], dx[b, :sr.EMB] / np.sqrt(k))
-    g["E"] = gE
-    return y, g
-
-
 def _cos(a, b):
     a, b = np.ravel(a), np.ravel(b)
     return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-300))
@@ -101,7 +71,7 @@ def test_forward_matches_reference(setup):
     x = sr.features(pop, params["E"], g.row_ptr, g.col)
     want, _ = sr.forward(params, x)
     assert _rel(y, want) < 1e-1, _rel(y, want)
-    same, _ = _bf16_model(params, pop, None, g.row_ptr, g.col)
+    _, _, same = sr.loss_and_grads_stored(params, pop, None, g.row_ptr, g.col)
     assert _rel(y, same) < 1e-2, _rel(y, same)
 
 
@@ -140,7 +110,7 @@ def test_gradients_and_adamw_match_reference(setup):
     before = sg.params()
     loss = sg.train_step(pop_d, torch.from_numpy(t).cuda())
     want_loss, want_g, _ = sr.loss_and_grads(before, pop, t.astype(np.float64), g.row_ptr, g.col)
-    _, same_g = _bf16_model(before, pop, t.astype(np.float64), g.row_ptr, g.col)
+    _, same_g, _ = sr.loss_and_grads_stored(before, pop, t.astype(np.float64), g.row_ptr, g.col)
     assert abs(loss - want_loss) <= 5e-2 * abs(want_loss)
     got_g = {name: sg.tensor(name, grad=True).astype(np.float64) for name in sr_names()}
     touched = np.unique(pop)

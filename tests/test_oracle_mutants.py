@@ -226,6 +226,14 @@ PY_MUTANTS = {
     "standardised counts without the floor at 1": (
         "oracle.surrogate_ref", "sd = max(np.sqrt(max(var, 0.0)), 1.0)", "sd = max(np.sqrt(max(var, 0.0)), 1e-12)",
         "test_oracle_surrogate_pins.py"),
+    "stored variant masks dz1 with the second layer": (
+        "oracle.surrogate_ref", "dz1 = rnd((dz2 @ W2.T) * (z1 > 0))", "dz1 = rnd((dz2 @ W2.T) * (z2 > 0))",
+        "test_oracle_surrogate_pins.py"),
+    "stored variant's loss gradient not averaged": (
+        "oracle.surrogate_ref", "dy = 2.0 * (y - t) / y.shape[0]", "dy = 2.0 * (y - t)", "test_oracle_surrogate_pins.py"),
+    "BF16 rounding truncates": (
+        "oracle.surrogate_ref", "r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "r = (u >> 16) << 16",
+        "test_oracle_surrogate_pins.py"),
     "degree feature: mean instead of max": (
         "oracle.surrogate_ref", "x[i, 65] = qi.max()", "x[i, 65] = qi.mean()", "test_oracle_surrogate_pins.py"),
 }
