@@ -517,8 +517,9 @@ def run_gapa(args, env: Env, gs):
         achieved = flop * fit_evals / (fit_ms / 1000.0) / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": None,
-                    "kernel": "sdst_gemm_t6_kernel (tcgen05.mma kind::f8f6f4 E4M3, 256 x 256 tiles as two "
-                              "M = 128, N = 256 products, FP32 accumulators in TMEM)",
+                    "kernel": "sdst_gemm_t7_kernel (tcgen05.mma kind::f8f6f4 E4M3, operands loaded by "
+                              "cp.async.bulk.tensor in 128-byte swizzled boxes, producer and MMA threads split, "
+                              "256 x 256 tiles as two M = 128, N = 256 products, FP32 accumulators in TMEM)",
                     "flop_per_eval": flop, "evals": fit_evals, "fitness_ms": fit_ms,
                     "peak_source": "measured bf16 burst (MEASURED_PEAKS.json bf16_tflops) x 2, the FP8/BF16 nominal "
                                    "ratio" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else

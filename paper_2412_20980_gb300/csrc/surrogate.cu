@@ -547,8 +547,13 @@ __global__ void __launch_bounds__(256) colsum_kernel(const bf16* __restrict__ H2
 // occurrences, an exclusive scan, a fill), then one warp per node sums its
 // rows' terms in registers and writes the node's 64 sums: no atomics on the
 // gradient and no clearing of it.
-__device__ __forceinline__ long long emb_term(const float* __restrict__ dX, int b, int d, float invsqrtk) {
-    return llrint((double)dX[(size_t)b * kIn + d] * invsqrtk * kFix);
+// The rounded terms once per (row, dimension): q[b][d] = round(dX[b][d] / sqrt(k) * 2^40)
+// (FP64 is slow on this part, so the per-node sums read these integers).
+__global__ void emb_terms_kernel(const float* __restrict__ dX, int B, float invsqrtk, long long* __restrict__ q) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * kEmb; i += gridDim.x * blockDim.x) {
+        const int b = i / kEmb, d = i % kEmb;
+        q[i] = llrint((double)dX[(size_t)b * kIn + d] * invsqrtk * kFix);
+    }
 }
 
 __global__ void emb_count_kernel(const int* __restrict__ pop, size_t cells, int n, int* __restrict__ cnt) {
@@ -645,16 +650,16 @@ __global__ void emb_fill_kernel(const int* __restrict__ pop, size_t cells, int k
 
 // One warp per node: lanes take dimensions lane and lane + 32.
 __global__ void __launch_bounds__(256) emb_gather_kernel(const int* __restrict__ off, const int* __restrict__ rows_of,
-                                                         const float* __restrict__ dX, float invsqrtk, int n,
+                                                         const long long* __restrict__ q, int n,
                                                          unsigned long long* __restrict__ Gi) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
         long long s0 = 0, s1 = 0;
         for (int e = __ldg(&off[v]), e1 = __ldg(&off[v + 1]); e < e1; ++e) {
-            const int b = __ldg(&rows_of[e]);
-            s0 += emb_term(dX, b, lane, invsqrtk);
-            s1 += emb_term(dX, b, lane + 32, invsqrtk);
+            const long long* qb = q + (size_t)__ldg(&rows_of[e]) * kEmb;
+            s0 += __ldg(qb + lane);
+            s1 += __ldg(qb + lane + 32);
         }
         Gi[(size_t)v * kEmb + lane] = (unsigned long long)s0;
         Gi[(size_t)v * kEmb + lane + 32] = (unsigned long long)s1;
@@ -916,6 +921,8 @@ struct gapa_surrogate {
     // and the rows of every node's list
     int *emb_cnt = nullptr, *emb_off = nullptr, *emb_cur = nullptr, *emb_blk = nullptr, *rows_of = nullptr;
     double* rstats = nullptr;  // means and deviations of the residual counts of the last rows computed
+    long long* emb_q = nullptr;  // the rounded gradient terms [rows][64] of the last training step
+    int emb_q_rows = 0;
     size_t rows_of_cap = 0;
 };
 
@@ -1000,7 +1007,17 @@ int forward(gapa_surrogate* s, const int32_t* pop, int rows, int k, bool keep, c
 }
 
 // Lists of rows per node for B rows of k genes (rows_of holds B * k entries).
-int ensure_csr(gapa_surrogate* s, size_t cells) {
+int ensure_csr(gapa_surrogate* s, size_t cells, int rows) {
+    if (rows > s->emb_q_rows) {
+        cudaFree(s->emb_q);
+        s->emb_q = nullptr;
+        s->emb_q_rows = 0;
+        if (cudaMalloc(&s->emb_q, (size_t)std::max(rows, 1) * kEmb * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return gapa_fail(GAPA_ERR_OOM, "embedding-gradient terms of %d rows", rows);
+        }
+        s->emb_q_rows = rows;
+    }
     if (cells <= s->rows_of_cap) return GAPA_OK;
     cudaFree(s->rows_of);
     s->rows_of = nullptr;
@@ -1016,7 +1033,7 @@ int ensure_csr(gapa_surrogate* s, size_t cells) {
 // The embedding gradient of a batch into s->Gi (fixed point): count, scan, fill, gather.
 int emb_gradient(gapa_surrogate* s, const int32_t* pop, int B, int k, cudaStream_t st) {
     const size_t cells = (size_t)B * k;
-    int rc = ensure_csr(s, cells);
+    int rc = ensure_csr(s, cells, B);
     if (rc != GAPA_OK) return rc;
     const int n = s->n, nb = (n + 1023) / 1024, grid = s->ctx->num_sms * 4;
     GAPA_CUDA(cudaMemsetAsync(s->emb_cnt, 0, (size_t)n * 4, st));
@@ -1025,8 +1042,8 @@ int emb_gradient(gapa_surrogate* s, const int32_t* pop, int B, int k, cudaStream
     scan_top_kernel<<<1, 1024, 0, st>>>(s->emb_blk, nb);
     scan_add_kernel<<<grid, 256, 0, st>>>(s->emb_off, s->emb_blk, s->emb_cnt, n, s->emb_cur);
     emb_fill_kernel<<<grid, 256, 0, st>>>(pop, cells, std::max(k, 1), n, s->emb_cur, s->rows_of);
-    emb_gather_kernel<<<grid * 2, 256, 0, st>>>(s->emb_off, s->rows_of, s->dX, 1.f / sqrtf((float)std::max(k, 1)), n,
-                                               s->Gi);
+    emb_terms_kernel<<<(B * kEmb + 255) / 256, 256, 0, st>>>(s->dX, B, 1.f / sqrtf((float)std::max(k, 1)), s->emb_q);
+    emb_gather_kernel<<<grid * 2, 256, 0, st>>>(s->emb_off, s->rows_of, s->emb_q, n, s->Gi);
     GAPA_CUDA(cudaGetLastError());
     return GAPA_OK;
 }
@@ -1036,7 +1053,7 @@ int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float*
                const ResidRow* resid = nullptr) {
     int rc = forward(s, pop, B, k, true, st, resid);
     if (rc != GAPA_OK) return rc;
-    ProfileScope prof(s->ctx, st, 2, 18);
+    ProfileScope prof(s->ctx, st, 2, 19);
     float* G = s->G;
     const Layout& L = s->L;
     loss_kernel<<<1, 256, 0, st>>>(s->y, t, B, s->dy, s->loss);
@@ -1122,7 +1139,7 @@ void free_surrogate(gapa_surrogate* s) {
     void* ps[] = {s->P, s->M, s->V, s->G, s->Gi, s->W1b, s->W1tb, s->W2b, s->W2tb, s->Eb, s->logdeg, s->deg,
                   s->X, s->XT, s->H1, s->H1T, s->H2, s->dZ2, s->dZ2T, s->dZ1, s->dZ1T, s->y, s->dy, s->dX,
                   s->loss, s->tbuf, s->batch_rows, s->stats, s->resid, s->nbr, s->emb_cnt, s->emb_off,
-                  s->emb_cur, s->emb_blk, s->rows_of, s->rstats};
+                  s->emb_cur, s->emb_blk, s->rows_of, s->rstats, s->emb_q};
     for (void* p : ps) cudaFree(p);
 }
 
@@ -1344,7 +1361,7 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
         return gapa_fail(GAPA_ERR_OOM, "surrogate run buffers");
     }
     if (s && ((rc = ensure_rows(s, std::max(lam, s->cfg.batch))) != GAPA_OK ||
-              (rc = ensure_csr(s, (size_t)s->cfg.batch * k)) != GAPA_OK)) {
+              (rc = ensure_csr(s, (size_t)s->cfg.batch * k, s->cfg.batch)) != GAPA_OK)) {
         cleanup();
         return rc;
     }
