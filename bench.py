@@ -401,7 +401,7 @@ def set_kernel(ctx, args):
     choice = getattr(args, "fitness_kernel", "auto")
     if choice != "auto":
         ctx.set_fitness_kernel({"tree_local": gp.FITNESS_TREE_LOCAL, "tree": gp.FITNESS_TREE,
-                                "piece": gp.FITNESS_PIECE}[choice])
+                                "piece": gp.FITNESS_PIECE, "sparse": gp.FITNESS_SPARSE}[choice])
 
 
 def run_workload(args, env: Env):
@@ -966,7 +966,7 @@ def main():
     ap.add_argument("--mode", choices=["split", "independent"], default="split",
                     help="with several ranks: split one population by members (default) or evolve independent "
                          "populations per rank")
-    ap.add_argument("--fitness-kernel", choices=["auto", "tree_local", "tree", "piece"], default="auto",
+    ap.add_argument("--fitness-kernel", choices=["auto", "tree_local", "tree", "piece", "sparse"], default="auto",
                     help="fitness kernel of the contexts (default: the library's choice)")
     ap.add_argument("--gens", type=int, default=0,
                     help="generations per run of the batched and surrogate workloads (default: the workload's; "

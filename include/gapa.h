@@ -303,10 +303,10 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
  * outside it scan their whole adjacency; EDGES runs union-find over every
  * undirected edge.  AUTO (the default) is TREE_LOCAL where it applies and
  * the graph has more than 2048 nodes, else TREE.  Where the labels do not fit
- * in shared memory (n above about 56,000 on GB300), the TREE settings run the
- * same phases on labels in global memory, eight members interleaved per
- * 32-byte sector, and EDGES and SAMPLED run one CTA per member over a global
- * label array. */
+ * in shared memory (n above about 56,000 on GB300), AUTO runs SPARSE
+ * (below), the TREE settings run the same phases on labels in global memory,
+ * eight members interleaved per 32-byte sector, and EDGES and SAMPLED run one
+ * CTA per member over a global label array. */
 #define GAPA_FITNESS_AUTO 0
 #define GAPA_FITNESS_EDGES 1
 #define GAPA_FITNESS_SAMPLED 2
@@ -324,6 +324,24 @@ int gapa_run_surrogate(gapa_ctx* ctx, const gapa_config* cfg, gapa_surrogate* sg
  * nodes, or beyond the kernel's shared-memory capacities, run the TREE_LOCAL
  * kernel instead.  Same graphs as TREE_LOCAL; PC and MCN objectives. */
 #define GAPA_FITNESS_PIECE 7
+/* SPARSE (AUTO's choice where the labels do not fit in shared memory, and
+ * selectable on any graph): work proportional to what the deletion disturbs.
+ * In the BFS forest every live child of a deleted node ("top") re-picks its
+ * first live lower-numbered neighbour and hops to the first top or tree root
+ * above that neighbour; hops decrease, so chains end at terminals (live tree
+ * roots, or tops that re-picked nothing) whose chained pieces are joined;
+ * tops chained to the latter unite their terminal's class with those of a
+ * few live neighbours (neighbour sampling).  Per touched component the class
+ * of one reference terminal (the root if live, else the terminal carrying
+ * the most subtree nodes) is kept whole; the pieces of the other classes are
+ * listed, their arcs unite classes, and PC follows from the graph's PC, the
+ * touched components' sizes and the classes apart from the reference.  One
+ * CTA per member with the deletion bitmap, the deleted nodes and their child
+ * offsets in shared memory (n/8 + 8k bytes + 12 KB: n = 2^20 with k up to
+ * about 12,000 on GB300; otherwise the TREE setting runs), per-CTA state in
+ * library-owned global scratch (32 bytes per node per resident CTA), cleared
+ * after each member.  PC and MCN objectives. */
+#define GAPA_FITNESS_SPARSE 8
 int gapa_set_fitness_kernel(gapa_ctx* ctx, int variant);
 
 /* Fitness objective of the context (all minimised; the end of Section III-C

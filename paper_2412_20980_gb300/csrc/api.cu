@@ -57,6 +57,11 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.lo_ptr);
     cudaFree(g.lo_col);
     cudaFree(g.palt);
+    cudaFree(g.sp_kids);
+    cudaFree(g.sp_croot);
+    cudaFree(g.sp_csize);
+    cudaFree(g.sp_sub);
+    cudaFree(g.sp_bysize);
     g = DeviceGraph();
 }
 
@@ -660,6 +665,7 @@ int gapa_create(gapa_ctx** out, int device, void* cuda_stream) {
         return bail(gapa_fail(GAPA_ERR_OOM, "run counters"));
     int rc = gapa_fitness_kernels_init(c);
     if (rc == GAPA_OK) rc = gapa_sixdst_init(c);
+    if (rc == GAPA_OK) rc = gapa_sparse_init(c);
     if (rc == GAPA_OK) rc = gapa_ga_kernels_init(c);
     if (rc != GAPA_OK) return bail(rc);
     *out = c;
@@ -674,6 +680,7 @@ void gapa_destroy(gapa_ctx* c) {
     cudaFree(c->status);
     cudaFree(c->labels);
     cudaFree(c->ig_aux);
+    cudaFree(c->sp_scratch);
     cudaFree(c->sdst_buf);
     for (auto p : c->stage_pop) cudaFree(p);
     for (auto p : c->stage_fit) cudaFree(p);
@@ -698,6 +705,49 @@ void gapa_destroy(gapa_ctx* c) {
 int gapa_set_stream(gapa_ctx* c, void* s) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
     c->stream = (cudaStream_t)s;
+    return GAPA_OK;
+}
+
+// Tables of the sparse fitness kernel from the BFS forest: children as (first, count) (BFS
+// numbers them consecutively), the root of every node's tree (in BFS order every component is one
+// tree), component sizes at their roots, subtree sizes, the roots by decreasing size (ties: lower
+// root) and the sum over components of C(size, 2).  Left null if some node's children are not
+// consecutive.
+int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
+    std::vector<int2> kids((size_t)n, make_int2(0, 0));
+    for (int32_t x = 0; x < n; ++x) {
+        const int32_t p = bf.tparent[x];
+        if (p == x) continue;
+        int2& kp = kids[p];
+        if (kp.y == 0) kp.x = x;
+        else if (kp.x + kp.y != x) return GAPA_OK;  // not consecutive: no sparse kernel on this graph
+        kp.y += 1;
+    }
+    std::vector<int32_t> croot((size_t)n), csize((size_t)n, 0), sub((size_t)n, 1), roots;
+    for (int32_t x = 0; x < n; ++x) {
+        const int32_t p = bf.tparent[x];
+        croot[x] = p == x ? x : croot[p];
+        csize[croot[x]] += 1;
+        if (p == x) roots.push_back(x);
+    }
+    for (int32_t x = n - 1; x >= 0; --x)
+        if (bf.tparent[x] != x) sub[bf.tparent[x]] += sub[x];
+    std::stable_sort(roots.begin(), roots.end(), [&](int32_t a, int32_t b) { return csize[a] > csize[b]; });
+    long long pc0 = 0;
+    for (int32_t r : roots) pc0 += (long long)csize[r] * (csize[r] - 1) / 2;
+    auto up = [](void** dst, const void* src, size_t bytes) {
+        return cudaMalloc(dst, std::max<size_t>(bytes, 16)) == cudaSuccess &&
+               (bytes == 0 || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess);
+    };
+    if (!(up((void**)&g.sp_kids, kids.data(), sizeof(int2) * (size_t)n) &&
+          up((void**)&g.sp_croot, croot.data(), 4 * (size_t)n) && up((void**)&g.sp_csize, csize.data(), 4 * (size_t)n) &&
+          up((void**)&g.sp_sub, sub.data(), 4 * (size_t)n) &&
+          up((void**)&g.sp_bysize, roots.data(), 4 * roots.size()))) {
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "sparse fitness tables of %d nodes", n);
+    }
+    g.sp_ncomp = (int)roots.size();
+    g.sp_pc0 = pc0;
     return GAPA_OK;
 }
 
@@ -883,6 +933,13 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     }
     if (!bf.lo_col.empty())
         GAPA_CUDA(cudaMemcpy(g.lo_col, bf.lo_col.data(), sizeof(int32_t) * bf.lo_col.size(), cudaMemcpyHostToDevice));
+    {
+        const int frc = upload_sparse_tables(bf, n, g);
+        if (frc != GAPA_OK) {
+            free_graph(g);
+            return frc;
+        }
+    }
     {
         // full adjacency in BFS numbers (the scans of the nodes outside the giant piece): 16-bit ids
         // for the shared-memory kernel, 32-bit ids for the global-label one
@@ -1108,7 +1165,7 @@ int gapa_run(gapa_ctx* c, const gapa_config* cfg, int32_t* best_set_host, int64_
 
 int gapa_set_fitness_kernel(gapa_ctx* c, int variant) {
     if (!c) return gapa_fail(GAPA_ERR_INVALID_ARG, "ctx is NULL");
-    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_PIECE)
+    if (variant < GAPA_FITNESS_AUTO || variant > GAPA_FITNESS_SPARSE)
         return gapa_fail(GAPA_ERR_INVALID_ARG, "unknown fitness kernel %d", variant);
     c->fitness_variant = variant;
     return GAPA_OK;

@@ -726,9 +726,20 @@ int launch_piece(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, in
 
 }  // namespace
 
+// The sparse kernel: on request, and by AUTO where the labels exceed shared memory.
+static bool sparse_selected(const gapa_ctx* c) {
+    return c->g.sp_kids != nullptr &&
+           (c->fitness_variant == GAPA_FITNESS_SPARSE ||
+            (c->fitness_variant == GAPA_FITNESS_AUTO && !c->g.packed16 && (size_t)c->g.n * 4 > c->fit_smem_max));
+}
+
 int gapa_fitness_prepare(gapa_ctx* c, int s) {
     const size_t lab_bytes = (size_t)c->g.n * 4;
     const bool tree = c->fitness_variant != GAPA_FITNESS_EDGES && c->fitness_variant != GAPA_FITNESS_SAMPLED;
+    if (sparse_selected(c)) {
+        int rc = gapa_sparse_prepare(c);
+        if (rc != GAPA_OK) return rc;
+    }
     if (tree) return (c->g.packed16 || lab_bytes <= c->fit_smem_max) ? GAPA_OK : gapa_ig_prepare(c, s);
     if (lab_bytes <= c->fit_smem_max) return GAPA_OK;
     // global labels: process members in waves of at most `wave` CTAs
@@ -835,6 +846,7 @@ int gapa_launch_fitness(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* 
         GAPA_CUDA(cudaGetLastError());
         return GAPA_OK;
     }
+    if (sparse_selected(c) && gapa_sparse_fits(c, k)) return gapa_launch_fitness_sparse(c, pop, s, k, fit, st, &prof.kernels);
     switch (c->fitness_variant) {
         case GAPA_FITNESS_EDGES:
             return launch_variant<V_EDGES>(c, ga, pop, s, k, f, st);
@@ -868,14 +880,13 @@ int gapa_fitness_kernels_init(gapa_ctx* c) {
 // ---------------------------------------------------------------------------
 // Allocation-free fitness (gapa_fitness_noalloc).
 //
-// For callers that must not allocate device memory: code that runs while a
-// framework captures the stream into a CUDA graph (where cudaMalloc is not
-// allowed), latency-critical loops that cannot take cudaMalloc's implicit
-// synchronisation, and processes whose device memory is owned by another
-// allocator under a fixed budget.  The caller passes the graph as a device
-// edge list and the population and output as device arrays; the label
-// scratch is the file-scope array below, which every GPU that loads this
-// library holds until the process exits.
+// For callers that must not allocate device memory: latency-critical loops
+// that cannot take cudaMalloc's implicit synchronisation, and processes whose
+// device memory is owned by another allocator under a fixed budget.  The call
+// blocks (it reads the status word back and synchronises the stream).  The
+// caller passes the graph as a device edge list and the population and output
+// as device arrays; the label scratch is the file-scope array below, which
+// every GPU that loads this library holds until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 

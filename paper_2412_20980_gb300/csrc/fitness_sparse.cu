@@ -1,0 +1,715 @@
+// Sparse fitness: work proportional to what a member's deletion disturbs,
+// for graphs whose labels do not fit in shared memory (Section III-C, Eq. 13;
+// PC(G) and MCN of Table "Whole").
+//
+// The upload's BFS forest numbers every component from its top hub, so a
+// node's tree parent is its lowest-numbered neighbour and a node's children
+// carry consecutive numbers.  Deleting a member's set D cuts each touched
+// component's tree into pieces: the root's piece (root live) and one piece
+// below every live child of a deleted node (a "top").  Per member:
+//  1. deletion bitmap in shared memory; the distinct deleted nodes listed;
+//     each touched component counts its deleted nodes;
+//  2. every top re-picks its first live lower-numbered neighbour q (none: the
+//     top is a terminal of its own) and hops to the first top or tree root
+//     met walking up the tree from q.  Hops strictly decrease, so following
+//     them ends at a terminal (a live tree root or a top that re-picked
+//     nothing), and the pieces whose chains end at one terminal are joined;
+//  3. terminals form classes (union-find): every top chained to a top that
+//     re-picked nothing unites that terminal's class with the terminals of
+//     its first live neighbours outside its piece (neighbour sampling: after
+//     the top hub is deleted, thousands of its children re-pick nothing and
+//     would otherwise each list a whole subtree); per touched component the
+//     class of one reference terminal becomes R: the root if it is live,
+//     else the terminal whose chained tops carry the most subtree nodes (any
+//     choice is exact; this one keeps the lists short);
+//  4. the pieces of the classes other than R are listed, grown down the tree
+//     from their tops; every listed node's arcs unite classes (an arc to an
+//     unlisted live node joins R, since every unlisted live node of the
+//     component lies in R's class);
+//  5. classes apart from R count their listed nodes; R's set is the
+//     component's size less its deleted nodes less those classes, so
+//     PC = PC(G) - sum over touched components of C(size, 2) + the new terms
+//     (MCN: the largest of those and of the largest untouched component).
+// Nothing inside a piece that stays joined is read, and nothing is done per
+// node of the graph.  One CTA per member at a time, persistent over a work
+// queue; its per-node state (hops, classes, counts, per-component sums) lives
+// in the CTA's own slice of global scratch, which it clears after every
+// member (entries start as -1 / 0 when the scratch is allocated).
+#include <climits>
+
+#include "gapa_internal.cuh"
+#include "tree16.cuh"
+
+namespace {
+
+using gapa_dev::bm_test;
+using gapa_dev::objective_add;
+using gapa_dev::Team;
+using gapa_dev::team_sum_ll;
+using gapa_dev::tree16l_owner;
+using gapa_dev::tree16l_scan;
+
+constexpr int kSpBlock = 1024;
+constexpr unsigned kSpFirst = 0x80000000u;  // D entry flag: first deletion seen in its component
+constexpr int kSpLinkScan = 4;              // adjacency entries a top samples for links
+constexpr int kSpInFlight = 4;              // tops per thread resolved together in the re-pick pass
+
+template <typename Col>
+struct SpGraph {
+    int n;
+    const int* perm;      // original id -> BFS number
+    const int* tparent;   // tree parent (roots: itself)
+    const int2* palt;     // (tree parent, second lower-numbered neighbour or -1)
+    const int* lo_ptr;    // lower-numbered neighbours, ascending (CSR)
+    const int* lo_col;
+    const int* fptr;      // full adjacency in BFS numbers (CSR)
+    const Col* fcol;
+    const int2* kids;     // (first child, number of children)
+    const int* croot;     // root of the node's component tree
+    const int* csize;     // size of the component, at its root
+    const int* sub;       // subtree size
+    const int* bysize;    // component roots by decreasing size (MCN)
+    int ncomp;
+    long long pc0;        // sum over components of C(size, 2)
+    int objective;        // 0: PC, 1: MCN
+};
+
+// One CTA's slice of the scratch (n entries each).  Reads go through L2 only
+// (__ldcg; a slice moves between SMs from one launch to the next, and within
+// a phase the union-find entries change under other threads' atomics); what a
+// phase writes, later phases read after a barrier.
+struct SpSlot {
+    int* hop;                  // live tops: hop, then terminal; -1 elsewhere
+    int* cls;                  // terminals: class link (terminal + 1; 0 = R); listed nodes: their class; -1 elsewhere
+    unsigned* cnt;             // terminals: chained subtree weight, then class size; 0 elsewhere
+    int* list;                 // listed nodes
+    int* tl;                   // live tops
+    unsigned long long* cacc;  // component roots: deleted << 32 | nodes apart from R; 0 elsewhere
+    unsigned long long* best;  // component roots whose root is deleted: weight << 32 | ~terminal
+};
+
+__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned ldcg(const unsigned* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ldcg(const unsigned long long* p) { return __ldcg(p); }
+
+__host__ __device__ __forceinline__ size_t sp_bitmap_bytes(int n) { return ((((size_t)n + 31) >> 5) * 4 + 15) & ~(size_t)15; }
+__host__ __device__ __forceinline__ size_t sp_smem_bytes(int n, int k) {
+    return sp_bitmap_bytes(n) + (((size_t)2 * k + 1) * 4 + 15) / 16 * 16 + (size_t)3 * kSpBlock * 4;
+}
+
+// Class of value a (terminal + 1; 0 = R): the root's value r, with the links
+// on the way that still lie below r pointed at it.  Links always point to
+// smaller values and only ever move to ancestors, so a link above r (another
+// thread compressed past r after r was hooked) ends the compression: every
+// node written lies strictly between a and r on a's path, and r is its
+// ancestor.
+__device__ __forceinline__ int sp_find(int* cls, int a) {
+    int r = a;
+    while (r != 0) {
+        const int p = ldcg(&cls[r - 1]);
+        if (p == r) break;
+        r = p;
+    }
+    while (a > r) {
+        const int p = ldcg(&cls[a - 1]);
+        if (p <= r) break;
+        cls[a - 1] = r;
+        a = p;
+    }
+    return r;
+}
+
+// Union of two classes: the larger value hooks under the smaller, so R (0) is never hooked.
+__device__ __forceinline__ void sp_unite(int* cls, int a, int b) {
+    a = sp_find(cls, a);
+    b = sp_find(cls, b);
+    while (a != b) {
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS(&cls[a - 1], a, b);
+        if (old == a) return;
+        a = sp_find(cls, old);
+        b = sp_find(cls, b);
+    }
+}
+
+// Warp-aggregated append of v (where want) to a list; called by all lanes.
+__device__ __forceinline__ void sp_append(bool want, int v, int lane, int* count, int* list) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    int first = 0;
+    if (lane == 0) first = atomicAdd(count, __popc(m));
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (want) list[first + __popc(m & ((1u << lane) - 1))] = v;
+}
+
+// The terminal of live node w's piece: walk up to the first top (its terminal) or tree root.
+template <typename Col>
+__device__ __forceinline__ int sp_terminal_of(const SpGraph<Col>& g, const unsigned* dead, const int* hop, int w,
+                                              int p) {
+    while (true) {
+        if (p == w) return w;
+        if (bm_test(dead, p)) return ldcg(&hop[w]);
+        w = p;
+        p = __ldg(&g.tparent[w]);
+    }
+}
+
+template <typename Col>
+__global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, SpSlot base, size_t stride,
+                                                               const int* __restrict__ pop, int s, int k,
+                                                               long long* __restrict__ fit, int* head, int* status) {
+    extern __shared__ __align__(16) unsigned char sp_smem[];
+    __shared__ long long red[32];
+    __shared__ int s_member, s_nd, s_nt, s_nlist;
+    const Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
+    const int tid = tm.tid, T = tm.T, lane = tid & 31, n = g.n;
+    const int words = (n + 31) >> 5;
+    unsigned* dead = reinterpret_cast<unsigned*>(sp_smem);
+    int* D = reinterpret_cast<int*>(sp_smem + sp_bitmap_bytes(n));
+    int* Doff = D + k;  // nd + 1 entries
+    int* s_off = reinterpret_cast<int*>(sp_smem + sp_smem_bytes(n, k) - (size_t)3 * kSpBlock * 4);
+    int* s_first = s_off + T;
+    int* s_val = s_first + T;
+    int* ws = reinterpret_cast<int*>(red);
+    const size_t o = (size_t)blockIdx.x * stride;
+    int* const hop = base.hop + o;
+    int* const cls = base.cls + o;
+    unsigned* const cnt = base.cnt + o;
+    int* const list = base.list + o;
+    int* const tl = base.tl + o;
+    unsigned long long* const cacc = base.cacc + o;
+    unsigned long long* const best = base.best + o;
+    constexpr int F = kSpInFlight;
+
+    for (;;) {
+        if (tid == 0) {
+            s_member = atomicAdd(head, 1);
+            s_nd = 0;
+            s_nt = 0;
+            s_nlist = 0;
+        }
+        for (int w = tid; w < words; w += T) dead[w] = 0u;
+        tm.sync();
+        const int m = s_member;
+        if (m >= s) break;
+        const int* genes = pop + (size_t)m * k;
+
+        // 1. perturbation P^(A, p) of Eq. 13 in BFS numbering; distinct deleted nodes listed
+        for (int j0 = 0; j0 < k; j0 += F * T) {
+            int b[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                const int j = j0 + u * T + tid;
+                b[u] = -1;
+                if (j < k) {
+                    const int d = __ldg(&genes[j]);
+                    if ((unsigned)d < (unsigned)n) b[u] = d;
+                    else atomicOr(status, GAPA_DEV_BAD_GENE);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u)
+                if (b[u] >= 0) b[u] = __ldg(&g.perm[b[u]]);
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                bool fresh = false;
+                if (b[u] >= 0) {
+                    const unsigned bit = 1u << (b[u] & 31);
+                    fresh = !(atomicOr(&dead[b[u] >> 5], bit) & bit);
+                }
+                sp_append(fresh, b[u], lane, &s_nd, D);
+            }
+        }
+        tm.sync();
+        const int nd = s_nd;
+        // children per deleted node -> offsets of the tops; deleted nodes per touched component
+        int ntops;
+        {
+            const int per = (nd + T - 1) / T, lo = min(nd, tid * per), hi = min(nd, lo + per);
+            int sum = 0;
+#pragma unroll 4
+            for (int i = lo; i < hi; ++i) sum += __ldg(&g.kids[D[i]].y);
+            int at = tree16l_scan(tm, sum, ws, &ntops);
+            for (int i = lo; i < hi; ++i) {
+                Doff[i] = at;
+                at += __ldg(&g.kids[D[i]].y);
+            }
+            tm.sync();  // the flags below go into D's entries
+            if (tid == 0) Doff[nd] = ntops;
+        }
+        for (int i0 = tid & ~31; i0 < nd; i0 += T) {
+            const int i = i0 + lane;
+            const int c = i < nd ? __ldg(&g.croot[D[i]]) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, c);
+            if (c >= 0 && lane == __ffs(peers) - 1) {
+                const unsigned long long old = atomicAdd(&cacc[c], (unsigned long long)__popc(peers) << 32);
+                if (old == 0ull) {
+                    D[i] = (int)((unsigned)D[i] | kSpFirst);
+                    if (!bm_test(dead, c)) cls[c] = c + 1;  // a live tree root is a terminal
+                }
+            }
+        }
+        tm.sync();
+
+        // 2. re-pick and hop of every top; the live tops are also listed compactly (tl) for the
+        // passes below.  F tops per thread are resolved together (their loads overlap).
+        for (int base_i = 0; base_i < ntops; base_i += F * T) {
+            int t[F], q[F], y[F];
+            int2 pa[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                const int i = base_i + u * T + tid;
+                t[u] = -1;
+                if (i < ntops) {
+                    const int ow = tree16l_owner(Doff, nd, i);
+                    t[u] = __ldg(&g.kids[(unsigned)D[ow] & ~kSpFirst].x) + i - Doff[ow];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                if (t[u] >= 0 && bm_test(dead, t[u])) t[u] = -1;  // a deleted child is no top
+                pa[u] = t[u] >= 0 ? __ldg(&g.palt[t[u]]) : make_int2(0, -1);
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                q[u] = t[u];
+                if (t[u] < 0 || pa[u].y < 0) continue;
+                if (!bm_test(dead, pa[u].y)) {
+                    q[u] = pa[u].y;
+                } else {
+                    const int end = __ldg(&g.lo_ptr[t[u] + 1]);
+                    for (int e = __ldg(&g.lo_ptr[t[u]]) + 2; e < end; ++e) {
+                        const int w = __ldg(&g.lo_col[e]);
+                        if (!bm_test(dead, w)) {
+                            q[u] = w;
+                            break;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u) y[u] = q[u] != t[u] ? __ldg(&g.tparent[q[u]]) : -1;
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                if (t[u] < 0) continue;
+                if (q[u] == t[u]) {
+                    hop[t[u]] = t[u];
+                    continue;
+                }
+                int x = q[u], p = y[u];  // walk up to the first top or tree root
+                while (p != x && !bm_test(dead, p)) {
+                    x = p;
+                    p = __ldg(&g.tparent[x]);
+                }
+                hop[t[u]] = x;
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u) sp_append(t[u] >= 0, t[u], lane, &s_nt, tl);
+        }
+        tm.sync();
+        const int nt = s_nt;
+        // terminal of every top (chains followed F at a time, then compressed); subtree weight of
+        // the chained tops at terminals whose component root is deleted
+        for (int base_j = 0; base_j < nt; base_j += F * T) {
+            int t[F], x[F];
+            bool act[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                const int j = base_j + u * T + tid;
+                t[u] = j < nt ? ldcg(&tl[j]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                act[u] = t[u] >= 0 && x[u] != t[u];
+                any |= act[u];
+            }
+            while (any) {
+                int h[F];
+#pragma unroll
+                for (int u = 0; u < F; ++u) h[u] = act[u] ? ldcg(&hop[x[u]]) : 0;
+                any = false;
+#pragma unroll
+                for (int u = 0; u < F; ++u) {
+                    if (!act[u]) continue;
+                    if (h[u] == -1 || h[u] == x[u]) {
+                        act[u] = false;
+                    } else {
+                        x[u] = h[u];
+                        any = true;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                int key = -1;
+                unsigned wgt = 0;
+                if (t[u] >= 0) {
+                    if (x[u] == t[u]) cls[t[u]] = t[u] + 1;  // a top that re-picked nothing is a terminal
+                    else hop[t[u]] = x[u];
+                    // x is a top that re-picked nothing, or a live tree root (never weighed)
+                    if (bm_test(dead, __ldg(&g.croot[x[u]]))) {
+                        key = x[u];
+                        wgt = (unsigned)__ldg(&g.sub[t[u]]);
+                    }
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const unsigned tot = __reduce_add_sync(peers, wgt);
+                if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], tot);
+            }
+        }
+        tm.sync();
+
+        // sampled links: a top that re-picked nothing unites its class with the classes of its first
+        // live neighbours outside its own piece (at most two)
+        for (int j0 = tid; j0 < nt; j0 += F * T) {
+            int t[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) t[u] = j0 + u * T < nt ? ldcg(&tl[j0 + u * T]) : -1;
+#pragma unroll
+            for (int u = 0; u < F; ++u)
+                if (t[u] >= 0 && ldcg(&hop[t[u]]) != t[u]) t[u] = -1;
+#pragma unroll 1
+            for (int u = 0; u < F; ++u) {
+                if (t[u] < 0) continue;
+                const int beg = __ldg(&g.fptr[t[u]]);
+                const int cntw = min(__ldg(&g.fptr[t[u] + 1]) - beg, kSpLinkScan);
+                int w[kSpLinkScan], pw[kSpLinkScan];
+#pragma unroll
+                for (int e = 0; e < kSpLinkScan; ++e) w[e] = e < cntw ? (int)__ldg(&g.fcol[beg + e]) : -1;
+#pragma unroll
+                for (int e = 0; e < kSpLinkScan; ++e) {
+                    if (w[e] >= 0 && bm_test(dead, w[e])) w[e] = -1;
+                    pw[e] = w[e] >= 0 ? __ldg(&g.tparent[w[e]]) : -1;
+                }
+                int links = 0;
+#pragma unroll
+                for (int e = 0; e < kSpLinkScan; ++e) {
+                    if (w[e] < 0 || pw[e] == t[u] || links == 2) continue;
+                    sp_unite(cls, t[u] + 1, sp_terminal_of(g, dead, hop, w[e], pw[e]) + 1);
+                    ++links;
+                }
+            }
+        }
+        tm.sync();
+
+        // 3. reference terminal of components whose root is deleted
+        for (int j0 = tid; j0 < nt; j0 += F * T) {
+            int t[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) t[u] = j0 + u * T < nt ? ldcg(&tl[j0 + u * T]) : -1;
+#pragma unroll
+            for (int u = 0; u < F; ++u)
+                if (t[u] >= 0 && ldcg(&hop[t[u]]) != t[u]) t[u] = -1;
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                if (t[u] < 0) continue;
+                const int c = __ldg(&g.croot[t[u]]);
+                if (bm_test(dead, c))
+                    atomicMax(&best[c], ((unsigned long long)ldcg(&cnt[t[u]]) << 32) | (unsigned long long)(~(unsigned)t[u]));
+            }
+        }
+        tm.sync();
+        // the reference's class becomes R (one thread per touched component; classes never span two)
+        for (int i = tid; i < nd; i += T) {
+            if (!((unsigned)D[i] & kSpFirst)) continue;
+            const int c = __ldg(&g.croot[(int)((unsigned)D[i] & ~kSpFirst)]);
+            int r;
+            if (!bm_test(dead, c)) {
+                r = c + 1;
+            } else {
+                const unsigned long long bk = ldcg(&best[c]);
+                if (bk == 0ull) continue;  // no live node left in the component
+                r = (int)(~(unsigned)(bk & 0xFFFFFFFFull)) + 1;
+            }
+            r = sp_find(cls, r);
+            while (r != 0) {
+                const int old = atomicCAS(&cls[r - 1], r, 0);
+                if (old == r) break;
+                r = sp_find(cls, old);
+            }
+        }
+        tm.sync();
+
+        // 4. listing: tops whose class is not R, then their pieces down the tree
+        for (int base_j = 0; base_j < nt; base_j += F * T) {
+            int t[F], x[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                const int j = base_j + u * T + tid;
+                t[u] = j < nt ? ldcg(&tl[j]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                bool want = false;
+                if (t[u] >= 0) {
+                    if (x[u] == t[u]) cnt[t[u]] = 0u;  // the weight has served
+                    if (sp_find(cls, x[u] + 1) != 0) {
+                        if (x[u] != t[u]) cls[t[u]] = x[u] + 1;  // a terminal keeps its class link
+                        want = true;
+                    }
+                }
+                sp_append(want, t[u], lane, &s_nlist, list);
+            }
+        }
+        tm.sync();
+        {
+            int head_i = 0, tail = s_nlist;
+            while (head_i < tail) {
+                for (int u0 = head_i; u0 < tail; u0 += T) {
+                    const int idx = u0 + tid;
+                    int2 ch = make_int2(0, 0);
+                    int cl = 0;
+                    if (idx < tail) {
+                        const int u = ldcg(&list[idx]);
+                        ch = __ldg(&g.kids[u]);
+                        cl = ldcg(&cls[u]);
+                    }
+                    int total;
+                    const int off = tree16l_scan(tm, ch.y, ws, &total);
+                    s_off[tid] = off;
+                    s_first[tid] = ch.x;
+                    s_val[tid] = cl;
+                    tm.sync();
+                    const int owners = min(T, tail - u0);
+                    for (int i0 = tid & ~31; i0 < total; i0 += T) {
+                        const int i = i0 + lane;
+                        bool want = false;
+                        int x = 0;
+                        if (i < total) {
+                            const int ow = tree16l_owner(s_off, owners, i);
+                            x = s_first[ow] + i - s_off[ow];
+                            if (!bm_test(dead, x)) {
+                                cls[x] = s_val[ow];
+                                want = true;
+                            }
+                        }
+                        sp_append(want, x, lane, &s_nlist, list);
+                    }
+                    tm.sync();
+                }
+                head_i = tail;
+                tail = s_nlist;
+                tm.sync();  // every thread has read the length before the next round appends
+            }
+        }
+        const int nl = s_nlist;
+
+        // join along the listed nodes' arcs (a class already joined to R scans nothing)
+        for (int v0 = 0; v0 < nl; v0 += T) {
+            const int idx = v0 + tid;
+            int v = 0, b = 0, d = 0;
+            if (idx < nl) {
+                v = ldcg(&list[idx]);
+                if (sp_find(cls, ldcg(&cls[v])) != 0) {
+                    b = __ldg(&g.fptr[v]);
+                    d = __ldg(&g.fptr[v + 1]) - b;
+                }
+            }
+            int total;
+            const int off = tree16l_scan(tm, d, ws, &total);
+            s_off[tid] = off;
+            s_first[tid] = b;
+            s_val[tid] = v;
+            tm.sync();
+            const int owners = min(T, nl - v0);
+            for (int i = tid; i < total; i += T) {
+                const int ow = tree16l_owner(s_off, owners, i);
+                const int w = (int)__ldg(&g.fcol[s_first[ow] + i - s_off[ow]]);
+                if (bm_test(dead, w)) continue;
+                const int cv = ldcg(&cls[s_val[ow]]), cw = ldcg(&cls[w]);
+                if (cw == -1) sp_unite(cls, cv, 0);
+                else if (cw != cv) sp_unite(cls, cv, cw);
+            }
+            tm.sync();
+        }
+
+        // 5. sizes of the classes apart from R, and per component the nodes apart from R
+        for (int i0 = tid & ~31; i0 < nl; i0 += T) {
+            const int i = i0 + lane;
+            int r = 0, c = -1;
+            if (i < nl) {
+                const int v = ldcg(&list[i]);
+                r = sp_find(cls, ldcg(&cls[v]));
+                if (r != 0) c = __ldg(&g.croot[v]);
+            }
+            const unsigned pr = __match_any_sync(0xffffffffu, r);
+            if (r != 0 && lane == __ffs(pr) - 1) atomicAdd(&cnt[r - 1], (unsigned)__popc(pr));
+            const unsigned pc = __match_any_sync(0xffffffffu, c);
+            if (c >= 0 && lane == __ffs(pc) - 1) atomicAdd(&cacc[c], (unsigned long long)__popc(pc));
+        }
+        tm.sync();
+        const bool mx = g.objective != 0;
+        long long acc = 0;
+        for (int i = tid; i < nl; i += T) {
+            const int v = ldcg(&list[i]);
+            if (ldcg(&cls[v]) == v + 1) acc = objective_add(acc, (long long)ldcg(&cnt[v]), g.objective);
+        }
+        for (int i = tid; i < nd; i += T) {
+            if (!((unsigned)D[i] & kSpFirst)) continue;
+            const int c = __ldg(&g.croot[(int)((unsigned)D[i] & ~kSpFirst)]);
+            const unsigned long long a = ldcg(&cacc[c]);
+            const long long cs = __ldg(&g.csize[c]);
+            const long long rs = cs - (long long)(a >> 32) - (long long)(a & 0xFFFFFFFFull);
+            if (mx) acc = rs > acc ? rs : acc;
+            else acc += rs * (rs - 1) / 2 - cs * (cs - 1) / 2;
+        }
+        long long tot = team_sum_ll(tm, acc, red, mx);
+        if (tid == 0) {
+            if (mx) {
+                // the largest untouched component
+                for (int j = 0; j < g.ncomp; ++j) {
+                    const int c = __ldg(&g.bysize[j]);
+                    if (ldcg(&cacc[c]) == 0ull) {
+                        const long long cs = __ldg(&g.csize[c]);
+                        tot = cs > tot ? cs : tot;
+                        break;
+                    }
+                }
+                fit[m] = tot;
+            } else {
+                fit[m] = g.pc0 + tot;
+            }
+        }
+        tm.sync();
+
+        // clear what this member wrote
+        for (int j0 = tid; j0 < nt; j0 += F * T) {
+            int t[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) t[u] = j0 + u * T < nt ? ldcg(&tl[j0 + u * T]) : -1;
+#pragma unroll
+            for (int u = 0; u < F; ++u)
+                if (t[u] >= 0) {
+                    hop[t[u]] = -1;
+                    cls[t[u]] = -1;
+                }
+        }
+        for (int i0 = tid; i0 < nl; i0 += F * T) {
+            int v[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) v[u] = i0 + u * T < nl ? ldcg(&list[i0 + u * T]) : -1;
+#pragma unroll
+            for (int u = 0; u < F; ++u)
+                if (v[u] >= 0) {
+                    cls[v[u]] = -1;
+                    cnt[v[u]] = 0u;
+                }
+        }
+        for (int i = tid; i < nd; i += T) {
+            if (!((unsigned)D[i] & kSpFirst)) continue;
+            const int c = __ldg(&g.croot[(int)((unsigned)D[i] & ~kSpFirst)]);
+            cacc[c] = 0ull;
+            best[c] = 0ull;
+            cls[c] = -1;
+        }
+        tm.sync();
+    }
+}
+
+template <typename Col>
+SpGraph<Col> sp_graph(const gapa_ctx* c, const Col* fcol) {
+    SpGraph<Col> g;
+    g.n = c->g.n;
+    g.perm = c->g.perm;
+    g.tparent = c->g.tparent;
+    g.palt = c->g.palt;
+    g.lo_ptr = c->g.lo_ptr;
+    g.lo_col = c->g.lo_col;
+    g.fptr = c->g.fptr;
+    g.fcol = fcol;
+    g.kids = c->g.sp_kids;
+    g.croot = c->g.sp_croot;
+    g.csize = c->g.sp_csize;
+    g.sub = c->g.sp_sub;
+    g.bysize = c->g.sp_bysize;
+    g.ncomp = c->g.sp_ncomp;
+    g.pc0 = c->g.sp_pc0;
+    g.objective = c->objective;
+    return g;
+}
+
+}  // namespace
+
+bool gapa_sparse_fits(const gapa_ctx* c, int k) {
+    return c->g.sp_kids != nullptr && c->sp_smem_max > 0 && sp_smem_bytes(c->g.n, k) <= c->sp_smem_max;
+}
+
+int gapa_sparse_init(gapa_ctx* c) {
+    int rc = gapa_set_smem_limit((const void*)cc_sparse_kernel<int>, c->smem_optin, &c->sp_smem_max);
+    size_t other = 0;
+    if (rc == GAPA_OK) rc = gapa_set_smem_limit((const void*)cc_sparse_kernel<unsigned short>, c->smem_optin, &other);
+    if (other < c->sp_smem_max) c->sp_smem_max = other;
+    return rc;
+}
+
+// Scratch of the persistent CTAs: seven n-entry arrays per CTA (hops, classes,
+// counts, listed nodes, live tops: int32; per-component sums and reference
+// keys: int64), set to -1 / 0 once here and left that way by every member.
+int gapa_sparse_prepare(gapa_ctx* c) {
+    const int n = c->g.n;
+    const size_t smem = sp_smem_bytes(n, 0);
+    int per_sm = 0;
+    GAPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cc_sparse_kernel<int>, kSpBlock, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int slots = c->num_sms * per_sm;
+    const size_t stride = ((size_t)n + 63) & ~(size_t)63;
+    const size_t bytes = (size_t)slots * stride * (5 * 4 + 2 * 8) + 64;
+    if (c->sp_scratch && c->sp_scratch_cap >= bytes && c->sp_stride == stride && c->sp_slots <= slots) return GAPA_OK;
+    cudaFree(c->sp_scratch);
+    c->sp_scratch = nullptr;
+    c->sp_scratch_cap = 0;
+    if (cudaMalloc(&c->sp_scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "sparse fitness scratch of %zu bytes", bytes);
+    }
+    c->sp_scratch_cap = bytes;
+    c->sp_stride = stride;
+    c->sp_slots = slots;
+    const size_t ints = (size_t)slots * stride;
+    char* p = static_cast<char*>(c->sp_scratch);
+    // hop, cls = -1; cnt, list, tl = 0; cacc, best = 0; the queue head last
+    GAPA_CUDA(cudaMemset(p, 0xFF, ints * 8));
+    GAPA_CUDA(cudaMemset(p + ints * 8, 0, ints * 12 + ints * 16 + 64));
+    GAPA_CUDA(cudaDeviceSynchronize());
+    return GAPA_OK;
+}
+
+int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
+                               int* kernels) {
+    if (!gapa_sparse_fits(c, k)) return gapa_fail(GAPA_ERR_INVALID_ARG, "sparse fitness: shared memory too small");
+    int rc = gapa_sparse_prepare(c);
+    if (rc != GAPA_OK) return rc;
+    const size_t ints = (size_t)c->sp_slots * c->sp_stride;
+    char* p = static_cast<char*>(c->sp_scratch);
+    SpSlot b;
+    b.hop = reinterpret_cast<int*>(p);
+    b.cls = reinterpret_cast<int*>(p + ints * 4);
+    b.cnt = reinterpret_cast<unsigned*>(p + ints * 8);
+    b.list = reinterpret_cast<int*>(p + ints * 12);
+    b.tl = reinterpret_cast<int*>(p + ints * 16);
+    b.cacc = reinterpret_cast<unsigned long long*>(p + ints * 20);
+    b.best = reinterpret_cast<unsigned long long*>(p + ints * 28);
+    int* head = reinterpret_cast<int*>(p + ints * 36);
+    GAPA_CUDA(cudaMemsetAsync(head, 0, sizeof(int), st));
+    const size_t smem = sp_smem_bytes(c->g.n, k);
+    const int grid = std::min(c->sp_slots, std::max(s, 1));
+    if (c->g.packed16)
+        cc_sparse_kernel<unsigned short><<<grid, kSpBlock, smem, st>>>(sp_graph(c, c->g.fcol16), b, c->sp_stride, pop, s,
+                                                                        k, reinterpret_cast<long long*>(fit), head,
+                                                                        c->status);
+    else
+        cc_sparse_kernel<int><<<grid, kSpBlock, smem, st>>>(sp_graph(c, (const int*)c->g.fcol32), b, c->sp_stride, pop,
+                                                             s, k, reinterpret_cast<long long*>(fit), head, c->status);
+    GAPA_CUDA(cudaGetLastError());
+    if (kernels) *kernels = 1;
+    return GAPA_OK;
+}

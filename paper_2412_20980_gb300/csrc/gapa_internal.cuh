@@ -164,6 +164,17 @@ struct DeviceGraph {
     int mean_deg_x16 = 0;               // 16 * 2E / n, rounded up
     bool packed16 = false;      // n <= 65536
     int bfs_depth = 0;          // largest BFS level
+    // sparse fitness kernel (any n; null when the BFS forest's children are not consecutive):
+    // (first child, number of children), the root of every node's component tree, the
+    // component's size at its root, subtree sizes, the component roots by decreasing size,
+    // their number and the sum over components of C(size, 2)
+    int2* sp_kids = nullptr;
+    int* sp_croot = nullptr;
+    int* sp_csize = nullptr;
+    int* sp_sub = nullptr;
+    int* sp_bysize = nullptr;
+    int sp_ncomp = 0;
+    long long sp_pc0 = 0;
 };
 
 constexpr int kProbe = 8;
@@ -185,6 +196,11 @@ struct gapa_ctx {
     int* status = nullptr;  // device status word
     // scratch owned by the context
     int* labels = nullptr;  // global label scratch for graphs too large for shared memory
+    void* sp_scratch = nullptr;  // per-CTA state of the sparse fitness kernel (hops, classes, counts, lists, sums)
+    size_t sp_scratch_cap = 0;   // bytes
+    size_t sp_stride = 0;        // entries per CTA slice
+    int sp_slots = 0;            // CTA slices
+    size_t sp_smem_max = 0;      // max dynamic shared memory of the sparse fitness kernel
     size_t labels_cap = 0;  // ints
     void* ig_aux = nullptr;  // per-member work counters and giant ids of the global-label fitness
     size_t ig_aux_cap = 0;
@@ -346,6 +362,13 @@ int gapa_sixdst_init(gapa_ctx* c);
 int gapa_launch_selftest_wait(gapa_ctx* c, long long limit, cudaStream_t st);
 int gapa_launch_read_probe(const void* buf, size_t bytes, int passes, int grid, unsigned* sink, cudaStream_t st);
 int gapa_ig_prepare(gapa_ctx* c, int s);
+// Sparse fitness kernel (fitness_sparse.cu): whether its shared memory fits k genes on this
+// context's graph, its one-time set-up, its scratch (outside any capture) and its launch.
+bool gapa_sparse_fits(const gapa_ctx* c, int k);
+int gapa_sparse_init(gapa_ctx* c);
+int gapa_sparse_prepare(gapa_ctx* c);
+int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
+                               int* kernels = nullptr);
 int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);
 int gapa_launch_offspring(gapa_ctx* c, const GaParams& p, const int32_t* pop_in, const int64_t* fit_in,
                           int32_t* pop_out, int64_t* fit_out, cudaStream_t st);

@@ -46,6 +46,7 @@ EXPORTS = [
 FITNESS_AUTO, FITNESS_EDGES, FITNESS_SAMPLED, FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_SCAN = 0, 1, 2, 3, 4, 5
 FITNESS_TREE_LOCAL = 6
 FITNESS_PIECE = 7
+FITNESS_SPARSE = 8
 OBJECTIVE_PC, OBJECTIVE_MCN, OBJECTIVE_SIXDST_PC, OBJECTIVE_SIXDST_MCN = 0, 1, 2, 3
 GENES_NODES, GENES_EDGES = 0, 1
 

@@ -362,3 +362,118 @@ def test_models_detect_a_non_atomic_hook():
         run_interleaved([thread(edges[i::8]) for i in range(8)], rng)
         failures += not same_partition(L, want)
     assert failures > 0
+
+
+# ---------------------------------------------------------------------------
+# The sparse kernel's class union-find: values are terminal + 1 with 0 = R (the reference class,
+# never hooked); the larger root hooks under the smaller by compare-and-swap, and a find points
+# the links on its path that still lie below the root it found straight at that root, stopping at
+# the first link at or above it.
+
+def sp_find(C, a, bound=True):
+    r = a
+    while r != 0:
+        p = C[r - 1]
+        yield
+        if p == r:
+            break
+        r = p
+    while (a > r) if bound else (a != r):
+        if a == 0:
+            raise IndexError("link of R read")
+        p = C[a - 1]
+        yield
+        if bound and p <= r:  # the kernel's stop: never write r above itself
+            break
+        if not bound and (p == a or p == r):  # a stop that lets the walk pass r
+            break
+        C[a - 1] = r
+        yield
+        a = p
+    return r
+
+
+def sp_unite(C, a, b, bound=True):
+    a = yield from sp_find(C, a, bound)
+    b = yield from sp_find(C, b, bound)
+    while a != b:
+        if a < b:
+            a, b = b, a
+        old = C[a - 1]
+        if old == a:
+            C[a - 1] = b  # compare-and-swap: one step
+            yield
+            return
+        yield
+        a = yield from sp_find(C, old, bound)
+        b = yield from sp_find(C, b, bound)
+
+
+def sp_classes(m, pairs):
+    """Sequential classes of m terminals (values 1..m) and R (0) under the pairs."""
+    parent = list(range(m + 1))
+
+    def f(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+
+    for a, b in pairs:
+        ra, rb = f(a), f(b)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    return [f(x) for x in range(m + 1)]
+
+
+def sp_check(C, want):
+    m = len(C)
+    got = [0] * (m + 1)
+    for v in range(1, m + 1):
+        x, steps = v, 0
+        while x != 0 and C[x - 1] != x:
+            assert C[x - 1] < x, "a link points up"
+            x = C[x - 1]
+            steps += 1
+            assert steps <= m, "a cycle"
+        got[v] = x
+    for a in range(m + 1):
+        for b in range(m + 1):
+            assert (got[a] == got[b]) == (want[a] == want[b])
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_sparse_class_unions_under_interleavings(seed):
+    """Unions of terminal classes, some with R, by many threads at once (linking, then the join's
+    unions with R): the classes equal the sequential ones, links only point down, no cycles."""
+    rng = random.Random(seed)
+    m = rng.randrange(4, 40)
+    pairs = []
+    for _ in range(rng.randrange(m, 3 * m)):
+        a = rng.randrange(1, m + 1)
+        b = 0 if rng.random() < 0.15 else rng.randrange(1, m + 1)
+        pairs.append((a, b))
+    C = list(range(1, m + 1))
+    threads = [sp_unite(C, a, b) for a, b in pairs]
+    # interleave in a few threads per "warp": every pair is a thread here
+    run_interleaved([t for t in threads], rng)
+    sp_check(C, sp_classes(m, pairs))
+
+
+def test_sparse_class_models_detect_compression_past_the_root():
+    """The earlier stop rule (break only at a root or at the root found) lets a find walk above the
+    root it found once another thread has compressed past it, writing that root into an ancestor
+    (a cycle) or reading the link of R; the interleavings find it."""
+    failures = 0
+    for seed in range(300):
+        rng = random.Random(seed)
+        m = rng.randrange(4, 12)
+        pairs = [(rng.randrange(1, m + 1), 0 if rng.random() < 0.3 else rng.randrange(1, m + 1))
+                 for _ in range(4 * m)]
+        C = list(range(1, m + 1))
+        threads = [sp_unite(C, a, b, bound=False) for a, b in pairs]
+        try:
+            run_interleaved(threads, rng)
+            sp_check(C, sp_classes(m, pairs))
+        except (AssertionError, IndexError, RecursionError):
+            failures += 1
+    assert failures > 0

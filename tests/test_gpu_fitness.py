@@ -3,7 +3,8 @@
 Fitness is integer (int64), so the bar is exact equality, element by element.
 Covers hand-worked values, exhaustive subsets of tiny graphs, the benchmark
 graphs (BA/HK n = 20000, k = 1000, s = 1024), graphs too large for shared
-memory (global labels), and degenerate sets and graphs.
+memory (global labels and the sparse kernel, which every test also runs on
+small graphs), and degenerate sets and graphs.
 """
 import itertools
 import json
@@ -20,20 +21,21 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pc_worked_examples.json")
 
 
-@pytest.fixture(scope="module", params=["piece", "tree_local", "tree", "tree_join", "tree_scan", "sampled", "edges"])
+@pytest.fixture(scope="module", params=["sparse", "piece", "tree_local", "tree", "tree_join", "tree_scan", "sampled",
+                                        "edges"])
 def ctx(request):
     import torch
 
     from paper_2412_20980_gb300 import Context
     from paper_2412_20980_gb300 import build as b
-    from paper_2412_20980_gb300.gapa import (FITNESS_EDGES, FITNESS_PIECE, FITNESS_SAMPLED, FITNESS_TREE,
-                                             FITNESS_TREE_JOIN, FITNESS_TREE_LOCAL, FITNESS_TREE_SCAN)
+    from paper_2412_20980_gb300.gapa import (FITNESS_EDGES, FITNESS_PIECE, FITNESS_SAMPLED, FITNESS_SPARSE,
+                                             FITNESS_TREE, FITNESS_TREE_JOIN, FITNESS_TREE_LOCAL, FITNESS_TREE_SCAN)
 
     b.build()
     c = Context(0)
     c.set_fitness_kernel({"tree": FITNESS_TREE, "tree_join": FITNESS_TREE_JOIN, "tree_scan": FITNESS_TREE_SCAN,
                           "tree_local": FITNESS_TREE_LOCAL, "piece": FITNESS_PIECE, "sampled": FITNESS_SAMPLED,
-                          "edges": FITNESS_EDGES}[request.param])
+                          "edges": FITNESS_EDGES, "sparse": FITNESS_SPARSE}[request.param])
     c.variant_name = request.param
     yield c
     torch.cuda.synchronize()
@@ -133,8 +135,8 @@ def test_global_label_partial_group(ctx):
 def test_full_size_rmat_sampled_members(ctx):
     """R-MAT scale 20 with 2^24 edges, k = 10000, s = 256 (the large configuration, evaluated as
     one batch); eight members spread over the batch are checked against the oracle one by one."""
-    if ctx.variant_name != "tree":
-        pytest.skip("full-size check runs on the default kernel only")
+    if ctx.variant_name not in ("tree", "sparse"):
+        pytest.skip("full-size check runs on the two large-graph kernels only")
     g = synth.rmat_graph(20, 1 << 24, seed=1)
     pop = synth.random_deletion_sets(g.n, 10000, 256, 0)
     got = gpu_fit(ctx, g, pop)
@@ -158,8 +160,8 @@ def test_global_label_path_hub_heavy(ctx, hubs):
     """A dense R-MAT graph (8 edges per node, so the sampling / giant / scan steps run) whose
     deletion sets hold the top hubs: the BFS tree shatters and the groups move between the
     outside-node scan and the non-tree join; sizes 17 members, a group and a ragged tail."""
-    if ctx.variant_name != "tree":
-        pytest.skip("global-label path runs on the default kernel only")
+    if ctx.variant_name not in ("tree", "sparse"):
+        pytest.skip("runs on the two large-graph kernels only")
     g = synth.rmat_graph(17, 1 << 20, seed=3, chunk=1 << 20)
     top = np.argsort(-g.degrees(), kind="stable")
     rng = np.random.default_rng(hubs)
@@ -265,8 +267,8 @@ def test_mcn_objective_matches_oracle(ctx, graph):
     """The maximum connectivity number objective, on the shared-memory and the global-label paths."""
     from paper_2412_20980_gb300.gapa import OBJECTIVE_MCN, OBJECTIVE_PC
 
-    if graph == "large" and ctx.variant_name != "tree":
-        pytest.skip("global-label path runs on the default kernel only")
+    if graph == "large" and ctx.variant_name not in ("tree", "sparse"):
+        pytest.skip("runs on the two large-graph kernels only")
     g = {"ba": lambda: synth.ba_graph(3000, 2, 4), "path": lambda: synth.named_graph("path", 4000),
          "star": lambda: synth.named_graph("star", 2500), "hub_deleted": lambda: synth.ba_graph(2000, 1, 6),
          "large": lambda: synth.ba_graph(100000, 3, 2)}[graph]()
