@@ -710,9 +710,9 @@ int gapa_set_stream(gapa_ctx* c, void* s) {
 
 // Tables of the sparse fitness kernel from the BFS forest: children as (first, count) (BFS
 // numbers them consecutively), the root of every node's tree (in BFS order every component is one
-// tree), component sizes at their roots, subtree sizes, the roots by decreasing size (ties: lower
-// root) and the sum over components of C(size, 2).  Left null if some node's children are not
-// consecutive.
+// tree; -1 for single-node components), component sizes at their roots, subtree sizes, the roots
+// by decreasing size (ties: lower root) and the sum over components of C(size, 2).  Left null if
+// some node's children are not consecutive.
 int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
     std::vector<int2> kids((size_t)n, make_int2(0, 0));
     for (int32_t x = 0; x < n; ++x) {
@@ -733,6 +733,8 @@ int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
     for (int32_t x = n - 1; x >= 0; --x)
         if (bf.tparent[x] != x) sub[bf.tparent[x]] += sub[x];
     std::stable_sort(roots.begin(), roots.end(), [&](int32_t a, int32_t b) { return csize[a] > csize[b]; });
+    for (int32_t x = 0; x < n; ++x)
+        if (csize[croot[x]] == 1) croot[x] = -1;  // a single-node component: nothing to recount
     long long pc0 = 0;
     for (int32_t r : roots) pc0 += (long long)csize[r] * (csize[r] - 1) / 2;
     auto up = [](void** dst, const void* src, size_t bytes) {
@@ -747,6 +749,7 @@ int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
         return gapa_fail(GAPA_ERR_OOM, "sparse fitness tables of %d nodes", n);
     }
     g.sp_ncomp = (int)roots.size();
+    g.sp_giant = roots.empty() ? -1 : roots[0];
     g.sp_pc0 = pc0;
     return GAPA_OK;
 }

@@ -50,7 +50,6 @@ using gapa_dev::tree16l_owner;
 using gapa_dev::tree16l_scan;
 
 constexpr int kSpBlock = 1024;
-constexpr unsigned kSpFirst = 0x80000000u;  // D entry flag: first deletion seen in its component
 constexpr int kSpLinkScan = 4;              // adjacency entries a top samples for links
 constexpr int kSpInFlight = 4;              // tops per thread resolved together in the re-pick pass
 
@@ -65,11 +64,12 @@ struct SpGraph {
     const int* fptr;      // full adjacency in BFS numbers (CSR)
     const Col* fcol;
     const int2* kids;     // (first child, number of children)
-    const int* croot;     // root of the node's component tree
+    const int* croot;     // root of the node's component tree (-1: a single-node component)
     const int* csize;     // size of the component, at its root
     const int* sub;       // subtree size
     const int* bysize;    // component roots by decreasing size (MCN)
     int ncomp;
+    int giant;            // root of the largest component
     long long pc0;        // sum over components of C(size, 2)
     int objective;        // 0: PC, 1: MCN
 };
@@ -84,6 +84,7 @@ struct SpSlot {
     unsigned* cnt;             // terminals: chained subtree weight, then class size; 0 elsewhere
     int* list;                 // listed nodes
     int* tl;                   // live tops
+    int* cl;                   // touched components (roots), single-node components excepted
     unsigned long long* cacc;  // component roots: deleted << 32 | nodes apart from R; 0 elsewhere
     unsigned long long* best;  // component roots whose root is deleted: weight << 32 | ~terminal
 };
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
                                                                long long* __restrict__ fit, int* head, int* status) {
     extern __shared__ __align__(16) unsigned char sp_smem[];
     __shared__ long long red[32];
-    __shared__ int s_member, s_nd, s_nt, s_nlist;
+    __shared__ int s_member, s_nd, s_nt, s_nterm, s_ncl, s_gdel, s_nlist;
     const Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
     const int tid = tm.tid, T = tm.T, lane = tid & 31, n = g.n;
     const int words = (n + 31) >> 5;
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
     unsigned* const cnt = base.cnt + o;
     int* const list = base.list + o;
     int* const tl = base.tl + o;
+    int* const cl = base.cl + o;
     unsigned long long* const cacc = base.cacc + o;
     unsigned long long* const best = base.best + o;
     constexpr int F = kSpInFlight;
@@ -190,6 +192,9 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
             s_member = atomicAdd(head, 1);
             s_nd = 0;
             s_nt = 0;
+            s_nterm = 0;
+            s_ncl = 0;
+            s_gdel = 0;
             s_nlist = 0;
         }
         for (int w = tid; w < words; w += T) dead[w] = 0u;
@@ -238,22 +243,36 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
                 Doff[i] = at;
                 at += __ldg(&g.kids[D[i]].y);
             }
-            tm.sync();  // the flags below go into D's entries
             if (tid == 0) Doff[nd] = ntops;
         }
-        for (int i0 = tid & ~31; i0 < nd; i0 += T) {
-            const int i = i0 + lane;
-            const int c = i < nd ? __ldg(&g.croot[D[i]]) : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, c);
-            if (c >= 0 && lane == __ffs(peers) - 1) {
-                const unsigned long long old = atomicAdd(&cacc[c], (unsigned long long)__popc(peers) << 32);
-                if (old == 0ull) {
-                    D[i] = (int)((unsigned)D[i] | kSpFirst);
-                    if (!bm_test(dead, c)) cls[c] = c + 1;  // a live tree root is a terminal
+        {
+            int gdel = 0;  // deletions in the largest component, summed in shared memory
+            for (int i0 = tid & ~31; i0 < nd; i0 += T) {
+                const int i = i0 + lane;
+                int c = i < nd ? __ldg(&g.croot[D[i]]) : -1;  // -1: a single-node component
+                if (c >= 0 && c == g.giant) {
+                    ++gdel;
+                    c = -1;
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, c);
+                if (c >= 0 && lane == __ffs(peers) - 1) {
+                    const unsigned long long old = atomicAdd(&cacc[c], (unsigned long long)__popc(peers) << 32);
+                    if (old == 0ull) {
+                        cl[atomicAdd(&s_ncl, 1)] = c;
+                        if (!bm_test(dead, c)) cls[c] = c + 1;  // a live tree root is a terminal
+                    }
                 }
             }
+            gdel = __reduce_add_sync(0xffffffffu, gdel);
+            if (lane == 0 && gdel) atomicAdd(&s_gdel, gdel);
         }
         tm.sync();
+        if (tid == 0 && s_gdel) {
+            const int c = g.giant;
+            cacc[c] = (unsigned long long)s_gdel << 32;
+            cl[s_ncl++] = c;
+            if (!bm_test(dead, c)) cls[c] = c + 1;
+        }
 
         // 2. re-pick and hop of every top; the live tops are also listed compactly (tl) for the
         // passes below.  F tops per thread are resolved together (their loads overlap).
@@ -266,7 +285,7 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
                 t[u] = -1;
                 if (i < ntops) {
                     const int ow = tree16l_owner(Doff, nd, i);
-                    t[u] = __ldg(&g.kids[(unsigned)D[ow] & ~kSpFirst].x) + i - Doff[ow];
+                    t[u] = __ldg(&g.kids[D[ow]].x) + i - Doff[ow];
                 }
             }
 #pragma unroll
@@ -312,11 +331,31 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
         }
         tm.sync();
         const int nt = s_nt;
-        // terminal of every top (chains followed F at a time, then compressed); subtree weight of
-        // the chained tops at terminals whose component root is deleted
+        // terminal of every top by pointer jumping (hop <- hop of hop until no hop changes)
+        for (;;) {
+            bool changed = false;
+            for (int j0 = tid; j0 < nt; j0 += F * T) {
+                int t[F], x[F], h[F];
+#pragma unroll
+                for (int u = 0; u < F; ++u) t[u] = j0 + u * T < nt ? ldcg(&tl[j0 + u * T]) : -1;
+#pragma unroll
+                for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
+#pragma unroll
+                for (int u = 0; u < F; ++u) h[u] = (t[u] >= 0 && x[u] != t[u]) ? ldcg(&hop[x[u]]) : -1;
+#pragma unroll
+                for (int u = 0; u < F; ++u)
+                    if (h[u] != -1 && h[u] != x[u]) {  // x is neither a tree root nor a terminal top
+                        hop[t[u]] = h[u];
+                        changed = true;
+                    }
+            }
+            if (!__syncthreads_or(changed)) break;
+        }
+        // terminals: tops that re-picked nothing start their class and are listed densely (in
+        // `list`, free until the listing); subtree weight of the chained tops at terminals whose
+        // component root is deleted
         for (int base_j = 0; base_j < nt; base_j += F * T) {
             int t[F], x[F];
-            bool act[F];
 #pragma unroll
             for (int u = 0; u < F; ++u) {
                 const int j = base_j + u * T + tid;
@@ -324,37 +363,16 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
             }
 #pragma unroll
             for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
-            bool any = false;
-#pragma unroll
-            for (int u = 0; u < F; ++u) {
-                act[u] = t[u] >= 0 && x[u] != t[u];
-                any |= act[u];
-            }
-            while (any) {
-                int h[F];
-#pragma unroll
-                for (int u = 0; u < F; ++u) h[u] = act[u] ? ldcg(&hop[x[u]]) : 0;
-                any = false;
-#pragma unroll
-                for (int u = 0; u < F; ++u) {
-                    if (!act[u]) continue;
-                    if (h[u] == -1 || h[u] == x[u]) {
-                        act[u] = false;
-                    } else {
-                        x[u] = h[u];
-                        any = true;
-                    }
-                }
-            }
 #pragma unroll
             for (int u = 0; u < F; ++u) {
                 int key = -1;
                 unsigned wgt = 0;
+                const bool term = t[u] >= 0 && x[u] == t[u];
+                if (term) cls[t[u]] = t[u] + 1;
                 if (t[u] >= 0) {
-                    if (x[u] == t[u]) cls[t[u]] = t[u] + 1;  // a top that re-picked nothing is a terminal
-                    else hop[t[u]] = x[u];
                     // x is a top that re-picked nothing, or a live tree root (never weighed)
-                    if (bm_test(dead, __ldg(&g.croot[x[u]]))) {
+                    const int cx = __ldg(&g.croot[x[u]]);
+                    if (cx >= 0 && bm_test(dead, cx)) {
                         key = x[u];
                         wgt = (unsigned)__ldg(&g.sub[t[u]]);
                     }
@@ -362,64 +380,48 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
                 const unsigned peers = __match_any_sync(0xffffffffu, key);
                 const unsigned tot = __reduce_add_sync(peers, wgt);
                 if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], tot);
+                sp_append(term, t[u], lane, &s_nterm, list);
             }
         }
         tm.sync();
+        const int nterm = s_nterm;
 
-        // sampled links: a top that re-picked nothing unites its class with the classes of its first
-        // live neighbours outside its own piece (at most two)
-        for (int j0 = tid; j0 < nt; j0 += F * T) {
-            int t[F];
+        // sampled links: a terminal unites its class with the classes of its first live neighbours
+        // outside its own piece (at most two)
+        for (int j = tid; j < nterm; j += T) {
+            const int t = ldcg(&list[j]);
+            const int beg = __ldg(&g.fptr[t]);
+            const int cntw = min(__ldg(&g.fptr[t + 1]) - beg, kSpLinkScan);
+            int w[kSpLinkScan], pw[kSpLinkScan];
 #pragma unroll
-            for (int u = 0; u < F; ++u) t[u] = j0 + u * T < nt ? ldcg(&tl[j0 + u * T]) : -1;
+            for (int e = 0; e < kSpLinkScan; ++e) w[e] = e < cntw ? (int)__ldg(&g.fcol[beg + e]) : -1;
 #pragma unroll
-            for (int u = 0; u < F; ++u)
-                if (t[u] >= 0 && ldcg(&hop[t[u]]) != t[u]) t[u] = -1;
-#pragma unroll 1
-            for (int u = 0; u < F; ++u) {
-                if (t[u] < 0) continue;
-                const int beg = __ldg(&g.fptr[t[u]]);
-                const int cntw = min(__ldg(&g.fptr[t[u] + 1]) - beg, kSpLinkScan);
-                int w[kSpLinkScan], pw[kSpLinkScan];
+            for (int e = 0; e < kSpLinkScan; ++e) {
+                if (w[e] >= 0 && bm_test(dead, w[e])) w[e] = -1;
+                pw[e] = w[e] >= 0 ? __ldg(&g.tparent[w[e]]) : -1;
+            }
+            int links = 0;
 #pragma unroll
-                for (int e = 0; e < kSpLinkScan; ++e) w[e] = e < cntw ? (int)__ldg(&g.fcol[beg + e]) : -1;
-#pragma unroll
-                for (int e = 0; e < kSpLinkScan; ++e) {
-                    if (w[e] >= 0 && bm_test(dead, w[e])) w[e] = -1;
-                    pw[e] = w[e] >= 0 ? __ldg(&g.tparent[w[e]]) : -1;
-                }
-                int links = 0;
-#pragma unroll
-                for (int e = 0; e < kSpLinkScan; ++e) {
-                    if (w[e] < 0 || pw[e] == t[u] || links == 2) continue;
-                    sp_unite(cls, t[u] + 1, sp_terminal_of(g, dead, hop, w[e], pw[e]) + 1);
-                    ++links;
-                }
+            for (int e = 0; e < kSpLinkScan; ++e) {
+                if (w[e] < 0 || pw[e] == t || links == 2) continue;
+                sp_unite(cls, t + 1, sp_terminal_of(g, dead, hop, w[e], pw[e]) + 1);
+                ++links;
             }
         }
         tm.sync();
 
         // 3. reference terminal of components whose root is deleted
-        for (int j0 = tid; j0 < nt; j0 += F * T) {
-            int t[F];
-#pragma unroll
-            for (int u = 0; u < F; ++u) t[u] = j0 + u * T < nt ? ldcg(&tl[j0 + u * T]) : -1;
-#pragma unroll
-            for (int u = 0; u < F; ++u)
-                if (t[u] >= 0 && ldcg(&hop[t[u]]) != t[u]) t[u] = -1;
-#pragma unroll
-            for (int u = 0; u < F; ++u) {
-                if (t[u] < 0) continue;
-                const int c = __ldg(&g.croot[t[u]]);
-                if (bm_test(dead, c))
-                    atomicMax(&best[c], ((unsigned long long)ldcg(&cnt[t[u]]) << 32) | (unsigned long long)(~(unsigned)t[u]));
-            }
+        for (int j = tid; j < nterm; j += T) {
+            const int t = ldcg(&list[j]);
+            const int c = __ldg(&g.croot[t]);
+            if (bm_test(dead, c))
+                atomicMax(&best[c], ((unsigned long long)ldcg(&cnt[t]) << 32) | (unsigned long long)(~(unsigned)t));
         }
         tm.sync();
         // the reference's class becomes R (one thread per touched component; classes never span two)
-        for (int i = tid; i < nd; i += T) {
-            if (!((unsigned)D[i] & kSpFirst)) continue;
-            const int c = __ldg(&g.croot[(int)((unsigned)D[i] & ~kSpFirst)]);
+        const int ncl = s_ncl;
+        for (int i = tid; i < ncl; i += T) {
+            const int c = ldcg(&cl[i]);
             int r;
             if (!bm_test(dead, c)) {
                 r = c + 1;
@@ -436,6 +438,13 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
             }
         }
         tm.sync();
+        // every terminal's and live root's link straight to its class root (0: R)
+        for (int j = tid; j < nterm; j += T) sp_find(cls, ldcg(&list[j]) + 1);
+        for (int i = tid; i < ncl; i += T) {
+            const int c = ldcg(&cl[i]);
+            if (!bm_test(dead, c)) sp_find(cls, c + 1);
+        }
+        tm.sync();
 
         // 4. listing: tops whose class is not R, then their pieces down the tree
         for (int base_j = 0; base_j < nt; base_j += F * T) {
@@ -447,12 +456,15 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
             }
 #pragma unroll
             for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
+            int cx[F];
+#pragma unroll
+            for (int u = 0; u < F; ++u) cx[u] = t[u] >= 0 ? ldcg(&cls[x[u]]) : 0;
 #pragma unroll
             for (int u = 0; u < F; ++u) {
                 bool want = false;
                 if (t[u] >= 0) {
                     if (x[u] == t[u]) cnt[t[u]] = 0u;  // the weight has served
-                    if (sp_find(cls, x[u] + 1) != 0) {
+                    if (cx[u] != 0) {
                         if (x[u] != t[u]) cls[t[u]] = x[u] + 1;  // a terminal keeps its class link
                         want = true;
                     }
@@ -553,9 +565,8 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
             const int v = ldcg(&list[i]);
             if (ldcg(&cls[v]) == v + 1) acc = objective_add(acc, (long long)ldcg(&cnt[v]), g.objective);
         }
-        for (int i = tid; i < nd; i += T) {
-            if (!((unsigned)D[i] & kSpFirst)) continue;
-            const int c = __ldg(&g.croot[(int)((unsigned)D[i] & ~kSpFirst)]);
+        for (int i = tid; i < ncl; i += T) {
+            const int c = ldcg(&cl[i]);
             const unsigned long long a = ldcg(&cacc[c]);
             const long long cs = __ldg(&g.csize[c]);
             const long long rs = cs - (long long)(a >> 32) - (long long)(a & 0xFFFFFFFFull);
@@ -568,7 +579,8 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
                 // the largest untouched component
                 for (int j = 0; j < g.ncomp; ++j) {
                     const int c = __ldg(&g.bysize[j]);
-                    if (ldcg(&cacc[c]) == 0ull) {
+                    const bool touched = __ldg(&g.csize[c]) == 1 ? bm_test(dead, c) : ldcg(&cacc[c]) != 0ull;
+                    if (!touched) {
                         const long long cs = __ldg(&g.csize[c]);
                         tot = cs > tot ? cs : tot;
                         break;
@@ -604,9 +616,8 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
                     cnt[v[u]] = 0u;
                 }
         }
-        for (int i = tid; i < nd; i += T) {
-            if (!((unsigned)D[i] & kSpFirst)) continue;
-            const int c = __ldg(&g.croot[(int)((unsigned)D[i] & ~kSpFirst)]);
+        for (int i = tid; i < ncl; i += T) {
+            const int c = ldcg(&cl[i]);
             cacc[c] = 0ull;
             best[c] = 0ull;
             cls[c] = -1;
@@ -632,6 +643,7 @@ SpGraph<Col> sp_graph(const gapa_ctx* c, const Col* fcol) {
     g.sub = c->g.sp_sub;
     g.bysize = c->g.sp_bysize;
     g.ncomp = c->g.sp_ncomp;
+    g.giant = c->g.sp_giant;
     g.pc0 = c->g.sp_pc0;
     g.objective = c->objective;
     return g;
@@ -651,9 +663,10 @@ int gapa_sparse_init(gapa_ctx* c) {
     return rc;
 }
 
-// Scratch of the persistent CTAs: seven n-entry arrays per CTA (hops, classes,
-// counts, listed nodes, live tops: int32; per-component sums and reference
-// keys: int64), set to -1 / 0 once here and left that way by every member.
+// Scratch of the persistent CTAs: eight n-entry arrays per CTA (hops, classes,
+// counts, listed nodes, live tops, touched components: int32; per-component
+// sums and reference keys: int64), set to -1 / 0 once here and left that way
+// by every member.
 int gapa_sparse_prepare(gapa_ctx* c) {
     const int n = c->g.n;
     const size_t smem = sp_smem_bytes(n, 0);
@@ -662,7 +675,7 @@ int gapa_sparse_prepare(gapa_ctx* c) {
     if (per_sm < 1) per_sm = 1;
     const int slots = c->num_sms * per_sm;
     const size_t stride = ((size_t)n + 63) & ~(size_t)63;
-    const size_t bytes = (size_t)slots * stride * (5 * 4 + 2 * 8) + 64;
+    const size_t bytes = (size_t)slots * stride * (6 * 4 + 2 * 8) + 64;
     if (c->sp_scratch && c->sp_scratch_cap >= bytes && c->sp_stride == stride && c->sp_slots <= slots) return GAPA_OK;
     cudaFree(c->sp_scratch);
     c->sp_scratch = nullptr;
@@ -676,9 +689,9 @@ int gapa_sparse_prepare(gapa_ctx* c) {
     c->sp_slots = slots;
     const size_t ints = (size_t)slots * stride;
     char* p = static_cast<char*>(c->sp_scratch);
-    // hop, cls = -1; cnt, list, tl = 0; cacc, best = 0; the queue head last
+    // hop, cls = -1; cnt, list, tl, cl = 0; cacc, best = 0; the queue head last
     GAPA_CUDA(cudaMemset(p, 0xFF, ints * 8));
-    GAPA_CUDA(cudaMemset(p + ints * 8, 0, ints * 12 + ints * 16 + 64));
+    GAPA_CUDA(cudaMemset(p + ints * 8, 0, ints * 16 + ints * 16 + 64));
     GAPA_CUDA(cudaDeviceSynchronize());
     return GAPA_OK;
 }
@@ -696,9 +709,10 @@ int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, in
     b.cnt = reinterpret_cast<unsigned*>(p + ints * 8);
     b.list = reinterpret_cast<int*>(p + ints * 12);
     b.tl = reinterpret_cast<int*>(p + ints * 16);
-    b.cacc = reinterpret_cast<unsigned long long*>(p + ints * 20);
-    b.best = reinterpret_cast<unsigned long long*>(p + ints * 28);
-    int* head = reinterpret_cast<int*>(p + ints * 36);
+    b.cl = reinterpret_cast<int*>(p + ints * 20);
+    b.cacc = reinterpret_cast<unsigned long long*>(p + ints * 24);
+    b.best = reinterpret_cast<unsigned long long*>(p + ints * 32);
+    int* head = reinterpret_cast<int*>(p + ints * 40);
     GAPA_CUDA(cudaMemsetAsync(head, 0, sizeof(int), st));
     const size_t smem = sp_smem_bytes(c->g.n, k);
     const int grid = std::min(c->sp_slots, std::max(s, 1));

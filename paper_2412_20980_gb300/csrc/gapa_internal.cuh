@@ -165,15 +165,17 @@ struct DeviceGraph {
     bool packed16 = false;      // n <= 65536
     int bfs_depth = 0;          // largest BFS level
     // sparse fitness kernel (any n; null when the BFS forest's children are not consecutive):
-    // (first child, number of children), the root of every node's component tree, the
-    // component's size at its root, subtree sizes, the component roots by decreasing size,
-    // their number and the sum over components of C(size, 2)
+    // (first child, number of children), the root of every node's component tree (-1 for a
+    // single-node component), the component's size at its root, subtree sizes, the component
+    // roots by decreasing size, their number, the largest one and the sum over components of
+    // C(size, 2)
     int2* sp_kids = nullptr;
     int* sp_croot = nullptr;
     int* sp_csize = nullptr;
     int* sp_sub = nullptr;
     int* sp_bysize = nullptr;
     int sp_ncomp = 0;
+    int sp_giant = -1;          // root of the largest component
     long long sp_pc0 = 0;
 };
 
