@@ -669,14 +669,14 @@ int gapa_sparse_init(gapa_ctx* c) {
 // by every member.
 int gapa_sparse_prepare(gapa_ctx* c) {
     const int n = c->g.n;
+    const size_t stride = ((size_t)n + 63) & ~(size_t)63;
+    if (c->sp_scratch && c->sp_stride == stride) return GAPA_OK;  // (also inside a stream capture)
     const size_t smem = sp_smem_bytes(n, 0);
     int per_sm = 0;
     GAPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cc_sparse_kernel<int>, kSpBlock, smem));
     if (per_sm < 1) per_sm = 1;
     const int slots = c->num_sms * per_sm;
-    const size_t stride = ((size_t)n + 63) & ~(size_t)63;
     const size_t bytes = (size_t)slots * stride * (6 * 4 + 2 * 8) + 64;
-    if (c->sp_scratch && c->sp_scratch_cap >= bytes && c->sp_stride == stride && c->sp_slots <= slots) return GAPA_OK;
     cudaFree(c->sp_scratch);
     c->sp_scratch = nullptr;
     c->sp_scratch_cap = 0;

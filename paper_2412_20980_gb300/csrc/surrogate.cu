@@ -686,7 +686,12 @@ __device__ __forceinline__ float adamw_one(float p, float g, float& m, float& v,
 __global__ void __launch_bounds__(256) emb_update_kernel(const ulonglong2* __restrict__ Gi, float4* __restrict__ P,
                                                          float4* __restrict__ M, float4* __restrict__ V,
                                                          uint2* __restrict__ Eb, size_t groups, float lr, float b1,
-                                                         float b2, float wd, float eps, float bc1, float bc2) {
+                                                         float b2, float wd, float eps, float bc1, float bc2,
+                                                         const float2* __restrict__ bcp) {
+    if (bcp) {
+        bc1 = bcp->x;
+        bc2 = bcp->y;
+    }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < groups; i += (size_t)gridDim.x * blockDim.x) {
         const ulonglong2 g01 = Gi[2 * i], g23 = Gi[2 * i + 1];
         float4 p = P[i], m = M[i], v = V[i];
@@ -710,7 +715,11 @@ __global__ void emb_grad_float_kernel(const unsigned long long* __restrict__ Gi,
 
 __global__ void adamw_kernel(float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
                              const float* __restrict__ G, size_t count, float lr, float b1, float b2, float wd,
-                             float eps, float bc1, float bc2) {
+                             float eps, float bc1, float bc2, const float2* __restrict__ bcp) {
+    if (bcp) {
+        bc1 = bcp->x;
+        bc2 = bcp->y;
+    }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
         const float g = G[i];
         const float m = b1 * M[i] + (1.f - b1) * g;
@@ -783,8 +792,9 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ sc
 // residual-degree counts; dst_cap > 0 writes ring slots (dst_first + r) mod dst_cap.
 __global__ void gather_rows_kernel(const int* __restrict__ src, const ResidRow* __restrict__ rsrc,
                                    const int* __restrict__ idx, int k, int* __restrict__ dst, ResidRow* __restrict__ rdst,
-                                   int dst_first, int dst_cap) {
+                                   int dst_first, int dst_cap, const int* __restrict__ first_dev) {
     const int r = blockIdx.x;
+    if (first_dev) dst_first = *first_dev;
     const int from = idx ? idx[r] : r;
     const int to = dst_cap > 0 ? (dst_first + r) % dst_cap : r;
     for (int j = threadIdx.x; j < k; j += blockDim.x) dst[(size_t)to * k + j] = src[(size_t)from * k + j];
@@ -805,8 +815,9 @@ __global__ void scatter_fit_kernel(const long long* __restrict__ fsel, const int
 // ring) or (l - mean) / std (mode 1: z-score among the row's siblings).
 __global__ void __launch_bounds__(1024) ring_target_kernel(const int64_t* __restrict__ f, int cnt, int mode,
                                                            double* __restrict__ ring_lp, int first, int cap,
-                                                           double* __restrict__ gstats) {
+                                                           double* __restrict__ gstats, const int* __restrict__ first_dev) {
     __shared__ double s1[1024], s2[1024];
+    if (first_dev) first = *first_dev;
     double a = 0, b = 0;
     for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
         const double l = log1p((double)f[r]);
@@ -838,8 +849,9 @@ __global__ void __launch_bounds__(1024) ring_target_kernel(const int64_t* __rest
 // Mean and standard deviation of log1p(fitness) over the ring (one CTA, FP64,
 // fixed-order reduction).
 __global__ void __launch_bounds__(1024) target_stats_kernel(const double* __restrict__ ring_lp, int valid,
-                                                            double* __restrict__ stats) {
+                                                            double* __restrict__ stats, const int* __restrict__ valid_dev) {
     __shared__ double s1[1024], s2[1024];
+    if (valid_dev) valid = *valid_dev;
     double a = 0, b = 0;
     for (int i = threadIdx.x; i < valid; i += blockDim.x) {
         const double l = ring_lp[i];
@@ -869,8 +881,11 @@ __global__ void __launch_bounds__(1024) target_stats_kernel(const double* __rest
 __global__ void batch_kernel(const int* __restrict__ ring, const ResidRow* __restrict__ ring_resid,
                              const double* __restrict__ ring_lp, int valid, int k, int B, RngKey key, int step,
                              int g, const double* __restrict__ stats, int* __restrict__ rows,
-                             ResidRow* __restrict__ resid, float* __restrict__ t) {
+                             ResidRow* __restrict__ resid, float* __restrict__ t, const int* __restrict__ valid_dev,
+                             const int* __restrict__ g_dev) {
     const int b = blockIdx.x;
+    if (valid_dev) valid = *valid_dev;
+    if (g_dev) g = *g_dev - 1;  // the record of this generation has advanced the counter
     const int idx = uniform_below(philox_word0((uint32_t)b, (uint32_t)step, (uint32_t)g, (8u << 24) | 1u, key.lo, key.hi),
                                   valid);
     for (int j = threadIdx.x; j < k; j += blockDim.x) rows[(size_t)b * k + j] = ring[(size_t)idx * k + j];
@@ -878,6 +893,21 @@ __global__ void batch_kernel(const int* __restrict__ ring, const ResidRow* __res
         t[b] = (float)((ring_lp[idx] - stats[0]) / stats[1]);
         resid[b] = ring_resid[idx];
     }
+}
+
+// Ring bookkeeping of a run on the device (so that generations can be replayed
+// from a CUDA graph): st[0] = next ring slot, st[1] = valid rows.
+__global__ void ring_advance_kernel(int* __restrict__ st, int added, int cap) {
+    st[0] = (st[0] + added) % cap;
+    st[1] = min(cap, st[1] + added);
+}
+
+// One AdamW step on the device: tau += 1 and its bias corrections from the
+// table the host computed (1 - beta1^tau, 1 - beta2^tau).
+__global__ void tau_step_kernel(int* __restrict__ tau, const float2* __restrict__ table, float2* __restrict__ bc) {
+    const int t = *tau + 1;
+    *tau = t;
+    *bc = table[t];
 }
 
 // Scores back to pairwise-connectivity estimates: expm1(mean + std * y) with
@@ -1049,8 +1079,12 @@ int emb_gradient(gapa_surrogate* s, const int32_t* pop, int B, int k, cudaStream
 }
 
 // One AdamW step on a batch (rows a multiple of 16) with targets t.
+// With tau_dev, the step count and its bias corrections live on the device (a
+// step of a CUDA-graph-replayed generation): tau_dev[0] is advanced and the
+// corrections come from `table` (indexed by the step) through bc_dev.
 int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float* t, cudaStream_t st,
-               const ResidRow* resid = nullptr) {
+               const ResidRow* resid = nullptr, int* tau_dev = nullptr, const float2* table = nullptr,
+               float2* bc_dev = nullptr) {
     int rc = forward(s, pop, B, k, true, st, resid);
     if (rc != GAPA_OK) return rc;
     ProfileScope prof(s->ctx, st, 2, 19);
@@ -1087,13 +1121,15 @@ int train_step(gapa_surrogate* s, const int32_t* pop, int B, int k, const float*
     if ((rc = emb_gradient(s, pop, B, k, st)) != GAPA_OK) return rc;
     s->tau += 1;
     const float bc1 = 1.f - powf(s->cfg.beta1, (float)s->tau), bc2 = 1.f - powf(s->cfg.beta2, (float)s->tau);
+    if (tau_dev) tau_step_kernel<<<1, 1, 0, st>>>(tau_dev, table, bc_dev);
     // dense parameters (W1 .. b3), then the embedding table in one fused pass
     adamw_kernel<<<64, 256, 0, st>>>(s->P, s->M, s->V, G, L.E, s->cfg.lr, s->cfg.beta1, s->cfg.beta2,
-                                     s->cfg.weight_decay, s->cfg.eps, bc1, bc2);
+                                     s->cfg.weight_decay, s->cfg.eps, bc1, bc2, tau_dev ? bc_dev : nullptr);
     emb_update_kernel<<<s->ctx->num_sms * 8, 256, 0, st>>>(
         reinterpret_cast<const ulonglong2*>(s->Gi), reinterpret_cast<float4*>(s->P + L.E),
         reinterpret_cast<float4*>(s->M + L.E), reinterpret_cast<float4*>(s->V + L.E), reinterpret_cast<uint2*>(s->Eb),
-        (size_t)s->n * kEmb / 4, s->cfg.lr, s->cfg.beta1, s->cfg.beta2, s->cfg.weight_decay, s->cfg.eps, bc1, bc2);
+        (size_t)s->n * kEmb / 4, s->cfg.lr, s->cfg.beta1, s->cfg.beta2, s->cfg.weight_decay, s->cfg.eps, bc1, bc2,
+        tau_dev ? bc_dev : nullptr);
     to_bf16_kernel<<<64, 256, 0, st>>>(s->P + L.W1, kIn, kHid, s->W1b, s->W1tb);
     to_bf16_kernel<<<128, 256, 0, st>>>(s->P + L.W2, kHid, kHid, s->W2b, s->W2tb);
     GAPA_CUDA(cudaGetLastError());
@@ -1325,7 +1361,11 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     gapa_config c2 = *cfg;
     int rc = gapa_run_prepare(c, &c2);
     if (rc != GAPA_OK) return rc;
-    cudaStream_t st = c->stream;
+    // the run goes on the context's own stream (a stream that can be captured), ordered after the
+    // caller's pending work and before the caller's later work
+    cudaStream_t st = c->own_stream;
+    GAPA_CUDA(cudaEventRecord(c->ev_a, c->stream));
+    GAPA_CUDA(cudaStreamWaitEvent(st, c->ev_a, 0));
     int32_t* P[2] = {c->stage_pop[0], c->stage_pop[1]};
     int64_t* F[2] = {c->stage_fit[0], c->stage_fit[1]};
     // surrogate buffers
@@ -1374,10 +1414,44 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     for (auto& e : ev) cudaEventCreate(&e);
     std::vector<int64_t> exact((size_t)G + 1, 0);
     int ring_pos = 0, ring_valid = 0, diag_rows = 0;
+    // the ring position, its valid rows and the AdamW step count live on the device (dstate[0..2]),
+    // with the bias corrections of every step of this run in a table, so that a generation can be
+    // replayed from a CUDA graph; the host keeps shadows for its own decisions
+    int* dstate = nullptr;
+    float2* bc_table = nullptr;
+    const int steps_max = s ? G * std::max(s->cfg.train_steps, 0) : 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     auto fail = [&](int code) {
         for (auto e : ev) cudaEventDestroy(e);
+        for (auto x : gexec)
+            if (x) cudaGraphExecDestroy(x);
+        cudaFree(dstate);
+        cudaFree(bc_table);
         cleanup();
         return code;
+    };
+    if (s) {
+        const int t0 = s->tau;
+        std::vector<float2> tab((size_t)t0 + steps_max + 2, make_float2(1.f, 1.f));
+        for (int t = 1; t < (int)tab.size(); ++t)
+            tab[t] = make_float2(1.f - powf(s->cfg.beta1, (float)t), 1.f - powf(s->cfg.beta2, (float)t));
+        if (cudaMalloc(&dstate, 16 + sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&bc_table, tab.size() * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(gapa_fail(GAPA_ERR_OOM, "surrogate run state"));
+        }
+        const int st0[4] = {0, 0, t0, 0};
+        GAPA_CUDA(cudaMemcpyAsync(dstate, st0, 16, cudaMemcpyHostToDevice, st));
+        GAPA_CUDA(cudaMemcpyAsync(bc_table, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    }
+    float2* bc_dev = dstate ? reinterpret_cast<float2*>(dstate + 4) : nullptr;
+    // rows (and their residual counts and exact fitness) enter the ring at the device's ring position
+    auto ring_append = [&](const int32_t* rows, const ResidRow* rr, const int64_t* f, int cnt) {
+        gather_rows_kernel<<<cnt, 256, 0, st>>>(rows, rr, nullptr, k, ring, ring_resid, 0, ring_cap, dstate);
+        ring_target_kernel<<<1, 1024, 0, st>>>(f, cnt, s->cfg.target_mode, ring_lp, 0, ring_cap, gstats, dstate);
+        ring_advance_kernel<<<1, 1, 0, st>>>(dstate, cnt, ring_cap);
+        ring_pos = (ring_pos + cnt) % ring_cap;
+        ring_valid = std::min(ring_cap, ring_valid + cnt);
     };
     GAPA_CUDA(cudaEventRecord(ev[0], st));
     GAPA_CUDA(cudaMemsetAsync(c->run_gen, 0, sizeof(int), st));
@@ -1389,60 +1463,45 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     exact[0] = mu;
     if (s) {  // the initial population enters the ring
         if ((rc = compute_resid(s, P[0], mu, k, st)) != GAPA_OK) return fail(rc);
-        gather_rows_kernel<<<mu, 256, 0, st>>>(P[0], s->resid, nullptr, k, ring, ring_resid, ring_pos, ring_cap);
-        ring_target_kernel<<<1, 1024, 0, st>>>(F[0], mu, s->cfg.target_mode, ring_lp, ring_pos, ring_cap, gstats);
-        ring_pos = (ring_pos + mu) % ring_cap;
-        ring_valid = std::min(ring_cap, ring_valid + mu);
+        ring_append(P[0], s->resid, F[0], mu);
     }
     GAPA_CUDA(cudaEventRecord(ev[1], st));
-    int cur = 0;
-    for (int g = 1; g <= G && rc == GAPA_OK; ++g) {
-        GaParams p = gapa_make_params(c, &c2, g, nullptr);
+    // One generation from P[cur] to P[cur ^ 1] (the generation index from the device counter).
+    auto generation = [&](int g, int cur, bool screen, bool diag, int* evaluated_out) -> int {
+        GaParams p = gapa_make_params(c, &c2, g, c->run_gen);
+        int rc2 = GAPA_OK;
         if (p.flags & GAPA_FLAG_ROULETTE) {
-            rc = gapa_launch_roulette_prefix(F[cur], mu, c->cum, st);
+            rc2 = gapa_launch_roulette_prefix(F[cur], mu, c->cum, st);
             p.cum = reinterpret_cast<const long long*>(c->cum);
         }
-        if (rc == GAPA_OK) rc = gapa_launch_children(c, p, lam, P[cur], F[cur], c->kids, st);
-        if (rc != GAPA_OK) break;
-        const bool screen = s && g > s->cfg.warmup && screened < lam;
-        const bool diag = s && s->cfg.diag_every > 0 && g % s->cfg.diag_every == 0 && diag_pred_host &&
-                          diag_exact_host && diag_rows + lam <= diag_cap;
+        if (rc2 == GAPA_OK) rc2 = gapa_launch_children(c, p, lam, P[cur], F[cur], c->kids, st);
+        if (rc2 != GAPA_OK) return rc2;
         int evaluated = lam;
-        if (screen || diag) rc = forward(s, c->kids, lam, k, false, st);
-        else if (s) rc = compute_resid(s, c->kids, lam, k, st);  // for the ring
-        if (rc == GAPA_OK && screen && !diag) {
+        if (screen || diag) rc2 = forward(s, c->kids, lam, k, false, st);
+        else if (s) rc2 = compute_resid(s, c->kids, lam, k, st);  // for the ring
+        if (rc2 == GAPA_OK && screen && !diag) {
             {
                 ProfileScope prof(c, st, 2, 2);
                 topk_kernel<<<1, 1024, (size_t)topk_P * 8, st>>>(s->y, lam, screened, sel, topk_P);
-                gather_rows_kernel<<<screened, 256, 0, st>>>(c->kids, s->resid, sel, k, sel_rows, sel_resid, 0, 0);
+                gather_rows_kernel<<<screened, 256, 0, st>>>(c->kids, s->resid, sel, k, sel_rows, sel_resid, 0, 0,
+                                                             nullptr);
             }
-            rc = gapa_launch_fitness(c, sel_rows, screened, k, fsel, st);
+            rc2 = gapa_launch_fitness(c, sel_rows, screened, k, fsel, st);
             {
                 ProfileScope prof(c, st, 2, 1);
                 scatter_fit_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const long long*>(fsel), sel, screened, lam,
                                                        reinterpret_cast<long long*>(c->kfit));
             }
             evaluated = screened;
-        } else if (rc == GAPA_OK) {
-            rc = gapa_launch_fitness(c, c->kids, lam, k, c->kfit, st);
+        } else if (rc2 == GAPA_OK) {
+            rc2 = gapa_launch_fitness(c, c->kids, lam, k, c->kfit, st);
         }
-        if (rc != GAPA_OK) break;
-        exact[g] = evaluated;
+        if (rc2 != GAPA_OK) return rc2;
+        *evaluated_out = evaluated;
         if (s) {  // evaluated children enter the ring
-            ProfileScope prof(c, st, 2, 2);
-            if (evaluated == lam) {
-                gather_rows_kernel<<<lam, 256, 0, st>>>(c->kids, s->resid, nullptr, k, ring, ring_resid, ring_pos,
-                                                        ring_cap);
-                ring_target_kernel<<<1, 1024, 0, st>>>(c->kfit, lam, s->cfg.target_mode, ring_lp, ring_pos, ring_cap,
-                                                       gstats);
-            } else {
-                gather_rows_kernel<<<evaluated, 256, 0, st>>>(sel_rows, sel_resid, nullptr, k, ring, ring_resid,
-                                                              ring_pos, ring_cap);
-                ring_target_kernel<<<1, 1024, 0, st>>>(fsel, evaluated, s->cfg.target_mode, ring_lp, ring_pos,
-                                                       ring_cap, gstats);
-            }
-            ring_pos = (ring_pos + evaluated) % ring_cap;
-            ring_valid = std::min(ring_cap, ring_valid + evaluated);
+            ProfileScope prof(c, st, 2, 3);
+            if (evaluated == lam) ring_append(c->kids, s->resid, c->kfit, lam);
+            else ring_append(sel_rows, sel_resid, fsel, evaluated);
         }
         if (diag) {
             // diagnostic generation: every child was evaluated exactly (and is used by the
@@ -1454,27 +1513,90 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
             GAPA_CUDA(cudaMemcpyAsync(diag_exact_host + diag_rows, c->kfit, (size_t)lam * 8, cudaMemcpyDeviceToHost, st));
             diag_rows += lam;
         }
-        rc = gapa_launch_mpl_replace(c, mu, lam, k, P[cur], F[cur], c->kids, c->kfit, c->src, P[cur ^ 1], F[cur ^ 1], st);
-        if (rc == GAPA_OK) rc = gapa_launch_record(c, F[cur ^ 1], mu, c->run_gen, c->run_traj, c->run_best, st);
-        cur ^= 1;
+        rc2 = gapa_launch_mpl_replace(c, mu, lam, k, P[cur], F[cur], c->kids, c->kfit, c->src, P[cur ^ 1], F[cur ^ 1],
+                                      st);
+        if (rc2 == GAPA_OK) rc2 = gapa_launch_record(c, F[cur ^ 1], mu, c->run_gen, c->run_traj, c->run_best, st);
         // online training on the ring
-        if (rc == GAPA_OK && s && ring_valid >= s->cfg.batch && s->cfg.train_steps > 0) {
+        if (rc2 == GAPA_OK && s && ring_valid >= s->cfg.batch && s->cfg.train_steps > 0) {
             if (s->cfg.target_mode == 0) {  // mode 1 keeps the identity statistics
                 ProfileScope prof(c, st, 2, 1);
-                target_stats_kernel<<<1, 1024, 0, st>>>(ring_lp, ring_valid, s->stats);
+                target_stats_kernel<<<1, 1024, 0, st>>>(ring_lp, ring_valid, s->stats, dstate + 1);
             }
-            for (int step = 0; step < s->cfg.train_steps && rc == GAPA_OK; ++step) {
+            for (int step = 0; step < s->cfg.train_steps && rc2 == GAPA_OK; ++step) {
                 {
                     ProfileScope prof(c, st, 2, 1);
                     batch_kernel<<<s->cfg.batch, 256, 0, st>>>(ring, ring_resid, ring_lp, ring_valid, k, s->cfg.batch,
                                                                s->key, step, g, s->stats, batch_rows, batch_resid,
-                                                               s->tbuf);
+                                                               s->tbuf, dstate + 1, c->run_gen);
                 }
-                rc = train_step(s, batch_rows, s->cfg.batch, k, s->tbuf, st, batch_resid);
+                rc2 = train_step(s, batch_rows, s->cfg.batch, k, s->tbuf, st, batch_resid, dstate + 2, bc_table,
+                                 bc_dev);
             }
         }
+        return rc2;
+    };
+    int cur = 0;
+    for (int g = 1; g <= G && rc == GAPA_OK; ++g) {
+        const bool screen = s && g > s->cfg.warmup && screened < lam;
+        const bool diag = s && s->cfg.diag_every > 0 && g % s->cfg.diag_every == 0 && diag_pred_host &&
+                          diag_exact_host && diag_rows + lam <= diag_cap;
+        // a screened generation that trains, once the ring holds a batch, is the same launch sequence
+        // every time: it is captured once per buffer parity and replayed (not while profiling, whose
+        // events go around single launches)
+        const bool steady = screen && !diag && ring_valid >= s->cfg.batch && s->cfg.train_steps > 0 &&
+                            !(cfg->flags & GAPA_FLAG_ROULETTE) && !c->profiling;
+        int evaluated = lam;
+        if (steady) {
+            if (!gexec[cur]) {
+                cudaGraph_t graph = nullptr;
+                const int shadow_pos = ring_pos, shadow_valid = ring_valid, shadow_tau = s->tau;
+                const cudaError_t be = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                if (be != cudaSuccess) {
+                    rc = gapa_cuda_fail(be, "capture of a screened generation");
+                    break;
+                }
+                c->capturing = true;
+                int crc = generation(g, cur, true, false, &evaluated);
+                cudaError_t ce = cudaStreamEndCapture(st, &graph);
+                c->capturing = false;
+                // capture ran no work: restore the host shadows it advanced
+                ring_pos = shadow_pos;
+                ring_valid = shadow_valid;
+                s->tau = shadow_tau;
+                if (crc != GAPA_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    rc = crc;
+                    break;
+                }
+                if (ce == cudaSuccess) ce = cudaGraphInstantiate(&gexec[cur], graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (ce != cudaSuccess) {
+                    rc = gapa_cuda_fail(ce, "capture of a screened generation");
+                    break;
+                }
+            }
+            const cudaError_t ce = cudaGraphLaunch(gexec[cur], st);
+            if (ce != cudaSuccess) {
+                rc = gapa_cuda_fail(ce, "replay of a screened generation");
+                break;
+            }
+            evaluated = screened;
+            ring_pos = (ring_pos + evaluated) % ring_cap;
+            ring_valid = std::min(ring_cap, ring_valid + evaluated);
+            s->tau += s->cfg.train_steps;
+        } else {
+            rc = generation(g, cur, screen, diag, &evaluated);
+            if (rc != GAPA_OK) break;
+        }
+        exact[g] = evaluated;
+        cur ^= 1;
         if (cudaEventRecord(ev[(size_t)g + 1], st) != cudaSuccess) rc = gapa_fail(GAPA_ERR_CUDA, "event record");
     }
+    for (auto& x : gexec)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
     if (rc != GAPA_OK) return fail(rc);
     GAPA_CUDA(cudaStreamSynchronize(st));
     int best = 0;
@@ -1496,7 +1618,12 @@ int gapa_run_surrogate(gapa_ctx* c, const gapa_config* cfg, gapa_surrogate* s, i
     int h = 0;
     cudaMemcpy(&h, c->status, 4, cudaMemcpyDeviceToHost);
     for (auto e : ev) cudaEventDestroy(e);
+    cudaFree(dstate);
+    cudaFree(bc_table);
     cleanup();
+    // later work on the caller's stream comes after the run
+    cudaEventRecord(c->ev_b, st);
+    cudaStreamWaitEvent(c->stream, c->ev_b, 0);
     if (h) {
         cudaMemset(c->status, 0, 4);
         return gapa_fail(GAPA_ERR_DEVICE, "device status 0x%x", h);

@@ -236,6 +236,42 @@ def test_screened_run_keeps_exact_fitness_and_plain_fallback_matches_mu_plus_lam
     ctx.close()
 
 
+def test_graph_replayed_generations_equal_launched_ones():
+    """Steady screened generations are replayed from CUDA graphs; with the context profiling every
+    launch they are launched one by one instead.  Both runs give the same trajectory, best set and
+    trained parameters bit for bit (the ring position, the valid rows, the generation and the AdamW
+    step come from the device in both), across an odd number of generations (both buffer parities
+    replayed) and a diagnostic generation in the middle."""
+    from paper_2412_20980_gb300 import FLAG_MU_PLUS_LAMBDA, Context, Surrogate, make_config, make_surrogate_config
+    from paper_2412_20980_gb300.gapa import run_surrogate
+
+    g = synth.ba_graph(5000, 3, 14)
+    ctx = Context(0)
+    ctx.graph_upload(g.row_ptr, g.col)
+    cfg = make_config(k=250, pop=64, gens=15, tourn=2, pc=0.8, pm=0.02, seed=9, flags=FLAG_MU_PLUS_LAMBDA, lam=256)
+    out = []
+    for profiled in (False, True):
+        sg = Surrogate(ctx, make_surrogate_config(screened=64, warmup=3, train_steps=2, batch=64, ring=2048,
+                                                  diag_every=7), seed=3)
+        if profiled:
+            ctx.profile_begin()
+        res = run_surrogate(ctx, cfg, sg, diag_cap=2 * 256)
+        if profiled:
+            ctx.profile_end()
+        res["params"] = sg.params()
+        sg.close()
+        out.append(res)
+    a, b = out
+    assert np.array_equal(a["traj"], b["traj"]) and a["best_fit"] == b["best_fit"]
+    assert np.array_equal(a["best_set"], b["best_set"])
+    assert np.array_equal(a["exact_evals"], b["exact_evals"])
+    assert np.array_equal(a["diag_exact"], b["diag_exact"]) and np.array_equal(a["diag_pred"], b["diag_pred"])
+    for name in a["params"]:
+        assert np.array_equal(a["params"][name], b["params"][name]), name
+    assert a["best_fit"] == oracle.pc(g.row_ptr, g.col, a["best_set"])
+    ctx.close()
+
+
 def test_diagnostic_pairs_recorded():
     from paper_2412_20980_gb300 import FLAG_MU_PLUS_LAMBDA, Context, Surrogate, make_config, make_surrogate_config
     from paper_2412_20980_gb300.gapa import run_surrogate
