@@ -82,7 +82,7 @@ WORKLOADS = {
                            "tournament 2, pc=0.8, pm=0.02, 300 generations; one step = one GA seed "
                            "(1000 rank + step) run plain (all 2048 children exact) and surrogate-screened: the 512 "
                            "lowest-scored children exact (the top 25 %), and beside it the 256 lowest-scored "
-                           "(12.5 %), after 3 warm-up generations; 2 AdamW steps of 512 rows per generation, lr 1e-3, "
+                           "(12.5 %), after 3 warm-up generations; 2 AdamW steps of 256 rows per generation, lr 1e-3, "
                            "on a 16384-row replay ring; targets z-scored over the ring; value = median over the steps "
                            "of the 25 % setting's speedup to the plain run's final best PC",
                       graphs=["ba_n100000_m3_seed1 (E=299991)"]),
@@ -781,7 +781,8 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
     screens = list(w["screens"])
 
     def scfg(diag_every=0, screened=None):
-        return make_surrogate_config(screened=screened or screens[0], warmup=3, train_steps=2, batch=512,
+        return make_surrogate_config(screened=screened or screens[0], warmup=3, train_steps=args.sur_steps,
+                                     batch=args.sur_batch,
                                      ring=16384, lr=1e-3, init_scale_emb=0.01, target_mode=0, diag_every=diag_every)
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -993,6 +994,8 @@ def main():
     ap.add_argument("--gens", type=int, default=0,
                     help="generations per run of the batched and surrogate workloads (default: the workload's; "
                          "shorter runs are for profiling, not for the reported line)")
+    ap.add_argument("--sur-steps", type=int, default=2, help="surrogate workload: AdamW steps per generation")
+    ap.add_argument("--sur-batch", type=int, default=256, help="surrogate workload: rows per AdamW step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")

@@ -404,7 +404,9 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
 #pragma unroll
             for (int e = 0; e < kSpLinkScan; ++e) {
                 if (w[e] < 0 || pw[e] == t || links == 2) continue;
-                sp_unite(cls, t + 1, sp_terminal_of(g, dead, hop, w[e], pw[e]) + 1);
+                const int b = sp_terminal_of(g, dead, hop, w[e], pw[e]);
+                if (b == t) continue;  // a neighbour chained to this terminal links nothing
+                sp_unite(cls, t + 1, b + 1);
                 ++links;
             }
         }

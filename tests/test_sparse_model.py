@@ -167,8 +167,10 @@ def sparse_eval(f, dead, objective="pc", stats=None, link=4, link_terminals_only
                 break
             if w in dead or f.tparent[w] == t:
                 continue
-            unite(a, terminal_of(w))
-            links += 1
+            b = terminal_of(w)
+            if b != a:  # a neighbour chained to the same terminal links nothing
+                unite(a, b)
+                links += 1
     # reference terminal per touched component
     weight = {}
     for t in tops:
