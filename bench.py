@@ -113,7 +113,7 @@ def graphs(workload: str):
     if workload == "batched":
         return [synth.ba_graph(d["n"], d["m"], d["graph_seed"]) for d in batched_specs()]
     if workload == "large":
-        return [synth.rmat_graph(20, 1 << 24, seed=1)]
+        return [synth.rmat_graph(RMAT_SCALE[0], 16 << RMAT_SCALE[0], seed=1)]
     if workload == "small":
         return [synth.ba_graph(1000, 3, 1)]
     if workload == "surrogate":
@@ -121,6 +121,15 @@ def graphs(workload: str):
     if workload == "sixdst":
         return [synth.er_graph(2018, 2705, 1)]
     return [synth.ba_graph(20000, 4, 1), synth.hk_graph(20000, 4, 0.3, 1)]
+
+
+# R-MAT scale of the large workload (20; smaller only for profiling captures, --rmat-scale):
+# 16 edges per node, k = 10000 scaled with the node count
+RMAT_SCALE = [20]
+
+
+def large_k() -> int:
+    return max(1, round(10000 * 2.0 ** (RMAT_SCALE[0] - 20)))
 
 
 def bytes_per_eval(n: int, num_edges: int, k: int) -> int:
@@ -171,12 +180,36 @@ def measured_peaks():
 
 
 # sources the fitness kernels of each workload are compiled from: the shared-memory kernels
-# (fitness.cu and its headers) and, for graphs whose labels exceed shared memory, the
-# interleaved-label kernels (fitness_ig.cu, dispatched from fitness.cu)
+# (fitness.cu and its headers) and, for graphs whose labels exceed shared memory, the sparse
+# kernel (fitness_sparse.cu, dispatched from fitness.cu)
 TRAFFIC_SOURCES = {
-    "large": ("fitness.cu", "fitness_ig.cu", "gapa_internal.cuh"),
+    "large": ("fitness.cu", "fitness_sparse.cu", "tree16.cuh", "gapa_internal.cuh"),
+    "surrogate": ("fitness.cu", "fitness_sparse.cu", "tree16.cuh", "gapa_internal.cuh"),
 }
 DEFAULT_TRAFFIC_SOURCES = ("fitness.cu", "tree16.cuh", "gapa_internal.cuh")
+
+
+KERNEL_TEXT = {
+    ("throughput", "auto"): "fitness phase: local_order_kernel + cc_smem_kernel<4> (cut-local TREE, two forests, "
+                            "estimates written by the operator kernel)",
+    ("small", "auto"): "cc_smem_kernel (full TREE pipeline, shared-memory labels; n <= 2048)",
+    ("large", "auto"): "cc_sparse_kernel<int> (sparse: re-picked tops, hop chains, sampled terminal links, listed "
+                       "pieces only; one persistent CTA per member)",
+    ("large", "tree"): "ig_* kernels (interleaved global labels, 8 members per 32-byte sector)",
+    ("throughput", "sparse"): "cc_sparse_kernel<unsigned short> (sparse kernel forced on a shared-memory graph)",
+    ("large", "sparse"): "cc_sparse_kernel<int>",
+}
+
+
+def measured_traffic_fraction(traffic: float, avg_launch_s: float) -> dict:
+    """DRAM bytes that ncu counted per fitness phase over the phase's duration, against the measured HBM
+    copy bandwidth: the graded figure where the algorithmic bytes (a full CSR pass per member)
+    overstate what a kernel that reads only the disturbed part of the graph moves."""
+    hbm, src = measured_peaks()
+    ach = traffic / avg_launch_s / 1e9
+    return {"achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per phase (profiles/fitness_traffic.json) "
+                     f"/ CUDA-event phase time; peak {src} HBM copy bandwidth"}
 
 
 def kernel_source_hash(workload: str) -> str:
@@ -427,7 +460,7 @@ def run_gapa(args, env: Env, gs):
     # operators and evaluates its slice of the children, fitness all-gathered; otherwise every
     # rank evolves its own populations
     split = args.mode == "split" and ws > 1 and wl in ("throughput", "large")
-    k, pop = w["k"], w["pop"]
+    k, pop = (large_k() if wl == "large" else w["k"]), w["pop"]
     pc, pm = (0.5, 0.3) if wl == "sixdst" else (PC, PM)
     seed = 0 if split else gd.rank_seed(0, rank)
     cfg = make_config(k=k, pop=pop, gens=w["gens"], tourn=TOURN, pc=pc, pm=pm, seed=seed)
@@ -531,15 +564,16 @@ def run_gapa(args, env: Env, gs):
         # launching stream around the phase
         avg_launch_s = fit_ms / 1000.0 / fit_calls
         achieved = beval * (fit_evals / fit_calls) / avg_launch_s / 1e9
+        traffic = ncu_traffic(wl) if RMAT_SCALE[0] == 20 else None
         roofline = memory_roofline(
             achieved, wl in ("throughput", "small"), ctxs[0],
-            traffic=ncu_traffic(wl),
-            kernel="fitness phase: local_order_kernel + cc_smem_kernel<4> (cut-local TREE, estimates written by the "
-                   "operator kernel) where the graph fits in shared memory and n > 2048, cc_smem_kernel (full TREE) "
-                   "for n <= 2048, ig_* kernels where the labels exceed shared memory",
+            traffic=traffic,
+            kernel=KERNEL_TEXT.get((wl, getattr(args, "fitness_kernel", "auto")), "fitness phase"),
             kernels_per_phase=fit_launches / fit_calls, bytes_per_eval=beval,
             evals_per_launch=fit_evals / fit_calls, avg_launch_ms=avg_launch_s * 1000,
             fitness_share_of_step=fit_ms / max(1e-9, total_ms))
+        if traffic:
+            roofline["measured"] = measured_traffic_fraction(traffic, avg_launch_s)
 
     # --- end to end through the C ABI with pinned host buffers ---
     e2e = None
@@ -861,11 +895,11 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
     beval = bytes_per_eval(g.n, g.num_edges, w["k"])
     roofline = None
     if prof["fitness_calls"]:
-        # the graph (1.2 M arcs) is L2-resident; labels live in global memory (interleaved groups)
+        # the graph (1.2 M arcs) is L2-resident; per-member state in the sparse kernel's global scratch
         avg_launch_s = prof["fitness_ms"] / 1e3 / prof["fitness_calls"]
         achieved = beval * prof["evals"] / prof["fitness_calls"] / avg_launch_s / 1e9
         roofline = memory_roofline(achieved, True, ctx, traffic=ncu_traffic("surrogate"),
-                                   kernel="fitness phase (screened children; interleaved global labels)",
+                                   kernel="fitness phase (screened children; cc_sparse_kernel<int>)",
                                    kernels_per_phase=prof["fitness_launches"] / prof["fitness_calls"],
                                    bytes_per_eval=beval, evals_per_launch=prof["evals"] / prof["fitness_calls"],
                                    avg_launch_ms=avg_launch_s * 1e3)
@@ -994,6 +1028,9 @@ def main():
     ap.add_argument("--gens", type=int, default=0,
                     help="generations per run of the batched and surrogate workloads (default: the workload's; "
                          "shorter runs are for profiling, not for the reported line)")
+    ap.add_argument("--rmat-scale", type=int, default=20,
+                    help="large workload: R-MAT scale (20; smaller for profiling captures: 16 edges per node, "
+                         "k = 10000 scaled with the nodes)")
     ap.add_argument("--sur-steps", type=int, default=2, help="surrogate workload: AdamW steps per generation")
     ap.add_argument("--sur-batch", type=int, default=256, help="surrogate workload: rows per AdamW step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1002,6 +1039,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads that the default line carries under 'workloads'")
     args = ap.parse_args()
+    RMAT_SCALE[0] = args.rmat_scale
     if args.warmup < 3 and args.impl == "gapa":
         log("warm-up raised to 3 steps")
         args.warmup = 3

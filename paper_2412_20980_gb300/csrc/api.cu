@@ -62,6 +62,7 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.sp_csize);
     cudaFree(g.sp_sub);
     cudaFree(g.sp_bysize);
+    cudaFree(g.sp_cost);
     g = DeviceGraph();
 }
 
@@ -681,6 +682,7 @@ void gapa_destroy(gapa_ctx* c) {
     cudaFree(c->labels);
     cudaFree(c->ig_aux);
     cudaFree(c->sp_scratch);
+    cudaFree(c->sp_order);
     cudaFree(c->sdst_buf);
     for (auto p : c->stage_pop) cudaFree(p);
     for (auto p : c->stage_fit) cudaFree(p);
@@ -735,6 +737,8 @@ int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
     std::stable_sort(roots.begin(), roots.end(), [&](int32_t a, int32_t b) { return csize[a] > csize[b]; });
     for (int32_t x = 0; x < n; ++x)
         if (csize[croot[x]] == 1) croot[x] = -1;  // a single-node component: nothing to recount
+    std::vector<int32_t> cost((size_t)n);  // by original id: children + 1
+    for (int32_t v = 0; v < n; ++v) cost[v] = kids[bf.perm[v]].y + 1;
     long long pc0 = 0;
     for (int32_t r : roots) pc0 += (long long)csize[r] * (csize[r] - 1) / 2;
     auto up = [](void** dst, const void* src, size_t bytes) {
@@ -744,7 +748,8 @@ int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
     if (!(up((void**)&g.sp_kids, kids.data(), sizeof(int2) * (size_t)n) &&
           up((void**)&g.sp_croot, croot.data(), 4 * (size_t)n) && up((void**)&g.sp_csize, csize.data(), 4 * (size_t)n) &&
           up((void**)&g.sp_sub, sub.data(), 4 * (size_t)n) &&
-          up((void**)&g.sp_bysize, roots.data(), 4 * roots.size()))) {
+          up((void**)&g.sp_bysize, roots.data(), 4 * roots.size()) &&
+          up((void**)&g.sp_cost, cost.data(), 4 * (size_t)n))) {
         cudaGetLastError();
         return gapa_fail(GAPA_ERR_OOM, "sparse fitness tables of %d nodes", n);
     }

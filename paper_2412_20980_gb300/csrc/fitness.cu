@@ -737,7 +737,7 @@ int gapa_fitness_prepare(gapa_ctx* c, int s) {
     const size_t lab_bytes = (size_t)c->g.n * 4;
     const bool tree = c->fitness_variant != GAPA_FITNESS_EDGES && c->fitness_variant != GAPA_FITNESS_SAMPLED;
     if (sparse_selected(c)) {
-        int rc = gapa_sparse_prepare(c);
+        int rc = gapa_sparse_prepare(c, s);
         if (rc != GAPA_OK) return rc;
     }
     if (tree) return (c->g.packed16 || lab_bytes <= c->fit_smem_max) ? GAPA_OK : gapa_ig_prepare(c, s);

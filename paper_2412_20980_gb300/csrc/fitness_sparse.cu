@@ -159,10 +159,53 @@ __device__ __forceinline__ int sp_terminal_of(const SpGraph<Col>& g, const unsig
     }
 }
 
+// Cost estimate of every member: the sum over its genes of (children + 1) in the BFS forest (the
+// tops its deletions make, plus itself), read through a table by original node id.
+__global__ void __launch_bounds__(128) sp_cost_kernel(const int* __restrict__ pop, int k, int n,
+                                                      const int* __restrict__ cost, unsigned* __restrict__ est) {
+    __shared__ unsigned long long part[4];
+    const int m = blockIdx.x, t = threadIdx.x;
+    const int* genes = pop + (size_t)m * k;
+    unsigned long long c = 0;
+    for (int j = t; j < k; j += 128) {
+        const int d = __ldg(&genes[j]);
+        if ((unsigned)d < (unsigned)n) c += (unsigned)__ldg(&cost[d]);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((t & 31) == 0) part[t >> 5] = c;
+    __syncthreads();
+    if (t == 0) {
+        const unsigned long long tot = part[0] + part[1] + part[2] + part[3];
+        est[m] = tot > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned)tot;
+    }
+}
+
+// Members by decreasing estimate (a counting sort on the estimate's bit length; one CTA), so that
+// the persistent CTAs take the costliest members first and none starts late.
+__global__ void __launch_bounds__(1024) sp_order_kernel(const unsigned* __restrict__ est, int s,
+                                                        int* __restrict__ order) {
+    __shared__ int cnt[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < s; m += blockDim.x) atomicAdd(&cnt[__clz(est[m])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < 33; ++c) {
+            const int x = cnt[c];
+            cnt[c] = acc;
+            acc += x;
+        }
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < s; m += blockDim.x) order[atomicAdd(&cnt[__clz(est[m])], 1)] = m;
+}
+
 template <typename Col>
 __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, SpSlot base, size_t stride,
                                                                const int* __restrict__ pop, int s, int k,
-                                                               long long* __restrict__ fit, int* head, int* status) {
+                                                               long long* __restrict__ fit, int* head, int* status,
+                                                               const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char sp_smem[];
     __shared__ long long red[32];
     __shared__ int s_member, s_nd, s_nt, s_nterm, s_ncl, s_gdel, s_nlist;
@@ -189,7 +232,8 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
 
     for (;;) {
         if (tid == 0) {
-            s_member = atomicAdd(head, 1);
+            const int q = atomicAdd(head, 1);
+            s_member = q < s && order ? order[q] : q;
             s_nd = 0;
             s_nt = 0;
             s_nterm = 0;
@@ -669,9 +713,14 @@ int gapa_sparse_init(gapa_ctx* c) {
 // counts, listed nodes, live tops, touched components: int32; per-component
 // sums and reference keys: int64), set to -1 / 0 once here and left that way
 // by every member.
-int gapa_sparse_prepare(gapa_ctx* c) {
+int gapa_sparse_prepare(gapa_ctx* c, int s) {
     const int n = c->g.n;
     const size_t stride = ((size_t)n + 63) & ~(size_t)63;
+    // member estimates and order (2 ints per member)
+    if ((size_t)2 * std::max(s, 1) > c->sp_order_cap) {
+        int rc = gapa_reserve((void**)&c->sp_order, &c->sp_order_cap, (size_t)2 * std::max(s, 1), sizeof(int));
+        if (rc != GAPA_OK) return rc;
+    }
     if (c->sp_scratch && c->sp_stride == stride) return GAPA_OK;  // (also inside a stream capture)
     const size_t smem = sp_smem_bytes(n, 0);
     int per_sm = 0;
@@ -701,7 +750,7 @@ int gapa_sparse_prepare(gapa_ctx* c) {
 int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
                                int* kernels) {
     if (!gapa_sparse_fits(c, k)) return gapa_fail(GAPA_ERR_INVALID_ARG, "sparse fitness: shared memory too small");
-    int rc = gapa_sparse_prepare(c);
+    int rc = gapa_sparse_prepare(c, s);
     if (rc != GAPA_OK) return rc;
     const size_t ints = (size_t)c->sp_slots * c->sp_stride;
     char* p = static_cast<char*>(c->sp_scratch);
@@ -718,14 +767,23 @@ int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, in
     GAPA_CUDA(cudaMemsetAsync(head, 0, sizeof(int), st));
     const size_t smem = sp_smem_bytes(c->g.n, k);
     const int grid = std::min(c->sp_slots, std::max(s, 1));
+    // more members than CTAs: the costliest first
+    const int* order = nullptr;
+    if (s > grid && c->g.sp_cost) {
+        unsigned* est = reinterpret_cast<unsigned*>(c->sp_order + s);
+        sp_cost_kernel<<<s, 128, 0, st>>>(pop, k, c->g.n, c->g.sp_cost, est);
+        sp_order_kernel<<<1, 1024, 0, st>>>(est, s, c->sp_order);
+        order = c->sp_order;
+    }
     if (c->g.packed16)
         cc_sparse_kernel<unsigned short><<<grid, kSpBlock, smem, st>>>(sp_graph(c, c->g.fcol16), b, c->sp_stride, pop, s,
                                                                         k, reinterpret_cast<long long*>(fit), head,
-                                                                        c->status);
+                                                                        c->status, order);
     else
         cc_sparse_kernel<int><<<grid, kSpBlock, smem, st>>>(sp_graph(c, (const int*)c->g.fcol32), b, c->sp_stride, pop,
-                                                             s, k, reinterpret_cast<long long*>(fit), head, c->status);
+                                                             s, k, reinterpret_cast<long long*>(fit), head, c->status,
+                                                             order);
     GAPA_CUDA(cudaGetLastError());
-    if (kernels) *kernels = 1;
+    if (kernels) *kernels = order ? 3 : 1;
     return GAPA_OK;
 }

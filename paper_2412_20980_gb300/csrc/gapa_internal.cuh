@@ -174,6 +174,7 @@ struct DeviceGraph {
     int* sp_csize = nullptr;
     int* sp_sub = nullptr;
     int* sp_bysize = nullptr;
+    int* sp_cost = nullptr;     // per original node id: its children in the forest + 1 (member cost estimates)
     int sp_ncomp = 0;
     int sp_giant = -1;          // root of the largest component
     long long sp_pc0 = 0;
@@ -203,6 +204,8 @@ struct gapa_ctx {
     size_t sp_stride = 0;        // entries per CTA slice
     int sp_slots = 0;            // CTA slices
     size_t sp_smem_max = 0;      // max dynamic shared memory of the sparse fitness kernel
+    int* sp_order = nullptr;     // the sparse kernel's member order, then the members' cost estimates
+    size_t sp_order_cap = 0;     // ints
     size_t labels_cap = 0;  // ints
     void* ig_aux = nullptr;  // per-member work counters and giant ids of the global-label fitness
     size_t ig_aux_cap = 0;
@@ -368,7 +371,7 @@ int gapa_ig_prepare(gapa_ctx* c, int s);
 // context's graph, its one-time set-up, its scratch (outside any capture) and its launch.
 bool gapa_sparse_fits(const gapa_ctx* c, int k);
 int gapa_sparse_init(gapa_ctx* c);
-int gapa_sparse_prepare(gapa_ctx* c);
+int gapa_sparse_prepare(gapa_ctx* c, int s);
 int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, int64_t* fit, cudaStream_t st,
                                int* kernels = nullptr);
 int gapa_launch_init(gapa_ctx* c, const GaParams& p, int32_t* pop, cudaStream_t st);

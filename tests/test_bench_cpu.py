@@ -79,8 +79,8 @@ def test_traffic_record_follows_its_sources(tmp_path, monkeypatch):
     (tmp_path / "profiles" / "fitness_traffic.json").write_text(json.dumps(rec))
     assert bench.ncu_traffic("throughput") == 1000 and bench.ncu_traffic("large") == 1001
     assert bench.ncu_traffic("sixdst") is None  # no record
-    # the interleaved-label source belongs to the large workload's kernels only
-    (csrc / "fitness_ig.cu").write_text("// changed\n")
+    # the sparse kernel's source belongs to the large workload's kernels only
+    (csrc / "fitness_sparse.cu").write_text("// changed\n")
     assert bench.ncu_traffic("throughput") == 1000 and bench.ncu_traffic("large") is None
     # a shared source invalidates both
     (csrc / "gapa_internal.cuh").write_text("// changed\n")
