@@ -224,27 +224,6 @@ __device__ __forceinline__ void resid_pair(const unsigned* bm, const int4* __res
     }
 }
 
-// The same with u's table entry already loaded (tu), so that several pairs' loads overlap: a u
-// whose first two neighbours are live is settled without another read.
-__device__ __forceinline__ void resid_pair_loaded(const unsigned* bm, const int4* __restrict__ T,
-                                                  const int* __restrict__ col, int v, int u, int4 tu, int& c0, int& c1,
-                                                  int& c2) {
-    if (u < 0 || bm_dead(bm, u)) return;
-    if (tu.w >= 0 && !bm_dead(bm, tu.z) && !bm_dead(bm, tu.w)) return;
-    int first_dead = -1, w = -1;
-    const int live = live_upto2(bm, T, col, u, &first_dead, &w);
-    if (live >= 2 || first_dead != v) return;
-    c0 += live == 0;
-    if (live == 1) {
-        c1 += 1;
-        int wl = -1;
-        const int4 tw = __ldg(T + w);
-        if ((u < w || tw.y == 1) && live_upto2(bm, T, col, w, nullptr, &wl) == 1) c2 += 1;
-    }
-}
-
-constexpr int kResidInFlight = 4;  // (gene, neighbour) pairs per lane whose loads overlap in resid_kernel
-
 __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop, int rows, int k, int n,
                                                     const int4* __restrict__ T, const int* __restrict__ col,
                                                     ResidRow* __restrict__ out) {
@@ -283,31 +262,19 @@ __global__ void __launch_bounds__(256) resid_kernel(const int* __restrict__ pop,
             if (lane >= o) incl += x;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        // kResidInFlight pairs per lane at a time: their neighbour ids, then their table entries,
-        // are loaded together
-        for (int base = 0; base < total; base += 32 * kResidInFlight) {
-            int ov[kResidInFlight], u[kResidInFlight];
-            int4 tu[kResidInFlight];
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            // owner = the first lane whose inclusive prefix exceeds idx
+            int lo = 0, hi = 31;
 #pragma unroll
-            for (int q = 0; q < kResidInFlight; ++q) {
-                const int idx = base + q * 32 + lane;
-                // owner = the first lane whose inclusive prefix exceeds idx
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int step = 0; step < 5; ++step) {
-                    const int mid = (lo + hi) >> 1;
-                    const int pm = __shfl_sync(0xffffffffu, incl, mid);
-                    if (pm > idx) hi = mid; else lo = mid + 1;
-                }
-                ov[q] = __shfl_sync(0xffffffffu, v, lo);
-                const int ob = __shfl_sync(0xffffffffu, b, lo), oi = __shfl_sync(0xffffffffu, incl, lo),
-                          od = __shfl_sync(0xffffffffu, d, lo);
-                u[q] = idx < total ? __ldg(col + ob + (idx - (oi - od))) : -1;
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const int pm = __shfl_sync(0xffffffffu, incl, mid);
+                if (pm > idx) hi = mid; else lo = mid + 1;
             }
-#pragma unroll
-            for (int q = 0; q < kResidInFlight; ++q) tu[q] = u[q] >= 0 ? __ldg(T + u[q]) : make_int4(0, 0, -1, -1);
-#pragma unroll
-            for (int q = 0; q < kResidInFlight; ++q) resid_pair_loaded(bm, T, col, ov[q], u[q], tu[q], c0, c1, c2);
+            const int ov = __shfl_sync(0xffffffffu, v, lo), ob = __shfl_sync(0xffffffffu, b, lo),
+                      oi = __shfl_sync(0xffffffffu, incl, lo), od = __shfl_sync(0xffffffffu, d, lo);
+            if (idx < total) resid_pair(bm, T, col, ov, __ldg(col + ob + (idx - (oi - od))), c0, c1, c2);
         }
         unsigned many = __ballot_sync(0xffffffffu, big);
         while (many) {
