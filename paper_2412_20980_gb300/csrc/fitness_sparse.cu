@@ -84,6 +84,7 @@ struct SpSlot {
     unsigned* cnt;             // terminals: chained subtree weight, then class size; 0 elsewhere
     int* list;                 // listed nodes
     int* tl;                   // live tops
+    int* th;                   // hop of the live top at the same position of tl (then its terminal)
     int* cl;                   // touched components (roots), single-node components excepted
     unsigned long long* cacc;  // component roots: deleted << 32 | nodes apart from R; 0 elsewhere
     unsigned long long* best;  // component roots whose root is deleted: weight << 32 | ~terminal
@@ -137,14 +138,17 @@ __device__ __forceinline__ void sp_unite(int* cls, int a, int b) {
     }
 }
 
-// Warp-aggregated append of v (where want) to a list; called by all lanes.
-__device__ __forceinline__ void sp_append(bool want, int v, int lane, int* count, int* list) {
+// Warp-aggregated append of v (where want) to a list; called by all lanes.  Returns v's
+// position (-1 where not wanted).
+__device__ __forceinline__ int sp_append(bool want, int v, int lane, int* count, int* list) {
     const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (!m) return;
+    if (!m) return -1;
     int first = 0;
     if (lane == 0) first = atomicAdd(count, __popc(m));
     first = __shfl_sync(0xffffffffu, first, 0);
-    if (want) list[first + __popc(m & ((1u << lane) - 1))] = v;
+    const int at = first + __popc(m & ((1u << lane) - 1));
+    if (want) list[at] = v;
+    return want ? at : -1;
 }
 
 // The terminal of live node w's piece: walk up to the first top (its terminal) or tree root.
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
     unsigned* const cnt = base.cnt + o;
     int* const list = base.list + o;
     int* const tl = base.tl + o;
+    int* const th = base.th + o;
     int* const cl = base.cl + o;
     unsigned long long* const cacc = base.cacc + o;
     unsigned long long* const best = base.best + o;
@@ -359,60 +364,71 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
 #pragma unroll
             for (int u = 0; u < F; ++u) {
                 if (t[u] < 0) continue;
-                if (q[u] == t[u]) {
-                    hop[t[u]] = t[u];
-                    continue;
-                }
-                int x = q[u], p = y[u];  // walk up to the first top or tree root
-                while (p != x && !bm_test(dead, p)) {
-                    x = p;
-                    p = __ldg(&g.tparent[x]);
+                int x = q[u];
+                if (q[u] != t[u]) {
+                    int p = y[u];  // walk up to the first top or tree root
+                    while (p != x && !bm_test(dead, p)) {
+                        x = p;
+                        p = __ldg(&g.tparent[x]);
+                    }
                 }
                 hop[t[u]] = x;
+                y[u] = x;
             }
 #pragma unroll
-            for (int u = 0; u < F; ++u) sp_append(t[u] >= 0, t[u], lane, &s_nt, tl);
+            for (int u = 0; u < F; ++u) {
+                const int at = sp_append(t[u] >= 0, t[u], lane, &s_nt, tl);
+                if (at >= 0) th[at] = y[u];
+            }
         }
         tm.sync();
         const int nt = s_nt;
-        // terminal of every top by pointer jumping (hop <- hop of hop until no hop changes)
-        for (;;) {
-            bool changed = false;
-            for (int j0 = tid; j0 < nt; j0 += F * T) {
-                int t[F], x[F], h[F];
-#pragma unroll
-                for (int u = 0; u < F; ++u) t[u] = j0 + u * T < nt ? ldcg(&tl[j0 + u * T]) : -1;
-#pragma unroll
-                for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
-#pragma unroll
-                for (int u = 0; u < F; ++u) h[u] = (t[u] >= 0 && x[u] != t[u]) ? ldcg(&hop[x[u]]) : -1;
-#pragma unroll
-                for (int u = 0; u < F; ++u)
-                    if (h[u] != -1 && h[u] != x[u]) {  // x is neither a tree root nor a terminal top
-                        hop[t[u]] = h[u];
-                        changed = true;
-                    }
-            }
-            if (!__syncthreads_or(changed)) break;
-        }
-        // terminals: tops that re-picked nothing start their class and are listed densely (in
-        // `list`, free until the listing); subtree weight of the chained tops at terminals whose
+        // terminal of every top: its hop chain followed (F tops per thread together, chains of a few
+        // hops) and compressed; tops that re-picked nothing start their class and are listed densely
+        // (in `list`, free until the listing); subtree weight of the chained tops at terminals whose
         // component root is deleted
         for (int base_j = 0; base_j < nt; base_j += F * T) {
             int t[F], x[F];
+            bool act[F];
 #pragma unroll
             for (int u = 0; u < F; ++u) {
                 const int j = base_j + u * T + tid;
                 t[u] = j < nt ? ldcg(&tl[j]) : -1;
+                x[u] = j < nt ? ldcg(&th[j]) : -1;
             }
+            bool any = false;
 #pragma unroll
-            for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
+            for (int u = 0; u < F; ++u) {
+                act[u] = t[u] >= 0 && x[u] != t[u];
+                any |= act[u];
+            }
+            while (any) {
+                int h[F];
+#pragma unroll
+                for (int u = 0; u < F; ++u) h[u] = act[u] ? ldcg(&hop[x[u]]) : 0;
+                any = false;
+#pragma unroll
+                for (int u = 0; u < F; ++u) {
+                    if (!act[u]) continue;
+                    if (h[u] == -1 || h[u] == x[u]) {  // a tree root or a top that re-picked nothing
+                        act[u] = false;
+                    } else {
+                        x[u] = h[u];
+                        any = true;
+                    }
+                }
+            }
 #pragma unroll
             for (int u = 0; u < F; ++u) {
                 int key = -1;
                 unsigned wgt = 0;
                 const bool term = t[u] >= 0 && x[u] == t[u];
-                if (term) cls[t[u]] = t[u] + 1;
+                if (term) {
+                    cls[t[u]] = t[u] + 1;
+                } else if (t[u] >= 0) {
+                    hop[t[u]] = x[u];
+                    th[base_j + u * T + tid] = x[u];
+                }
                 if (t[u] >= 0) {
                     // x is a top that re-picked nothing, or a live tree root (never weighed)
                     const int cx = __ldg(&g.croot[x[u]]);
@@ -499,9 +515,8 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
             for (int u = 0; u < F; ++u) {
                 const int j = base_j + u * T + tid;
                 t[u] = j < nt ? ldcg(&tl[j]) : -1;
+                x[u] = j < nt ? ldcg(&th[j]) : -1;
             }
-#pragma unroll
-            for (int u = 0; u < F; ++u) x[u] = t[u] >= 0 ? ldcg(&hop[t[u]]) : -1;
             int cx[F];
 #pragma unroll
             for (int u = 0; u < F; ++u) cx[u] = t[u] >= 0 ? ldcg(&cls[x[u]]) : 0;
@@ -709,10 +724,10 @@ int gapa_sparse_init(gapa_ctx* c) {
     return rc;
 }
 
-// Scratch of the persistent CTAs: eight n-entry arrays per CTA (hops, classes,
-// counts, listed nodes, live tops, touched components: int32; per-component
-// sums and reference keys: int64), set to -1 / 0 once here and left that way
-// by every member.
+// Scratch of the persistent CTAs: nine n-entry arrays per CTA (hops, classes,
+// counts, listed nodes, live tops, their hops, touched components: int32;
+// per-component sums and reference keys: int64), set to -1 / 0 once here and
+// left that way by every member.
 int gapa_sparse_prepare(gapa_ctx* c, int s) {
     const int n = c->g.n;
     const size_t stride = ((size_t)n + 63) & ~(size_t)63;
@@ -727,7 +742,7 @@ int gapa_sparse_prepare(gapa_ctx* c, int s) {
     GAPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cc_sparse_kernel<int>, kSpBlock, smem));
     if (per_sm < 1) per_sm = 1;
     const int slots = c->num_sms * per_sm;
-    const size_t bytes = (size_t)slots * stride * (6 * 4 + 2 * 8) + 64;
+    const size_t bytes = (size_t)slots * stride * (7 * 4 + 2 * 8) + 64;
     cudaFree(c->sp_scratch);
     c->sp_scratch = nullptr;
     c->sp_scratch_cap = 0;
@@ -740,9 +755,9 @@ int gapa_sparse_prepare(gapa_ctx* c, int s) {
     c->sp_slots = slots;
     const size_t ints = (size_t)slots * stride;
     char* p = static_cast<char*>(c->sp_scratch);
-    // hop, cls = -1; cnt, list, tl, cl = 0; cacc, best = 0; the queue head last
+    // hop, cls = -1; cnt, list, tl, th, cl = 0; cacc, best = 0; the queue head last
     GAPA_CUDA(cudaMemset(p, 0xFF, ints * 8));
-    GAPA_CUDA(cudaMemset(p + ints * 8, 0, ints * 16 + ints * 16 + 64));
+    GAPA_CUDA(cudaMemset(p + ints * 8, 0, ints * 20 + ints * 16 + 64));
     GAPA_CUDA(cudaDeviceSynchronize());
     return GAPA_OK;
 }
@@ -760,10 +775,11 @@ int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, in
     b.cnt = reinterpret_cast<unsigned*>(p + ints * 8);
     b.list = reinterpret_cast<int*>(p + ints * 12);
     b.tl = reinterpret_cast<int*>(p + ints * 16);
-    b.cl = reinterpret_cast<int*>(p + ints * 20);
-    b.cacc = reinterpret_cast<unsigned long long*>(p + ints * 24);
-    b.best = reinterpret_cast<unsigned long long*>(p + ints * 32);
-    int* head = reinterpret_cast<int*>(p + ints * 40);
+    b.th = reinterpret_cast<int*>(p + ints * 20);
+    b.cl = reinterpret_cast<int*>(p + ints * 24);
+    b.cacc = reinterpret_cast<unsigned long long*>(p + ints * 28);
+    b.best = reinterpret_cast<unsigned long long*>(p + ints * 36);
+    int* head = reinterpret_cast<int*>(p + ints * 44);
     GAPA_CUDA(cudaMemsetAsync(head, 0, sizeof(int), st));
     const size_t smem = sp_smem_bytes(c->g.n, k);
     const int grid = std::min(c->sp_slots, std::max(s, 1));
