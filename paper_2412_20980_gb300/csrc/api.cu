@@ -57,12 +57,14 @@ void free_graph(DeviceGraph& g) {
     cudaFree(g.lo_ptr);
     cudaFree(g.lo_col);
     cudaFree(g.palt);
-    cudaFree(g.sp_kids);
-    cudaFree(g.sp_croot);
-    cudaFree(g.sp_csize);
-    cudaFree(g.sp_sub);
-    cudaFree(g.sp_bysize);
-    cudaFree(g.sp_cost);
+    for (SparseForest& f : g.spf) {
+        void* tabs[] = {f.kids, f.croot, f.csize, f.sub, f.bysize, f.cost};
+        for (void* q : tabs) cudaFree(q);
+        if (f.owns) {
+            void* own[] = {f.perm, f.tparent, f.palt, f.lo_ptr, f.lo_col, f.fptr, f.fcol32, f.fcol16};
+            for (void* q : own) cudaFree(q);
+        }
+    }
     g = DeviceGraph();
 }
 
@@ -710,19 +712,23 @@ int gapa_set_stream(gapa_ctx* c, void* s) {
     return GAPA_OK;
 }
 
-// Tables of the sparse fitness kernel from the BFS forest: children as (first, count) (BFS
-// numbers them consecutively), the root of every node's tree (in BFS order every component is one
-// tree; -1 for single-node components), component sizes at their roots, subtree sizes, the roots
-// by decreasing size (ties: lower root) and the sum over components of C(size, 2).  Left null if
-// some node's children are not consecutive.
-int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
+// A forest of the sparse fitness kernel from a BFS forest of G (or of G without some hubs' edges):
+// children as (first, count) (BFS numbers them consecutively), the root of every node's tree (in BFS
+// order every component is one tree; -1 for single-node components), component sizes at their
+// roots, subtree sizes, the roots by decreasing size (ties: lower root), the per-member cost table
+// by original id (children + 1) and the sum over components of C(size, 2).  With `own`, also the
+// forest's numbering, parents, parent pairs and lower-neighbour and full adjacency in its
+// numbering (rp, col: the graph it was built from).  Returns 1 (nothing uploaded) if some node's
+// children are not consecutive.
+int upload_sparse_forest(const BfsForest& bf, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                         int32_t n, bool own, bool packed16, SparseForest& f) {
     std::vector<int2> kids((size_t)n, make_int2(0, 0));
     for (int32_t x = 0; x < n; ++x) {
         const int32_t p = bf.tparent[x];
         if (p == x) continue;
         int2& kp = kids[p];
         if (kp.y == 0) kp.x = x;
-        else if (kp.x + kp.y != x) return GAPA_OK;  // not consecutive: no sparse kernel on this graph
+        else if (kp.x + kp.y != x) return 1;  // not consecutive: no sparse kernel on this forest
         kp.y += 1;
     }
     std::vector<int32_t> croot((size_t)n), csize((size_t)n, 0), sub((size_t)n, 1), roots;
@@ -745,17 +751,95 @@ int upload_sparse_tables(const BfsForest& bf, int32_t n, DeviceGraph& g) {
         return cudaMalloc(dst, std::max<size_t>(bytes, 16)) == cudaSuccess &&
                (bytes == 0 || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess);
     };
-    if (!(up((void**)&g.sp_kids, kids.data(), sizeof(int2) * (size_t)n) &&
-          up((void**)&g.sp_croot, croot.data(), 4 * (size_t)n) && up((void**)&g.sp_csize, csize.data(), 4 * (size_t)n) &&
-          up((void**)&g.sp_sub, sub.data(), 4 * (size_t)n) &&
-          up((void**)&g.sp_bysize, roots.data(), 4 * roots.size()) &&
-          up((void**)&g.sp_cost, cost.data(), 4 * (size_t)n))) {
-        cudaGetLastError();
-        return gapa_fail(GAPA_ERR_OOM, "sparse fitness tables of %d nodes", n);
+    bool ok = up((void**)&f.kids, kids.data(), sizeof(int2) * (size_t)n) &&
+              up((void**)&f.croot, croot.data(), 4 * (size_t)n) && up((void**)&f.csize, csize.data(), 4 * (size_t)n) &&
+              up((void**)&f.sub, sub.data(), 4 * (size_t)n) && up((void**)&f.bysize, roots.data(), 4 * roots.size()) &&
+              up((void**)&f.cost, cost.data(), 4 * (size_t)n);
+    if (ok && own) {
+        f.owns = true;
+        std::vector<int2> palt((size_t)n);
+        for (int32_t b = 0; b < n; ++b) {
+            const int32_t cnt = bf.lo_ptr[b + 1] - bf.lo_ptr[b];
+            palt[b] = make_int2(bf.tparent[b], cnt >= 2 ? bf.lo_col[bf.lo_ptr[b] + 1] : -1);
+        }
+        std::vector<int32_t> inv((size_t)n), fptr((size_t)n + 1, 0), fcol(std::max<size_t>(col.size(), 1));
+        for (int32_t v = 0; v < n; ++v) inv[bf.perm[v]] = v;
+        for (int32_t b = 0; b < n; ++b) {
+            const int32_t v = inv[b];
+            int32_t o = fptr[b];
+            for (int32_t e = rp[v]; e < rp[v + 1]; ++e) fcol[o++] = bf.perm[col[e]];
+            fptr[b + 1] = o;
+        }
+        ok = up((void**)&f.perm, bf.perm.data(), 4 * (size_t)n) && up((void**)&f.tparent, bf.tparent.data(), 4 * (size_t)n) &&
+             up((void**)&f.palt, palt.data(), sizeof(int2) * (size_t)n) &&
+             up((void**)&f.lo_ptr, bf.lo_ptr.data(), 4 * ((size_t)n + 1)) &&
+             up((void**)&f.lo_col, bf.lo_col.data(), 4 * bf.lo_col.size()) &&
+             up((void**)&f.fptr, fptr.data(), 4 * ((size_t)n + 1));
+        if (ok && packed16) {
+            std::vector<uint16_t> f16(fcol.begin(), fcol.end());
+            ok = up((void**)&f.fcol16, f16.data(), 2 * f16.size());
+        } else if (ok) {
+            ok = up((void**)&f.fcol32, fcol.data(), 4 * fcol.size());
+        }
     }
-    g.sp_ncomp = (int)roots.size();
-    g.sp_giant = roots.empty() ? -1 : roots[0];
-    g.sp_pc0 = pc0;
+    if (!ok) {
+        cudaGetLastError();
+        return gapa_fail(GAPA_ERR_OOM, "sparse fitness forest of %d nodes", n);
+    }
+    f.ncomp = (int)roots.size();
+    f.giant = roots.empty() ? -1 : roots[0];
+    f.pc0 = pc0;
+    return GAPA_OK;
+}
+
+// The sparse kernel's forests: forest 0 on G (borrowing the graph's BFS arrays), then forests of G
+// with every edge of the top hub, of the two top hubs, and of the second hub removed (the hubs by
+// degree; a member that deletes them has the same PC on either graph, and in the reduced graph's
+// forest deleting them cuts nothing).
+int upload_sparse_forests(const BfsForest& bf, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                          const std::vector<int32_t>& by_degree, int32_t n, DeviceGraph& g) {
+    SparseForest& f0 = g.spf[0];
+    f0.perm = g.perm;
+    f0.tparent = g.tparent;
+    f0.palt = g.palt;
+    f0.lo_ptr = g.lo_ptr;
+    f0.lo_col = g.lo_col;
+    f0.fptr = g.fptr;
+    f0.fcol32 = g.fcol32;
+    f0.fcol16 = g.fcol16;
+    int rc = upload_sparse_forest(bf, rp, col, n, false, g.packed16, f0);
+    if (rc == 1) {  // no sparse kernel on this graph
+        f0 = SparseForest();
+        return GAPA_OK;
+    }
+    if (rc != GAPA_OK) return rc;
+    g.sp_nforests = 1;
+    for (int i = 0; i < 2; ++i) {
+        const int32_t h = i < (int)by_degree.size() ? by_degree[i] : -1;
+        g.sp_hub[i] = (h >= 0 && rp[h + 1] > rp[h]) ? h : -1;
+    }
+    // removed hubs of forests 1, 2, 3
+    const int32_t removed[3][2] = {{g.sp_hub[0], -1}, {g.sp_hub[0], g.sp_hub[1]}, {g.sp_hub[1], -1}};
+    for (int fi = 1; fi < kSpForests; ++fi) {
+        const int32_t a = removed[fi - 1][0], b = removed[fi - 1][1];
+        if (a < 0 || (fi == 2 && b < 0)) continue;
+        std::vector<int32_t> rp2((size_t)n + 1, 0), col2;
+        col2.reserve(col.size());
+        for (int32_t v = 0; v < n; ++v) {
+            if (v != a && v != b)
+                for (int32_t e = rp[v]; e < rp[v + 1]; ++e)
+                    if (col[e] != a && col[e] != b) col2.push_back(col[e]);
+            rp2[v + 1] = (int32_t)col2.size();
+        }
+        const BfsForest bf2 = bfs_forest(n, rp2, col2);
+        rc = upload_sparse_forest(bf2, rp2, col2, n, true, g.packed16, g.spf[fi]);
+        if (rc == 1) {
+            g.spf[fi] = SparseForest();
+            continue;
+        }
+        if (rc != GAPA_OK) return rc;
+    }
+    g.sp_nforests = kSpForests;
     return GAPA_OK;
 }
 
@@ -941,13 +1025,7 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     }
     if (!bf.lo_col.empty())
         GAPA_CUDA(cudaMemcpy(g.lo_col, bf.lo_col.data(), sizeof(int32_t) * bf.lo_col.size(), cudaMemcpyHostToDevice));
-    {
-        const int frc = upload_sparse_tables(bf, n, g);
-        if (frc != GAPA_OK) {
-            free_graph(g);
-            return frc;
-        }
-    }
+
     {
         // full adjacency in BFS numbers (the scans of the nodes outside the giant piece): 16-bit ids
         // for the shared-memory kernel, 32-bit ids for the global-label one
@@ -986,6 +1064,13 @@ int gapa_graph_upload(gapa_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
         std::vector<int2> w(bf.nontree.size());
         for (size_t i = 0; i < w.size(); ++i) w[i] = make_int2(bf.nontree[i].first, bf.nontree[i].second);
         if (!w.empty()) GAPA_CUDA(cudaMemcpy(g.nontree, w.data(), 8 * w.size(), cudaMemcpyHostToDevice));
+    }
+    {
+        const int frc = upload_sparse_forests(bf, rp, sorted, order, n, g);
+        if (frc != GAPA_OK) {
+            free_graph(g);
+            return frc;
+        }
     }
     c->g = g;
     return GAPA_OK;

@@ -728,7 +728,7 @@ int launch_piece(gapa_ctx* c, const GraphArgs& ga, const int32_t* pop, int s, in
 
 // The sparse kernel: on request, and by AUTO where the labels exceed shared memory.
 static bool sparse_selected(const gapa_ctx* c) {
-    return c->g.sp_kids != nullptr &&
+    return c->g.sp_nforests > 0 &&
            (c->fitness_variant == GAPA_FITNESS_SPARSE ||
             (c->fitness_variant == GAPA_FITNESS_AUTO && !c->g.packed16 && (size_t)c->g.n * 4 > c->fit_smem_max));
 }

@@ -52,6 +52,8 @@ using gapa_dev::tree16l_scan;
 constexpr int kSpBlock = 1024;
 constexpr int kSpLinkScan = 4;              // adjacency entries a top samples for links
 constexpr int kSpInFlight = 4;              // tops per thread resolved together in the re-pick pass
+constexpr int kSpForestShift = 28;          // order entry: member | forest << 28
+constexpr int kSpMemberMask = (1 << kSpForestShift) - 1;
 
 template <typename Col>
 struct SpGraph {
@@ -72,6 +74,13 @@ struct SpGraph {
     int giant;            // root of the largest component
     long long pc0;        // sum over components of C(size, 2)
     int objective;        // 0: PC, 1: MCN
+};
+
+// The forests of one graph (forest 0 on G; 1, 2, 3 on G without the edges of the top hub, of the two
+// top hubs, of the second hub; an absent forest has kids == nullptr).
+template <typename Col>
+struct SpGraphs {
+    SpGraph<Col> f[kSpForests];
 };
 
 // One CTA's slice of the scratch (n entries each).  Reads go through L2 only
@@ -163,13 +172,39 @@ __device__ __forceinline__ int sp_terminal_of(const SpGraph<Col>& g, const unsig
     }
 }
 
-// Cost estimate of every member: the sum over its genes of (children + 1) in the BFS forest (the
-// tops its deletions make, plus itself), read through a table by original node id.
-__global__ void __launch_bounds__(128) sp_cost_kernel(const int* __restrict__ pop, int k, int n,
-                                                      const int* __restrict__ cost, unsigned* __restrict__ est) {
+// Forest of every member and its cost estimate: a member that deletes the top hub (h0) and / or the
+// second hub (h1) is evaluated on the forest of G without those hubs' edges, where deleting them cuts
+// nothing (forest 2: both, 1: h0, 3: h1, 0: neither; an absent forest falls back to forest 0); the
+// estimate is the sum over its genes of (children + 1) in that forest, read through a table by
+// original node id.
+struct SpCostArgs {
+    const int* cost[kSpForests];  // null: forest absent
+    int hub0, hub1;
+};
+
+__global__ void __launch_bounds__(128) sp_cost_kernel(const int* __restrict__ pop, int k, int n, SpCostArgs a,
+                                                      unsigned* __restrict__ est, int* __restrict__ forest) {
     __shared__ unsigned long long part[4];
+    __shared__ int s_f;
     const int m = blockIdx.x, t = threadIdx.x;
     const int* genes = pop + (size_t)m * k;
+    int h0 = 0, h1 = 0;
+    for (int j = t; j < k; j += 128) {
+        const int d = __ldg(&genes[j]);
+        h0 |= d == a.hub0;
+        h1 |= d == a.hub1;
+    }
+    h0 = __syncthreads_or(h0);
+    h1 = __syncthreads_or(h1);
+    if (t == 0) {
+        int f = 0;
+        if (h0 && h1 && a.cost[2]) f = 2;
+        else if (h0 && a.cost[1]) f = 1;
+        else if (h1 && a.cost[3]) f = 3;
+        s_f = f;
+    }
+    __syncthreads();
+    const int* cost = a.cost[s_f];
     unsigned long long c = 0;
     for (int j = t; j < k; j += 128) {
         const int d = __ldg(&genes[j]);
@@ -181,12 +216,15 @@ __global__ void __launch_bounds__(128) sp_cost_kernel(const int* __restrict__ po
     if (t == 0) {
         const unsigned long long tot = part[0] + part[1] + part[2] + part[3];
         est[m] = tot > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned)tot;
+        forest[m] = s_f;
     }
 }
 
 // Members by decreasing estimate (a counting sort on the estimate's bit length; one CTA), so that
-// the persistent CTAs take the costliest members first and none starts late.
-__global__ void __launch_bounds__(1024) sp_order_kernel(const unsigned* __restrict__ est, int s,
+// the persistent CTAs take the costliest members first and none starts late; entry = member |
+// forest << 28.
+__global__ void __launch_bounds__(1024) sp_order_kernel(const unsigned* __restrict__ est,
+                                                        const int* __restrict__ forest, int s,
                                                         int* __restrict__ order) {
     __shared__ int cnt[33];
     if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
@@ -202,19 +240,20 @@ __global__ void __launch_bounds__(1024) sp_order_kernel(const unsigned* __restri
         }
     }
     __syncthreads();
-    for (int m = threadIdx.x; m < s; m += blockDim.x) order[atomicAdd(&cnt[__clz(est[m])], 1)] = m;
+    for (int m = threadIdx.x; m < s; m += blockDim.x)
+        order[atomicAdd(&cnt[__clz(est[m])], 1)] = m | (forest[m] << kSpForestShift);
 }
 
 template <typename Col>
-__global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, SpSlot base, size_t stride,
-                                                               const int* __restrict__ pop, int s, int k,
-                                                               long long* __restrict__ fit, int* head, int* status,
-                                                               const int* __restrict__ order) {
+__global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(const __grid_constant__ SpGraphs<Col> gs, SpSlot base,
+                                                               size_t stride, const int* __restrict__ pop, int s,
+                                                               int k, long long* __restrict__ fit, int* head,
+                                                               int* status, const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char sp_smem[];
     __shared__ long long red[32];
-    __shared__ int s_member, s_nd, s_nt, s_nterm, s_ncl, s_gdel, s_nlist;
+    __shared__ int s_member, s_forest, s_nd, s_nt, s_nterm, s_ncl, s_gdel, s_nlist;
     const Team tm{(int)threadIdx.x, (int)blockDim.x, 0};
-    const int tid = tm.tid, T = tm.T, lane = tid & 31, n = g.n;
+    const int tid = tm.tid, T = tm.T, lane = tid & 31, n = gs.f[0].n;
     const int words = (n + 31) >> 5;
     unsigned* dead = reinterpret_cast<unsigned*>(sp_smem);
     int* D = reinterpret_cast<int*>(sp_smem + sp_bitmap_bytes(n));
@@ -238,7 +277,9 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
     for (;;) {
         if (tid == 0) {
             const int q = atomicAdd(head, 1);
-            s_member = q < s && order ? order[q] : q;
+            const int e = q < s ? order[q] : q;
+            s_member = q < s ? (e & kSpMemberMask) : q;
+            s_forest = q < s ? (e >> kSpForestShift) : 0;
             s_nd = 0;
             s_nt = 0;
             s_nterm = 0;
@@ -250,6 +291,7 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
         tm.sync();
         const int m = s_member;
         if (m >= s) break;
+        const SpGraph<Col>& g = gs.f[s_forest];  // this member's forest
         const int* genes = pop + (size_t)m * k;
 
         // 1. perturbation P^(A, p) of Eq. 13 in BFS numbering; distinct deleted nodes listed
@@ -688,32 +730,43 @@ __global__ void __launch_bounds__(kSpBlock, 1) cc_sparse_kernel(SpGraph<Col> g, 
 }
 
 template <typename Col>
-SpGraph<Col> sp_graph(const gapa_ctx* c, const Col* fcol) {
+SpGraph<Col> sp_graph(const gapa_ctx* c, const SparseForest& f, const Col* fcol) {
     SpGraph<Col> g;
     g.n = c->g.n;
-    g.perm = c->g.perm;
-    g.tparent = c->g.tparent;
-    g.palt = c->g.palt;
-    g.lo_ptr = c->g.lo_ptr;
-    g.lo_col = c->g.lo_col;
-    g.fptr = c->g.fptr;
+    g.perm = f.perm;
+    g.tparent = f.tparent;
+    g.palt = f.palt;
+    g.lo_ptr = f.lo_ptr;
+    g.lo_col = f.lo_col;
+    g.fptr = f.fptr;
     g.fcol = fcol;
-    g.kids = c->g.sp_kids;
-    g.croot = c->g.sp_croot;
-    g.csize = c->g.sp_csize;
-    g.sub = c->g.sp_sub;
-    g.bysize = c->g.sp_bysize;
-    g.ncomp = c->g.sp_ncomp;
-    g.giant = c->g.sp_giant;
-    g.pc0 = c->g.sp_pc0;
+    g.kids = f.kids;
+    g.croot = f.croot;
+    g.csize = f.csize;
+    g.sub = f.sub;
+    g.bysize = f.bysize;
+    g.ncomp = f.ncomp;
+    g.giant = f.giant;
+    g.pc0 = f.pc0;
     g.objective = c->objective;
     return g;
+}
+
+template <typename Col>
+SpGraphs<Col> sp_graphs(const gapa_ctx* c) {
+    SpGraphs<Col> gs;
+    for (int i = 0; i < kSpForests; ++i) {
+        const SparseForest& f = c->g.spf[i];
+        if constexpr (sizeof(Col) == 2) gs.f[i] = sp_graph<Col>(c, f, f.fcol16);
+        else gs.f[i] = sp_graph<Col>(c, f, reinterpret_cast<const Col*>(f.fcol32));
+    }
+    return gs;
 }
 
 }  // namespace
 
 bool gapa_sparse_fits(const gapa_ctx* c, int k) {
-    return c->g.sp_kids != nullptr && c->sp_smem_max > 0 && sp_smem_bytes(c->g.n, k) <= c->sp_smem_max;
+    return c->g.sp_nforests > 0 && c->sp_smem_max > 0 && sp_smem_bytes(c->g.n, k) <= c->sp_smem_max;
 }
 
 int gapa_sparse_init(gapa_ctx* c) {
@@ -731,9 +784,9 @@ int gapa_sparse_init(gapa_ctx* c) {
 int gapa_sparse_prepare(gapa_ctx* c, int s) {
     const int n = c->g.n;
     const size_t stride = ((size_t)n + 63) & ~(size_t)63;
-    // member estimates and order (2 ints per member)
-    if ((size_t)2 * std::max(s, 1) > c->sp_order_cap) {
-        int rc = gapa_reserve((void**)&c->sp_order, &c->sp_order_cap, (size_t)2 * std::max(s, 1), sizeof(int));
+    // member order, estimates and forests (3 ints per member)
+    if ((size_t)3 * std::max(s, 1) > c->sp_order_cap) {
+        int rc = gapa_reserve((void**)&c->sp_order, &c->sp_order_cap, (size_t)3 * std::max(s, 1), sizeof(int));
         if (rc != GAPA_OK) return rc;
     }
     if (c->sp_scratch && c->sp_stride == stride) return GAPA_OK;  // (also inside a stream capture)
@@ -783,23 +836,24 @@ int gapa_launch_fitness_sparse(gapa_ctx* c, const int32_t* pop, int s, int k, in
     GAPA_CUDA(cudaMemsetAsync(head, 0, sizeof(int), st));
     const size_t smem = sp_smem_bytes(c->g.n, k);
     const int grid = std::min(c->sp_slots, std::max(s, 1));
-    // more members than CTAs: the costliest first
-    const int* order = nullptr;
-    if (s > grid && c->g.sp_cost) {
-        unsigned* est = reinterpret_cast<unsigned*>(c->sp_order + s);
-        sp_cost_kernel<<<s, 128, 0, st>>>(pop, k, c->g.n, c->g.sp_cost, est);
-        sp_order_kernel<<<1, 1024, 0, st>>>(est, s, c->sp_order);
-        order = c->sp_order;
-    }
+    // every member's forest and cost estimate, then the members costliest first
+    unsigned* est = reinterpret_cast<unsigned*>(c->sp_order + s);
+    int* forest = c->sp_order + 2 * (size_t)s;
+    SpCostArgs ca;
+    for (int i = 0; i < kSpForests; ++i) ca.cost[i] = c->g.spf[i].kids ? c->g.spf[i].cost : nullptr;
+    ca.hub0 = c->g.sp_hub[0];
+    ca.hub1 = c->g.sp_hub[1];
+    sp_cost_kernel<<<s, 128, 0, st>>>(pop, k, c->g.n, ca, est, forest);
+    sp_order_kernel<<<1, 1024, 0, st>>>(est, forest, s, c->sp_order);
     if (c->g.packed16)
-        cc_sparse_kernel<unsigned short><<<grid, kSpBlock, smem, st>>>(sp_graph(c, c->g.fcol16), b, c->sp_stride, pop, s,
-                                                                        k, reinterpret_cast<long long*>(fit), head,
-                                                                        c->status, order);
+        cc_sparse_kernel<unsigned short><<<grid, kSpBlock, smem, st>>>(sp_graphs<unsigned short>(c), b, c->sp_stride,
+                                                                        pop, s, k, reinterpret_cast<long long*>(fit),
+                                                                        head, c->status, c->sp_order);
     else
-        cc_sparse_kernel<int><<<grid, kSpBlock, smem, st>>>(sp_graph(c, (const int*)c->g.fcol32), b, c->sp_stride, pop,
-                                                             s, k, reinterpret_cast<long long*>(fit), head, c->status,
-                                                             order);
+        cc_sparse_kernel<int><<<grid, kSpBlock, smem, st>>>(sp_graphs<int>(c), b, c->sp_stride, pop, s, k,
+                                                             reinterpret_cast<long long*>(fit), head, c->status,
+                                                             c->sp_order);
     GAPA_CUDA(cudaGetLastError());
-    if (kernels) *kernels = order ? 3 : 1;
+    if (kernels) *kernels = 3;
     return GAPA_OK;
 }

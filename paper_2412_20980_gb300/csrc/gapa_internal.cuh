@@ -115,6 +115,35 @@ struct DeviceForest {
     int* csize = nullptr;
 };
 
+// One BFS forest of the sparse fitness kernel (fitness_sparse.cu): numbering, tree parents, the
+// (tree parent, second lower neighbour) pairs, lower-neighbour and full adjacency CSR in its
+// numbering, and per node (first child, children), the root of its component tree (-1 for a
+// single-node component), the component's size at its root, subtree sizes, the component roots by
+// decreasing size, and by original id the member cost estimate (children + 1); the number of
+// components, the largest one's root and the sum over components of C(size, 2).  `owns`: the
+// numbering and adjacency arrays are this forest's own (forest 0 borrows the graph's).
+struct SparseForest {
+    int* perm = nullptr;
+    int* tparent = nullptr;
+    int2* palt = nullptr;
+    int* lo_ptr = nullptr;
+    int* lo_col = nullptr;
+    int* fptr = nullptr;
+    int* fcol32 = nullptr;
+    unsigned short* fcol16 = nullptr;
+    int2* kids = nullptr;
+    int* croot = nullptr;
+    int* csize = nullptr;
+    int* sub = nullptr;
+    int* bysize = nullptr;
+    int* cost = nullptr;
+    int ncomp = 0;
+    int giant = -1;
+    long long pc0 = 0;
+    bool owns = false;
+};
+constexpr int kSpForests = 4;
+
 struct DeviceGraph {
     int n = 0;
     long long nnz = 0;        // arcs = 2E
@@ -164,20 +193,13 @@ struct DeviceGraph {
     int mean_deg_x16 = 0;               // 16 * 2E / n, rounded up
     bool packed16 = false;      // n <= 65536
     int bfs_depth = 0;          // largest BFS level
-    // sparse fitness kernel (any n; null when the BFS forest's children are not consecutive):
-    // (first child, number of children), the root of every node's component tree (-1 for a
-    // single-node component), the component's size at its root, subtree sizes, the component
-    // roots by decreasing size, their number, the largest one and the sum over components of
-    // C(size, 2)
-    int2* sp_kids = nullptr;
-    int* sp_croot = nullptr;
-    int* sp_csize = nullptr;
-    int* sp_sub = nullptr;
-    int* sp_bysize = nullptr;
-    int* sp_cost = nullptr;     // per original node id: its children in the forest + 1 (member cost estimates)
-    int sp_ncomp = 0;
-    int sp_giant = -1;          // root of the largest component
-    long long sp_pc0 = 0;
+    // sparse fitness kernel (any n; sp_nforests = 0 when a BFS forest's children are not consecutive):
+    // forest 0 on G itself (borrowing the arrays above), and forests of G with every edge of the top
+    // hub (1), of the two top hubs (2) or of the second hub (3) removed, for members that delete those
+    // hubs (on which G and the reduced graph have the same PC); sp_hub = the two hubs' original ids
+    SparseForest spf[kSpForests];
+    int sp_nforests = 0;
+    int sp_hub[2] = {-1, -1};
 };
 
 constexpr int kProbe = 8;
@@ -204,7 +226,8 @@ struct gapa_ctx {
     size_t sp_stride = 0;        // entries per CTA slice
     int sp_slots = 0;            // CTA slices
     size_t sp_smem_max = 0;      // max dynamic shared memory of the sparse fitness kernel
-    int* sp_order = nullptr;     // the sparse kernel's member order, then the members' cost estimates
+    int* sp_order = nullptr;     // the sparse kernel's member order (member | forest << 28), then the
+                                 // members' cost estimates and forests
     size_t sp_order_cap = 0;     // ints
     size_t labels_cap = 0;  // ints
     void* ig_aux = nullptr;  // per-member work counters and giant ids of the global-label fitness

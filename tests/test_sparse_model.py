@@ -346,3 +346,34 @@ def test_sparse_model_links_keep_hub_deleting_lists_short():
     assert sparse_eval(f, dead, stats=every, link_terminals_only=False) == want
     assert linked["terminals"] > 50
     assert plain["listed"] > 10 * linked["listed"]
+
+
+def _without_edges_of(g, h):
+    """G' = G with every edge of node h removed (h stays, isolated)."""
+    u, v = g.edge_list()
+    keep = (u != h) & (v != h)
+    return synth.csr_from_edges(g.n, u[keep], v[keep])
+
+
+@pytest.mark.parametrize("name,g", _graphs()[:4], ids=lambda x: x if isinstance(x, str) else "")
+def test_sparse_model_on_the_graph_without_the_top_hub(name, g):
+    """A member that deletes the top hub h0 has the same PC and MCN on G and on G' = G without h0's
+    edges, and on G' the hub is an isolated node, so deleting it cuts nothing in G''s BFS forest: the
+    sparse kernel evaluates such members on G''s forest.  Checked on that forest against the
+    oracle on G, with h0 alone and with more of the top hubs, and the tops it saves."""
+    h0 = int(np.argmax(g.degrees()))
+    gp = _without_edges_of(g, h0)
+    f, fp = Forest(g), Forest(gp)
+    assert fp.tparent[fp.num[h0]] == fp.num[h0] and fp.csize[fp.num[h0]] == 1
+    top = np.argsort(-g.degrees(), kind="stable")
+    rng = np.random.default_rng(18)
+    for hubs in (1, 3, 10):
+        rest = rng.choice(top[hubs:], g.n // 20, replace=False)
+        genes = np.concatenate([top[:hubs], rest]).astype(np.int32)
+        st, stp = {}, {}
+        want = oracle.pc(g.row_ptr, g.col, genes)
+        assert sparse_eval(f, [f.num[int(v)] for v in genes], stats=st) == want
+        assert sparse_eval(fp, [fp.num[int(v)] for v in genes], stats=stp) == want
+        assert sparse_eval(fp, [fp.num[int(v)] for v in genes], "mcn") == oracle.mcn(g.row_ptr, g.col, genes)
+        if hubs == 1:
+            assert stp["tops"] < st["tops"]
