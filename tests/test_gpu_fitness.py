@@ -175,6 +175,28 @@ def test_global_label_path_hub_heavy(ctx, hubs):
     assert np.array_equal(gpu_fit(ctx, g, pop), want)
 
 
+@pytest.mark.parametrize("graph", ["rmat", "ba"])
+def test_top_hub_combinations(ctx, graph):
+    """Members deleting neither, the first, the second or both of the two highest-degree nodes, with
+    and without more hubs: the sparse kernel evaluates each on the forest of G without the deleted
+    top hubs' edges (every routing case), the other kernels on G; all equal the oracle."""
+    g = (synth.rmat_graph(17, 1 << 20, seed=4, chunk=1 << 20) if graph == "rmat"
+         else synth.ba_graph(30000, 3, 5))
+    top = np.argsort(-g.degrees(), kind="stable")
+    k = 600
+    rng = np.random.default_rng(19)
+    heads = [[], [0], [1], [0, 1], [1, 2, 3], [0, 2, 3, 4], [0, 1, 2, 3, 4, 5, 6, 7]]
+    rows = []
+    for h in heads:
+        for _ in range(3):
+            fixed = top[h].astype(np.int64)
+            rest = rng.choice(top[8:], k - len(fixed), replace=False)
+            rows.append(rng.permutation(np.concatenate([fixed, rest])))
+    pop = np.stack(rows).astype(np.int32)
+    want = oracle.fitness(g.row_ptr, g.col, pop, nthreads=oracle.max_threads())
+    assert np.array_equal(gpu_fit(ctx, g, pop), want)
+
+
 def test_adversarial_graphs(ctx):
     path = synth.named_graph("path", 30000)  # deep union-find chains
     pop = np.zeros((1, 0), dtype=np.int32)
