@@ -75,25 +75,41 @@ def test_forward_matches_reference(setup):
     assert _rel(y, same) < 1e-2, _rel(y, same)
 
 
-@pytest.mark.parametrize("graph", ["ba", "path", "star", "er"])
-def test_residual_counts_bit_exact(graph):
-    """r0 / r1 / r2 are integers: the GPU counts equal the reference's on random and adversarial sets."""
+@pytest.mark.parametrize("graph,k", [("ba", 300), ("path", 300), ("star", 300), ("er", 300), ("ba", 2900),
+                                     ("ba100k", 2000), ("rmat18", 300)])
+def test_residual_counts_bit_exact(graph, k):
+    """r0 / r1 / r2 are integers: the GPU counts equal the reference's on random and adversarial sets.
+
+    Cases: small graphs of every shape; BA n = 3000 with k = 2900 (almost everything deleted);
+    BA n = 100000 with k = 2000 (the surrogate workload's shape); R-MAT 2^18 (a 32 KB deletion
+    bitmap, hubs of degree near 10^4); and on each, the top hub's neighbours deleted so that it
+    keeps no live neighbour or one, where k allows."""
     import torch
 
     from paper_2412_20980_gb300 import Context, Surrogate, make_surrogate_config
 
     g = {"ba": lambda: synth.ba_graph(3000, 2, 6), "path": lambda: synth.named_graph("path", 5000),
-         "star": lambda: synth.named_graph("star", 2000), "er": lambda: synth.er_graph(4000, 6000, 3)}[graph]()
+         "star": lambda: synth.named_graph("star", 2000), "er": lambda: synth.er_graph(4000, 6000, 3),
+         "ba100k": lambda: synth.ba_graph(100000, 3, 6),
+         "rmat18": lambda: synth.rmat_graph(18, 4 << 18, seed=5)}[graph]()
     ctx = Context(0)
     ctx.graph_upload(g.row_ptr, g.col)
     sg = Surrogate(ctx, make_surrogate_config(batch=16, ring=1024), seed=1)
     rng = np.random.default_rng(2)
-    rows = [rng.choice(g.n, 300, replace=False) for _ in range(40)]
+    rows = [rng.choice(g.n, k, replace=False) for _ in range(40)]
     hubs = np.argsort(-g.degrees(), kind="stable")
-    rows.append(hubs[:300])  # the hubs: many isolated leaves
-    rows.append(np.arange(0, 600, 2)[:300])  # every other node of a prefix
-    rows.append(np.arange(0, 900, 3)[:300])  # every third node: isolated pairs on a path
-    pop = np.stack(rows).astype(np.int32)
+    rows.append(hubs[:k])  # the hubs: many isolated leaves
+    for step in (2, 3):  # every other node of a prefix; every third: isolated pairs on a path
+        if step * k <= g.n:
+            rows.append(np.arange(0, step * k, step))
+    leaves = np.asarray(g.col[g.row_ptr[hubs[0]]:g.row_ptr[hubs[0] + 1]])
+    for drop in (0, 1):  # the top hub left with no live neighbour, or with one, where k allows
+        r = leaves[drop:drop + k]
+        pool = rng.permutation(g.n)
+        pool = pool[~np.isin(pool, np.append(leaves, hubs[0]))]
+        rows.append(np.concatenate([r, pool[:k - len(r)]]))
+    pop = np.stack([np.asarray(r)[:k] for r in rows]).astype(np.int32)
+    assert all(len(set(r)) == k for r in pop)
     got = sg.residual(torch.from_numpy(pop).cuda()).cpu().numpy()
     want = np.array([sr.residual_degree_counts(g.row_ptr, g.col, r) for r in pop])
     assert np.array_equal(got, want)
