@@ -171,12 +171,36 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs a) {
 // larger adjacency together.  Genes outside [0, n) are ignored.
 __device__ __forceinline__ bool bm_dead(const unsigned* bm, int w) { return (bm[w >> 5] >> (w & 31)) & 1u; }
 
-// Per node: {first arc, degree, first neighbour, second neighbour} (-1 when absent).
+// Per node: {first arc, degree, a, b}: a and b are the two neighbours of lowest
+// degree (earlier arcs first among equals; -1 when absent).  Any two live
+// neighbours settle a node, and a deletion set that favours hubs is least likely
+// to hold u's lowest-degree neighbours.  One thread per node, once per surrogate.
 __global__ void nbr_table_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col, int n,
                                  int4* __restrict__ T) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         const int b = row_ptr[u], d = row_ptr[u + 1] - b;
-        T[u] = make_int4(b, d, d > 0 ? col[b] : -1, d > 1 ? col[b + 1] : -1);
+        int a1 = -1, a2 = -1, d1 = INT_MAX, d2 = INT_MAX;
+        for (int q0 = b; q0 < b + d; q0 += 4) {
+            int x[4], dx[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = q0 + i < b + d ? __ldg(col + q0 + i) : -1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dx[i] = x[i] >= 0 ? __ldg(row_ptr + x[i] + 1) - __ldg(row_ptr + x[i]) : INT_MAX;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (x[i] < 0) continue;
+                if (dx[i] < d1) {
+                    a2 = a1;
+                    d2 = d1;
+                    a1 = x[i];
+                    d1 = dx[i];
+                } else if (dx[i] < d2) {
+                    a2 = x[i];
+                    d2 = dx[i];
+                }
+            }
+        }
+        T[u] = make_int4(b, d, a1, a2);
     }
 }
 
@@ -208,7 +232,7 @@ struct __align__(16) ResidRow {
 
 // (u live) -> +1 to c0 or c1 when u has at most one live neighbour and v is its
 // first deleted one; +1 to c2 when that neighbour closes a two-node component.
-// Most live u keep their first two neighbours: one 16-byte table read settles them.
+// Most live u keep the two neighbours of their table entry: one 16-byte read settles them.
 __device__ __forceinline__ void resid_pair(const unsigned* bm, const int4* __restrict__ T,
                                            const int* __restrict__ col, int v, int u, int& c0, int& c1, int& c2) {
     if (bm_dead(bm, u)) return;
@@ -956,7 +980,7 @@ struct gapa_surrogate {
          *dZ1 = nullptr, *dZ1T = nullptr;
     float *y = nullptr, *dy = nullptr, *dX = nullptr, *loss = nullptr, *tbuf = nullptr;
     ResidRow* resid = nullptr;   // residual-degree counts (and their z) of the rows of the last forward
-    int4* nbr = nullptr;         // per node: first arc, degree, first two neighbours
+    int4* nbr = nullptr;         // per node: first arc, degree, its two lowest-degree neighbours
     const int* row_ptr = nullptr;  // the context's CSR (original node ids)
     const int* col = nullptr;
     size_t resid_smem = 0;       // deletion bitmap bytes of resid_kernel
