@@ -990,7 +990,7 @@ def run_surrogate_bench(args, gs, dist, ws, rank, local, dev):
 
 # workloads timed beside the headline in the default line: (steps, warm-up, CPU-baseline seconds)
 EXTRA = {"small": (20, 3, 3.0), "large": (5, 3, 3.0), "batched": (3, 3, 3.0), "sixdst": (10, 3, 3.0),
-         "surrogate": (2, 1, 3.0)}
+         "surrogate": (2, 3, 3.0)}
 EXTRA_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "gens_per_s", "evals_per_s", "roofline",
               "cpu_baseline", "e2e", "gpu_launches", "clocks", "by_screen", "surrogate_quality", "phase_split_ms")
 
@@ -1013,11 +1013,14 @@ def run_extra(args, env: Env) -> dict:
     return out
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for the throughput workload, else the workload's own count "
+                         "in the default line)")
+    ap.add_argument("--warmup", type=int, default=None,
+                    help="untimed warm-up steps, at least 3 (default: 5 for throughput, else the workload's own)")
     ap.add_argument("--impl", choices=["gapa", "reference"], default="gapa")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="throughput")
     ap.add_argument("--mode", choices=["split", "independent"], default="split",
@@ -1038,11 +1041,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads that the default line carries under 'workloads'")
-    args = ap.parse_args()
-    RMAT_SCALE[0] = args.rmat_scale
+    args = ap.parse_args(argv)
+    own = EXTRA.get(args.workload)
+    if args.steps is None:
+        args.steps = own[0] if own and args.workload != "throughput" else 200
+    if args.warmup is None:
+        args.warmup = own[1] if own and args.workload != "throughput" else 5
     if args.warmup < 3 and args.impl == "gapa":
         log("warm-up raised to 3 steps")
         args.warmup = 3
+    return args
+
+
+def main():
+    args = parse_args()
+    RMAT_SCALE[0] = args.rmat_scale
     if args.impl == "reference":
         return run_reference(args)
     env = setup()

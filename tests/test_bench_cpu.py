@@ -1,7 +1,7 @@
 """Host-side checks of bench.py: the reference arm's JSON line (the oracle on the host cores), its
-rank rule under several processes, the algorithmic bytes per evaluation used for the roofline, and
-the rule that a recorded DRAM-traffic figure is reported only while its kernel sources are the ones
-it was taken on.  No GPU is touched."""
+rank rule under several processes, the algorithmic bytes per evaluation used for the roofline, the
+rule that a recorded DRAM-traffic figure is reported only while its kernel sources are the ones it
+was taken on, and the step and warm-up counts each workload runs with.  No GPU is touched."""
 import json
 import os
 import subprocess
@@ -92,3 +92,18 @@ def test_workload_table_is_complete(wl):
     w = bench.WORKLOADS[wl]
     for key in ("metric", "unit", "desc", "graphs"):
         assert w[key], key
+
+
+def test_step_defaults_follow_the_workload():
+    a = bench.parse_args([])
+    assert (a.workload, a.steps, a.warmup, a.gpus) == ("throughput", 200, 5, 1)
+    for wl, (steps, warmup, _) in bench.EXTRA.items():
+        a = bench.parse_args(["--workload", wl])
+        assert (a.steps, a.warmup) == (steps, max(warmup, 3)), wl
+    a = bench.parse_args(["--workload", "surrogate", "--steps", "7", "--warmup", "1"])
+    assert (a.steps, a.warmup) == (7, 3)  # never fewer than three warm-up steps
+
+
+def test_every_reported_workload_warms_up_three_steps():
+    assert all(warmup >= 3 for _, warmup, _ in bench.EXTRA.values())
+
